@@ -1,0 +1,344 @@
+/*
+ * rich.h — C ABI of the GB300 Cherenkov-photon propagator.
+ *
+ * The library propagates Cherenkov photons through a RICH-like optical
+ * geometry: photons are emitted along charged tracks at cos(theta) = 1/(n*beta)
+ * (paper Sec. 3), carry a wavelength drawn from the Frank-Tamm 1/lambda^2
+ * spectrum, are traced through spherical and flat mirrors (analytic surfaces,
+ * or triangle meshes behind a BVH, as in the mesh scene of Sec. 4.1), are
+ * reflected with a wavelength-dependent reflectivity and accepted by a
+ * quantum-efficiency table (the binned efficiencies and accept/reject of
+ * Sec. 4.3, applied in flight as proposed in Sec. 6), and are recorded as a
+ * list of detector-plane positions relative to the plane's bottom-left corner
+ * (Sec. 4.4 and the hit-list detector proposed in Sec. 6) and binned into
+ * pixels.
+ *
+ * Conventions shared by every entry point
+ *   - Lengths are millimetres, wavelengths nanometres, momenta GeV/c, masses
+ *     GeV/c^2.
+ *   - "device" pointers are CUDA global-memory addresses on the context's
+ *     device; "host" pointers are ordinary CPU memory. The caller owns every
+ *     buffer it passes; the context owns the geometry, the BVH, the response
+ *     tables and its own scratch.
+ *   - Calls are ordered on the context's CUDA stream and are asynchronous
+ *     unless stated otherwise. Entry points that return counts to the host
+ *     (rich_emit with a non-NULL count pointer, rich_hits, rich_trace_grad)
+ *     synchronise that stream.
+ *   - Every entry point returns a rich_status and never throws. The message
+ *     of the last failure on a context is available from rich_last_error().
+ *     Device-side failures (hit-buffer overflow, a bounded wait that expired)
+ *     are recorded in a device status word and reported by the next call
+ *     that synchronises (rich_hits).
+ *   - Random numbers: every random draw is a Philox4x32-10 output (Salmon et
+ *     al., SC'11) with key = (seed_lo, seed_hi) and counter = (block, photon,
+ *     track id, event). Results therefore do not depend on launch shape,
+ *     batching or sharding. The draw map is:
+ *       per photon, block 0: w0 -> position along the track, w1 -> azimuth,
+ *                            w2 -> wavelength, w3 -> quantum-efficiency test
+ *       per photon, block 1: reflectivity tests at mirror reflections 0..3
+ *       per photon, block 2: reflectivity tests at mirror reflections 4..7
+ *       per photon, block 3: w0, w1 -> Gaussian smear of the hit (loss only)
+ *       per track (photon = 0xFFFFFFFF), blocks 0,1,...: Poisson sampler
+ *     A 32-bit word w maps to the uniform (w >> 8) * 2^-24 in [0, 1).
+ */
+#ifndef RICH_H
+#define RICH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+typedef enum rich_status {
+    RICH_OK = 0,
+    RICH_ERR_ARG = 1,       /* invalid argument (NULL, size, out of range)   */
+    RICH_ERR_CUDA = 2,      /* a CUDA runtime call failed                    */
+    RICH_ERR_OOM = 3,       /* device allocation failed                      */
+    RICH_ERR_OVERFLOW = 4,  /* an output buffer was too small (truncated)    */
+    RICH_ERR_TIMEOUT = 5,   /* a bounded device wait expired                 */
+    RICH_ERR_GEOMETRY = 6,  /* malformed geometry description                */
+    RICH_ERR_STATE = 7      /* call out of order (e.g. trace before geometry)*/
+} rich_status;
+
+/* ----------------------------------------------------- geometry description */
+enum { RICH_TABLE_CONST = 0, RICH_TABLE_GAUSS = 1, RICH_TABLE_HIST = 2 };
+enum { RICH_MAT_MIRROR = 0, RICH_MAT_ABSORBER = 1, RICH_MAT_DETECTOR = 2 };
+enum { RICH_MAT_SMOOTH = 1 }; /* material flag: triangles use vertex normals */
+
+#define RICH_TABLE_MAX_BINS 64
+#define RICH_SPHERE_MAX_EDGES 8
+#define RICH_MAX_BOUNCES 8   /* mirror reflections per photon (draw map)    */
+#define RICH_MAX_STEPS 16    /* surface interactions per photon             */
+
+/* Wavelength response (reflectivity or quantum efficiency), Sec. 4.3.
+ *   CONST: P = p0
+ *   GAUSS: P = p0 * exp(-((lambda - p1) / p2)^2)
+ *   HIST : P = values[clamp(floor((lambda - p0) / p1), 0, nbins - 1)]
+ *          (piecewise-constant histogram, e.g. 33 nm bins for QE and 25 nm
+ *           bins for reflectivity as in Sec. 4.3)
+ * P is evaluated in FP32. 280 bytes. */
+typedef struct rich_table {
+    int32_t kind;
+    int32_t nbins;
+    float p0, p1, p2, p3;
+    float values[RICH_TABLE_MAX_BINS];
+} rich_table;
+
+/* Surface material. kind: RICH_MAT_*. table: index of the reflectivity
+ * (mirror) or quantum-efficiency (detector) table. plane: detector-plane
+ * index for detectors (selects the hit plane and histogram slice), else -1.
+ * flags: RICH_MAT_SMOOTH. Mirrors reflect on their front side and absorb on
+ * the back; detectors accept on the front and are transparent from the back;
+ * absorbers absorb on both sides. */
+typedef struct rich_material {
+    int32_t kind, table, plane, flags;
+} rich_material;
+
+/* Analytic spherical-mirror tile. The sphere has centre `center` and radius
+ * `radius`; the tile is the part of the sphere with unit vector
+ * w = (p - center) / radius satisfying w . axis >= cos_min and, with
+ * x = (p - center) . e1 and y = (p - center) . e2 (mm), every aperture edge
+ * edges[j] = (a, b, c) satisfies a*x + b*y <= c. The reflective (front) side
+ * is the concave one, facing the centre. 160 bytes. */
+typedef struct rich_sphere {
+    float center[3];
+    float radius;
+    float axis[3];
+    float cos_min;
+    float e1[3];
+    int32_t n_edges;
+    float e2[3];
+    int32_t material;
+    float edges[RICH_SPHERE_MAX_EDGES][3];
+} rich_sphere;
+
+/* Flat rectangle (flat mirror, absorber or detector plane). A point p is on
+ * the rectangle when u = (p - origin) . u_axis lies in [0, width) and
+ * v = (p - origin) . v_axis lies in [0, height). The front side is the side
+ * `normal` points to (a ray with d . normal < 0 hits the front). Detector
+ * rectangles carry an nx x ny pixel grid of pitch `pitch` with origin at the
+ * bottom-left corner (Sec. 4.4); width = nx*pitch and height = ny*pitch.
+ * 80 bytes. */
+typedef struct rich_rect {
+    float origin[3];
+    float width;
+    float u_axis[3];
+    float height;
+    float v_axis[3];
+    float pitch;
+    float normal[3];
+    int32_t material;
+    int32_t nx, ny, reserved0, reserved1;
+} rich_rect;
+
+/* Whole scene, all HOST pointers (copied by rich_init_geometry).
+ * tri_vertices: n_triangles x 3 vertices x 3 floats. tri_normals: same shape,
+ * per-vertex unit normals used by RICH_MAT_SMOOTH materials (may be NULL when
+ * no material is smooth). tri_material: n_triangles material indices.
+ * Primitive ids: spheres are 0..n_spheres-1, rectangles follow, triangles
+ * follow the rectangles (ids used in ties: the lowest id wins). */
+typedef struct rich_geometry_desc {
+    int32_t n_tables;
+    int32_t n_materials;
+    int32_t n_spheres;
+    int32_t n_rects;
+    int64_t n_triangles;
+    const rich_table *tables;
+    const rich_material *materials;
+    const rich_sphere *spheres;
+    const rich_rect *rects;
+    const float *tri_vertices;
+    const float *tri_normals;
+    const int32_t *tri_material;
+} rich_geometry_desc;
+
+/* ------------------------------------------------------------------ inputs */
+/* Charged tracks, structure of arrays, all DEVICE pointers of length n,
+ * read-only, owned by the caller and kept alive until the rich_trace that
+ * consumes this emission has completed on the stream.
+ * (x,y,z) track origin; (dx,dy,dz) direction (normalised by the library);
+ * p momentum; mass (0 -> beta = 1); length: emission length along the track
+ * (0 -> point source); event: event id; id: track id within the event
+ * (NULL -> the array index); n_fixed: fixed photon count per track (NULL ->
+ * Poisson with the Frank-Tamm mean). */
+typedef struct rich_tracks {
+    int64_t n;
+    const float *x, *y, *z;
+    const float *dx, *dy, *dz;
+    const float *p, *mass, *length;
+    const uint32_t *event;
+    const uint32_t *id;
+    const uint32_t *n_fixed;
+} rich_tracks;
+
+/* Radiator and spectrum. seed: Philox key. n_minus_1: refractive index
+ * minus one (constant, no dispersion). lambda_min/max: emission band (nm). */
+typedef struct rich_emit_params {
+    uint64_t seed;
+    float n_minus_1;
+    float lambda_min;
+    float lambda_max;
+    float reserved;
+} rich_emit_params;
+
+/* Materialised photons, structure of arrays of DEVICE pointers (caller
+ * owned). rich_emit fills them when asked; rich_trace can consume them, or
+ * photons supplied by the caller (e.g. from an external simulation), whose
+ * keys (event, track, photon) select their reflectivity/QE random draws.
+ * (dx,dy,dz) must be unit vectors. */
+typedef struct rich_photons {
+    uint64_t n;
+    uint64_t capacity;
+    float *x, *y, *z;
+    float *dx, *dy, *dz;
+    float *lambda;
+    uint32_t *event, *track, *photon;
+} rich_photons;
+
+/* ----------------------------------------------------------------- options */
+enum {
+    RICH_PREC_FP32 = 0,     /* FP32 trace; FP64 only for the sphere quadratic */
+    RICH_PREC_REFINE64 = 1  /* FP32 trace, then the detected photon's recorded
+                               surface sequence is replayed in FP64 to give
+                               the hit position and pixel */
+};
+
+typedef struct rich_trace_opts {
+    int32_t precision;      /* RICH_PREC_*                                    */
+    int32_t max_bounces;    /* mirror reflections, 1..RICH_MAX_BOUNCES        */
+    int32_t max_steps;      /* surface interactions, 1..RICH_MAX_STEPS        */
+    float t_min;            /* minimum hit distance after an interaction (mm) */
+    /* launch knobs (0 -> tuned default) */
+    int32_t block_threads;  /* threads per block (multiple of 32)            */
+    int32_t blocks_per_sm;  /* resident blocks per SM for the persistent grid*/
+    int32_t refill_min;     /* refill a warp when at least this many lanes are
+                               idle (1..32): the compaction interval          */
+    int32_t chunk;          /* photons a warp takes from the queue at a time */
+} rich_trace_opts;
+
+/* ----------------------------------------------------------------- outputs */
+/* One detected photon, 40 bytes. (u, v): position on the detector plane in
+ * mm relative to its bottom-left corner; (ix, iy) = floor((u, v) / pitch). */
+typedef struct rich_hit {
+    uint32_t event, track, photon;
+    uint8_t plane;
+    uint8_t n_reflections;
+    uint16_t reserved;
+    uint16_t ix, iy;
+    float lambda;
+    double u, v;
+} rich_hit;
+
+/* Photon fates (optional per-photon output). */
+enum {
+    RICH_FATE_NONE = 0,
+    RICH_FATE_ESCAPED = 1,        /* left the scene                          */
+    RICH_FATE_MIRROR_ABSORBED = 2,/* failed the reflectivity test            */
+    RICH_FATE_ABSORBED = 3,       /* absorber, or the back of a mirror       */
+    RICH_FATE_QE_REJECTED = 4,    /* reached a detector, failed the QE test  */
+    RICH_FATE_DETECTED = 5,       /* recorded hit                            */
+    RICH_FATE_MAX_BOUNCES = 6,    /* more than max_bounces reflections       */
+    RICH_FATE_MAX_STEPS = 7       /* more than max_steps interactions        */
+};
+
+/* DEVICE output buffers, caller owned.
+ * hits: capacity hit_capacity; hits beyond it are counted, not written.
+ *   Hits are appended in no particular order (sort by key if needed).
+ * pixel_counts: u32 histogram [n_hist_events][sum over planes of ny*nx],
+ *   plane slices in plane-index order, row-major (iy, ix); accumulated
+ *   (not cleared) by rich_trace; photons with event >= n_hist_events are not
+ *   binned. May be NULL.
+ * event_sums: FP64 [n_hist_events][n_planes][4] = (hits, sum u, sum v,
+ *   sum lambda), accumulated. May be NULL.
+ * fate: one byte per photon (RICH_FATE_*) indexed by the photon's global
+ *   emission index. May be NULL. */
+typedef struct rich_outputs {
+    rich_hit *hits;
+    uint64_t hit_capacity;
+    uint32_t *pixel_counts;
+    double *event_sums;
+    uint32_t n_hist_events;
+    uint32_t reserved;
+    uint8_t *fate;
+} rich_outputs;
+
+/* Counters of the last rich_trace, read by rich_hits. */
+typedef struct rich_stats {
+    uint64_t n_photons;      /* photons that entered the trace              */
+    uint64_t n_hits;         /* detected photons (may exceed hit_capacity)  */
+    uint64_t n_fate[8];      /* photons per RICH_FATE_* code                */
+    uint32_t device_status;  /* RICH_OK or the first device-side error      */
+    uint32_t reserved;
+} rich_stats;
+
+typedef struct rich_ctx rich_ctx;
+
+/* ------------------------------------------------------------ entry points */
+
+/* Create a context on CUDA device `device`, ordered on `stream` (a
+ * cudaStream_t, or NULL for the legacy default stream). *out receives the
+ * handle. Allocates the context's small device state. */
+rich_status rich_create(rich_ctx **out, int device, void *stream);
+
+/* Release every resource owned by the context (geometry, scratch). Waits for
+ * the context's stream. NULL is accepted. */
+rich_status rich_destroy(rich_ctx *ctx);
+
+/* Change the stream later calls are ordered on. */
+rich_status rich_set_stream(rich_ctx *ctx, void *stream);
+
+/* Upload a scene (Sec. 4.1: mirrors and detector as separate surfaces with
+ * their own materials; Sec. 4.3: wavelength tables). All pointers in `desc`
+ * are HOST memory and are copied. Builds the SAH BVH over the triangles on
+ * the host and uploads it. Replaces any previous geometry. Returns
+ * RICH_ERR_GEOMETRY for inconsistent descriptions (bad indices, non-finite
+ * values, pixel grid not matching a detector rectangle). Synchronous. */
+rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc *desc);
+
+/* Photon yield and emission (Sec. 3: cos(theta) = 1/(n beta), azimuth
+ * uniform; photons are the input of the trace as in Sec. 4.2). For each
+ * track computes beta, the Cherenkov angle and the Frank-Tamm mean
+ * mu = L * 2*pi*alpha * sin^2(theta) * (1/lambda_min - 1/lambda_max) in FP64,
+ * draws N_t ~ Poisson(mu) (or takes n_fixed), and scans the counts into
+ * photon offsets kept in the context for the next fused rich_trace.
+ * tracks: DEVICE arrays (see rich_tracks). out: if non-NULL, the photons are
+ * also materialised into the caller's SoA (RICH_ERR_OVERFLOW if capacity is
+ * too small; nothing is written then) and out->n is set on the host after a
+ * synchronisation. n_photons: if non-NULL, receives the total photon count
+ * (synchronises the stream); if NULL the call stays asynchronous. */
+rich_status rich_emit(rich_ctx *ctx, const rich_tracks *tracks,
+                      const rich_emit_params *params, rich_photons *out,
+                      uint64_t *n_photons);
+
+/* Propagate photons through the scene. `in` NULL: the photons of the last
+ * rich_emit are generated on the fly inside the trace kernel (fused emission,
+ * no photon round trip through memory); otherwise the caller's photons are
+ * traced. Mirrors reflect with probability R(lambda) at each reflection;
+ * detectors accept with probability QE(lambda) (Sec. 4.3, in flight as in
+ * Sec. 6); accepted photons are appended to out->hits and binned. Clears the
+ * context's counters first; asynchronous. */
+rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
+                       const rich_trace_opts *opts, const rich_outputs *out);
+
+/* Wait for the last rich_trace and report its counters. n_hits (host, may be
+ * NULL) receives the number of detected photons; stats (host, may be NULL)
+ * receives all counters. Returns RICH_ERR_OVERFLOW if hits were dropped for
+ * lack of capacity (the count still reports every hit), or the device-side
+ * error recorded during the trace. */
+rich_status rich_hits(rich_ctx *ctx, uint64_t *n_hits, rich_stats *stats);
+
+/* Message for the last failure on ctx (or of rich_create when ctx is NULL).
+ * The string is owned by the library and valid until the next call. */
+const char *rich_last_error(rich_ctx *ctx);
+
+/* Library version string. */
+const char *rich_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RICH_H */

@@ -1,0 +1,458 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Each test checks an oracle function against a library routine, a closed
+form, a textbook constant, an invariant, a statistical law or brute force,
+chosen so that a plausible slip (a wrong multiplier or sign, a dropped term,
+a swapped index, an off-by-one bin) fails at least one of them. None of
+these tests needs a GPU.
+"""
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+
+import numpy as np
+import pytest
+
+from paper_2309_12496_gb300 import workloads as w
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")
+PAPER = json.load(open(GOLDEN))
+ETA_C4F10 = float(np.float32(0.0014))   # n - 1 as the FP32 input holds it
+ETA_CF4 = float(np.float32(0.0005))
+
+
+# ------------------------------------------------------------------ Philox
+_TRITON_SCRIPT = r"""
+import os, sys
+os.environ["TRITON_INTERPRET"] = "1"
+import numpy as np, torch, triton, triton.language as tl
+@triton.jit
+def k(c_ptr, o_ptr, seed, N: tl.constexpr):
+    i = tl.arange(0, N)
+    c0 = tl.load(c_ptr + 4 * i + 0)
+    c1 = tl.load(c_ptr + 4 * i + 1)
+    c2 = tl.load(c_ptr + 4 * i + 2)
+    c3 = tl.load(c_ptr + 4 * i + 3)
+    a, b, c, d = tl.philox(seed, c0, c1, c2, c3)
+    tl.store(o_ptr + 4 * i + 0, a)
+    tl.store(o_ptr + 4 * i + 1, b)
+    tl.store(o_ptr + 4 * i + 2, c)
+    tl.store(o_ptr + 4 * i + 3, d)
+z = np.load(sys.argv[1])
+ctr = torch.from_numpy(z["ctr"].view(np.int32).copy())
+out = torch.zeros_like(ctr)
+k[(1,)](ctr, out, int(z["seed"]), N=ctr.numel() // 4)
+np.save(sys.argv[2], out.numpy().view(np.uint32))
+"""
+
+
+def test_philox_matches_triton_library(oracle_lib):
+    """Philox4x32-10 of the oracle equals Triton's tl.philox (a library
+    implementation, run by Triton's CPU interpreter) on random counters and
+    a 64-bit seed split into (lo, hi) key words."""
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(7)
+    ctr = rng.integers(0, 2**32, size=(256, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    ctr[1] = [0xFFFFFFFF] * 4
+    seed = 0x0123456789ABCDEF
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "in.npz")
+        dst = os.path.join(d, "out.npy")
+        np.savez(src, ctr=ctr, seed=np.uint64(seed))
+        env = dict(os.environ, TRITON_INTERPRET="1")
+        r = subprocess.run([sys.executable, "-c", _TRITON_SCRIPT, src, dst],
+                           env=env, capture_output=True, text=True, timeout=600)
+        if r.returncode != 0:
+            pytest.skip("triton interpreter unavailable: " + r.stderr[-300:])
+        ref = np.load(dst).reshape(-1, 4)
+    key = np.array([seed & 0xFFFFFFFF, seed >> 32], np.uint32)
+    got = oracle_lib.philox(ctr, key)
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_philox_bijective_and_uniform(oracle_lib):
+    """Distinct counters give distinct outputs; words are uniform (chi^2 on
+    256 bins) and uncorrelated across the 4 lanes."""
+    n = 1 << 16
+    ctr = np.zeros((n, 4), np.uint32)
+    ctr[:, 0] = np.arange(n)
+    ctr[:, 2] = 12345
+    out = oracle_lib.philox(ctr, np.array([0, 0], np.uint32))
+    packed = out.view(np.uint64).reshape(n, 2)
+    assert len(np.unique(packed[:, 0] ^ (packed[:, 1] << np.uint64(1)))) == n
+    from scipy import stats
+    for lane in range(4):
+        hist = np.bincount(out[:, lane] >> 24, minlength=256)
+        assert stats.chisquare(hist).pvalue > 1e-4
+    c = np.corrcoef(out.astype(np.float64).T)
+    assert np.abs(c - np.eye(4)).max() < 0.02
+
+
+# ------------------------------------------------------------- Frank-Tamm
+def test_yield_matches_pdg_constant(oracle_lib):
+    """Frank-Tamm: d2N/dx dE = (alpha / hbar c) z^2 sin^2(theta), with
+    alpha/(hbar c) = 369.81 eV^-1 cm^-1 (PDG review of passage of particles
+    through matter) and hc = 1239.84 eV nm. For beta = 1 in C4F10 and CF4
+    this gives 0.4270 and 0.1527 photons/mm over 200-600 nm."""
+    def pdg(eta, beta):
+        nb = (1 + eta) * beta
+        s2 = 1 - 1 / nb**2 if nb > 1 else 0.0
+        de = 1239.84193 / 200.0 - 1239.84193 / 600.0
+        return 369.81 * s2 * de / 10.0
+    for eta in (ETA_C4F10, ETA_CF4, 0.33):
+        got = oracle_lib.yield_per_mm(eta, 1.0)
+        assert got == pytest.approx(pdg(eta, 1.0), rel=2e-4)
+    assert oracle_lib.yield_per_mm(ETA_C4F10, 1.0) == pytest.approx(0.42704, abs=1e-5)
+    assert oracle_lib.yield_per_mm(ETA_CF4, 1.0) == pytest.approx(0.15272, abs=1e-5)
+
+
+def test_yield_threshold(oracle_lib):
+    """No light below threshold beta = 1/n: for a pion in C4F10 the
+    threshold momentum is m / sqrt(n^2 - 1) = 2.637 GeV/c."""
+    m = w.PION_MASS
+    n = 1 + ETA_C4F10
+    p_thr = m / math.sqrt(n * n - 1)
+    assert p_thr == pytest.approx(2.637, abs=1e-3)
+    beta = lambda p: p / math.sqrt(p * p + m * m)
+    assert oracle_lib.yield_per_mm(ETA_C4F10, beta(p_thr * 0.999)) == 0.0
+    assert oracle_lib.yield_per_mm(ETA_C4F10, beta(p_thr * 1.01)) > 0.0
+
+
+def test_mean_photons_per_track_rich1_spectrum(oracle_lib):
+    """Mean Frank-Tamm mean over the log-uniform 2-100 GeV/c pion spectrum,
+    by quadrature of the closed form, equals the oracle's per-track means
+    averaged over many tracks (to statistical precision)."""
+    from scipy import integrate
+    m, n, L = w.PION_MASS, 1 + ETA_C4F10, 1000.0
+    k = 369.81 * (1239.84193 / 200 - 1239.84193 / 600) / 10.0
+
+    def mu(lnp):
+        p = math.exp(lnp)
+        b = p / math.sqrt(p * p + m * m)
+        s2 = max(0.0, 1 - 1 / (n * b) ** 2)
+        return L * k * s2
+    a, b = math.log(2.0), math.log(100.0)
+    expect = integrate.quad(mu, a, b, points=[math.log(2.637)])[0] / (b - a)
+    assert expect == pytest.approx(342.3, abs=0.5)
+    tr = w.pion_tracks(20000, seed=3)
+    wl = w.Workload("t", None, tr, n_minus_1=0.0014)
+    nph, mus, off = oracle_lib.track_yield(tr, oracle_lib.params(wl))
+    assert mus.mean() == pytest.approx(expect, rel=0.02)
+    # Poisson counts: mean matches the means, variance ~ mean + var(mu)
+    assert nph.mean() == pytest.approx(mus.mean(), rel=0.01)
+    assert int(off[-1]) == int(nph.sum())
+
+
+@pytest.mark.parametrize("mu", [0.7, 3.0, 9.5, 10.0, 42.0, 341.0])
+def test_poisson_sampler_distribution(oracle_lib, mu):
+    """The keyed Poisson draw (inversion below 10, PTRS above) follows the
+    Poisson law: chi^2 against scipy's pmf over 20,000 independent keys."""
+    from scipy import stats
+    ks = np.array([oracle_lib.poisson(mu, seed=11, event=1, track=t)
+                   for t in range(20000)])
+    assert ks.mean() == pytest.approx(mu, abs=4 * math.sqrt(mu / 20000))
+    lo, hi = int(max(0, mu - 4 * math.sqrt(mu) - 2)), int(mu + 4 * math.sqrt(mu) + 3)
+    edges = np.arange(lo, hi + 1)
+    obs = np.array([(ks == k).sum() for k in edges[:-1]] + [(ks >= edges[-1]).sum()])
+    obs[0] += (ks < lo).sum()
+    pmf = stats.poisson.pmf(edges[:-1], mu)
+    exp = np.concatenate([pmf, [stats.poisson.sf(edges[-1] - 1, mu)]])
+    exp[0] += stats.poisson.cdf(lo - 1, mu)
+    exp = exp * len(ks)
+    keep = exp > 5
+    chi2 = ((obs[keep] - exp[keep]) ** 2 / exp[keep]).sum()
+    dof = keep.sum() - 1
+    assert stats.chi2.sf(chi2, dof) > 1e-4
+
+
+# --------------------------------------------------------------- emission
+def test_emission_angle_is_cherenkov(oracle_lib):
+    """Sec. 3: photons leave at cos(theta) = 1/(n beta) to the track,
+    independent of azimuth; directions are unit vectors; the origin lies on
+    the track segment [0, L)."""
+    tr = w.pion_tracks(50, seed=5)
+    wl = w.Workload("t", None, tr, n_minus_1=0.0014)
+    prm = oracle_lib.params(wl)
+    m = w.PION_MASS
+    for i in range(0, 50, 7):
+        p = float(tr.p[i])
+        beta = p / math.sqrt(p * p + float(np.float32(m)) ** 2)
+        if (1 + ETA_C4F10) * beta <= 1:
+            continue
+        t = np.array([tr.dx[i], tr.dy[i], tr.dz[i]], np.float64)
+        t /= np.linalg.norm(t)
+        for j in range(20):
+            o, d, lam = oracle_lib.emit(tr, prm, i, j)
+            assert np.linalg.norm(d) == pytest.approx(1.0, abs=1e-14)
+            assert np.dot(d, t) == pytest.approx(1 / ((1 + ETA_C4F10) * beta), abs=1e-13)
+            s = np.dot(o, t)
+            assert 0.0 <= s < float(tr.length[i])
+            assert np.linalg.norm(o - s * t) < 1e-9
+            assert 200.0 <= lam <= 600.0
+
+
+def test_emission_azimuth_and_wavelength_laws(oracle_lib):
+    """Azimuth uniform on [0, 2 pi) (measured in a frame built here, not the
+    oracle's); wavelength follows the Frank-Tamm spectrum dN/dl ~ 1/l^2 on
+    [200, 600] nm, whose CDF is (1/200 - 1/l)/(1/200 - 1/600) (KS tests)."""
+    from scipy import stats
+    wl = w.point_source(4000)
+    prm = oracle_lib.params(wl)
+    phis, lams = [], []
+    for j in range(4000):
+        _, d, lam = oracle_lib.emit(wl.tracks, prm, 0, j)
+        phis.append(math.atan2(d[1], d[0]) % (2 * math.pi))
+        lams.append(lam)
+    assert stats.kstest(np.array(phis) / (2 * math.pi), "uniform").pvalue > 1e-3
+    cdf = lambda l: (1 / 200.0 - 1 / l) / (1 / 200.0 - 1 / 600.0)
+    assert stats.kstest(np.array(lams, np.float64), cdf).pvalue > 1e-3
+
+
+# ----------------------------------------------------------------- tables
+def test_tables_follow_paper_binning(oracle_lib):
+    """Sec. 4.3: QE histogram in 33 nm bins with its 35% peak in the bin
+    containing 450 nm; reflectivity in 25 nm bins from 94% to 89% over
+    200-600 nm. The oracle's lookup returns the bin holding lambda, clamped
+    at the ends."""
+    sc = oracle_lib.Scene(w.rich1_scene(meshed=False))
+    tab = w.rich1_scene(meshed=False).tables
+    assert tab[0]["p1"] == PAPER["qe_bin_width_nm"]["value"]
+    assert tab[1]["p1"] == PAPER["reflectivity_bin_width_nm"]["value"]
+    qe_peak = PAPER["qe_peak"]
+    assert sc.table(0, qe_peak["lambda_nm"]) == pytest.approx(qe_peak["value"], abs=1e-6)
+    assert max(sc.table(0, l) for l in np.arange(200, 1000, 1.0)) == pytest.approx(0.35, abs=1e-6)
+    r = PAPER["reflectivity_range"]
+    assert sc.table(1, 200.5) == pytest.approx(r["high"], abs=1e-6)
+    assert sc.table(1, 599.5) == pytest.approx(r["low"], abs=0.0015)
+    # bin edges: [200 + 25 k, 200 + 25 (k + 1)) and clamping
+    vals = tab[1]["values"]
+    for k in range(16):
+        assert sc.table(1, 200.0 + 25 * k) == vals[k]
+        assert sc.table(1, np.nextafter(np.float32(225.0 + 25 * k), np.float32(0))) == vals[k]
+    assert sc.table(1, 150.0) == vals[0]
+    assert sc.table(1, 700.0) == vals[15]
+    # analytic Gaussian QE of the point-source scene, evaluated in FP32
+    sp = oracle_lib.Scene(w.point_source_scene())
+    for lam in (250.0, 400.0, 537.5):
+        x = np.float32(np.float32(lam) - np.float32(400)) / np.float32(120)
+        ref = np.float32(0.3) * np.exp(-np.float32(x * x), dtype=np.float32)
+        assert sp.table(0, lam) == pytest.approx(float(ref), rel=3e-7)
+    assert sp.table(1, 431.0) == pytest.approx(0.9, rel=1e-7)
+
+
+# ------------------------------------------------- closed-form geometries
+def _ring_radii(out, rect):
+    det = out["fate"] == 5
+    half_u = -float(np.dot(rect["origin"], rect["u_axis"]))
+    half_v = -float(np.dot(rect["origin"], rect["v_axis"]))
+    return det, np.hypot(out["u"][det] - half_u, out["v"][det] - half_v)
+
+
+def test_point_source_ring_radius(oracle_lib):
+    """Source at the mirror's centre of curvature: every reflected photon
+    returns through the centre, so every hit on the plane at R/2 lies at
+    radius (R/2) tan(theta) = 71.72495 mm with tan(theta) = sqrt(n^2 - 1)
+    for beta = 1 (Sec. 3 angle; the ring radius measures the Cherenkov
+    angle as in Sec. 6)."""
+    wl = w.point_source(20000)
+    sc = oracle_lib.Scene(wl.scene)
+    out = sc.trace(wl.tracks, oracle_lib.params(wl))
+    det, rad = _ring_radii(out, wl.scene.rects[0])
+    n = 1 + ETA_C4F10
+    expect = 1355.0 * math.sqrt(n * n - 1)
+    assert expect == pytest.approx(71.72495, abs=2e-5)
+    assert det.sum() > 1000
+    assert np.abs(rad - expect).max() < 1e-9
+    # every photon reaches the mirror: fates are only mirror-absorbed,
+    # QE-rejected or detected
+    assert set(np.unique(out["fate"])) <= {2, 4, 5}
+
+
+def test_point_source_expected_counts(oracle_lib):
+    """Detected fraction = R * <QE> with <QE> the spectrum-weighted mean of
+    0.3 exp(-((l - 400)/120)^2) under dN/dl ~ 1/l^2 on [200, 600] nm
+    (quadrature: 0.13435); 10^5 photons give 12,092 +- 103 hits (binomial),
+    and the reflectivity draw rejects 10% of photons."""
+    from scipy import integrate
+    num = integrate.quad(lambda l: 0.3 * math.exp(-((l - 400) / 120) ** 2) / l**2, 200, 600)[0]
+    den = integrate.quad(lambda l: 1 / l**2, 200, 600)[0]
+    qe = num / den
+    assert qe == pytest.approx(0.13435, abs=1e-5)
+    wl = w.point_source(100000)
+    sc = oracle_lib.Scene(wl.scene)
+    out = sc.trace(wl.tracks, oracle_lib.params(wl))
+    n_det = int((out["fate"] == 5).sum())
+    p = 0.9 * qe
+    assert abs(n_det - 1e5 * p) < 4 * math.sqrt(1e5 * p * (1 - p))
+    n_abs = int((out["fate"] == 2).sum())
+    assert abs(n_abs - 1e4) < 4 * math.sqrt(1e5 * 0.09)
+    # azimuth of hits uniform around the ring centre
+    from scipy import stats
+    det = out["fate"] == 5
+    ang = np.arctan2(out["v"][det] - 368.64, out["u"][det] - 368.64)
+    assert stats.kstest((ang + math.pi) / (2 * math.pi), "uniform").pvalue > 1e-3
+    # histogram and per-event sums agree with the hit list
+    assert out["pixel_counts"].sum() == n_det
+    es = out["event_sums"][0, 0]
+    assert es[0] == n_det
+    assert es[1] == pytest.approx(out["u"][det].sum(), rel=1e-12)
+    assert es[3] == pytest.approx(out["lambda"][det].astype(np.float64).sum(), rel=1e-12)
+
+
+def _flat_mirror_scene(meshed, n_cells=1):
+    """Point source at the origin, flat mirror at z = 1000 facing the source,
+    detector plane at z = 500 facing +z (the mirror)."""
+    b = w._Builder("flat")
+    t1 = b.table_const(1.0)
+    m_mir = b.material(w.MAT_MIRROR, t1)
+    m_det = b.material(w.MAT_DETECTOR, t1, plane=0)
+    side = 800.0
+    origin = np.array([side / 2, -side / 2, 1000.0])
+    u_ax, v_ax = np.array([-1.0, 0, 0]), np.array([0, 1.0, 0])
+    if meshed:
+        b.triangles(w._mesh_rectangle(origin, u_ax, v_ax, side, side, n_cells, n_cells),
+                    None, m_mir, smooth=False)
+    else:
+        b.rect(origin, u_ax, v_ax, side, side, m_mir)
+    half = 128 * 2.88
+    b.rect((-half, -half, 500.0), (1.0, 0, 0), (0, 1.0, 0), 256 * 2.88, 256 * 2.88,
+           m_det, nx=256, ny=256, pitch=2.88)
+    return b.build()
+
+
+@pytest.mark.parametrize("meshed,cells", [(False, 1), (True, 1), (True, 7)])
+def test_flat_mirror_image_method(oracle_lib, meshed, cells):
+    """Law of reflection via the image method: a flat mirror at z = 1000
+    images the source at z = 2000, so the reflected cone reaches the plane
+    z = 500 at radius 1500 tan(theta). Checks rectangle and triangle
+    intersection (through the BVH and by brute force) and the reflection."""
+    sc_ = _flat_mirror_scene(meshed, cells)
+    tr = w.point_source_tracks(3000)
+    wl = w.Workload("flat", sc_, tr, n_minus_1=0.0014)
+    sc = oracle_lib.Scene(sc_, leaf_size=2)
+    n = 1 + ETA_C4F10
+    expect = 1500.0 * math.sqrt(n * n - 1)
+    for bvh in (True, False):
+        out = sc.trace(tr, oracle_lib.params(wl, use_bvh=bvh))
+        det, rad = _ring_radii(out, sc_.rects[-1])
+        assert det.sum() == 3000      # QE = R = 1
+        assert np.abs(rad - expect).max() < 1e-9
+
+
+def test_sphere_intersection_closed_forms(oracle_lib):
+    """Ray from the centre of a sphere: t = R. Ray along the axis from
+    outside, at distance D from the centre: the concave (far) side at
+    t = D + R is hit only when the near point is off the tile; the convex
+    back at t = D - R is hit when it is on the tile."""
+    b = w._Builder("sph")
+    t1 = b.table_const(1.0)
+    m = b.material(w.MAT_MIRROR, t1)
+    b.sphere((0.0, 0.0, 0.0), 1000.0, (0.0, 0.0, 1.0), (1.0, 0, 0), (0, 1.0, 0), m,
+             cos_min=0.5)
+    sc = oracle_lib.Scene(b.build())
+    rng = np.random.default_rng(0)
+    d = rng.normal(size=(200, 3))
+    d[:, 2] = np.abs(d[:, 2]) + 2.0
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    d = d[d[:, 2] > 0.55]          # inside the 60-degree cap
+    t, prim = sc.raycast(np.zeros((len(d), 3)), d)
+    assert len(d) > 150 and np.all(prim == 0)
+    np.testing.assert_allclose(t, 1000.0, rtol=0, atol=1e-9)
+    # from below (outside), aiming +z: near intersection z = -1000 is off the
+    # cap (w.axis = -1), far one z = +1000 is on it
+    t, prim = sc.raycast([[0.0, 0.0, -3000.0]], [[0.0, 0.0, 1.0]])
+    assert prim[0] == 0 and t[0] == pytest.approx(4000.0, abs=1e-9)
+    # from above (outside), aiming -z: the convex back at z = +1000
+    t, prim = sc.raycast([[0.0, 0.0, 3000.0]], [[0.0, 0.0, -1.0]])
+    assert prim[0] == 0 and t[0] == pytest.approx(2000.0, abs=1e-9)
+    # tangent-missing ray
+    t, prim = sc.raycast([[1000.5, 0.0, -3000.0]], [[0.0, 0.0, 1.0]])
+    assert prim[0] == -1
+
+
+def test_triangle_intersection_closed_form(oracle_lib):
+    """Ray through a known barycentric point of a triangle hits at the
+    distance to that point; rays outside its edges miss."""
+    b = w._Builder("tri")
+    t1 = b.table_const(1.0)
+    m = b.material(w.MAT_ABSORBER, t1)
+    V = np.array([[[0.0, 0.0, 100.0], [50.0, 0.0, 110.0], [0.0, 40.0, 95.0]]])
+    b.triangles(V, None, m, smooth=False)
+    sc = oracle_lib.Scene(b.build())
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        b1, b2 = rng.random(2) * 0.5
+        p = V[0, 0] + b1 * (V[0, 1] - V[0, 0]) + b2 * (V[0, 2] - V[0, 0])
+        o = rng.normal(size=3) * 30.0
+        d = (p - o) / np.linalg.norm(p - o)
+        t, prim = sc.raycast([o], [d])
+        assert prim[0] == 0
+        assert t[0] == pytest.approx(np.linalg.norm(p - o), abs=1e-9)
+        q = V[0, 0] + 1.05 * (V[0, 1] - V[0, 0]) + 0.2 * (V[0, 2] - V[0, 0])
+        t, prim = sc.raycast([o], [(q - o) / np.linalg.norm(q - o)])
+        assert prim[0] == -1
+
+
+def test_bvh_matches_brute_force(oracle_lib):
+    """The oracle's median-split BVH returns exactly the brute-force nearest
+    hit (distance and primitive) for random rays on a ~1000-triangle patch
+    of the RICH1 mesh and on the full mesh."""
+    full = w.rich1_scene(meshed=True)
+    for n_tri in (1000, full.n_triangles):
+        sub = w.Scene("sub", full.tables, full.materials, full.spheres[:0],
+                      full.rects[:0], full.tri_vertices[:n_tri],
+                      full.tri_normals[:n_tri], full.tri_material[:n_tri])
+        sc = oracle_lib.Scene(sub, leaf_size=3)
+        rng = np.random.default_rng(2)
+        n = 3000 if n_tri == 1000 else 1500
+        o = rng.normal(size=(n, 3)) * 100.0
+        tgt = sub.tri_vertices[rng.integers(0, n_tri, n)].mean(axis=1)
+        tgt = tgt + rng.normal(size=(n, 3)) * 8.0
+        d = tgt - o
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        t1, p1 = sc.raycast(o, d, use_bvh=True)
+        t2, p2 = sc.raycast(o, d, use_bvh=False)
+        np.testing.assert_array_equal(p1, p2)
+        np.testing.assert_array_equal(t1, t2)
+        assert (p1 >= 0).mean() > 0.3
+
+
+def test_results_invariant_to_sharding(oracle_lib):
+    """Keyed random numbers: tracing a sub-range of tracks reproduces the
+    same per-photon results as the full run."""
+    wl = w.rich1(60, meshed=False)
+    sc = oracle_lib.Scene(wl.scene)
+    prm = oracle_lib.params(wl)
+    full = sc.trace(wl.tracks, prm)
+    off = full["offsets"]
+    part = sc.trace(wl.tracks, prm, offsets=off, track_range=(20, 45))
+    a, b = int(off[20]), int(off[45])
+    for k in ("fate", "plane", "ix", "iy", "u", "v", "lambda", "n_refl"):
+        np.testing.assert_array_equal(part[k][a:b], full[k][a:b])
+    assert np.all(part["fate"][:a] == 0)
+
+
+def test_rich1_bookkeeping(oracle_lib):
+    """Fates partition the photons; pixel counts and per-event sums agree
+    with the hit list; hits lie inside their pixel; grazes are rare."""
+    wl = w.rich1(100, meshed=True)
+    sc = oracle_lib.Scene(wl.scene)
+    out = sc.trace(wl.tracks, oracle_lib.params(wl))
+    f = out["fate"]
+    assert np.all((f >= 1) & (f <= 7))
+    det = f == 5
+    assert out["pixel_counts"].sum() == det.sum()
+    assert out["event_sums"][0, :, 0].sum() == det.sum()
+    pitch = 2.88
+    u, v = out["u"][det], out["v"][det]
+    ix, iy = out["ix"][det], out["iy"][det]
+    assert np.all(ix * np.float64(np.float32(pitch)) <= u + 1e-12)
+    assert np.all(u < (ix + 1) * np.float64(np.float32(pitch)) + 1e-12)
+    assert np.all((iy >= 0) & (iy < 256))
+    assert (out["graze"] != 0).mean() < 0.01
+    # planes 0/1 collect light after two reflections mostly
+    assert (out["n_refl"][det & (out["plane"] < 2)] == 2).mean() > 0.8
