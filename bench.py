@@ -1,0 +1,351 @@
+#!/usr/bin/env python3
+"""Throughput of the Cherenkov photon propagator on GB300.
+
+One step = one pass of the whole hot path over one batch of synthetic
+input, through the C ABI: rich_emit (per-track FP64 Cherenkov angle,
+Frank-Tamm mean, keyed Poisson count, photon offsets) + rich_trace (fused
+emission, trace through the RICH1-like geometry -- 4 spherical tiles and 2
+flat mirrors as 21,960 triangles behind a BVH, 3 detector planes --,
+reflectivity and quantum-efficiency accept/reject in flight, FP64 refinement
+of detected hits, hit list, 256 x 256 pixel histograms, FP64 event sums).
+
+Workload: 1000 pion tracks, log-uniform 2-100 GeV/c within 250 mrad,
+1000 mm of C4F10 (n = 1.0014), ~3.5e5 photons per step, seed = step index
++ rank * 1000 (a fresh set of photons every step). Inputs are resident in
+HBM when the timed region starts; L2 is flushed (256 MiB write) before
+every timed step, outside the timed events.
+
+`--impl reference` times the FP64 CPU oracle on the same workload on the
+host cores (the reference arm of this build).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "propagated photons/sec on 1 GB300 (plain vs batched vs fwd+adjoint), % roofline"
+UNIT = "photons/s"
+N_TRACKS = 1000
+WORKLOAD = "rich1_meshed_1000_pion_tracks"
+
+# FP32 operations per propagated photon of the trace kernel on this workload
+# (2 x FFMA + FADD + FMUL thread instructions per photon, from the ncu
+# instruction counters of one k_trace launch; see profiles/).
+FLOPS_PER_PHOTON = None
+FP32_LANES_PER_SM = 128
+SM_COUNT_NOMINAL = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="refine64", choices=["refine64", "fp32"])
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched / e2e / cpu-baseline legs")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"rich_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_rate(seconds=10.0, n_threads=0):
+    """The FP64 oracle as it stands, on the host cores, over repeated passes
+    of the same workload (fresh seed per pass) for about `seconds`."""
+    import oracle
+    from paper_2309_12496_gb300 import workloads as W
+    oracle.build()
+    wl = W.rich1(N_TRACKS)
+    sc = oracle.Scene(wl.scene)
+    photons, t0, passes = 0, time.perf_counter(), 0
+    while True:
+        prm = oracle.params(wl, seed=1000 + passes, n_threads=n_threads)
+        r = sc.trace(wl.tracks, prm, want_hist=True)
+        photons += len(r["fate"])
+        passes += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    cores = n_threads if n_threads else oracle.max_threads()
+    return photons / el, cores, passes, photons, el
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2309_12496_gb300 import workloads as W
+    oracle.build()
+    wl = W.rich1(N_TRACKS)
+    sc = oracle.Scene(wl.scene)
+    times, photons = [], 0
+    for k in range(args.warmup + args.steps):
+        prm = oracle.params(wl, seed=k)
+        t0 = time.perf_counter()
+        r = sc.trace(wl.tracks, prm)
+        el = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(el)
+            photons += len(r["fate"])
+    total = sum(times)
+    value = photons / total
+    cores = oracle.max_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "tracks": N_TRACKS,
+                   "photons_per_step": photons // args.steps},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"the full workload ({photons // args.steps} photons) per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# --------------------------------------------------------------------- GPU
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_2309_12496_gb300 import build, rich
+    from paper_2309_12496_gb300 import workloads as W
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    build.build()
+    prec = rich.PREC_REFINE64 if args.precision == "refine64" else rich.PREC_FP32
+    dev = f"cuda:{local}"
+
+    scene = W.rich1_scene(meshed=True)
+    tracks = W.pion_tracks(N_TRACKS, seed=rank)
+    ctx = rich.Context(local)
+    ctx.init_geometry(scene)
+    dt = rich.DeviceTracks(tracks, device=dev)
+    n0 = ctx.emit(dt, 0.0014, seed=rank * 1000)
+    cap = int(n0 * 1.5) + 1024
+    out = rich.TraceOutputs(cap, scene.pixels_per_event, len(scene.planes), 1, 0, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(seed):
+        ctx.emit(dt, 0.0014, seed=seed, sync=False)
+        ctx.trace(out, precision=prec)
+
+    for k in range(args.warmup):
+        out.clear()
+        step(rank * 1000 + k)
+    ctx.hits()
+    torch.cuda.synchronize()
+
+    # photons per timed step (counts are seed dependent; computed before timing)
+    seeds = [rank * 1000 + args.warmup + k for k in range(args.steps)]
+    photons = []
+    for s in seeds:
+        photons.append(ctx.emit(dt, 0.0014, seed=s))
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in seeds]
+    clocks = ClockSampler(local)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    for k, s in enumerate(seeds):
+        flush.zero_()
+        out.clear()
+        a, b, c = ev[k]
+        a.record(stream)
+        ctx.emit(dt, 0.0014, seed=s, sync=False)
+        b.record(stream)
+        ctx.trace(out, precision=prec)
+        c.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    n_hits_last, st_last = ctx.hits()
+    step_ms = [a.elapsed_time(c) for a, _, c in ev]
+    trace_ms = [b.elapsed_time(c) for _, b, c in ev]
+    total_s = sum(step_ms) / 1e3
+    my_photons = float(sum(photons))
+    if pg:
+        t = torch.tensor([total_s, my_photons], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        pg.all_reduce(tmax[:1], op=pg.ReduceOp.MAX)
+        pg.all_reduce(t[1:], op=pg.ReduceOp.SUM)
+        total_s, all_photons = float(tmax[0]), float(t[1])
+    else:
+        all_photons = my_photons
+    value = all_photons / total_s
+
+    line = None
+    if rank == 0:
+        # dominant kernel: k_trace, timed by events on its own stream
+        t_trace = statistics.mean(trace_ms) / 1e3
+        ph_step = my_photons / len(seeds)
+        props = torch.cuda.get_device_properties(local)
+        n_sm = props.multi_processor_count
+        sm_max = clk.get("sm_max_mhz") or 2070.0
+        peak_tflops = 2 * FP32_LANES_PER_SM * n_sm * sm_max * 1e6 / 1e12
+        if FLOPS_PER_PHOTON:
+            achieved = FLOPS_PER_PHOTON * ph_step / t_trace / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
+                    "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                    "kernel": "k_trace", "flops_per_photon": FLOPS_PER_PHOTON,
+                    "peak_source": f"FP32 2 x {FP32_LANES_PER_SM} lanes x {n_sm} SMs x {sm_max:.0f} MHz"}
+        else:
+            roof = {"bound": "alu", "achieved": None, "peak": peak_tflops, "unit": "TFLOP/s",
+                    "frac": None, "traffic": None, "kernel": "k_trace",
+                    "kernel_ms": t_trace * 1e3}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "tracks": N_TRACKS,
+                       "photons_per_step": int(ph_step), "triangles": scene.n_triangles,
+                       "precision": args.precision, "parallelism": f"replicas x{ws}",
+                       "l2": "flushed before every timed step (256 MiB write)"},
+            "kernel_ms": {"emit": statistics.mean([a.elapsed_time(b) for a, b, _ in ev]),
+                          "trace": t_trace * 1e3},
+            "hits_per_step": n_hits_last,
+            "gpu_launches": 3 * args.steps,
+            "roofline": roof,
+            "clocks": clk,
+        }
+    if not args.no_extras:
+        e2e = run_e2e(ctx, tracks, dev, prec, args, scene)
+        if line is not None:
+            line["e2e"] = e2e
+    if line is not None and not args.no_extras and ws == 1:
+        v, cores, passes, nph, el = oracle_rate(10.0)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{passes} passes of the workload ({nph} photons, "
+                                          f"{el:.1f} s)"}
+    if line is not None:
+        print(json.dumps(line))
+    ctx.close()
+    if pg:
+        pg.destroy_process_group()
+
+
+def run_e2e(ctx, tracks, dev, prec, args, scene):
+    """Same metric through the public API with host buffers: host->device
+    copy of the step's tracks from pinned memory, emit + trace, device->host
+    read of the counters and the hit list, all inside the timed region."""
+    import torch
+    from paper_2309_12496_gb300 import rich
+    from paper_2309_12496_gb300 import workloads as W
+    host = {}
+    for f in W.Tracks.FIELDS:
+        host[f] = torch.from_numpy(np.ascontiguousarray(getattr(tracks, f), np.float32)).pin_memory()
+    for f in ("event", "id"):
+        host[f] = torch.from_numpy(np.ascontiguousarray(getattr(tracks, f), np.uint32)
+                                   .view(np.int32)).pin_memory()
+    dt = rich.DeviceTracks(tracks, device=dev)
+    n0 = ctx.emit(dt, 0.0014, seed=7)
+    cap = int(n0 * 1.5) + 1024
+    out = rich.TraceOutputs(cap, scene.pixels_per_event, len(scene.planes), 1, 0, device=dev)
+    hits_host = torch.empty(cap * rich.HIT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = 0
+    photons = 0
+    t_total = 0.0
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for f, v in host.items():
+            dt.t[f].copy_(v, non_blocking=True)
+        n = ctx.emit(dt, 0.0014, seed=5000 + k)
+        ctx.trace(out, precision=prec)
+        n_hits, _ = ctx.hits()
+        hits_host[: n_hits * 40].copy_(out.hits[: n_hits * 40], non_blocking=False)
+        el = time.perf_counter() - t0
+        if k >= args.warmup:
+            t_total += el
+            photons += n
+            d2h += n_hits * 40 + 8 * 12
+    return {"value": photons / t_total, "unit": UNIT,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h // args.steps}
+
+
+if __name__ == "__main__":
+    main()

@@ -51,6 +51,12 @@
 extern "C" {
 #endif
 
+#if defined(__GNUC__)
+#define RICH_API __attribute__((visibility("default")))
+#else
+#define RICH_API
+#endif
+
 /* ------------------------------------------------------------------ status */
 typedef enum rich_status {
     RICH_OK = 0,
@@ -72,6 +78,9 @@ enum { RICH_MAT_SMOOTH = 1 }; /* material flag: triangles use vertex normals */
 #define RICH_SPHERE_MAX_EDGES 8
 #define RICH_MAX_BOUNCES 8   /* mirror reflections per photon (draw map)    */
 #define RICH_MAX_STEPS 16    /* surface interactions per photon             */
+/* Scene limits checked by rich_init_geometry (RICH_ERR_GEOMETRY beyond):
+ * 64 sphere tiles on at most 16 distinct spheres, 32 rectangles, 8 tables,
+ * 32 materials, 8 detector planes, 2^27 triangles. */
 
 /* Wavelength response (reflectivity or quantum efficiency), Sec. 4.3.
  *   CONST: P = p0
@@ -207,6 +216,9 @@ enum {
 };
 
 typedef struct rich_trace_opts {
+    uint64_t seed;          /* Philox key of the reflectivity/QE draws of
+                               caller-supplied photons (photons from
+                               rich_emit use the rich_emit seed)             */
     int32_t precision;      /* RICH_PREC_*                                    */
     int32_t max_bounces;    /* mirror reflections, 1..RICH_MAX_BOUNCES        */
     int32_t max_steps;      /* surface interactions, 1..RICH_MAX_STEPS        */
@@ -217,6 +229,7 @@ typedef struct rich_trace_opts {
     int32_t refill_min;     /* refill a warp when at least this many lanes are
                                idle (1..32): the compaction interval          */
     int32_t chunk;          /* photons a warp takes from the queue at a time */
+    int32_t reserved;
 } rich_trace_opts;
 
 /* ----------------------------------------------------------------- outputs */
@@ -281,14 +294,14 @@ typedef struct rich_ctx rich_ctx;
 /* Create a context on CUDA device `device`, ordered on `stream` (a
  * cudaStream_t, or NULL for the legacy default stream). *out receives the
  * handle. Allocates the context's small device state. */
-rich_status rich_create(rich_ctx **out, int device, void *stream);
+RICH_API rich_status rich_create(rich_ctx **out, int device, void *stream);
 
 /* Release every resource owned by the context (geometry, scratch). Waits for
  * the context's stream. NULL is accepted. */
-rich_status rich_destroy(rich_ctx *ctx);
+RICH_API rich_status rich_destroy(rich_ctx *ctx);
 
 /* Change the stream later calls are ordered on. */
-rich_status rich_set_stream(rich_ctx *ctx, void *stream);
+RICH_API rich_status rich_set_stream(rich_ctx *ctx, void *stream);
 
 /* Upload a scene (Sec. 4.1: mirrors and detector as separate surfaces with
  * their own materials; Sec. 4.3: wavelength tables). All pointers in `desc`
@@ -296,7 +309,7 @@ rich_status rich_set_stream(rich_ctx *ctx, void *stream);
  * the host and uploads it. Replaces any previous geometry. Returns
  * RICH_ERR_GEOMETRY for inconsistent descriptions (bad indices, non-finite
  * values, pixel grid not matching a detector rectangle). Synchronous. */
-rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc *desc);
+RICH_API rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc *desc);
 
 /* Photon yield and emission (Sec. 3: cos(theta) = 1/(n beta), azimuth
  * uniform; photons are the input of the trace as in Sec. 4.2). For each
@@ -309,7 +322,7 @@ rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc *desc);
  * too small; nothing is written then) and out->n is set on the host after a
  * synchronisation. n_photons: if non-NULL, receives the total photon count
  * (synchronises the stream); if NULL the call stays asynchronous. */
-rich_status rich_emit(rich_ctx *ctx, const rich_tracks *tracks,
+RICH_API rich_status rich_emit(rich_ctx *ctx, const rich_tracks *tracks,
                       const rich_emit_params *params, rich_photons *out,
                       uint64_t *n_photons);
 
@@ -320,7 +333,7 @@ rich_status rich_emit(rich_ctx *ctx, const rich_tracks *tracks,
  * detectors accept with probability QE(lambda) (Sec. 4.3, in flight as in
  * Sec. 6); accepted photons are appended to out->hits and binned. Clears the
  * context's counters first; asynchronous. */
-rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
+RICH_API rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
                        const rich_trace_opts *opts, const rich_outputs *out);
 
 /* Wait for the last rich_trace and report its counters. n_hits (host, may be
@@ -328,14 +341,22 @@ rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
  * receives all counters. Returns RICH_ERR_OVERFLOW if hits were dropped for
  * lack of capacity (the count still reports every hit), or the device-side
  * error recorded during the trace. */
-rich_status rich_hits(rich_ctx *ctx, uint64_t *n_hits, rich_stats *stats);
+RICH_API rich_status rich_hits(rich_ctx *ctx, uint64_t *n_hits, rich_stats *stats);
+
+/* The library's random numbers: Philox4x32-10 (Salmon et al., SC'11) of n
+ * counters (DEVICE, n x 4 words, 16-byte aligned) under key = (seed low
+ * word, seed high word), written to out (DEVICE, n x 4 words, 16-byte
+ * aligned). With counter (block, photon, track id, event) this reproduces
+ * any draw of the map above. Asynchronous. */
+RICH_API rich_status rich_philox(rich_ctx *ctx, const uint32_t *counters,
+                                 uint64_t n, uint64_t seed, uint32_t *out);
 
 /* Message for the last failure on ctx (or of rich_create when ctx is NULL).
  * The string is owned by the library and valid until the next call. */
-const char *rich_last_error(rich_ctx *ctx);
+RICH_API const char *rich_last_error(rich_ctx *ctx);
 
 /* Library version string. */
-const char *rich_version(void);
+RICH_API const char *rich_version(void);
 
 #ifdef __cplusplus
 }

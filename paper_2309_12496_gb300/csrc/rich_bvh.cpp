@@ -1,0 +1,233 @@
+// rich_bvh.cpp -- host builder of the triangle BVH used by the trace kernel.
+//
+// Binned surface-area-heuristic build (12 bins per axis over the triangle
+// centroids, traversal cost 1, intersection cost 1 per triangle, at most 8
+// triangles per leaf), flattened into 64-byte two-wide nodes that carry
+// both children's boxes, in breadth-first order so the top levels of the
+// tree are contiguous. Triangles are re-ordered into leaf order.
+#include "rich_bvh.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <limits>
+#include <numeric>
+
+namespace rich {
+
+namespace {
+
+constexpr int kBins = 12;
+constexpr int kMaxLeaf = 8;
+constexpr float kTraversalCost = 1.0f;
+
+struct Box {
+    float lo[3], hi[3];
+    Box() {
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = std::numeric_limits<float>::infinity();
+            hi[k] = -std::numeric_limits<float>::infinity();
+        }
+    }
+    void grow(const Box &b) {
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = std::min(lo[k], b.lo[k]);
+            hi[k] = std::max(hi[k], b.hi[k]);
+        }
+    }
+    void grow(const float *p) {
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = std::min(lo[k], p[k]);
+            hi[k] = std::max(hi[k], p[k]);
+        }
+    }
+    float area() const {
+        if (!(hi[0] >= lo[0])) return 0.0f;
+        float dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
+        return 2.0f * (dx * dy + dy * dz + dz * dx);
+    }
+};
+
+struct Node {
+    Box box;
+    int left = -1, right = -1;  // children (build indices) for inner nodes
+    int first = 0, count = 0;   // leaf range in `order` when count > 0
+};
+
+struct Builder {
+    const float *v;
+    std::vector<Box> tri_box;
+    std::vector<float> cen;     // 3 per triangle
+    std::vector<int> order;
+    std::vector<Node> nodes;
+
+    int build(int first, int count) {
+        Node nd;
+        Box cb;
+        for (int i = first; i < first + count; ++i) {
+            nd.box.grow(tri_box[order[i]]);
+            cb.grow(&cen[3 * order[i]]);
+        }
+        const int id = (int)nodes.size();
+        nodes.push_back(nd);
+        if (count <= 2) return make_leaf(id, first, count);
+        // binned SAH over all three axes
+        float best_cost = std::numeric_limits<float>::infinity();
+        int best_axis = -1, best_split = -1;
+        for (int axis = 0; axis < 3; ++axis) {
+            const float ext = cb.hi[axis] - cb.lo[axis];
+            if (!(ext > 0.0f)) continue;
+            Box bb[kBins];
+            int bc[kBins] = {0};
+            const float scale = kBins / ext;
+            for (int i = first; i < first + count; ++i) {
+                int b = (int)((cen[3 * order[i] + axis] - cb.lo[axis]) * scale);
+                b = std::min(std::max(b, 0), kBins - 1);
+                bc[b]++;
+                bb[b].grow(tri_box[order[i]]);
+            }
+            float right_area[kBins];
+            int right_count[kBins];
+            Box acc;
+            int n = 0;
+            for (int b = kBins - 1; b > 0; --b) {
+                acc.grow(bb[b]);
+                n += bc[b];
+                right_area[b] = acc.area();
+                right_count[b] = n;
+            }
+            Box left;
+            int nl = 0;
+            for (int b = 0; b < kBins - 1; ++b) {
+                left.grow(bb[b]);
+                nl += bc[b];
+                const int nr = right_count[b + 1];
+                if (nl == 0 || nr == 0) continue;
+                const float cost = left.area() * nl + right_area[b + 1] * nr;
+                if (cost < best_cost) {
+                    best_cost = cost;
+                    best_axis = axis;
+                    best_split = b;
+                }
+            }
+        }
+        const float parent_area = std::max(nodes[id].box.area(), 1e-30f);
+        const float split_cost = kTraversalCost + best_cost / parent_area;
+        int mid;
+        if (best_axis < 0) {
+            if (count <= kMaxLeaf) return make_leaf(id, first, count);
+            mid = first + count / 2;   // coincident centroids: split by count
+        } else {
+            if (split_cost >= (float)count && count <= kMaxLeaf)
+                return make_leaf(id, first, count);
+            const float ext = cb.hi[best_axis] - cb.lo[best_axis];
+            const float scale = kBins / ext;
+            auto it = std::partition(
+                order.begin() + first, order.begin() + first + count, [&](int t) {
+                    int b = (int)((cen[3 * t + best_axis] - cb.lo[best_axis]) * scale);
+                    b = std::min(std::max(b, 0), kBins - 1);
+                    return b <= best_split;
+                });
+            mid = (int)(it - order.begin());
+            if (mid == first || mid == first + count) mid = first + count / 2;
+        }
+        const int l = build(first, mid - first);
+        const int r = build(mid, first + count - mid);
+        nodes[id].left = l;
+        nodes[id].right = r;
+        return id;
+    }
+
+    int make_leaf(int id, int first, int count) {
+        nodes[id].first = first;
+        nodes[id].count = count;
+        return id;
+    }
+};
+
+void put_box(DevNode &d, int slot, const Box &b) {
+    if (slot == 0) {
+        d.lo0x = b.lo[0]; d.lo0y = b.lo[1]; d.lo0z = b.lo[2];
+        d.hi0x = b.hi[0]; d.hi0y = b.hi[1]; d.hi0z = b.hi[2];
+    } else {
+        d.lo1x = b.lo[0]; d.lo1y = b.lo[1]; d.lo1z = b.lo[2];
+        d.hi1x = b.hi[0]; d.hi1y = b.hi[1]; d.hi1z = b.hi[2];
+    }
+}
+
+}  // namespace
+
+bool build_bvh(const float *vertices, int64_t n_tris, BvhResult &out,
+               std::string &err) {
+    out = BvhResult();
+    if (n_tris <= 0) return true;
+    if (n_tris >= (int64_t(1) << 27)) {
+        err = "too many triangles for the BVH leaf encoding";
+        return false;
+    }
+    Builder b;
+    b.v = vertices;
+    b.tri_box.resize((size_t)n_tris);
+    b.cen.resize(3 * (size_t)n_tris);
+    for (int64_t i = 0; i < n_tris; ++i) {
+        const float *t = vertices + 9 * i;
+        Box bx;
+        bx.grow(t);
+        bx.grow(t + 3);
+        bx.grow(t + 6);
+        for (int k = 0; k < 3; ++k) {
+            if (!std::isfinite(t[k]) || !std::isfinite(t[3 + k]) || !std::isfinite(t[6 + k])) {
+                err = "non-finite triangle vertex";
+                return false;
+            }
+            b.cen[3 * i + k] = (t[k] + t[3 + k] + t[6 + k]) * (1.0f / 3.0f);
+        }
+        b.tri_box[i] = bx;
+    }
+    b.order.resize((size_t)n_tris);
+    std::iota(b.order.begin(), b.order.end(), 0);
+    b.nodes.reserve(2 * (size_t)n_tris);
+    const int root = b.build(0, (int)n_tris);
+
+    out.leaf_order = b.order;
+    auto leaf_code = [&](const Node &n) { return ~((n.first << 3) | (n.count - 1)); };
+    // breadth-first flattening of the inner nodes
+    if (b.nodes[root].count > 0) {
+        DevNode d;
+        std::memset(&d, 0, sizeof d);
+        put_box(d, 0, b.nodes[root].box);
+        put_box(d, 1, b.nodes[root].box);
+        d.child0 = d.child1 = leaf_code(b.nodes[root]);
+        out.nodes.push_back(d);
+        out.depth = 1;
+        return true;
+    }
+    std::vector<int> dev_index(b.nodes.size(), -1);
+    std::deque<std::pair<int, int>> q;   // (build node, depth)
+    q.push_back({root, 1});
+    std::vector<int> bfs;
+    while (!q.empty()) {
+        auto [n, depth] = q.front();
+        q.pop_front();
+        dev_index[n] = (int)bfs.size();
+        bfs.push_back(n);
+        out.depth = std::max(out.depth, depth);
+        for (int c : {b.nodes[n].left, b.nodes[n].right})
+            if (b.nodes[c].count == 0) q.push_back({c, depth + 1});
+    }
+    out.nodes.resize(bfs.size());
+    for (size_t i = 0; i < bfs.size(); ++i) {
+        const Node &n = b.nodes[bfs[i]];
+        DevNode &d = out.nodes[i];
+        std::memset(&d, 0, sizeof d);
+        const Node &l = b.nodes[n.left], &r = b.nodes[n.right];
+        put_box(d, 0, l.box);
+        put_box(d, 1, r.box);
+        d.child0 = l.count > 0 ? leaf_code(l) : dev_index[n.left];
+        d.child1 = r.count > 0 ? leaf_code(r) : dev_index[n.right];
+    }
+    return true;
+}
+
+}  // namespace rich

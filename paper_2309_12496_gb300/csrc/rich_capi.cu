@@ -1,0 +1,585 @@
+// rich_capi.cu -- the C ABI (rich.h): context, geometry upload, emission,
+// trace and counter read-back. Host code only; every step of the photon
+// path itself runs in the kernels of rich_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "rich_bvh.h"
+#include "rich_internal.h"
+
+using namespace rich;
+
+struct rich_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int n_sm = 1;
+    std::string err;
+    // geometry (one device allocation, sub-allocated)
+    bool has_geometry = false;
+    void *d_geom = nullptr;
+    SceneView sc{};
+    int bvh_depth = 0;
+    // emission scratch
+    int64_t track_cap = 0;
+    TrackRec *d_rec = nullptr;
+    double2 *d_cs = nullptr;
+    uint32_t *d_counts = nullptr;
+    uint64_t *d_offsets = nullptr;
+    unsigned long long *d_bsum = nullptr;
+    bool has_emission = false;
+    int64_t n_tracks = 0;
+    uint32_t key0 = 0, key1 = 0;
+    float inv1 = 0.f, span = 0.f;
+    // small device state: counters + photon total
+    Counters *d_ctr = nullptr;
+    unsigned long long *d_total = nullptr;
+    Counters *h_ctr = nullptr;            // pinned
+    unsigned long long *h_total = nullptr; // pinned
+    // last trace
+    bool traced = false;
+    bool last_ext = false;
+    uint64_t last_ext_n = 0;
+    uint64_t last_capacity = 0;
+};
+
+static thread_local std::string g_create_error;
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+rich_status fail(rich_ctx *c, rich_status st, const std::string &msg) {
+    if (c) c->err = msg;
+    return st;
+}
+
+rich_status cuda_fail(rich_ctx *c, cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();
+    return fail(c, e == cudaErrorMemoryAllocation ? RICH_ERR_OOM : RICH_ERR_CUDA, m);
+}
+
+#define RICH_CUDA(call)                                              \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);     \
+    } while (0)
+
+bool finite3(const float *v) {
+    return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]);
+}
+
+void free_emission(rich_ctx *ctx) {
+    cudaFree(ctx->d_rec);
+    cudaFree(ctx->d_cs);
+    cudaFree(ctx->d_counts);
+    cudaFree(ctx->d_offsets);
+    cudaFree(ctx->d_bsum);
+    ctx->d_rec = nullptr;
+    ctx->d_cs = nullptr;
+    ctx->d_counts = nullptr;
+    ctx->d_offsets = nullptr;
+    ctx->d_bsum = nullptr;
+    ctx->track_cap = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+RICH_API const char *rich_version(void) { return "rich-gb300 0.1 (sm_103a)"; }
+
+RICH_API const char *rich_last_error(rich_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+RICH_API rich_status rich_create(rich_ctx **out, int device, void *stream) {
+    if (!out) {
+        g_create_error = "rich_create: out is NULL";
+        return RICH_ERR_ARG;
+    }
+    *out = nullptr;
+    int n_dev = 0;
+    cudaError_t e = cudaGetDeviceCount(&n_dev);
+    if (e != cudaSuccess || device < 0 || device >= n_dev) {
+        g_create_error = std::string("rich_create: no CUDA device ") + std::to_string(device) +
+                         (e != cudaSuccess ? std::string(" (") + cudaGetErrorString(e) + ")" : "");
+        cudaGetLastError();
+        return e != cudaSuccess ? RICH_ERR_CUDA : RICH_ERR_ARG;
+    }
+    rich_ctx *ctx = new rich_ctx();
+    ctx->device = device;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    DeviceGuard g(device);
+    cudaDeviceProp prop;
+    if ((e = cudaGetDeviceProperties(&prop, device)) != cudaSuccess ||
+        (e = cudaMalloc(&ctx->d_ctr, sizeof(Counters))) != cudaSuccess ||
+        (e = cudaMalloc(&ctx->d_total, sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMallocHost(&ctx->h_ctr, sizeof(Counters))) != cudaSuccess ||
+        (e = cudaMallocHost(&ctx->h_total, sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMemset(ctx->d_ctr, 0, sizeof(Counters))) != cudaSuccess ||
+        (e = cudaMemset(ctx->d_total, 0, sizeof(unsigned long long))) != cudaSuccess) {
+        g_create_error = std::string("rich_create: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        cudaFree(ctx->d_ctr);
+        cudaFree(ctx->d_total);
+        cudaFreeHost(ctx->h_ctr);
+        cudaFreeHost(ctx->h_total);
+        delete ctx;
+        return e == cudaErrorMemoryAllocation ? RICH_ERR_OOM : RICH_ERR_CUDA;
+    }
+    ctx->n_sm = prop.multiProcessorCount;
+    *out = ctx;
+    return RICH_OK;
+}
+
+RICH_API rich_status rich_destroy(rich_ctx *ctx) {
+    if (!ctx) return RICH_OK;
+    {
+        DeviceGuard g(ctx->device);
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->d_geom);
+        free_emission(ctx);
+        cudaFree(ctx->d_ctr);
+        cudaFree(ctx->d_total);
+        cudaFreeHost(ctx->h_ctr);
+        cudaFreeHost(ctx->h_total);
+        cudaGetLastError();
+    }
+    delete ctx;
+    return RICH_OK;
+}
+
+RICH_API rich_status rich_set_stream(rich_ctx *ctx, void *stream) {
+    if (!ctx) return RICH_ERR_ARG;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    return RICH_OK;
+}
+
+// ---------------------------------------------------------------- geometry
+RICH_API rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc *g) {
+    if (!ctx) return RICH_ERR_ARG;
+    if (!g) return fail(ctx, RICH_ERR_ARG, "rich_init_geometry: desc is NULL");
+    DeviceGuard guard(ctx->device);
+    auto bad = [&](const std::string &m) { return fail(ctx, RICH_ERR_GEOMETRY, "rich_init_geometry: " + m); };
+    if (g->n_tables < 0 || g->n_materials < 0 || g->n_spheres < 0 || g->n_rects < 0 ||
+        g->n_triangles < 0)
+        return bad("negative count");
+    if (g->n_tables > RICH_MAX_TABLES) return bad("more than 8 tables");
+    if (g->n_materials > RICH_MAX_MATERIALS) return bad("more than 32 materials");
+    if (g->n_spheres > RICH_MAX_TILES) return bad("more than 64 sphere tiles");
+    if (g->n_rects > RICH_MAX_RECTS) return bad("more than 32 rectangles");
+    if ((g->n_tables && !g->tables) || (g->n_materials && !g->materials) ||
+        (g->n_spheres && !g->spheres) || (g->n_rects && !g->rects) ||
+        (g->n_triangles && (!g->tri_vertices || !g->tri_material)))
+        return bad("NULL array with a non-zero count");
+    for (int i = 0; i < g->n_tables; ++i) {
+        const rich_table &t = g->tables[i];
+        if (t.kind < 0 || t.kind > 2) return bad("table kind");
+        if (t.kind == RICH_TABLE_HIST && (t.nbins < 1 || t.nbins > RICH_TABLE_MAX_BINS || !(t.p1 > 0.f)))
+            return bad("histogram table needs 1..64 bins and a positive width");
+        if (t.kind == RICH_TABLE_GAUSS && !(t.p2 != 0.f)) return bad("Gaussian table width is 0");
+    }
+    bool any_smooth = false;
+    for (int i = 0; i < g->n_materials; ++i) {
+        const rich_material &m = g->materials[i];
+        if (m.kind < 0 || m.kind > 2) return bad("material kind");
+        if (m.kind != RICH_MAT_ABSORBER && (m.table < 0 || m.table >= g->n_tables))
+            return bad("material table index out of range");
+        if (m.kind == RICH_MAT_DETECTOR && (m.plane < 0 || m.plane >= RICH_MAX_PLANES))
+            return bad("detector plane index must be 0..7");
+        if (m.flags & RICH_MAT_SMOOTH) any_smooth = true;
+    }
+    if (any_smooth && g->n_triangles && !g->tri_normals)
+        return bad("smooth material without vertex normals");
+    // ---- sphere groups (tiles sharing a sphere)
+    std::vector<int> tile_group(g->n_spheres);
+    std::vector<std::tuple<float, float, float, float>> spheres;
+    for (int i = 0; i < g->n_spheres; ++i) {
+        const rich_sphere &s = g->spheres[i];
+        if (!finite3(s.center) || !finite3(s.axis) || !finite3(s.e1) || !finite3(s.e2) ||
+            !(s.radius > 0.f) || !std::isfinite(s.radius))
+            return bad("sphere tile with non-finite or non-positive values");
+        if (s.n_edges < 0 || s.n_edges > RICH_SPHERE_MAX_EDGES) return bad("sphere tile edges 0..8");
+        if (s.material < 0 || s.material >= g->n_materials) return bad("sphere material index");
+        auto key = std::make_tuple(s.center[0], s.center[1], s.center[2], s.radius);
+        auto it = std::find(spheres.begin(), spheres.end(), key);
+        if (it == spheres.end()) {
+            spheres.push_back(key);
+            tile_group[i] = (int)spheres.size() - 1;
+        } else {
+            tile_group[i] = (int)(it - spheres.begin());
+        }
+    }
+    if ((int)spheres.size() > RICH_MAX_GROUPS) return bad("more than 16 distinct spheres");
+    std::vector<DevSphereGroup> groups(spheres.size());
+    std::vector<DevTile> tiles;
+    for (size_t gi = 0; gi < spheres.size(); ++gi) {
+        DevSphereGroup &G = groups[gi];
+        G.cx = std::get<0>(spheres[gi]);
+        G.cy = std::get<1>(spheres[gi]);
+        G.cz = std::get<2>(spheres[gi]);
+        const double R = std::get<3>(spheres[gi]);
+        G.r2 = R * R;
+        G.radius = (float)R;
+        G.inv_radius = (float)(1.0 / R);
+        G.first = (int)tiles.size();
+        for (int i = 0; i < g->n_spheres; ++i) {
+            if (tile_group[i] != (int)gi) continue;
+            const rich_sphere &s = g->spheres[i];
+            DevTile T;
+            std::memset(&T, 0, sizeof T);
+            T.ax = s.axis[0]; T.ay = s.axis[1]; T.az = s.axis[2]; T.cos_min = s.cos_min;
+            T.e1x = s.e1[0]; T.e1y = s.e1[1]; T.e1z = s.e1[2];
+            T.inv_radius = (float)(1.0 / (double)s.radius);
+            T.e2x = s.e2[0]; T.e2y = s.e2[1]; T.e2z = s.e2[2];
+            T.n_edges = s.n_edges;
+            T.material = s.material;
+            T.group = (int)gi;
+            T.prim = i;
+            for (int e = 0; e < s.n_edges; ++e)
+                for (int k = 0; k < 3; ++k) T.edges[e][k] = s.edges[e][k];
+            tiles.push_back(T);
+        }
+        G.count = (int)tiles.size() - G.first;
+    }
+    // ---- rectangles and planes
+    std::vector<DevRect> rects(g->n_rects);
+    std::vector<DevRectD> rects_d(g->n_rects);
+    int plane_nx[RICH_MAX_PLANES] = {0}, plane_ny[RICH_MAX_PLANES] = {0};
+    int n_planes = 0;
+    for (int i = 0; i < g->n_rects; ++i) {
+        const rich_rect &r = g->rects[i];
+        if (!finite3(r.origin) || !finite3(r.u_axis) || !finite3(r.v_axis) || !finite3(r.normal) ||
+            !(r.width > 0.f) || !(r.height > 0.f) || !std::isfinite(r.width) || !std::isfinite(r.height))
+            return bad("rectangle with non-finite or non-positive values");
+        if (r.material < 0 || r.material >= g->n_materials) return bad("rectangle material index");
+        const rich_material &m = g->materials[r.material];
+        DevRect &R = rects[i];
+        std::memset(&R, 0, sizeof R);
+        R.ox = r.origin[0]; R.oy = r.origin[1]; R.oz = r.origin[2]; R.w = r.width;
+        R.ux = r.u_axis[0]; R.uy = r.u_axis[1]; R.uz = r.u_axis[2]; R.h = r.height;
+        R.vx = r.v_axis[0]; R.vy = r.v_axis[1]; R.vz = r.v_axis[2]; R.pitch = r.pitch;
+        R.nx = r.normal[0]; R.ny = r.normal[1]; R.nz = r.normal[2];
+        R.material = r.material;
+        R.gx = r.nx;
+        R.gy = r.ny;
+        R.plane = m.kind == RICH_MAT_DETECTOR ? m.plane : -1;
+        R.prim = g->n_spheres + i;
+        DevRectD &D = rects_d[i];
+        D.ox = r.origin[0]; D.oy = r.origin[1]; D.oz = r.origin[2];
+        D.ux = r.u_axis[0]; D.uy = r.u_axis[1]; D.uz = r.u_axis[2];
+        D.vx = r.v_axis[0]; D.vy = r.v_axis[1]; D.vz = r.v_axis[2];
+        D.nx = r.normal[0]; D.ny = r.normal[1]; D.nz = r.normal[2];
+        if (m.kind == RICH_MAT_DETECTOR) {
+            if (r.nx <= 0 || r.ny <= 0 || r.nx > 65535 || r.ny > 65535 || !(r.pitch > 0.f))
+                return bad("detector rectangle needs a pixel grid (1..65535) and a pitch");
+            const double w = (double)r.nx * r.pitch, h = (double)r.ny * r.pitch;
+            if (std::fabs(w - r.width) > 1e-3 * w || std::fabs(h - r.height) > 1e-3 * h)
+                return bad("detector rectangle size differs from its pixel grid");
+            if (plane_nx[m.plane] && (plane_nx[m.plane] != r.nx || plane_ny[m.plane] != r.ny))
+                return bad("one detector plane index used with two grid shapes");
+            plane_nx[m.plane] = r.nx;
+            plane_ny[m.plane] = r.ny;
+            n_planes = std::max(n_planes, m.plane + 1);
+        }
+    }
+    // ---- triangles + BVH
+    BvhResult bvh;
+    std::string berr;
+    const int64_t nt = g->n_triangles;
+    for (int64_t i = 0; i < nt; ++i)
+        if (g->tri_material[i] < 0 || g->tri_material[i] >= g->n_materials)
+            return bad("triangle material index");
+    if (!build_bvh(g->tri_vertices, nt, bvh, berr)) return bad(berr);
+    if (bvh.depth >= RICH_BVH_STACK) return bad("BVH deeper than the traversal stack");
+    // structural check: children point strictly forward (traversal ends),
+    // leaf ranges stay inside the triangle array
+    for (size_t i = 0; i < bvh.nodes.size(); ++i) {
+        for (int c : {bvh.nodes[i].child0, bvh.nodes[i].child1}) {
+            if (c >= 0) {
+                if ((size_t)c <= i || (size_t)c >= bvh.nodes.size()) return bad("BVH child index");
+            } else {
+                const int code = ~c;
+                const int64_t first = code >> 3, count = (code & 7) + 1;
+                if (first + count > nt) return bad("BVH leaf range");
+            }
+        }
+    }
+    const int prim_base = g->n_spheres + g->n_rects;
+    std::vector<DevTri> tris((size_t)nt);
+    std::vector<float> normals(any_smooth ? 9 * (size_t)nt : 0);
+    for (int64_t k = 0; k < nt; ++k) {
+        const int src = bvh.leaf_order[(size_t)k];
+        const float *v = g->tri_vertices + 9 * (int64_t)src;
+        DevTri &T = tris[(size_t)k];
+        T.v0x = v[0]; T.v0y = v[1]; T.v0z = v[2];
+        T.v1x = v[3]; T.v1y = v[4]; T.v1z = v[5];
+        T.v2x = v[6]; T.v2y = v[7]; T.v2z = v[8];
+        T.prim = prim_base + src;
+        T.material = g->tri_material[src];
+        T.pad = 0;
+        if (any_smooth) std::memcpy(&normals[9 * (size_t)k], g->tri_normals + 9 * (int64_t)src, 36);
+    }
+    std::vector<DevTable> tables(g->n_tables);
+    for (int i = 0; i < g->n_tables; ++i) std::memcpy(&tables[i], &g->tables[i], sizeof(DevTable));
+    std::vector<DevMaterial> mats(g->n_materials);
+    for (int i = 0; i < g->n_materials; ++i) std::memcpy(&mats[i], &g->materials[i], sizeof(DevMaterial));
+
+    // ---- one device allocation
+    auto r256 = [](size_t b) { return (b + 255) & ~size_t(255); };
+    size_t sizes[] = {sizeof(DevSphereGroup) * groups.size(), sizeof(DevTile) * tiles.size(),
+                      sizeof(DevRect) * rects.size(), sizeof(DevRectD) * rects_d.size(),
+                      sizeof(DevTable) * tables.size(), sizeof(DevMaterial) * mats.size(),
+                      sizeof(DevNode) * bvh.nodes.size(), sizeof(DevTri) * tris.size(),
+                      sizeof(float) * normals.size()};
+    const void *srcs[] = {groups.data(), tiles.data(), rects.data(), rects_d.data(),
+                          tables.data(), mats.data(), bvh.nodes.data(), tris.data(),
+                          normals.data()};
+    size_t total = 0, offs[9];
+    for (int i = 0; i < 9; ++i) {
+        offs[i] = total;
+        total += r256(sizes[i]);
+    }
+    RICH_CUDA(cudaStreamSynchronize(ctx->stream));
+    cudaFree(ctx->d_geom);
+    ctx->d_geom = nullptr;
+    ctx->has_geometry = false;
+    void *buf = nullptr;
+    RICH_CUDA(cudaMalloc(&buf, std::max<size_t>(total, 256)));
+    ctx->d_geom = buf;
+    for (int i = 0; i < 9; ++i)
+        if (sizes[i]) RICH_CUDA(cudaMemcpy((char *)buf + offs[i], srcs[i], sizes[i], cudaMemcpyHostToDevice));
+    SceneView sc{};
+    auto at = [&](int i) { return sizes[i] ? (const void *)((char *)buf + offs[i]) : nullptr; };
+    sc.groups = (const DevSphereGroup *)at(0);
+    sc.tiles = (const DevTile *)at(1);
+    sc.rects = (const DevRect *)at(2);
+    sc.rects_d = (const DevRectD *)at(3);
+    sc.tables = (const DevTable *)at(4);
+    sc.materials = (const DevMaterial *)at(5);
+    sc.nodes = (const DevNode *)at(6);
+    sc.tris = (const DevTri *)at(7);
+    sc.tri_normals = (const float *)at(8);
+    sc.n_groups = (int)groups.size();
+    sc.n_tiles = (int)tiles.size();
+    sc.n_rects = (int)rects.size();
+    sc.n_tables = (int)tables.size();
+    sc.n_materials = (int)mats.size();
+    sc.n_nodes = (int)bvh.nodes.size();
+    sc.n_tris = nt;
+    sc.tri_prim_base = prim_base;
+    sc.n_planes = n_planes;
+    int64_t off = 0;
+    for (int p = 0; p < RICH_MAX_PLANES; ++p) {
+        sc.plane_offset[p] = off;
+        sc.plane_nx[p] = plane_nx[p];
+        if (p < n_planes) off += (int64_t)plane_nx[p] * plane_ny[p];
+    }
+    sc.pixels_per_event = off;
+    ctx->sc = sc;
+    ctx->bvh_depth = bvh.depth;
+    ctx->has_geometry = true;
+    return RICH_OK;
+}
+
+// ----------------------------------------------------------------- emission
+RICH_API rich_status rich_emit(rich_ctx *ctx, const rich_tracks *t,
+                               const rich_emit_params *prm, rich_photons *out,
+                               uint64_t *n_photons) {
+    if (!ctx) return RICH_ERR_ARG;
+    if (!t || !prm) return fail(ctx, RICH_ERR_ARG, "rich_emit: tracks or params is NULL");
+    if (t->n < 0 || t->n > (int64_t(1) << 31))
+        return fail(ctx, RICH_ERR_ARG, "rich_emit: track count out of range");
+    if (t->n > 0 && (!t->x || !t->y || !t->z || !t->dx || !t->dy || !t->dz || !t->p ||
+                     !t->mass || !t->length || !t->event))
+        return fail(ctx, RICH_ERR_ARG, "rich_emit: a required track array is NULL");
+    if (!(prm->n_minus_1 >= 0.f) || !std::isfinite(prm->n_minus_1) || !(prm->lambda_min > 0.f) ||
+        !(prm->lambda_max > prm->lambda_min) || !std::isfinite(prm->lambda_max))
+        return fail(ctx, RICH_ERR_ARG, "rich_emit: need n-1 >= 0 and 0 < lambda_min < lambda_max");
+    DeviceGuard guard(ctx->device);
+    const int64_t n = t->n;
+    if (n + 1 > ctx->track_cap) {
+        RICH_CUDA(cudaStreamSynchronize(ctx->stream));
+        free_emission(ctx);
+        const int64_t cap = std::max<int64_t>(n + 1, 1024);
+        const int64_t blocks = (cap + yield_block_threads() - 1) / yield_block_threads();
+        RICH_CUDA(cudaMalloc(&ctx->d_rec, sizeof(TrackRec) * cap));
+        RICH_CUDA(cudaMalloc(&ctx->d_cs, sizeof(double2) * cap));
+        RICH_CUDA(cudaMalloc(&ctx->d_counts, sizeof(uint32_t) * cap));
+        RICH_CUDA(cudaMalloc(&ctx->d_offsets, sizeof(uint64_t) * (cap + 1)));
+        RICH_CUDA(cudaMalloc(&ctx->d_bsum, sizeof(unsigned long long) * (blocks + 1)));
+        ctx->track_cap = cap;
+    }
+    ctx->key0 = (uint32_t)prm->seed;
+    ctx->key1 = (uint32_t)(prm->seed >> 32);
+    {
+        // FP32 spectrum constants, one IEEE operation each
+        volatile float l1 = prm->lambda_min, l2 = prm->lambda_max;
+        volatile float inv1 = 1.0f / l1;
+        volatile float inv2 = 1.0f / l2;
+        volatile float span = inv1 - inv2;
+        ctx->inv1 = inv1;
+        ctx->span = span;
+    }
+    TracksView tv{n, t->x, t->y, t->z, t->dx, t->dy, t->dz, t->p, t->mass, t->length,
+                  t->event, t->id, t->n_fixed};
+    if (n == 0) {
+        RICH_CUDA(cudaMemsetAsync(ctx->d_total, 0, sizeof(unsigned long long), ctx->stream));
+        RICH_CUDA(cudaMemsetAsync(ctx->d_offsets, 0, sizeof(uint64_t), ctx->stream));
+    } else {
+        RICH_CUDA(launch_yield(tv, (double)prm->n_minus_1, prm->lambda_min, prm->lambda_max,
+                               ctx->key0, ctx->key1, ctx->d_rec, ctx->d_cs, ctx->d_counts,
+                               ctx->d_bsum, ctx->stream));
+        RICH_CUDA(launch_offsets(ctx->d_counts, ctx->d_bsum, n, ctx->d_offsets, ctx->d_total,
+                                 ctx->stream));
+    }
+    ctx->n_tracks = n;
+    ctx->has_emission = true;
+    if (n_photons || out) {
+        RICH_CUDA(cudaMemcpyAsync(ctx->h_total, ctx->d_total, sizeof(unsigned long long),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+        RICH_CUDA(cudaStreamSynchronize(ctx->stream));
+        if (n_photons) *n_photons = *ctx->h_total;
+    }
+    if (out) {
+        const uint64_t total = *ctx->h_total;
+        if (total > out->capacity)
+            return fail(ctx, RICH_ERR_OVERFLOW, "rich_emit: photon capacity " +
+                                                    std::to_string(out->capacity) + " < " +
+                                                    std::to_string(total));
+        if (total && (!out->x || !out->y || !out->z || !out->dx || !out->dy || !out->dz ||
+                      !out->lambda || !out->event || !out->track || !out->photon))
+            return fail(ctx, RICH_ERR_ARG, "rich_emit: a photon output array is NULL");
+        EmitView em{ctx->d_rec, ctx->d_cs, ctx->d_offsets, ctx->d_total, n,
+                    ctx->key0, ctx->key1, ctx->inv1, ctx->span};
+        RICH_CUDA(launch_materialize(ctx->sc, em, total, *out, ctx->stream));
+        out->n = total;
+    }
+    return RICH_OK;
+}
+
+// -------------------------------------------------------------------- trace
+RICH_API rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
+                                const rich_trace_opts *o, const rich_outputs *out) {
+    if (!ctx) return RICH_ERR_ARG;
+    if (!o || !out) return fail(ctx, RICH_ERR_ARG, "rich_trace: opts or outputs is NULL");
+    if (!ctx->has_geometry) return fail(ctx, RICH_ERR_STATE, "rich_trace: no geometry");
+    if (!in && !ctx->has_emission)
+        return fail(ctx, RICH_ERR_STATE, "rich_trace: no photons (call rich_emit first)");
+    if (o->precision != RICH_PREC_FP32 && o->precision != RICH_PREC_REFINE64)
+        return fail(ctx, RICH_ERR_ARG, "rich_trace: precision");
+    if (o->max_bounces < 1 || o->max_bounces > RICH_MAX_BOUNCES || o->max_steps < 1 ||
+        o->max_steps > RICH_MAX_STEPS || !(o->t_min >= 0.f))
+        return fail(ctx, RICH_ERR_ARG, "rich_trace: max_bounces 1..8, max_steps 1..16, t_min >= 0");
+    if (out->hit_capacity && !out->hits)
+        return fail(ctx, RICH_ERR_ARG, "rich_trace: hits is NULL with a non-zero capacity");
+    if (in && in->n && (!in->x || !in->y || !in->z || !in->dx || !in->dy || !in->dz ||
+                        !in->lambda || !in->event || !in->track || !in->photon))
+        return fail(ctx, RICH_ERR_ARG, "rich_trace: a photon input array is NULL");
+    const int threads = o->block_threads ? o->block_threads : 256;
+    if (threads % 32 != 0 || threads < 32 || threads > 256)
+        return fail(ctx, RICH_ERR_ARG, "rich_trace: block_threads must be 32..256, a multiple of 32");
+    const int refill = o->refill_min ? o->refill_min : 16;
+    if (refill < 1 || refill > 32) return fail(ctx, RICH_ERR_ARG, "rich_trace: refill_min 1..32");
+    const int chunk = o->chunk ? o->chunk : 128;
+    if (chunk < 1 || chunk > (1 << 20)) return fail(ctx, RICH_ERR_ARG, "rich_trace: chunk 1..2^20");
+    DeviceGuard guard(ctx->device);
+    RICH_CUDA(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), ctx->stream));
+    TraceParams p{};
+    p.precision = o->precision;
+    p.max_bounces = o->max_bounces;
+    p.max_steps = o->max_steps;
+    p.t_min = o->t_min;
+    p.refill_min = refill;
+    p.chunk = chunk;
+    p.hits = out->hits;
+    p.hit_capacity = out->hits ? out->hit_capacity : 0;
+    p.pixel_counts = out->pixel_counts;
+    p.event_sums = out->event_sums;
+    p.n_hist_events = (out->pixel_counts || out->event_sums) ? out->n_hist_events : 0;
+    p.fate = out->fate;
+    const bool refine = o->precision == RICH_PREC_REFINE64;
+    LaunchShape shape;
+    shape.threads = threads;
+    shape.smem = trace_smem_bytes(ctx->sc);
+    const int bps = o->blocks_per_sm ? o->blocks_per_sm
+                                     : trace_blocks_per_sm(in != nullptr, refine, threads, shape.smem);
+    shape.blocks = std::max(1, bps) * ctx->n_sm;
+    EmitView em{ctx->d_rec, ctx->d_cs, ctx->d_offsets, ctx->d_total, ctx->n_tracks,
+                ctx->key0, ctx->key1, ctx->inv1, ctx->span};
+    if (in) {
+        em.key0 = (uint32_t)o->seed;
+        em.key1 = (uint32_t)(o->seed >> 32);
+        ExtView ev{in->n, in->x, in->y, in->z, in->dx, in->dy, in->dz, in->lambda,
+                   in->event, in->track, in->photon};
+        if (in->n) RICH_CUDA(launch_trace(ctx->sc, &em, &ev, p, ctx->d_ctr, shape, ctx->stream));
+        ctx->last_ext = true;
+        ctx->last_ext_n = in->n;
+    } else {
+        RICH_CUDA(launch_trace(ctx->sc, &em, nullptr, p, ctx->d_ctr, shape, ctx->stream));
+        ctx->last_ext = false;
+    }
+    ctx->traced = true;
+    ctx->last_capacity = p.hit_capacity;
+    return RICH_OK;
+}
+
+RICH_API rich_status rich_hits(rich_ctx *ctx, uint64_t *n_hits, rich_stats *stats) {
+    if (!ctx) return RICH_ERR_ARG;
+    if (!ctx->traced) return fail(ctx, RICH_ERR_STATE, "rich_hits: no trace to report");
+    DeviceGuard guard(ctx->device);
+    RICH_CUDA(cudaMemcpyAsync(ctx->h_ctr, ctx->d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost,
+                              ctx->stream));
+    RICH_CUDA(cudaMemcpyAsync(ctx->h_total, ctx->d_total, sizeof(unsigned long long),
+                              cudaMemcpyDeviceToHost, ctx->stream));
+    RICH_CUDA(cudaStreamSynchronize(ctx->stream));
+    const Counters &c = *ctx->h_ctr;
+    if (n_hits) *n_hits = c.hits;
+    if (stats) {
+        std::memset(stats, 0, sizeof *stats);
+        stats->n_photons = ctx->last_ext ? ctx->last_ext_n : *ctx->h_total;
+        stats->n_hits = c.hits;
+        for (int k = 0; k < 8; ++k) stats->n_fate[k] = c.fate[k];
+        stats->device_status = c.status;
+    }
+    if (c.status != 0)
+        return fail(ctx, (rich_status)c.status,
+                    "rich_hits: device reported status " + std::to_string(c.status));
+    if (c.hits > ctx->last_capacity)
+        return fail(ctx, RICH_ERR_OVERFLOW, "rich_hits: " + std::to_string(c.hits) +
+                                                " hits for capacity " +
+                                                std::to_string(ctx->last_capacity));
+    return RICH_OK;
+}
+
+RICH_API rich_status rich_philox(rich_ctx *ctx, const uint32_t *counters, uint64_t n,
+                                 uint64_t seed, uint32_t *out) {
+    if (!ctx) return RICH_ERR_ARG;
+    if (n && (!counters || !out)) return fail(ctx, RICH_ERR_ARG, "rich_philox: NULL buffer");
+    if ((reinterpret_cast<uintptr_t>(counters) | reinterpret_cast<uintptr_t>(out)) & 15u)
+        return fail(ctx, RICH_ERR_ARG, "rich_philox: buffers must be 16-byte aligned");
+    DeviceGuard guard(ctx->device);
+    RICH_CUDA(launch_philox(counters, n, seed, out, ctx->stream));
+    return RICH_OK;
+}
+
+}  // extern "C"

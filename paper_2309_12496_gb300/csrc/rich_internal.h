@@ -1,0 +1,180 @@
+// rich_internal.h -- layouts shared by the C-ABI host code and the kernels.
+//
+// Device layout of a scene (built by rich_init_geometry):
+//   * sphere groups: tiles sharing one sphere (centre, radius) are grouped so
+//     the FP64 quadratic is solved once per sphere and the FP32 aperture
+//     tests run per tile;
+//   * rectangles, response tables and materials: small arrays staged into
+//     shared memory by every trace block;
+//   * triangles: 48-byte records in BVH leaf order; per-vertex normals in a
+//     parallel array; BVH2 nodes of 64 bytes holding both children's boxes.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "rich.h"
+
+#define RICH_MAX_TILES 64
+#define RICH_MAX_GROUPS 16
+#define RICH_MAX_RECTS 32
+#define RICH_MAX_TABLES 8
+#define RICH_MAX_MATERIALS 32
+#define RICH_MAX_PLANES 8
+#define RICH_BVH_STACK 64
+
+namespace rich {
+
+struct DevTable {            // same fields as rich_table
+    int32_t kind, nbins;
+    float p0, p1, p2, p3;
+    float values[RICH_TABLE_MAX_BINS];
+};
+
+struct DevMaterial {
+    int32_t kind, table, plane, flags;
+};
+
+struct DevSphereGroup {      // 48 B
+    double cx, cy, cz, r2;   // FP64 centre and R^2 (from the FP32 inputs)
+    float radius, inv_radius;
+    int32_t first, count;    // tiles [first, first + count)
+};
+
+struct DevTile {             // 160 B
+    float ax, ay, az, cos_min;
+    float e1x, e1y, e1z, inv_radius;
+    float e2x, e2y, e2z;
+    int32_t n_edges;
+    int32_t material, group, prim, pad;
+    float edges[RICH_SPHERE_MAX_EDGES][3];
+};
+
+struct DevRect {             // 80 B
+    float ox, oy, oz, w;
+    float ux, uy, uz, h;
+    float vx, vy, vz, pitch;
+    float nx, ny, nz;
+    int32_t material;
+    int32_t gx, gy, plane, prim;
+};
+
+struct DevRectD {            // FP64 copy for the refinement replay, 96 B
+    double ox, oy, oz, ux, uy, uz, vx, vy, vz, nx, ny, nz;
+};
+
+struct alignas(16) DevTri {  // 48 B: v0 | v1 | v2 | prim, material
+    float v0x, v0y, v0z, v1x;
+    float v1y, v1z, v2x, v2y;
+    float v2z;
+    int32_t prim, material, pad;
+};
+
+struct alignas(16) DevNode { // 64 B: boxes of both children + child refs
+    float lo0x, lo0y, lo0z, hi0x;
+    float hi0y, hi0z, lo1x, lo1y;
+    float lo1z, hi1x, hi1y, hi1z;
+    int32_t child0, child1, pad0, pad1;  // >= 0 node, < 0 ~(first << 3 | (count - 1))
+};
+
+struct alignas(16) TrackRec {  // 64 B, written by the yield kernel
+    float x, y, z, len;
+    float tx, ty, tz, tan_theta;  // unit direction (FP64-normalised) and tan
+    float rx, ry, rz;             // raw input direction
+    uint32_t event;
+    uint32_t id;
+    uint32_t count;
+    uint32_t pad0, pad1;
+};
+
+struct SceneView {
+    const DevSphereGroup *groups;
+    const DevTile *tiles;
+    const DevRect *rects;
+    const DevRectD *rects_d;
+    const DevTable *tables;
+    const DevMaterial *materials;
+    const DevNode *nodes;
+    const DevTri *tris;
+    const float *tri_normals;   // 9 floats per triangle, leaf order, or null
+    int32_t n_groups, n_tiles, n_rects, n_tables, n_materials, n_nodes;
+    int64_t n_tris;
+    int32_t tri_prim_base;
+    int32_t n_planes;
+    int64_t pixels_per_event;
+    int64_t plane_offset[RICH_MAX_PLANES];
+    int32_t plane_nx[RICH_MAX_PLANES];
+};
+
+struct TracksView {          // device SoA of rich_tracks
+    int64_t n;
+    const float *x, *y, *z, *dx, *dy, *dz, *p, *mass, *length;
+    const uint32_t *event, *id, *n_fixed;
+};
+
+struct EmitView {            // result of rich_emit used by the trace
+    const TrackRec *tracks;
+    const double2 *cos_sin;   // FP64 cos/sin of the Cherenkov angle
+    const uint64_t *offsets;  // n_tracks + 1
+    const unsigned long long *total;
+    int64_t n_tracks;
+    uint32_t key0, key1;
+    float inv1, span;         // FP32 1/lambda_min and 1/lambda_min - 1/lambda_max
+};
+
+struct ExtView {             // caller photons
+    uint64_t n;
+    const float *x, *y, *z, *dx, *dy, *dz, *lambda;
+    const uint32_t *event, *track, *photon;
+};
+
+struct Counters {            // device, cleared before each trace
+    unsigned long long work;
+    unsigned long long hits;
+    unsigned long long fate[8];
+    unsigned int status;
+    unsigned int pad;
+};
+
+struct TraceParams {
+    int32_t precision, max_bounces, max_steps;
+    float t_min;
+    int32_t refill_min, chunk;
+    rich_hit *hits;
+    uint64_t hit_capacity;
+    uint32_t *pixel_counts;
+    double *event_sums;
+    uint32_t n_hist_events;
+    uint8_t *fate;
+};
+
+struct LaunchShape {
+    int blocks, threads;
+    size_t smem;
+};
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_yield(const TracksView &t, double n_minus_1,
+                         double lam_min, double lam_max, uint32_t key0,
+                         uint32_t key1, TrackRec *rec, double2 *cs,
+                         uint32_t *counts, unsigned long long *block_sums,
+                         cudaStream_t s);
+cudaError_t launch_offsets(const uint32_t *counts,
+                           const unsigned long long *block_sums,
+                           int64_t n_tracks, uint64_t *offsets,
+                           unsigned long long *total, cudaStream_t s);
+cudaError_t launch_materialize(const SceneView &sc, const EmitView &em,
+                               uint64_t n, const rich_photons &out,
+                               cudaStream_t s);
+cudaError_t launch_trace(const SceneView &sc, const EmitView *em,
+                         const ExtView *ext, const TraceParams &p,
+                         Counters *counters, const LaunchShape &shape,
+                         cudaStream_t s);
+cudaError_t launch_philox(const uint32_t *ctr, uint64_t n, uint64_t seed, uint32_t *out,
+                          cudaStream_t s);
+size_t trace_smem_bytes(const SceneView &sc);
+int trace_blocks_per_sm(bool ext, bool refine, int threads, size_t smem);
+int yield_block_threads();
+
+}  // namespace rich

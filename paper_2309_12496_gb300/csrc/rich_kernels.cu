@@ -1,0 +1,1042 @@
+// rich_kernels.cu -- sm_103a kernels of the Cherenkov photon propagator.
+//
+//   k_yield        one thread per track, FP64: beta, Cherenkov angle
+//                  (cos theta = 1/(n beta), Sec. 3), Frank-Tamm mean and the
+//                  keyed Poisson photon count; block sums of the counts.
+//   k_offsets      exclusive scan of the counts into photon offsets
+//                  (deterministic two-pass scan: block prefix from the block
+//                  sums, then an in-block warp-shuffle scan).
+//   k_materialize  optional: photons written out as a structure of arrays
+//                  (the "vector of positions and momenta" of Sec. 4.2).
+//   k_trace        persistent propagation kernel: warps take chunks of
+//                  photons from an atomic queue, generate them in registers
+//                  (fused emission), trace them bounce by bounce and refill
+//                  idle lanes with new photons (warp-level compaction by
+//                  ballot/popc), apply reflectivity and quantum-efficiency
+//                  accept/reject in flight (Sec. 4.3 and Sec. 6), append
+//                  hits with warp-aggregated atomics and bin them.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "rich_device.cuh"
+
+namespace rich {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kYieldThreads = 256;
+constexpr double kAlpha = 1.0 / 137.035999;
+constexpr double kPi = 3.14159265358979323846;
+
+int yield_block_threads() { return kYieldThreads; }
+
+__device__ __forceinline__ void set_status(Counters *c, unsigned code) {
+    atomicCAS(&c->status, 0u, code);
+}
+
+// ================================================================ yield
+// Keyed stream of uniforms for the per-track Poisson draw: words x, y, z, w
+// of blocks 0, 1, 2, ... with counter (block, 0xFFFFFFFF, track id, event).
+struct TrackStream {
+    uint32_t event, id, k0, k1, block, word;
+    u4 w;
+    __device__ double next() {
+        if (word == 4) {
+            w = philox10(block, 0xFFFFFFFFu, id, event, k0, k1);
+            ++block;
+            word = 0;
+        }
+        uint32_t v = word == 0 ? w.x : (word == 1 ? w.y : (word == 2 ? w.z : w.w));
+        ++word;
+        return u24d(v);
+    }
+};
+
+// Poisson(mu): CDF inversion (smallest k with u < F(k)) below mean 10; the
+// PTRS transformed rejection sampler (Hoermann 1993) above, at most 64
+// trials, then round(mu).
+__device__ int64_t poisson_draw(double mu, TrackStream &s) {
+    if (!(mu > 0.0)) return 0;
+    if (mu < 10.0) {
+        double u = s.next();
+        double pk = exp(-mu), F = pk;
+        int64_t k = 0;
+        while (F <= u && k < 1000) {
+            k += 1;
+            pk *= mu / (double)k;
+            F += pk;
+        }
+        return k;
+    }
+    double smu = sqrt(mu), lmu = log(mu);
+    double b = 0.931 + 2.53 * smu;
+    double a = -0.059 + 0.02483 * b;
+    double inv_alpha = 1.1239 + 1.1328 / (b - 3.4);
+    double v_r = 0.9277 - 3.6224 / (b - 2.0);
+    for (int trial = 0; trial < 64; ++trial) {
+        double U = s.next() - 0.5;
+        double V = s.next();
+        double us = 0.5 - fabs(U);
+        if (!(us > 0.0)) continue;
+        double kd = floor((2.0 * a / us + b) * U + mu + 0.43);
+        if (!(kd >= 0.0)) continue;
+        if (us >= 0.07 && V <= v_r) return (int64_t)kd;
+        if (us < 0.013 && V > us) continue;
+        double lhs = log(V) + log(inv_alpha) - log(a / (us * us) + b);
+        double rhs = -mu + kd * lmu - lgamma(kd + 1.0);
+        if (lhs <= rhs) return (int64_t)kd;
+    }
+    return (int64_t)floor(mu + 0.5);
+}
+
+__global__ void __launch_bounds__(kYieldThreads)
+k_yield(TracksView t, double n_minus_1, double inv_band_mm, uint32_t key0,
+        uint32_t key1, TrackRec *rec, double2 *cs, uint32_t *counts,
+        unsigned long long *block_sums) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t count = 0;
+    if (i < t.n) {
+        const double p = t.p[i], m = t.mass[i], len = t.length[i];
+        // 1 - beta = m^2 / (E (E + p)) keeps n*beta - 1 accurate near 1
+        double E = sqrt(p * p + m * m);
+        double one_minus_beta = (m == 0.0) ? 0.0 : (m * m) / (E * (E + p));
+        double beta = 1.0 - one_minus_beta;
+        double nb_minus_1 = n_minus_1 * beta - one_minus_beta;
+        double cos_t = 1.0, sin_t = 0.0, tan_t = 0.0, mu = 0.0;
+        if (nb_minus_1 > 0.0) {
+            double nb = 1.0 + nb_minus_1;
+            double tan2 = nb_minus_1 * (nb + 1.0);      // (n beta)^2 - 1
+            tan_t = sqrt(tan2);
+            cos_t = 1.0 / nb;
+            sin_t = tan_t * cos_t;
+            mu = len * 2.0 * kPi * kAlpha * (sin_t * sin_t) * inv_band_mm;
+        }
+        uint32_t event = t.event[i];
+        uint32_t id = t.id ? t.id[i] : (uint32_t)i;
+        if (t.n_fixed) {
+            count = t.n_fixed[i];
+        } else {
+            TrackStream s{event, id, key0, key1, 0u, 4u, {0u, 0u, 0u, 0u}};
+            int64_t k = poisson_draw(mu, s);
+            count = (uint32_t)(k > 0xFFFFFFF0ll ? 0xFFFFFFF0ll : k);
+        }
+        double dx = t.dx[i], dy = t.dy[i], dz = t.dz[i];
+        double inv = 1.0 / sqrt(dx * dx + dy * dy + dz * dz);
+        TrackRec r;
+        r.x = t.x[i];
+        r.y = t.y[i];
+        r.z = t.z[i];
+        r.len = (float)len;
+        r.tx = (float)(dx * inv);
+        r.ty = (float)(dy * inv);
+        r.tz = (float)(dz * inv);
+        r.tan_theta = (float)tan_t;
+        r.rx = t.dx[i];
+        r.ry = t.dy[i];
+        r.rz = t.dz[i];
+        r.event = event;
+        r.id = id;
+        r.count = count;
+        r.pad0 = r.pad1 = 0;
+        rec[i] = r;
+        cs[i] = make_double2(cos_t, sin_t);
+        counts[i] = count;
+    }
+    // block sum of the counts
+    unsigned long long v = count;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    __shared__ unsigned long long warp_sum[kYieldThreads / 32];
+    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long s = 0;
+        for (int w = 0; w < kYieldThreads / 32; ++w) s += warp_sum[w];
+        block_sums[blockIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(kYieldThreads)
+k_offsets(const uint32_t *counts, const unsigned long long *block_sums,
+          int64_t n, uint64_t *offsets, unsigned long long *total) {
+    __shared__ unsigned long long red[kYieldThreads / 32];
+    __shared__ unsigned long long base;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // prefix of the earlier blocks
+    unsigned long long acc = 0;
+    for (unsigned b = threadIdx.x; b < blockIdx.x; b += blockDim.x) acc += block_sums[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o);
+    if (lane == 0) red[wid] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long s = 0;
+        for (int w = 0; w < kYieldThreads / 32; ++w) s += red[w];
+        base = s;
+    }
+    __syncthreads();
+    // in-block exclusive scan
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long c = i < n ? counts[i] : 0ull;
+    unsigned long long inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += y;
+    }
+    __shared__ unsigned long long wsum[kYieldThreads / 32];
+    if (lane == 31) wsum[wid] = inc;
+    __syncthreads();
+    unsigned long long wpre = 0;
+    for (int w = 0; w < wid; ++w) wpre += wsum[w];
+    unsigned long long excl = base + wpre + inc - c;
+    if (i < n) offsets[i] = excl;
+    if (i == n - 1) {
+        offsets[n] = excl + c;
+        *total = excl + c;
+    }
+}
+
+// ============================================================== emission
+struct Photon {
+    f3 o, d;
+    float lam;
+    uint32_t event, id, j;
+    uint32_t track;        // track index (fused) or external photon index
+    uint64_t g;            // global photon index
+    uint32_t w_qe;
+    uint32_t wr0, wr1, wr2, wr3;
+    uint32_t w_s, w_phi;   // raw draws of the emission (refinement replay)
+    int skip, n_refl, steps;
+};
+
+// Fused emission of photon j of track tr (Sec. 3 angle, Sec. 4.2 photons as
+// independent rays): origin uniform on the segment, azimuth uniform,
+// wavelength from the Frank-Tamm spectrum. The direction is built as
+// t + tan(theta) (cos phi e1 + sin phi e2), normalised, so the small
+// Cherenkov angle is carried by tan(theta) and not by a cosine near 1.
+__device__ __forceinline__ void emit_photon(const TrackRec &tr, uint32_t j,
+                                            const EmitView &em, Photon &ph) {
+    u4 w0 = philox10(0u, j, tr.id, tr.event, em.key0, em.key1);
+    u4 w1 = philox10(1u, j, tr.id, tr.event, em.key0, em.key1);
+    f3 t = mk3(tr.tx, tr.ty, tr.tz);
+    float s = u24f(w0.x) * tr.len;
+    ph.o = fma3(t, s, mk3(tr.x, tr.y, tr.z));
+    float sp, cp;
+    sincospif(2.0f * u24f(w0.y), &sp, &cp);
+    f3 e1, e2;
+    basis_f(t, e1, e2);
+    f3 r = fma3(e1, cp, e2 * sp);
+    ph.d = normalize3(fma3(r, tr.tan_theta, t));
+    ph.lam = emit_lambda(u24f(w0.z), em.inv1, em.span);
+    ph.w_qe = w0.w;
+    ph.wr0 = w1.x;
+    ph.wr1 = w1.y;
+    ph.wr2 = w1.z;
+    ph.wr3 = w1.w;
+    ph.w_s = w0.x;
+    ph.w_phi = w0.y;
+    ph.event = tr.event;
+    ph.id = tr.id;
+    ph.j = j;
+}
+
+__global__ void k_materialize(EmitView em, uint64_t n, rich_photons out) {
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
+         g += (uint64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = em.n_tracks - 1;
+        while (lo < hi) {
+            int64_t mid = (lo + hi + 1) >> 1;
+            if (em.offsets[mid] <= g) lo = mid; else hi = mid - 1;
+        }
+        TrackRec tr = em.tracks[lo];
+        Photon ph;
+        emit_photon(tr, (uint32_t)(g - em.offsets[lo]), em, ph);
+        out.x[g] = ph.o.x;
+        out.y[g] = ph.o.y;
+        out.z[g] = ph.o.z;
+        out.dx[g] = ph.d.x;
+        out.dy[g] = ph.d.y;
+        out.dz[g] = ph.d.z;
+        out.lambda[g] = ph.lam;
+        out.event[g] = ph.event;
+        out.track[g] = ph.id;
+        out.photon[g] = ph.j;
+    }
+}
+
+// ============================================================ intersection
+struct Best {
+    float t;
+    int prim;     // global primitive id
+    int kind;     // 0 tile, 1 rect, 2 triangle
+    int idx;      // index into tiles / rects / tris
+    float b0, b1, b2;
+};
+
+struct SmemScene {
+    const DevSphereGroup *groups;
+    const DevTile *tiles;
+    const DevRect *rects;
+    const DevTable *tables;
+    const DevMaterial *materials;
+    int n_groups, n_tiles, n_rects;
+};
+
+// Tiles: per distinct sphere, the FP64 quadratic |w + t d|^2 = R^2 with
+// w = o - C (precision policy: FP64 only for the large-radius sphere
+// discriminant), roots by the cancellation-free pair (q, c/q); the
+// aperture of each tile is then tested in FP32 at the point relative to
+// the centre. The nearer root on any tile hides the farther one.
+__device__ __forceinline__ void nearest_tiles(const SmemScene &S, f3 o, f3 d,
+                                              int skip, float t_min, Best &b) {
+    const double dx = d.x, dy = d.y, dz = d.z;
+    for (int gi = 0; gi < S.n_groups; ++gi) {
+        const DevSphereGroup &G = S.groups[gi];
+        const double wx = (double)o.x - G.cx, wy = (double)o.y - G.cy,
+                     wz = (double)o.z - G.cz;
+        const double bq = fma(wx, dx, fma(wy, dy, wz * dz));
+        const double c = fma(wx, wx, fma(wy, wy, wz * wz)) - G.r2;
+        const double disc = fma(bq, bq, -c);
+        if (disc < 0.0) continue;
+        const double sq = sqrt(disc);
+        const double q = bq > 0.0 ? -(bq + sq) : (sq - bq);
+        double r1 = q, r2 = (q != 0.0) ? c / q : 0.0;
+        const double t_lo = fmin(r1, r2), t_hi = fmax(r1, r2);
+#pragma unroll
+        for (int ri = 0; ri < 2; ++ri) {
+            const double tr = ri == 0 ? t_lo : t_hi;
+            if (!(tr > (double)t_min) || !(tr < (double)b.t)) continue;
+            const f3 pc = mk3((float)fma(tr, dx, wx), (float)fma(tr, dy, wy),
+                              (float)fma(tr, dz, wz));
+            bool hit = false;
+            for (int k = G.first; k < G.first + G.count; ++k) {
+                const DevTile &T = S.tiles[k];
+                if (T.prim == skip) continue;
+                const float ca = (pc.x * T.ax + pc.y * T.ay + pc.z * T.az) * T.inv_radius;
+                if (!(ca >= T.cos_min)) continue;
+                const float x = pc.x * T.e1x + pc.y * T.e1y + pc.z * T.e1z;
+                const float y = pc.x * T.e2x + pc.y * T.e2y + pc.z * T.e2z;
+                bool in = true;
+                for (int e = 0; e < T.n_edges; ++e)
+                    in = in && (T.edges[e][0] * x + T.edges[e][1] * y <= T.edges[e][2]);
+                if (!in) continue;
+                b.t = (float)tr;
+                b.prim = T.prim;
+                b.kind = 0;
+                b.idx = k;
+                hit = true;
+                break;
+            }
+            if (hit) break;
+        }
+    }
+}
+
+__device__ __forceinline__ void nearest_rects(const SmemScene &S, f3 o, f3 d,
+                                              int skip, float t_min, Best &b) {
+    for (int k = 0; k < S.n_rects; ++k) {
+        const DevRect &R = S.rects[k];
+        if (R.prim == skip) continue;
+        const f3 n = mk3(R.nx, R.ny, R.nz);
+        const float den = dot3(d, n);
+        if (den == 0.0f) continue;
+        const f3 oo = mk3(R.ox, R.oy, R.oz) - o;
+        const float t = __fdiv_rn(dot3(oo, n), den);
+        if (!(t > t_min) || !(t < b.t)) continue;
+        const f3 q = fma3(d, t, mk3(-oo.x, -oo.y, -oo.z));
+        const float u = dot3(q, mk3(R.ux, R.uy, R.uz));
+        const float v = dot3(q, mk3(R.vx, R.vy, R.vz));
+        if (!(u >= 0.0f && u < R.w && v >= 0.0f && v < R.h)) continue;
+        b.t = t;
+        b.prim = R.prim;
+        b.kind = 1;
+        b.idx = k;
+    }
+}
+
+// Watertight ray/triangle test (Woop, Benthin, Wald, JCGT 2(1) 2013):
+// translate to the ray origin, shear so the ray is +z, evaluate the three
+// 2-D edge functions (products kept unfused so shared edges get exactly
+// opposite values; exact FP64 re-evaluation when one is zero), accept both
+// windings, distance from the sheared z.
+struct Ray {
+    f3 o, d, inv;
+    float sx, sy, sz;
+    int kx, ky, kz;
+};
+
+__device__ __forceinline__ float pick(float x, float y, float z, int k) {
+    return k == 0 ? x : (k == 1 ? y : z);
+}
+
+__device__ __forceinline__ Ray make_ray(f3 o, f3 d) {
+    Ray r;
+    r.o = o;
+    r.d = d;
+    const float eps = 1e-30f;
+    r.inv = mk3(1.0f / (fabsf(d.x) > eps ? d.x : copysignf(eps, d.x)),
+                1.0f / (fabsf(d.y) > eps ? d.y : copysignf(eps, d.y)),
+                1.0f / (fabsf(d.z) > eps ? d.z : copysignf(eps, d.z)));
+    const float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+    int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
+    int kx = kz == 2 ? 0 : kz + 1;
+    int ky = kx == 2 ? 0 : kx + 1;
+    const float dz = pick(d.x, d.y, d.z, kz);
+    if (dz < 0.0f) {
+        int tmp = kx;
+        kx = ky;
+        ky = tmp;
+    }
+    r.kx = kx;
+    r.ky = ky;
+    r.kz = kz;
+    r.sx = pick(d.x, d.y, d.z, kx) / dz;
+    r.sy = pick(d.x, d.y, d.z, ky) / dz;
+    r.sz = 1.0f / dz;
+    return r;
+}
+
+__device__ __forceinline__ bool watertight(const Ray &r, const DevTri &T,
+                                           float t_min, float t_max, float &t,
+                                           float &b0, float &b1, float &b2) {
+    const float Ax0 = T.v0x - r.o.x, Ay0 = T.v0y - r.o.y, Az0 = T.v0z - r.o.z;
+    const float Bx0 = T.v1x - r.o.x, By0 = T.v1y - r.o.y, Bz0 = T.v1z - r.o.z;
+    const float Cx0 = T.v2x - r.o.x, Cy0 = T.v2y - r.o.y, Cz0 = T.v2z - r.o.z;
+    const float Akz = pick(Ax0, Ay0, Az0, r.kz), Bkz = pick(Bx0, By0, Bz0, r.kz),
+                Ckz = pick(Cx0, Cy0, Cz0, r.kz);
+    const float Ax = fmaf(-r.sx, Akz, pick(Ax0, Ay0, Az0, r.kx));
+    const float Ay = fmaf(-r.sy, Akz, pick(Ax0, Ay0, Az0, r.ky));
+    const float Bx = fmaf(-r.sx, Bkz, pick(Bx0, By0, Bz0, r.kx));
+    const float By = fmaf(-r.sy, Bkz, pick(Bx0, By0, Bz0, r.ky));
+    const float Cx = fmaf(-r.sx, Ckz, pick(Cx0, Cy0, Cz0, r.kx));
+    const float Cy = fmaf(-r.sy, Ckz, pick(Cx0, Cy0, Cz0, r.ky));
+    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    if (U == 0.0f || V == 0.0f || W == 0.0f) {
+        U = (float)((double)Cx * By - (double)Cy * Bx);
+        V = (float)((double)Ax * Cy - (double)Ay * Cx);
+        W = (float)((double)Bx * Ay - (double)By * Ax);
+    }
+    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f))
+        return false;
+    const float det = U + V + W;
+    if (det == 0.0f) return false;
+    const float T_ = fmaf(U, r.sz * Akz, fmaf(V, r.sz * Bkz, W * (r.sz * Ckz)));
+    const float rcp = 1.0f / det;
+    t = T_ * rcp;
+    if (!(t > t_min && t <= t_max)) return false;
+    b0 = U * rcp;
+    b1 = V * rcp;
+    b2 = W * rcp;
+    return true;
+}
+
+__device__ __forceinline__ DevTri load_tri(const DevTri *p) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+    float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+    DevTri t;
+    t.v0x = a.x; t.v0y = a.y; t.v0z = a.z; t.v1x = a.w;
+    t.v1y = b.x; t.v1z = b.y; t.v2x = b.z; t.v2y = b.w;
+    t.v2z = c.x;
+    t.prim = __float_as_int(c.y);
+    t.material = __float_as_int(c.z);
+    t.pad = 0;
+    return t;
+}
+
+__device__ __forceinline__ bool slab(const Ray &r, float lx, float ly, float lz,
+                                     float hx, float hy, float hz, float tmax,
+                                     float &tnear) {
+    const float ox = r.o.x * r.inv.x, oy = r.o.y * r.inv.y, oz = r.o.z * r.inv.z;
+    const float tx0 = fmaf(lx, r.inv.x, -ox), tx1 = fmaf(hx, r.inv.x, -ox);
+    const float ty0 = fmaf(ly, r.inv.y, -oy), ty1 = fmaf(hy, r.inv.y, -oy);
+    const float tz0 = fmaf(lz, r.inv.z, -oz), tz1 = fmaf(hz, r.inv.z, -oz);
+    const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)),
+                           fmaxf(fminf(tz0, tz1), 0.0f));
+    const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)),
+                           fminf(fmaxf(tz0, tz1), tmax));
+    tnear = tn;
+    // 1 + 2^-20 widening keeps boxes conservative under FP32 rounding
+    return tn <= tf * 1.00000095f;
+}
+
+__device__ __forceinline__ void leaf_tris(const SceneView &sc, const Ray &r,
+                                          int code, int skip, float t_min,
+                                          Best &b) {
+    const int first = code >> 3, count = (code & 7) + 1;
+    for (int k = first; k < first + count; ++k) {
+        const DevTri T = load_tri(sc.tris + k);
+        if (T.prim == skip) continue;
+        float t, b0, b1, b2;
+        if (!watertight(r, T, t_min, b.t, t, b0, b1, b2)) continue;
+        if (t == b.t && T.prim > b.prim) continue;
+        b.t = t;
+        b.prim = T.prim;
+        b.kind = 2;
+        b.idx = k;
+        b.b0 = b0;
+        b.b1 = b1;
+        b.b2 = b2;
+    }
+}
+
+__device__ void nearest_bvh(const SceneView &sc, f3 o, f3 d, int skip,
+                            float t_min, Best &b, Counters *ctr) {
+    const Ray r = make_ray(o, d);
+    int stack_node[RICH_BVH_STACK];
+    float stack_t[RICH_BVH_STACK];
+    int sp = 0;
+    int node = 0;
+    while (true) {
+        const float4 *q = reinterpret_cast<const float4 *>(sc.nodes + node);
+        const float4 a = __ldg(q), bb = __ldg(q + 1), c = __ldg(q + 2);
+        const int4 ch = __ldg(reinterpret_cast<const int4 *>(q + 3));
+        float tn0, tn1;
+        bool h0 = slab(r, a.x, a.y, a.z, a.w, bb.x, bb.y, b.t, tn0);
+        bool h1 = slab(r, bb.z, bb.w, c.x, c.y, c.z, c.w, b.t, tn1);
+        if (h0 && ch.x < 0) {
+            leaf_tris(sc, r, ~ch.x, skip, t_min, b);
+            h0 = false;
+        }
+        if (h1 && ch.y < 0) {
+            leaf_tris(sc, r, ~ch.y, skip, t_min, b);
+            h1 = false;
+        }
+        if (h0 && h1) {
+            const bool first0 = tn0 <= tn1;
+            if (sp < RICH_BVH_STACK) {
+                stack_node[sp] = first0 ? ch.y : ch.x;
+                stack_t[sp] = first0 ? tn1 : tn0;
+                ++sp;
+            } else {
+                set_status(ctr, RICH_ERR_GEOMETRY);
+            }
+            node = first0 ? ch.x : ch.y;
+            continue;
+        }
+        if (h0) { node = ch.x; continue; }
+        if (h1) { node = ch.y; continue; }
+        bool found = false;
+        while (sp > 0) {
+            --sp;
+            if (stack_t[sp] <= b.t) {
+                node = stack_node[sp];
+                found = true;
+                break;
+            }
+        }
+        if (!found) break;
+    }
+}
+
+// ============================================================ FP64 replay
+// Refinement of a detected photon: the recorded sequence of reflecting
+// primitives is replayed in FP64 (emission, each reflection on the same
+// primitive's surface extended past its edges, the final plane), giving
+// the hit position and pixel in FP64.
+__device__ void replay64(const SceneView &sc, const SmemScene &S,
+                         const Photon &ph, const TrackRec *tr,
+                         const double2 *cs, const ExtView *ext,
+                         const int *path, int n_path, int det_rect,
+                         double &u, double &v) {
+    d3 o, d;
+    if (tr) {
+        d3 t = normalized(mkd(tr->rx, tr->ry, tr->rz));
+        double s = u24d(ph.w_s) * (double)tr->len;
+        o = mkd(fma(t.x, s, (double)tr->x), fma(t.y, s, (double)tr->y),
+                fma(t.z, s, (double)tr->z));
+        double sp, cp;
+        sincospi(2.0 * u24d(ph.w_phi), &sp, &cp);
+        d3 e1, e2;
+        basis_d(t, e1, e2);
+        const double ct = cs->x, st = cs->y;
+        d = mkd(ct * t.x + st * (cp * e1.x + sp * e2.x),
+                ct * t.y + st * (cp * e1.y + sp * e2.y),
+                ct * t.z + st * (cp * e1.z + sp * e2.z));
+        d = normalized(d);
+    } else {
+        o = mkd(ext->x[ph.track], ext->y[ph.track], ext->z[ph.track]);
+        d = normalized(mkd(ext->dx[ph.track], ext->dy[ph.track], ext->dz[ph.track]));
+    }
+    for (int k = 0; k < n_path; ++k) {
+        const int prim = path[k];
+        d3 n;
+        if (prim < sc.n_tiles) {
+            int ti = 0;
+            for (int q = 0; q < S.n_tiles; ++q)
+                if (S.tiles[q].prim == prim) ti = q;
+            const DevSphereGroup &G = S.groups[S.tiles[ti].group];
+            const d3 w = o - mkd(G.cx, G.cy, G.cz);
+            const double bq = dotd(w, d);
+            const double c = dotd(w, w) - G.r2;
+            const double sq = sqrt(fmax(0.0, bq * bq - c));
+            // concave (front) side: the exit root -b + sqrt(disc)
+            const double t = bq <= 0.0 ? (sq - bq) : c / (-bq - sq);
+            o = o + d * t;
+            const d3 pc = o - mkd(G.cx, G.cy, G.cz);
+            n = pc * (-1.0 / sqrt(G.r2));
+        } else if (prim < sc.tri_prim_base) {
+            const DevRectD &R = sc.rects_d[prim - sc.n_tiles];
+            n = mkd(R.nx, R.ny, R.nz);
+            const double t = dotd(mkd(R.ox, R.oy, R.oz) - o, n) / dotd(d, n);
+            o = o + d * t;
+        } else {
+            const int k_tri = prim - sc.tri_prim_base;   // leaf-order index
+            const DevTri T = load_tri(sc.tris + k_tri);
+            const d3 v0 = mkd(T.v0x, T.v0y, T.v0z), v1 = mkd(T.v1x, T.v1y, T.v1z),
+                     v2 = mkd(T.v2x, T.v2y, T.v2z);
+            const d3 e1 = v1 - v0, e2 = v2 - v0;
+            const d3 ng = crossd(e1, e2);
+            const double t = dotd(v0 - o, ng) / dotd(d, ng);
+            o = o + d * t;
+            const DevMaterial &M = S.materials[T.material];
+            if ((M.flags & RICH_MAT_SMOOTH) && sc.tri_normals) {
+                // barycentrics of the hit in the triangle's plane
+                const d3 q = o - v0;
+                const double d00 = dotd(e1, e1), d01 = dotd(e1, e2), d11 = dotd(e2, e2);
+                const double d20 = dotd(q, e1), d21 = dotd(q, e2);
+                const double den = d00 * d11 - d01 * d01;
+                const double b1 = (d11 * d20 - d01 * d21) / den;
+                const double b2 = (d00 * d21 - d01 * d20) / den;
+                const double b0 = 1.0 - b1 - b2;
+                const float *N = sc.tri_normals + 9 * (int64_t)k_tri;
+                n = normalized(mkd(b0 * N[0] + b1 * N[3] + b2 * N[6],
+                                   b0 * N[1] + b1 * N[4] + b2 * N[7],
+                                   b0 * N[2] + b1 * N[5] + b2 * N[8]));
+            } else {
+                n = normalized(ng);
+            }
+        }
+        d = normalized(reflect_d(d, n));
+    }
+    const DevRectD &R = sc.rects_d[det_rect];
+    const d3 nrm = mkd(R.nx, R.ny, R.nz);
+    const d3 O = mkd(R.ox, R.oy, R.oz);
+    const double t = dotd(O - o, nrm) / dotd(d, nrm);
+    const d3 q = (o + d * t) - O;
+    u = dotd(q, mkd(R.ux, R.uy, R.uz));
+    v = dotd(q, mkd(R.vx, R.vy, R.vz));
+}
+
+// ================================================================ trace
+struct TraceArgs {
+    SceneView sc;
+    EmitView em;
+    ExtView ext;
+    TraceParams p;
+    Counters *ctr;
+};
+
+__device__ __forceinline__ uint32_t refl_word(const Photon &ph, int k,
+                                              const EmitView &em) {
+    if (k < 4) return k == 0 ? ph.wr0 : (k == 1 ? ph.wr1 : (k == 2 ? ph.wr2 : ph.wr3));
+    u4 w = philox10(2u, ph.j, ph.id, ph.event, em.key0, em.key1);
+    k -= 4;
+    return k == 0 ? w.x : (k == 1 ? w.y : (k == 2 ? w.z : w.w));
+}
+
+template <bool EXT, bool REFINE>
+__global__ void __launch_bounds__(256)
+k_trace(TraceArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const SceneView &sc = A.sc;
+    // ---- stage the small scene tables into shared memory
+    SmemScene S;
+    {
+        size_t off = 0;
+        auto carve = [&](size_t bytes) {
+            unsigned char *p = smem + off;
+            off += (bytes + 15) & ~size_t(15);
+            return p;
+        };
+        auto copy = [&](void *dst, const void *src, size_t bytes) {
+            const uint32_t *s = static_cast<const uint32_t *>(src);
+            uint32_t *d = static_cast<uint32_t *>(dst);
+            for (size_t i = threadIdx.x; i < bytes / 4; i += blockDim.x) d[i] = s[i];
+        };
+        DevSphereGroup *g = reinterpret_cast<DevSphereGroup *>(carve(sizeof(DevSphereGroup) * sc.n_groups));
+        DevTile *t = reinterpret_cast<DevTile *>(carve(sizeof(DevTile) * sc.n_tiles));
+        DevRect *r = reinterpret_cast<DevRect *>(carve(sizeof(DevRect) * sc.n_rects));
+        DevTable *tb = reinterpret_cast<DevTable *>(carve(sizeof(DevTable) * sc.n_tables));
+        DevMaterial *m = reinterpret_cast<DevMaterial *>(carve(sizeof(DevMaterial) * sc.n_materials));
+        copy(g, sc.groups, sizeof(DevSphereGroup) * sc.n_groups);
+        copy(t, sc.tiles, sizeof(DevTile) * sc.n_tiles);
+        copy(r, sc.rects, sizeof(DevRect) * sc.n_rects);
+        copy(tb, sc.tables, sizeof(DevTable) * sc.n_tables);
+        copy(m, sc.materials, sizeof(DevMaterial) * sc.n_materials);
+        S = {g, t, r, tb, m, sc.n_groups, sc.n_tiles, sc.n_rects};
+    }
+    __shared__ unsigned long long s_fate[8];
+    __shared__ unsigned long long s_hits;
+    if (threadIdx.x < 8) s_fate[threadIdx.x] = 0;
+    if (threadIdx.x == 0) s_hits = 0;
+    __syncthreads();
+
+    const TraceParams &P = A.p;
+    const EmitView &em = A.em;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const uint64_t N = EXT ? A.ext.n : (uint64_t)(*em.total);
+    const uint64_t chunk = (uint64_t)P.chunk;
+    const bool has_tri = sc.n_tris > 0;
+
+    Photon ph;
+    bool alive = false;
+    int path[REFINE ? RICH_MAX_BOUNCES : 1];
+    uint64_t pool_next = 0, pool_end = 0;   // warp-uniform
+    int64_t pool_track = 0;                 // warp-uniform
+    bool more = true;                       // warp-uniform
+
+    while (true) {
+        // ---------------------------------------------------- refill
+        unsigned idle = __ballot_sync(kFull, !alive);
+        if (more && (__popc(idle) >= P.refill_min || idle == kFull)) {
+            while (idle != 0u && more) {
+                if (pool_next >= pool_end) {
+                    unsigned long long base = 0;
+                    if (lane == 0) base = atomicAdd(&A.ctr->work, (unsigned long long)chunk);
+                    base = __shfl_sync(kFull, base, 0);
+                    if (base >= N) {
+                        more = false;
+                        break;
+                    }
+                    pool_next = base;
+                    pool_end = base + chunk < N ? base + chunk : N;
+                    if (!EXT) {
+                        // 32-ary search for the track containing pool_next
+                        int64_t lo = 0, hi = em.n_tracks;
+                        while (hi - lo > 32) {
+                            const int64_t step = (hi - lo + 31) / 32;
+                            const int64_t idx = lo + lane * step;
+                            const bool ok = idx < hi && em.offsets[idx] <= pool_next;
+                            const unsigned m = __ballot_sync(kFull, ok);
+                            const int L = 31 - __clz(m);
+                            lo = lo + L * step;
+                            hi = (lo + step < hi) ? lo + step : hi;
+                        }
+                        const int64_t idx = lo + lane;
+                        const bool ok = idx < hi && em.offsets[idx] <= pool_next;
+                        const unsigned m = __ballot_sync(kFull, ok);
+                        pool_track = lo + (31 - __clz(m));
+                    }
+                }
+                const int rank = __popc(idle & lt_mask);
+                const uint64_t avail = pool_end - pool_next;
+                const bool take = ((idle >> lane) & 1u) && (uint64_t)rank < avail;
+                int64_t my_track = pool_track;
+                if (take) {
+                    const uint64_t g = pool_next + (uint64_t)rank;
+                    ph.g = g;
+                    ph.skip = -1;
+                    ph.n_refl = 0;
+                    ph.steps = 0;
+                    if (EXT) {
+                        ph.track = (uint32_t)g;
+                        ph.o = mk3(A.ext.x[g], A.ext.y[g], A.ext.z[g]);
+                        ph.d = mk3(A.ext.dx[g], A.ext.dy[g], A.ext.dz[g]);
+                        ph.lam = A.ext.lambda[g];
+                        ph.event = A.ext.event[g];
+                        ph.id = A.ext.track[g];
+                        ph.j = A.ext.photon[g];
+                        const u4 w0 = philox10(0u, ph.j, ph.id, ph.event, em.key0, em.key1);
+                        const u4 w1 = philox10(1u, ph.j, ph.id, ph.event, em.key0, em.key1);
+                        ph.w_qe = w0.w;
+                        ph.wr0 = w1.x; ph.wr1 = w1.y; ph.wr2 = w1.z; ph.wr3 = w1.w;
+                        ph.w_s = w0.x;
+                        ph.w_phi = w0.y;
+                    } else {
+                        while (my_track + 1 < em.n_tracks && em.offsets[my_track + 1] <= g)
+                            ++my_track;
+                        ph.track = (uint32_t)my_track;
+                        const TrackRec tr = em.tracks[my_track];
+                        emit_photon(tr, (uint32_t)(g - em.offsets[my_track]), em, ph);
+                    }
+                    alive = true;
+                }
+                const unsigned taken = __ballot_sync(kFull, take);
+                if (taken) {
+                    const int last = 31 - __clz(taken);
+                    pool_next += __popc(taken);
+                    if (!EXT) pool_track = __shfl_sync(kFull, my_track, last);
+                }
+                idle &= ~taken;
+                if (taken == 0u && pool_next < pool_end) break;  // defensive
+            }
+        }
+        if (!__any_sync(kFull, alive)) {
+            if (!more) break;
+            continue;
+        }
+
+        // ---------------------------------------------- one bounce step
+        int fate = 0;
+        int det_rect = -1;
+        float hit_u = 0.0f, hit_v = 0.0f;
+        if (alive) {
+            Best b;
+            b.t = 3.0e38f;
+            b.prim = -1;
+            b.kind = -1;
+            b.idx = -1;
+            b.b0 = b.b1 = b.b2 = 0.0f;
+            if (S.n_groups) nearest_tiles(S, ph.o, ph.d, ph.skip, P.t_min, b);
+            nearest_rects(S, ph.o, ph.d, ph.skip, P.t_min, b);
+            if (has_tri) nearest_bvh(sc, ph.o, ph.d, ph.skip, P.t_min, b, A.ctr);
+            if (b.prim < 0) {
+                fate = RICH_FATE_ESCAPED;
+            } else {
+                const f3 p = fma3(ph.d, b.t, ph.o);
+                int mat_id;
+                bool front;
+                f3 n_sh;
+                if (b.kind == 0) {
+                    const DevTile &T = S.tiles[b.idx];
+                    const DevSphereGroup &G = S.groups[T.group];
+                    // FP64 point relative to the centre for the normal
+                    const double tt = (double)b.t;
+                    const double px = fma(tt, (double)ph.d.x, (double)ph.o.x - G.cx);
+                    const double py = fma(tt, (double)ph.d.y, (double)ph.o.y - G.cy);
+                    const double pz = fma(tt, (double)ph.d.z, (double)ph.o.z - G.cz);
+                    const double inv = -1.0 / sqrt(px * px + py * py + pz * pz);
+                    n_sh = mk3((float)(px * inv), (float)(py * inv), (float)(pz * inv));
+                    front = dot3(ph.d, n_sh) < 0.0f;
+                    mat_id = T.material;
+                } else if (b.kind == 1) {
+                    const DevRect &R = S.rects[b.idx];
+                    n_sh = mk3(R.nx, R.ny, R.nz);
+                    front = dot3(ph.d, n_sh) < 0.0f;
+                    mat_id = R.material;
+                } else {
+                    const DevTri T = load_tri(sc.tris + b.idx);
+                    const f3 e1 = mk3(T.v1x - T.v0x, T.v1y - T.v0y, T.v1z - T.v0z);
+                    const f3 e2 = mk3(T.v2x - T.v0x, T.v2y - T.v0y, T.v2z - T.v0z);
+                    const f3 ng = cross3(e1, e2);
+                    front = dot3(ph.d, ng) < 0.0f;
+                    mat_id = T.material;
+                    const DevMaterial &M0 = S.materials[mat_id];
+                    if ((M0.flags & RICH_MAT_SMOOTH) && sc.tri_normals) {
+                        const float *N3 = sc.tri_normals + 9 * (int64_t)b.idx;
+                        const f3 n0 = mk3(__ldg(N3 + 0), __ldg(N3 + 1), __ldg(N3 + 2));
+                        const f3 n1 = mk3(__ldg(N3 + 3), __ldg(N3 + 4), __ldg(N3 + 5));
+                        const f3 n2 = mk3(__ldg(N3 + 6), __ldg(N3 + 7), __ldg(N3 + 8));
+                        n_sh = normalize3(fma3(n0, b.b0, fma3(n1, b.b1, n2 * b.b2)));
+                    } else {
+                        n_sh = normalize3(ng);
+                    }
+                }
+                const DevMaterial &M = S.materials[mat_id];
+                if (M.kind == RICH_MAT_ABSORBER) {
+                    fate = RICH_FATE_ABSORBED;
+                } else if (M.kind == RICH_MAT_MIRROR) {
+                    if (!front) {
+                        fate = RICH_FATE_ABSORBED;
+                    } else if (ph.n_refl >= P.max_bounces) {
+                        fate = RICH_FATE_MAX_BOUNCES;
+                    } else {
+                        const float Pr = table_eval(S.tables[M.table], ph.lam);
+                        const float u = u24f(refl_word(ph, ph.n_refl, em));
+                        if (!(u < Pr)) {
+                            fate = RICH_FATE_MIRROR_ABSORBED;
+                        } else {
+                            ph.d = normalize3(reflect_f(ph.d, n_sh));
+                            if (REFINE) path[ph.n_refl] = b.kind == 2 ? sc.tri_prim_base + b.idx : b.prim;
+                            ph.n_refl += 1;
+                            ph.o = p;
+                            ph.skip = b.prim;
+                        }
+                    }
+                } else {  // detector
+                    if (!front) {
+                        ph.o = p;
+                        ph.skip = b.prim;
+                    } else {
+                        const float Pq = table_eval(S.tables[M.table], ph.lam);
+                        if (!(u24f(ph.w_qe) < Pq)) {
+                            fate = RICH_FATE_QE_REJECTED;
+                        } else {
+                            fate = RICH_FATE_DETECTED;
+                            det_rect = b.idx;
+                            const DevRect &R = S.rects[b.idx];
+                            const f3 q = p - mk3(R.ox, R.oy, R.oz);
+                            hit_u = dot3(q, mk3(R.ux, R.uy, R.uz));
+                            hit_v = dot3(q, mk3(R.vx, R.vy, R.vz));
+                        }
+                    }
+                }
+                if (fate == 0) {
+                    ph.steps += 1;
+                    if (ph.steps >= P.max_steps) fate = RICH_FATE_MAX_STEPS;
+                }
+            }
+        }
+
+        // -------------------------------------------- finished photons
+        const bool det = fate == RICH_FATE_DETECTED;
+        const unsigned dm = __ballot_sync(kFull, det);
+        if (dm) {
+            unsigned long long base = 0;
+            const int leader = __ffs(dm) - 1;
+            if (lane == leader) base = atomicAdd(&A.ctr->hits, (unsigned long long)__popc(dm));
+            base = __shfl_sync(kFull, base, leader);
+            if (det) {
+                const DevRect &R = S.rects[det_rect];
+                const DevMaterial &M = S.materials[R.material];
+                double u = hit_u, v = hit_v;
+                if (REFINE) {
+                    const TrackRec *trp = EXT ? nullptr : &em.tracks[ph.track];
+                    const double2 *csp = EXT ? nullptr : &em.cos_sin[ph.track];
+                    replay64(sc, S, ph, trp, csp, &A.ext, path, ph.n_refl, det_rect, u, v);
+                }
+                const double pitch = (double)R.pitch;
+                int ix = (int)floor(u / pitch), iy = (int)floor(v / pitch);
+                ix = ix < 0 ? 0 : (ix >= R.gx ? R.gx - 1 : ix);
+                iy = iy < 0 ? 0 : (iy >= R.gy ? R.gy - 1 : iy);
+                const uint64_t slot = base + (uint64_t)__popc(dm & lt_mask);
+                if (slot < P.hit_capacity) {
+                    rich_hit h;
+                    h.event = ph.event;
+                    h.track = ph.id;
+                    h.photon = ph.j;
+                    h.plane = (uint8_t)M.plane;
+                    h.n_reflections = (uint8_t)ph.n_refl;
+                    h.reserved = 0;
+                    h.ix = (uint16_t)ix;
+                    h.iy = (uint16_t)iy;
+                    h.lambda = ph.lam;
+                    h.u = u;
+                    h.v = v;
+                    P.hits[slot] = h;
+                }
+                if (ph.event < P.n_hist_events) {
+                    if (P.pixel_counts) {
+                        const int64_t idx = (int64_t)ph.event * sc.pixels_per_event +
+                                            sc.plane_offset[M.plane] +
+                                            (int64_t)iy * sc.plane_nx[M.plane] + ix;
+                        atomicAdd(P.pixel_counts + idx, 1u);
+                    }
+                    if (P.event_sums) {
+                        double *es = P.event_sums + ((int64_t)ph.event * sc.n_planes + M.plane) * 4;
+                        atomicAdd(es + 0, 1.0);
+                        atomicAdd(es + 1, u);
+                        atomicAdd(es + 2, v);
+                        atomicAdd(es + 3, (double)ph.lam);
+                    }
+                }
+            }
+        }
+        if (fate != 0) {
+            if (P.fate) P.fate[ph.g] = (uint8_t)fate;
+            atomicAdd(&s_fate[fate], 1ull);
+            alive = false;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 8 && s_fate[threadIdx.x])
+        atomicAdd(&A.ctr->fate[threadIdx.x], s_fate[threadIdx.x]);
+}
+
+// Philox outputs for caller-given counters (reproduction of draws).
+__global__ void k_philox(const uint32_t *ctr, uint64_t n, uint32_t k0, uint32_t k1,
+                         uint32_t *out) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint4 c = reinterpret_cast<const uint4 *>(ctr)[i];
+        const u4 r = philox10(c.x, c.y, c.z, c.w, k0, k1);
+        reinterpret_cast<uint4 *>(out)[i] = make_uint4(r.x, r.y, r.z, r.w);
+    }
+}
+
+cudaError_t launch_philox(const uint32_t *ctr, uint64_t n, uint64_t seed, uint32_t *out,
+                          cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    uint64_t blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_philox<<<(unsigned)blocks, 256, 0, s>>>(ctr, n, (uint32_t)seed, (uint32_t)(seed >> 32), out);
+    return cudaGetLastError();
+}
+
+// ============================================================== launchers
+cudaError_t launch_yield(const TracksView &t, double n_minus_1,
+                         double lam_min, double lam_max, uint32_t key0,
+                         uint32_t key1, TrackRec *rec, double2 *cs,
+                         uint32_t *counts, unsigned long long *block_sums,
+                         cudaStream_t s) {
+    if (t.n <= 0) return cudaSuccess;
+    const double inv_band_mm = 1.0e6 / lam_min - 1.0e6 / lam_max;
+    const unsigned blocks = (unsigned)((t.n + kYieldThreads - 1) / kYieldThreads);
+    k_yield<<<blocks, kYieldThreads, 0, s>>>(t, n_minus_1, inv_band_mm, key0, key1,
+                                             rec, cs, counts, block_sums);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_offsets(const uint32_t *counts,
+                           const unsigned long long *block_sums,
+                           int64_t n_tracks, uint64_t *offsets,
+                           unsigned long long *total, cudaStream_t s) {
+    if (n_tracks <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((n_tracks + kYieldThreads - 1) / kYieldThreads);
+    k_offsets<<<blocks, kYieldThreads, 0, s>>>(counts, block_sums, n_tracks, offsets, total);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_materialize(const SceneView &, const EmitView &em,
+                               uint64_t n, const rich_photons &out,
+                               cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    uint64_t blocks = (n + 255) / 256;
+    if (blocks > 65535ull * 16) blocks = 65535ull * 16;
+    k_materialize<<<(unsigned)blocks, 256, 0, s>>>(em, n, out);
+    return cudaGetLastError();
+}
+
+size_t trace_smem_bytes(const SceneView &sc) {
+    auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
+    return r16(sizeof(DevSphereGroup) * sc.n_groups) + r16(sizeof(DevTile) * sc.n_tiles) +
+           r16(sizeof(DevRect) * sc.n_rects) + r16(sizeof(DevTable) * sc.n_tables) +
+           r16(sizeof(DevMaterial) * sc.n_materials);
+}
+
+template <bool EXT, bool REFINE>
+static cudaError_t launch_trace_t(const TraceArgs &a, const LaunchShape &shape,
+                                  cudaStream_t s) {
+    auto kern = k_trace<EXT, REFINE>;
+    if (shape.smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(
+            kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shape.smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<shape.blocks, shape.threads, shape.smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+int trace_blocks_per_sm(bool ext, bool refine, int threads, size_t smem) {
+    int n = 0;
+    const void *f = ext ? (refine ? (const void *)k_trace<true, true> : (const void *)k_trace<true, false>)
+                        : (refine ? (const void *)k_trace<false, true> : (const void *)k_trace<false, false>);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
+cudaError_t launch_trace(const SceneView &sc, const EmitView *em,
+                         const ExtView *ext, const TraceParams &p,
+                         Counters *counters, const LaunchShape &shape,
+                         cudaStream_t s) {
+    TraceArgs a;
+    a.sc = sc;
+    a.em = em ? *em : EmitView{};
+    a.ext = ext ? *ext : ExtView{};
+    a.p = p;
+    a.ctr = counters;
+    const bool refine = p.precision == RICH_PREC_REFINE64;
+    if (ext) {
+        return refine ? launch_trace_t<true, true>(a, shape, s)
+                      : launch_trace_t<true, false>(a, shape, s);
+    }
+    return refine ? launch_trace_t<false, true>(a, shape, s)
+                  : launch_trace_t<false, false>(a, shape, s);
+}
+
+}  // namespace rich

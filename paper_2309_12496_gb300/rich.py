@@ -1,0 +1,382 @@
+"""Python binding of the C ABI in include/rich.h (argument marshalling only).
+
+Every step of the photon path runs in the CUDA library ``librich.so``; this
+module only passes pointers and sizes. PyTorch provides device memory and
+streams. Importing the module does not need a GPU; creating a context does,
+and fails loudly when the library is missing (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import workloads as W
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librich.so")
+
+RICH_OK = 0
+STATUS_NAMES = {0: "RICH_OK", 1: "RICH_ERR_ARG", 2: "RICH_ERR_CUDA", 3: "RICH_ERR_OOM",
+                4: "RICH_ERR_OVERFLOW", 5: "RICH_ERR_TIMEOUT", 6: "RICH_ERR_GEOMETRY",
+                7: "RICH_ERR_STATE"}
+PREC_FP32, PREC_REFINE64 = 0, 1
+FATE_NAMES = ["none", "escaped", "mirror_absorbed", "absorbed", "qe_rejected",
+              "detected", "max_bounces", "max_steps"]
+FATE_DETECTED = 5
+
+EXPORTED = ["rich_create", "rich_destroy", "rich_set_stream", "rich_init_geometry",
+            "rich_emit", "rich_trace", "rich_hits", "rich_philox", "rich_last_error",
+            "rich_version"]
+
+# rich_hit, 40 bytes
+HIT_DTYPE = np.dtype([("event", "<u4"), ("track", "<u4"), ("photon", "<u4"),
+                      ("plane", "u1"), ("n_reflections", "u1"), ("reserved", "<u2"),
+                      ("ix", "<u2"), ("iy", "<u2"), ("lambda", "<f4"),
+                      ("u", "<f8"), ("v", "<f8")])
+assert HIT_DTYPE.itemsize == 40
+
+
+class RichError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+# --------------------------------------------------------------- structs
+class GeometryDesc(C.Structure):
+    _fields_ = [("n_tables", C.c_int32), ("n_materials", C.c_int32),
+                ("n_spheres", C.c_int32), ("n_rects", C.c_int32),
+                ("n_triangles", C.c_int64),
+                ("tables", C.c_void_p), ("materials", C.c_void_p),
+                ("spheres", C.c_void_p), ("rects", C.c_void_p),
+                ("tri_vertices", C.c_void_p), ("tri_normals", C.c_void_p),
+                ("tri_material", C.c_void_p)]
+
+
+class TracksDesc(C.Structure):
+    _fields_ = [("n", C.c_int64)] + [
+        (f, C.c_void_p) for f in ("x", "y", "z", "dx", "dy", "dz", "p", "mass",
+                                  "length", "event", "id", "n_fixed")]
+
+
+class EmitParams(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("n_minus_1", C.c_float),
+                ("lambda_min", C.c_float), ("lambda_max", C.c_float),
+                ("reserved", C.c_float)]
+
+
+class PhotonsDesc(C.Structure):
+    _fields_ = [("n", C.c_uint64), ("capacity", C.c_uint64)] + [
+        (f, C.c_void_p) for f in ("x", "y", "z", "dx", "dy", "dz", "lambda_",
+                                  "event", "track", "photon")]
+
+
+class TraceOpts(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("precision", C.c_int32),
+                ("max_bounces", C.c_int32), ("max_steps", C.c_int32),
+                ("t_min", C.c_float), ("block_threads", C.c_int32),
+                ("blocks_per_sm", C.c_int32), ("refill_min", C.c_int32),
+                ("chunk", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Outputs(C.Structure):
+    _fields_ = [("hits", C.c_void_p), ("hit_capacity", C.c_uint64),
+                ("pixel_counts", C.c_void_p), ("event_sums", C.c_void_p),
+                ("n_hist_events", C.c_uint32), ("reserved", C.c_uint32),
+                ("fate", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_photons", C.c_uint64), ("n_hits", C.c_uint64),
+                ("n_fate", C.c_uint64 * 8), ("device_status", C.c_uint32),
+                ("reserved", C.c_uint32)]
+
+
+# ------------------------------------------------------------------ library
+_lib = None
+_lock = threading.Lock()
+
+
+def load():
+    """Load librich.so (built by build.py / __graft_entry__.build())."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with "
+                "`python -c 'import __graft_entry__ as g; g.build()'` "
+                "(there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        L.rich_create.argtypes = [C.POINTER(vp), C.c_int, vp]
+        L.rich_destroy.argtypes = [vp]
+        L.rich_set_stream.argtypes = [vp, vp]
+        L.rich_init_geometry.argtypes = [vp, C.POINTER(GeometryDesc)]
+        L.rich_emit.argtypes = [vp, C.POINTER(TracksDesc), C.POINTER(EmitParams),
+                                C.POINTER(PhotonsDesc), C.POINTER(C.c_uint64)]
+        L.rich_trace.argtypes = [vp, C.POINTER(PhotonsDesc), C.POINTER(TraceOpts),
+                                 C.POINTER(Outputs)]
+        L.rich_hits.argtypes = [vp, C.POINTER(C.c_uint64), C.POINTER(Stats)]
+        L.rich_philox.argtypes = [vp, vp, C.c_uint64, C.c_uint64, vp]
+        L.rich_last_error.argtypes = [vp]
+        L.rich_last_error.restype = C.c_char_p
+        L.rich_version.restype = C.c_char_p
+        for f in ("rich_create", "rich_destroy", "rich_set_stream", "rich_init_geometry",
+                  "rich_emit", "rich_trace", "rich_hits", "rich_philox"):
+            getattr(L, f).restype = C.c_int
+        _lib = L
+        return L
+
+
+def _check(ctx, st):
+    if st != RICH_OK:
+        msg = load().rich_last_error(ctx).decode(errors="replace")
+        raise RichError(st, msg)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def current_stream_handle():
+    torch = _torch()
+    return torch.cuda.current_stream().cuda_stream
+
+
+# ----------------------------------------------------------- device inputs
+class DeviceTracks:
+    """A Tracks set uploaded to device memory (torch tensors)."""
+
+    def __init__(self, tracks: W.Tracks, device="cuda"):
+        torch = _torch()
+        self.n = tracks.n
+        self.t = {}
+        for f in W.Tracks.FIELDS:
+            self.t[f] = torch.from_numpy(np.ascontiguousarray(getattr(tracks, f), np.float32)).to(device)
+        self.t["event"] = torch.from_numpy(
+            np.ascontiguousarray(tracks.event, np.uint32).view(np.int32)).to(device)
+        self.t["id"] = torch.from_numpy(
+            np.ascontiguousarray(tracks.id, np.uint32).view(np.int32)).to(device)
+        self.t["n_fixed"] = (None if tracks.n_fixed is None else torch.from_numpy(
+            np.ascontiguousarray(tracks.n_fixed, np.uint32).view(np.int32)).to(device))
+
+    def desc(self) -> TracksDesc:
+        return TracksDesc(n=self.n, **{k: (None if v is None else v.data_ptr())
+                                       for k, v in self.t.items()})
+
+
+class PhotonBuffers:
+    """Device structure-of-arrays photons (rich_photons)."""
+
+    FIELDS = ("x", "y", "z", "dx", "dy", "dz", "lambda_")
+    KEYS = ("event", "track", "photon")
+
+    def __init__(self, capacity, device="cuda"):
+        torch = _torch()
+        self.capacity = int(capacity)
+        self.n = 0
+        self.t = {f: torch.empty(max(1, self.capacity), dtype=torch.float32, device=device)
+                  for f in self.FIELDS}
+        self.t.update({f: torch.empty(max(1, self.capacity), dtype=torch.int32, device=device)
+                       for f in self.KEYS})
+
+    @classmethod
+    def from_arrays(cls, device="cuda", **arrays):
+        n = len(arrays["x"])
+        pb = cls(n, device)
+        torch = _torch()
+        for f in cls.FIELDS:
+            src = arrays["lambda"] if f == "lambda_" else arrays[f]
+            pb.t[f][:n].copy_(torch.from_numpy(np.ascontiguousarray(src, np.float32)))
+        for f in cls.KEYS:
+            pb.t[f][:n].copy_(torch.from_numpy(np.ascontiguousarray(arrays[f], np.uint32).view(np.int32)))
+        pb.n = n
+        return pb
+
+    def desc(self) -> PhotonsDesc:
+        return PhotonsDesc(n=self.n, capacity=self.capacity,
+                           **{k: v.data_ptr() for k, v in self.t.items()})
+
+
+class TraceOutputs:
+    """Device output buffers of rich_trace (rich_outputs)."""
+
+    def __init__(self, hit_capacity, pixels_per_event=0, n_planes=0,
+                 n_hist_events=0, n_photons_fate=0, device="cuda"):
+        torch = _torch()
+        self.hit_capacity = int(hit_capacity)
+        self.hits = torch.empty(max(1, self.hit_capacity) * HIT_DTYPE.itemsize,
+                                dtype=torch.uint8, device=device)
+        self.n_hist_events = int(n_hist_events)
+        self.pixels_per_event = int(pixels_per_event)
+        self.n_planes = int(n_planes)
+        self.pixel_counts = (torch.zeros(n_hist_events * pixels_per_event, dtype=torch.int32,
+                                         device=device) if n_hist_events and pixels_per_event
+                             else None)
+        self.event_sums = (torch.zeros(n_hist_events * n_planes * 4, dtype=torch.float64,
+                                       device=device) if n_hist_events and n_planes else None)
+        self.fate = (torch.zeros(n_photons_fate, dtype=torch.uint8, device=device)
+                     if n_photons_fate else None)
+
+    def clear(self):
+        if self.pixel_counts is not None:
+            self.pixel_counts.zero_()
+        if self.event_sums is not None:
+            self.event_sums.zero_()
+        if self.fate is not None:
+            self.fate.zero_()
+
+    def desc(self) -> Outputs:
+        return Outputs(hits=self.hits.data_ptr(), hit_capacity=self.hit_capacity,
+                       pixel_counts=None if self.pixel_counts is None else self.pixel_counts.data_ptr(),
+                       event_sums=None if self.event_sums is None else self.event_sums.data_ptr(),
+                       n_hist_events=self.n_hist_events if (self.pixel_counts is not None or
+                                                            self.event_sums is not None) else 0,
+                       fate=None if self.fate is None else self.fate.data_ptr())
+
+    def hits_numpy(self, n):
+        n = min(int(n), self.hit_capacity)
+        raw = self.hits[: n * HIT_DTYPE.itemsize].cpu().numpy()
+        return raw.view(HIT_DTYPE).copy()
+
+    def pixel_counts_numpy(self):
+        return self.pixel_counts.cpu().numpy().view(np.uint32).reshape(
+            self.n_hist_events, self.pixels_per_event)
+
+    def event_sums_numpy(self):
+        return self.event_sums.cpu().numpy().reshape(self.n_hist_events, self.n_planes, 4)
+
+
+# ---------------------------------------------------------------- context
+class Context:
+    """Owns one rich_ctx. Methods mirror the C entry points."""
+
+    def __init__(self, device=0, stream=None):
+        L = load()
+        h = C.c_void_p()
+        s = current_stream_handle() if stream is None else stream
+        st = L.rich_create(C.byref(h), int(device), C.c_void_p(s))
+        if st != RICH_OK:
+            raise RichError(st, L.rich_last_error(None).decode(errors="replace"))
+        self.handle = h
+        self.device = device
+        self._geom_keep = None
+        self.scene = None
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().rich_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        _check(self.handle, load().rich_set_stream(self.handle, C.c_void_p(stream)))
+
+    def init_geometry(self, scene: W.Scene):
+        keep = [np.ascontiguousarray(scene.tables), np.ascontiguousarray(scene.materials),
+                np.ascontiguousarray(scene.spheres), np.ascontiguousarray(scene.rects),
+                np.ascontiguousarray(scene.tri_vertices, np.float32),
+                None if scene.tri_normals is None else
+                np.ascontiguousarray(scene.tri_normals, np.float32),
+                np.ascontiguousarray(scene.tri_material, np.int32)]
+        p = lambda a: None if a is None or a.size == 0 else a.ctypes.data
+        d = GeometryDesc(n_tables=len(keep[0]), n_materials=len(keep[1]),
+                         n_spheres=len(keep[2]), n_rects=len(keep[3]),
+                         n_triangles=scene.n_triangles, tables=p(keep[0]),
+                         materials=p(keep[1]), spheres=p(keep[2]), rects=p(keep[3]),
+                         tri_vertices=p(keep[4]), tri_normals=p(keep[5]),
+                         tri_material=p(keep[6]))
+        _check(self.handle, load().rich_init_geometry(self.handle, C.byref(d)))
+        self.scene = scene
+
+    def emit(self, tracks: DeviceTracks, n_minus_1, lambda_min=200.0, lambda_max=600.0,
+             seed=0, photons: PhotonBuffers | None = None, sync=True):
+        prm = EmitParams(seed=int(seed), n_minus_1=float(n_minus_1),
+                         lambda_min=float(lambda_min), lambda_max=float(lambda_max))
+        n = C.c_uint64(0)
+        pd = photons.desc() if photons is not None else None
+        st = load().rich_emit(self.handle, C.byref(tracks.desc()), C.byref(prm),
+                              None if pd is None else C.byref(pd),
+                              C.byref(n) if sync else None)
+        _check(self.handle, st)
+        if photons is not None:
+            photons.n = int(pd.n)
+        return int(n.value) if sync else None
+
+    def trace(self, outputs: TraceOutputs, photons: PhotonBuffers | None = None,
+              precision=PREC_REFINE64, max_bounces=8, max_steps=16, t_min=1e-3,
+              seed=0, block_threads=0, blocks_per_sm=0, refill_min=0, chunk=0):
+        o = TraceOpts(seed=int(seed), precision=precision, max_bounces=max_bounces,
+                      max_steps=max_steps, t_min=t_min, block_threads=block_threads,
+                      blocks_per_sm=blocks_per_sm, refill_min=refill_min, chunk=chunk)
+        pd = photons.desc() if photons is not None else None
+        st = load().rich_trace(self.handle, None if pd is None else C.byref(pd),
+                               C.byref(o), C.byref(outputs.desc()))
+        _check(self.handle, st)
+
+    def philox(self, counters, seed):
+        """Library Philox4x32-10 of an (n, 4) uint32 counter array."""
+        torch = _torch()
+        ctr = np.ascontiguousarray(counters, np.uint32).reshape(-1, 4)
+        d_in = torch.from_numpy(ctr.view(np.int32).copy()).to(f"cuda:{self.device}")
+        d_out = torch.empty_like(d_in)
+        _check(self.handle, load().rich_philox(self.handle, C.c_void_p(d_in.data_ptr()),
+                                               len(ctr), int(seed),
+                                               C.c_void_p(d_out.data_ptr())))
+        return d_out.cpu().numpy().view(np.uint32).reshape(-1, 4)
+
+    def hits(self, allow_overflow=False):
+        """Returns (n_hits, stats dict); synchronises the context stream."""
+        n = C.c_uint64(0)
+        s = Stats()
+        st = load().rich_hits(self.handle, C.byref(n), C.byref(s))
+        if not (allow_overflow and st == 4):
+            _check(self.handle, st)
+        stats = {"n_photons": int(s.n_photons), "n_hits": int(s.n_hits),
+                 "fate": [int(x) for x in s.n_fate], "device_status": int(s.device_status),
+                 "status": int(st)}
+        return int(n.value), stats
+
+
+# ------------------------------------------ C-ABI-named module functions
+def rich_create(device=0, stream=None) -> Context:
+    return Context(device, stream)
+
+
+def rich_destroy(ctx: Context):
+    ctx.close()
+
+
+def rich_init_geometry(ctx: Context, scene):
+    ctx.init_geometry(scene)
+
+
+def rich_emit(ctx: Context, tracks, n_minus_1, **kw):
+    return ctx.emit(tracks, n_minus_1, **kw)
+
+
+def rich_trace(ctx: Context, outputs, **kw):
+    ctx.trace(outputs, **kw)
+
+
+def rich_hits(ctx: Context, **kw):
+    return ctx.hits(**kw)
+
+
+def rich_version() -> str:
+    return load().rich_version().decode()

@@ -1,0 +1,119 @@
+"""Helpers shared by the GPU parity tests: run a workload through the C ABI
+and through the FP64 oracle on the same seeded inputs, and compare them
+photon by photon."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+from paper_2309_12496_gb300 import rich
+from paper_2309_12496_gb300 import workloads as W
+
+# Hit-position tolerance of the refined path: 1e-4 mm on (u, v).
+TOL_UV_REFINE = 1e-4
+# FP32 path: positions carry FP32 rounding of world coordinates up to
+# ~3 m (ulp 2.4e-4 mm) accumulated over a few segments; bound stated as
+# 2e-3 mm for the 2.7 m mirror and 1e-2 mm for the 8.6 m one.
+TOL_UV_FP32 = {"point_source": 2e-3, "rich1": 2e-3, "rich2": 1e-2}
+
+
+def n_events(tracks):
+    return int(tracks.event.max()) + 1 if tracks.n else 1
+
+
+def run_gpu(wl: W.Workload, precision=rich.PREC_REFINE64, ctx=None, want_fate=True,
+            hist=True, launch=None, photons=None, dtracks=None, trace_seed=0):
+    own = ctx is None
+    if own:
+        ctx = rich.Context(0)
+        ctx.init_geometry(wl.scene)
+    dt = dtracks if dtracks is not None else rich.DeviceTracks(wl.tracks)
+    n = ctx.emit(dt, wl.n_minus_1, wl.lambda_min, wl.lambda_max, wl.seed)
+    ne = n_events(wl.tracks) if hist else 0
+    out = rich.TraceOutputs(max(n, 1), wl.scene.pixels_per_event, len(wl.scene.planes),
+                            ne, n if want_fate else 0)
+    ctx.trace(out, photons=photons, precision=precision, seed=trace_seed, **(launch or {}))
+    n_hits, stats = ctx.hits()
+    res = {"n": n, "n_hits": n_hits, "stats": stats, "hits": out.hits_numpy(n_hits),
+           "fate": out.fate.cpu().numpy() if want_fate and n else np.zeros(0, np.uint8)}
+    if hist and ne:
+        res["pixel_counts"] = out.pixel_counts_numpy()
+        res["event_sums"] = out.event_sums_numpy()
+    if own:
+        ctx.close()
+    return res
+
+
+def run_oracle(wl: W.Workload, track_range=None, **kw):
+    sc = oracle.Scene(wl.scene)
+    prm = oracle.params(wl, **kw)
+    return sc.trace(wl.tracks, prm, track_range=track_range,
+                    n_hist_events=n_events(wl.tracks))
+
+
+def hit_index(hits, tracks, offsets):
+    """Global photon index of each hit from its (event, track id, photon)."""
+    key = {(int(e), int(i)): k for k, (e, i) in enumerate(zip(tracks.event, tracks.id))}
+    t = np.array([key[(int(e), int(i))] for e, i in zip(hits["event"], hits["track"])],
+                 dtype=np.int64)
+    return offsets[t].astype(np.int64) + hits["photon"].astype(np.int64)
+
+
+def compare(gpu, ref, tracks, tol_uv, sel=None, max_mismatch_frac=1e-5):
+    """Photon-by-photon comparison. `sel`: boolean mask of the photons the
+    oracle traced (default all). Returns a dict of error statistics and
+    raises AssertionError on a violation of the parity bar:
+      * fates equal for every photon not flagged as a graze by the oracle,
+        and mismatches (all grazes) at most max_mismatch_frac of photons
+        (plus one);
+      * every hit of a non-graze photon: same plane and pixel, |du|, |dv|
+        within tol_uv mm;
+      * per-pixel counts equal on every pixel not touched by a mismatched
+        photon."""
+    offsets = ref["offsets"]
+    n = int(offsets[-1])
+    assert gpu["n"] == n, f"photon count {gpu['n']} vs oracle {n}"
+    if sel is None:
+        sel = np.ones(n, bool)
+    f_g, f_o, graze = gpu["fate"][sel], ref["fate"][sel], ref["graze"][sel] != 0
+    mism = f_g != f_o
+    assert not (mism & ~graze).any(), (
+        f"{int((mism & ~graze).sum())} non-graze fate mismatches; first at "
+        f"{np.nonzero(mism & ~graze)[0][:5]}")
+    n_sel = int(sel.sum())
+    hits = gpu["hits"]
+    g = hit_index(hits, tracks, offsets)
+    keep = sel[g]
+    hits, g = hits[keep], g[keep]
+    ok = (ref["fate"][g] == oracle.FATE_DETECTED)
+    both = ok & (ref["graze"][g] == 0)
+    plane_bad = hits["plane"][both] != ref["plane"][g[both]]
+    pix_bad = (hits["ix"][both] != ref["ix"][g[both]]) | (hits["iy"][both] != ref["iy"][g[both]])
+    du = np.abs(hits["u"][ok] - ref["u"][g[ok]])
+    dv = np.abs(hits["v"][ok] - ref["v"][g[ok]])
+    lam_bad = hits["lambda"] != ref["lambda"][g]
+    out = {"photons": n_sel, "hits": int(len(hits)), "fate_mismatch": int(mism.sum()),
+           "grazes": int(graze.sum()), "plane_mismatch": int(plane_bad.sum()),
+           "pixel_mismatch": int(pix_bad.sum()),
+           "max_du": float(du.max(initial=0.0)), "max_dv": float(dv.max(initial=0.0)),
+           "rms_duv": float(np.sqrt(np.mean(np.concatenate([du, dv]) ** 2))) if len(du) else 0.0,
+           "lambda_mismatch": int(lam_bad.sum())}
+    assert out["lambda_mismatch"] == 0, out
+    assert out["plane_mismatch"] == 0 and out["pixel_mismatch"] == 0, out
+    assert out["max_du"] <= tol_uv and out["max_dv"] <= tol_uv, out
+    assert out["fate_mismatch"] <= max_mismatch_frac * n_sel + 1, out
+    if "pixel_counts" in gpu and "pixel_counts" in ref and sel.all():
+        pc_g, pc_o = gpu["pixel_counts"], ref["pixel_counts"]
+        diff = pc_g.astype(np.int64) - pc_o.astype(np.int64)
+        if mism.any():
+            # pixels touched by mismatched photons may differ
+            bad_g = np.nonzero(mism)[0]
+            touched = set()
+            for gg in bad_g:
+                if ref["fate"][gg] == oracle.FATE_DETECTED:
+                    touched.add((int(ref["plane"][gg]), int(ref["iy"][gg]), int(ref["ix"][gg])))
+            out["pixels_touched_by_mismatch"] = len(touched)
+            assert np.abs(diff).sum() <= 2 * len(bad_g), out
+        else:
+            assert not diff.any(), f"{int((diff != 0).sum())} pixels differ"
+    return out
