@@ -224,12 +224,17 @@ typedef struct rich_trace_opts {
     int32_t max_steps;      /* surface interactions, 1..RICH_MAX_STEPS        */
     float t_min;            /* minimum hit distance after an interaction (mm) */
     /* launch knobs (0 -> tuned default) */
-    int32_t block_threads;  /* threads per block (multiple of 32)            */
-    int32_t blocks_per_sm;  /* resident blocks per SM for the persistent grid*/
+    int32_t block_threads;  /* threads per block, multiple of 32, <= 1024;
+                               above 256 one block runs per SM             */
+    int32_t blocks_per_sm;  /* resident blocks per SM of the persistent grid
+                               (0 or above the occupancy limit -> the limit) */
     int32_t refill_min;     /* refill a warp when at least this many lanes are
                                idle (1..32): the compaction interval          */
     int32_t chunk;          /* photons a warp takes from the queue at a time */
-    int32_t reserved;
+    int32_t wide_regs;      /* <= 256 threads: 0 caps the trace kernel at 64
+                               registers (four blocks per SM), 1 uncapped    */
+    int32_t bvh_smem_nodes; /* top BVH nodes staged in shared memory per block
+                               by a TMA bulk copy (-1: default)              */
 } rich_trace_opts;
 
 /* ----------------------------------------------------------------- outputs */

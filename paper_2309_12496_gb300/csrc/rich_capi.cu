@@ -48,6 +48,12 @@ struct rich_ctx {
     bool last_ext = false;
     uint64_t last_ext_n = 0;
     uint64_t last_capacity = 0;
+    // refinement side records, one per storable hit
+    RefineRec *d_refine = nullptr;
+    uint64_t refine_cap = 0;
+    // occupancy per (external, refine, threads, smem), queried once
+    std::map<std::tuple<bool, bool, int, int, size_t>, int> occupancy;
+    int smem_optin = 48 * 1024;
 };
 
 static thread_local std::string g_create_error;
@@ -147,6 +153,7 @@ RICH_API rich_status rich_create(rich_ctx **out, int device, void *stream) {
         return e == cudaErrorMemoryAllocation ? RICH_ERR_OOM : RICH_ERR_CUDA;
     }
     ctx->n_sm = prop.multiProcessorCount;
+    ctx->smem_optin = (int)prop.sharedMemPerBlockOptin;
     *out = ctx;
     return RICH_OK;
 }
@@ -157,6 +164,7 @@ RICH_API rich_status rich_destroy(rich_ctx *ctx) {
         DeviceGuard g(ctx->device);
         cudaStreamSynchronize(ctx->stream);
         cudaFree(ctx->d_geom);
+        cudaFree(ctx->d_refine);
         free_emission(ctx);
         cudaFree(ctx->d_ctr);
         cudaFree(ctx->d_total);
@@ -495,14 +503,29 @@ RICH_API rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
     if (in && in->n && (!in->x || !in->y || !in->z || !in->dx || !in->dy || !in->dz ||
                         !in->lambda || !in->event || !in->track || !in->photon))
         return fail(ctx, RICH_ERR_ARG, "rich_trace: a photon input array is NULL");
-    const int threads = o->block_threads ? o->block_threads : 256;
-    if (threads % 32 != 0 || threads < 32 || threads > 256)
-        return fail(ctx, RICH_ERR_ARG, "rich_trace: block_threads must be 32..256, a multiple of 32");
-    const int refill = o->refill_min ? o->refill_min : 16;
+    const int threads = o->block_threads ? o->block_threads : 1024;
+    if (threads % 32 != 0 || threads < 32 || threads > 1024)
+        return fail(ctx, RICH_ERR_ARG, "rich_trace: block_threads must be 32..1024, a multiple of 32");
+    const int refill = o->refill_min ? o->refill_min : 32;
     if (refill < 1 || refill > 32) return fail(ctx, RICH_ERR_ARG, "rich_trace: refill_min 1..32");
-    const int chunk = o->chunk ? o->chunk : 128;
+    const int chunk = o->chunk ? o->chunk : 32;
     if (chunk < 1 || chunk > (1 << 20)) return fail(ctx, RICH_ERR_ARG, "rich_trace: chunk 1..2^20");
+    const int cls = trace_shape_class(threads, o->wide_regs != 0);
+    int smem_nodes = o->bvh_smem_nodes;
+    if (smem_nodes < 0) smem_nodes = threads > 256 ? 1536 : 0;
+    if (smem_nodes > ctx->sc.n_nodes) smem_nodes = ctx->sc.n_nodes;
+    if (ctx->sc.n_tris == 0) smem_nodes = 0;
     DeviceGuard guard(ctx->device);
+    const bool refine = o->precision == RICH_PREC_REFINE64;
+    const uint64_t hit_cap = out->hits ? out->hit_capacity : 0;
+    if (refine && hit_cap > ctx->refine_cap) {
+        RICH_CUDA(cudaStreamSynchronize(ctx->stream));
+        cudaFree(ctx->d_refine);
+        ctx->d_refine = nullptr;
+        ctx->refine_cap = 0;
+        RICH_CUDA(cudaMalloc(&ctx->d_refine, sizeof(RefineRec) * hit_cap));
+        ctx->refine_cap = hit_cap;
+    }
     RICH_CUDA(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), ctx->stream));
     TraceParams p{};
     p.precision = o->precision;
@@ -517,12 +540,25 @@ RICH_API rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
     p.event_sums = out->event_sums;
     p.n_hist_events = (out->pixel_counts || out->event_sums) ? out->n_hist_events : 0;
     p.fate = out->fate;
-    const bool refine = o->precision == RICH_PREC_REFINE64;
+    p.refine = ctx->d_refine;
+    p.smem_nodes = smem_nodes;
     LaunchShape shape;
     shape.threads = threads;
-    shape.smem = trace_smem_bytes(ctx->sc);
-    const int bps = o->blocks_per_sm ? o->blocks_per_sm
-                                     : trace_blocks_per_sm(in != nullptr, refine, threads, shape.smem);
+    shape.smem = trace_smem_bytes(ctx->sc, smem_nodes);
+    shape.cls = cls;
+    if (shape.smem > (size_t)ctx->smem_optin)
+        return fail(ctx, RICH_ERR_ARG, "rich_trace: staged BVH nodes exceed shared memory");
+    int bps = o->blocks_per_sm;
+    {
+        const auto key = std::make_tuple(in != nullptr, refine, cls, threads, shape.smem);
+        auto it = ctx->occupancy.find(key);
+        if (it == ctx->occupancy.end())
+            it = ctx->occupancy.emplace(key, trace_blocks_per_sm(in != nullptr, refine, cls,
+                                                                 threads, shape.smem)).first;
+        if (it->second < 1)
+            return fail(ctx, RICH_ERR_ARG, "rich_trace: launch shape does not fit on an SM");
+        if (!bps || bps > it->second) bps = it->second;
+    }
     shape.blocks = std::max(1, bps) * ctx->n_sm;
     EmitView em{ctx->d_rec, ctx->d_cs, ctx->d_offsets, ctx->d_total, ctx->n_tracks,
                 ctx->key0, ctx->key1, ctx->inv1, ctx->span};
@@ -531,11 +567,17 @@ RICH_API rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
         em.key1 = (uint32_t)(o->seed >> 32);
         ExtView ev{in->n, in->x, in->y, in->z, in->dx, in->dy, in->dz, in->lambda,
                    in->event, in->track, in->photon};
-        if (in->n) RICH_CUDA(launch_trace(ctx->sc, &em, &ev, p, ctx->d_ctr, shape, ctx->stream));
+        if (in->n) {
+            RICH_CUDA(launch_trace(ctx->sc, &em, &ev, p, ctx->d_ctr, shape, ctx->stream));
+            if (refine)
+                RICH_CUDA(launch_refine(ctx->sc, &em, &ev, p, ctx->d_ctr, ctx->n_sm, ctx->stream));
+        }
         ctx->last_ext = true;
         ctx->last_ext_n = in->n;
     } else {
         RICH_CUDA(launch_trace(ctx->sc, &em, nullptr, p, ctx->d_ctr, shape, ctx->stream));
+        if (refine)
+            RICH_CUDA(launch_refine(ctx->sc, &em, nullptr, p, ctx->d_ctr, ctx->n_sm, ctx->stream));
         ctx->last_ext = false;
     }
     ctx->traced = true;

@@ -137,6 +137,16 @@ struct Counters {            // device, cleared before each trace
     unsigned int pad;
 };
 
+// Per stored hit, what the FP64 refinement pass needs to replay the photon:
+// its track (or caller-photon) index, the detector rectangle and the
+// sequence of reflecting primitives (triangles by BVH leaf position).
+struct RefineRec {             // 40 B
+    uint32_t index;
+    uint8_t det_rect, n_path;
+    uint16_t pad;
+    int32_t path[RICH_MAX_BOUNCES];
+};
+
 struct TraceParams {
     int32_t precision, max_bounces, max_steps;
     float t_min;
@@ -147,11 +157,14 @@ struct TraceParams {
     double *event_sums;
     uint32_t n_hist_events;
     uint8_t *fate;
+    RefineRec *refine;        // capacity hit_capacity (refined precision only)
+    int32_t smem_nodes;       // BVH nodes [0, smem_nodes) staged in shared memory
 };
 
 struct LaunchShape {
     int blocks, threads;
     size_t smem;
+    int cls;                  // kernel variant class (trace_shape_class)
 };
 
 // ---------------------------------------------------------------- launchers
@@ -171,10 +184,14 @@ cudaError_t launch_trace(const SceneView &sc, const EmitView *em,
                          const ExtView *ext, const TraceParams &p,
                          Counters *counters, const LaunchShape &shape,
                          cudaStream_t s);
+cudaError_t launch_refine(const SceneView &sc, const EmitView *em,
+                          const ExtView *ext, const TraceParams &p,
+                          Counters *counters, int n_sm, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t *ctr, uint64_t n, uint64_t seed, uint32_t *out,
                           cudaStream_t s);
-size_t trace_smem_bytes(const SceneView &sc);
-int trace_blocks_per_sm(bool ext, bool refine, int threads, size_t smem);
+size_t trace_smem_bytes(const SceneView &sc, int smem_nodes);
+int trace_shape_class(int threads, bool wide);
+int trace_blocks_per_sm(bool ext, bool refine, int cls, int threads, size_t smem);
 int yield_block_threads();
 
 }  // namespace rich

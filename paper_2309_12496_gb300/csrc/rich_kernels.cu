@@ -15,6 +15,7 @@
 //                  ballot/popc), apply reflectivity and quantum-efficiency
 //                  accept/reject in flight (Sec. 4.3 and Sec. 6), append
 //                  hits with warp-aggregated atomics and bin them.
+#include <climits>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -23,7 +24,9 @@
 namespace rich {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr int kYieldThreads = 256;
+constexpr int kYieldThreads = 256;   // tracks per scan group / scan block
+constexpr int kYieldBlock = 64;      // threads per yield block (spreads the
+                                     // FP64 Poisson work over more SMs)
 constexpr double kAlpha = 1.0 / 137.035999;
 constexpr double kPi = 3.14159265358979323846;
 
@@ -88,7 +91,7 @@ __device__ int64_t poisson_draw(double mu, TrackStream &s) {
     return (int64_t)floor(mu + 0.5);
 }
 
-__global__ void __launch_bounds__(kYieldThreads)
+__global__ void __launch_bounds__(kYieldBlock)
 k_yield(TracksView t, double n_minus_1, double inv_band_mm, uint32_t key0,
         uint32_t key1, TrackRec *rec, double2 *cs, uint32_t *counts,
         unsigned long long *block_sums) {
@@ -141,17 +144,19 @@ k_yield(TracksView t, double n_minus_1, double inv_band_mm, uint32_t key0,
         cs[i] = make_double2(cos_t, sin_t);
         counts[i] = count;
     }
-    // block sum of the counts
+    // sum of the counts of this block, added to its 256-track scan group
+    // (integer atomics: exact and order independent)
     unsigned long long v = count;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
-    __shared__ unsigned long long warp_sum[kYieldThreads / 32];
+    __shared__ unsigned long long warp_sum[kYieldBlock / 32];
     if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long s = 0;
-        for (int w = 0; w < kYieldThreads / 32; ++w) s += warp_sum[w];
-        block_sums[blockIdx.x] = s;
+        for (int w = 0; w < kYieldBlock / 32; ++w) s += warp_sum[w];
+        const int64_t first = (int64_t)blockIdx.x * kYieldBlock;
+        if (s) atomicAdd(&block_sums[first / kYieldThreads], s);
     }
 }
 
@@ -205,7 +210,6 @@ struct Photon {
     uint64_t g;            // global photon index
     uint32_t w_qe;
     uint32_t wr0, wr1, wr2, wr3;
-    uint32_t w_s, w_phi;   // raw draws of the emission (refinement replay)
     int skip, n_refl, steps;
 };
 
@@ -233,8 +237,6 @@ __device__ __forceinline__ void emit_photon(const TrackRec &tr, uint32_t j,
     ph.wr1 = w1.y;
     ph.wr2 = w1.z;
     ph.wr3 = w1.w;
-    ph.w_s = w0.x;
-    ph.w_phi = w0.y;
     ph.event = tr.event;
     ph.id = tr.id;
     ph.j = j;
@@ -481,52 +483,85 @@ __device__ __forceinline__ void leaf_tris(const SceneView &sc, const Ray &r,
     }
 }
 
-__device__ void nearest_bvh(const SceneView &sc, f3 o, f3 d, int skip,
-                            float t_min, Best &b, Counters *ctr) {
+__device__ __forceinline__ void load_node(const SceneView &sc, const DevNode *snodes,
+                                          int n_snodes, int ref, float4 &a, float4 &b,
+                                          float4 &c, int4 &ch) {
+    if (ref < n_snodes) {
+        const float4 *q = reinterpret_cast<const float4 *>(snodes + ref);
+        a = q[0];
+        b = q[1];
+        c = q[2];
+        ch = *reinterpret_cast<const int4 *>(q + 3);
+    } else {
+        const float4 *q = reinterpret_cast<const float4 *>(sc.nodes + ref);
+        a = __ldg(q);
+        b = __ldg(q + 1);
+        c = __ldg(q + 2);
+        ch = __ldg(reinterpret_cast<const int4 *>(q + 3));
+    }
+}
+
+// Nearest triangle along the ray: two-wide BVH in the "while-while" order
+// of Aila and Laine (HPG 2009): descend inner nodes (near child first, the
+// far one stacked with its entry distance) until a leaf is found, postpone
+// it, and intersect postponed leaves together once every active lane holds
+// one, which keeps the lanes of a warp on the same kind of work. The top
+// levels of the tree are read from shared memory.
+__device__ void nearest_bvh(const SceneView &sc, const DevNode *snodes, int n_snodes,
+                            f3 o, f3 d, int skip, float t_min, Best &b, Counters *ctr) {
+    constexpr int kEmpty = INT_MIN;
     const Ray r = make_ray(o, d);
-    int stack_node[RICH_BVH_STACK];
+    int stack_ref[RICH_BVH_STACK];
     float stack_t[RICH_BVH_STACK];
     int sp = 0;
-    int node = 0;
-    while (true) {
-        const float4 *q = reinterpret_cast<const float4 *>(sc.nodes + node);
-        const float4 a = __ldg(q), bb = __ldg(q + 1), c = __ldg(q + 2);
-        const int4 ch = __ldg(reinterpret_cast<const int4 *>(q + 3));
-        float tn0, tn1;
-        bool h0 = slab(r, a.x, a.y, a.z, a.w, bb.x, bb.y, b.t, tn0);
-        bool h1 = slab(r, bb.z, bb.w, c.x, c.y, c.z, c.w, b.t, tn1);
-        if (h0 && ch.x < 0) {
-            leaf_tris(sc, r, ~ch.x, skip, t_min, b);
-            h0 = false;
-        }
-        if (h1 && ch.y < 0) {
-            leaf_tris(sc, r, ~ch.y, skip, t_min, b);
-            h1 = false;
-        }
-        if (h0 && h1) {
-            const bool first0 = tn0 <= tn1;
-            if (sp < RICH_BVH_STACK) {
-                stack_node[sp] = first0 ? ch.y : ch.x;
-                stack_t[sp] = first0 ? tn1 : tn0;
-                ++sp;
-            } else {
-                set_status(ctr, RICH_ERR_GEOMETRY);
-            }
-            node = first0 ? ch.x : ch.y;
-            continue;
-        }
-        if (h0) { node = ch.x; continue; }
-        if (h1) { node = ch.y; continue; }
-        bool found = false;
+    int ref = 0, leaf = kEmpty;
+    auto pop = [&]() -> int {
         while (sp > 0) {
             --sp;
-            if (stack_t[sp] <= b.t) {
-                node = stack_node[sp];
-                found = true;
-                break;
+            if (stack_t[sp] <= b.t) return stack_ref[sp];
+        }
+        return kEmpty;
+    };
+    while (ref != kEmpty || leaf != kEmpty) {
+        while (ref >= 0) {
+            float4 na, nb, nc;
+            int4 ch;
+            load_node(sc, snodes, n_snodes, ref, na, nb, nc, ch);
+            float tn0, tn1;
+            const bool h0 = slab(r, na.x, na.y, na.z, na.w, nb.x, nb.y, b.t, tn0);
+            const bool h1 = slab(r, nb.z, nb.w, nc.x, nc.y, nc.z, nc.w, b.t, tn1);
+            if (h0 && h1) {
+                const bool first0 = tn0 <= tn1;
+                if (sp < RICH_BVH_STACK) {
+                    stack_ref[sp] = first0 ? ch.y : ch.x;
+                    stack_t[sp] = first0 ? tn1 : tn0;
+                    ++sp;
+                } else {
+                    set_status(ctr, RICH_ERR_GEOMETRY);
+                }
+                ref = first0 ? ch.x : ch.y;
+            } else if (h0) {
+                ref = ch.x;
+            } else if (h1) {
+                ref = ch.y;
+            } else {
+                ref = pop();
+            }
+            if (ref < 0 && ref != kEmpty && leaf == kEmpty) {
+                leaf = ref;
+                ref = pop();
+            }
+            // scheduling only: leave once every lane still here holds a leaf
+            if (!__any_sync(__activemask(), leaf == kEmpty)) break;
+        }
+        while (leaf != kEmpty) {
+            leaf_tris(sc, r, ~leaf, skip, t_min, b);
+            leaf = kEmpty;
+            if (ref < 0 && ref != kEmpty) {
+                leaf = ref;
+                ref = pop();
             }
         }
-        if (!found) break;
     }
 }
 
@@ -534,53 +569,35 @@ __device__ void nearest_bvh(const SceneView &sc, f3 o, f3 d, int skip,
 // Refinement of a detected photon: the recorded sequence of reflecting
 // primitives is replayed in FP64 (emission, each reflection on the same
 // primitive's surface extended past its edges, the final plane), giving
-// the hit position and pixel in FP64.
-__device__ void replay64(const SceneView &sc, const SmemScene &S,
-                         const Photon &ph, const TrackRec *tr,
-                         const double2 *cs, const ExtView *ext,
-                         const int *path, int n_path, int det_rect,
-                         double &u, double &v) {
-    d3 o, d;
-    if (tr) {
-        d3 t = normalized(mkd(tr->rx, tr->ry, tr->rz));
-        double s = u24d(ph.w_s) * (double)tr->len;
-        o = mkd(fma(t.x, s, (double)tr->x), fma(t.y, s, (double)tr->y),
-                fma(t.z, s, (double)tr->z));
-        double sp, cp;
-        sincospi(2.0 * u24d(ph.w_phi), &sp, &cp);
-        d3 e1, e2;
-        basis_d(t, e1, e2);
-        const double ct = cs->x, st = cs->y;
-        d = mkd(ct * t.x + st * (cp * e1.x + sp * e2.x),
-                ct * t.y + st * (cp * e1.y + sp * e2.y),
-                ct * t.z + st * (cp * e1.z + sp * e2.z));
-        d = normalized(d);
-    } else {
-        o = mkd(ext->x[ph.track], ext->y[ph.track], ext->z[ph.track]);
-        d = normalized(mkd(ext->dx[ph.track], ext->dy[ph.track], ext->dz[ph.track]));
-    }
-    for (int k = 0; k < n_path; ++k) {
-        const int prim = path[k];
+// the hit position and pixel in FP64. Runs in its own pass (k_refine), one
+// thread per stored hit, so the slow FP64 pipe sees converged warps.
+__device__ void replay64(const SceneView &sc, const d3 o0, const d3 d0,
+                         const RefineRec &rr, double &u, double &v) {
+    d3 o = o0, d = d0;
+    for (int k = 0; k < rr.n_path; ++k) {
+        const int prim = rr.path[k];
         d3 n;
         if (prim < sc.n_tiles) {
             int ti = 0;
-            for (int q = 0; q < S.n_tiles; ++q)
-                if (S.tiles[q].prim == prim) ti = q;
-            const DevSphereGroup &G = S.groups[S.tiles[ti].group];
+            for (int q = 0; q < sc.n_tiles; ++q)
+                if (sc.tiles[q].prim == prim) ti = q;
+            const DevSphereGroup &G = sc.groups[sc.tiles[ti].group];
             const d3 w = o - mkd(G.cx, G.cy, G.cz);
             const double bq = dotd(w, d);
             const double c = dotd(w, w) - G.r2;
-            const double sq = sqrt(fmax(0.0, bq * bq - c));
-            // concave (front) side: the exit root -b + sqrt(disc)
-            const double t = bq <= 0.0 ? (sq - bq) : c / (-bq - sq);
-            o = o + d * t;
+            const double disc = fmax(0.0, fma(bq, bq, -c));
+            const double sq = disc > 0.0 ? disc * rsqrt64(disc) : 0.0;
+            // concave (front) side: the exit root -b + sqrt(disc), taken in
+            // the form free of cancellation
+            const double t = bq <= 0.0 ? (sq - bq) : c * rcp64(-bq - sq);
+            o = mkd(fma(d.x, t, o.x), fma(d.y, t, o.y), fma(d.z, t, o.z));
             const d3 pc = o - mkd(G.cx, G.cy, G.cz);
-            n = pc * (-1.0 / sqrt(G.r2));
+            n = pc * -rsqrt64(dotd(pc, pc));
         } else if (prim < sc.tri_prim_base) {
             const DevRectD &R = sc.rects_d[prim - sc.n_tiles];
             n = mkd(R.nx, R.ny, R.nz);
-            const double t = dotd(mkd(R.ox, R.oy, R.oz) - o, n) / dotd(d, n);
-            o = o + d * t;
+            const double t = dotd(mkd(R.ox, R.oy, R.oz) - o, n) * rcp64(dotd(d, n));
+            o = mkd(fma(d.x, t, o.x), fma(d.y, t, o.y), fma(d.z, t, o.z));
         } else {
             const int k_tri = prim - sc.tri_prim_base;   // leaf-order index
             const DevTri T = load_tri(sc.tris + k_tri);
@@ -588,17 +605,17 @@ __device__ void replay64(const SceneView &sc, const SmemScene &S,
                      v2 = mkd(T.v2x, T.v2y, T.v2z);
             const d3 e1 = v1 - v0, e2 = v2 - v0;
             const d3 ng = crossd(e1, e2);
-            const double t = dotd(v0 - o, ng) / dotd(d, ng);
-            o = o + d * t;
-            const DevMaterial &M = S.materials[T.material];
+            const double t = dotd(v0 - o, ng) * rcp64(dotd(d, ng));
+            o = mkd(fma(d.x, t, o.x), fma(d.y, t, o.y), fma(d.z, t, o.z));
+            const DevMaterial &M = sc.materials[T.material];
             if ((M.flags & RICH_MAT_SMOOTH) && sc.tri_normals) {
                 // barycentrics of the hit in the triangle's plane
                 const d3 q = o - v0;
                 const double d00 = dotd(e1, e1), d01 = dotd(e1, e2), d11 = dotd(e2, e2);
                 const double d20 = dotd(q, e1), d21 = dotd(q, e2);
-                const double den = d00 * d11 - d01 * d01;
-                const double b1 = (d11 * d20 - d01 * d21) / den;
-                const double b2 = (d00 * d21 - d01 * d20) / den;
+                const double inv_den = rcp64(fma(d00, d11, -d01 * d01));
+                const double b1 = fma(d11, d20, -d01 * d21) * inv_den;
+                const double b2 = fma(d00, d21, -d01 * d20) * inv_den;
                 const double b0 = 1.0 - b1 - b2;
                 const float *N = sc.tri_normals + 9 * (int64_t)k_tri;
                 n = normalized(mkd(b0 * N[0] + b1 * N[3] + b2 * N[6],
@@ -608,15 +625,81 @@ __device__ void replay64(const SceneView &sc, const SmemScene &S,
                 n = normalized(ng);
             }
         }
-        d = normalized(reflect_d(d, n));
+        // |d| = 1 is kept by the reflection about a unit normal
+        d = reflect_d(d, n);
     }
-    const DevRectD &R = sc.rects_d[det_rect];
+    const DevRectD &R = sc.rects_d[rr.det_rect];
     const d3 nrm = mkd(R.nx, R.ny, R.nz);
     const d3 O = mkd(R.ox, R.oy, R.oz);
-    const double t = dotd(O - o, nrm) / dotd(d, nrm);
-    const d3 q = (o + d * t) - O;
+    const double t = dotd(O - o, nrm) * rcp64(dotd(d, nrm));
+    const d3 q = mkd(fma(d.x, t, o.x - O.x), fma(d.y, t, o.y - O.y), fma(d.z, t, o.z - O.z));
     u = dotd(q, mkd(R.ux, R.uy, R.uz));
     v = dotd(q, mkd(R.vx, R.vy, R.vz));
+}
+
+// FP64 emission of photon j of a track (the same draws as emit_photon).
+__device__ void emit64(const TrackRec &tr, double2 cs, uint32_t j, const EmitView &em,
+                       d3 &o, d3 &d) {
+    const u4 w0 = philox10(0u, j, tr.id, tr.event, em.key0, em.key1);
+    const d3 t = normalized(mkd(tr.rx, tr.ry, tr.rz));
+    const double s = u24d(w0.x) * (double)tr.len;
+    o = mkd(fma(t.x, s, (double)tr.x), fma(t.y, s, (double)tr.y), fma(t.z, s, (double)tr.z));
+    double sp, cp;
+    sincospi(2.0 * u24d(w0.y), &sp, &cp);
+    d3 e1, e2;
+    basis_d(t, e1, e2);
+    const double ct = cs.x, st = cs.y;
+    d = normalized(mkd(ct * t.x + st * (cp * e1.x + sp * e2.x),
+                       ct * t.y + st * (cp * e1.y + sp * e2.y),
+                       ct * t.z + st * (cp * e1.z + sp * e2.z)));
+}
+
+// Sum `val` over the lanes of `peers` (lanes sharing one key) and add it
+// once, from the lowest peer, to *addr.
+__device__ __forceinline__ void peer_add(unsigned peers, double val, double *addr) {
+    double sum = 0.0;
+    unsigned m = peers;
+    while (m) {
+        const int src = __ffs(m) - 1;
+        sum += __shfl_sync(peers, val, src);
+        m &= m - 1;
+    }
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(addr, sum);
+}
+
+__device__ __forceinline__ void bin_hit(const SceneView &sc, const TraceParams &P,
+                                        uint32_t event, int plane, int ix, int iy) {
+    if (P.pixel_counts && event < P.n_hist_events) {
+        const int64_t idx = (int64_t)event * sc.pixels_per_event + sc.plane_offset[plane] +
+                            (int64_t)iy * sc.plane_nx[plane] + ix;
+        atomicAdd(P.pixel_counts + idx, 1u);
+    }
+}
+
+__device__ __forceinline__ void pixel_of(const DevRect &R, double u, double v, int &ix,
+                                         int &iy) {
+    const double pitch = (double)R.pitch;
+    ix = (int)floor(u / pitch);
+    iy = (int)floor(v / pitch);
+    ix = ix < 0 ? 0 : (ix >= R.gx ? R.gx - 1 : ix);
+    iy = iy < 0 ? 0 : (iy >= R.gy ? R.gy - 1 : iy);
+}
+
+// Event sums (hits, sum u, sum v, sum lambda) with one FP64 atomic per
+// (event, plane) group of lanes of the calling converged warp.
+__device__ __forceinline__ void add_event_sums(const SceneView &sc, const TraceParams &P,
+                                               bool on, uint32_t event, int plane,
+                                               double u, double v, float lam) {
+    const bool take = on && P.event_sums && event < P.n_hist_events;
+    const unsigned act = __ballot_sync(0xFFFFFFFFu, take);
+    if (!take) return;
+    const long long key = (long long)event * sc.n_planes + plane;
+    const unsigned peers = __match_any_sync(act, key);
+    double *es = P.event_sums + key * 4;
+    peer_add(peers, 1.0, es + 0);
+    peer_add(peers, u, es + 1);
+    peer_add(peers, v, es + 2);
+    peer_add(peers, (double)lam, es + 3);
 }
 
 // ================================================================ trace
@@ -636,15 +719,48 @@ __device__ __forceinline__ uint32_t refl_word(const Photon &ph, int k,
     return k == 0 ? w.x : (k == 1 ? w.y : (k == 2 ? w.z : w.w));
 }
 
-template <bool EXT, bool REFINE>
-__global__ void __launch_bounds__(256)
+template <bool EXT, bool REFINE, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB)
 k_trace(TraceArgs A) {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const SceneView &sc = A.sc;
+    // ---- top BVH levels: one TMA bulk copy into shared memory, completion
+    //      tracked by an mbarrier; the wait is bounded and falls back to
+    //      global reads (with an error status) if it ever runs out
+    __shared__ __align__(8) unsigned long long s_bar;
+    const int n_snodes_req = A.p.smem_nodes;
+    int n_snodes = n_snodes_req;
+    const DevNode *snodes = reinterpret_cast<const DevNode *>(smem);
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&s_bar);
+    if (n_snodes_req > 0) {
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const uint32_t bytes = (uint32_t)n_snodes_req * (uint32_t)sizeof(DevNode);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                         "r"(bytes)
+                         : "memory");
+            const uint32_t dst = (uint32_t)__cvta_generic_to_shared(smem);
+            const char *src = reinterpret_cast<const char *>(sc.nodes);
+            for (uint32_t off = 0; off < bytes; off += 32768u) {
+                const uint32_t len = bytes - off < 32768u ? bytes - off : 32768u;
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+                    "[%0], [%1], %2, [%3];" ::"r"(dst + off),
+                    "l"(src + off), "r"(len), "r"(bar)
+                    : "memory");
+            }
+        }
+    }
+    const size_t scene_off = ((size_t)n_snodes_req * sizeof(DevNode) + 127) & ~size_t(127);
     // ---- stage the small scene tables into shared memory
     SmemScene S;
     {
-        size_t off = 0;
+        size_t off = scene_off;
         auto carve = [&](size_t bytes) {
             unsigned char *p = smem + off;
             off += (bytes + 15) & ~size_t(15);
@@ -667,6 +783,22 @@ k_trace(TraceArgs A) {
         copy(m, sc.materials, sizeof(DevMaterial) * sc.n_materials);
         S = {g, t, r, tb, m, sc.n_groups, sc.n_tiles, sc.n_rects};
     }
+    if (n_snodes_req > 0) {
+        uint32_t done = 0;
+        for (int it = 0; it < (1 << 20) && !done; ++it) {
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(done)
+                : "r"(bar)
+                : "memory");
+        }
+        if (!done) {
+            set_status(A.ctr, RICH_ERR_TIMEOUT);
+            n_snodes = 0;
+        }
+    }
     __shared__ unsigned long long s_fate[8];
     __shared__ unsigned long long s_hits;
     if (threadIdx.x < 8) s_fate[threadIdx.x] = 0;
@@ -683,7 +815,7 @@ k_trace(TraceArgs A) {
 
     Photon ph;
     bool alive = false;
-    int path[REFINE ? RICH_MAX_BOUNCES : 1];
+    int path[RICH_MAX_BOUNCES];
     uint64_t pool_next = 0, pool_end = 0;   // warp-uniform
     int64_t pool_track = 0;                 // warp-uniform
     bool more = true;                       // warp-uniform
@@ -743,8 +875,6 @@ k_trace(TraceArgs A) {
                         const u4 w1 = philox10(1u, ph.j, ph.id, ph.event, em.key0, em.key1);
                         ph.w_qe = w0.w;
                         ph.wr0 = w1.x; ph.wr1 = w1.y; ph.wr2 = w1.z; ph.wr3 = w1.w;
-                        ph.w_s = w0.x;
-                        ph.w_phi = w0.y;
                     } else {
                         while (my_track + 1 < em.n_tracks && em.offsets[my_track + 1] <= g)
                             ++my_track;
@@ -782,7 +912,7 @@ k_trace(TraceArgs A) {
             b.b0 = b.b1 = b.b2 = 0.0f;
             if (S.n_groups) nearest_tiles(S, ph.o, ph.d, ph.skip, P.t_min, b);
             nearest_rects(S, ph.o, ph.d, ph.skip, P.t_min, b);
-            if (has_tri) nearest_bvh(sc, ph.o, ph.d, ph.skip, P.t_min, b, A.ctr);
+            if (has_tri) nearest_bvh(sc, snodes, n_snodes, ph.o, ph.d, ph.skip, P.t_min, b, A.ctr);
             if (b.prim < 0) {
                 fate = RICH_FATE_ESCAPED;
             } else {
@@ -874,6 +1004,9 @@ k_trace(TraceArgs A) {
         // -------------------------------------------- finished photons
         const bool det = fate == RICH_FATE_DETECTED;
         const unsigned dm = __ballot_sync(kFull, det);
+        bool binned_here = false;
+        double hu = 0.0, hv = 0.0;
+        int hplane = 0;
         if (dm) {
             unsigned long long base = 0;
             const int leader = __ffs(dm) - 1;
@@ -881,50 +1014,44 @@ k_trace(TraceArgs A) {
             base = __shfl_sync(kFull, base, leader);
             if (det) {
                 const DevRect &R = S.rects[det_rect];
-                const DevMaterial &M = S.materials[R.material];
-                double u = hit_u, v = hit_v;
-                if (REFINE) {
-                    const TrackRec *trp = EXT ? nullptr : &em.tracks[ph.track];
-                    const double2 *csp = EXT ? nullptr : &em.cos_sin[ph.track];
-                    replay64(sc, S, ph, trp, csp, &A.ext, path, ph.n_refl, det_rect, u, v);
-                }
-                const double pitch = (double)R.pitch;
-                int ix = (int)floor(u / pitch), iy = (int)floor(v / pitch);
-                ix = ix < 0 ? 0 : (ix >= R.gx ? R.gx - 1 : ix);
-                iy = iy < 0 ? 0 : (iy >= R.gy ? R.gy - 1 : iy);
+                hplane = S.materials[R.material].plane;
+                hu = hit_u;
+                hv = hit_v;
+                int ix, iy;
+                pixel_of(R, hu, hv, ix, iy);
                 const uint64_t slot = base + (uint64_t)__popc(dm & lt_mask);
-                if (slot < P.hit_capacity) {
+                const bool stored = slot < P.hit_capacity;
+                if (stored) {
                     rich_hit h;
                     h.event = ph.event;
                     h.track = ph.id;
                     h.photon = ph.j;
-                    h.plane = (uint8_t)M.plane;
+                    h.plane = (uint8_t)hplane;
                     h.n_reflections = (uint8_t)ph.n_refl;
                     h.reserved = 0;
                     h.ix = (uint16_t)ix;
                     h.iy = (uint16_t)iy;
                     h.lambda = ph.lam;
-                    h.u = u;
-                    h.v = v;
+                    h.u = hu;
+                    h.v = hv;
                     P.hits[slot] = h;
-                }
-                if (ph.event < P.n_hist_events) {
-                    if (P.pixel_counts) {
-                        const int64_t idx = (int64_t)ph.event * sc.pixels_per_event +
-                                            sc.plane_offset[M.plane] +
-                                            (int64_t)iy * sc.plane_nx[M.plane] + ix;
-                        atomicAdd(P.pixel_counts + idx, 1u);
-                    }
-                    if (P.event_sums) {
-                        double *es = P.event_sums + ((int64_t)ph.event * sc.n_planes + M.plane) * 4;
-                        atomicAdd(es + 0, 1.0);
-                        atomicAdd(es + 1, u);
-                        atomicAdd(es + 2, v);
-                        atomicAdd(es + 3, (double)ph.lam);
+                    if (REFINE) {
+                        RefineRec rr;
+                        rr.index = ph.track;
+                        rr.det_rect = (uint8_t)det_rect;
+                        rr.n_path = (uint8_t)ph.n_refl;
+                        rr.pad = 0;
+#pragma unroll
+                        for (int k = 0; k < RICH_MAX_BOUNCES; ++k) rr.path[k] = path[k];
+                        P.refine[slot] = rr;
                     }
                 }
+                // refined hits are binned by the refinement pass; the rest here
+                binned_here = !(REFINE && stored);
+                if (binned_here) bin_hit(sc, P, ph.event, hplane, ix, iy);
             }
         }
+        add_event_sums(sc, P, binned_here, ph.event, hplane, hu, hv, ph.lam);
         if (fate != 0) {
             if (P.fate) P.fate[ph.g] = (uint8_t)fate;
             atomicAdd(&s_fate[fate], 1ull);
@@ -934,6 +1061,79 @@ k_trace(TraceArgs A) {
     __syncthreads();
     if (threadIdx.x < 8 && s_fate[threadIdx.x])
         atomicAdd(&A.ctr->fate[threadIdx.x], s_fate[threadIdx.x]);
+    if (n_snodes_req > 0 && n_snodes == 0) {
+        // the copy had not completed: give it a second bounded wait so the
+        // block does not retire with a transfer into its shared memory
+        uint32_t done = 0;
+        for (int it = 0; it < (1 << 20) && !done; ++it) {
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(done)
+                : "r"(bar)
+                : "memory");
+        }
+    }
+}
+
+// FP64 refinement pass: one thread per stored hit (converged warps).
+template <bool EXT>
+__global__ void __launch_bounds__(256)
+k_refine(SceneView sc, EmitView em, ExtView ext, TraceParams P, Counters *ctr) {
+    const uint64_t n_hits = ctr->hits < P.hit_capacity ? ctr->hits : P.hit_capacity;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t start = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // uniform trip count so every lane takes part in the warp collectives
+    const uint64_t trips = (n_hits + stride - 1) / stride;
+    for (uint64_t it = 0; it < trips; ++it) {
+        const uint64_t i = start + it * stride;
+        const bool on = i < n_hits;
+        double u = 0.0, v = 0.0;
+        int plane = 0;
+        uint32_t event = 0;
+        float lam = 0.0f;
+        if (on) {
+            rich_hit h = P.hits[i];
+            const RefineRec rr = P.refine[i];
+            d3 o, d;
+            if (EXT) {
+                const uint32_t g = rr.index;
+                o = mkd(ext.x[g], ext.y[g], ext.z[g]);
+                d = normalized(mkd(ext.dx[g], ext.dy[g], ext.dz[g]));
+            } else {
+                emit64(em.tracks[rr.index], em.cos_sin[rr.index], h.photon, em, o, d);
+            }
+            replay64(sc, o, d, rr, u, v);
+            int ix, iy;
+            pixel_of(sc.rects[rr.det_rect], u, v, ix, iy);
+            h.u = u;
+            h.v = v;
+            h.ix = (uint16_t)ix;
+            h.iy = (uint16_t)iy;
+            P.hits[i] = h;
+            plane = h.plane;
+            event = h.event;
+            lam = h.lambda;
+            bin_hit(sc, P, event, plane, ix, iy);
+        }
+        add_event_sums(sc, P, on, event, plane, u, v, lam);
+    }
+}
+
+cudaError_t launch_refine(const SceneView &sc, const EmitView *em, const ExtView *ext,
+                          const TraceParams &p, Counters *counters, int n_sm,
+                          cudaStream_t s) {
+    if (p.hit_capacity == 0) return cudaSuccess;
+    uint64_t blocks = (p.hit_capacity + 255) / 256;
+    const uint64_t cap = (uint64_t)n_sm * 8;
+    if (blocks > cap) blocks = cap;
+    if (ext)
+        k_refine<true><<<(unsigned)blocks, 256, 0, s>>>(sc, em ? *em : EmitView{}, *ext, p,
+                                                       counters);
+    else
+        k_refine<false><<<(unsigned)blocks, 256, 0, s>>>(sc, *em, ExtView{}, p, counters);
+    return cudaGetLastError();
 }
 
 // Philox outputs for caller-given counters (reproduction of draws).
@@ -964,9 +1164,12 @@ cudaError_t launch_yield(const TracksView &t, double n_minus_1,
                          cudaStream_t s) {
     if (t.n <= 0) return cudaSuccess;
     const double inv_band_mm = 1.0e6 / lam_min - 1.0e6 / lam_max;
-    const unsigned blocks = (unsigned)((t.n + kYieldThreads - 1) / kYieldThreads);
-    k_yield<<<blocks, kYieldThreads, 0, s>>>(t, n_minus_1, inv_band_mm, key0, key1,
-                                             rec, cs, counts, block_sums);
+    const int64_t groups = (t.n + kYieldThreads - 1) / kYieldThreads;
+    cudaError_t e = cudaMemsetAsync(block_sums, 0, sizeof(unsigned long long) * groups, s);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)((t.n + kYieldBlock - 1) / kYieldBlock);
+    k_yield<<<blocks, kYieldBlock, 0, s>>>(t, n_minus_1, inv_band_mm, key0, key1,
+                                           rec, cs, counts, block_sums);
     return cudaGetLastError();
 }
 
@@ -990,17 +1193,18 @@ cudaError_t launch_materialize(const SceneView &, const EmitView &em,
     return cudaGetLastError();
 }
 
-size_t trace_smem_bytes(const SceneView &sc) {
+size_t trace_smem_bytes(const SceneView &sc, int smem_nodes) {
     auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
-    return r16(sizeof(DevSphereGroup) * sc.n_groups) + r16(sizeof(DevTile) * sc.n_tiles) +
+    const size_t nodes = ((size_t)smem_nodes * sizeof(DevNode) + 127) & ~size_t(127);
+    return nodes + r16(sizeof(DevSphereGroup) * sc.n_groups) + r16(sizeof(DevTile) * sc.n_tiles) +
            r16(sizeof(DevRect) * sc.n_rects) + r16(sizeof(DevTable) * sc.n_tables) +
            r16(sizeof(DevMaterial) * sc.n_materials);
 }
 
-template <bool EXT, bool REFINE>
+template <bool EXT, bool REFINE, int THREADS, int MINB>
 static cudaError_t launch_trace_t(const TraceArgs &a, const LaunchShape &shape,
                                   cudaStream_t s) {
-    auto kern = k_trace<EXT, REFINE>;
+    auto kern = k_trace<EXT, REFINE, THREADS, MINB>;
     if (shape.smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(
             kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shape.smem);
@@ -1010,14 +1214,46 @@ static cudaError_t launch_trace_t(const TraceArgs &a, const LaunchShape &shape,
     return cudaGetLastError();
 }
 
-int trace_blocks_per_sm(bool ext, bool refine, int threads, size_t smem) {
+// Kernel variants: caller photons or fused emission; FP64 refinement side
+// records or not; block shape class: up to 256 threads capped at 64
+// registers (4 blocks per SM), up to 256 threads uncapped, or up to 1024
+// threads (one block per SM sharing one staged copy of the BVH top).
+enum { kShape256x4 = 0, kShape256x1 = 1, kShape1024 = 2 };
+
+template <bool EXT, bool REFINE>
+static const void *trace_kernel_t(int cls) {
+    if (cls == kShape1024) return (const void *)k_trace<EXT, REFINE, 1024, 1>;
+    if (cls == kShape256x1) return (const void *)k_trace<EXT, REFINE, 256, 1>;
+    return (const void *)k_trace<EXT, REFINE, 256, 4>;
+}
+
+static const void *trace_kernel(bool ext, bool refine, int cls) {
+    if (ext) return refine ? trace_kernel_t<true, true>(cls) : trace_kernel_t<true, false>(cls);
+    return refine ? trace_kernel_t<false, true>(cls) : trace_kernel_t<false, false>(cls);
+}
+
+int trace_shape_class(int threads, bool wide) {
+    if (threads > 256) return kShape1024;
+    return wide ? kShape256x1 : kShape256x4;
+}
+
+int trace_blocks_per_sm(bool ext, bool refine, int cls, int threads, size_t smem) {
     int n = 0;
-    const void *f = ext ? (refine ? (const void *)k_trace<true, true> : (const void *)k_trace<true, false>)
-                        : (refine ? (const void *)k_trace<false, true> : (const void *)k_trace<false, false>);
+    const void *f = trace_kernel(ext, refine, cls);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem) != cudaSuccess) return 1;
-    return n > 0 ? n : 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+template <bool EXT, bool REFINE>
+static cudaError_t launch_cls(const TraceArgs &a, const LaunchShape &shape, cudaStream_t s) {
+    if (shape.cls == kShape1024) return launch_trace_t<EXT, REFINE, 1024, 1>(a, shape, s);
+    if (shape.cls == kShape256x1) return launch_trace_t<EXT, REFINE, 256, 1>(a, shape, s);
+    return launch_trace_t<EXT, REFINE, 256, 4>(a, shape, s);
 }
 
 cudaError_t launch_trace(const SceneView &sc, const EmitView *em,
@@ -1031,12 +1267,8 @@ cudaError_t launch_trace(const SceneView &sc, const EmitView *em,
     a.p = p;
     a.ctr = counters;
     const bool refine = p.precision == RICH_PREC_REFINE64;
-    if (ext) {
-        return refine ? launch_trace_t<true, true>(a, shape, s)
-                      : launch_trace_t<true, false>(a, shape, s);
-    }
-    return refine ? launch_trace_t<false, true>(a, shape, s)
-                  : launch_trace_t<false, false>(a, shape, s);
+    if (ext) return refine ? launch_cls<true, true>(a, shape, s) : launch_cls<true, false>(a, shape, s);
+    return refine ? launch_cls<false, true>(a, shape, s) : launch_cls<false, false>(a, shape, s);
 }
 
 }  // namespace rich

@@ -79,7 +79,8 @@ class TraceOpts(C.Structure):
                 ("max_bounces", C.c_int32), ("max_steps", C.c_int32),
                 ("t_min", C.c_float), ("block_threads", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("refill_min", C.c_int32),
-                ("chunk", C.c_int32), ("reserved", C.c_int32)]
+                ("chunk", C.c_int32), ("wide_regs", C.c_int32),
+                ("bvh_smem_nodes", C.c_int32)]
 
 
 class Outputs(C.Structure):
@@ -320,10 +321,12 @@ class Context:
 
     def trace(self, outputs: TraceOutputs, photons: PhotonBuffers | None = None,
               precision=PREC_REFINE64, max_bounces=8, max_steps=16, t_min=1e-3,
-              seed=0, block_threads=0, blocks_per_sm=0, refill_min=0, chunk=0):
+              seed=0, block_threads=0, blocks_per_sm=0, refill_min=0, chunk=0,
+              wide_regs=0, bvh_smem_nodes=-1):
         o = TraceOpts(seed=int(seed), precision=precision, max_bounces=max_bounces,
                       max_steps=max_steps, t_min=t_min, block_threads=block_threads,
-                      blocks_per_sm=blocks_per_sm, refill_min=refill_min, chunk=chunk)
+                      blocks_per_sm=blocks_per_sm, refill_min=refill_min, chunk=chunk,
+                      wide_regs=wide_regs, bvh_smem_nodes=bvh_smem_nodes)
         pd = photons.desc() if photons is not None else None
         st = load().rich_trace(self.handle, None if pd is None else C.byref(pd),
                                C.byref(o), C.byref(outputs.desc()))

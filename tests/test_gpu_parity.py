@@ -94,13 +94,13 @@ def test_point_source_parity(precision):
     ref = P.run_oracle(wl)
     gpu = P.run_gpu(wl, precision)
     tol = P.TOL_UV_REFINE if precision == rich.PREC_REFINE64 else P.TOL_UV_FP32["point_source"]
-    st = P.compare(gpu, ref, wl.tracks, tol)
+    st = P.compare(gpu, ref, wl.tracks, tol, name=f"point_source_prec{precision}")
     # closed form: every hit at (R/2) tan(theta) from the plane's axis point
     h = gpu["hits"]
     r = np.hypot(h["u"] - 368.64, h["v"] - 368.64)
     n = 1 + float(np.float32(0.0014))
     st["max_ring_err_mm"] = float(np.abs(r - 1355.0 * math.sqrt(n * n - 1)).max())
-    report(f"point_source_prec{precision}", st)
+    report(f"point_source_prec{precision}_ring", {"max_ring_err_mm": st["max_ring_err_mm"]})
     assert st["max_ring_err_mm"] < tol + 1e-6
     es = gpu["event_sums"][0, 0]
     assert es[0] == gpu["n_hits"]
@@ -117,8 +117,7 @@ def test_rich1_parity_full(meshed, precision):
     ref = P.run_oracle(wl)
     gpu = P.run_gpu(wl, precision)
     tol = P.TOL_UV_REFINE if precision == rich.PREC_REFINE64 else P.TOL_UV_FP32["rich1"]
-    st = P.compare(gpu, ref, wl.tracks, tol)
-    report(f"rich1_meshed{int(meshed)}_prec{precision}", st)
+    st = P.compare(gpu, ref, wl.tracks, tol, name=f"rich1_meshed{int(meshed)}_prec{precision}")
     sums_g, sums_o = gpu["event_sums"], ref["event_sums"]
     np.testing.assert_allclose(sums_g[..., 0], sums_o[..., 0], atol=st["fate_mismatch"])
 
@@ -129,8 +128,7 @@ def test_rich2_parity_subset():
     wl = W.rich2(300)
     ref = P.run_oracle(wl)
     gpu = P.run_gpu(wl, rich.PREC_REFINE64)
-    st = P.compare(gpu, ref, wl.tracks, P.TOL_UV_REFINE)
-    report("rich2_meshed_300", st)
+    P.compare(gpu, ref, wl.tracks, P.TOL_UV_REFINE, name="rich2_meshed_300")
 
 
 def test_batched_events_sampled():
@@ -158,8 +156,7 @@ def test_batched_events_sampled():
         else:
             for k in ("fate", "plane", "ix", "iy", "u", "v", "lambda", "graze", "n_refl"):
                 merged[k][int(off[a]):int(off[b])] = r[k][int(off[a]):int(off[b])]
-    st = P.compare(gpu, merged, wl.tracks, P.TOL_UV_REFINE, sel=sel)
-    report("batched_256_sampled", st)
+    st = P.compare(gpu, merged, wl.tracks, P.TOL_UV_REFINE, sel=sel, name="batched_256_sampled")
     if st["fate_mismatch"] == 0:
         np.testing.assert_array_equal(gpu["pixel_counts"][events], ref_pc[events])
 
@@ -168,9 +165,10 @@ def test_batched_events_sampled():
 def test_external_photons_match_fused():
     """Photons materialised by rich_emit and traced as caller photons (the
     photon-vector input of Sec. 4.2) give bit-identical fates and FP32 hits
-    to the fused emission; refined hits agree within the tolerance (the
-    fused replay re-emits in FP64, the caller photons start from their FP32
-    values)."""
+    to the fused emission. Refined hits of caller photons are exact for
+    their FP32 inputs, whose direction rounding (~6e-8 rad) over the ~3 m
+    lever arm of the optics moves a hit by up to ~2e-4 mm from the fused
+    path's FP64 emission: bound 5e-4 mm."""
     wl = W.rich1(300)
     ctx = rich.Context(0)
     ctx.init_geometry(wl.scene)
@@ -189,8 +187,8 @@ def test_external_photons_match_fused():
         else:
             for k in ("event", "track", "photon", "plane", "lambda", "n_reflections"):
                 np.testing.assert_array_equal(a[k], b[k])
-            assert np.abs(a["u"] - b["u"]).max() < 1e-4
-            assert np.abs(a["v"] - b["v"]).max() < 1e-4
+            assert np.abs(a["u"] - b["u"]).max() < 5e-4
+            assert np.abs(a["v"] - b["v"]).max() < 5e-4
     ctx.close()
 
 
