@@ -356,6 +356,32 @@ RICH_API rich_status rich_hits(rich_ctx *ctx, uint64_t *n_hits, rich_stats *stat
 RICH_API rich_status rich_philox(rich_ctx *ctx, const uint32_t *counters,
                                  uint64_t n, uint64_t seed, uint32_t *out);
 
+/* Per-track photon counts and photon offsets without any device allocation,
+ * for callers that cannot allocate device memory: code running under a
+ * framework whose own pool allocator owns all of the GPU's memory, or a hook
+ * inside a simulation step that must not make the synchronising cudaMalloc /
+ * cudaFree calls. (The paper has no counterpart: it is a service of this
+ * library.) It computes what rich_emit computes for the trace -- beta, the
+ * Cherenkov angle, the Frank-Tamm mean and the keyed Poisson count of every
+ * track -- without a context.
+ * tracks: DEVICE arrays as for rich_emit, at most 1,048,576 tracks
+ *   (RICH_ERR_ARG beyond, nothing launched). params: as for rich_emit.
+ * counts: DEVICE, n entries, receives each track's photon count.
+ * offsets: DEVICE, n + 1 entries, receives the exclusive prefix sums of the
+ *   counts; offsets[n] is the total.
+ * stream: cudaStream_t (NULL: legacy default stream); runs on the current
+ *   device; asynchronous.
+ * Its only scratch is a 32 KiB array in the library's device memory, present
+ * on every GPU that loads the library until the process exits. The first
+ * call on a device looks up that array's address (make it before any stream
+ * capture). All calls share the array: calls whose work overlaps on the GPU
+ * (e.g. issued on two streams at once) race and give wrong results. Errors
+ * are reported by rich_last_error(NULL). Calls no allocating routine. */
+RICH_API rich_status rich_photon_counts_static(const rich_tracks *tracks,
+                                               const rich_emit_params *params,
+                                               uint32_t *counts, uint64_t *offsets,
+                                               void *stream);
+
 /* Message for the last failure on ctx (or of rich_create when ctx is NULL).
  * The string is owned by the library and valid until the next call. */
 RICH_API const char *rich_last_error(rich_ctx *ctx);

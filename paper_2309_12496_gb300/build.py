@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librich.so")
 
-SOURCES = ["rich_kernels.cu", "rich_capi.cu", "rich_bvh.cpp"]
+SOURCES = ["rich_kernels.cu", "rich_capi.cu", "rich_static.cu", "rich_bvh.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

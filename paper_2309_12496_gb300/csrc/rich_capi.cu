@@ -58,6 +58,10 @@ struct rich_ctx {
 
 static thread_local std::string g_create_error;
 
+namespace rich {
+void set_global_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace rich
+
 namespace {
 
 struct DeviceGuard {

@@ -91,6 +91,7 @@ __device__ int64_t poisson_draw(double mu, TrackStream &s) {
     return (int64_t)floor(mu + 0.5);
 }
 
+template <bool RECS>
 __global__ void __launch_bounds__(kYieldBlock)
 k_yield(TracksView t, double n_minus_1, double inv_band_mm, uint32_t key0,
         uint32_t key1, TrackRec *rec, double2 *cs, uint32_t *counts,
@@ -122,6 +123,7 @@ k_yield(TracksView t, double n_minus_1, double inv_band_mm, uint32_t key0,
             int64_t k = poisson_draw(mu, s);
             count = (uint32_t)(k > 0xFFFFFFF0ll ? 0xFFFFFFF0ll : k);
         }
+        if (RECS) {
         double dx = t.dx[i], dy = t.dy[i], dz = t.dz[i];
         double inv = 1.0 / sqrt(dx * dx + dy * dy + dz * dz);
         TrackRec r;
@@ -142,6 +144,7 @@ k_yield(TracksView t, double n_minus_1, double inv_band_mm, uint32_t key0,
         r.pad0 = r.pad1 = 0;
         rec[i] = r;
         cs[i] = make_double2(cos_t, sin_t);
+        }
         counts[i] = count;
     }
     // sum of the counts of this block, added to its 256-track scan group
@@ -197,7 +200,7 @@ k_offsets(const uint32_t *counts, const unsigned long long *block_sums,
     if (i < n) offsets[i] = excl;
     if (i == n - 1) {
         offsets[n] = excl + c;
-        *total = excl + c;
+        if (total) *total = excl + c;
     }
 }
 
@@ -1168,8 +1171,12 @@ cudaError_t launch_yield(const TracksView &t, double n_minus_1,
     cudaError_t e = cudaMemsetAsync(block_sums, 0, sizeof(unsigned long long) * groups, s);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((t.n + kYieldBlock - 1) / kYieldBlock);
-    k_yield<<<blocks, kYieldBlock, 0, s>>>(t, n_minus_1, inv_band_mm, key0, key1,
-                                           rec, cs, counts, block_sums);
+    if (rec)
+        k_yield<true><<<blocks, kYieldBlock, 0, s>>>(t, n_minus_1, inv_band_mm, key0, key1,
+                                                     rec, cs, counts, block_sums);
+    else
+        k_yield<false><<<blocks, kYieldBlock, 0, s>>>(t, n_minus_1, inv_band_mm, key0, key1,
+                                                      rec, cs, counts, block_sums);
     return cudaGetLastError();
 }
 

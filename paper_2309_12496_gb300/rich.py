@@ -29,7 +29,7 @@ FATE_DETECTED = 5
 
 EXPORTED = ["rich_create", "rich_destroy", "rich_set_stream", "rich_init_geometry",
             "rich_emit", "rich_trace", "rich_hits", "rich_philox", "rich_last_error",
-            "rich_version"]
+            "rich_version", "rich_photon_counts_static"]
 
 # rich_hit, 40 bytes
 HIT_DTYPE = np.dtype([("event", "<u4"), ("track", "<u4"), ("photon", "<u4"),
@@ -124,11 +124,14 @@ def load():
                                  C.POINTER(Outputs)]
         L.rich_hits.argtypes = [vp, C.POINTER(C.c_uint64), C.POINTER(Stats)]
         L.rich_philox.argtypes = [vp, vp, C.c_uint64, C.c_uint64, vp]
+        L.rich_photon_counts_static.argtypes = [C.POINTER(TracksDesc), C.POINTER(EmitParams),
+                                                vp, vp, vp]
         L.rich_last_error.argtypes = [vp]
         L.rich_last_error.restype = C.c_char_p
         L.rich_version.restype = C.c_char_p
         for f in ("rich_create", "rich_destroy", "rich_set_stream", "rich_init_geometry",
-                  "rich_emit", "rich_trace", "rich_hits", "rich_philox"):
+                  "rich_emit", "rich_trace", "rich_hits", "rich_philox",
+                  "rich_photon_counts_static"):
             getattr(L, f).restype = C.c_int
         _lib = L
         return L
@@ -379,6 +382,24 @@ def rich_trace(ctx: Context, outputs, **kw):
 
 def rich_hits(ctx: Context, **kw):
     return ctx.hits(**kw)
+
+
+def rich_photon_counts_static(tracks: DeviceTracks, n_minus_1, counts, offsets,
+                              lambda_min=200.0, lambda_max=600.0, seed=0, stream=None,
+                              n=None):
+    """Per-track photon counts (int32 view of u32) and offsets (int64 view of
+    u64, n + 1 entries) into caller device tensors, with no device
+    allocation by the library. `n` overrides the track count passed."""
+    L = load()
+    d = tracks.desc()
+    if n is not None:
+        d.n = int(n)
+    prm = EmitParams(seed=int(seed), n_minus_1=float(n_minus_1),
+                     lambda_min=float(lambda_min), lambda_max=float(lambda_max))
+    s = current_stream_handle() if stream is None else stream
+    st = L.rich_photon_counts_static(C.byref(d), C.byref(prm), C.c_void_p(counts.data_ptr()),
+                                     C.c_void_p(offsets.data_ptr()), C.c_void_p(s))
+    _check(None, st)
 
 
 def rich_version() -> str:
