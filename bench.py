@@ -39,10 +39,13 @@ UNIT = "photons/s"
 N_TRACKS = 1000
 WORKLOAD = "rich1_meshed_1000_pion_tracks"
 
-# FP32 operations per propagated photon of the trace kernel on this workload
-# (2 x FFMA + FADD + FMUL thread instructions per photon, from the ncu
-# instruction counters of one k_trace launch; see profiles/).
-FLOPS_PER_PHOTON = None
+# FP32 operations per propagated photon of the trace kernel on this workload:
+# 2 x FFMA + FADD + FMUL thread instructions of one k_trace launch from the
+# ncu counters (smsp__sass_thread_inst_executed_op_{ffma,fadd,fmul}_pred_on)
+# divided by its 350,350 photons: (2 x 360.71 M + 53.05 M + 93.71 M) / 350,350.
+FLOPS_PER_PHOTON = 2481.0
+# dram__bytes_read.sum + dram__bytes_write.sum of the same k_trace launch.
+TRACE_DRAM_BYTES = 10834944 + 315392
 FP32_LANES_PER_SM = 128
 SM_COUNT_NOMINAL = 152
 
@@ -267,7 +270,8 @@ def main():
         if FLOPS_PER_PHOTON:
             achieved = FLOPS_PER_PHOTON * ph_step / t_trace / 1e12
             roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
-                    "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                    "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                    "traffic": TRACE_DRAM_BYTES,
                     "kernel": "k_trace", "flops_per_photon": FLOPS_PER_PHOTON,
                     "peak_source": f"FP32 2 x {FP32_LANES_PER_SM} lanes x {n_sm} SMs x {sm_max:.0f} MHz"}
         else:
