@@ -111,6 +111,13 @@ def _declare(L):
     L.oracle_trace.argtypes = [vp, vp, vp, vp, i64, i64, vp]
     L.oracle_trace.restype = C.c_int
     L.oracle_max_threads.restype = C.c_int
+    L.oracle_trace_grad.argtypes = [vp, vp, vp, vp, vp, C.c_int, C.c_double, C.c_double,
+                                    C.c_double, vp, vp, vp]
+    L.oracle_trace_grad.restype = i64
+    L.oracle_trace_at.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.oracle_trace_at.restype = C.c_int
+    L.oracle_hit_jacobian.argtypes = [vp, vp, vp, vp, i64, u32, vp, vp, vp, vp]
+    L.oracle_hit_jacobian.restype = C.c_int
 
 
 def _ptr(a):
@@ -233,6 +240,60 @@ class Scene:
         lib().oracle_raycast(self.handle, len(o), _ptr(o), _ptr(d), _ptr(sk),
                              t_min, int(use_bvh), _ptr(t), _ptr(prim))
         return t, prim
+
+    def grad(self, tracks, prm, theta, targets, sigma=1.0, fd=False, h_angle=1e-6,
+             h_rel=1e-6):
+        """Soft ring chi^2 loss at theta (10 parameters: 8 tile tilts, the
+        radius of curvature, n - 1), its dual-number gradient and, with fd,
+        its central-difference gradient. targets: float32 [n_tracks][n_planes][4]
+        = (cu, cv, r, weight). Returns (loss, grad, grad_fd or None, n_used)."""
+        h = _TracksHold(tracks)
+        th = np.ascontiguousarray(theta, np.float64).reshape(10)
+        tg = np.ascontiguousarray(targets, np.float32)
+        g = np.zeros(10)
+        gfd = np.zeros(10) if fd else None
+        loss = np.zeros(1)
+        used = lib().oracle_trace_grad(self.handle, C.byref(h.rec), C.byref(prm), _ptr(th),
+                                       _ptr(tg), self.n_planes, sigma, h_angle, h_rel,
+                                       _ptr(loss), _ptr(g), _ptr(gfd))
+        if used < 0:
+            raise ValueError("oracle_trace_grad rejected its parameters")
+        return float(loss[0]), g, gfd, int(used)
+
+    def hit_jacobian(self, tracks, prm, theta, track, photon):
+        """(fate, u, v, du/dtheta[10], dv/dtheta[10]) of one photon at theta."""
+        h = _TracksHold(tracks)
+        th = np.ascontiguousarray(theta, np.float64).reshape(10)
+        u, v = np.zeros(1), np.zeros(1)
+        du, dv = np.zeros(10), np.zeros(10)
+        fate = lib().oracle_hit_jacobian(self.handle, C.byref(h.rec), C.byref(prm), _ptr(th),
+                                         int(track), int(photon), _ptr(u), _ptr(v), _ptr(du),
+                                         _ptr(dv))
+        return int(fate), float(u[0]), float(v[0]), du, dv
+
+    def trace_at(self, tracks, prm, theta, n_hist_events=None):
+        """Per-photon results of the forward trace at theta."""
+        th = np.ascontiguousarray(theta, np.float64).reshape(10)
+        p2 = Params(**{f: getattr(prm, f) for f, _ in Params._fields_})
+        p2.n_minus_1 = float(th[9])
+        _, _, off = track_yield(tracks, p2)
+        n = int(off[-1])
+        h = _TracksHold(tracks)
+        out = {k: np.zeros(n, dt) for k, dt in (("fate", np.uint8), ("ix", np.int32),
+                                                ("iy", np.int32), ("u", np.float64),
+                                                ("v", np.float64), ("lambda", np.float32),
+                                                ("n_refl", np.uint8), ("graze", np.uint8))}
+        out["plane"] = np.full(n, -1, np.int32)
+        rec = PhotonOut(fate=_ptr(out["fate"]), plane=_ptr(out["plane"]), ix=_ptr(out["ix"]),
+                        iy=_ptr(out["iy"]), u=_ptr(out["u"]), v=_ptr(out["v"]),
+                        lambda_=_ptr(out["lambda"]), n_refl=_ptr(out["n_refl"]),
+                        graze=_ptr(out["graze"]), n_hist_events=0)
+        rc = lib().oracle_trace_at(self.handle, C.byref(h.rec), C.byref(p2), _ptr(th),
+                                   _ptr(np.ascontiguousarray(off, np.uint64)), C.byref(rec))
+        if rc != 0:
+            raise ValueError("oracle_trace_at rejected its parameters")
+        out["offsets"] = off
+        return out
 
     def trace(self, tracks, prm, offsets=None, track_range=None,
               n_hist_events=None, want_path=False, want_final=False,

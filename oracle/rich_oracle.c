@@ -1093,3 +1093,388 @@ int oracle_max_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* 7. Gradient of the soft ring chi^2 with respect to the mirror tilts, the */
+/*    radius of curvature and n - 1 (the differentiation pattern).          */
+/*                                                                          */
+/* Parameters theta[0..9]: (alpha_k, beta_k) for sphere tiles k = 0..3 --   */
+/* rotation of the tile about the axis through its pole P_k = C_k + R a_k   */
+/* parallel to its nominal e1 by alpha_k, then about the nominal e2 by      */
+/* beta_k (Rodrigues' formula); theta[8] = radius of curvature of every     */
+/* sphere tile (pole fixed: C = P - R a); theta[9] = n - 1.                 */
+/* Loss over the detected photons whose (track, plane) target has weight    */
+/* > 0: the hit (u, v) is smeared by sigma (g1, g2), a Box-Muller pair from */
+/* the photon's draw block 3, rho = (|(u~, v~) - (cu, cv)| - r) / sigma and */
+/* L = mean rho^2. Derivatives follow the photon's recorded sequence of     */
+/* reflecting surfaces (fixed topology: each surface extended past its     */
+/* edges), by forward-mode dual numbers with 10 tangents, and separately   */
+/* by central finite differences of the same replay.                        */
+/* ------------------------------------------------------------------------ */
+#define NG 10
+typedef struct { double v; double d[NG]; } dn;
+typedef struct { dn x, y, z; } dv;
+
+static dn dc(double v) { dn r; r.v = v; memset(r.d, 0, sizeof r.d); return r; }
+static dn dadd(dn a, dn b) { for (int k = 0; k < NG; ++k) a.d[k] += b.d[k]; a.v += b.v; return a; }
+static dn dsub(dn a, dn b) { for (int k = 0; k < NG; ++k) a.d[k] -= b.d[k]; a.v -= b.v; return a; }
+static dn dmul(dn a, dn b)
+{
+    dn r; r.v = a.v * b.v;
+    for (int k = 0; k < NG; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+    return r;
+}
+static dn dscl(dn a, double s) { for (int k = 0; k < NG; ++k) a.d[k] *= s; a.v *= s; return a; }
+static dn ddiv(dn a, dn b)
+{
+    dn r; r.v = a.v / b.v;
+    for (int k = 0; k < NG; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) / b.v;
+    return r;
+}
+static dn dsqrt(dn a)
+{
+    dn r; r.v = sqrt(a.v);
+    for (int k = 0; k < NG; ++k) r.d[k] = a.d[k] / (2.0 * r.v);
+    return r;
+}
+static dn dsin(dn a)
+{
+    dn r; r.v = sin(a.v); double c = cos(a.v);
+    for (int k = 0; k < NG; ++k) r.d[k] = c * a.d[k];
+    return r;
+}
+static dn dcos(dn a)
+{
+    dn r; r.v = cos(a.v); double s = -sin(a.v);
+    for (int k = 0; k < NG; ++k) r.d[k] = s * a.d[k];
+    return r;
+}
+static dv dvc(v3 a) { dv r = {dc(a.x), dc(a.y), dc(a.z)}; return r; }
+static dv dvadd(dv a, dv b) { dv r = {dadd(a.x, b.x), dadd(a.y, b.y), dadd(a.z, b.z)}; return r; }
+static dv dvsub(dv a, dv b) { dv r = {dsub(a.x, b.x), dsub(a.y, b.y), dsub(a.z, b.z)}; return r; }
+static dv dvscl(dv a, dn s) { dv r = {dmul(a.x, s), dmul(a.y, s), dmul(a.z, s)}; return r; }
+static dn dvdot(dv a, dv b) { return dadd(dadd(dmul(a.x, b.x), dmul(a.y, b.y)), dmul(a.z, b.z)); }
+static dn dvdotc(dv a, v3 b)
+{
+    return dadd(dadd(dscl(a.x, b.x), dscl(a.y, b.y)), dscl(a.z, b.z));
+}
+/* u x v with u a fixed vector */
+static dv dcrossc(v3 u, dv v)
+{
+    dv r = {dsub(dscl(v.z, u.y), dscl(v.y, u.z)), dsub(dscl(v.x, u.z), dscl(v.z, u.x)),
+            dsub(dscl(v.y, u.x), dscl(v.x, u.y))};
+    return r;
+}
+/* Rodrigues: v cos(phi) + (u x v) sin(phi) + u (u.v)(1 - cos(phi)), u unit */
+static dv drot(v3 u, dn phi, dv v)
+{
+    dn c = dcos(phi), s = dsin(phi);
+    dn uv = dvdotc(v, u);
+    dn k = dmul(uv, dsub(dc(1.0), c));
+    dv a = dvscl(v, c);
+    dv b = dvscl(dcrossc(u, v), s);
+    dv w = {dmul(dc(u.x), k), dmul(dc(u.y), k), dmul(dc(u.z), k)};
+    return dvadd(dvadd(a, b), w);
+}
+
+typedef struct {
+    dv c, a, e1, e2;
+    dn R;
+} o_tile_d;
+
+/* Tile k at parameters theta (duals). */
+static o_tile_d tile_at(const o_sphere *sp, int k, const dn th[NG])
+{
+    v3 P = add(sp->c, scl(sp->axis, sp->R));
+    dn al = k < 4 ? th[2 * k] : dc(0.0);
+    dn be = k < 4 ? th[2 * k + 1] : dc(0.0);
+    o_tile_d t;
+    t.a = drot(sp->e2, be, drot(sp->e1, al, dvc(sp->axis)));
+    t.e1 = drot(sp->e2, be, drot(sp->e1, al, dvc(sp->e1)));
+    t.e2 = drot(sp->e2, be, drot(sp->e1, al, dvc(sp->e2)));
+    t.R = th[8];
+    t.c = dvsub(dvc(P), dvscl(t.a, t.R));
+    return t;
+}
+
+/* Plain-double transformed copy of the scene's tiles at theta. */
+static void tiles_at_theta(const o_scene *nom, const double theta[NG], o_sphere *out)
+{
+    dn th[NG];
+    for (int k = 0; k < NG; ++k) th[k] = dc(theta[k]);
+    for (int i = 0; i < nom->n_spheres; ++i) {
+        o_tile_d t = tile_at(&nom->spheres[i], i, th);
+        out[i] = nom->spheres[i];
+        out[i].c = mk(t.c.x.v, t.c.y.v, t.c.z.v);
+        out[i].axis = mk(t.a.x.v, t.a.y.v, t.a.z.v);
+        out[i].e1 = mk(t.e1.x.v, t.e1.y.v, t.e1.z.v);
+        out[i].e2 = mk(t.e2.x.v, t.e2.y.v, t.e2.z.v);
+        out[i].R = t.R.v;
+    }
+}
+
+static dv dreflect(dv d, dv n)
+{
+    dn k = dscl(dvdot(d, n), 2.0);
+    return dvsub(d, dvscl(n, k));
+}
+
+/* Replay of one detected photon along its reflecting surfaces with duals.
+ * refl: primitive ids of the reflections in order; det: detector rectangle. */
+static void replay_dual(const o_scene *nom, const o_tracks_in *t, const o_params *prm,
+                        int64_t i, uint32_t j, const int32_t *refl, int n_refl,
+                        int det, const dn th[NG], dn *u_out, dn *v_out)
+{
+    uint32_t event = t->event[i];
+    uint32_t tid = t->id ? t->id[i] : (uint32_t)i;
+    uint32_t w0[4];
+    draw_block(prm->seed, event, tid, j, 0, w0);
+    v3 dir = unit(mk(t->dx[i], t->dy[i], t->dz[i]));
+    double s = u24(w0[0]) * (double)t->length[i];
+    dv o = dvc(add(mk(t->x[i], t->y[i], t->z[i]), scl(dir, s)));
+    double phi = 2.0 * PI_D * u24(w0[1]);
+    double beta = track_beta(t->p[i], t->mass[i]);
+    dn nb = dscl(dadd(dc(1.0), th[9]), beta);
+    dn ct = ddiv(dc(1.0), nb);
+    dn st = dsqrt(dsub(dc(1.0), dmul(ct, ct)));
+    v3 e1, e2;
+    basis(dir, &e1, &e2);
+    v3 tr = add(scl(e1, cos(phi)), scl(e2, sin(phi)));
+    dv d = dvadd(dvscl(dvc(dir), ct), dvscl(dvc(tr), st));
+    for (int k = 0; k < n_refl; ++k) {
+        int prim = refl[k];
+        dv n;
+        if (prim < nom->n_spheres) {
+            o_tile_d tl = tile_at(&nom->spheres[prim], prim, th);
+            dv w = dvsub(o, tl.c);
+            dn b = dvdot(w, d);
+            dn c = dsub(dvdot(w, w), dmul(tl.R, tl.R));
+            dn sq = dsqrt(dsub(dmul(b, b), c));
+            /* exit root (concave side) in the form free of cancellation */
+            dn tt = b.v <= 0.0 ? dsub(sq, b) : ddiv(c, dsub(dscl(b, -1.0), sq));
+            o = dvadd(o, dvscl(d, tt));
+            n = dvscl(dvsub(tl.c, o), ddiv(dc(1.0), tl.R));
+        } else if (prim < nom->n_spheres + nom->n_rects) {
+            const o_rect *rc = &nom->rects[prim - nom->n_spheres];
+            n = dvc(rc->n);
+            dn tt = ddiv(dvdotc(dvsub(dvc(rc->o), o), rc->n), dvdotc(d, rc->n));
+            o = dvadd(o, dvscl(d, tt));
+        } else {
+            const o_tri *tri = &nom->tris[prim - nom->n_spheres - nom->n_rects];
+            dn tt = ddiv(dvdotc(dvsub(dvc(tri->v0), o), tri->ng), dvdotc(d, tri->ng));
+            o = dvadd(o, dvscl(d, tt));
+            const o_material_in *m = &nom->materials[tri->material];
+            if (m->flags & MAT_SMOOTH) {
+                v3 ea = sub(tri->v1, tri->v0), eb = sub(tri->v2, tri->v0);
+                dv q = dvsub(o, dvc(tri->v0));
+                double d00 = dot(ea, ea), d01 = dot(ea, eb), d11 = dot(eb, eb);
+                dn d20 = dvdotc(q, ea), d21 = dvdotc(q, eb);
+                double den = d00 * d11 - d01 * d01;
+                dn b1 = dscl(dsub(dscl(d20, d11), dscl(d21, d01)), 1.0 / den);
+                dn b2 = dscl(dsub(dscl(d21, d00), dscl(d20, d01)), 1.0 / den);
+                dn b0 = dsub(dsub(dc(1.0), b1), b2);
+                dv nn = dvadd(dvadd(dvscl(dvc(tri->n0), b0), dvscl(dvc(tri->n1), b1)),
+                              dvscl(dvc(tri->n2), b2));
+                n = dvscl(nn, ddiv(dc(1.0), dsqrt(dvdot(nn, nn))));
+            } else {
+                n = dvc(tri->ng);
+            }
+        }
+        d = dreflect(d, n);
+        /* keep |d| = 1 exactly as the forward trace renormalises */
+        d = dvscl(d, ddiv(dc(1.0), dsqrt(dvdot(d, d))));
+    }
+    const o_rect *rc = &nom->rects[det];
+    dn tt = ddiv(dvdotc(dvsub(dvc(rc->o), o), rc->n), dvdotc(d, rc->n));
+    dv q = dvsub(dvadd(o, dvscl(d, tt)), dvc(rc->o));
+    *u_out = dvdotc(q, rc->u);
+    *v_out = dvdotc(q, rc->v);
+}
+
+/* Box-Muller pair from draw block 3 (words 0 and 1). */
+static void smear_pair(uint64_t seed, uint32_t event, uint32_t tid, uint32_t j,
+                       double *g1, double *g2)
+{
+    uint32_t w[4];
+    draw_block(seed, event, tid, j, 3, w);
+    double u1 = ((double)(w[0] >> 8) + 0.5) * (1.0 / 16777216.0);
+    double u2 = u24(w[1]);
+    double r = sqrt(-2.0 * log(u1));
+    *g1 = r * cos(2.0 * PI_D * u2);
+    *g2 = r * sin(2.0 * PI_D * u2);
+}
+
+/* rho = (|h~ - c| - r) / sigma with dual hit coordinates */
+static dn ring_residual(dn u, dn v, double g1, double g2, const float *tg, double sigma)
+{
+    dn du = dadd(u, dc(sigma * g1 - tg[0]));
+    dn dvv = dadd(v, dc(sigma * g2 - tg[1]));
+    dn dist = dsqrt(dadd(dmul(du, du), dmul(dvv, dvv)));
+    return dscl(dsub(dist, dc(tg[2])), 1.0 / sigma);
+}
+
+/* Loss, gradient (dual numbers) and central-difference gradient at theta.
+ * targets: [n_tracks][n_planes][4] = (cu, cv, r, weight); hits of a
+ * (track, plane) with weight <= 0 are not used. h_angle: step of the tilt
+ * differences (rad); h_rel: relative step for R and n - 1. grad_fd may be
+ * NULL (no differences). Returns the number of hits used, or -1. */
+int64_t oracle_trace_grad(void *scene, const o_tracks_in *t, const o_params *prm_in,
+                          const double theta[NG], const float *targets, int n_planes,
+                          double sigma, double h_angle, double h_rel, double *loss,
+                          double *grad, double *grad_fd)
+{
+    const o_scene *nom = (const o_scene *)scene;
+    if (prm_in->max_steps > 16 || prm_in->max_bounces > 8) return -1;
+    o_params prm = *prm_in;
+    prm.n_minus_1 = theta[9];
+    /* the scene at theta (forward trace decides the topology) */
+    o_scene at = *nom;
+    at.spheres = (o_sphere *)calloc((size_t)nom->n_spheres + 1, sizeof(o_sphere));
+    tiles_at_theta(nom, theta, at.spheres);
+    uint64_t *off = (uint64_t *)malloc(sizeof(uint64_t) * ((size_t)t->n + 1));
+    oracle_yield(t, &prm, NULL, NULL, off);
+    int64_t total = (int64_t)off[t->n];
+    double hk[NG];
+    for (int k = 0; k < NG; ++k) hk[k] = k < 8 ? h_angle : h_rel * fabs(theta[k]);
+    double acc_l = 0.0, acc_g[NG] = {0}, acc_fd[NG] = {0};
+    int64_t used = 0;
+#ifdef _OPENMP
+    if (prm.n_threads > 0) omp_set_num_threads(prm.n_threads);
+#pragma omp parallel
+#endif
+    {
+        double l_l = 0.0, l_g[NG] = {0}, l_fd[NG] = {0};
+        int64_t l_used = 0;
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 256)
+#endif
+        for (int64_t g = 0; g < total; ++g) {
+            int64_t lo = 0, hi = t->n - 1;
+            while (lo < hi) {
+                int64_t mid = (lo + hi + 1) / 2;
+                if ((int64_t)off[mid] <= g) lo = mid; else hi = mid - 1;
+            }
+            uint32_t j = (uint32_t)(g - (int64_t)off[lo]);
+            o_photon ph;
+            emit_photon(t, &prm, lo, j, &ph);
+            int32_t path[16];
+            o_result r;
+            trace_photon(&at, &prm, &ph, &r, path);
+            if (r.fate != FATE_DETECTED) continue;
+            const float *tg = targets + ((size_t)lo * n_planes + r.plane) * 4;
+            if (!(tg[3] > 0.0f)) continue;
+            int32_t refl[16];
+            int nr = 0, det = -1;
+            for (int s = 0; s < prm.max_steps && path[s] >= 0; ++s) {
+                int prim = path[s];
+                int mat;
+                if (prim < at.n_spheres) mat = at.spheres[prim].material;
+                else if (prim < at.n_spheres + at.n_rects) mat = at.rects[prim - at.n_spheres].material;
+                else mat = at.tris[prim - at.n_spheres - at.n_rects].material;
+                if (at.materials[mat].kind == MAT_MIRROR) refl[nr++] = prim;
+                det = prim;
+            }
+            det -= at.n_spheres;   /* detector rectangle index */
+            double g1, g2;
+            smear_pair(prm.seed, t->event[lo], t->id ? t->id[lo] : (uint32_t)lo, j, &g1, &g2);
+            dn th[NG];
+            for (int k = 0; k < NG; ++k) { th[k] = dc(theta[k]); th[k].d[k] = 1.0; }
+            dn u, v;
+            replay_dual(nom, t, &prm, lo, j, refl, nr, det, th, &u, &v);
+            dn rho = ring_residual(u, v, g1, g2, tg, sigma);
+            l_l += rho.v * rho.v;
+            for (int k = 0; k < NG; ++k) l_g[k] += 2.0 * rho.v * rho.d[k];
+            l_used++;
+            if (grad_fd) {
+                for (int k = 0; k < NG; ++k) {
+                    dn tp[NG], tm[NG];
+                    for (int q = 0; q < NG; ++q) { tp[q] = dc(theta[q]); tm[q] = dc(theta[q]); }
+                    tp[k].v += hk[k];
+                    tm[k].v -= hk[k];
+                    dn up, vp, um, vm;
+                    replay_dual(nom, t, &prm, lo, j, refl, nr, det, tp, &up, &vp);
+                    replay_dual(nom, t, &prm, lo, j, refl, nr, det, tm, &um, &vm);
+                    double rp = ring_residual(up, vp, g1, g2, tg, sigma).v;
+                    double rm = ring_residual(um, vm, g1, g2, tg, sigma).v;
+                    l_fd[k] += (rp * rp - rm * rm) / (2.0 * hk[k]);
+                }
+            }
+        }
+#ifdef _OPENMP
+#pragma omp critical(oracle_grad)
+#endif
+        {
+            acc_l += l_l;
+            used += l_used;
+            for (int k = 0; k < NG; ++k) { acc_g[k] += l_g[k]; acc_fd[k] += l_fd[k]; }
+        }
+    }
+    double inv = used ? 1.0 / (double)used : 0.0;
+    *loss = acc_l * inv;
+    for (int k = 0; k < NG; ++k) {
+        grad[k] = acc_g[k] * inv;
+        if (grad_fd) grad_fd[k] = acc_fd[k] * inv;
+    }
+    free(off);
+    free(at.spheres);
+    return used;
+}
+
+/* Hits of the forward trace at theta (for ring targets and checks): same as
+ * oracle_trace on the transformed scene with n - 1 = theta[9]. */
+int oracle_trace_at(void *scene, const o_tracks_in *t, const o_params *prm_in,
+                    const double theta[NG], const uint64_t *offsets,
+                    const o_photon_out *out)
+{
+    const o_scene *nom = (const o_scene *)scene;
+    o_params prm = *prm_in;
+    prm.n_minus_1 = theta[9];
+    o_scene at = *nom;
+    at.spheres = (o_sphere *)calloc((size_t)nom->n_spheres + 1, sizeof(o_sphere));
+    tiles_at_theta(nom, theta, at.spheres);
+    int rc = oracle_trace(&at, t, &prm, offsets, 0, t->n, out);
+    free(at.spheres);
+    return rc;
+}
+
+/* Hit position and its derivatives d(u, v)/d(theta_k) of one photon (track
+ * i, photon j) at theta. Returns the photon's fate; u, v, du, dv are set
+ * when it is detected. */
+int oracle_hit_jacobian(void *scene, const o_tracks_in *t, const o_params *prm_in,
+                        const double theta[NG], int64_t i, uint32_t j, double *u,
+                        double *v, double *du, double *dv_)
+{
+    const o_scene *nom = (const o_scene *)scene;
+    o_params prm = *prm_in;
+    prm.n_minus_1 = theta[9];
+    o_scene at = *nom;
+    at.spheres = (o_sphere *)calloc((size_t)nom->n_spheres + 1, sizeof(o_sphere));
+    tiles_at_theta(nom, theta, at.spheres);
+    o_photon ph;
+    emit_photon(t, &prm, i, j, &ph);
+    int32_t path[16];
+    o_result r;
+    trace_photon(&at, &prm, &ph, &r, path);
+    if (r.fate == FATE_DETECTED) {
+        int32_t refl[16];
+        int nr = 0, det = -1;
+        for (int s = 0; s < prm.max_steps && path[s] >= 0; ++s) {
+            int prim = path[s];
+            int mat;
+            if (prim < at.n_spheres) mat = at.spheres[prim].material;
+            else if (prim < at.n_spheres + at.n_rects) mat = at.rects[prim - at.n_spheres].material;
+            else mat = at.tris[prim - at.n_spheres - at.n_rects].material;
+            if (at.materials[mat].kind == MAT_MIRROR) refl[nr++] = prim;
+            det = prim;
+        }
+        dn th[NG];
+        for (int k = 0; k < NG; ++k) { th[k] = dc(theta[k]); th[k].d[k] = 1.0; }
+        dn uu, vv;
+        replay_dual(nom, t, &prm, i, j, refl, nr, det - at.n_spheres, th, &uu, &vv);
+        *u = uu.v;
+        *v = vv.v;
+        for (int k = 0; k < NG; ++k) { du[k] = uu.d[k]; dv_[k] = vv.d[k]; }
+    }
+    free(at.spheres);
+    return r.fate;
+}

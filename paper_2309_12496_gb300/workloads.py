@@ -669,3 +669,52 @@ def rich2(n_tracks=330_000, seed=0, meshed=True) -> Workload:
                     description=f"{n_tracks} pion tracks, 2000 mm CF4 "
                     "(n=1.0005), 56 hex tiles R=8600 mm + flats + support, "
                     "2 x 512^2 planes")
+
+
+# ------------------------------------------------------------- ring targets
+def ring_targets(n_tracks, n_planes, track_index, plane, u, v, min_hits=10):
+    """Expected ring of every (track, plane) from a set of hits: centre =
+    mean hit position, radius = mean distance to it; weight 1 when at least
+    min_hits hits define it, else 0. Returns float32 [n_tracks][n_planes][4]
+    = (cu, cv, r, weight), the targets of the soft ring chi^2."""
+    out = np.zeros((n_tracks, n_planes, 4), np.float64)
+    key = np.asarray(track_index, np.int64) * n_planes + np.asarray(plane, np.int64)
+    u = np.asarray(u, np.float64)
+    v = np.asarray(v, np.float64)
+    cnt = np.bincount(key, minlength=n_tracks * n_planes).astype(np.float64)
+    su = np.bincount(key, u, minlength=n_tracks * n_planes)
+    sv = np.bincount(key, v, minlength=n_tracks * n_planes)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        cu = su / cnt
+        cv = sv / cnt
+    dist = np.hypot(u - cu[key], v - cv[key])
+    sr = np.bincount(key, dist, minlength=n_tracks * n_planes)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        r = sr / cnt
+    ok = cnt >= min_hits
+    flat = out.reshape(-1, 4)
+    flat[ok, 0] = cu[ok]
+    flat[ok, 1] = cv[ok]
+    flat[ok, 2] = r[ok]
+    flat[ok, 3] = 1.0
+    return out.astype(np.float32)
+
+
+def adjoint_workload(n_tracks=200, photons_per_track=5000, seed=0) -> Workload:
+    """The gradient configuration: the RICH1-like geometry with analytic
+    tiles and flat mirrors, n_tracks pion tracks with a fixed photon count
+    each (1e6 photons by default)."""
+    return Workload("adjoint", rich1_scene(meshed=False),
+                    pion_tracks(n_tracks, seed=seed, n_fixed=photons_per_track),
+                    n_minus_1=0.0014, seed=seed,
+                    description=f"{n_tracks} pion tracks x {photons_per_track} photons, "
+                    "RICH1-like analytic geometry, 10 parameters")
+
+
+def nominal_theta(scene, n_minus_1):
+    """Parameters at the nominal geometry: tilts 0, the tiles' radius of
+    curvature, n - 1 (as the FP32 inputs hold them)."""
+    th = np.zeros(10)
+    th[8] = float(scene.spheres[0]["radius"]) if len(scene.spheres) else 0.0
+    th[9] = float(np.float32(n_minus_1))
+    return th
