@@ -348,6 +348,43 @@ RICH_API rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
  * error recorded during the trace. */
 RICH_API rich_status rich_hits(rich_ctx *ctx, uint64_t *n_hits, rich_stats *stats);
 
+/* Parameters of the gradient (10 scalars).
+ *   tilt[2k], tilt[2k+1]: rotation of sphere tile k (k = 0..3, descriptor
+ *     order) about the axis through its pole parallel to its nominal e1,
+ *     then about the nominal e2 (rad); the pole stays fixed.
+ *   radius: radius of curvature of every sphere tile (mm), pole fixed.
+ *   n_minus_1: refractive index of the radiator minus one. */
+typedef struct rich_grad_params {
+    float tilt[8];
+    float radius;
+    float n_minus_1;
+} rich_grad_params;
+
+/* Soft ring chi^2 and its gradient with respect to rich_grad_params (the
+ * differentiation of the mirror alignment and of the Cherenkov angle,
+ * cos(theta) = 1/(n beta), Sec. 3, through the propagation of Sec. 4). The
+ * tracks are emitted with n - 1 = theta->n_minus_1 (emit->n_minus_1 is
+ * ignored; seed and band are used) and traced through the scene with its
+ * sphere tiles moved to theta; every detected photon is then replayed along
+ * its recorded reflecting surfaces (fixed topology, the photon's path
+ * recomputed per photon, not stored) in forward mode: FP64 values, 10 FP32
+ * tangents. The hit (u, v) is smeared by sigma (g1, g2), a Box-Muller pair
+ * from the photon's draw block 3; rho = (|(u~, v~) - (cu, cv)| - r) / sigma
+ * and loss = mean rho^2 over the hits whose (track index, plane) target has
+ * weight > 0.
+ * targets: DEVICE float [n_tracks][n_planes][4] = (cu, cv, r, weight).
+ * out: DEVICE outputs of the forward pass; hits must have room for every
+ *   hit (RICH_ERR_OVERFLOW otherwise: missing hits are not in the gradient);
+ *   pixel_counts optional; event_sums ignored. Hits carry FP64 positions.
+ * grad, loss, n_used: HOST results (mean over the hits used). Synchronous. */
+RICH_API rich_status rich_trace_grad(rich_ctx *ctx, const rich_tracks *tracks,
+                                     const rich_emit_params *emit,
+                                     const rich_grad_params *theta,
+                                     const float *targets, float sigma,
+                                     const rich_trace_opts *opts,
+                                     const rich_outputs *out, double grad[10],
+                                     double *loss, uint64_t *n_used);
+
 /* The library's random numbers: Philox4x32-10 (Salmon et al., SC'11) of n
  * counters (DEVICE, n x 4 words, 16-byte aligned) under key = (seed low
  * word, seed high word), written to out (DEVICE, n x 4 words, 16-byte

@@ -1236,7 +1236,14 @@ static void replay_dual(const o_scene *nom, const o_tracks_in *t, const o_params
     double beta = track_beta(t->p[i], t->mass[i]);
     dn nb = dscl(dadd(dc(1.0), th[9]), beta);
     dn ct = ddiv(dc(1.0), nb);
-    dn st = dsqrt(dsub(dc(1.0), dmul(ct, ct)));
+    dn one_m = dsub(dc(1.0), dmul(ct, ct));
+    dn st;
+    if (one_m.v > 0.0) {
+        st = dsqrt(one_m);
+    } else {   /* below threshold: the emission leaves along the track */
+        ct = dc(1.0);
+        st = dc(0.0);
+    }
     v3 e1, e2;
     basis(dir, &e1, &e2);
     v3 tr = add(scl(e1, cos(phi)), scl(e2, sin(phi)));

@@ -54,6 +54,12 @@ struct rich_ctx {
     // occupancy per (external, refine, threads, smem), queried once
     std::map<std::tuple<bool, bool, int, int, size_t>, int> occupancy;
     int smem_optin = 48 * 1024;
+    // gradient: nominal tiles (host), their frames (device), tilted copies
+    std::vector<rich_sphere> nom_spheres;
+    DevTileNom *d_tile_nom = nullptr;
+    void *d_grad_tiles = nullptr;          // groups + tiles at theta
+    double *d_acc = nullptr;               // 12 FP64 accumulators
+    double *h_acc = nullptr;               // pinned
 };
 
 static thread_local std::string g_create_error;
@@ -97,6 +103,117 @@ bool finite3(const float *v) {
     return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]);
 }
 
+// Tiles sharing one sphere (identical FP32 centre and radius) form a group:
+// the FP64 quadratic is solved once per group.
+bool group_tiles(const rich_sphere *sp, int n, int n_materials,
+                 std::vector<DevSphereGroup> &groups, std::vector<DevTile> &tiles,
+                 std::string &err) {
+    groups.clear();
+    tiles.clear();
+    std::vector<int> tile_group(n);
+    std::vector<std::tuple<float, float, float, float>> spheres;
+    for (int i = 0; i < n; ++i) {
+        const rich_sphere &s = sp[i];
+        if (!finite3(s.center) || !finite3(s.axis) || !finite3(s.e1) || !finite3(s.e2) ||
+            !(s.radius > 0.f) || !std::isfinite(s.radius)) {
+            err = "sphere tile with non-finite or non-positive values";
+            return false;
+        }
+        if (s.n_edges < 0 || s.n_edges > RICH_SPHERE_MAX_EDGES) {
+            err = "sphere tile edges 0..8";
+            return false;
+        }
+        if (s.material < 0 || s.material >= n_materials) {
+            err = "sphere material index";
+            return false;
+        }
+        auto key = std::make_tuple(s.center[0], s.center[1], s.center[2], s.radius);
+        auto it = std::find(spheres.begin(), spheres.end(), key);
+        if (it == spheres.end()) {
+            spheres.push_back(key);
+            tile_group[i] = (int)spheres.size() - 1;
+        } else {
+            tile_group[i] = (int)(it - spheres.begin());
+        }
+    }
+    if ((int)spheres.size() > RICH_MAX_GROUPS) {
+        err = "more than 16 distinct spheres";
+        return false;
+    }
+    groups.resize(spheres.size());
+    for (size_t gi = 0; gi < spheres.size(); ++gi) {
+        DevSphereGroup &G = groups[gi];
+        G.cx = std::get<0>(spheres[gi]);
+        G.cy = std::get<1>(spheres[gi]);
+        G.cz = std::get<2>(spheres[gi]);
+        const double R = std::get<3>(spheres[gi]);
+        G.r2 = R * R;
+        G.radius = (float)R;
+        G.inv_radius = (float)(1.0 / R);
+        G.first = (int)tiles.size();
+        for (int i = 0; i < n; ++i) {
+            if (tile_group[i] != (int)gi) continue;
+            const rich_sphere &s = sp[i];
+            DevTile T;
+            std::memset(&T, 0, sizeof T);
+            T.ax = s.axis[0]; T.ay = s.axis[1]; T.az = s.axis[2]; T.cos_min = s.cos_min;
+            T.e1x = s.e1[0]; T.e1y = s.e1[1]; T.e1z = s.e1[2];
+            T.inv_radius = (float)(1.0 / (double)s.radius);
+            T.e2x = s.e2[0]; T.e2y = s.e2[1]; T.e2z = s.e2[2];
+            T.n_edges = s.n_edges;
+            T.material = s.material;
+            T.group = (int)gi;
+            T.prim = i;
+            for (int e = 0; e < s.n_edges; ++e)
+                for (int k = 0; k < 3; ++k) T.edges[e][k] = s.edges[e][k];
+            tiles.push_back(T);
+        }
+        G.count = (int)tiles.size() - G.first;
+    }
+    return true;
+}
+
+// Rodrigues rotation of v about the unit axis u by phi (FP64).
+void rotate(const double u[3], double phi, double v[3]) {
+    const double c = std::cos(phi), s = std::sin(phi);
+    const double uv = u[0] * v[0] + u[1] * v[1] + u[2] * v[2];
+    const double x[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2],
+                         u[0] * v[1] - u[1] * v[0]};
+    for (int k = 0; k < 3; ++k) v[k] = v[k] * c + x[k] * s + u[k] * uv * (1.0 - c);
+}
+
+// Tile i at the parameters theta: rotated about its pole by theta[2i] (about
+// its nominal e1) then theta[2i+1] (about its nominal e2) for i < 4, radius
+// theta[8], centre = pole - radius * axis.
+rich_sphere tile_at_theta(const rich_sphere &s, int i, const double theta[10]) {
+    const double R0 = s.radius;
+    double P[3], a[3], e1[3], e2[3], u1[3], u2[3];
+    for (int k = 0; k < 3; ++k) {
+        P[k] = (double)s.center[k] + R0 * s.axis[k];
+        a[k] = s.axis[k];
+        e1[k] = s.e1[k];
+        e2[k] = s.e2[k];
+        u1[k] = s.e1[k];
+        u2[k] = s.e2[k];
+    }
+    if (i < 4) {
+        for (double *v : {a, e1, e2}) {
+            rotate(u1, theta[2 * i], v);
+            rotate(u2, theta[2 * i + 1], v);
+        }
+    }
+    rich_sphere t = s;
+    const double R = theta[8];
+    for (int k = 0; k < 3; ++k) {
+        t.center[k] = (float)(P[k] - R * a[k]);
+        t.axis[k] = (float)a[k];
+        t.e1[k] = (float)e1[k];
+        t.e2[k] = (float)e2[k];
+    }
+    t.radius = (float)R;
+    return t;
+}
+
 void free_emission(rich_ctx *ctx) {
     cudaFree(ctx->d_rec);
     cudaFree(ctx->d_cs);
@@ -109,6 +226,51 @@ void free_emission(rich_ctx *ctx) {
     ctx->d_offsets = nullptr;
     ctx->d_bsum = nullptr;
     ctx->track_cap = 0;
+}
+
+// Yield, Poisson counts and photon offsets of the tracks into the context's
+// scratch (asynchronous).
+rich_status emit_core(rich_ctx *ctx, const rich_tracks *t, uint64_t seed, float n_minus_1,
+                      float lambda_min, float lambda_max) {
+    const int64_t n = t->n;
+    if (n + 1 > ctx->track_cap) {
+        RICH_CUDA(cudaStreamSynchronize(ctx->stream));
+        free_emission(ctx);
+        const int64_t cap = std::max<int64_t>(n + 1, 1024);
+        const int64_t blocks = (cap + yield_block_threads() - 1) / yield_block_threads();
+        RICH_CUDA(cudaMalloc(&ctx->d_rec, sizeof(TrackRec) * cap));
+        RICH_CUDA(cudaMalloc(&ctx->d_cs, sizeof(double2) * cap));
+        RICH_CUDA(cudaMalloc(&ctx->d_counts, sizeof(uint32_t) * cap));
+        RICH_CUDA(cudaMalloc(&ctx->d_offsets, sizeof(uint64_t) * (cap + 1)));
+        RICH_CUDA(cudaMalloc(&ctx->d_bsum, sizeof(unsigned long long) * (blocks + 1)));
+        ctx->track_cap = cap;
+    }
+    ctx->key0 = (uint32_t)seed;
+    ctx->key1 = (uint32_t)(seed >> 32);
+    {
+        // FP32 spectrum constants, one IEEE operation each
+        volatile float l1 = lambda_min, l2 = lambda_max;
+        volatile float inv1 = 1.0f / l1;
+        volatile float inv2 = 1.0f / l2;
+        volatile float span = inv1 - inv2;
+        ctx->inv1 = inv1;
+        ctx->span = span;
+    }
+    TracksView tv{n, t->x, t->y, t->z, t->dx, t->dy, t->dz, t->p, t->mass, t->length,
+                  t->event, t->id, t->n_fixed};
+    if (n == 0) {
+        RICH_CUDA(cudaMemsetAsync(ctx->d_total, 0, sizeof(unsigned long long), ctx->stream));
+        RICH_CUDA(cudaMemsetAsync(ctx->d_offsets, 0, sizeof(uint64_t), ctx->stream));
+    } else {
+        RICH_CUDA(launch_yield(tv, (double)n_minus_1, lambda_min, lambda_max, ctx->key0,
+                               ctx->key1, ctx->d_rec, ctx->d_cs, ctx->d_counts, ctx->d_bsum,
+                               ctx->stream));
+        RICH_CUDA(launch_offsets(ctx->d_counts, ctx->d_bsum, n, ctx->d_offsets, ctx->d_total,
+                                 ctx->stream));
+    }
+    ctx->n_tracks = n;
+    ctx->has_emission = true;
+    return RICH_OK;
 }
 
 }  // namespace
@@ -169,6 +331,10 @@ RICH_API rich_status rich_destroy(rich_ctx *ctx) {
         cudaStreamSynchronize(ctx->stream);
         cudaFree(ctx->d_geom);
         cudaFree(ctx->d_refine);
+        cudaFree(ctx->d_tile_nom);
+        cudaFree(ctx->d_grad_tiles);
+        cudaFree(ctx->d_acc);
+        cudaFreeHost(ctx->h_acc);
         free_emission(ctx);
         cudaFree(ctx->d_ctr);
         cudaFree(ctx->d_total);
@@ -223,55 +389,12 @@ RICH_API rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc 
     if (any_smooth && g->n_triangles && !g->tri_normals)
         return bad("smooth material without vertex normals");
     // ---- sphere groups (tiles sharing a sphere)
-    std::vector<int> tile_group(g->n_spheres);
-    std::vector<std::tuple<float, float, float, float>> spheres;
-    for (int i = 0; i < g->n_spheres; ++i) {
-        const rich_sphere &s = g->spheres[i];
-        if (!finite3(s.center) || !finite3(s.axis) || !finite3(s.e1) || !finite3(s.e2) ||
-            !(s.radius > 0.f) || !std::isfinite(s.radius))
-            return bad("sphere tile with non-finite or non-positive values");
-        if (s.n_edges < 0 || s.n_edges > RICH_SPHERE_MAX_EDGES) return bad("sphere tile edges 0..8");
-        if (s.material < 0 || s.material >= g->n_materials) return bad("sphere material index");
-        auto key = std::make_tuple(s.center[0], s.center[1], s.center[2], s.radius);
-        auto it = std::find(spheres.begin(), spheres.end(), key);
-        if (it == spheres.end()) {
-            spheres.push_back(key);
-            tile_group[i] = (int)spheres.size() - 1;
-        } else {
-            tile_group[i] = (int)(it - spheres.begin());
-        }
-    }
-    if ((int)spheres.size() > RICH_MAX_GROUPS) return bad("more than 16 distinct spheres");
-    std::vector<DevSphereGroup> groups(spheres.size());
+    std::vector<DevSphereGroup> groups;
     std::vector<DevTile> tiles;
-    for (size_t gi = 0; gi < spheres.size(); ++gi) {
-        DevSphereGroup &G = groups[gi];
-        G.cx = std::get<0>(spheres[gi]);
-        G.cy = std::get<1>(spheres[gi]);
-        G.cz = std::get<2>(spheres[gi]);
-        const double R = std::get<3>(spheres[gi]);
-        G.r2 = R * R;
-        G.radius = (float)R;
-        G.inv_radius = (float)(1.0 / R);
-        G.first = (int)tiles.size();
-        for (int i = 0; i < g->n_spheres; ++i) {
-            if (tile_group[i] != (int)gi) continue;
-            const rich_sphere &s = g->spheres[i];
-            DevTile T;
-            std::memset(&T, 0, sizeof T);
-            T.ax = s.axis[0]; T.ay = s.axis[1]; T.az = s.axis[2]; T.cos_min = s.cos_min;
-            T.e1x = s.e1[0]; T.e1y = s.e1[1]; T.e1z = s.e1[2];
-            T.inv_radius = (float)(1.0 / (double)s.radius);
-            T.e2x = s.e2[0]; T.e2y = s.e2[1]; T.e2z = s.e2[2];
-            T.n_edges = s.n_edges;
-            T.material = s.material;
-            T.group = (int)gi;
-            T.prim = i;
-            for (int e = 0; e < s.n_edges; ++e)
-                for (int k = 0; k < 3; ++k) T.edges[e][k] = s.edges[e][k];
-            tiles.push_back(T);
-        }
-        G.count = (int)tiles.size() - G.first;
+    {
+        std::string gerr;
+        if (!group_tiles(g->spheres, g->n_spheres, g->n_materials, groups, tiles, gerr))
+            return bad(gerr);
     }
     // ---- rectangles and planes
     std::vector<DevRect> rects(g->n_rects);
@@ -409,6 +532,27 @@ RICH_API rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc 
     sc.pixels_per_event = off;
     ctx->sc = sc;
     ctx->bvh_depth = bvh.depth;
+    // nominal tile frames for the gradient
+    ctx->nom_spheres.assign(g->spheres, g->spheres + g->n_spheres);
+    cudaFree(ctx->d_tile_nom);
+    ctx->d_tile_nom = nullptr;
+    cudaFree(ctx->d_grad_tiles);
+    ctx->d_grad_tiles = nullptr;
+    if (g->n_spheres) {
+        std::vector<DevTileNom> nom(g->n_spheres);
+        for (int i = 0; i < g->n_spheres; ++i) {
+            const rich_sphere &q = g->spheres[i];
+            const double R0 = q.radius;
+            nom[i] = {q.center[0] + R0 * q.axis[0], q.center[1] + R0 * q.axis[1],
+                      q.center[2] + R0 * q.axis[2], q.axis[0], q.axis[1], q.axis[2],
+                      q.e1[0], q.e1[1], q.e1[2], q.e2[0], q.e2[1], q.e2[2]};
+        }
+        RICH_CUDA(cudaMalloc(&ctx->d_tile_nom, sizeof(DevTileNom) * nom.size()));
+        RICH_CUDA(cudaMemcpy(ctx->d_tile_nom, nom.data(), sizeof(DevTileNom) * nom.size(),
+                             cudaMemcpyHostToDevice));
+        RICH_CUDA(cudaMalloc(&ctx->d_grad_tiles,
+                             sizeof(DevSphereGroup) * RICH_MAX_GROUPS + sizeof(DevTile) * RICH_MAX_TILES));
+    }
     ctx->has_geometry = true;
     return RICH_OK;
 }
@@ -429,43 +573,11 @@ RICH_API rich_status rich_emit(rich_ctx *ctx, const rich_tracks *t,
         return fail(ctx, RICH_ERR_ARG, "rich_emit: need n-1 >= 0 and 0 < lambda_min < lambda_max");
     DeviceGuard guard(ctx->device);
     const int64_t n = t->n;
-    if (n + 1 > ctx->track_cap) {
-        RICH_CUDA(cudaStreamSynchronize(ctx->stream));
-        free_emission(ctx);
-        const int64_t cap = std::max<int64_t>(n + 1, 1024);
-        const int64_t blocks = (cap + yield_block_threads() - 1) / yield_block_threads();
-        RICH_CUDA(cudaMalloc(&ctx->d_rec, sizeof(TrackRec) * cap));
-        RICH_CUDA(cudaMalloc(&ctx->d_cs, sizeof(double2) * cap));
-        RICH_CUDA(cudaMalloc(&ctx->d_counts, sizeof(uint32_t) * cap));
-        RICH_CUDA(cudaMalloc(&ctx->d_offsets, sizeof(uint64_t) * (cap + 1)));
-        RICH_CUDA(cudaMalloc(&ctx->d_bsum, sizeof(unsigned long long) * (blocks + 1)));
-        ctx->track_cap = cap;
-    }
-    ctx->key0 = (uint32_t)prm->seed;
-    ctx->key1 = (uint32_t)(prm->seed >> 32);
     {
-        // FP32 spectrum constants, one IEEE operation each
-        volatile float l1 = prm->lambda_min, l2 = prm->lambda_max;
-        volatile float inv1 = 1.0f / l1;
-        volatile float inv2 = 1.0f / l2;
-        volatile float span = inv1 - inv2;
-        ctx->inv1 = inv1;
-        ctx->span = span;
+        const rich_status st = emit_core(ctx, t, prm->seed, prm->n_minus_1, prm->lambda_min,
+                                         prm->lambda_max);
+        if (st != RICH_OK) return st;
     }
-    TracksView tv{n, t->x, t->y, t->z, t->dx, t->dy, t->dz, t->p, t->mass, t->length,
-                  t->event, t->id, t->n_fixed};
-    if (n == 0) {
-        RICH_CUDA(cudaMemsetAsync(ctx->d_total, 0, sizeof(unsigned long long), ctx->stream));
-        RICH_CUDA(cudaMemsetAsync(ctx->d_offsets, 0, sizeof(uint64_t), ctx->stream));
-    } else {
-        RICH_CUDA(launch_yield(tv, (double)prm->n_minus_1, prm->lambda_min, prm->lambda_max,
-                               ctx->key0, ctx->key1, ctx->d_rec, ctx->d_cs, ctx->d_counts,
-                               ctx->d_bsum, ctx->stream));
-        RICH_CUDA(launch_offsets(ctx->d_counts, ctx->d_bsum, n, ctx->d_offsets, ctx->d_total,
-                                 ctx->stream));
-    }
-    ctx->n_tracks = n;
-    ctx->has_emission = true;
     if (n_photons || out) {
         RICH_CUDA(cudaMemcpyAsync(ctx->h_total, ctx->d_total, sizeof(unsigned long long),
                                   cudaMemcpyDeviceToHost, ctx->stream));
@@ -614,6 +726,148 @@ RICH_API rich_status rich_hits(rich_ctx *ctx, uint64_t *n_hits, rich_stats *stat
         return fail(ctx, RICH_ERR_OVERFLOW, "rich_hits: " + std::to_string(c.hits) +
                                                 " hits for capacity " +
                                                 std::to_string(ctx->last_capacity));
+    return RICH_OK;
+}
+
+RICH_API rich_status rich_trace_grad(rich_ctx *ctx, const rich_tracks *t,
+                                     const rich_emit_params *prm, const rich_grad_params *th,
+                                     const float *targets, float sigma,
+                                     const rich_trace_opts *o, const rich_outputs *out,
+                                     double grad[10], double *loss, uint64_t *n_used) {
+    if (!ctx) return RICH_ERR_ARG;
+    if (!t || !prm || !th || !o || !out || !grad || !loss)
+        return fail(ctx, RICH_ERR_ARG, "rich_trace_grad: NULL argument");
+    if (!ctx->has_geometry) return fail(ctx, RICH_ERR_STATE, "rich_trace_grad: no geometry");
+    if (!targets || !(sigma > 0.f) || !out->hits || out->hit_capacity == 0)
+        return fail(ctx, RICH_ERR_ARG,
+                    "rich_trace_grad: need targets, sigma > 0 and a hit buffer");
+    if (!(th->radius > 0.f) || !(th->n_minus_1 >= 0.f))
+        return fail(ctx, RICH_ERR_ARG, "rich_trace_grad: need radius > 0 and n - 1 >= 0");
+    for (int k = 0; k < 8; ++k)
+        if (!std::isfinite(th->tilt[k]) || std::fabs(th->tilt[k]) > 0.5f)
+            return fail(ctx, RICH_ERR_ARG, "rich_trace_grad: tilts must be finite, |tilt| <= 0.5 rad");
+    if (t->n > 0 && (!t->x || !t->y || !t->z || !t->dx || !t->dy || !t->dz || !t->p ||
+                     !t->mass || !t->length || !t->event))
+        return fail(ctx, RICH_ERR_ARG, "rich_trace_grad: a required track array is NULL");
+    DeviceGuard guard(ctx->device);
+    double theta[10];
+    for (int k = 0; k < 8; ++k) theta[k] = th->tilt[k];
+    theta[8] = th->radius;
+    theta[9] = th->n_minus_1;
+    // tiles at theta
+    SceneView sv = ctx->sc;
+    const int ns = (int)ctx->nom_spheres.size();
+    if (ns) {
+        std::vector<rich_sphere> at(ns);
+        for (int i = 0; i < ns; ++i) at[i] = tile_at_theta(ctx->nom_spheres[i], i, theta);
+        std::vector<DevSphereGroup> groups;
+        std::vector<DevTile> tiles;
+        std::string gerr;
+        if (!group_tiles(at.data(), ns, ctx->sc.n_materials, groups, tiles, gerr))
+            return fail(ctx, RICH_ERR_ARG, "rich_trace_grad: " + gerr);
+        char *base = static_cast<char *>(ctx->d_grad_tiles);
+        RICH_CUDA(cudaMemcpyAsync(base, groups.data(), sizeof(DevSphereGroup) * groups.size(),
+                                  cudaMemcpyHostToDevice, ctx->stream));
+        char *tb = base + sizeof(DevSphereGroup) * RICH_MAX_GROUPS;
+        RICH_CUDA(cudaMemcpyAsync(tb, tiles.data(), sizeof(DevTile) * tiles.size(),
+                                  cudaMemcpyHostToDevice, ctx->stream));
+        sv.groups = reinterpret_cast<const DevSphereGroup *>(base);
+        sv.tiles = reinterpret_cast<const DevTile *>(tb);
+        sv.n_groups = (int)groups.size();
+        // host vectors must outlive the asynchronous copies
+        RICH_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    {
+        const rich_status st = emit_core(ctx, t, prm->seed, th->n_minus_1, prm->lambda_min,
+                                         prm->lambda_max);
+        if (st != RICH_OK) return st;
+    }
+    // forward trace recording each detected photon's reflecting surfaces
+    rich_trace_opts fo = *o;
+    fo.precision = RICH_PREC_REFINE64;
+    const uint64_t hit_cap = out->hit_capacity;
+    if (hit_cap > ctx->refine_cap) {
+        RICH_CUDA(cudaStreamSynchronize(ctx->stream));
+        cudaFree(ctx->d_refine);
+        ctx->d_refine = nullptr;
+        ctx->refine_cap = 0;
+        RICH_CUDA(cudaMalloc(&ctx->d_refine, sizeof(RefineRec) * hit_cap));
+        ctx->refine_cap = hit_cap;
+    }
+    if (!ctx->d_acc) {
+        RICH_CUDA(cudaMalloc(&ctx->d_acc, sizeof(double) * 12));
+        RICH_CUDA(cudaMallocHost(&ctx->h_acc, sizeof(double) * 12));
+    }
+    const int threads = fo.block_threads ? fo.block_threads : 1024;
+    const int cls = trace_shape_class(threads, fo.wide_regs != 0);
+    int smem_nodes = fo.bvh_smem_nodes;
+    if (smem_nodes < 0) smem_nodes = threads > 256 ? 1536 : 0;
+    if (smem_nodes > ctx->sc.n_nodes) smem_nodes = ctx->sc.n_nodes;
+    if (ctx->sc.n_tris == 0) smem_nodes = 0;
+    TraceParams p{};
+    p.precision = RICH_PREC_REFINE64;
+    p.max_bounces = fo.max_bounces;
+    p.max_steps = fo.max_steps;
+    p.t_min = fo.t_min;
+    p.refill_min = fo.refill_min ? fo.refill_min : 32;
+    p.chunk = fo.chunk ? fo.chunk : 32;
+    p.hits = out->hits;
+    p.hit_capacity = hit_cap;
+    p.pixel_counts = out->pixel_counts;
+    p.event_sums = nullptr;
+    p.n_hist_events = out->pixel_counts ? out->n_hist_events : 0;
+    p.fate = out->fate;
+    p.refine = ctx->d_refine;
+    p.smem_nodes = smem_nodes;
+    if (p.max_bounces < 1 || p.max_bounces > RICH_MAX_BOUNCES || p.max_steps < 1 ||
+        p.max_steps > RICH_MAX_STEPS || threads % 32 || threads > 1024)
+        return fail(ctx, RICH_ERR_ARG, "rich_trace_grad: trace options out of range");
+    LaunchShape shape;
+    shape.threads = threads;
+    shape.cls = cls;
+    shape.smem = trace_smem_bytes(sv, smem_nodes);
+    const int bps = trace_blocks_per_sm(false, true, cls, threads, shape.smem);
+    if (bps < 1) return fail(ctx, RICH_ERR_ARG, "rich_trace_grad: launch shape does not fit");
+    shape.blocks = bps * ctx->n_sm;
+    RICH_CUDA(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), ctx->stream));
+    RICH_CUDA(cudaMemsetAsync(ctx->d_acc, 0, sizeof(double) * 12, ctx->stream));
+    EmitView em{ctx->d_rec, ctx->d_cs, ctx->d_offsets, ctx->d_total, ctx->n_tracks,
+                ctx->key0, ctx->key1, ctx->inv1, ctx->span};
+    RICH_CUDA(launch_trace(sv, &em, nullptr, p, ctx->d_ctr, shape, ctx->stream));
+    GradView gv{};
+    gv.nom = ctx->d_tile_nom;
+    gv.n_tiles = ns;
+    gv.n_planes = ctx->sc.n_planes;
+    for (int k = 0; k < 10; ++k) gv.theta[k] = theta[k];
+    gv.targets = reinterpret_cast<const float4 *>(targets);
+    gv.sigma = sigma;
+    gv.acc = ctx->d_acc;
+    gv.tracks = TracksView{t->n, t->x, t->y, t->z, t->dx, t->dy, t->dz, t->p, t->mass,
+                           t->length, t->event, t->id, t->n_fixed};
+    RICH_CUDA(launch_adjoint(sv, em, p, gv, ctx->d_ctr, ctx->n_sm, ctx->stream));
+    RICH_CUDA(cudaMemcpyAsync(ctx->h_acc, ctx->d_acc, sizeof(double) * 12,
+                              cudaMemcpyDeviceToHost, ctx->stream));
+    RICH_CUDA(cudaMemcpyAsync(ctx->h_ctr, ctx->d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost,
+                              ctx->stream));
+    RICH_CUDA(cudaMemcpyAsync(ctx->h_total, ctx->d_total, sizeof(unsigned long long),
+                              cudaMemcpyDeviceToHost, ctx->stream));
+    RICH_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->traced = true;
+    ctx->last_ext = false;
+    ctx->last_capacity = hit_cap;
+    const double used = ctx->h_acc[1];
+    const double inv = used > 0 ? 1.0 / used : 0.0;
+    *loss = ctx->h_acc[0] * inv;
+    for (int k = 0; k < 10; ++k) grad[k] = ctx->h_acc[2 + k] * inv;
+    if (n_used) *n_used = (uint64_t)used;
+    if (ctx->h_ctr->status)
+        return fail(ctx, (rich_status)ctx->h_ctr->status,
+                    "rich_trace_grad: device reported status " + std::to_string(ctx->h_ctr->status));
+    if (ctx->h_ctr->hits > hit_cap)
+        return fail(ctx, RICH_ERR_OVERFLOW,
+                    "rich_trace_grad: " + std::to_string(ctx->h_ctr->hits) +
+                        " hits for capacity " + std::to_string(hit_cap) +
+                        " (hits beyond it are not in the gradient)");
     return RICH_OK;
 }
 

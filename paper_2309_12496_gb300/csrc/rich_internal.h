@@ -161,6 +161,26 @@ struct TraceParams {
     int32_t smem_nodes;       // BVH nodes [0, smem_nodes) staged in shared memory
 };
 
+// Nominal frame of a sphere tile for the gradient: pole P = C + R a, axis
+// a (centre -> pole) and tangent axes e1, e2, in FP64.
+struct DevTileNom {           // 96 B
+    double px, py, pz, ax, ay, az, e1x, e1y, e1z, e2x, e2y, e2z;
+};
+
+// Gradient of the soft ring chi^2: parameters theta (8 tile tilts, radius of
+// curvature, n - 1), ring targets [n_tracks][n_planes] = (cu, cv, r, weight)
+// and the FP64 accumulators (loss sum, hits used, 10 gradient sums).
+struct GradView {
+    const DevTileNom *nom;
+    int32_t n_tiles;
+    int32_t n_planes;
+    double theta[10];
+    const float4 *targets;
+    double sigma;
+    double *acc;              // 12 doubles
+    TracksView tracks;
+};
+
 struct LaunchShape {
     int blocks, threads;
     size_t smem;
@@ -189,6 +209,9 @@ cudaError_t launch_refine(const SceneView &sc, const EmitView *em,
                           Counters *counters, int n_sm, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t *ctr, uint64_t n, uint64_t seed, uint32_t *out,
                           cudaStream_t s);
+cudaError_t launch_adjoint(const SceneView &sc, const EmitView &em, const TraceParams &p,
+                           const GradView &gv, Counters *counters, int n_sm,
+                           cudaStream_t s);
 size_t trace_smem_bytes(const SceneView &sc, int smem_nodes);
 int trace_shape_class(int threads, bool wide);
 int trace_blocks_per_sm(bool ext, bool refine, int cls, int threads, size_t smem);

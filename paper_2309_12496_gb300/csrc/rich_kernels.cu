@@ -1139,6 +1139,291 @@ cudaError_t launch_refine(const SceneView &sc, const EmitView *em, const ExtView
     return cudaGetLastError();
 }
 
+// ============================================================== adjoint
+// Gradient of the soft ring chi^2 with respect to theta = (tilt alpha_k,
+// beta_k of sphere tiles 0..3, radius of curvature, n - 1): every stored hit
+// is replayed along its recorded reflecting surfaces (fixed topology) in
+// forward mode, with FP64 values and 10 FP32 tangents per quantity.
+constexpr int kNG = 10;
+struct Dm {
+    double v;
+    float d[kNG];
+};
+struct Dm3 {
+    Dm x, y, z;
+};
+
+__device__ __forceinline__ Dm dm_c(double v) {
+    Dm r;
+    r.v = v;
+#pragma unroll
+    for (int k = 0; k < kNG; ++k) r.d[k] = 0.0f;
+    return r;
+}
+__device__ __forceinline__ Dm dm_add(const Dm &a, const Dm &b) {
+    Dm r;
+    r.v = a.v + b.v;
+#pragma unroll
+    for (int k = 0; k < kNG; ++k) r.d[k] = a.d[k] + b.d[k];
+    return r;
+}
+__device__ __forceinline__ Dm dm_sub(const Dm &a, const Dm &b) {
+    Dm r;
+    r.v = a.v - b.v;
+#pragma unroll
+    for (int k = 0; k < kNG; ++k) r.d[k] = a.d[k] - b.d[k];
+    return r;
+}
+__device__ __forceinline__ Dm dm_mul(const Dm &a, const Dm &b) {
+    Dm r;
+    r.v = a.v * b.v;
+    const float av = (float)a.v, bv = (float)b.v;
+#pragma unroll
+    for (int k = 0; k < kNG; ++k) r.d[k] = fmaf(a.d[k], bv, av * b.d[k]);
+    return r;
+}
+__device__ __forceinline__ Dm dm_scl(const Dm &a, double s) {
+    Dm r;
+    r.v = a.v * s;
+    const float sf = (float)s;
+#pragma unroll
+    for (int k = 0; k < kNG; ++k) r.d[k] = a.d[k] * sf;
+    return r;
+}
+__device__ __forceinline__ Dm dm_div(const Dm &a, const Dm &b) {
+    Dm r;
+    const double ib = rcp64(b.v);
+    r.v = a.v * ib;
+    const float ibf = (float)ib, rv = (float)r.v;
+#pragma unroll
+    for (int k = 0; k < kNG; ++k) r.d[k] = (a.d[k] - rv * b.d[k]) * ibf;
+    return r;
+}
+__device__ __forceinline__ Dm dm_sqrt(const Dm &a) {
+    Dm r;
+    const double is = a.v > 0.0 ? rsqrt64(a.v) : 0.0;
+    r.v = a.v * is;
+    const float h = (float)(0.5 * is);
+#pragma unroll
+    for (int k = 0; k < kNG; ++k) r.d[k] = a.d[k] * h;
+    return r;
+}
+__device__ __forceinline__ void dm_sincos(const Dm &a, Dm &sn, Dm &cs) {
+    double s, c;
+    sincos(a.v, &s, &c);
+    sn.v = s;
+    cs.v = c;
+    const float sf = (float)s, cf = (float)c;
+#pragma unroll
+    for (int k = 0; k < kNG; ++k) {
+        sn.d[k] = cf * a.d[k];
+        cs.d[k] = -sf * a.d[k];
+    }
+}
+__device__ __forceinline__ Dm3 dm3_c(d3 a) { return {dm_c(a.x), dm_c(a.y), dm_c(a.z)}; }
+__device__ __forceinline__ Dm3 dm3_add(const Dm3 &a, const Dm3 &b) {
+    return {dm_add(a.x, b.x), dm_add(a.y, b.y), dm_add(a.z, b.z)};
+}
+__device__ __forceinline__ Dm3 dm3_sub(const Dm3 &a, const Dm3 &b) {
+    return {dm_sub(a.x, b.x), dm_sub(a.y, b.y), dm_sub(a.z, b.z)};
+}
+__device__ __forceinline__ Dm3 dm3_scl(const Dm3 &a, const Dm &s) {
+    return {dm_mul(a.x, s), dm_mul(a.y, s), dm_mul(a.z, s)};
+}
+__device__ __forceinline__ Dm dm3_dot(const Dm3 &a, const Dm3 &b) {
+    return dm_add(dm_add(dm_mul(a.x, b.x), dm_mul(a.y, b.y)), dm_mul(a.z, b.z));
+}
+__device__ __forceinline__ Dm dm3_dotc(const Dm3 &a, d3 b) {
+    return dm_add(dm_add(dm_scl(a.x, b.x), dm_scl(a.y, b.y)), dm_scl(a.z, b.z));
+}
+// Rodrigues rotation of v about the fixed unit axis u by the angle phi.
+__device__ __forceinline__ Dm3 dm3_rot(d3 u, const Dm &phi, const Dm3 &v) {
+    Dm sn, cs;
+    dm_sincos(phi, sn, cs);
+    const Dm uv = dm3_dotc(v, u);
+    const Dm k = dm_mul(uv, dm_sub(dm_c(1.0), cs));
+    const Dm3 uxv = {dm_sub(dm_scl(v.z, u.y), dm_scl(v.y, u.z)),
+                     dm_sub(dm_scl(v.x, u.z), dm_scl(v.z, u.x)),
+                     dm_sub(dm_scl(v.y, u.x), dm_scl(v.x, u.y))};
+    Dm3 r = dm3_add(dm3_scl(v, cs), dm3_scl(uxv, sn));
+    return dm3_add(r, {dm_scl(k, u.x), dm_scl(k, u.y), dm_scl(k, u.z)});
+}
+__device__ __forceinline__ Dm3 dm3_reflect_unit(const Dm3 &d, const Dm3 &n) {
+    const Dm k = dm_scl(dm3_dot(d, n), 2.0);
+    Dm3 r = dm3_sub(d, dm3_scl(n, k));
+    const Dm inv = dm_div(dm_c(1.0), dm_sqrt(dm3_dot(r, r)));
+    return dm3_scl(r, inv);
+}
+__device__ __forceinline__ Dm dm_theta(const GradView &gv, int k) {
+    Dm r = dm_c(gv.theta[k]);
+    r.d[k] = 1.0f;
+    return r;
+}
+
+__device__ void replay_dual(const SceneView &sc, const GradView &gv, const EmitView &em,
+                            const RefineRec &rr, uint32_t j, Dm &u_out, Dm &v_out) {
+    const TrackRec tr = em.tracks[rr.index];
+    const TracksView &tv = gv.tracks;
+    // emission: n beta = 1 + (n - 1) beta - (1 - beta), tangent in n - 1
+    const double p = tv.p[rr.index], m = tv.mass[rr.index];
+    const double E = sqrt(p * p + m * m);
+    const double omb = (m == 0.0) ? 0.0 : (m * m) / (E * (E + p));
+    const double beta = 1.0 - omb;
+    const Dm nbm1 = dm_sub(dm_scl(dm_theta(gv, 9), beta), dm_c(omb));
+    const Dm nb = dm_add(dm_c(1.0), nbm1);
+    Dm ct, st;
+    if (nbm1.v > 0.0) {
+        ct = dm_div(dm_c(1.0), nb);
+        st = dm_mul(dm_sqrt(dm_mul(nbm1, dm_add(nb, dm_c(1.0)))), ct);
+    } else {   // below threshold: the emission leaves along the track
+        ct = dm_c(1.0);
+        st = dm_c(0.0);
+    }
+    const u4 w0 = philox10(0u, j, tr.id, tr.event, em.key0, em.key1);
+    const d3 t = normalized(mkd(tr.rx, tr.ry, tr.rz));
+    const double s = u24d(w0.x) * (double)tr.len;
+    Dm3 o = dm3_c(mkd(fma(t.x, s, (double)tr.x), fma(t.y, s, (double)tr.y),
+                      fma(t.z, s, (double)tr.z)));
+    double sp, cp;
+    sincospi(2.0 * u24d(w0.y), &sp, &cp);
+    d3 e1, e2;
+    basis_d(t, e1, e2);
+    const d3 rr_dir = mkd(cp * e1.x + sp * e2.x, cp * e1.y + sp * e2.y, cp * e1.z + sp * e2.z);
+    Dm3 d = dm3_add(dm3_scl(dm3_c(t), ct), dm3_scl(dm3_c(rr_dir), st));
+    const Dm R = dm_theta(gv, 8);
+    for (int k = 0; k < rr.n_path; ++k) {
+        const int prim = rr.path[k];
+        Dm3 n;
+        if (prim < sc.n_tiles) {
+            const DevTileNom &T = gv.nom[prim];
+            const Dm al = prim < 4 ? dm_theta(gv, 2 * prim) : dm_c(0.0);
+            const Dm be = prim < 4 ? dm_theta(gv, 2 * prim + 1) : dm_c(0.0);
+            const Dm3 a = dm3_rot(mkd(T.e2x, T.e2y, T.e2z), be,
+                                  dm3_rot(mkd(T.e1x, T.e1y, T.e1z), al,
+                                          dm3_c(mkd(T.ax, T.ay, T.az))));
+            const Dm3 C = dm3_sub(dm3_c(mkd(T.px, T.py, T.pz)), dm3_scl(a, R));
+            const Dm3 w = dm3_sub(o, C);
+            const Dm b = dm3_dot(w, d);
+            const Dm c = dm_sub(dm3_dot(w, w), dm_mul(R, R));
+            const Dm sq = dm_sqrt(dm_sub(dm_mul(b, b), c));
+            const Dm tt = b.v <= 0.0 ? dm_sub(sq, b) : dm_div(c, dm_sub(dm_scl(b, -1.0), sq));
+            o = dm3_add(o, dm3_scl(d, tt));
+            n = dm3_scl(dm3_sub(C, o), dm_div(dm_c(1.0), R));
+        } else if (prim < sc.tri_prim_base) {
+            const DevRectD &Rc = sc.rects_d[prim - sc.n_tiles];
+            const d3 nn = mkd(Rc.nx, Rc.ny, Rc.nz);
+            const Dm tt = dm_div(dm3_dotc(dm3_sub(dm3_c(mkd(Rc.ox, Rc.oy, Rc.oz)), o), nn),
+                                 dm3_dotc(d, nn));
+            o = dm3_add(o, dm3_scl(d, tt));
+            n = dm3_c(nn);
+        } else {
+            const int k_tri = prim - sc.tri_prim_base;
+            const DevTri T = load_tri(sc.tris + k_tri);
+            const d3 v0 = mkd(T.v0x, T.v0y, T.v0z), v1 = mkd(T.v1x, T.v1y, T.v1z),
+                     v2 = mkd(T.v2x, T.v2y, T.v2z);
+            const d3 ea = v1 - v0, eb = v2 - v0;
+            const d3 ngr = crossd(ea, eb);
+            const d3 ng = ngr * rsqrt64(dotd(ngr, ngr));
+            const Dm tt = dm_div(dm3_dotc(dm3_sub(dm3_c(v0), o), ng), dm3_dotc(d, ng));
+            o = dm3_add(o, dm3_scl(d, tt));
+            const DevMaterial &M = sc.materials[T.material];
+            if ((M.flags & RICH_MAT_SMOOTH) && sc.tri_normals) {
+                const Dm3 q = dm3_sub(o, dm3_c(v0));
+                const double d00 = dotd(ea, ea), d01 = dotd(ea, eb), d11 = dotd(eb, eb);
+                const Dm d20 = dm3_dotc(q, ea), d21 = dm3_dotc(q, eb);
+                const double iden = rcp64(d00 * d11 - d01 * d01);
+                const Dm b1 = dm_scl(dm_sub(dm_scl(d20, d11), dm_scl(d21, d01)), iden);
+                const Dm b2 = dm_scl(dm_sub(dm_scl(d21, d00), dm_scl(d20, d01)), iden);
+                const Dm b0 = dm_sub(dm_sub(dm_c(1.0), b1), b2);
+                const float *N = sc.tri_normals + 9 * (int64_t)k_tri;
+                const Dm3 nn = dm3_add(
+                    dm3_add(dm3_scl(dm3_c(mkd(N[0], N[1], N[2])), b0),
+                            dm3_scl(dm3_c(mkd(N[3], N[4], N[5])), b1)),
+                    dm3_scl(dm3_c(mkd(N[6], N[7], N[8])), b2));
+                n = dm3_scl(nn, dm_div(dm_c(1.0), dm_sqrt(dm3_dot(nn, nn))));
+            } else {
+                n = dm3_c(ng);
+            }
+        }
+        d = dm3_reflect_unit(d, n);
+    }
+    const DevRectD &Rc = sc.rects_d[rr.det_rect];
+    const d3 nn = mkd(Rc.nx, Rc.ny, Rc.nz);
+    const d3 O = mkd(Rc.ox, Rc.oy, Rc.oz);
+    const Dm tt = dm_div(dm3_dotc(dm3_sub(dm3_c(O), o), nn), dm3_dotc(d, nn));
+    const Dm3 q = dm3_sub(dm3_add(o, dm3_scl(d, tt)), dm3_c(O));
+    u_out = dm3_dotc(q, mkd(Rc.ux, Rc.uy, Rc.uz));
+    v_out = dm3_dotc(q, mkd(Rc.vx, Rc.vy, Rc.vz));
+}
+
+constexpr int kAdjThreads = 128;
+
+__global__ void __launch_bounds__(kAdjThreads)
+k_adjoint(SceneView sc, EmitView em, TraceParams P, GradView gv, Counters *ctr) {
+    const uint64_t n_hits = ctr->hits < P.hit_capacity ? ctr->hits : P.hit_capacity;
+    double acc[2 + kNG];
+#pragma unroll
+    for (int k = 0; k < 2 + kNG; ++k) acc[k] = 0.0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_hits;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        rich_hit h = P.hits[i];
+        const RefineRec rr = P.refine[i];
+        Dm u, v;
+        replay_dual(sc, gv, em, rr, h.photon, u, v);
+        const DevRect Rc = sc.rects[rr.det_rect];
+        int ix, iy;
+        pixel_of(Rc, u.v, v.v, ix, iy);
+        h.u = u.v;
+        h.v = v.v;
+        h.ix = (uint16_t)ix;
+        h.iy = (uint16_t)iy;
+        P.hits[i] = h;
+        bin_hit(sc, P, h.event, h.plane, ix, iy);
+        const float4 tg = gv.targets[(int64_t)rr.index * gv.n_planes + h.plane];
+        if (tg.w > 0.0f) {
+            const u4 w3 = philox10(3u, h.photon, h.track, h.event, em.key0, em.key1);
+            const double u1 = ((double)(w3.x >> 8) + 0.5) * 5.9604644775390625e-8;
+            const double rr_ = sqrt(-2.0 * log(u1));
+            double s2, c2;
+            sincospi(2.0 * u24d(w3.y), &s2, &c2);
+            const Dm du = dm_add(u, dm_c(gv.sigma * rr_ * c2 - (double)tg.x));
+            const Dm dv = dm_add(v, dm_c(gv.sigma * rr_ * s2 - (double)tg.y));
+            const Dm dist = dm_sqrt(dm_add(dm_mul(du, du), dm_mul(dv, dv)));
+            const Dm rho = dm_scl(dm_sub(dist, dm_c((double)tg.z)), 1.0 / gv.sigma);
+            acc[0] += rho.v * rho.v;
+            acc[1] += 1.0;
+#pragma unroll
+            for (int k = 0; k < kNG; ++k) acc[2 + k] += 2.0 * rho.v * (double)rho.d[k];
+        }
+    }
+    // block reduction, one FP64 atomic per accumulator per block
+    __shared__ double red[kAdjThreads / 32][2 + kNG];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 2 + kNG; ++k) {
+        double x = acc[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFull, x, o);
+        if (lane == 0) red[wid][k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 + kNG) {
+        double x = 0.0;
+        for (int w = 0; w < kAdjThreads / 32; ++w) x += red[w][threadIdx.x];
+        if (x != 0.0) atomicAdd(gv.acc + threadIdx.x, x);
+    }
+}
+
+cudaError_t launch_adjoint(const SceneView &sc, const EmitView &em, const TraceParams &p,
+                           const GradView &gv, Counters *counters, int n_sm,
+                           cudaStream_t s) {
+    if (p.hit_capacity == 0) return cudaSuccess;
+    uint64_t blocks = (p.hit_capacity + kAdjThreads - 1) / kAdjThreads;
+    const uint64_t cap = (uint64_t)n_sm * 8;
+    if (blocks > cap) blocks = cap;
+    k_adjoint<<<(unsigned)blocks, kAdjThreads, 0, s>>>(sc, em, p, gv, counters);
+    return cudaGetLastError();
+}
+
 // Philox outputs for caller-given counters (reproduction of draws).
 __global__ void k_philox(const uint32_t *ctr, uint64_t n, uint32_t k0, uint32_t k1,
                          uint32_t *out) {

@@ -29,7 +29,7 @@ FATE_DETECTED = 5
 
 EXPORTED = ["rich_create", "rich_destroy", "rich_set_stream", "rich_init_geometry",
             "rich_emit", "rich_trace", "rich_hits", "rich_philox", "rich_last_error",
-            "rich_version", "rich_photon_counts_static"]
+            "rich_version", "rich_photon_counts_static", "rich_trace_grad"]
 
 # rich_hit, 40 bytes
 HIT_DTYPE = np.dtype([("event", "<u4"), ("track", "<u4"), ("photon", "<u4"),
@@ -90,6 +90,10 @@ class Outputs(C.Structure):
                 ("fate", C.c_void_p)]
 
 
+class GradParams(C.Structure):
+    _fields_ = [("tilt", C.c_float * 8), ("radius", C.c_float), ("n_minus_1", C.c_float)]
+
+
 class Stats(C.Structure):
     _fields_ = [("n_photons", C.c_uint64), ("n_hits", C.c_uint64),
                 ("n_fate", C.c_uint64 * 8), ("device_status", C.c_uint32),
@@ -126,12 +130,17 @@ def load():
         L.rich_philox.argtypes = [vp, vp, C.c_uint64, C.c_uint64, vp]
         L.rich_photon_counts_static.argtypes = [C.POINTER(TracksDesc), C.POINTER(EmitParams),
                                                 vp, vp, vp]
+        L.rich_trace_grad.argtypes = [vp, C.POINTER(TracksDesc), C.POINTER(EmitParams),
+                                      C.POINTER(GradParams), vp, C.c_float,
+                                      C.POINTER(TraceOpts), C.POINTER(Outputs),
+                                      C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                      C.POINTER(C.c_uint64)]
         L.rich_last_error.argtypes = [vp]
         L.rich_last_error.restype = C.c_char_p
         L.rich_version.restype = C.c_char_p
         for f in ("rich_create", "rich_destroy", "rich_set_stream", "rich_init_geometry",
                   "rich_emit", "rich_trace", "rich_hits", "rich_philox",
-                  "rich_photon_counts_static"):
+                  "rich_photon_counts_static", "rich_trace_grad"):
             getattr(L, f).restype = C.c_int
         _lib = L
         return L
@@ -346,6 +355,33 @@ class Context:
                                                C.c_void_p(d_out.data_ptr())))
         return d_out.cpu().numpy().view(np.uint32).reshape(-1, 4)
 
+    def trace_grad(self, tracks: DeviceTracks, theta, targets, outputs: TraceOutputs,
+                   sigma=1.0, seed=0, lambda_min=200.0, lambda_max=600.0, max_bounces=8,
+                   max_steps=16, t_min=1e-3, **launch):
+        """Soft ring chi^2 loss, its gradient (10) and the number of hits used
+        at theta = (8 tile tilts, radius of curvature, n - 1). targets: device
+        float32 tensor [n_tracks][n_planes][4]."""
+        th = [float(x) for x in theta]
+        gp = GradParams(tilt=(C.c_float * 8)(*th[:8]), radius=th[8], n_minus_1=th[9])
+        prm = EmitParams(seed=int(seed), n_minus_1=th[9], lambda_min=float(lambda_min),
+                         lambda_max=float(lambda_max))
+        o = TraceOpts(seed=0, precision=PREC_REFINE64, max_bounces=max_bounces,
+                      max_steps=max_steps, t_min=t_min,
+                      block_threads=launch.get("block_threads", 0),
+                      blocks_per_sm=launch.get("blocks_per_sm", 0),
+                      refill_min=launch.get("refill_min", 0), chunk=launch.get("chunk", 0),
+                      wide_regs=launch.get("wide_regs", 0),
+                      bvh_smem_nodes=launch.get("bvh_smem_nodes", -1))
+        g = (C.c_double * 10)()
+        loss = C.c_double(0.0)
+        used = C.c_uint64(0)
+        st = load().rich_trace_grad(self.handle, C.byref(tracks.desc()), C.byref(prm),
+                                    C.byref(gp), C.c_void_p(targets.data_ptr()),
+                                    float(sigma), C.byref(o), C.byref(outputs.desc()), g,
+                                    C.byref(loss), C.byref(used))
+        _check(self.handle, st)
+        return float(loss.value), np.array(g[:], np.float64), int(used.value)
+
     def hits(self, allow_overflow=False):
         """Returns (n_hits, stats dict); synchronises the context stream."""
         n = C.c_uint64(0)
@@ -404,3 +440,31 @@ def rich_photon_counts_static(tracks: DeviceTracks, n_minus_1, counts, offsets,
 
 def rich_version() -> str:
     return load().rich_version().decode()
+
+
+def ring_chi2(ctx: Context, theta, tracks: DeviceTracks, targets, outputs: TraceOutputs,
+              sigma=1.0, seed=0):
+    """Differentiable soft ring chi^2: a torch.autograd.Function over the
+    10 parameters (8 tile tilts, radius of curvature, n - 1); its backward
+    is the gradient from rich_trace_grad's adjoint pass."""
+    torch = _torch()
+
+    class _RingChi2(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, th):
+            loss, grad, used = ctx.trace_grad(tracks, th.detach().cpu().tolist(), targets,
+                                              outputs, sigma=sigma, seed=seed)
+            fctx.save_for_backward(torch.tensor(grad, dtype=th.dtype, device=th.device))
+            fctx.n_used = used
+            return th.new_tensor(loss)
+
+        @staticmethod
+        def backward(fctx, gout):
+            (grad,) = fctx.saved_tensors
+            return gout * grad
+
+    return _RingChi2.apply(theta)
+
+
+def rich_trace_grad(ctx: Context, tracks, theta, targets, outputs, **kw):
+    return ctx.trace_grad(tracks, theta, targets, outputs, **kw)

@@ -703,9 +703,10 @@ def ring_targets(n_tracks, n_planes, track_index, plane, u, v, min_hits=10):
 def adjoint_workload(n_tracks=200, photons_per_track=5000, seed=0) -> Workload:
     """The gradient configuration: the RICH1-like geometry with analytic
     tiles and flat mirrors, n_tracks pion tracks with a fixed photon count
-    each (1e6 photons by default)."""
+    each (1e6 photons by default); momenta from 3 GeV/c so every track is
+    above the 2.64 GeV/c Cherenkov threshold of C4F10."""
     return Workload("adjoint", rich1_scene(meshed=False),
-                    pion_tracks(n_tracks, seed=seed, n_fixed=photons_per_track),
+                    pion_tracks(n_tracks, seed=seed, n_fixed=photons_per_track, p_min=3.0),
                     n_minus_1=0.0014, seed=seed,
                     description=f"{n_tracks} pion tracks x {photons_per_track} photons, "
                     "RICH1-like analytic geometry, 10 parameters")

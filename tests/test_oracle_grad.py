@@ -96,3 +96,26 @@ def test_dual_gradient_matches_finite_differences(oracle_lib, at_nominal):
     # every tile tilt reaches the loss at the tilted point
     if not at_nominal:
         assert np.all(np.abs(g[:8]) > 0)
+
+
+def test_replay_reproduces_forward_hits(oracle_lib):
+    """The value part of the dual replay along a photon's recorded surfaces
+    equals the forward trace's hit, including photons of a fixed-count track
+    below the Cherenkov threshold (they leave along the track)."""
+    tr = W.pion_tracks(6, seed=2, n_fixed=300)
+    tr.p[0] = 2.0                     # below the 2.64 GeV/c threshold
+    wl = W.Workload("g", W.rich1_scene(meshed=False), tr, n_minus_1=0.0014)
+    sc = oracle_lib.Scene(wl.scene)
+    prm = oracle_lib.params(wl)
+    th = W.nominal_theta(wl.scene, wl.n_minus_1)
+    out = sc.trace(wl.tracks, prm)
+    off = out["offsets"].astype(np.int64)
+    checked = 0
+    for g in np.nonzero(out["fate"] == 5)[0][::7]:
+        t = int(np.searchsorted(off, g, side="right") - 1)
+        fate, u, v, du, dv = sc.hit_jacobian(wl.tracks, prm, th, t, int(g - off[t]))
+        assert fate == 5
+        assert abs(u - out["u"][g]) < 1e-9 and abs(v - out["v"][g]) < 1e-9
+        assert np.all(np.isfinite(du)) and np.all(np.isfinite(dv))
+        checked += 1
+    assert checked > 20
