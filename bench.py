@@ -207,9 +207,12 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
+    from paper_2309_12496_gb300 import autotune
+    knobs, _, _ = autotune.tune(ctx, out, n0, prec)
+
     def step(seed):
         ctx.emit(dt, 0.0014, seed=seed, sync=False)
-        ctx.trace(out, precision=prec)
+        ctx.trace(out, precision=prec, **knobs)
 
     for k in range(args.warmup):
         out.clear()
@@ -239,7 +242,7 @@ def main():
         a.record(stream)
         ctx.emit(dt, 0.0014, seed=s, sync=False)
         b.record(stream)
-        ctx.trace(out, precision=prec)
+        ctx.trace(out, precision=prec, **knobs)
         c.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -287,11 +290,12 @@ def main():
             "config": {"workload": WORKLOAD, "tracks": N_TRACKS,
                        "photons_per_step": int(ph_step), "triangles": scene.n_triangles,
                        "precision": args.precision, "parallelism": f"replicas x{ws}",
+                       "launch": knobs,
                        "l2": "flushed before every timed step (256 MiB write)"},
             "kernel_ms": {"emit": statistics.mean([a.elapsed_time(b) for a, b, _ in ev]),
                           "trace": t_trace * 1e3},
             "hits_per_step": n_hits_last,
-            "gpu_launches": 3 * args.steps,
+            "gpu_launches": (4 if prec == rich.PREC_REFINE64 else 3) * args.steps,
             "roofline": roof,
             "clocks": clk,
         }
@@ -301,6 +305,7 @@ def main():
             line["e2e"] = e2e
             line["batched"] = run_batched(dev, prec, rank)
             line["adjoint"] = run_adjoint(dev, rank)
+            line["rich2_chunked"] = run_chunked(dev, rank)
     if line is not None and not args.no_extras and ws == 1:
         v, cores, passes, nph, el = oracle_rate(10.0)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -346,16 +351,61 @@ def run_batched(dev, prec, rank, n_events=4096):
     out = rich.TraceOutputs(int(n * 0.2) + 1024, wl.scene.pixels_per_event,
                             len(wl.scene.planes), n_events, 0, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
-
-    def step():
-        ctx.emit(dt, wl.n_minus_1, seed=wl.seed, sync=False)
-        ctx.trace(out, precision=prec)
-    ms = _time_steps(step, 3, 2, flush)
+    # one emit + one persistent trace launch (+ refinement) captured as a
+    # CUDA graph, replayed per step
+    ctx.graph_capture(dt, out, wl.n_minus_1, seed=wl.seed, precision=prec)
+    ms = _time_steps(ctx.graph_launch, 3, 2, flush)
     n_hits, _ = ctx.hits()
     ctx.close()
     return {"value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "photons_per_step": n,
             "events": n_events, "tracks": wl.tracks.n, "hits_per_step": n_hits,
-            "histogram_bytes": n_events * wl.scene.pixels_per_event * 4}
+            "histogram_bytes": n_events * wl.scene.pixels_per_event * 4,
+            "launch": "CUDA graph: yield + scan + counter reset + persistent trace + refine"}
+
+
+def run_chunked(dev, rank, n_chunks=10, tracks_per_chunk=490_000):
+    """RICH2-like throughput: CF4 (n = 1.0005), 2000 mm, 56 hexagonal tiles
+    + flats + support (148,872 triangles), two 512 x 512 planes; 10 chunks
+    of ~1e8 photons (490k tracks each, keyed by chunk), refined hits,
+    histograms accumulated over the chunks. The chunk index and the
+    accumulated histograms are the whole state needed to resume."""
+    import torch
+    from paper_2309_12496_gb300 import rich
+    from paper_2309_12496_gb300 import workloads as W
+    scene = W.rich2_scene(meshed=True)
+    ctx = rich.Context(int(dev.split(":")[1]))
+    ctx.init_geometry(scene)
+    chunks = []
+    for c in range(n_chunks):
+        tr = W.pion_tracks(tracks_per_chunk, seed=10_000 * rank + c, length=2000.0,
+                           max_angle=0.15)
+        tr.event[:] = 0
+        tr.id[:] = np.arange(tracks_per_chunk) + c * tracks_per_chunk
+        chunks.append(rich.DeviceTracks(tr, device=dev))
+    n_first = ctx.emit(chunks[0], 0.0005, seed=7)
+    out = rich.TraceOutputs(int(n_first * 0.2) + 1024, scene.pixels_per_event,
+                            len(scene.planes), 1, 0, device=dev)
+    ctx.trace(out, precision=rich.PREC_REFINE64)
+    torch.cuda.synchronize()
+    out.clear()
+    st = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    photons = 0
+    hits = 0
+    counts = [ctx.emit(ch, 0.0005, seed=7) for ch in chunks]
+    torch.cuda.synchronize()
+    a.record(st)
+    for ch in chunks:
+        ctx.emit(ch, 0.0005, seed=7, sync=False)
+        ctx.trace(out, precision=rich.PREC_REFINE64)
+    b.record(st)
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    photons = sum(counts)
+    hits = int(out.pixel_counts.sum())
+    ctx.close()
+    return {"value": photons / (ms / 1e3), "unit": UNIT, "ms_total": ms, "photons": photons,
+            "chunks": n_chunks, "binned_hits": hits, "triangles": scene.n_triangles}
 
 
 def run_adjoint(dev, rank):

@@ -348,6 +348,25 @@ RICH_API rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
  * error recorded during the trace. */
 RICH_API rich_status rich_hits(rich_ctx *ctx, uint64_t *n_hits, rich_stats *stats);
 
+/* Batched launch as a CUDA graph: captures rich_emit(tracks, params) +
+ * rich_trace(fused photons, opts, out) -- the yield and scan kernels, the
+ * counter reset, the persistent trace launch and the refinement pass -- into
+ * one graph owned by the context, after an uncaptured warm-up pass that
+ * makes every allocation (the pass is also a full trace: its results are in
+ * out). The graph keeps the pointers it was captured with: the caller's
+ * track and output buffers must stay valid; replays see their current
+ * contents (new track values, same count). Outputs accumulate across
+ * replays unless the caller clears them. Replaces any earlier graph.
+ * Synchronous. */
+RICH_API rich_status rich_graph_capture(rich_ctx *ctx, const rich_tracks *tracks,
+                                        const rich_emit_params *params,
+                                        const rich_trace_opts *opts,
+                                        const rich_outputs *out);
+
+/* Replays the captured graph on the context's stream (asynchronous); read
+ * the counters with rich_hits. */
+RICH_API rich_status rich_graph_launch(rich_ctx *ctx);
+
 /* Parameters of the gradient (10 scalars).
  *   tilt[2k], tilt[2k+1]: rotation of sphere tile k (k = 0..3, descriptor
  *     order) about the axis through its pole parallel to its nominal e1,

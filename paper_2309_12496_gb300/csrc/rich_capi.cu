@@ -60,6 +60,11 @@ struct rich_ctx {
     void *d_grad_tiles = nullptr;          // groups + tiles at theta
     double *d_acc = nullptr;               // 12 FP64 accumulators
     double *h_acc = nullptr;               // pinned
+    // captured emit + trace (CUDA graph) and the stream it was captured on
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    uint64_t graph_capacity = 0;
 };
 
 static thread_local std::string g_create_error;
@@ -333,6 +338,9 @@ RICH_API rich_status rich_destroy(rich_ctx *ctx) {
         cudaFree(ctx->d_refine);
         cudaFree(ctx->d_tile_nom);
         cudaFree(ctx->d_grad_tiles);
+        if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+        if (ctx->graph) cudaGraphDestroy(ctx->graph);
+        if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
         cudaFree(ctx->d_acc);
         cudaFreeHost(ctx->h_acc);
         free_emission(ctx);
@@ -868,6 +876,59 @@ RICH_API rich_status rich_trace_grad(rich_ctx *ctx, const rich_tracks *t,
                     "rich_trace_grad: " + std::to_string(ctx->h_ctr->hits) +
                         " hits for capacity " + std::to_string(hit_cap) +
                         " (hits beyond it are not in the gradient)");
+    return RICH_OK;
+}
+
+RICH_API rich_status rich_graph_capture(rich_ctx *ctx, const rich_tracks *t,
+                                        const rich_emit_params *prm,
+                                        const rich_trace_opts *o, const rich_outputs *out) {
+    if (!ctx) return RICH_ERR_ARG;
+    if (!t || !prm || !o || !out)
+        return fail(ctx, RICH_ERR_ARG, "rich_graph_capture: NULL argument");
+    DeviceGuard guard(ctx->device);
+    // warm-up pass: allocates scratch and fills the launch caches so the
+    // captured pass makes no allocation and no synchronising call
+    rich_status st = rich_emit(ctx, t, prm, nullptr, nullptr);
+    if (st == RICH_OK) st = rich_trace(ctx, nullptr, o, out);
+    if (st != RICH_OK) return st;
+    RICH_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (!ctx->capture_stream)
+        RICH_CUDA(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+    if (ctx->graph_exec) {
+        cudaGraphExecDestroy(ctx->graph_exec);
+        ctx->graph_exec = nullptr;
+    }
+    if (ctx->graph) {
+        cudaGraphDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    cudaStream_t user = ctx->stream;
+    ctx->stream = ctx->capture_stream;
+    RICH_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    st = rich_emit(ctx, t, prm, nullptr, nullptr);
+    if (st == RICH_OK) st = rich_trace(ctx, nullptr, o, out);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    ctx->stream = user;
+    if (st != RICH_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+    ctx->graph = g;
+    RICH_CUDA(cudaGraphInstantiate(&ctx->graph_exec, g, 0));
+    ctx->graph_capacity = out->hits ? out->hit_capacity : 0;
+    return RICH_OK;
+}
+
+RICH_API rich_status rich_graph_launch(rich_ctx *ctx) {
+    if (!ctx) return RICH_ERR_ARG;
+    if (!ctx->graph_exec) return fail(ctx, RICH_ERR_STATE, "rich_graph_launch: nothing captured");
+    DeviceGuard guard(ctx->device);
+    RICH_CUDA(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
+    ctx->traced = true;
+    ctx->last_ext = false;
+    ctx->last_capacity = ctx->graph_capacity;
     return RICH_OK;
 }
 

@@ -1497,10 +1497,14 @@ template <bool EXT, bool REFINE, int THREADS, int MINB>
 static cudaError_t launch_trace_t(const TraceArgs &a, const LaunchShape &shape,
                                   cudaStream_t s) {
     auto kern = k_trace<EXT, REFINE, THREADS, MINB>;
-    if (shape.smem > 48 * 1024) {
+    // raise the dynamic shared-memory limit once per variant and size (the
+    // attribute persists; a captured replay then issues no such call)
+    static size_t raised = 48 * 1024;
+    if (shape.smem > raised) {
         cudaError_t e = cudaFuncSetAttribute(
             kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shape.smem);
         if (e != cudaSuccess) return e;
+        raised = shape.smem;
     }
     kern<<<shape.blocks, shape.threads, shape.smem, s>>>(a);
     return cudaGetLastError();

@@ -29,7 +29,8 @@ FATE_DETECTED = 5
 
 EXPORTED = ["rich_create", "rich_destroy", "rich_set_stream", "rich_init_geometry",
             "rich_emit", "rich_trace", "rich_hits", "rich_philox", "rich_last_error",
-            "rich_version", "rich_photon_counts_static", "rich_trace_grad"]
+            "rich_version", "rich_photon_counts_static", "rich_trace_grad",
+            "rich_graph_capture", "rich_graph_launch"]
 
 # rich_hit, 40 bytes
 HIT_DTYPE = np.dtype([("event", "<u4"), ("track", "<u4"), ("photon", "<u4"),
@@ -130,6 +131,9 @@ def load():
         L.rich_philox.argtypes = [vp, vp, C.c_uint64, C.c_uint64, vp]
         L.rich_photon_counts_static.argtypes = [C.POINTER(TracksDesc), C.POINTER(EmitParams),
                                                 vp, vp, vp]
+        L.rich_graph_capture.argtypes = [vp, C.POINTER(TracksDesc), C.POINTER(EmitParams),
+                                         C.POINTER(TraceOpts), C.POINTER(Outputs)]
+        L.rich_graph_launch.argtypes = [vp]
         L.rich_trace_grad.argtypes = [vp, C.POINTER(TracksDesc), C.POINTER(EmitParams),
                                       C.POINTER(GradParams), vp, C.c_float,
                                       C.POINTER(TraceOpts), C.POINTER(Outputs),
@@ -140,7 +144,8 @@ def load():
         L.rich_version.restype = C.c_char_p
         for f in ("rich_create", "rich_destroy", "rich_set_stream", "rich_init_geometry",
                   "rich_emit", "rich_trace", "rich_hits", "rich_philox",
-                  "rich_photon_counts_static", "rich_trace_grad"):
+                  "rich_photon_counts_static", "rich_trace_grad", "rich_graph_capture",
+                  "rich_graph_launch"):
             getattr(L, f).restype = C.c_int
         _lib = L
         return L
@@ -354,6 +359,26 @@ class Context:
                                                len(ctr), int(seed),
                                                C.c_void_p(d_out.data_ptr())))
         return d_out.cpu().numpy().view(np.uint32).reshape(-1, 4)
+
+    def graph_capture(self, tracks: DeviceTracks, outputs: TraceOutputs, n_minus_1,
+                      lambda_min=200.0, lambda_max=600.0, seed=0, precision=PREC_REFINE64,
+                      max_bounces=8, max_steps=16, t_min=1e-3, block_threads=0,
+                      blocks_per_sm=0, refill_min=0, chunk=0, wide_regs=0,
+                      bvh_smem_nodes=-1):
+        """Capture emit + trace into a CUDA graph (after a warm-up pass)."""
+        prm = EmitParams(seed=int(seed), n_minus_1=float(n_minus_1),
+                         lambda_min=float(lambda_min), lambda_max=float(lambda_max))
+        o = TraceOpts(seed=0, precision=precision, max_bounces=max_bounces,
+                      max_steps=max_steps, t_min=t_min, block_threads=block_threads,
+                      blocks_per_sm=blocks_per_sm, refill_min=refill_min, chunk=chunk,
+                      wide_regs=wide_regs, bvh_smem_nodes=bvh_smem_nodes)
+        self._graph_keep = (tracks, outputs)
+        _check(self.handle, load().rich_graph_capture(self.handle, C.byref(tracks.desc()),
+                                                      C.byref(prm), C.byref(o),
+                                                      C.byref(outputs.desc())))
+
+    def graph_launch(self):
+        _check(self.handle, load().rich_graph_launch(self.handle))
 
     def trace_grad(self, tracks: DeviceTracks, theta, targets, outputs: TraceOutputs,
                    sigma=1.0, seed=0, lambda_min=200.0, lambda_max=600.0, max_bounces=8,

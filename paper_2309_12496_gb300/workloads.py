@@ -673,30 +673,37 @@ def rich2(n_tracks=330_000, seed=0, meshed=True) -> Workload:
 
 # ------------------------------------------------------------- ring targets
 def ring_targets(n_tracks, n_planes, track_index, plane, u, v, min_hits=10):
-    """Expected ring of every (track, plane) from a set of hits: centre =
-    mean hit position, radius = mean distance to it; weight 1 when at least
-    min_hits hits define it, else 0. Returns float32 [n_tracks][n_planes][4]
-    = (cu, cv, r, weight), the targets of the soft ring chi^2."""
+    """Expected ring of every (track, plane) from a set of hits: the
+    algebraic least-squares circle (Kasa's fit: u^2 + v^2 + D u + E v + F
+    = 0 solved linearly, centre (-D/2, -E/2), radius sqrt(|c|^2 - F)),
+    which recovers centre and radius from partial arcs; weight 1 when at
+    least min_hits hits define it, else 0. Returns float32
+    [n_tracks][n_planes][4] = (cu, cv, r, weight), the targets of the soft
+    ring chi^2."""
     out = np.zeros((n_tracks, n_planes, 4), np.float64)
     key = np.asarray(track_index, np.int64) * n_planes + np.asarray(plane, np.int64)
     u = np.asarray(u, np.float64)
     v = np.asarray(v, np.float64)
-    cnt = np.bincount(key, minlength=n_tracks * n_planes).astype(np.float64)
-    su = np.bincount(key, u, minlength=n_tracks * n_planes)
-    sv = np.bincount(key, v, minlength=n_tracks * n_planes)
-    with np.errstate(invalid="ignore", divide="ignore"):
-        cu = su / cnt
-        cv = sv / cnt
-    dist = np.hypot(u - cu[key], v - cv[key])
-    sr = np.bincount(key, dist, minlength=n_tracks * n_planes)
-    with np.errstate(invalid="ignore", divide="ignore"):
-        r = sr / cnt
-    ok = cnt >= min_hits
+    order = np.argsort(key, kind="stable")
+    ks, us, vs = key[order], u[order], v[order]
+    bounds = np.flatnonzero(np.diff(ks)) + 1
+    starts = np.concatenate([[0], bounds])
+    ends = np.concatenate([bounds, [len(ks)]])
     flat = out.reshape(-1, 4)
-    flat[ok, 0] = cu[ok]
-    flat[ok, 1] = cv[ok]
-    flat[ok, 2] = r[ok]
-    flat[ok, 3] = 1.0
+    for a, b in zip(starts, ends):
+        if b - a < min_hits:
+            continue
+        uu, vv = us[a:b], vs[a:b]
+        mu, mv = uu.mean(), vv.mean()          # centre the fit for conditioning
+        x, y = uu - mu, vv - mv
+        A = np.stack([x, y, np.ones_like(x)], axis=1)
+        rhs = -(x * x + y * y)
+        (D, E, F), *_ = np.linalg.lstsq(A, rhs, rcond=None)
+        cx, cy = -D / 2.0, -E / 2.0
+        r2 = cx * cx + cy * cy - F
+        if not (r2 > 0.0):
+            continue
+        flat[ks[a], :] = (cx + mu, cy + mv, np.sqrt(r2), 1.0)
     return out.astype(np.float32)
 
 
