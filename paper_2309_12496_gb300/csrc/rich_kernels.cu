@@ -25,8 +25,10 @@ namespace rich {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kYieldThreads = 256;   // tracks per scan group / scan block
-constexpr int kYieldBlock = 64;      // threads per yield block (spreads the
-                                     // FP64 Poisson work over more SMs)
+constexpr int kYieldBlock = 32;      // threads per yield block: one warp, so
+                                     // the FP64 Poisson chains of a small
+                                     // batch spread over as many SMs as
+                                     // possible (2 FP64 lanes per SM)
 constexpr double kAlpha = 1.0 / 137.035999;
 constexpr double kPi = 3.14159265358979323846;
 
@@ -54,9 +56,21 @@ struct TrackStream {
     }
 };
 
+// log Gamma(x) for x >= 10 by Stirling's series with four correction terms
+// (truncation < 1/(1188 x^9), below 1e-12 at x = 10).
+__device__ __forceinline__ double lgamma_stirling(double x) {
+    constexpr double kHalfLog2Pi = 0.91893853320467274178;
+    const double r = rcp64(x), r2 = r * r;
+    const double series = r * (1.0 / 12.0 - r2 * (1.0 / 360.0 - r2 * (1.0 / 1260.0 -
+                                                                     r2 * (1.0 / 1680.0))));
+    return (x - 0.5) * log(x) - x + kHalfLog2Pi + series;
+}
+
 // Poisson(mu): CDF inversion (smallest k with u < F(k)) below mean 10; the
 // PTRS transformed rejection sampler (Hoermann 1993) above, at most 64
-// trials, then round(mu).
+// trials, then round(mu). The GPU's FP64 pipe is slow, so the rejection
+// test log V + log(1/alpha) - log(a/us^2 + b) <= -mu + k log mu - log k! is
+// taken with one log on the left and Stirling's series for log k! (k >= 9).
 __device__ int64_t poisson_draw(double mu, TrackStream &s) {
     if (!(mu > 0.0)) return 0;
     if (mu < 10.0) {
@@ -70,11 +84,13 @@ __device__ int64_t poisson_draw(double mu, TrackStream &s) {
         }
         return k;
     }
-    double smu = sqrt(mu), lmu = log(mu);
-    double b = 0.931 + 2.53 * smu;
-    double a = -0.059 + 0.02483 * b;
-    double inv_alpha = 1.1239 + 1.1328 / (b - 3.4);
-    double v_r = 0.9277 - 3.6224 / (b - 2.0);
+    // per-track constants in IEEE arithmetic (they set the candidate k and
+    // the quick-accept bound); only the per-trial tail uses Newton reciprocals
+    const double smu = sqrt(mu), lmu = log(mu);
+    const double b = 0.931 + 2.53 * smu;
+    const double a = -0.059 + 0.02483 * b;
+    const double inv_alpha = 1.1239 + 1.1328 / (b - 3.4);
+    const double v_r = 0.9277 - 3.6224 / (b - 2.0);
     for (int trial = 0; trial < 64; ++trial) {
         double U = s.next() - 0.5;
         double V = s.next();
@@ -84,8 +100,9 @@ __device__ int64_t poisson_draw(double mu, TrackStream &s) {
         if (!(kd >= 0.0)) continue;
         if (us >= 0.07 && V <= v_r) return (int64_t)kd;
         if (us < 0.013 && V > us) continue;
-        double lhs = log(V) + log(inv_alpha) - log(a / (us * us) + b);
-        double rhs = -mu + kd * lmu - lgamma(kd + 1.0);
+        const double lhs = log(V * inv_alpha * rcp64(a * rcp64(us * us) + b));
+        const double lg = kd >= 9.0 ? lgamma_stirling(kd + 1.0) : lgamma(kd + 1.0);
+        const double rhs = -mu + kd * lmu - lg;
         if (lhs <= rhs) return (int64_t)kd;
     }
     return (int64_t)floor(mu + 0.5);
@@ -125,7 +142,7 @@ k_yield(TracksView t, double n_minus_1, double inv_band_mm, uint32_t key0,
         }
         if (RECS) {
         double dx = t.dx[i], dy = t.dy[i], dz = t.dz[i];
-        double inv = 1.0 / sqrt(dx * dx + dy * dy + dz * dz);
+        double inv = rsqrt64(dx * dx + dy * dy + dz * dz);
         TrackRec r;
         r.x = t.x[i];
         r.y = t.y[i];

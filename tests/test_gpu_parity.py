@@ -87,6 +87,34 @@ def test_emission_matches_oracle():
     ctx.close()
 
 
+def test_poisson_counts_over_wide_mean_range():
+    """Photon counts of 500,000 tracks whose Frank-Tamm means span 0 to ~3000
+    (CDF inversion below 10, PTRS above) equal the oracle's exactly. Both
+    draw in FP64; the kernel's per-trial tail (one log, Stirling's series
+    for log k!, Newton reciprocals) differs from the oracle's textbook forms
+    by ~1e-13, so a count could differ only if a rejection test fell that
+    close to its threshold."""
+    n = 500_000
+    rng = np.random.default_rng(11)
+    tr = W.pion_tracks(n, seed=11, p_min=0.3, p_max=100.0)
+    tr.length[:] = (np.exp(rng.uniform(np.log(1.0), np.log(9000.0), n))).astype(tr.length.dtype)
+    dt = rich.DeviceTracks(tr)
+    counts = torch.empty(n, dtype=torch.int32, device="cuda")
+    offsets = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    for seed in (1, 0xDEADBEEF12345):
+        rich.rich_photon_counts_static(dt, 0.0014, counts, offsets, seed=seed)
+        torch.cuda.synchronize()
+        got = counts.cpu().numpy().view(np.uint32)
+        ref, mu, off = oracle.track_yield(tr, oracle.params(seed=seed, n_minus_1=0.0014,
+                                                            lambda_min=200.0, lambda_max=600.0))
+        report("poisson_wide", {"seed": seed, "tracks": n, "mu_max": float(mu.max()),
+                                "below_10": int((mu < 10).sum()),
+                                "mismatches": int((got != ref).sum())})
+        assert mu.max() > 2000 and (mu < 10).sum() > 10_000 and (mu == 0).sum() > 1000
+        np.testing.assert_array_equal(got, ref)
+        assert int(offsets[-1]) == int(off[-1])
+
+
 # --------------------------------------------------------------- point source
 @pytest.mark.parametrize("precision", [rich.PREC_REFINE64, rich.PREC_FP32])
 def test_point_source_parity(precision):
