@@ -232,7 +232,9 @@ typedef struct rich_trace_opts {
                                idle (1..32): the compaction interval          */
     int32_t chunk;          /* photons a warp takes from the queue at a time */
     int32_t wide_regs;      /* <= 256 threads: 0 caps the trace kernel at 64
-                               registers (four blocks per SM), 1 uncapped    */
+                               registers (four blocks per SM), 1 uncapped;
+                               257..768 threads: 1 caps it at 80 registers
+                               (0: the 1024-thread variant, 64 registers)   */
     int32_t bvh_smem_nodes; /* top BVH nodes staged in shared memory per block
                                by a TMA bulk copy (-1: default)              */
 } rich_trace_opts;

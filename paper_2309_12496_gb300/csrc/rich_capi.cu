@@ -151,6 +151,10 @@ bool group_tiles(const rich_sphere *sp, int n, int n_materials,
         G.cx = std::get<0>(spheres[gi]);
         G.cy = std::get<1>(spheres[gi]);
         G.cz = std::get<2>(spheres[gi]);
+        G.fcx = (float)G.cx;
+        G.fcy = (float)G.cy;
+        G.fcz = (float)G.cz;
+        G.pad = 0.0f;
         const double R = std::get<3>(spheres[gi]);
         G.r2 = R * R;
         G.radius = (float)R;

@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include "rich_device.cuh"
+#include "rich_ff.cuh"
 
 namespace rich {
 
@@ -497,6 +498,12 @@ __device__ __forceinline__ void leaf_tris(const SceneView &sc, const Ray &r,
         b.prim = T.prim;
         b.kind = 2;
         b.idx = k;
+        if (sc.tri_normals) {
+            // the shading step reads this triangle's vertex normals next
+            const float *nrm = sc.tri_normals + 9 * (int64_t)k;
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(nrm));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(nrm + 8));
+        }
         b.b0 = b0;
         b.b1 = b1;
         b.b2 = b2;
@@ -585,93 +592,121 @@ __device__ void nearest_bvh(const SceneView &sc, const DevNode *snodes, int n_sn
     }
 }
 
-// ============================================================ FP64 replay
+// ======================================================= refinement replay
 // Refinement of a detected photon: the recorded sequence of reflecting
-// primitives is replayed in FP64 (emission, each reflection on the same
-// primitive's surface extended past its edges, the final plane), giving
-// the hit position and pixel in FP64. Runs in its own pass (k_refine), one
-// thread per stored hit, so the slow FP64 pipe sees converged warps.
-__device__ void replay64(const SceneView &sc, const d3 o0, const d3 d0,
-                         const RefineRec &rr, double &u, double &v) {
-    d3 o = o0, d = d0;
+// primitives is replayed in double-word arithmetic (about 48 bits, see
+// rich_ff.cuh): emission, each reflection on the same primitive's surface
+// extended past its edges, the final plane. All geometry is FP32 input, so
+// it enters the replay exactly. Runs in its own pass (k_refine), one thread
+// per stored hit, so the warps are converged.
+__device__ void replay_ff(const SceneView &sc, ff3 o, ff3 d, const RefineRec &rr, ff &u,
+                          ff &v) {
     for (int k = 0; k < rr.n_path; ++k) {
         const int prim = rr.path[k];
-        d3 n;
+        ff3 n;
         if (prim < sc.n_tiles) {
             int ti = 0;
             for (int q = 0; q < sc.n_tiles; ++q)
                 if (sc.tiles[q].prim == prim) ti = q;
             const DevSphereGroup &G = sc.groups[sc.tiles[ti].group];
-            const d3 w = o - mkd(G.cx, G.cy, G.cz);
-            const double bq = dotd(w, d);
-            const double c = dotd(w, w) - G.r2;
-            const double disc = fmax(0.0, fma(bq, bq, -c));
-            const double sq = disc > 0.0 ? disc * rsqrt64(disc) : 0.0;
+            const ff3 C = ff3v(G.fcx, G.fcy, G.fcz);
+            const ff3 w = ff3_sub(o, C);
+            const ff bq = ff3_dot(w, d);
+            const ff c = ff_sub(ff3_dot(w, w), two_prod(G.radius, G.radius));
+            const ff disc = ff_sub(ff_mul(bq, bq), c);
+            const ff sq = ff_sqrt(disc);
             // concave (front) side: the exit root -b + sqrt(disc), taken in
             // the form free of cancellation
-            const double t = bq <= 0.0 ? (sq - bq) : c * rcp64(-bq - sq);
-            o = mkd(fma(d.x, t, o.x), fma(d.y, t, o.y), fma(d.z, t, o.z));
-            const d3 pc = o - mkd(G.cx, G.cy, G.cz);
-            n = pc * -rsqrt64(dotd(pc, pc));
+            const ff t = bq.hi <= 0.0f ? ff_sub(sq, bq) : ff_div(c, ff_sub(ff_neg(bq), sq));
+            o = ff3_axpy(t, d, o);
+            const ff3 pc = ff3_sub(o, C);
+            n = ff3_scale(pc, ff_neg(ff_rsqrt(ff3_dot(pc, pc))));
         } else if (prim < sc.tri_prim_base) {
-            const DevRectD &R = sc.rects_d[prim - sc.n_tiles];
-            n = mkd(R.nx, R.ny, R.nz);
-            const double t = dotd(mkd(R.ox, R.oy, R.oz) - o, n) * rcp64(dotd(d, n));
-            o = mkd(fma(d.x, t, o.x), fma(d.y, t, o.y), fma(d.z, t, o.z));
+            const DevRect &R = sc.rects[prim - sc.n_tiles];
+            n = ff3v(R.nx, R.ny, R.nz);
+            const ff t = ff_div(ff3_dot(ff3_sub(ff3v(R.ox, R.oy, R.oz), o), n), ff3_dot(d, n));
+            o = ff3_axpy(t, d, o);
         } else {
             const int k_tri = prim - sc.tri_prim_base;   // leaf-order index
             const DevTri T = load_tri(sc.tris + k_tri);
-            const d3 v0 = mkd(T.v0x, T.v0y, T.v0z), v1 = mkd(T.v1x, T.v1y, T.v1z),
-                     v2 = mkd(T.v2x, T.v2y, T.v2z);
-            const d3 e1 = v1 - v0, e2 = v2 - v0;
-            const d3 ng = crossd(e1, e2);
-            const double t = dotd(v0 - o, ng) * rcp64(dotd(d, ng));
-            o = mkd(fma(d.x, t, o.x), fma(d.y, t, o.y), fma(d.z, t, o.z));
+            const ff3 v0 = ff3v(T.v0x, T.v0y, T.v0z);
+            const ff3 e1 = ff3_diff(T.v1x, T.v1y, T.v1z, T.v0x, T.v0y, T.v0z);
+            const ff3 e2 = ff3_diff(T.v2x, T.v2y, T.v2z, T.v0x, T.v0y, T.v0z);
+            const ff3 ng = ff3_cross(e1, e2);
+            const ff t = ff_div(ff3_dot(ff3_sub(v0, o), ng), ff3_dot(d, ng));
+            o = ff3_axpy(t, d, o);
             const DevMaterial &M = sc.materials[T.material];
             if ((M.flags & RICH_MAT_SMOOTH) && sc.tri_normals) {
                 // barycentrics of the hit in the triangle's plane
-                const d3 q = o - v0;
-                const double d00 = dotd(e1, e1), d01 = dotd(e1, e2), d11 = dotd(e2, e2);
-                const double d20 = dotd(q, e1), d21 = dotd(q, e2);
-                const double inv_den = rcp64(fma(d00, d11, -d01 * d01));
-                const double b1 = fma(d11, d20, -d01 * d21) * inv_den;
-                const double b2 = fma(d00, d21, -d01 * d20) * inv_den;
-                const double b0 = 1.0 - b1 - b2;
+                const ff3 q = ff3_sub(o, v0);
+                const ff d00 = ff3_dot(e1, e1), d01 = ff3_dot(e1, e2), d11 = ff3_dot(e2, e2);
+                const ff d20 = ff3_dot(q, e1), d21 = ff3_dot(q, e2);
+                const ff den = ff_sub(ff_mul(d00, d11), ff_mul(d01, d01));
+                const ff b1 = ff_div(ff_sub(ff_mul(d11, d20), ff_mul(d01, d21)), den);
+                const ff b2 = ff_div(ff_sub(ff_mul(d00, d21), ff_mul(d01, d20)), den);
+                const ff b0 = ff_sub(ff_sub(ffv(1.0f), b1), b2);
                 const float *N = sc.tri_normals + 9 * (int64_t)k_tri;
-                n = normalized(mkd(b0 * N[0] + b1 * N[3] + b2 * N[6],
-                                   b0 * N[1] + b1 * N[4] + b2 * N[7],
-                                   b0 * N[2] + b1 * N[5] + b2 * N[8]));
+                const ff3 m = ff3_add(ff3_add(ff3_scale(ff3v(N[0], N[1], N[2]), b0),
+                                              ff3_scale(ff3v(N[3], N[4], N[5]), b1)),
+                                      ff3_scale(ff3v(N[6], N[7], N[8]), b2));
+                n = ff3_normalized(m);
             } else {
-                n = normalized(ng);
+                n = ff3_normalized(ng);
             }
         }
         // |d| = 1 is kept by the reflection about a unit normal
-        d = reflect_d(d, n);
+        d = ff3_reflect(d, n);
     }
-    const DevRectD &R = sc.rects_d[rr.det_rect];
-    const d3 nrm = mkd(R.nx, R.ny, R.nz);
-    const d3 O = mkd(R.ox, R.oy, R.oz);
-    const double t = dotd(O - o, nrm) * rcp64(dotd(d, nrm));
-    const d3 q = mkd(fma(d.x, t, o.x - O.x), fma(d.y, t, o.y - O.y), fma(d.z, t, o.z - O.z));
-    u = dotd(q, mkd(R.ux, R.uy, R.uz));
-    v = dotd(q, mkd(R.vx, R.vy, R.vz));
+    const DevRect &R = sc.rects[rr.det_rect];
+    const ff3 nrm = ff3v(R.nx, R.ny, R.nz);
+    const ff3 O = ff3v(R.ox, R.oy, R.oz);
+    const ff t = ff_div(ff3_dot(ff3_sub(O, o), nrm), ff3_dot(d, nrm));
+    const ff3 q = ff3_sub(ff3_axpy(t, d, o), O);
+    u = ff3_dot(q, R.ux, R.uy, R.uz);
+    v = ff3_dot(q, R.vx, R.vy, R.vz);
 }
 
-// FP64 emission of photon j of a track (the same draws as emit_photon).
-__device__ void emit64(const TrackRec &tr, double2 cs, uint32_t j, const EmitView &em,
-                       d3 &o, d3 &d) {
+// Orthonormal basis around a unit double-word vector (the branch-free form
+// of Duff et al., JCGT 6(1) 2017, as basis_f).
+__device__ __forceinline__ void basis_ff(const ff3 &t, ff3 &e1, ff3 &e2) {
+    const float s = t.z.hi >= 0.0f ? 1.0f : -1.0f;
+    const ff a = ff_div(ffv(-1.0f), ff_add(t.z, s));
+    const ff b = ff_mul(ff_mul(t.x, t.y), a);
+    e1 = {ff_add(ff_mul(ff_mul(ff_mul(t.x, t.x), a), s), 1.0f), ff_mul(b, s),
+          ff_mul(t.x, -s)};
+    e2 = {b, ff_add(ff_mul(ff_mul(t.y, t.y), a), s), ff_neg(t.y)};
+}
+
+// Emission of photon j of a track with the same draws as emit_photon:
+// the track direction normalised, the origin at s = u L along it, the
+// azimuth 2 pi u from an FP64 sincospi, cos and sin of the Cherenkov angle
+// from the FP64 yield pass.
+__device__ void emit_ff(const TrackRec &tr, double2 cs, uint32_t j, const EmitView &em,
+                        ff3 &o, ff3 &d) {
     const u4 w0 = philox10(0u, j, tr.id, tr.event, em.key0, em.key1);
-    const d3 t = normalized(mkd(tr.rx, tr.ry, tr.rz));
-    const double s = u24d(w0.x) * (double)tr.len;
-    o = mkd(fma(t.x, s, (double)tr.x), fma(t.y, s, (double)tr.y), fma(t.z, s, (double)tr.z));
+    const ff3 t = ff3_normalized(ff3v(tr.rx, tr.ry, tr.rz));
+    const ff s = two_prod(u24f(w0.x), tr.len);      // exact: 24 x 24 bits
+    o = ff3_axpy(s, t, ff3v(tr.x, tr.y, tr.z));
     double sp, cp;
     sincospi(2.0 * u24d(w0.y), &sp, &cp);
-    d3 e1, e2;
-    basis_d(t, e1, e2);
-    const double ct = cs.x, st = cs.y;
-    d = normalized(mkd(ct * t.x + st * (cp * e1.x + sp * e2.x),
-                       ct * t.y + st * (cp * e1.y + sp * e2.y),
-                       ct * t.z + st * (cp * e1.z + sp * e2.z)));
+    ff3 e1, e2;
+    basis_ff(t, e1, e2);
+    const ff r_x = ff_add(ff_mul(e1.x, ff_from_double(cp)), ff_mul(e2.x, ff_from_double(sp)));
+    const ff r_y = ff_add(ff_mul(e1.y, ff_from_double(cp)), ff_mul(e2.y, ff_from_double(sp)));
+    const ff r_z = ff_add(ff_mul(e1.z, ff_from_double(cp)), ff_mul(e2.z, ff_from_double(sp)));
+    const ff ct = ff_from_double(cs.x), st = ff_from_double(cs.y);
+    d = ff3_normalized({ff_add(ff_mul(t.x, ct), ff_mul(r_x, st)),
+                        ff_add(ff_mul(t.y, ct), ff_mul(r_y, st)),
+                        ff_add(ff_mul(t.z, ct), ff_mul(r_z, st))});
+}
+
+// Pixel of a double-word position: floor(u / pitch), clamped to the grid.
+__device__ __forceinline__ void pixel_of_ff(const DevRect &R, ff u, ff v, int &ix, int &iy) {
+    const ff p = ffv(R.pitch);
+    ix = (int)ff_floor(ff_div(u, p));
+    iy = (int)ff_floor(ff_div(v, p));
+    ix = ix < 0 ? 0 : (ix >= R.gx ? R.gx - 1 : ix);
+    iy = iy < 0 ? 0 : (iy >= R.gy ? R.gy - 1 : iy);
 }
 
 // Sum `val` over the lanes of `peers` (lanes sharing one key) and add it
@@ -1037,10 +1072,13 @@ k_trace(TraceArgs A) {
                 hplane = S.materials[R.material].plane;
                 hu = hit_u;
                 hv = hit_v;
-                int ix, iy;
-                pixel_of(R, hu, hv, ix, iy);
                 const uint64_t slot = base + (uint64_t)__popc(dm & lt_mask);
                 const bool stored = slot < P.hit_capacity;
+                // refined hits are binned (and their pixel found, in FP64)
+                // by the refinement pass; the rest here
+                binned_here = !(REFINE && stored);
+                int ix = 0, iy = 0;
+                if (binned_here) pixel_of(R, hu, hv, ix, iy);
                 if (stored) {
                     rich_hit h;
                     h.event = ph.event;
@@ -1066,8 +1104,6 @@ k_trace(TraceArgs A) {
                         P.refine[slot] = rr;
                     }
                 }
-                // refined hits are binned by the refinement pass; the rest here
-                binned_here = !(REFINE && stored);
                 if (binned_here) bin_hit(sc, P, ph.event, hplane, ix, iy);
             }
         }
@@ -1116,17 +1152,20 @@ k_refine(SceneView sc, EmitView em, ExtView ext, TraceParams P, Counters *ctr) {
         if (on) {
             rich_hit h = P.hits[i];
             const RefineRec rr = P.refine[i];
-            d3 o, d;
+            ff3 o, d;
             if (EXT) {
                 const uint32_t g = rr.index;
-                o = mkd(ext.x[g], ext.y[g], ext.z[g]);
-                d = normalized(mkd(ext.dx[g], ext.dy[g], ext.dz[g]));
+                o = ff3v(ext.x[g], ext.y[g], ext.z[g]);
+                d = ff3_normalized(ff3v(ext.dx[g], ext.dy[g], ext.dz[g]));
             } else {
-                emit64(em.tracks[rr.index], em.cos_sin[rr.index], h.photon, em, o, d);
+                emit_ff(em.tracks[rr.index], em.cos_sin[rr.index], h.photon, em, o, d);
             }
-            replay64(sc, o, d, rr, u, v);
+            ff uf, vf;
+            replay_ff(sc, o, d, rr, uf, vf);
             int ix, iy;
-            pixel_of(sc.rects[rr.det_rect], u, v, ix, iy);
+            pixel_of_ff(sc.rects[rr.det_rect], uf, vf, ix, iy);
+            u = ff_to_double(uf);
+            v = ff_to_double(vf);
             h.u = u;
             h.v = v;
             h.ix = (uint16_t)ix;
@@ -1529,13 +1568,15 @@ static cudaError_t launch_trace_t(const TraceArgs &a, const LaunchShape &shape,
 
 // Kernel variants: caller photons or fused emission; FP64 refinement side
 // records or not; block shape class: up to 256 threads capped at 64
-// registers (4 blocks per SM), up to 256 threads uncapped, or up to 1024
-// threads (one block per SM sharing one staged copy of the BVH top).
-enum { kShape256x4 = 0, kShape256x1 = 1, kShape1024 = 2 };
+// registers (4 blocks per SM), up to 256 threads uncapped, up to 768
+// threads capped at 80 registers, or up to 1024 threads capped at 64 (one
+// block per SM sharing one staged copy of the BVH top).
+enum { kShape256x4 = 0, kShape256x1 = 1, kShape1024 = 2, kShape768 = 3 };
 
 template <bool EXT, bool REFINE>
 static const void *trace_kernel_t(int cls) {
     if (cls == kShape1024) return (const void *)k_trace<EXT, REFINE, 1024, 1>;
+    if (cls == kShape768) return (const void *)k_trace<EXT, REFINE, 768, 1>;
     if (cls == kShape256x1) return (const void *)k_trace<EXT, REFINE, 256, 1>;
     return (const void *)k_trace<EXT, REFINE, 256, 4>;
 }
@@ -1546,7 +1587,7 @@ static const void *trace_kernel(bool ext, bool refine, int cls) {
 }
 
 int trace_shape_class(int threads, bool wide) {
-    if (threads > 256) return kShape1024;
+    if (threads > 256) return (wide && threads <= 768) ? kShape768 : kShape1024;
     return wide ? kShape256x1 : kShape256x4;
 }
 
@@ -1565,6 +1606,7 @@ int trace_blocks_per_sm(bool ext, bool refine, int cls, int threads, size_t smem
 template <bool EXT, bool REFINE>
 static cudaError_t launch_cls(const TraceArgs &a, const LaunchShape &shape, cudaStream_t s) {
     if (shape.cls == kShape1024) return launch_trace_t<EXT, REFINE, 1024, 1>(a, shape, s);
+    if (shape.cls == kShape768) return launch_trace_t<EXT, REFINE, 768, 1>(a, shape, s);
     if (shape.cls == kShape256x1) return launch_trace_t<EXT, REFINE, 256, 1>(a, shape, s);
     return launch_trace_t<EXT, REFINE, 256, 4>(a, shape, s);
 }
