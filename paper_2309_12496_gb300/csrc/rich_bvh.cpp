@@ -21,10 +21,6 @@ namespace {
 constexpr int kBins = 12;
 constexpr int kMaxLeaf = 8;
 constexpr float kTraversalCost = 1.0f;
-#ifndef RICH_WIDE_LEAF
-#define RICH_WIDE_LEAF 4
-#endif
-constexpr int kWideLeaf = RICH_WIDE_LEAF;   // subtrees of <= this many triangles become one wide-BVH leaf
 
 struct Box {
     float lo[3], hi[3];
@@ -57,10 +53,7 @@ struct Node {
     Box box;
     int left = -1, right = -1;  // children (build indices) for inner nodes
     int first = 0, count = 0;   // leaf range in `order` when count > 0
-    int span_first = 0, span = 0;  // triangles of the whole subtree
 };
-
-bool wide_leaf(const Node &n) { return n.count > 0 || n.span <= kWideLeaf; }
 
 struct Builder {
     const float *v;
@@ -77,8 +70,6 @@ struct Builder {
             cb.grow(&cen[3 * order[i]]);
         }
         const int id = (int)nodes.size();
-        nd.span_first = first;
-        nd.span = count;
         nodes.push_back(nd);
         if (count <= 2) return make_leaf(id, first, count);
         // binned SAH over all three axes
@@ -165,13 +156,17 @@ void put_box(DevNode &d, int slot, const Box &b) {
     }
 }
 
-// Binary SAH build shared by both node layouts; returns the root id.
-bool binary_build(const float *vertices, int64_t n_tris, Builder &b, int &root,
-                  std::string &err) {
+}  // namespace
+
+bool build_bvh(const float *vertices, int64_t n_tris, BvhResult &out,
+               std::string &err) {
+    out = BvhResult();
+    if (n_tris <= 0) return true;
     if (n_tris >= (int64_t(1) << 27)) {
         err = "too many triangles for the BVH leaf encoding";
         return false;
     }
+    Builder b;
     b.v = vertices;
     b.tri_box.resize((size_t)n_tris);
     b.cen.resize(3 * (size_t)n_tris);
@@ -193,127 +188,7 @@ bool binary_build(const float *vertices, int64_t n_tris, Builder &b, int &root,
     b.order.resize((size_t)n_tris);
     std::iota(b.order.begin(), b.order.end(), 0);
     b.nodes.reserve(2 * (size_t)n_tris);
-    root = b.build(0, (int)n_tris);
-    return true;
-}
-
-// Children of the wide node rooted at binary node n: starting from n's two
-// children, the inner child of largest surface area is replaced by its own
-// two children until there are eight or only leaves remain.
-void wide_children(const Builder &b, int n, std::vector<int> &ch) {
-    ch.clear();
-    const Node &N = b.nodes[n];
-    if (wide_leaf(N)) {
-        ch.push_back(n);
-        return;
-    }
-    ch.push_back(N.left);
-    ch.push_back(N.right);
-    while (ch.size() < 8) {
-        int best = -1;
-        float best_area = -1.0f;
-        for (size_t i = 0; i < ch.size(); ++i) {
-            const Node &c = b.nodes[ch[i]];
-            if (!wide_leaf(c) && c.box.area() > best_area) {
-                best_area = c.box.area();
-                best = (int)i;
-            }
-        }
-        if (best < 0) break;
-        const int c = ch[(size_t)best];
-        ch[(size_t)best] = b.nodes[c].left;
-        ch.push_back(b.nodes[c].right);
-    }
-}
-
-// Octant slots: child i goes to slot s, bit k of s set when the child lies
-// on the + side of axis k. Greedy: the (child, slot) pair with the largest
-// projection of (child centre - node centre) on the slot's diagonal first.
-void assign_slots(const Builder &b, const Box &nb, const std::vector<int> &ch,
-                  int child_at[8]) {
-    for (int s = 0; s < 8; ++s) child_at[s] = -1;
-    float c0[3];
-    for (int k = 0; k < 3; ++k) c0[k] = 0.5f * (nb.lo[k] + nb.hi[k]);
-    float score[8][8];
-    for (size_t i = 0; i < ch.size(); ++i) {
-        const Box &cb = b.nodes[ch[i]].box;
-        for (int s = 0; s < 8; ++s) {
-            float v = 0.0f;
-            for (int k = 0; k < 3; ++k) {
-                const float d = 0.5f * (cb.lo[k] + cb.hi[k]) - c0[k];
-                v += ((s >> k) & 1) ? d : -d;
-            }
-            score[i][s] = v;
-        }
-    }
-    bool used_child[8] = {false}, used_slot[8] = {false};
-    for (size_t round = 0; round < ch.size(); ++round) {
-        float best = -std::numeric_limits<float>::infinity();
-        int bi = -1, bs = -1;
-        for (size_t i = 0; i < ch.size(); ++i) {
-            if (used_child[i]) continue;
-            for (int s = 0; s < 8; ++s)
-                if (!used_slot[s] && (bi < 0 || score[i][s] > best)) {
-                    best = score[i][s];
-                    bi = (int)i;
-                    bs = s;
-                }
-        }
-        used_child[bi] = used_slot[bs] = true;
-        child_at[bs] = ch[(size_t)bi];
-    }
-}
-
-// Outward quantisation of the child boxes of one wide node; false if a
-// decoded box would not contain its child's box.
-bool quantise(const Box &nb, const Box *cb, const bool *valid, DevNode8 &d) {
-    int eb[3];
-    float p[3];
-    for (int k = 0; k < 3; ++k) {
-        p[k] = nb.lo[k];
-        const double ext = (double)nb.hi[k] - (double)nb.lo[k];
-        int e = -126;
-        if (ext > 0.0) {
-            int x = 0;
-            std::frexp(ext / 255.0, &x);   // ext / 255 < 2^x
-            e = std::max(x, -126);
-        }
-        if (e > 127) return false;
-        eb[k] = e + 127;
-        const double scale = std::ldexp(1.0, e);
-        for (int s = 0; s < 8; ++s) {
-            if (!valid[s]) {
-                d.q[2 * k][s] = 255;      // inverted: never hit
-                d.q[2 * k + 1][s] = 0;
-                continue;
-            }
-            double ql = std::floor(((double)cb[s].lo[k] - p[k]) / scale);
-            double qh = std::ceil(((double)cb[s].hi[k] - p[k]) / scale);
-            ql = std::min(std::max(ql, 0.0), 255.0);
-            qh = std::min(std::max(qh, 0.0), 255.0);
-            if (!(p[k] + ql * scale <= (double)cb[s].lo[k]) ||
-                !(p[k] + qh * scale >= (double)cb[s].hi[k]))
-                return false;
-            d.q[2 * k][s] = (uint8_t)ql;
-            d.q[2 * k + 1][s] = (uint8_t)qh;
-        }
-    }
-    d.px = p[0];
-    d.py = p[1];
-    d.pz = p[2];
-    d.meta = (uint32_t)eb[0] | ((uint32_t)eb[1] << 8) | ((uint32_t)eb[2] << 16);
-    return true;
-}
-
-}  // namespace
-
-bool build_bvh(const float *vertices, int64_t n_tris, BvhResult &out,
-               std::string &err) {
-    out = BvhResult();
-    if (n_tris <= 0) return true;
-    Builder b;
-    int root = 0;
-    if (!binary_build(vertices, n_tris, b, root, err)) return false;
+    const int root = b.build(0, (int)n_tris);
 
     out.leaf_order = b.order;
     auto leaf_code = [&](const Node &n) { return ~((n.first << 3) | (n.count - 1)); };
@@ -351,66 +226,6 @@ bool build_bvh(const float *vertices, int64_t n_tris, BvhResult &out,
         put_box(d, 1, r.box);
         d.child0 = l.count > 0 ? leaf_code(l) : dev_index[n.left];
         d.child1 = r.count > 0 ? leaf_code(r) : dev_index[n.right];
-    }
-    return true;
-}
-
-bool build_bvh8(const float *vertices, int64_t n_tris, Bvh8Result &out,
-                std::string &err) {
-    out = Bvh8Result();
-    if (n_tris <= 0) return true;
-    Builder b;
-    int root = 0;
-    if (!binary_build(vertices, n_tris, b, root, err)) return false;
-    // breadth-first over wide nodes; the inner children of a node are
-    // enqueued together in slot order, so they are contiguous
-    std::vector<int> queue{root}, level{1};
-    std::vector<int> ch;
-    out.leaf_order.reserve((size_t)n_tris);
-    for (size_t qi = 0; qi < queue.size(); ++qi) {
-        const int n = queue[qi];
-        wide_children(b, n, ch);
-        int child_at[8];
-        assign_slots(b, b.nodes[n].box, ch, child_at);
-        DevNode8 d;
-        std::memset(&d, 0, sizeof d);
-        d.child_base = (uint32_t)queue.size();
-        d.tri_base = (uint32_t)out.leaf_order.size();
-        uint32_t imask = 0, counts = 0;
-        Box cb[8];
-        bool valid[8];
-        for (int s = 0; s < 8; ++s) {
-            const int c = child_at[s];
-            valid[s] = c >= 0;
-            if (c < 0) continue;
-            const Node &C = b.nodes[c];
-            cb[s] = C.box;
-            if (!wide_leaf(C)) {
-                imask |= 1u << s;
-                queue.push_back(c);
-                level.push_back(level[qi] + 1);
-            } else {
-                if (C.span > 15) {
-                    err = "BVH leaf larger than 15 triangles";
-                    return false;
-                }
-                counts |= (uint32_t)C.span << (4 * s);
-                for (int t = C.span_first; t < C.span_first + C.span; ++t)
-                    out.leaf_order.push_back(b.order[(size_t)t]);
-            }
-        }
-        if (!quantise(b.nodes[n].box, cb, valid, d)) {
-            err = "BVH box quantisation failed (coordinates out of range)";
-            return false;
-        }
-        d.meta |= imask << 24;
-        d.counts = counts;
-        out.nodes.push_back(d);
-        out.depth = std::max(out.depth, level[qi]);
-    }
-    if ((int64_t)out.leaf_order.size() != n_tris) {
-        err = "BVH leaves do not cover every triangle";
-        return false;
     }
     return true;
 }

@@ -79,22 +79,6 @@ struct alignas(16) DevNode { // 64 B: boxes of both children + child refs
     int32_t child0, child1, pad0, pad1;  // >= 0 node, < 0 ~(first << 3 | (count - 1))
 };
 
-// Eight-wide BVH node (80 B). Child boxes are quantised to 8 bits per bound
-// on the grid p + q * 2^e of each axis (e stored biased by 127), rounded
-// outwards so every decoded box contains its child's exact box. Slot s of
-// a node holds the child whose centre lies in octant s of the node (bit k
-// of s set: + side of axis k), so visiting slots in the order i ^ octant of
-// the ray approximates near-to-far order without sorting.
-struct alignas(16) DevNode8 {
-    float px, py, pz;
-    uint32_t meta;           // ex | ey << 8 | ez << 16 | imask << 24
-    uint32_t child_base;     // node index of the first inner child (slot order)
-    uint32_t tri_base;       // first triangle (leaf order) of the leaf children
-    uint32_t counts;         // 4 bits per slot: triangles of a leaf child, else 0
-    uint32_t pad;
-    uint8_t q[6][8];         // lo x, hi x, lo y, hi y, lo z, hi z; per slot
-};
-
 struct alignas(16) TrackRec {  // 64 B, written by the yield kernel
     float x, y, z, len;
     float tx, ty, tz, tan_theta;  // unit direction (FP64-normalised) and tan
