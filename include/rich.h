@@ -291,7 +291,9 @@ typedef struct rich_stats {
     uint64_t n_hits;         /* detected photons (may exceed hit_capacity)  */
     uint64_t n_fate[8];      /* photons per RICH_FATE_* code                */
     uint32_t device_status;  /* RICH_OK or the first device-side error      */
-    uint32_t reserved;
+    uint32_t photon_order;   /* 1: the trace took each track's photons in
+                                azimuth order (a processing order only;
+                                results do not depend on it), 0: index order */
 } rich_stats;
 
 typedef struct rich_ctx rich_ctx;

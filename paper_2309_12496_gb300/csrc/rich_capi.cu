@@ -36,6 +36,13 @@ struct rich_ctx {
     unsigned long long *d_bsum = nullptr;
     bool has_emission = false;
     int64_t n_tracks = 0;
+    // azimuth order of each track's photons (sized from the last photon
+    // total the host has seen; an emission that does not fit keeps index
+    // order, flagged on the device)
+    uint32_t *d_perm = nullptr;
+    uint64_t perm_cap = 0;
+    uint32_t *d_perm_ok = nullptr;
+    uint64_t known_total = 0;
     uint32_t key0 = 0, key1 = 0;
     float inv1 = 0.f, span = 0.f;
     // small device state: counters + photon total
@@ -223,7 +230,18 @@ rich_sphere tile_at_theta(const rich_sphere &s, int i, const double theta[10]) {
     return t;
 }
 
+// A captured graph refers to the context's buffers: drop it before any of
+// them is freed or replaced (rich_graph_launch then reports that nothing
+// is captured).
+void drop_graph(rich_ctx *ctx) {
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    ctx->graph_exec = nullptr;
+    ctx->graph = nullptr;
+}
+
 void free_emission(rich_ctx *ctx) {
+    drop_graph(ctx);
     cudaFree(ctx->d_rec);
     cudaFree(ctx->d_cs);
     cudaFree(ctx->d_counts);
@@ -282,6 +300,31 @@ rich_status emit_core(rich_ctx *ctx, const rich_tracks *t, uint64_t seed, float 
     return RICH_OK;
 }
 
+// Azimuth order of the photons of the last emission. The buffer is sized
+// from the largest photon total the host has read (with a margin); an
+// emission that does not fit is traced in index order (device flag).
+rich_status order_photons(rich_ctx *ctx) {
+    const uint64_t want = ctx->known_total + ctx->known_total / 4 + 1024;
+    if (ctx->known_total && want > ctx->perm_cap) {
+        RICH_CUDA(cudaStreamSynchronize(ctx->stream));
+        drop_graph(ctx);
+        cudaFree(ctx->d_perm);
+        ctx->d_perm = nullptr;
+        ctx->perm_cap = 0;
+        RICH_CUDA(cudaMalloc(&ctx->d_perm, sizeof(uint32_t) * want));
+        ctx->perm_cap = want;
+    }
+    EmitView em{ctx->d_rec, ctx->d_cs, ctx->d_offsets, ctx->d_total, ctx->n_tracks, ctx->key0,
+                ctx->key1, ctx->inv1, ctx->span, ctx->d_perm, ctx->d_perm_ok};
+    if (ctx->n_tracks == 0) {
+        RICH_CUDA(cudaMemsetAsync(ctx->d_perm_ok, 0, sizeof(uint32_t), ctx->stream));
+        return RICH_OK;
+    }
+    RICH_CUDA(launch_order(em, ctx->d_perm, ctx->perm_cap, ctx->d_perm_ok, ctx->n_sm,
+                           ctx->stream));
+    return RICH_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -314,6 +357,8 @@ RICH_API rich_status rich_create(rich_ctx **out, int device, void *stream) {
     if ((e = cudaGetDeviceProperties(&prop, device)) != cudaSuccess ||
         (e = cudaMalloc(&ctx->d_ctr, sizeof(Counters))) != cudaSuccess ||
         (e = cudaMalloc(&ctx->d_total, sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMalloc(&ctx->d_perm_ok, sizeof(uint32_t))) != cudaSuccess ||
+        (e = cudaMemset(ctx->d_perm_ok, 0, sizeof(uint32_t))) != cudaSuccess ||
         (e = cudaMallocHost(&ctx->h_ctr, sizeof(Counters))) != cudaSuccess ||
         (e = cudaMallocHost(&ctx->h_total, sizeof(unsigned long long))) != cudaSuccess ||
         (e = cudaMemset(ctx->d_ctr, 0, sizeof(Counters))) != cudaSuccess ||
@@ -322,6 +367,7 @@ RICH_API rich_status rich_create(rich_ctx **out, int device, void *stream) {
         cudaGetLastError();
         cudaFree(ctx->d_ctr);
         cudaFree(ctx->d_total);
+        cudaFree(ctx->d_perm_ok);
         cudaFreeHost(ctx->h_ctr);
         cudaFreeHost(ctx->h_total);
         delete ctx;
@@ -348,6 +394,8 @@ RICH_API rich_status rich_destroy(rich_ctx *ctx) {
         cudaFree(ctx->d_acc);
         cudaFreeHost(ctx->h_acc);
         free_emission(ctx);
+        cudaFree(ctx->d_perm);
+        cudaFree(ctx->d_perm_ok);
         cudaFree(ctx->d_ctr);
         cudaFree(ctx->d_total);
         cudaFreeHost(ctx->h_ctr);
@@ -507,6 +555,7 @@ RICH_API rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc 
         total += r256(sizes[i]);
     }
     RICH_CUDA(cudaStreamSynchronize(ctx->stream));
+    drop_graph(ctx);
     cudaFree(ctx->d_geom);
     ctx->d_geom = nullptr;
     ctx->has_geometry = false;
@@ -594,7 +643,12 @@ RICH_API rich_status rich_emit(rich_ctx *ctx, const rich_tracks *t,
         RICH_CUDA(cudaMemcpyAsync(ctx->h_total, ctx->d_total, sizeof(unsigned long long),
                                   cudaMemcpyDeviceToHost, ctx->stream));
         RICH_CUDA(cudaStreamSynchronize(ctx->stream));
+        ctx->known_total = std::max<uint64_t>(ctx->known_total, *ctx->h_total);
         if (n_photons) *n_photons = *ctx->h_total;
+    }
+    {
+        const rich_status st = order_photons(ctx);
+        if (st != RICH_OK) return st;
     }
     if (out) {
         const uint64_t total = *ctx->h_total;
@@ -606,7 +660,7 @@ RICH_API rich_status rich_emit(rich_ctx *ctx, const rich_tracks *t,
                       !out->lambda || !out->event || !out->track || !out->photon))
             return fail(ctx, RICH_ERR_ARG, "rich_emit: a photon output array is NULL");
         EmitView em{ctx->d_rec, ctx->d_cs, ctx->d_offsets, ctx->d_total, n,
-                    ctx->key0, ctx->key1, ctx->inv1, ctx->span};
+                    ctx->key0, ctx->key1, ctx->inv1, ctx->span, ctx->d_perm, ctx->d_perm_ok};
         RICH_CUDA(launch_materialize(ctx->sc, em, total, *out, ctx->stream));
         out->n = total;
     }
@@ -648,6 +702,7 @@ RICH_API rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
     const uint64_t hit_cap = out->hits ? out->hit_capacity : 0;
     if (refine && hit_cap > ctx->refine_cap) {
         RICH_CUDA(cudaStreamSynchronize(ctx->stream));
+        drop_graph(ctx);
         cudaFree(ctx->d_refine);
         ctx->d_refine = nullptr;
         ctx->refine_cap = 0;
@@ -689,7 +744,7 @@ RICH_API rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
     }
     shape.blocks = std::max(1, bps) * ctx->n_sm;
     EmitView em{ctx->d_rec, ctx->d_cs, ctx->d_offsets, ctx->d_total, ctx->n_tracks,
-                ctx->key0, ctx->key1, ctx->inv1, ctx->span};
+                ctx->key0, ctx->key1, ctx->inv1, ctx->span, ctx->d_perm, ctx->d_perm_ok};
     if (in) {
         em.key0 = (uint32_t)o->seed;
         em.key1 = (uint32_t)(o->seed >> 32);
@@ -722,6 +777,7 @@ RICH_API rich_status rich_hits(rich_ctx *ctx, uint64_t *n_hits, rich_stats *stat
     RICH_CUDA(cudaMemcpyAsync(ctx->h_total, ctx->d_total, sizeof(unsigned long long),
                               cudaMemcpyDeviceToHost, ctx->stream));
     RICH_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (!ctx->last_ext) ctx->known_total = std::max<uint64_t>(ctx->known_total, *ctx->h_total);
     const Counters &c = *ctx->h_ctr;
     if (n_hits) *n_hits = c.hits;
     if (stats) {
@@ -730,6 +786,7 @@ RICH_API rich_status rich_hits(rich_ctx *ctx, uint64_t *n_hits, rich_stats *stat
         stats->n_hits = c.hits;
         for (int k = 0; k < 8; ++k) stats->n_fate[k] = c.fate[k];
         stats->device_status = c.status;
+        stats->photon_order = c.ordered;
     }
     if (c.status != 0)
         return fail(ctx, (rich_status)c.status,
@@ -790,8 +847,9 @@ RICH_API rich_status rich_trace_grad(rich_ctx *ctx, const rich_tracks *t,
         RICH_CUDA(cudaStreamSynchronize(ctx->stream));
     }
     {
-        const rich_status st = emit_core(ctx, t, prm->seed, th->n_minus_1, prm->lambda_min,
-                                         prm->lambda_max);
+        rich_status st = emit_core(ctx, t, prm->seed, th->n_minus_1, prm->lambda_min,
+                                   prm->lambda_max);
+        if (st == RICH_OK) st = order_photons(ctx);
         if (st != RICH_OK) return st;
     }
     // forward trace recording each detected photon's reflecting surfaces
@@ -800,6 +858,7 @@ RICH_API rich_status rich_trace_grad(rich_ctx *ctx, const rich_tracks *t,
     const uint64_t hit_cap = out->hit_capacity;
     if (hit_cap > ctx->refine_cap) {
         RICH_CUDA(cudaStreamSynchronize(ctx->stream));
+        drop_graph(ctx);
         cudaFree(ctx->d_refine);
         ctx->d_refine = nullptr;
         ctx->refine_cap = 0;
@@ -844,7 +903,7 @@ RICH_API rich_status rich_trace_grad(rich_ctx *ctx, const rich_tracks *t,
     RICH_CUDA(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), ctx->stream));
     RICH_CUDA(cudaMemsetAsync(ctx->d_acc, 0, sizeof(double) * 12, ctx->stream));
     EmitView em{ctx->d_rec, ctx->d_cs, ctx->d_offsets, ctx->d_total, ctx->n_tracks,
-                ctx->key0, ctx->key1, ctx->inv1, ctx->span};
+                ctx->key0, ctx->key1, ctx->inv1, ctx->span, ctx->d_perm, ctx->d_perm_ok};
     RICH_CUDA(launch_trace(sv, &em, nullptr, p, ctx->d_ctr, shape, ctx->stream));
     GradView gv{};
     gv.nom = ctx->d_tile_nom;
@@ -890,9 +949,11 @@ RICH_API rich_status rich_graph_capture(rich_ctx *ctx, const rich_tracks *t,
     if (!t || !prm || !o || !out)
         return fail(ctx, RICH_ERR_ARG, "rich_graph_capture: NULL argument");
     DeviceGuard guard(ctx->device);
-    // warm-up pass: allocates scratch and fills the launch caches so the
-    // captured pass makes no allocation and no synchronising call
-    rich_status st = rich_emit(ctx, t, prm, nullptr, nullptr);
+    // warm-up pass: allocates scratch (reading the photon total sizes the
+    // azimuth-order buffer) and fills the launch caches so the captured
+    // pass makes no allocation and no synchronising call
+    uint64_t n_warm = 0;
+    rich_status st = rich_emit(ctx, t, prm, nullptr, &n_warm);
     if (st == RICH_OK) st = rich_trace(ctx, nullptr, o, out);
     if (st != RICH_OK) return st;
     RICH_CUDA(cudaStreamSynchronize(ctx->stream));

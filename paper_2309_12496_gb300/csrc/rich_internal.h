@@ -122,6 +122,8 @@ struct EmitView {            // result of rich_emit used by the trace
     int64_t n_tracks;
     uint32_t key0, key1;
     float inv1, span;         // FP32 1/lambda_min and 1/lambda_min - 1/lambda_max
+    const uint32_t *perm;     // per track, photon indices in azimuth order, or null
+    const uint32_t *perm_ok;  // device flag: perm covers this emission
 };
 
 struct ExtView {             // caller photons
@@ -135,7 +137,7 @@ struct Counters {            // device, cleared before each trace
     unsigned long long hits;
     unsigned long long fate[8];
     unsigned int status;
-    unsigned int pad;
+    unsigned int ordered;    // 1: photons were taken in azimuth order
 };
 
 // Per stored hit, what the FP64 refinement pass needs to replay the photon:
@@ -198,6 +200,12 @@ cudaError_t launch_offsets(const uint32_t *counts,
                            const unsigned long long *block_sums,
                            int64_t n_tracks, uint64_t *offsets,
                            unsigned long long *total, cudaStream_t s);
+// Azimuth ordering of each track's photons (the trace takes them in this
+// order so a warp's rays are spatially coherent); tracks with more than
+// kOrderMaxPhotons photons keep index order.
+constexpr uint32_t kOrderMaxPhotons = 16384;
+cudaError_t launch_order(const EmitView &em, uint32_t *perm, uint64_t cap, uint32_t *perm_ok,
+                         int n_sm, cudaStream_t s);
 cudaError_t launch_materialize(const SceneView &sc, const EmitView &em,
                                uint64_t n, const rich_photons &out,
                                cudaStream_t s);

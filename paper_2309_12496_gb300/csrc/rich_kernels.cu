@@ -222,6 +222,63 @@ k_offsets(const uint32_t *counts, const unsigned long long *block_sums,
     }
 }
 
+// ============================================================ ordering
+// Photons of a track sorted by azimuth bin (the top 5 bits of the azimuth
+// draw): photons that leave the track in nearby directions hit nearby
+// points of the mirror and, being nearly parallel there, are focused to
+// nearby points after it, so a warp that takes consecutive entries traces
+// coherent rays at every bounce. Processing order only: every photon keeps
+// its own draws and results. One block per track (grid-stride), counting
+// sort in shared memory, order within a bin arbitrary.
+constexpr int kAzBins = 32;
+
+__global__ void __launch_bounds__(128) k_order(EmitView em, uint32_t *perm, uint64_t cap,
+                                               uint32_t *perm_ok) {
+    const uint64_t total = *em.total;
+    const bool fits = total <= cap;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *perm_ok = fits ? 1u : 0u;
+    if (!fits) return;
+    __shared__ uint32_t hist[kAzBins];
+    for (int64_t t = blockIdx.x; t < em.n_tracks; t += gridDim.x) {
+        const uint64_t off = em.offsets[t];
+        const uint64_t n = em.offsets[t + 1] - off;
+        if (n == 0 || n > kOrderMaxPhotons) continue;      // uniform in the block
+        const uint32_t id = em.tracks[t].id, ev = em.tracks[t].event;
+        if (threadIdx.x < kAzBins) hist[threadIdx.x] = 0u;
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j < (uint32_t)n; j += blockDim.x) {
+            const uint32_t bin = philox10(0u, j, id, ev, em.key0, em.key1).y >> 27;
+            atomicAdd(&hist[bin], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const uint32_t c = hist[threadIdx.x];
+            uint32_t inc = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, inc, o);
+                if ((int)threadIdx.x >= o) inc += y;
+            }
+            hist[threadIdx.x] = inc - c;                     // bin cursors
+        }
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j < (uint32_t)n; j += blockDim.x) {
+            const uint32_t bin = philox10(0u, j, id, ev, em.key0, em.key1).y >> 27;
+            perm[off + atomicAdd(&hist[bin], 1u)] = j;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_order(const EmitView &em, uint32_t *perm, uint64_t cap, uint32_t *perm_ok,
+                         int n_sm, cudaStream_t s) {
+    int64_t blocks = em.n_tracks < 1 ? 1 : em.n_tracks;
+    const int64_t max_blocks = (int64_t)n_sm * 16;
+    if (blocks > max_blocks) blocks = max_blocks;
+    k_order<<<(unsigned)blocks, 128, 0, s>>>(em, perm, cap, perm_ok);
+    return cudaGetLastError();
+}
+
 // ============================================================== emission
 struct Photon {
     f3 o, d;
@@ -867,6 +924,8 @@ k_trace(TraceArgs A) {
     const uint64_t N = EXT ? A.ext.n : (uint64_t)(*em.total);
     const uint64_t chunk = (uint64_t)P.chunk;
     const bool has_tri = sc.n_tris > 0;
+    const bool ordered = !EXT && em.perm && *em.perm_ok;
+    if (blockIdx.x == 0 && threadIdx.x == 0) A.ctr->ordered = ordered ? 1u : 0u;
 
     Photon ph;
     bool alive = false;
@@ -935,7 +994,12 @@ k_trace(TraceArgs A) {
                             ++my_track;
                         ph.track = (uint32_t)my_track;
                         const TrackRec tr = em.tracks[my_track];
-                        emit_photon(tr, (uint32_t)(g - em.offsets[my_track]), em, ph);
+                        const uint64_t toff = em.offsets[my_track];
+                        uint32_t j = (uint32_t)(g - toff);
+                        if (ordered && em.offsets[my_track + 1] - toff <= kOrderMaxPhotons)
+                            j = em.perm[g];
+                        ph.g = toff + j;
+                        emit_photon(tr, j, em, ph);
                     }
                     alive = true;
                 }

@@ -98,7 +98,7 @@ class GradParams(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("n_photons", C.c_uint64), ("n_hits", C.c_uint64),
                 ("n_fate", C.c_uint64 * 8), ("device_status", C.c_uint32),
-                ("reserved", C.c_uint32)]
+                ("photon_order", C.c_uint32)]
 
 
 # ------------------------------------------------------------------ library
@@ -416,7 +416,7 @@ class Context:
             _check(self.handle, st)
         stats = {"n_photons": int(s.n_photons), "n_hits": int(s.n_hits),
                  "fate": [int(x) for x in s.n_fate], "device_status": int(s.device_status),
-                 "status": int(st)}
+                 "photon_order": int(s.photon_order), "status": int(st)}
         return int(n.value), stats
 
 

@@ -238,6 +238,34 @@ def test_results_invariant_to_launch_shape(launch):
     np.testing.assert_array_equal(base["pixel_counts"], other["pixel_counts"])
 
 
+def test_azimuth_order_changes_nothing():
+    """The trace takes each track's photons in azimuth order once the
+    context knows the photon total (a synchronised emission); a fresh
+    context emitting without synchronising traces in index order. Both give
+    the same fates, hits and pixel counts."""
+    wl = W.rich1(300)
+    res = {}
+    for sync in (False, True):
+        ctx = rich.Context(0)
+        ctx.init_geometry(wl.scene)
+        dt = rich.DeviceTracks(wl.tracks)
+        n = int(ctx.emit(dt, wl.n_minus_1, seed=wl.seed, sync=True)) if sync else None
+        if not sync:
+            ctx.emit(dt, wl.n_minus_1, seed=wl.seed, sync=False)
+            n = 400_000
+        out = rich.TraceOutputs(n, wl.scene.pixels_per_event, len(wl.scene.planes), 1, n)
+        ctx.trace(out, precision=rich.PREC_REFINE64)
+        nh, st = ctx.hits()
+        res[sync] = (st["photon_order"], st["n_photons"], out.fate[: st["n_photons"]].cpu().numpy(),
+                     np.sort(out.hits_numpy(nh), order=["event", "track", "photon"]),
+                     out.pixel_counts_numpy())
+        ctx.close()
+    assert res[False][0] == 0 and res[True][0] == 1
+    assert res[False][1] == res[True][1]
+    for k in (2, 3, 4):
+        np.testing.assert_array_equal(res[False][k], res[True][k])
+
+
 # --------------------------------------------------------------- edge cases
 def test_zero_tracks_and_empty_emission():
     wl = W.rich1(10)
