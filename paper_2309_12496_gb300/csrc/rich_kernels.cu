@@ -18,9 +18,11 @@
 #include <climits>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <math_constants.h>
 
 #include "rich_device.cuh"
 #include "rich_ff.cuh"
+#include "rich_log_tables.h"
 
 namespace rich {
 
@@ -57,21 +59,50 @@ struct TrackStream {
     }
 };
 
-// log Gamma(x) for x >= 10 by Stirling's series with four correction terms
-// (truncation < 1/(1188 x^9), below 1e-12 at x = 10).
-__device__ __forceinline__ double lgamma_stirling(double x) {
+// FP64 natural logarithm of a positive normal x, table-driven after Tang
+// (ACM TOMS 16(4), 1990): x = 2^e m with m in [1, 2); c the centre of the
+// 1/128-wide interval of m (its top 7 mantissa bits); r = m (1/c) - 1 with
+// one fused multiply-add, |r| < 2^-8; log x = e log 2 + log(1/(1/c)) +
+// log(1 + r), the last by its Taylor series to r^7 (truncation < 2^-59
+// relative). log 2 is split so e * hi is exact. x = 0 gives -infinity.
+__device__ __forceinline__ double log64(double x) {
+    if (!(x > 0.0)) return -CUDART_INF;
+    constexpr double kLn2Hi = 0x1.62e42fefa3800p-1, kLn2Lo = 0x1.ef35793c76730p-45;
+    const long long bits = __double_as_longlong(x);
+    const int e = (int)((bits >> 52) & 0x7FF) - 1023;
+    const double m = __longlong_as_double((bits & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
+    const int i = (int)((bits >> (52 - kLogTableBits)) & ((1 << kLogTableBits) - 1));
+    const double inv_c = __ldg(&g_log_tab[i][0]);
+    const double lc_hi = __ldg(&g_log_tab[i][1]), lc_lo = __ldg(&g_log_tab[i][2]);
+    const double r = fma(m, inv_c, -1.0);
+    double q = fma(r, 1.0 / 7.0, -1.0 / 6.0);           // log(1+r) = r + r^2 q(r)
+    q = fma(q, r, 0.2);
+    q = fma(q, r, -0.25);
+    q = fma(q, r, 1.0 / 3.0);
+    q = fma(q, r, -0.5);
+    const double ed = (double)e;
+    const double hi = fma(ed, kLn2Hi, lc_hi);
+    const double lo = fma(ed, kLn2Lo, lc_lo);
+    return hi + (r + fma(r * r, q, lo));
+}
+
+// log k! (k >= 0): the table below 2048, Stirling's series above (four
+// correction terms, truncation < 1/(1188 k^9)).
+__device__ __forceinline__ double log_factorial(double kd) {
+    if (kd < (double)kLogFactTable) return __ldg(&g_logfact[(int)kd]);
     constexpr double kHalfLog2Pi = 0.91893853320467274178;
-    const double r = rcp64(x), r2 = r * r;
+    const double x = kd + 1.0, r = rcp64(x), r2 = r * r;
     const double series = r * (1.0 / 12.0 - r2 * (1.0 / 360.0 - r2 * (1.0 / 1260.0 -
                                                                      r2 * (1.0 / 1680.0))));
-    return (x - 0.5) * log(x) - x + kHalfLog2Pi + series;
+    return (x - 0.5) * log64(x) - x + kHalfLog2Pi + series;
 }
 
 // Poisson(mu): CDF inversion (smallest k with u < F(k)) below mean 10; the
 // PTRS transformed rejection sampler (Hoermann 1993) above, at most 64
 // trials, then round(mu). The GPU's FP64 pipe is slow, so the rejection
 // test log V + log(1/alpha) - log(a/us^2 + b) <= -mu + k log mu - log k! is
-// taken with one log on the left and Stirling's series for log k! (k >= 9).
+// taken as log(V us^2 / (alpha (a + b us^2))) with one table-driven log and
+// log k! from a table.
 __device__ int64_t poisson_draw(double mu, TrackStream &s) {
     if (!(mu > 0.0)) return 0;
     if (mu < 10.0) {
@@ -85,12 +116,12 @@ __device__ int64_t poisson_draw(double mu, TrackStream &s) {
         }
         return k;
     }
-    // per-track constants in IEEE arithmetic (they set the candidate k and
-    // the quick-accept bound); only the per-trial tail uses Newton reciprocals
-    const double smu = sqrt(mu), lmu = log(mu);
+    // per-track constants; those that set the candidate k and the
+    // quick-accept bound in IEEE arithmetic
+    const double smu = sqrt(mu), lmu = log64(mu);
     const double b = 0.931 + 2.53 * smu;
     const double a = -0.059 + 0.02483 * b;
-    const double inv_alpha = 1.1239 + 1.1328 / (b - 3.4);
+    const double inv_alpha = 1.1239 + 1.1328 * rcp64(b - 3.4);
     const double v_r = 0.9277 - 3.6224 / (b - 2.0);
     for (int trial = 0; trial < 64; ++trial) {
         double U = s.next() - 0.5;
@@ -101,9 +132,9 @@ __device__ int64_t poisson_draw(double mu, TrackStream &s) {
         if (!(kd >= 0.0)) continue;
         if (us >= 0.07 && V <= v_r) return (int64_t)kd;
         if (us < 0.013 && V > us) continue;
-        const double lhs = log(V * inv_alpha * rcp64(a * rcp64(us * us) + b));
-        const double lg = kd >= 9.0 ? lgamma_stirling(kd + 1.0) : lgamma(kd + 1.0);
-        const double rhs = -mu + kd * lmu - lg;
+        const double us2 = us * us;
+        const double lhs = log64(V * inv_alpha * us2 * rcp64(fma(b, us2, a)));
+        const double rhs = -mu + kd * lmu - log_factorial(kd);
         if (lhs <= rhs) return (int64_t)kd;
     }
     return (int64_t)floor(mu + 0.5);
@@ -228,54 +259,65 @@ k_offsets(const uint32_t *counts, const unsigned long long *block_sums,
 // points of the mirror and, being nearly parallel there, are focused to
 // nearby points after it, so a warp that takes consecutive entries traces
 // coherent rays at every bounce. Processing order only: every photon keeps
-// its own draws and results. One block per track (grid-stride), counting
-// sort in shared memory, order within a bin arbitrary.
+// its own draws and results. One warp per track (grid-stride), counting
+// sort in shared memory (the bins of the first kOrderBinCache photons kept
+// from the counting pass), order within a bin arbitrary.
 constexpr int kAzBins = 32;
+constexpr int kOrderWarps = 4;
+constexpr uint32_t kOrderBinCache = 2048;
 
-__global__ void __launch_bounds__(128) k_order(EmitView em, uint32_t *perm, uint64_t cap,
-                                               uint32_t *perm_ok) {
+__global__ void __launch_bounds__(32 * kOrderWarps) k_order(EmitView em, uint32_t *perm,
+                                                            uint64_t cap, uint32_t *perm_ok) {
     const uint64_t total = *em.total;
     const bool fits = total <= cap;
     if (blockIdx.x == 0 && threadIdx.x == 0) *perm_ok = fits ? 1u : 0u;
     if (!fits) return;
-    __shared__ uint32_t hist[kAzBins];
-    for (int64_t t = blockIdx.x; t < em.n_tracks; t += gridDim.x) {
+    __shared__ uint32_t hist_all[kOrderWarps][kAzBins];
+    __shared__ uint8_t bins_all[kOrderWarps][kOrderBinCache];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t *hist = hist_all[w];
+    uint8_t *bins = bins_all[w];
+    const int64_t warps = (int64_t)gridDim.x * kOrderWarps;
+    for (int64_t t = (int64_t)blockIdx.x * kOrderWarps + w; t < em.n_tracks; t += warps) {
         const uint64_t off = em.offsets[t];
-        const uint64_t n = em.offsets[t + 1] - off;
-        if (n == 0 || n > kOrderMaxPhotons) continue;      // uniform in the block
+        const uint64_t n64 = em.offsets[t + 1] - off;
+        if (n64 == 0 || n64 > kOrderMaxPhotons) continue;   // uniform in the warp
+        const uint32_t n = (uint32_t)n64;
         const uint32_t id = em.tracks[t].id, ev = em.tracks[t].event;
-        if (threadIdx.x < kAzBins) hist[threadIdx.x] = 0u;
-        __syncthreads();
-        for (uint32_t j = threadIdx.x; j < (uint32_t)n; j += blockDim.x) {
+        hist[lane] = 0u;
+        __syncwarp();
+        for (uint32_t j = lane; j < n; j += 32) {
             const uint32_t bin = philox10(0u, j, id, ev, em.key0, em.key1).y >> 27;
+            if (j < kOrderBinCache) bins[j] = (uint8_t)bin;
             atomicAdd(&hist[bin], 1u);
         }
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            const uint32_t c = hist[threadIdx.x];
-            uint32_t inc = c;
+        __syncwarp();
+        const uint32_t c = hist[lane];
+        uint32_t inc = c;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(kFull, inc, o);
-                if ((int)threadIdx.x >= o) inc += y;
-            }
-            hist[threadIdx.x] = inc - c;                     // bin cursors
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += y;
         }
-        __syncthreads();
-        for (uint32_t j = threadIdx.x; j < (uint32_t)n; j += blockDim.x) {
-            const uint32_t bin = philox10(0u, j, id, ev, em.key0, em.key1).y >> 27;
+        hist[lane] = inc - c;                                   // bin cursors
+        __syncwarp();
+        for (uint32_t j = lane; j < n; j += 32) {
+            const uint32_t bin = j < kOrderBinCache
+                                     ? (uint32_t)bins[j]
+                                     : philox10(0u, j, id, ev, em.key0, em.key1).y >> 27;
             perm[off + atomicAdd(&hist[bin], 1u)] = j;
         }
-        __syncthreads();
+        __syncwarp();
     }
 }
 
 cudaError_t launch_order(const EmitView &em, uint32_t *perm, uint64_t cap, uint32_t *perm_ok,
                          int n_sm, cudaStream_t s) {
-    int64_t blocks = em.n_tracks < 1 ? 1 : em.n_tracks;
+    int64_t blocks = (em.n_tracks + kOrderWarps - 1) / kOrderWarps;
+    if (blocks < 1) blocks = 1;
     const int64_t max_blocks = (int64_t)n_sm * 16;
     if (blocks > max_blocks) blocks = max_blocks;
-    k_order<<<(unsigned)blocks, 128, 0, s>>>(em, perm, cap, perm_ok);
+    k_order<<<(unsigned)blocks, 32 * kOrderWarps, 0, s>>>(em, perm, cap, perm_ok);
     return cudaGetLastError();
 }
 
