@@ -42,10 +42,10 @@ WORKLOAD = "rich1_meshed_1000_pion_tracks"
 # FP32 operations per propagated photon of the trace kernel on this workload:
 # 2 x FFMA + FADD + FMUL thread instructions of one k_trace launch from the
 # ncu counters (smsp__sass_thread_inst_executed_op_{ffma,fadd,fmul}_pred_on)
-# divided by its 350,350 photons: (2 x 360.71 M + 53.05 M + 93.71 M) / 350,350.
-FLOPS_PER_PHOTON = 2481.0
+# divided by its 350,350 photons: (2 x 360.29 M + 52.70 M + 93.51 M) / 350,350.
+FLOPS_PER_PHOTON = 2474.1
 # dram__bytes_read.sum + dram__bytes_write.sum of the same k_trace launch.
-TRACE_DRAM_BYTES = 10834944 + 315392
+TRACE_DRAM_BYTES = 7047680 + 157952
 FP32_LANES_PER_SM = 128
 SM_COUNT_NOMINAL = 152
 
@@ -295,7 +295,7 @@ def main():
             "kernel_ms": {"emit": statistics.mean([a.elapsed_time(b) for a, b, _ in ev]),
                           "trace": t_trace * 1e3},
             "hits_per_step": n_hits_last,
-            "gpu_launches": (4 if prec == rich.PREC_REFINE64 else 3) * args.steps,
+            "gpu_launches": (5 if prec == rich.PREC_REFINE64 else 4) * args.steps,
             "roofline": roof,
             "clocks": clk,
         }
