@@ -25,8 +25,9 @@ _lock = threading.Lock()
 _lib = None
 
 FATE_NAMES = ["none", "escaped", "mirror_absorbed", "absorbed", "qe_rejected",
-              "detected", "max_bounces", "max_steps"]
+              "detected", "max_bounces", "max_steps", "prefiltered"]
 FATE_DETECTED = 5
+FATE_PREFILTERED = 8
 
 
 def build(force: bool = False) -> str:
@@ -76,7 +77,8 @@ class Params(C.Structure):
                 ("max_bounces", C.c_int32), ("max_steps", C.c_int32),
                 ("t_min", C.c_double), ("eps", C.c_double),
                 ("prob_eps", C.c_double), ("use_bvh", C.c_int32),
-                ("n_threads", C.c_int32)]
+                ("n_threads", C.c_int32), ("n_prefilter", C.c_int32),
+                ("prefilter_tables", C.c_int32 * 4)]
 
 
 class PhotonOut(C.Structure):
@@ -158,8 +160,10 @@ class _TracksHold:
 
 def params(workload=None, seed=None, n_minus_1=None, lambda_min=None,
            lambda_max=None, max_bounces=8, max_steps=16, t_min=1e-3,
-           eps=1e-3, prob_eps=1e-6, use_bvh=True, n_threads=0):
-    """Oracle parameters; radiator and seed default to the workload's."""
+           eps=1e-3, prob_eps=1e-6, use_bvh=True, n_threads=0, prefilter=()):
+    """Oracle parameters; radiator and seed default to the workload's.
+    prefilter: indices of the scene tables whose product is applied as one
+    accept/reject before propagation (Sec. 4.3); empty: in flight."""
     w = workload
     # n - 1 and the band are FP32 inputs of the propagator: promote exactly
     nm1 = float(np.float32(n_minus_1 if n_minus_1 is not None else w.n_minus_1))
@@ -169,7 +173,8 @@ def params(workload=None, seed=None, n_minus_1=None, lambda_min=None,
                   lambda_max=lambda_max if lambda_max is not None else w.lambda_max,
                   max_bounces=max_bounces, max_steps=max_steps, t_min=t_min,
                   eps=eps, prob_eps=prob_eps, use_bvh=int(use_bvh),
-                  n_threads=n_threads)
+                  n_threads=n_threads, n_prefilter=len(prefilter),
+                  prefilter_tables=(C.c_int32 * 4)(*(list(prefilter) + [0] * (4 - len(prefilter)))))
 
 
 def track_yield(tracks, prm):

@@ -110,6 +110,12 @@ typedef struct {
     double prob_eps;   /* probability graze margin             */
     int32_t use_bvh;
     int32_t n_threads;
+    /* Efficiencies applied before propagation (Sec. 4.3): when n_prefilter
+     * > 0 a photon is propagated only if its QE uniform is below the product
+     * of the listed tables at its wavelength, and is then propagated with
+     * the in-flight reflectivity and QE tests switched off. */
+    int32_t n_prefilter;
+    int32_t prefilter_tables[4];
 } o_params;
 
 /* Per-photon results, arrays indexed by global photon index. Any pointer
@@ -132,7 +138,7 @@ typedef struct {
 
 enum { FATE_NONE = 0, FATE_ESCAPED = 1, FATE_MIRROR_ABSORBED = 2,
        FATE_ABSORBED = 3, FATE_QE_REJECTED = 4, FATE_DETECTED = 5,
-       FATE_MAX_BOUNCES = 6, FATE_MAX_STEPS = 7 };
+       FATE_MAX_BOUNCES = 6, FATE_MAX_STEPS = 7, FATE_PREFILTERED = 8 };
 enum { TAB_CONST = 0, TAB_GAUSS = 1, TAB_HIST = 2 };
 enum { MAT_MIRROR = 0, MAT_ABSORBER = 1, MAT_DETECTOR = 2 };
 enum { MAT_SMOOTH = 1 };
@@ -919,9 +925,39 @@ typedef struct {
     v3 o, d;
 } o_result;
 
-/* Trace one photon to its fate. */
+/* Acceptance probability of the efficiencies applied before propagation
+ * (Sec. 4.3: "the three efficiencies" -- the detector's quantum efficiency
+ * and the reflectivities of the mirrors on the photon's way -- combined in
+ * one accept/reject per photon at its wavelength): the product of the
+ * listed tables, in FP32, multiplied left to right. */
+static float prefilter_prob(const o_scene *sc, const o_params *prm, float lam)
+{
+    volatile float P = table_eval(&sc->tables[prm->prefilter_tables[0]], lam);
+    for (int k = 1; k < prm->n_prefilter; ++k) {
+        volatile float f = table_eval(&sc->tables[prm->prefilter_tables[k]], lam);
+        P = P * f;
+    }
+    return P;
+}
+
+/* Photon that failed the efficiencies before propagation: not traced. */
+static void prefiltered(const o_photon *ph, float P, const o_params *prm,
+                        o_result *res)
+{
+    memset(res, 0, sizeof *res);
+    res->plane = -1;
+    res->fate = FATE_PREFILTERED;
+    res->o = ph->o;
+    res->d = ph->d;
+    if (fabs(ph->u_qe - (double)P) < prm->prob_eps) res->graze = 2;
+}
+
+/* Trace one photon to its fate. With `filtered` set the photon has already
+ * passed the efficiencies before propagation (Sec. 4.3): mirrors reflect it
+ * and the detector records it without a further random test. */
 static void trace_photon(const o_scene *sc, const o_params *prm,
-                         const o_photon *ph, o_result *res, int32_t *path)
+                         const o_photon *ph, o_result *res, int32_t *path,
+                         int filtered)
 {
     v3 o = ph->o, d = unit(ph->d);
     int skip = -1, n_refl = 0, graze = 0;
@@ -959,13 +995,15 @@ static void trace_photon(const o_scene *sc, const o_params *prm,
                 o = p;
                 break;
             }
-            float P = table_eval(&sc->tables[m->table], ph->lambda);
-            double u = ph->u_refl[n_refl];
-            if (fabs(u - (double)P) < prm->prob_eps) graze |= 2;
-            if (!(u < (double)P)) {
-                res->fate = FATE_MIRROR_ABSORBED;
-                o = p;
-                break;
+            if (!filtered) {
+                float P = table_eval(&sc->tables[m->table], ph->lambda);
+                double u = ph->u_refl[n_refl];
+                if (fabs(u - (double)P) < prm->prob_eps) graze |= 2;
+                if (!(u < (double)P)) {
+                    res->fate = FATE_MIRROR_ABSORBED;
+                    o = p;
+                    break;
+                }
             }
             d = unit(reflect(d, n_sh));
             n_refl++;
@@ -979,12 +1017,14 @@ static void trace_photon(const o_scene *sc, const o_params *prm,
             skip = h.prim;
             continue;
         }
-        float P = table_eval(&sc->tables[m->table], ph->lambda);
-        if (fabs(ph->u_qe - (double)P) < prm->prob_eps) graze |= 2;
         o = p;
-        if (!(ph->u_qe < (double)P)) {
-            res->fate = FATE_QE_REJECTED;
-            break;
+        if (!filtered) {
+            float P = table_eval(&sc->tables[m->table], ph->lambda);
+            if (fabs(ph->u_qe - (double)P) < prm->prob_eps) graze |= 2;
+            if (!(ph->u_qe < (double)P)) {
+                res->fate = FATE_QE_REJECTED;
+                break;
+            }
         }
         const o_rect *rc = &sc->rects[h.index];
         v3 q = sub(p, rc->o);
@@ -1020,6 +1060,10 @@ int oracle_trace(void *scene, const o_tracks_in *t, const o_params *prm,
 {
     const o_scene *sc = (const o_scene *)scene;
     if (prm->max_steps > 16 || prm->max_bounces > 8) return -1;
+    if (prm->n_prefilter < 0 || prm->n_prefilter > 4) return -1;
+    for (int k = 0; k < prm->n_prefilter; ++k)
+        if (prm->prefilter_tables[k] < 0 || prm->prefilter_tables[k] >= sc->n_tables)
+            return -1;
     int64_t first = (int64_t)offsets[track_begin];
     int64_t last = (int64_t)offsets[track_end];
 #ifdef _OPENMP
@@ -1037,8 +1081,24 @@ int oracle_trace(void *scene, const o_tracks_in *t, const o_params *prm,
         o_photon ph;
         emit_photon(t, prm, lo, j, &ph);
         o_result r;
-        trace_photon(sc, prm, &ph, &r,
-                     out->path ? out->path + g * prm->max_steps : NULL);
+        int32_t *path = out->path ? out->path + g * prm->max_steps : NULL;
+        int run = 1;
+        if (prm->n_prefilter > 0) {
+            /* Sec. 4.3: accept/reject on the product of the efficiencies
+             * before propagation, with the photon's QE uniform */
+            float P = prefilter_prob(sc, prm, ph.lambda);
+            if (!(ph.u_qe < (double)P)) {
+                prefiltered(&ph, P, prm, &r);
+                if (path) for (int k = 0; k < prm->max_steps; ++k) path[k] = -1;
+                run = 0;
+            } else if (fabs(ph.u_qe - (double)P) < prm->prob_eps) {
+                run = 2;
+            }
+        }
+        if (run) {
+            trace_photon(sc, prm, &ph, &r, path, prm->n_prefilter > 0);
+            if (run == 2) r.graze |= 2;
+        }
         if (out->fate) out->fate[g] = (uint8_t)r.fate;
         if (out->plane) out->plane[g] = r.plane;
         if (out->ix) out->ix[g] = r.ix;
@@ -1366,7 +1426,7 @@ int64_t oracle_trace_grad(void *scene, const o_tracks_in *t, const o_params *prm
             emit_photon(t, &prm, lo, j, &ph);
             int32_t path[16];
             o_result r;
-            trace_photon(&at, &prm, &ph, &r, path);
+            trace_photon(&at, &prm, &ph, &r, path, 0);
             if (r.fate != FATE_DETECTED) continue;
             const float *tg = targets + ((size_t)lo * n_planes + r.plane) * 4;
             if (!(tg[3] > 0.0f)) continue;
@@ -1461,7 +1521,7 @@ int oracle_hit_jacobian(void *scene, const o_tracks_in *t, const o_params *prm_i
     emit_photon(t, &prm, i, j, &ph);
     int32_t path[16];
     o_result r;
-    trace_photon(&at, &prm, &ph, &r, path);
+    trace_photon(&at, &prm, &ph, &r, path, 0);
     if (r.fate == FATE_DETECTED) {
         int32_t refl[16];
         int nr = 0, det = -1;

@@ -456,3 +456,72 @@ def test_rich1_bookkeeping(oracle_lib):
     assert (out["graze"] != 0).mean() < 0.01
     # planes 0/1 collect light after two reflections mostly
     assert (out["n_refl"][det & (out["plane"] < 2)] == 2).mean() > 0.8
+
+
+# ------------------------------- efficiencies before propagation (Sec. 4.3)
+def test_prefilter_point_source_counts_and_ring(oracle_lib):
+    """The three efficiencies applied as one accept/reject before
+    propagation (Sec. 4.3). On the point-source scene every photon reaches
+    the mirror and returns to the plane, so with the prefilter on (QE table
+    x reflectivity table) every accepted photon is detected and nothing
+    else is: fates are only 'detected' or 'prefiltered'. The count follows
+    the same closed form as in flight, 1e5 x 0.9 x <QE> = 12,092 +- 103,
+    and every hit lies on the ring of radius (R/2) tan(theta)."""
+    assert PAPER["efficiencies_before_propagation"]["count"] == 3
+    wl = w.point_source(100000)
+    sc = oracle_lib.Scene(wl.scene)
+    out = sc.trace(wl.tracks, oracle_lib.params(wl, prefilter=(0, 1)))
+    f = out["fate"]
+    assert set(np.unique(f)) <= {oracle_lib.FATE_DETECTED, oracle_lib.FATE_PREFILTERED}
+    n_det = int((f == oracle_lib.FATE_DETECTED).sum())
+    p = 0.9 * 0.13435
+    assert abs(n_det - 1e5 * p) < 4 * math.sqrt(1e5 * p * (1 - p))
+    det, rad = _ring_radii(out, wl.scene.rects[0])
+    n = 1 + ETA_C4F10
+    assert np.abs(rad - 1355.0 * math.sqrt(n * n - 1)).max() < 1e-9
+    assert out["pixel_counts"].sum() == n_det
+    # rejected photons are not propagated: no reflections recorded
+    assert np.all(out["n_refl"][f == oracle_lib.FATE_PREFILTERED] == 0)
+
+
+def test_prefilter_uses_the_qe_draw_and_switches_in_flight_tests_off(oracle_lib):
+    """With the QE table alone as the prefilter, the accept decision is the
+    in-flight QE decision (the same draw and table), and mirrors then
+    always reflect. So a photon detected in flight is detected with the
+    prefilter; a photon detected only with the prefilter failed the
+    in-flight reflectivity test; a constant-one prefilter detects every
+    photon."""
+    wl = w.point_source(30000)
+    sc = oracle_lib.Scene(wl.scene)
+    fly = sc.trace(wl.tracks, oracle_lib.params(wl))["fate"]
+    pre = sc.trace(wl.tracks, oracle_lib.params(wl, prefilter=(0,)))["fate"]
+    D = oracle_lib.FATE_DETECTED
+    assert np.all(pre[fly == D] == D)
+    only = (pre == D) & (fly != D)
+    assert only.sum() > 0
+    assert np.all(fly[only] == 2)          # mirror-absorbed in flight
+    assert np.all(pre[fly == 4] == oracle_lib.FATE_PREFILTERED)   # QE-rejected
+    # a scene whose first table is the constant 1 passes every photon
+    ones = wl.scene.tables.copy()
+    ones[1]["p0"] = 1.0
+    sc1 = oracle_lib.Scene(w.Scene(**{**wl.scene.__dict__, "tables": ones}))
+    all_det = sc1.trace(wl.tracks, oracle_lib.params(wl, prefilter=(1,)))["fate"]
+    assert np.all(all_det == D)
+
+
+def test_prefilter_matches_in_flight_statistics_rich1(oracle_lib):
+    """RICH1-like scene: photons that meet the spherical mirror, the flat
+    mirror and the detector have the same detection probability
+    QE x R_a x R_b whether the efficiencies are applied before propagation
+    or in flight, so the detected counts on the two focal planes agree
+    within statistics, and no photon is mirror-absorbed or QE-rejected
+    with the prefilter."""
+    wl = w.rich1(200, meshed=False)
+    sc = oracle_lib.Scene(wl.scene)
+    fly = sc.trace(wl.tracks, oracle_lib.params(wl))
+    pre = sc.trace(wl.tracks, oracle_lib.params(wl, prefilter=(0, 1, 2)))
+    assert not np.isin(pre["fate"], (2, 4)).any()
+    sel = lambda o: int(((o["fate"] == 5) & (o["plane"] < 2) & (o["n_refl"] == 2)).sum())
+    a, b = sel(fly), sel(pre)
+    assert a > 5000
+    assert abs(a - b) < 4 * math.sqrt(a + b)
