@@ -306,6 +306,7 @@ def main():
             line["batched"] = run_batched(dev, prec, rank)
             line["adjoint"] = run_adjoint(dev, rank)
             line["rich2_chunked"] = run_chunked(dev, rank)
+            line["prefilter"] = run_prefilter(dev, prec, rank)
     if line is not None and not args.no_extras and ws == 1:
         v, cores, passes, nph, el = oracle_rate(10.0)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -406,6 +407,40 @@ def run_chunked(dev, rank, n_chunks=10, tracks_per_chunk=490_000):
     ctx.close()
     return {"value": photons / (ms / 1e3), "unit": UNIT, "ms_total": ms, "photons": photons,
             "chunks": n_chunks, "binned_hits": hits, "triangles": scene.n_triangles}
+
+
+def run_prefilter(dev, prec, rank, n_tracks=10_000):
+    """The three efficiencies (QE, spherical- and flat-mirror reflectivity)
+    applied as one accept/reject per photon before propagation (Sec. 4.3)
+    against the same efficiencies in flight, on 10,000 RICH1-like pion
+    tracks (~3.5e6 photons, enough to fill the GPU after the filter keeps
+    ~1 photon in 7): emitted photons/s of each mode, and the photons that
+    passed the filter and were propagated."""
+    import torch
+    from paper_2309_12496_gb300 import rich
+    from paper_2309_12496_gb300 import workloads as W
+    scene = W.rich1_scene(meshed=True)
+    tracks = W.pion_tracks(n_tracks, seed=50 + rank)
+    ctx = rich.Context(int(dev.split(":")[1]))
+    ctx.init_geometry(scene)
+    dt = rich.DeviceTracks(tracks, device=dev)
+    n = ctx.emit(dt, 0.0014, seed=rank * 1000 + 77)
+    out = rich.TraceOutputs(int(n * 0.3) + 1024, scene.pixels_per_event, len(scene.planes), 1, 0,
+                            device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    res = {"tracks": n_tracks, "photons_per_step": n}
+    for name, pre in (("in_flight", ()), ("prefilter", (0, 1, 2))):
+        def step():
+            ctx.emit(dt, 0.0014, seed=rank * 1000 + 77, sync=False)
+            ctx.trace(out, precision=prec, prefilter=pre)
+        ms = _time_steps(step, 10, 3, flush)
+        n_hits, st = ctx.hits()
+        traced = n - st["fate"][rich.FATE_PREFILTERED]
+        res[name] = {"value": n / (ms / 1e3), "unit": "emitted photons/s", "ms_per_step": ms,
+                     "propagated_per_step": traced,
+                     "propagated_photons_per_s": traced / (ms / 1e3), "hits_per_step": n_hits}
+    ctx.close()
+    return res
 
 
 def run_adjoint(dev, rank):

@@ -237,6 +237,18 @@ typedef struct rich_trace_opts {
                                (0: the 1024-thread variant, 64 registers)   */
     int32_t bvh_smem_nodes; /* top BVH nodes staged in shared memory per block
                                by a TMA bulk copy (-1: default)              */
+    /* Efficiencies applied before propagation (Sec. 4.3: the quantum
+     * efficiency and the mirror reflectivities combined into one
+     * accept/reject per photon at its wavelength, and rejected photons not
+     * propagated). n_prefilter = 0: off (every efficiency is applied in
+     * flight). 1..4: the photon enters the trace only if its QE uniform
+     * (draw block 0, word 3) is below the FP32 product, taken left to right,
+     * of the listed scene tables at its wavelength; it then reflects at
+     * every mirror front and is recorded at every detector front without
+     * further random tests. Rejected photons get RICH_FATE_PREFILTERED.
+     * prefilter_tables: indices into the scene's tables. */
+    int32_t n_prefilter;
+    int32_t prefilter_tables[4];
 } rich_trace_opts;
 
 /* ----------------------------------------------------------------- outputs */
@@ -261,8 +273,11 @@ enum {
     RICH_FATE_QE_REJECTED = 4,    /* reached a detector, failed the QE test  */
     RICH_FATE_DETECTED = 5,       /* recorded hit                            */
     RICH_FATE_MAX_BOUNCES = 6,    /* more than max_bounces reflections       */
-    RICH_FATE_MAX_STEPS = 7       /* more than max_steps interactions        */
+    RICH_FATE_MAX_STEPS = 7,      /* more than max_steps interactions        */
+    RICH_FATE_PREFILTERED = 8     /* failed the efficiencies applied before
+                                     propagation (rich_trace_opts.n_prefilter) */
 };
+#define RICH_N_FATES 9
 
 /* DEVICE output buffers, caller owned.
  * hits: capacity hit_capacity; hits beyond it are counted, not written.
@@ -287,9 +302,11 @@ typedef struct rich_outputs {
 
 /* Counters of the last rich_trace, read by rich_hits. */
 typedef struct rich_stats {
-    uint64_t n_photons;      /* photons that entered the trace              */
+    uint64_t n_photons;      /* photons handed to the trace (with the
+                                prefilter on, n_photons - n_fate[8] photons
+                                were propagated)                            */
     uint64_t n_hits;         /* detected photons (may exceed hit_capacity)  */
-    uint64_t n_fate[8];      /* photons per RICH_FATE_* code                */
+    uint64_t n_fate[RICH_N_FATES]; /* photons per RICH_FATE_* code          */
     uint32_t device_status;  /* RICH_OK or the first device-side error      */
     uint32_t photon_order;   /* 1: the trace took each track's photons in
                                 azimuth order (a processing order only;
@@ -340,8 +357,12 @@ RICH_API rich_status rich_emit(rich_ctx *ctx, const rich_tracks *tracks,
  * no photon round trip through memory); otherwise the caller's photons are
  * traced. Mirrors reflect with probability R(lambda) at each reflection;
  * detectors accept with probability QE(lambda) (Sec. 4.3, in flight as in
- * Sec. 6); accepted photons are appended to out->hits and binned. Clears the
- * context's counters first; asynchronous. */
+ * Sec. 6); accepted photons are appended to out->hits and binned. With
+ * opts->n_prefilter > 0 the efficiencies are instead applied once per photon
+ * before propagation (Sec. 4.3) and only accepted photons are traced.
+ * RICH_ERR_ARG for an invalid option (including a prefilter table index
+ * outside the scene's tables). Clears the context's counters first;
+ * asynchronous. */
 RICH_API rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
                        const rich_trace_opts *opts, const rich_outputs *out);
 
@@ -399,7 +420,8 @@ typedef struct rich_grad_params {
  * out: DEVICE outputs of the forward pass; hits must have room for every
  *   hit (RICH_ERR_OVERFLOW otherwise: missing hits are not in the gradient);
  *   pixel_counts optional; event_sums ignored. Hits carry FP64 positions.
- * grad, loss, n_used: HOST results (mean over the hits used). Synchronous. */
+ * grad, loss, n_used: HOST results (mean over the hits used). Synchronous.
+ * opts->n_prefilter must be 0 (RICH_ERR_ARG otherwise). */
 RICH_API rich_status rich_trace_grad(rich_ctx *ctx, const rich_tracks *tracks,
                                      const rich_emit_params *emit,
                                      const rich_grad_params *theta,

@@ -692,6 +692,11 @@ RICH_API rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
     if (refill < 1 || refill > 32) return fail(ctx, RICH_ERR_ARG, "rich_trace: refill_min 1..32");
     const int chunk = o->chunk ? o->chunk : 32;
     if (chunk < 1 || chunk > (1 << 20)) return fail(ctx, RICH_ERR_ARG, "rich_trace: chunk 1..2^20");
+    if (o->n_prefilter < 0 || o->n_prefilter > 4)
+        return fail(ctx, RICH_ERR_ARG, "rich_trace: n_prefilter 0..4");
+    for (int k = 0; k < o->n_prefilter; ++k)
+        if (o->prefilter_tables[k] < 0 || o->prefilter_tables[k] >= ctx->sc.n_tables)
+            return fail(ctx, RICH_ERR_ARG, "rich_trace: prefilter table index outside the scene's tables");
     const int cls = trace_shape_class(threads, o->wide_regs != 0);
     int smem_nodes = o->bvh_smem_nodes;
     if (smem_nodes < 0) smem_nodes = threads > 256 ? 1536 : 0;
@@ -725,6 +730,8 @@ RICH_API rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
     p.fate = out->fate;
     p.refine = ctx->d_refine;
     p.smem_nodes = smem_nodes;
+    p.n_prefilter = o->n_prefilter;
+    for (int k = 0; k < 4; ++k) p.prefilter_tables[k] = k < o->n_prefilter ? o->prefilter_tables[k] : 0;
     LaunchShape shape;
     shape.threads = threads;
     shape.smem = trace_smem_bytes(ctx->sc, smem_nodes);
@@ -784,7 +791,7 @@ RICH_API rich_status rich_hits(rich_ctx *ctx, uint64_t *n_hits, rich_stats *stat
         std::memset(stats, 0, sizeof *stats);
         stats->n_photons = ctx->last_ext ? ctx->last_ext_n : *ctx->h_total;
         stats->n_hits = c.hits;
-        for (int k = 0; k < 8; ++k) stats->n_fate[k] = c.fate[k];
+        for (int k = 0; k < RICH_N_FATES; ++k) stats->n_fate[k] = c.fate[k];
         stats->device_status = c.status;
         stats->photon_order = c.ordered;
     }
@@ -812,6 +819,9 @@ RICH_API rich_status rich_trace_grad(rich_ctx *ctx, const rich_tracks *t,
                     "rich_trace_grad: need targets, sigma > 0 and a hit buffer");
     if (!(th->radius > 0.f) || !(th->n_minus_1 >= 0.f))
         return fail(ctx, RICH_ERR_ARG, "rich_trace_grad: need radius > 0 and n - 1 >= 0");
+    if (o->n_prefilter != 0)
+        return fail(ctx, RICH_ERR_ARG,
+                    "rich_trace_grad: the gradient takes in-flight efficiencies (n_prefilter = 0)");
     for (int k = 0; k < 8; ++k)
         if (!std::isfinite(th->tilt[k]) || std::fabs(th->tilt[k]) > 0.5f)
             return fail(ctx, RICH_ERR_ARG, "rich_trace_grad: tilts must be finite, |tilt| <= 0.5 rad");

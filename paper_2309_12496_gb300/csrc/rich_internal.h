@@ -135,7 +135,7 @@ struct ExtView {             // caller photons
 struct Counters {            // device, cleared before each trace
     unsigned long long work;
     unsigned long long hits;
-    unsigned long long fate[8];
+    unsigned long long fate[RICH_N_FATES];
     unsigned int status;
     unsigned int ordered;    // 1: photons were taken in azimuth order
 };
@@ -162,6 +162,8 @@ struct TraceParams {
     uint8_t *fate;
     RefineRec *refine;        // capacity hit_capacity (refined precision only)
     int32_t smem_nodes;       // BVH nodes [0, smem_nodes) staged in shared memory
+    int32_t n_prefilter;      // > 0: efficiencies applied before propagation
+    int32_t prefilter_tables[4];
 };
 
 // Nominal frame of a sphere tile for the gradient: pole P = C + R a, axis

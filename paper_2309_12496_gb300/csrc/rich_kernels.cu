@@ -339,8 +339,7 @@ struct Photon {
 // t + tan(theta) (cos phi e1 + sin phi e2), normalised, so the small
 // Cherenkov angle is carried by tan(theta) and not by a cosine near 1.
 __device__ __forceinline__ void emit_photon(const TrackRec &tr, uint32_t j,
-                                            const EmitView &em, Photon &ph) {
-    u4 w0 = philox10(0u, j, tr.id, tr.event, em.key0, em.key1);
+                                            const EmitView &em, const u4 &w0, Photon &ph) {
     u4 w1 = philox10(1u, j, tr.id, tr.event, em.key0, em.key1);
     f3 t = mk3(tr.tx, tr.ty, tr.tz);
     float s = u24f(w0.x) * tr.len;
@@ -360,6 +359,11 @@ __device__ __forceinline__ void emit_photon(const TrackRec &tr, uint32_t j,
     ph.event = tr.event;
     ph.id = tr.id;
     ph.j = j;
+}
+
+__device__ __forceinline__ void emit_photon(const TrackRec &tr, uint32_t j,
+                                            const EmitView &em, Photon &ph) {
+    emit_photon(tr, j, em, philox10(0u, j, tr.id, tr.event, em.key0, em.key1), ph);
 }
 
 __global__ void k_materialize(EmitView em, uint64_t n, rich_photons out) {
@@ -856,6 +860,16 @@ __device__ __forceinline__ void add_event_sums(const SceneView &sc, const TraceP
     peer_add(peers, (double)lam, es + 3);
 }
 
+// Efficiencies applied before propagation (Sec. 4.3): the FP32 product,
+// left to right, of the listed response tables at the photon's wavelength.
+__device__ __forceinline__ float prefilter_prob(const SmemScene &S, const TraceParams &P,
+                                                float lam) {
+    float pr = table_eval(S.tables[P.prefilter_tables[0]], lam);
+    for (int k = 1; k < P.n_prefilter; ++k)
+        pr = __fmul_rn(pr, table_eval(S.tables[P.prefilter_tables[k]], lam));
+    return pr;
+}
+
 // ================================================================ trace
 struct TraceArgs {
     SceneView sc;
@@ -953,9 +967,9 @@ k_trace(TraceArgs A) {
             n_snodes = 0;
         }
     }
-    __shared__ unsigned long long s_fate[8];
+    __shared__ unsigned long long s_fate[RICH_N_FATES];
     __shared__ unsigned long long s_hits;
-    if (threadIdx.x < 8) s_fate[threadIdx.x] = 0;
+    if (threadIdx.x < RICH_N_FATES) s_fate[threadIdx.x] = 0;
     if (threadIdx.x == 0) s_hits = 0;
     __syncthreads();
 
@@ -1013,6 +1027,7 @@ k_trace(TraceArgs A) {
                 const uint64_t avail = pool_end - pool_next;
                 const bool take = ((idle >> lane) & 1u) && (uint64_t)rank < avail;
                 int64_t my_track = pool_track;
+                bool rejected = false;
                 if (take) {
                     const uint64_t g = pool_next + (uint64_t)rank;
                     ph.g = g;
@@ -1021,16 +1036,20 @@ k_trace(TraceArgs A) {
                     ph.steps = 0;
                     if (EXT) {
                         ph.track = (uint32_t)g;
-                        ph.o = mk3(A.ext.x[g], A.ext.y[g], A.ext.z[g]);
-                        ph.d = mk3(A.ext.dx[g], A.ext.dy[g], A.ext.dz[g]);
                         ph.lam = A.ext.lambda[g];
                         ph.event = A.ext.event[g];
                         ph.id = A.ext.track[g];
                         ph.j = A.ext.photon[g];
                         const u4 w0 = philox10(0u, ph.j, ph.id, ph.event, em.key0, em.key1);
-                        const u4 w1 = philox10(1u, ph.j, ph.id, ph.event, em.key0, em.key1);
                         ph.w_qe = w0.w;
-                        ph.wr0 = w1.x; ph.wr1 = w1.y; ph.wr2 = w1.z; ph.wr3 = w1.w;
+                        if (P.n_prefilter && !(u24f(w0.w) < prefilter_prob(S, P, ph.lam))) {
+                            rejected = true;
+                        } else {
+                            ph.o = mk3(A.ext.x[g], A.ext.y[g], A.ext.z[g]);
+                            ph.d = mk3(A.ext.dx[g], A.ext.dy[g], A.ext.dz[g]);
+                            const u4 w1 = philox10(1u, ph.j, ph.id, ph.event, em.key0, em.key1);
+                            ph.wr0 = w1.x; ph.wr1 = w1.y; ph.wr2 = w1.z; ph.wr3 = w1.w;
+                        }
                     } else {
                         while (my_track + 1 < em.n_tracks && em.offsets[my_track + 1] <= g)
                             ++my_track;
@@ -1041,17 +1060,32 @@ k_trace(TraceArgs A) {
                         if (ordered && em.offsets[my_track + 1] - toff <= kOrderMaxPhotons)
                             j = em.perm[g];
                         ph.g = toff + j;
-                        emit_photon(tr, j, em, ph);
+                        const u4 w0 = philox10(0u, j, tr.id, tr.event, em.key0, em.key1);
+                        // efficiencies before propagation (Sec. 4.3): only
+                        // the wavelength is needed to decide
+                        if (P.n_prefilter &&
+                            !(u24f(w0.w) <
+                              prefilter_prob(S, P, emit_lambda(u24f(w0.z), em.inv1, em.span))))
+                            rejected = true;
+                        else
+                            emit_photon(tr, j, em, w0, ph);
                     }
-                    alive = true;
+                    if (rejected) {
+                        if (P.fate) P.fate[ph.g] = (uint8_t)RICH_FATE_PREFILTERED;
+                    } else {
+                        alive = true;
+                    }
                 }
                 const unsigned taken = __ballot_sync(kFull, take);
+                const unsigned rej = __ballot_sync(kFull, rejected);
+                if (rej && lane == 0)
+                    atomicAdd(&s_fate[RICH_FATE_PREFILTERED], (unsigned long long)__popc(rej));
                 if (taken) {
                     const int last = 31 - __clz(taken);
                     pool_next += __popc(taken);
                     if (!EXT) pool_track = __shfl_sync(kFull, my_track, last);
                 }
-                idle &= ~taken;
+                idle &= ~(taken & ~rej);
                 if (taken == 0u && pool_next < pool_end) break;  // defensive
             }
         }
@@ -1125,9 +1159,12 @@ k_trace(TraceArgs A) {
                     } else if (ph.n_refl >= P.max_bounces) {
                         fate = RICH_FATE_MAX_BOUNCES;
                     } else {
-                        const float Pr = table_eval(S.tables[M.table], ph.lam);
-                        const float u = u24f(refl_word(ph, ph.n_refl, em));
-                        if (!(u < Pr)) {
+                        // with the efficiencies applied before propagation
+                        // every front-side reflection succeeds
+                        const bool pass =
+                            P.n_prefilter ||
+                            u24f(refl_word(ph, ph.n_refl, em)) < table_eval(S.tables[M.table], ph.lam);
+                        if (!pass) {
                             fate = RICH_FATE_MIRROR_ABSORBED;
                         } else {
                             ph.d = normalize3(reflect_f(ph.d, n_sh));
@@ -1142,8 +1179,9 @@ k_trace(TraceArgs A) {
                         ph.o = p;
                         ph.skip = b.prim;
                     } else {
-                        const float Pq = table_eval(S.tables[M.table], ph.lam);
-                        if (!(u24f(ph.w_qe) < Pq)) {
+                        const bool pass =
+                            P.n_prefilter || u24f(ph.w_qe) < table_eval(S.tables[M.table], ph.lam);
+                        if (!pass) {
                             fate = RICH_FATE_QE_REJECTED;
                         } else {
                             fate = RICH_FATE_DETECTED;
@@ -1221,7 +1259,7 @@ k_trace(TraceArgs A) {
         }
     }
     __syncthreads();
-    if (threadIdx.x < 8 && s_fate[threadIdx.x])
+    if (threadIdx.x < RICH_N_FATES && s_fate[threadIdx.x])
         atomicAdd(&A.ctr->fate[threadIdx.x], s_fate[threadIdx.x]);
     if (n_snodes_req > 0 && n_snodes == 0) {
         // the copy had not completed: give it a second bounded wait so the

@@ -24,8 +24,10 @@ STATUS_NAMES = {0: "RICH_OK", 1: "RICH_ERR_ARG", 2: "RICH_ERR_CUDA", 3: "RICH_ER
                 7: "RICH_ERR_STATE"}
 PREC_FP32, PREC_REFINE64 = 0, 1
 FATE_NAMES = ["none", "escaped", "mirror_absorbed", "absorbed", "qe_rejected",
-              "detected", "max_bounces", "max_steps"]
+              "detected", "max_bounces", "max_steps", "prefiltered"]
 FATE_DETECTED = 5
+FATE_PREFILTERED = 8
+N_FATES = 9
 
 EXPORTED = ["rich_create", "rich_destroy", "rich_set_stream", "rich_init_geometry",
             "rich_emit", "rich_trace", "rich_hits", "rich_philox", "rich_last_error",
@@ -81,7 +83,18 @@ class TraceOpts(C.Structure):
                 ("t_min", C.c_float), ("block_threads", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("refill_min", C.c_int32),
                 ("chunk", C.c_int32), ("wide_regs", C.c_int32),
-                ("bvh_smem_nodes", C.c_int32)]
+                ("bvh_smem_nodes", C.c_int32), ("n_prefilter", C.c_int32),
+                ("prefilter_tables", C.c_int32 * 4)]
+
+
+def _prefilter_fields(prefilter):
+    """TraceOpts fields of a prefilter table list (Sec. 4.3 efficiencies
+    applied before propagation; empty: in flight)."""
+    tabs = [int(x) for x in (prefilter or ())]
+    if len(tabs) > 4:
+        raise ValueError("at most 4 prefilter tables")
+    return {"n_prefilter": len(tabs),
+            "prefilter_tables": (C.c_int32 * 4)(*(tabs + [0] * (4 - len(tabs))))}
 
 
 class Outputs(C.Structure):
@@ -97,7 +110,7 @@ class GradParams(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("n_photons", C.c_uint64), ("n_hits", C.c_uint64),
-                ("n_fate", C.c_uint64 * 8), ("device_status", C.c_uint32),
+                ("n_fate", C.c_uint64 * N_FATES), ("device_status", C.c_uint32),
                 ("photon_order", C.c_uint32)]
 
 
@@ -339,11 +352,14 @@ class Context:
     def trace(self, outputs: TraceOutputs, photons: PhotonBuffers | None = None,
               precision=PREC_REFINE64, max_bounces=8, max_steps=16, t_min=1e-3,
               seed=0, block_threads=0, blocks_per_sm=0, refill_min=0, chunk=0,
-              wide_regs=0, bvh_smem_nodes=-1):
+              wide_regs=0, bvh_smem_nodes=-1, prefilter=()):
+        """prefilter: scene table indices whose product is applied as one
+        accept/reject per photon before propagation (Sec. 4.3)."""
         o = TraceOpts(seed=int(seed), precision=precision, max_bounces=max_bounces,
                       max_steps=max_steps, t_min=t_min, block_threads=block_threads,
                       blocks_per_sm=blocks_per_sm, refill_min=refill_min, chunk=chunk,
-                      wide_regs=wide_regs, bvh_smem_nodes=bvh_smem_nodes)
+                      wide_regs=wide_regs, bvh_smem_nodes=bvh_smem_nodes,
+                      **_prefilter_fields(prefilter))
         pd = photons.desc() if photons is not None else None
         st = load().rich_trace(self.handle, None if pd is None else C.byref(pd),
                                C.byref(o), C.byref(outputs.desc()))
@@ -364,14 +380,15 @@ class Context:
                       lambda_min=200.0, lambda_max=600.0, seed=0, precision=PREC_REFINE64,
                       max_bounces=8, max_steps=16, t_min=1e-3, block_threads=0,
                       blocks_per_sm=0, refill_min=0, chunk=0, wide_regs=0,
-                      bvh_smem_nodes=-1):
+                      bvh_smem_nodes=-1, prefilter=()):
         """Capture emit + trace into a CUDA graph (after a warm-up pass)."""
         prm = EmitParams(seed=int(seed), n_minus_1=float(n_minus_1),
                          lambda_min=float(lambda_min), lambda_max=float(lambda_max))
         o = TraceOpts(seed=0, precision=precision, max_bounces=max_bounces,
                       max_steps=max_steps, t_min=t_min, block_threads=block_threads,
                       blocks_per_sm=blocks_per_sm, refill_min=refill_min, chunk=chunk,
-                      wide_regs=wide_regs, bvh_smem_nodes=bvh_smem_nodes)
+                      wide_regs=wide_regs, bvh_smem_nodes=bvh_smem_nodes,
+                      **_prefilter_fields(prefilter))
         self._graph_keep = (tracks, outputs)
         _check(self.handle, load().rich_graph_capture(self.handle, C.byref(tracks.desc()),
                                                       C.byref(prm), C.byref(o),

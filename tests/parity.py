@@ -25,7 +25,7 @@ def n_events(tracks):
 
 
 def run_gpu(wl: W.Workload, precision=rich.PREC_REFINE64, ctx=None, want_fate=True,
-            hist=True, launch=None, photons=None, dtracks=None, trace_seed=0):
+            hist=True, launch=None, photons=None, dtracks=None, trace_seed=0, prefilter=()):
     set_grid(wl.scene.planes)
     own = ctx is None
     if own:
@@ -36,7 +36,8 @@ def run_gpu(wl: W.Workload, precision=rich.PREC_REFINE64, ctx=None, want_fate=Tr
     ne = n_events(wl.tracks) if hist else 0
     out = rich.TraceOutputs(max(n, 1), wl.scene.pixels_per_event, len(wl.scene.planes),
                             ne, n if want_fate else 0)
-    ctx.trace(out, photons=photons, precision=precision, seed=trace_seed, **(launch or {}))
+    ctx.trace(out, photons=photons, precision=precision, seed=trace_seed, prefilter=prefilter,
+              **(launch or {}))
     n_hits, stats = ctx.hits()
     res = {"n": n, "n_hits": n_hits, "stats": stats, "hits": out.hits_numpy(n_hits),
            "fate": out.fate.cpu().numpy() if want_fate and n else np.zeros(0, np.uint8)}
