@@ -78,7 +78,8 @@ class Params(C.Structure):
                 ("t_min", C.c_double), ("eps", C.c_double),
                 ("prob_eps", C.c_double), ("use_bvh", C.c_int32),
                 ("n_threads", C.c_int32), ("n_prefilter", C.c_int32),
-                ("prefilter_tables", C.c_int32 * 4)]
+                ("prefilter_tables", C.c_int32 * 4), ("source", C.c_int32),
+                ("yield_per_mm", C.c_float), ("spectrum", C.c_void_p)]
 
 
 class PhotonOut(C.Structure):
@@ -167,14 +168,26 @@ def params(workload=None, seed=None, n_minus_1=None, lambda_min=None,
     w = workload
     # n - 1 and the band are FP32 inputs of the propagator: promote exactly
     nm1 = float(np.float32(n_minus_1 if n_minus_1 is not None else w.n_minus_1))
-    return Params(seed=int(seed if seed is not None else w.seed),
+    # light source: Cherenkov, or isotropic with a yield per mm and a binned
+    # spectrum taken from the scene's tables (a CDF table)
+    source = int(getattr(w, "source", 0)) if w is not None else 0
+    spec = None
+    st = int(getattr(w, "spectrum_table", -1)) if w is not None else -1
+    if source == 1 and st >= 0:
+        spec = np.ascontiguousarray(w.scene.tables[st:st + 1])
+    prm = Params(seed=int(seed if seed is not None else w.seed),
                   n_minus_1=nm1,
                   lambda_min=lambda_min if lambda_min is not None else w.lambda_min,
                   lambda_max=lambda_max if lambda_max is not None else w.lambda_max,
                   max_bounces=max_bounces, max_steps=max_steps, t_min=t_min,
                   eps=eps, prob_eps=prob_eps, use_bvh=int(use_bvh),
                   n_threads=n_threads, n_prefilter=len(prefilter),
-                  prefilter_tables=(C.c_int32 * 4)(*(list(prefilter) + [0] * (4 - len(prefilter)))))
+                  prefilter_tables=(C.c_int32 * 4)(*(list(prefilter) + [0] * (4 - len(prefilter)))),
+                  source=source,
+                  yield_per_mm=float(getattr(w, "yield_per_mm", 0.0)) if w is not None else 0.0,
+                  spectrum=None if spec is None else spec.ctypes.data)
+    prm._keep = spec
+    return prm
 
 
 def track_yield(tracks, prm):

@@ -116,6 +116,14 @@ typedef struct {
      * the in-flight reflectivity and QE tests switched off. */
     int32_t n_prefilter;
     int32_t prefilter_tables[4];
+    /* Light source (Sec. 6 names liquids and scintillation as the next
+     * sources): 0 = Cherenkov emission along the track; 1 = isotropic
+     * emission along the track (scintillation), yield_per_mm photons per mm
+     * on average, wavelength from the `spectrum` CDF table (kind 3) or, when
+     * spectrum is NULL, from the 1/lambda^2 law on [lambda_min, lambda_max]. */
+    int32_t source;
+    float yield_per_mm;
+    const void *spectrum;
 } o_params;
 
 /* Per-photon results, arrays indexed by global photon index. Any pointer
@@ -139,7 +147,8 @@ typedef struct {
 enum { FATE_NONE = 0, FATE_ESCAPED = 1, FATE_MIRROR_ABSORBED = 2,
        FATE_ABSORBED = 3, FATE_QE_REJECTED = 4, FATE_DETECTED = 5,
        FATE_MAX_BOUNCES = 6, FATE_MAX_STEPS = 7, FATE_PREFILTERED = 8 };
-enum { TAB_CONST = 0, TAB_GAUSS = 1, TAB_HIST = 2 };
+enum { TAB_CONST = 0, TAB_GAUSS = 1, TAB_HIST = 2, TAB_CDF = 3 };
+enum { SRC_CHERENKOV = 0, SRC_ISOTROPIC = 1 };
 enum { MAT_MIRROR = 0, MAT_ABSORBER = 1, MAT_DETECTOR = 2 };
 enum { MAT_SMOOTH = 1 };
 enum { PRIM_SPHERE = 0, PRIM_RECT = 1, PRIM_TRI = 2 };
@@ -306,9 +315,11 @@ int64_t oracle_yield(const o_tracks_in *t, const o_params *prm,
     uint64_t total = 0;
     for (int64_t i = 0; i < t->n; ++i) {
         double beta = track_beta(t->p[i], t->mass[i]);
-        double mu = (double)t->length[i] *
-                    oracle_yield_per_mm(prm->n_minus_1, beta,
-                                        prm->lambda_min, prm->lambda_max);
+        double mu = prm->source == SRC_ISOTROPIC
+                        ? (double)t->length[i] * (double)prm->yield_per_mm
+                        : (double)t->length[i] *
+                              oracle_yield_per_mm(prm->n_minus_1, beta,
+                                                  prm->lambda_min, prm->lambda_max);
         int64_t k;
         if (t->n_fixed) {
             k = t->n_fixed[i];
@@ -355,6 +366,24 @@ static float emit_lambda(float u, float lam1, float lam2)
     return 1.0f / inv;
 }
 
+/* Wavelength from a binned emission spectrum by inverting its CDF: the
+ * table holds c_0 = 0 <= c_1 <= ... <= c_n = 1 at the bin edges
+ * lambda_0 + k w; the bin is the k with c_k <= u < c_{k+1} and the
+ * wavelength is linear inside it. FP32, one IEEE operation at a time (the
+ * wavelength selects response-table bins). */
+static float spectrum_lambda(const o_table_in *tab, float u)
+{
+    int k = 0;
+    while (k + 1 < tab->nbins && tab->values[k + 1] <= u) ++k;
+    volatile float num = u - tab->values[k];
+    volatile float den = tab->values[k + 1] - tab->values[k];
+    volatile float fr = num / den;
+    volatile float kk = (float)k + fr;
+    volatile float off = kk * tab->p1;
+    volatile float lam = tab->p0 + off;
+    return lam;
+}
+
 /* Orthonormal basis around a unit vector t (Duff, Burgess, Christensen,
  * Hery, Kensler, Liani, Villemin, "Building an orthonormal basis,
  * revisited", JCGT 6(1), 2017). */
@@ -390,8 +419,27 @@ static void emit_photon(const o_tracks_in *t, const o_params *prm, int64_t i,
     double s = u24(w0[0]) * (double)t->length[i];
     ph->o = add(mk(t->x[i], t->y[i], t->z[i]), scl(dir, s));
     double phi = 2.0 * PI_D * u24(w0[1]);
-    ph->lambda = emit_lambda((float)u24(w0[2]), prm->lambda_min,
-                             prm->lambda_max);
+    if (prm->source == SRC_ISOTROPIC && prm->spectrum)
+        ph->lambda = spectrum_lambda((const o_table_in *)prm->spectrum,
+                                     (float)u24(w0[2]));
+    else
+        ph->lambda = emit_lambda((float)u24(w0[2]), prm->lambda_min,
+                                 prm->lambda_max);
+    ph->u_qe = u24(w0[3]);
+    for (int k = 0; k < 4; ++k) {
+        ph->u_refl[k] = u24(w1[k]);
+        ph->u_refl[4 + k] = u24(w2[k]);
+    }
+    ph->u_smear[0] = u24(w3[0]);
+    ph->u_smear[1] = u24(w3[1]);
+    if (prm->source == SRC_ISOTROPIC) {
+        /* uniform on the unit sphere in the world frame: cos(theta) uniform
+         * on [-1, 1] from draw block 3 word 2, azimuth from block 0 word 1 */
+        double ct = 1.0 - 2.0 * u24(w3[2]);
+        double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+        ph->d = mk(st * cos(phi), st * sin(phi), ct);
+        return;
+    }
     double beta = track_beta(t->p[i], t->mass[i]);
     double nb = (1.0 + prm->n_minus_1) * beta;
     double ct = 1.0 / nb;
@@ -400,13 +448,6 @@ static void emit_photon(const o_tracks_in *t, const o_params *prm, int64_t i,
     basis(dir, &e1, &e2);
     ph->d = add(scl(dir, ct),
                 scl(add(scl(e1, cos(phi)), scl(e2, sin(phi))), st));
-    ph->u_qe = u24(w0[3]);
-    for (int k = 0; k < 4; ++k) {
-        ph->u_refl[k] = u24(w1[k]);
-        ph->u_refl[4 + k] = u24(w2[k]);
-    }
-    ph->u_smear[0] = u24(w3[0]);
-    ph->u_smear[1] = u24(w3[1]);
 }
 
 void oracle_emit(const o_tracks_in *t, const o_params *prm, int64_t track,
@@ -1061,6 +1102,7 @@ int oracle_trace(void *scene, const o_tracks_in *t, const o_params *prm,
     const o_scene *sc = (const o_scene *)scene;
     if (prm->max_steps > 16 || prm->max_bounces > 8) return -1;
     if (prm->n_prefilter < 0 || prm->n_prefilter > 4) return -1;
+    if (prm->source != SRC_CHERENKOV && prm->source != SRC_ISOTROPIC) return -1;
     for (int k = 0; k < prm->n_prefilter; ++k)
         if (prm->prefilter_tables[k] < 0 || prm->prefilter_tables[k] >= sc->n_tables)
             return -1;

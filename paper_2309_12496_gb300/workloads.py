@@ -63,7 +63,8 @@ assert MATERIAL_DTYPE.itemsize == 16
 assert SPHERE_DTYPE.itemsize == 160
 assert RECT_DTYPE.itemsize == 80
 
-TABLE_CONST, TABLE_GAUSS, TABLE_HIST = 0, 1, 2
+TABLE_CONST, TABLE_GAUSS, TABLE_HIST, TABLE_CDF = 0, 1, 2, 3
+SOURCE_CHERENKOV, SOURCE_ISOTROPIC = 0, 1
 MAT_MIRROR, MAT_ABSORBER, MAT_DETECTOR = 0, 1, 2
 MAT_SMOOTH = 1
 
@@ -133,6 +134,22 @@ class _Builder:
         t["kind"], t["p0"], t["p1"] = TABLE_HIST, lam0, width
         t["nbins"] = len(values)
         t["values"][: len(values)] = values
+        self.tables.append(t)
+        return len(self.tables) - 1
+
+    def table_cdf(self, lam0, width, weights):
+        """Binned emission spectrum as its CDF at the bin edges: c_0 = 0,
+        c_n = 1, nondecreasing, rounded to FP32 (both sides invert the same
+        FP32 table)."""
+        w = np.asarray(weights, np.float64)
+        c = np.concatenate([[0.0], np.cumsum(w) / w.sum()])
+        c = f32(c)
+        c[0], c[-1] = 0.0, 1.0
+        c = np.maximum.accumulate(c)
+        t = np.zeros((), TABLE_DTYPE)
+        t["kind"], t["p0"], t["p1"] = TABLE_CDF, lam0, width
+        t["nbins"] = len(w)
+        t["values"][: len(c)] = c
         self.tables.append(t)
         return len(self.tables) - 1
 
@@ -637,6 +654,9 @@ class Workload:
     lambda_max: float = 600.0
     seed: int = 0
     description: str = ""
+    source: int = SOURCE_CHERENKOV
+    yield_per_mm: float = 0.0         # isotropic source: mean photons per mm
+    spectrum_table: int = -1          # isotropic source: CDF table index
 
 
 def point_source(n_photons=100_000) -> Workload:
@@ -726,3 +746,119 @@ def nominal_theta(scene, n_minus_1):
     th[8] = float(scene.spheres[0]["radius"]) if len(scene.spheres) else 0.0
     th[9] = float(np.float32(n_minus_1))
     return th
+
+
+# ------------------------------------------- other light sources (Sec. 6)
+# Sec. 6 names water Cherenkov detectors and scintillation light in liquid
+# noble-gas detectors as the next light sources. Two synthetic stand-ins:
+
+# Wavelength-shifted scintillation light (TPB-like emission, peak near
+# 425 nm), 20 bins of 15 nm from 350 nm (synthetic shape).
+SCINT_LAMBDA0, SCINT_WIDTH = 350.0, 15.0
+SCINT_WEIGHTS = [math.exp(-0.5 * ((350.0 + 15.0 * (k + 0.5) - 425.0) / 30.0) ** 2)
+                 for k in range(20)]
+# Specular wall reflectivity of the scintillator box, 25 nm bins over
+# 300-700 nm (synthetic shape).
+WALL_LAMBDA0, WALL_WIDTH = 300.0, 25.0
+WALL_R = [0.97 - 0.0025 * k for k in range(16)]
+
+
+def _box_walls(b, half, material_for_face, n_pix):
+    """Six inward-facing faces of the cube [-half, half]^3; faces 0/1 are
+    z = -half / z = +half (detector planes of n_pix^2 pixels when their
+    material is a detector), 2..5 the side walls."""
+    side = 2.0 * half
+    pitch = side / n_pix
+    faces = [
+        ((-half, -half, -half), (1, 0, 0), (0, 1, 0)),    # z = -half, normal +z
+        ((-half, half, half), (1, 0, 0), (0, -1, 0)),     # z = +half, normal -z
+        ((-half, -half, -half), (0, 1, 0), (0, 0, 1)),    # x = -half, normal +x
+        ((half, half, -half), (0, -1, 0), (0, 0, 1)),     # x = +half, normal -x
+        ((half, -half, -half), (-1, 0, 0), (0, 0, 1)),    # y = -half, normal +y
+        ((-half, half, -half), (1, 0, 0), (0, 0, 1)),     # y = +half, normal -y
+    ]
+    for k, (o, u, v) in enumerate(faces):
+        m = material_for_face(k)
+        det = b.materials[m]["kind"] == MAT_DETECTOR
+        b.rect(origin=o, u_axis=u, v_axis=v, width=side, height=side, material=m,
+               nx=n_pix if det else 0, ny=n_pix if det else 0, pitch=pitch if det else 0.0)
+
+
+def scint_box_scene(half=500.0, n_pix=256) -> Scene:
+    """Liquid-argon-like scintillator volume (synthetic): the cube
+    [-500, 500]^3 mm with photodetector planes of 256^2 pixels
+    (3.90625 mm) on the top and bottom faces and specular reflecting side
+    walls, so photons reach the planes after up to several reflections.
+    Tables: 0 QE, 1 wall reflectivity, 2 emission spectrum (CDF)."""
+    b = _Builder("scint_box")
+    t_qe = b.table_hist(QE_LAMBDA0, QE_WIDTH, QE_BINS)
+    t_wall = b.table_hist(WALL_LAMBDA0, WALL_WIDTH, WALL_R)
+    b.table_cdf(SCINT_LAMBDA0, SCINT_WIDTH, SCINT_WEIGHTS)
+    m_wall = b.material(MAT_MIRROR, t_wall)
+    m_det = [b.material(MAT_DETECTOR, t_qe, plane=i) for i in range(2)]
+    _box_walls(b, half, lambda k: m_det[k] if k < 2 else m_wall, n_pix)
+    return b.build()
+
+
+def scint_tracks(n, seed=0, length=100.0, inner=350.0, event=0) -> Tracks:
+    """n straight segments of `length` mm starting uniformly in the cube
+    [-inner, inner]^3, isotropic directions (they stay inside the box for
+    inner + length < 500)."""
+    rng = np.random.default_rng(seed)
+    o = rng.uniform(-inner, inner, (n, 3))
+    ct = rng.uniform(-1.0, 1.0, n)
+    ph = rng.uniform(0.0, 2.0 * math.pi, n)
+    st = np.sqrt(1.0 - ct * ct)
+    d = np.stack([st * np.cos(ph), st * np.sin(ph), ct], axis=1)
+    t = _make_tracks(n, (0.0, 0.0, 0.0), d, np.full(n, 1.0), np.full(n, MUON_MASS),
+                     np.full(n, length), np.full(n, event), np.arange(n))
+    t.x, t.y, t.z = f32(o[:, 0]), f32(o[:, 1]), f32(o[:, 2])
+    return t
+
+
+def scintillation(n_tracks=200, seed=0, yield_per_mm=20.0) -> Workload:
+    """Isotropic scintillation light from n_tracks 100 mm segments inside
+    the scintillator box, yield_per_mm photons per mm (Poisson), the
+    binned emission spectrum of the scene (~4e5 photons for 200 tracks)."""
+    return Workload("scintillation", scint_box_scene(), scint_tracks(n_tracks, seed=seed),
+                    n_minus_1=0.0, lambda_min=SCINT_LAMBDA0,
+                    lambda_max=SCINT_LAMBDA0 + SCINT_WIDTH * len(SCINT_WEIGHTS),
+                    seed=seed, source=SOURCE_ISOTROPIC, yield_per_mm=yield_per_mm,
+                    spectrum_table=2,
+                    description=f"{n_tracks} x 100 mm segments, isotropic emission, "
+                    f"{yield_per_mm} photons/mm, 1 m scintillator box, mirror side walls")
+
+
+def water_tank_scene(half=2000.0, n_pix=256) -> Scene:
+    """Water Cherenkov tank (synthetic): the cube [-2000, 2000]^3 mm with
+    all six faces photodetector planes of 256^2 pixels (15.625 mm).
+    Tables: 0 QE."""
+    b = _Builder("water_tank")
+    t_qe = b.table_hist(QE_LAMBDA0, QE_WIDTH, QE_BINS)
+    m_det = [b.material(MAT_DETECTOR, t_qe, plane=i) for i in range(6)]
+    _box_walls(b, half, lambda k: m_det[k], n_pix)
+    return b.build()
+
+
+def water_muons(n, seed=0, length=2000.0, max_angle=0.3, event=0) -> Tracks:
+    """n through-going muons entering near the top of the tank and heading
+    down within max_angle of -z, p log-uniform 1-20 GeV/c, emitting along
+    `length` mm."""
+    rng = np.random.default_rng(seed)
+    p = 1.0 * 20.0 ** rng.random(n)
+    d = _cone_dirs(rng, n, max_angle)
+    d[:, 2] = -d[:, 2]
+    o = np.stack([rng.uniform(-600, 600, n), rng.uniform(-600, 600, n),
+                  np.full(n, 1500.0)], axis=1)
+    t = _make_tracks(n, (0.0, 0.0, 0.0), d, p, np.full(n, MUON_MASS), np.full(n, length),
+                     np.full(n, event), np.arange(n))
+    t.x, t.y, t.z = f32(o[:, 0]), f32(o[:, 1]), f32(o[:, 2])
+    return t
+
+
+def water(n_tracks=10, seed=0) -> Workload:
+    """Cherenkov light of muons in water (n = 1.33, theta ~ 41 degrees,
+    ~33 photons/mm over 300-600 nm): ~6.6e5 photons for 10 tracks."""
+    return Workload("water", water_tank_scene(), water_muons(n_tracks, seed=seed),
+                    n_minus_1=0.33, lambda_min=300.0, lambda_max=600.0, seed=seed,
+                    description=f"{n_tracks} muons, 2000 mm of water, 4 m tank of detector walls")

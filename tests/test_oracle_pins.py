@@ -525,3 +525,134 @@ def test_prefilter_matches_in_flight_statistics_rich1(oracle_lib):
     a, b = sel(fly), sel(pre)
     assert a > 5000
     assert abs(a - b) < 4 * math.sqrt(a + b)
+
+
+# ----------------------------------------------- other light sources (Sec. 6)
+def _all_detector_box(half=500.0, n_pix=64, qe=1.0):
+    """Cube of six inward-facing detector planes with a constant QE."""
+    b = w._Builder("detector_box")
+    t = b.table_const(qe)
+    mats = [b.material(w.MAT_DETECTOR, t, plane=i) for i in range(6)]
+    w._box_walls(b, half, lambda k: mats[k], n_pix)
+    return b.build()
+
+
+def test_isotropic_emission_laws(oracle_lib):
+    """Isotropic (scintillation) emission: unit directions with cos(theta)
+    uniform on [-1, 1] and uniform azimuth; origins on the segment; the
+    wavelength follows the binned spectrum (bin frequencies by chi^2 against
+    the CDF differences, uniform inside each bin)."""
+    from scipy import stats
+    wl = w.scintillation(20)
+    prm = oracle_lib.params(wl)
+    n, mu, off = oracle_lib.track_yield(wl.tracks, prm)
+    tab = wl.scene.tables[wl.spectrum_table]
+    cdf = tab["values"][: tab["nbins"] + 1].astype(np.float64)
+    dirs, lams, s_rel = [], [], []
+    for i in range(4):
+        t0 = np.array([wl.tracks.x[i], wl.tracks.y[i], wl.tracks.z[i]], np.float64)
+        td = np.array([wl.tracks.dx[i], wl.tracks.dy[i], wl.tracks.dz[i]], np.float64)
+        td /= np.linalg.norm(td)
+        for j in range(int(n[i])):
+            o, d, lam = oracle_lib.emit(wl.tracks, prm, i, j)
+            dirs.append(d)
+            lams.append(lam)
+            r = o - t0
+            s = float(np.dot(r, td))
+            assert np.linalg.norm(r - s * td) < 1e-9
+            s_rel.append(s / float(wl.tracks.length[i]))
+    d = np.array(dirs)
+    assert np.abs(np.linalg.norm(d, axis=1) - 1).max() < 1e-14
+    assert stats.kstest((d[:, 2] + 1) / 2, "uniform").pvalue > 1e-3
+    phi = np.arctan2(d[:, 1], d[:, 0])
+    assert stats.kstest((phi + math.pi) / (2 * math.pi), "uniform").pvalue > 1e-3
+    assert stats.kstest(np.array(s_rel), "uniform").pvalue > 1e-3
+    lam = np.array(lams, np.float64)
+    k = np.floor((lam - tab["p0"]) / tab["p1"]).astype(int)
+    counts = np.bincount(k, minlength=tab["nbins"])[: tab["nbins"]]
+    p = np.diff(cdf)
+    big = p * len(lam) > 20
+    e = p[big] * len(lam)
+    chi2 = (((counts[big] - e) ** 2) / e).sum()
+    assert stats.chi2.sf(chi2, big.sum() - 1) > 1e-4
+    frac = (lam - tab["p0"]) / tab["p1"] - k
+    assert stats.kstest(frac, "uniform").pvalue > 1e-3
+
+
+def test_isotropic_yield_is_poisson_in_length(oracle_lib):
+    """Photon count per segment ~ Poisson(yield x length): mean and variance
+    of 400 segments of 100 mm at 20 photons/mm."""
+    wl = w.scintillation(400)
+    n, mu, _ = oracle_lib.track_yield(wl.tracks, oracle_lib.params(wl))
+    assert np.allclose(mu, 2000.0, rtol=1e-6)
+    assert abs(n.mean() - 2000.0) < 4 * math.sqrt(2000.0 / 400)
+    assert 0.75 < n.var() / 2000.0 < 1.3
+
+
+def test_isotropic_point_in_detector_box_solid_angle(oracle_lib):
+    """An isotropic point source at the centre of a cube of detector faces
+    (QE = 1): no photon escapes, each face receives 1/6 of them, and on a
+    face at distance d the fraction of photons within radius rho of the
+    face centre is (1 - d / sqrt(rho^2 + d^2)) / 2 (solid angle of a cone)."""
+    from scipy import stats
+    scene = _all_detector_box()
+    tr = w._make_tracks(1, (0.0, 0.0, 0.0), np.array([[0.0, 0.0, 1.0]]), p=[1.0],
+                        mass=[0.0], length=[0.0], event=[0], tid=[0], n_fixed=[60000])
+    wl = w.Workload("iso_point", scene, tr, n_minus_1=0.0, source=w.SOURCE_ISOTROPIC,
+                    lambda_min=300.0, lambda_max=500.0)
+    out = oracle_lib.Scene(scene).trace(tr, oracle_lib.params(wl))
+    assert np.all(out["fate"] == 5)
+    per = np.bincount(out["plane"], minlength=6)
+    assert stats.chisquare(per).pvalue > 1e-3
+    top = out["plane"] == 1
+    rho = np.hypot(out["u"][top] - 500.0, out["v"][top] - 500.0)
+    inside = rho < 500.0
+    cdf = lambda r: (1 - 500.0 / np.sqrt(r * r + 500.0 ** 2)) / 2
+    # conditional on rho < 500 (the inscribed disc)
+    x = cdf(rho[inside]) / cdf(500.0)
+    assert stats.kstest(x, "uniform").pvalue > 1e-3
+    assert abs(inside.sum() / len(out["fate"]) - cdf(500.0)) < 4 * math.sqrt(cdf(500.0) / 60000)
+
+
+def test_water_point_source_ring(oracle_lib):
+    """Water (n = 1.33), beta = 1: a point source at the tank centre along
+    +z puts every photon on the top face at radius d tan(theta) =
+    2000 sqrt(n^2 - 1) = 1753.67 mm from its centre (Sec. 3 angle; the
+    liquid radiators of Sec. 6); the Frank-Tamm yield per mm over 300-600 nm
+    is 2 pi alpha (1 - 1/n^2)(1/300 nm - 1/600 nm)."""
+    scene = w.water_tank_scene()
+    tr = w._make_tracks(1, (0.0, 0.0, 0.0), np.array([[0.0, 0.0, 1.0]]), p=[1e6],
+                        mass=[0.0], length=[0.0], event=[0], tid=[0], n_fixed=[5000])
+    wl = w.Workload("water_point", scene, tr, n_minus_1=0.33, lambda_min=300.0,
+                    lambda_max=600.0)
+    out = oracle_lib.Scene(scene).trace(tr, oracle_lib.params(wl))
+    hit = out["fate"] == 5
+    assert hit.sum() > 500
+    assert np.all(out["plane"][hit] == 1)
+    n = 1 + float(np.float32(0.33))
+    r = np.hypot(out["u"][hit] - 2000.0, out["v"][hit] - 2000.0)
+    assert np.abs(r - 2000.0 * math.sqrt(n * n - 1)).max() < 1e-9
+    assert set(np.unique(out["fate"])) <= {4, 5}
+    y = oracle_lib.yield_per_mm(float(np.float32(0.33)), 1.0, 300.0, 600.0)
+    alpha = 1 / 137.035999
+    assert y == pytest.approx(2 * math.pi * alpha * (1 - 1 / n**2) * (1e6 / 300 - 1e6 / 600),
+                              rel=1e-12)
+    assert 30 < y < 36
+
+
+def test_scintillation_box_bookkeeping(oracle_lib):
+    """Scintillation box: photons end detected on the top/bottom planes,
+    QE-rejected, absorbed by a wall reflection or at the reflection limit;
+    hits after k wall reflections exist for several k; counts and sums agree
+    with the hit list."""
+    wl = w.scintillation(30)
+    out = oracle_lib.Scene(wl.scene).trace(wl.tracks, oracle_lib.params(wl))
+    f = out["fate"]
+    esc = (f == 1) & (out["graze"] == 0)
+    assert esc.sum() == 0
+    assert set(np.unique(f)) <= {1, 2, 4, 5, 6}
+    det = f == 5
+    assert set(np.unique(out["plane"][det])) == {0, 1}
+    assert len(np.unique(out["n_refl"][det])) >= 4
+    assert out["pixel_counts"].sum() == det.sum()
+    assert (out["graze"] != 0).mean() < 0.01
