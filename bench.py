@@ -307,6 +307,7 @@ def main():
             line["adjoint"] = run_adjoint(dev, rank)
             line["rich2_chunked"] = run_chunked(dev, rank)
             line["prefilter"] = run_prefilter(dev, prec, rank)
+            line["other_sources"] = run_sources(dev, prec, rank)
     if line is not None and not args.no_extras and ws == 1:
         v, cores, passes, nph, el = oracle_rate(10.0)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -440,6 +441,40 @@ def run_prefilter(dev, prec, rank, n_tracks=10_000):
                      "propagated_per_step": traced,
                      "propagated_photons_per_s": traced / (ms / 1e3), "hits_per_step": n_hits}
     ctx.close()
+    return res
+
+
+def run_sources(dev, prec, rank):
+    """The other light sources named in Sec. 6: isotropic scintillation
+    light (2000 segments of 100 mm at 20 photons/mm, ~4e6 photons, in the
+    1 m box with mirror side walls) and Cherenkov light of 100 muons in the
+    4 m water tank (~6.6e6 photons); emit + trace per step."""
+    import torch
+    from paper_2309_12496_gb300 import rich
+    from paper_2309_12496_gb300 import workloads as W
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    res = {}
+    for name, wl in (("scintillation", W.scintillation(2000, seed=rank)),
+                     ("water", W.water(100, seed=rank))):
+        ctx = rich.Context(int(dev.split(":")[1]))
+        ctx.init_geometry(wl.scene)
+        dt = rich.DeviceTracks(wl.tracks, device=dev)
+        kw = dict(source=wl.source, yield_per_mm=wl.yield_per_mm,
+                  spectrum_table=wl.spectrum_table)
+        n = ctx.emit(dt, wl.n_minus_1, wl.lambda_min, wl.lambda_max, seed=wl.seed, **kw)
+        out = rich.TraceOutputs(int(n * 0.5) + 1024, wl.scene.pixels_per_event,
+                                len(wl.scene.planes), 1, 0, device=dev)
+
+        def step():
+            ctx.emit(dt, wl.n_minus_1, wl.lambda_min, wl.lambda_max, seed=wl.seed, sync=False,
+                     **kw)
+            ctx.trace(out, precision=prec)
+        ms = _time_steps(step, 5, 2, flush)
+        n_hits, _ = ctx.hits()
+        ctx.close()
+        res[name] = {"value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                     "photons_per_step": n, "hits_per_step": n_hits,
+                     "workload": wl.description}
     return res
 
 

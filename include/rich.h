@@ -37,7 +37,8 @@
  *                            w2 -> wavelength, w3 -> quantum-efficiency test
  *       per photon, block 1: reflectivity tests at mirror reflections 0..3
  *       per photon, block 2: reflectivity tests at mirror reflections 4..7
- *       per photon, block 3: w0, w1 -> Gaussian smear of the hit (loss only)
+ *       per photon, block 3: w0, w1 -> Gaussian smear of the hit (loss only),
+ *                            w2 -> cos(theta) of an isotropic photon
  *       per track (photon = 0xFFFFFFFF), blocks 0,1,...: Poisson sampler
  *     A 32-bit word w maps to the uniform (w >> 8) * 2^-24 in [0, 1).
  */
@@ -70,7 +71,7 @@ typedef enum rich_status {
 } rich_status;
 
 /* ----------------------------------------------------- geometry description */
-enum { RICH_TABLE_CONST = 0, RICH_TABLE_GAUSS = 1, RICH_TABLE_HIST = 2 };
+enum { RICH_TABLE_CONST = 0, RICH_TABLE_GAUSS = 1, RICH_TABLE_HIST = 2, RICH_TABLE_CDF = 3 };
 enum { RICH_MAT_MIRROR = 0, RICH_MAT_ABSORBER = 1, RICH_MAT_DETECTOR = 2 };
 enum { RICH_MAT_SMOOTH = 1 }; /* material flag: triangles use vertex normals */
 
@@ -88,6 +89,13 @@ enum { RICH_MAT_SMOOTH = 1 }; /* material flag: triangles use vertex normals */
  *   HIST : P = values[clamp(floor((lambda - p0) / p1), 0, nbins - 1)]
  *          (piecewise-constant histogram, e.g. 33 nm bins for QE and 25 nm
  *           bins for reflectivity as in Sec. 4.3)
+ *   CDF  : not a response but a binned emission spectrum for the isotropic
+ *          source (rich_emit_params): values[0..nbins] is its cumulative
+ *          distribution at the bin edges p0 + k*p1 (values[0] = 0,
+ *          values[nbins] = 1, nondecreasing, nbins <= 63). A uniform u picks
+ *          the bin k with values[k] <= u < values[k+1]; the wavelength is
+ *          p0 + p1 * (k + (u - values[k]) / (values[k+1] - values[k])),
+ *          each operation rounded in FP32.
  * P is evaluated in FP32. 280 bytes. */
 typedef struct rich_table {
     int32_t kind;
@@ -183,14 +191,32 @@ typedef struct rich_tracks {
     const uint32_t *n_fixed;
 } rich_tracks;
 
+/* Light sources (Sec. 6 names the Cherenkov light of liquid radiators such
+ * as water, and scintillation light, as the next sources). */
+enum { RICH_SOURCE_CHERENKOV = 0, RICH_SOURCE_ISOTROPIC = 1 };
+
 /* Radiator and spectrum. seed: Philox key. n_minus_1: refractive index
- * minus one (constant, no dispersion). lambda_min/max: emission band (nm). */
+ * minus one (constant, no dispersion). lambda_min/max: emission band (nm).
+ * source: RICH_SOURCE_CHERENKOV (the zero default): photons on the cone
+ *   cos(theta) = 1/(n beta) around the track, Frank-Tamm mean count and
+ *   1/lambda^2 spectrum on [lambda_min, lambda_max].
+ *   RICH_SOURCE_ISOTROPIC: photons uniform on the unit sphere (world frame;
+ *   cos(theta) from draw block 3 word 2, azimuth from block 0 word 1) from
+ *   points uniform along each track, Poisson mean yield_per_mm * length
+ *   (or the track's n_fixed), wavelength from the scene's RICH_TABLE_CDF
+ *   table `spectrum_table` (>= 0; needs the geometry loaded), or from the
+ *   1/lambda^2 law on [lambda_min, lambda_max] when spectrum_table < 0.
+ *   n_minus_1 and the track momenta are not used. */
 typedef struct rich_emit_params {
     uint64_t seed;
     float n_minus_1;
     float lambda_min;
     float lambda_max;
     float reserved;
+    int32_t source;
+    float yield_per_mm;
+    int32_t spectrum_table;
+    int32_t reserved2;
 } rich_emit_params;
 
 /* Materialised photons, structure of arrays of DEVICE pointers (caller

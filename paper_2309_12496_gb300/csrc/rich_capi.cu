@@ -45,6 +45,9 @@ struct rich_ctx {
     uint64_t known_total = 0;
     uint32_t key0 = 0, key1 = 0;
     float inv1 = 0.f, span = 0.f;
+    int32_t source = RICH_SOURCE_CHERENKOV;   // light source of the last emission
+    int32_t spectrum = -1;                    // its CDF table, or -1
+    std::vector<int32_t> table_kind;          // kinds of the scene's tables (host)
     // small device state: counters + photon total
     Counters *d_ctr = nullptr;
     unsigned long long *d_total = nullptr;
@@ -255,10 +258,19 @@ void free_emission(rich_ctx *ctx) {
     ctx->track_cap = 0;
 }
 
+// The last emission as the kernels see it.
+EmitView emit_view(const rich_ctx *ctx) {
+    EmitView em{ctx->d_rec, ctx->d_cs, ctx->d_offsets, ctx->d_total, ctx->n_tracks,
+                ctx->key0, ctx->key1, ctx->inv1, ctx->span, ctx->d_perm, ctx->d_perm_ok,
+                ctx->source, ctx->spectrum};
+    return em;
+}
+
 // Yield, Poisson counts and photon offsets of the tracks into the context's
 // scratch (asynchronous).
 rich_status emit_core(rich_ctx *ctx, const rich_tracks *t, uint64_t seed, float n_minus_1,
-                      float lambda_min, float lambda_max) {
+                      float lambda_min, float lambda_max, int32_t source = RICH_SOURCE_CHERENKOV,
+                      float yield_per_mm = 0.f, int32_t spectrum = -1) {
     const int64_t n = t->n;
     if (n + 1 > ctx->track_cap) {
         RICH_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -291,11 +303,14 @@ rich_status emit_core(rich_ctx *ctx, const rich_tracks *t, uint64_t seed, float 
     } else {
         RICH_CUDA(launch_yield(tv, (double)n_minus_1, lambda_min, lambda_max, ctx->key0,
                                ctx->key1, ctx->d_rec, ctx->d_cs, ctx->d_counts, ctx->d_bsum,
-                               ctx->stream));
+                               ctx->stream,
+                               source == RICH_SOURCE_ISOTROPIC ? (double)yield_per_mm : -1.0));
         RICH_CUDA(launch_offsets(ctx->d_counts, ctx->d_bsum, n, ctx->d_offsets, ctx->d_total,
                                  ctx->stream));
     }
     ctx->n_tracks = n;
+    ctx->source = source;
+    ctx->spectrum = source == RICH_SOURCE_ISOTROPIC ? spectrum : -1;
     ctx->has_emission = true;
     return RICH_OK;
 }
@@ -314,8 +329,7 @@ rich_status order_photons(rich_ctx *ctx) {
         RICH_CUDA(cudaMalloc(&ctx->d_perm, sizeof(uint32_t) * want));
         ctx->perm_cap = want;
     }
-    EmitView em{ctx->d_rec, ctx->d_cs, ctx->d_offsets, ctx->d_total, ctx->n_tracks, ctx->key0,
-                ctx->key1, ctx->inv1, ctx->span, ctx->d_perm, ctx->d_perm_ok};
+    const EmitView em = emit_view(ctx);
     if (ctx->n_tracks == 0) {
         RICH_CUDA(cudaMemsetAsync(ctx->d_perm_ok, 0, sizeof(uint32_t), ctx->stream));
         return RICH_OK;
@@ -431,7 +445,17 @@ RICH_API rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc 
         return bad("NULL array with a non-zero count");
     for (int i = 0; i < g->n_tables; ++i) {
         const rich_table &t = g->tables[i];
-        if (t.kind < 0 || t.kind > 2) return bad("table kind");
+        if (t.kind < 0 || t.kind > 3) return bad("table kind");
+        if (t.kind == RICH_TABLE_CDF) {
+            if (t.nbins < 1 || t.nbins > RICH_TABLE_MAX_BINS - 1 || !(t.p1 > 0.f) ||
+                !std::isfinite(t.p0) || !std::isfinite(t.p1))
+                return bad("spectrum (CDF) table needs 1..63 bins and a positive width");
+            if (t.values[0] != 0.f || t.values[t.nbins] != 1.f)
+                return bad("spectrum (CDF) table must run from 0 to 1");
+            for (int k = 0; k < t.nbins; ++k)
+                if (!(t.values[k + 1] >= t.values[k]))
+                    return bad("spectrum (CDF) table must be nondecreasing");
+        }
         if (t.kind == RICH_TABLE_HIST && (t.nbins < 1 || t.nbins > RICH_TABLE_MAX_BINS || !(t.p1 > 0.f)))
             return bad("histogram table needs 1..64 bins and a positive width");
         if (t.kind == RICH_TABLE_GAUSS && !(t.p2 != 0.f)) return bad("Gaussian table width is 0");
@@ -442,6 +466,8 @@ RICH_API rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc 
         if (m.kind < 0 || m.kind > 2) return bad("material kind");
         if (m.kind != RICH_MAT_ABSORBER && (m.table < 0 || m.table >= g->n_tables))
             return bad("material table index out of range");
+        if (m.kind != RICH_MAT_ABSORBER && g->tables[m.table].kind == RICH_TABLE_CDF)
+            return bad("a spectrum (CDF) table is not a response table");
         if (m.kind == RICH_MAT_DETECTOR && (m.plane < 0 || m.plane >= RICH_MAX_PLANES))
             return bad("detector plane index must be 0..7");
         if (m.flags & RICH_MAT_SMOOTH) any_smooth = true;
@@ -614,6 +640,8 @@ RICH_API rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc 
         RICH_CUDA(cudaMalloc(&ctx->d_grad_tiles,
                              sizeof(DevSphereGroup) * RICH_MAX_GROUPS + sizeof(DevTile) * RICH_MAX_TILES));
     }
+    ctx->table_kind.assign(g->n_tables, 0);
+    for (int i = 0; i < g->n_tables; ++i) ctx->table_kind[i] = g->tables[i].kind;
     ctx->has_geometry = true;
     return RICH_OK;
 }
@@ -632,11 +660,23 @@ RICH_API rich_status rich_emit(rich_ctx *ctx, const rich_tracks *t,
     if (!(prm->n_minus_1 >= 0.f) || !std::isfinite(prm->n_minus_1) || !(prm->lambda_min > 0.f) ||
         !(prm->lambda_max > prm->lambda_min) || !std::isfinite(prm->lambda_max))
         return fail(ctx, RICH_ERR_ARG, "rich_emit: need n-1 >= 0 and 0 < lambda_min < lambda_max");
+    if (prm->source != RICH_SOURCE_CHERENKOV && prm->source != RICH_SOURCE_ISOTROPIC)
+        return fail(ctx, RICH_ERR_ARG, "rich_emit: unknown light source");
+    if (prm->source == RICH_SOURCE_ISOTROPIC) {
+        if (!(prm->yield_per_mm >= 0.f) || !std::isfinite(prm->yield_per_mm))
+            return fail(ctx, RICH_ERR_ARG, "rich_emit: isotropic source needs a finite yield_per_mm >= 0");
+        if (prm->spectrum_table >= 0 &&
+            (!ctx->has_geometry || prm->spectrum_table >= (int32_t)ctx->table_kind.size() ||
+             ctx->table_kind[prm->spectrum_table] != RICH_TABLE_CDF))
+            return fail(ctx, RICH_ERR_ARG,
+                        "rich_emit: spectrum_table is not a CDF table of the loaded scene");
+    }
     DeviceGuard guard(ctx->device);
     const int64_t n = t->n;
     {
         const rich_status st = emit_core(ctx, t, prm->seed, prm->n_minus_1, prm->lambda_min,
-                                         prm->lambda_max);
+                                         prm->lambda_max, prm->source, prm->yield_per_mm,
+                                         prm->spectrum_table < 0 ? -1 : prm->spectrum_table);
         if (st != RICH_OK) return st;
     }
     if (n_photons || out) {
@@ -659,8 +699,7 @@ RICH_API rich_status rich_emit(rich_ctx *ctx, const rich_tracks *t,
         if (total && (!out->x || !out->y || !out->z || !out->dx || !out->dy || !out->dz ||
                       !out->lambda || !out->event || !out->track || !out->photon))
             return fail(ctx, RICH_ERR_ARG, "rich_emit: a photon output array is NULL");
-        EmitView em{ctx->d_rec, ctx->d_cs, ctx->d_offsets, ctx->d_total, n,
-                    ctx->key0, ctx->key1, ctx->inv1, ctx->span, ctx->d_perm, ctx->d_perm_ok};
+        const EmitView em = emit_view(ctx);
         RICH_CUDA(launch_materialize(ctx->sc, em, total, *out, ctx->stream));
         out->n = total;
     }
@@ -697,6 +736,14 @@ RICH_API rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
     for (int k = 0; k < o->n_prefilter; ++k)
         if (o->prefilter_tables[k] < 0 || o->prefilter_tables[k] >= ctx->sc.n_tables)
             return fail(ctx, RICH_ERR_ARG, "rich_trace: prefilter table index outside the scene's tables");
+    for (int k = 0; k < o->n_prefilter; ++k)
+        if (ctx->table_kind[o->prefilter_tables[k]] == RICH_TABLE_CDF)
+            return fail(ctx, RICH_ERR_ARG, "rich_trace: a spectrum (CDF) table is not a response table");
+    if (!in && ctx->spectrum >= 0 &&
+        (ctx->spectrum >= (int32_t)ctx->table_kind.size() ||
+         ctx->table_kind[ctx->spectrum] != RICH_TABLE_CDF))
+        return fail(ctx, RICH_ERR_STATE,
+                    "rich_trace: the emission's spectrum table is not in the current scene");
     const int cls = trace_shape_class(threads, o->wide_regs != 0);
     int smem_nodes = o->bvh_smem_nodes;
     if (smem_nodes < 0) smem_nodes = threads > 256 ? 1536 : 0;
@@ -750,8 +797,7 @@ RICH_API rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
         if (!bps || bps > it->second) bps = it->second;
     }
     shape.blocks = std::max(1, bps) * ctx->n_sm;
-    EmitView em{ctx->d_rec, ctx->d_cs, ctx->d_offsets, ctx->d_total, ctx->n_tracks,
-                ctx->key0, ctx->key1, ctx->inv1, ctx->span, ctx->d_perm, ctx->d_perm_ok};
+    EmitView em = emit_view(ctx);
     if (in) {
         em.key0 = (uint32_t)o->seed;
         em.key1 = (uint32_t)(o->seed >> 32);
@@ -822,6 +868,8 @@ RICH_API rich_status rich_trace_grad(rich_ctx *ctx, const rich_tracks *t,
     if (o->n_prefilter != 0)
         return fail(ctx, RICH_ERR_ARG,
                     "rich_trace_grad: the gradient takes in-flight efficiencies (n_prefilter = 0)");
+    if (prm->source != RICH_SOURCE_CHERENKOV)
+        return fail(ctx, RICH_ERR_ARG, "rich_trace_grad: the gradient is defined for the Cherenkov source");
     for (int k = 0; k < 8; ++k)
         if (!std::isfinite(th->tilt[k]) || std::fabs(th->tilt[k]) > 0.5f)
             return fail(ctx, RICH_ERR_ARG, "rich_trace_grad: tilts must be finite, |tilt| <= 0.5 rad");
@@ -912,8 +960,7 @@ RICH_API rich_status rich_trace_grad(rich_ctx *ctx, const rich_tracks *t,
     shape.blocks = bps * ctx->n_sm;
     RICH_CUDA(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), ctx->stream));
     RICH_CUDA(cudaMemsetAsync(ctx->d_acc, 0, sizeof(double) * 12, ctx->stream));
-    EmitView em{ctx->d_rec, ctx->d_cs, ctx->d_offsets, ctx->d_total, ctx->n_tracks,
-                ctx->key0, ctx->key1, ctx->inv1, ctx->span, ctx->d_perm, ctx->d_perm_ok};
+    const EmitView em = emit_view(ctx);
     RICH_CUDA(launch_trace(sv, &em, nullptr, p, ctx->d_ctr, shape, ctx->stream));
     GradView gv{};
     gv.nom = ctx->d_tile_nom;

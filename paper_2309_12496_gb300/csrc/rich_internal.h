@@ -124,6 +124,8 @@ struct EmitView {            // result of rich_emit used by the trace
     float inv1, span;         // FP32 1/lambda_min and 1/lambda_min - 1/lambda_max
     const uint32_t *perm;     // per track, photon indices in azimuth order, or null
     const uint32_t *perm_ok;  // device flag: perm covers this emission
+    int32_t source;           // RICH_SOURCE_*
+    int32_t spectrum;         // isotropic: CDF table index of the scene, or -1
 };
 
 struct ExtView {             // caller photons
@@ -193,11 +195,13 @@ struct LaunchShape {
 };
 
 // ---------------------------------------------------------------- launchers
+// iso_yield_per_mm >= 0: isotropic source with that mean per mm (the
+// Cherenkov angle is not computed); < 0: Cherenkov source.
 cudaError_t launch_yield(const TracksView &t, double n_minus_1,
                          double lam_min, double lam_max, uint32_t key0,
                          uint32_t key1, TrackRec *rec, double2 *cs,
                          uint32_t *counts, unsigned long long *block_sums,
-                         cudaStream_t s);
+                         cudaStream_t s, double iso_yield_per_mm = -1.0);
 cudaError_t launch_offsets(const uint32_t *counts,
                            const unsigned long long *block_sums,
                            int64_t n_tracks, uint64_t *offsets,

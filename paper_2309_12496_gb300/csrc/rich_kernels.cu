@@ -144,7 +144,7 @@ template <bool RECS>
 __global__ void __launch_bounds__(kYieldBlock)
 k_yield(TracksView t, double n_minus_1, double inv_band_mm, uint32_t key0,
         uint32_t key1, TrackRec *rec, double2 *cs, uint32_t *counts,
-        unsigned long long *block_sums) {
+        unsigned long long *block_sums, double iso_yield) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t count = 0;
     if (i < t.n) {
@@ -155,7 +155,10 @@ k_yield(TracksView t, double n_minus_1, double inv_band_mm, uint32_t key0,
         double beta = 1.0 - one_minus_beta;
         double nb_minus_1 = n_minus_1 * beta - one_minus_beta;
         double cos_t = 1.0, sin_t = 0.0, tan_t = 0.0, mu = 0.0;
-        if (nb_minus_1 > 0.0) {
+        if (iso_yield >= 0.0) {
+            // isotropic source: mean photons = yield per mm x length
+            mu = len * iso_yield;
+        } else if (nb_minus_1 > 0.0) {
             double nb = 1.0 + nb_minus_1;
             double tan2 = nb_minus_1 * (nb + 1.0);      // (n beta)^2 - 1
             tan_t = sqrt(tan2);
@@ -333,24 +336,51 @@ struct Photon {
     int skip, n_refl, steps;
 };
 
+// Wavelength from a binned emission spectrum (CDF table): the bin k with
+// c_k <= u < c_{k+1}, linear inside it, each operation rounded in FP32.
+__device__ __forceinline__ float spectrum_lambda(const DevTable &T, float u) {
+    int k = 0;
+    while (k + 1 < T.nbins && T.values[k + 1] <= u) ++k;
+    const float fr = __fdiv_rn(__fsub_rn(u, T.values[k]), __fsub_rn(T.values[k + 1], T.values[k]));
+    return __fadd_rn(T.p0, __fmul_rn(__fadd_rn((float)k, fr), T.p1));
+}
+
+// Wavelength of a photon from its draw: the source's binned spectrum, or the
+// Frank-Tamm 1/lambda^2 law on the emission band.
+__device__ __forceinline__ float photon_lambda(uint32_t w, const EmitView &em,
+                                               const DevTable *spec) {
+    return spec ? spectrum_lambda(*spec, u24f(w)) : emit_lambda(u24f(w), em.inv1, em.span);
+}
+
 // Fused emission of photon j of track tr (Sec. 3 angle, Sec. 4.2 photons as
 // independent rays): origin uniform on the segment, azimuth uniform,
 // wavelength from the Frank-Tamm spectrum. The direction is built as
 // t + tan(theta) (cos phi e1 + sin phi e2), normalised, so the small
 // Cherenkov angle is carried by tan(theta) and not by a cosine near 1.
+// Isotropic source (the scintillation light named in Sec. 6): the
+// direction is uniform on the sphere, cos(theta) = 1 - 2u from draw block 3,
+// and the wavelength comes from the source's spectrum table `spec`.
 __device__ __forceinline__ void emit_photon(const TrackRec &tr, uint32_t j,
-                                            const EmitView &em, const u4 &w0, Photon &ph) {
+                                            const EmitView &em, const u4 &w0,
+                                            const DevTable *spec, Photon &ph) {
     u4 w1 = philox10(1u, j, tr.id, tr.event, em.key0, em.key1);
     f3 t = mk3(tr.tx, tr.ty, tr.tz);
     float s = u24f(w0.x) * tr.len;
     ph.o = fma3(t, s, mk3(tr.x, tr.y, tr.z));
     float sp, cp;
     sincospif(2.0f * u24f(w0.y), &sp, &cp);
-    f3 e1, e2;
-    basis_f(t, e1, e2);
-    f3 r = fma3(e1, cp, e2 * sp);
-    ph.d = normalize3(fma3(r, tr.tan_theta, t));
-    ph.lam = emit_lambda(u24f(w0.z), em.inv1, em.span);
+    if (em.source == RICH_SOURCE_ISOTROPIC) {
+        const u4 w3 = philox10(3u, j, tr.id, tr.event, em.key0, em.key1);
+        const float ct = 1.0f - 2.0f * u24f(w3.z);      // exact
+        const float st = sqrtf(fmaxf(0.0f, (1.0f - ct) * (1.0f + ct)));
+        ph.d = normalize3(mk3(st * cp, st * sp, ct));
+    } else {
+        f3 e1, e2;
+        basis_f(t, e1, e2);
+        f3 r = fma3(e1, cp, e2 * sp);
+        ph.d = normalize3(fma3(r, tr.tan_theta, t));
+    }
+    ph.lam = photon_lambda(w0.z, em, spec);
     ph.w_qe = w0.w;
     ph.wr0 = w1.x;
     ph.wr1 = w1.y;
@@ -361,12 +391,8 @@ __device__ __forceinline__ void emit_photon(const TrackRec &tr, uint32_t j,
     ph.j = j;
 }
 
-__device__ __forceinline__ void emit_photon(const TrackRec &tr, uint32_t j,
-                                            const EmitView &em, Photon &ph) {
-    emit_photon(tr, j, em, philox10(0u, j, tr.id, tr.event, em.key0, em.key1), ph);
-}
-
-__global__ void k_materialize(EmitView em, uint64_t n, rich_photons out) {
+__global__ void k_materialize(SceneView sc, EmitView em, uint64_t n, rich_photons out) {
+    const DevTable *spec = em.spectrum >= 0 ? sc.tables + em.spectrum : nullptr;
     for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
          g += (uint64_t)gridDim.x * blockDim.x) {
         int64_t lo = 0, hi = em.n_tracks - 1;
@@ -376,7 +402,8 @@ __global__ void k_materialize(EmitView em, uint64_t n, rich_photons out) {
         }
         TrackRec tr = em.tracks[lo];
         Photon ph;
-        emit_photon(tr, (uint32_t)(g - em.offsets[lo]), em, ph);
+        const uint32_t j = (uint32_t)(g - em.offsets[lo]);
+        emit_photon(tr, j, em, philox10(0u, j, tr.id, tr.event, em.key0, em.key1), spec, ph);
         out.x[g] = ph.o.x;
         out.y[g] = ph.o.y;
         out.z[g] = ph.o.z;
@@ -783,7 +810,8 @@ __device__ __forceinline__ void basis_ff(const ff3 &t, ff3 &e1, ff3 &e2) {
 // Emission of photon j of a track with the same draws as emit_photon:
 // the track direction normalised, the origin at s = u L along it, the
 // azimuth 2 pi u from an FP64 sincospi, cos and sin of the Cherenkov angle
-// from the FP64 yield pass.
+// from the FP64 yield pass. Isotropic source: cos(theta) = 1 - 2u (exact)
+// and sin(theta) = 2 sqrt(u (1 - u)) from the exact product u (1 - u).
 __device__ void emit_ff(const TrackRec &tr, double2 cs, uint32_t j, const EmitView &em,
                         ff3 &o, ff3 &d) {
     const u4 w0 = philox10(0u, j, tr.id, tr.event, em.key0, em.key1);
@@ -792,6 +820,14 @@ __device__ void emit_ff(const TrackRec &tr, double2 cs, uint32_t j, const EmitVi
     o = ff3_axpy(s, t, ff3v(tr.x, tr.y, tr.z));
     double sp, cp;
     sincospi(2.0 * u24d(w0.y), &sp, &cp);
+    if (em.source == RICH_SOURCE_ISOTROPIC) {
+        const u4 w3 = philox10(3u, j, tr.id, tr.event, em.key0, em.key1);
+        const float u = u24f(w3.z);
+        const ff st = ff_mul(ff_sqrt(two_prod(u, 1.0f - u)), 2.0f);
+        d = {ff_mul(st, ff_from_double(cp)), ff_mul(st, ff_from_double(sp)),
+             ffv(1.0f - 2.0f * u)};
+        return;
+    }
     ff3 e1, e2;
     basis_ff(t, e1, e2);
     const ff r_x = ff_add(ff_mul(e1.x, ff_from_double(cp)), ff_mul(e2.x, ff_from_double(sp)));
@@ -981,6 +1017,7 @@ k_trace(TraceArgs A) {
     const uint64_t chunk = (uint64_t)P.chunk;
     const bool has_tri = sc.n_tris > 0;
     const bool ordered = !EXT && em.perm && *em.perm_ok;
+    const DevTable *spec = (!EXT && em.spectrum >= 0) ? S.tables + em.spectrum : nullptr;
     if (blockIdx.x == 0 && threadIdx.x == 0) A.ctr->ordered = ordered ? 1u : 0u;
 
     Photon ph;
@@ -1064,11 +1101,10 @@ k_trace(TraceArgs A) {
                         // efficiencies before propagation (Sec. 4.3): only
                         // the wavelength is needed to decide
                         if (P.n_prefilter &&
-                            !(u24f(w0.w) <
-                              prefilter_prob(S, P, emit_lambda(u24f(w0.z), em.inv1, em.span))))
+                            !(u24f(w0.w) < prefilter_prob(S, P, photon_lambda(w0.z, em, spec))))
                             rejected = true;
                         else
-                            emit_photon(tr, j, em, w0, ph);
+                            emit_photon(tr, j, em, w0, spec, ph);
                     }
                     if (rejected) {
                         if (P.fate) P.fate[ph.g] = (uint8_t)RICH_FATE_PREFILTERED;
@@ -1649,7 +1685,7 @@ cudaError_t launch_yield(const TracksView &t, double n_minus_1,
                          double lam_min, double lam_max, uint32_t key0,
                          uint32_t key1, TrackRec *rec, double2 *cs,
                          uint32_t *counts, unsigned long long *block_sums,
-                         cudaStream_t s) {
+                         cudaStream_t s, double iso_yield_per_mm) {
     if (t.n <= 0) return cudaSuccess;
     const double inv_band_mm = 1.0e6 / lam_min - 1.0e6 / lam_max;
     const int64_t groups = (t.n + kYieldThreads - 1) / kYieldThreads;
@@ -1658,10 +1694,12 @@ cudaError_t launch_yield(const TracksView &t, double n_minus_1,
     const unsigned blocks = (unsigned)((t.n + kYieldBlock - 1) / kYieldBlock);
     if (rec)
         k_yield<true><<<blocks, kYieldBlock, 0, s>>>(t, n_minus_1, inv_band_mm, key0, key1,
-                                                     rec, cs, counts, block_sums);
+                                                     rec, cs, counts, block_sums,
+                                                     iso_yield_per_mm);
     else
         k_yield<false><<<blocks, kYieldBlock, 0, s>>>(t, n_minus_1, inv_band_mm, key0, key1,
-                                                      rec, cs, counts, block_sums);
+                                                      rec, cs, counts, block_sums,
+                                                      iso_yield_per_mm);
     return cudaGetLastError();
 }
 
@@ -1675,13 +1713,13 @@ cudaError_t launch_offsets(const uint32_t *counts,
     return cudaGetLastError();
 }
 
-cudaError_t launch_materialize(const SceneView &, const EmitView &em,
+cudaError_t launch_materialize(const SceneView &sc, const EmitView &em,
                                uint64_t n, const rich_photons &out,
                                cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     uint64_t blocks = (n + 255) / 256;
     if (blocks > 65535ull * 16) blocks = 65535ull * 16;
-    k_materialize<<<(unsigned)blocks, 256, 0, s>>>(em, n, out);
+    k_materialize<<<(unsigned)blocks, 256, 0, s>>>(sc, em, n, out);
     return cudaGetLastError();
 }
 

@@ -55,6 +55,11 @@ extern "C" RICH_API rich_status rich_photon_counts_static(const rich_tracks *t,
         set_global_error("rich_photon_counts_static: a required array is NULL");
         return RICH_ERR_ARG;
     }
+    if (prm->source != RICH_SOURCE_CHERENKOV &&
+        (prm->source != RICH_SOURCE_ISOTROPIC || !(prm->yield_per_mm >= 0.f))) {
+        set_global_error("rich_photon_counts_static: unknown source or negative yield");
+        return RICH_ERR_ARG;
+    }
     if (!(prm->n_minus_1 >= 0.f) || !(prm->lambda_min > 0.f) ||
         !(prm->lambda_max > prm->lambda_min)) {
         set_global_error("rich_photon_counts_static: need n-1 >= 0 and 0 < lambda_min < lambda_max");
@@ -93,7 +98,8 @@ extern "C" RICH_API rich_status rich_photon_counts_static(const rich_tracks *t,
         const uint32_t key0 = (uint32_t)prm->seed, key1 = (uint32_t)(prm->seed >> 32);
         // launch_yield clears the group sums this call uses before adding
         e = launch_yield(tv, (double)prm->n_minus_1, prm->lambda_min, prm->lambda_max, key0, key1,
-                         nullptr, nullptr, counts, sums, s);
+                         nullptr, nullptr, counts, sums, s,
+                         prm->source == RICH_SOURCE_ISOTROPIC ? (double)prm->yield_per_mm : -1.0);
         if (e == cudaSuccess) e = launch_offsets(counts, sums, t->n, offsets, nullptr, s);
     }
     if (e != cudaSuccess) {

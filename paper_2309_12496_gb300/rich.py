@@ -65,10 +65,15 @@ class TracksDesc(C.Structure):
                                   "length", "event", "id", "n_fixed")]
 
 
+SOURCE_CHERENKOV, SOURCE_ISOTROPIC = 0, 1
+
+
 class EmitParams(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("n_minus_1", C.c_float),
                 ("lambda_min", C.c_float), ("lambda_max", C.c_float),
-                ("reserved", C.c_float)]
+                ("reserved", C.c_float), ("source", C.c_int32),
+                ("yield_per_mm", C.c_float), ("spectrum_table", C.c_int32),
+                ("reserved2", C.c_int32)]
 
 
 class PhotonsDesc(C.Structure):
@@ -336,9 +341,15 @@ class Context:
         self.scene = scene
 
     def emit(self, tracks: DeviceTracks, n_minus_1, lambda_min=200.0, lambda_max=600.0,
-             seed=0, photons: PhotonBuffers | None = None, sync=True):
+             seed=0, photons: PhotonBuffers | None = None, sync=True,
+             source=SOURCE_CHERENKOV, yield_per_mm=0.0, spectrum_table=-1):
+        """source: SOURCE_CHERENKOV, or SOURCE_ISOTROPIC with yield_per_mm
+        photons per mm and the scene's CDF table spectrum_table (-1: the
+        1/lambda^2 law on the band)."""
         prm = EmitParams(seed=int(seed), n_minus_1=float(n_minus_1),
-                         lambda_min=float(lambda_min), lambda_max=float(lambda_max))
+                         lambda_min=float(lambda_min), lambda_max=float(lambda_max),
+                         source=int(source), yield_per_mm=float(yield_per_mm),
+                         spectrum_table=int(spectrum_table))
         n = C.c_uint64(0)
         pd = photons.desc() if photons is not None else None
         st = load().rich_emit(self.handle, C.byref(tracks.desc()), C.byref(prm),
@@ -464,7 +475,7 @@ def rich_hits(ctx: Context, **kw):
 
 def rich_photon_counts_static(tracks: DeviceTracks, n_minus_1, counts, offsets,
                               lambda_min=200.0, lambda_max=600.0, seed=0, stream=None,
-                              n=None):
+                              n=None, source=SOURCE_CHERENKOV, yield_per_mm=0.0):
     """Per-track photon counts (int32 view of u32) and offsets (int64 view of
     u64, n + 1 entries) into caller device tensors, with no device
     allocation by the library. `n` overrides the track count passed."""
@@ -473,7 +484,8 @@ def rich_photon_counts_static(tracks: DeviceTracks, n_minus_1, counts, offsets,
     if n is not None:
         d.n = int(n)
     prm = EmitParams(seed=int(seed), n_minus_1=float(n_minus_1),
-                     lambda_min=float(lambda_min), lambda_max=float(lambda_max))
+                     lambda_min=float(lambda_min), lambda_max=float(lambda_max),
+                     source=int(source), yield_per_mm=float(yield_per_mm), spectrum_table=-1)
     s = current_stream_handle() if stream is None else stream
     st = L.rich_photon_counts_static(C.byref(d), C.byref(prm), C.c_void_p(counts.data_ptr()),
                                      C.c_void_p(offsets.data_ptr()), C.c_void_p(s))
