@@ -79,7 +79,9 @@ class Params(C.Structure):
                 ("prob_eps", C.c_double), ("use_bvh", C.c_int32),
                 ("n_threads", C.c_int32), ("n_prefilter", C.c_int32),
                 ("prefilter_tables", C.c_int32 * 4), ("source", C.c_int32),
-                ("yield_per_mm", C.c_float), ("spectrum", C.c_void_p)]
+                ("yield_per_mm", C.c_float), ("spectrum", C.c_void_p),
+                ("dispersion", C.c_int32), ("disp_a", C.c_float),
+                ("disp_lambda0", C.c_float)]
 
 
 class PhotonOut(C.Structure):
@@ -95,6 +97,8 @@ def _declare(L):
     L.oracle_philox_batch.argtypes = [i64, vp, vp, vp]
     L.oracle_yield_per_mm.argtypes = [C.c_double] * 4
     L.oracle_yield_per_mm.restype = C.c_double
+    L.oracle_disp_yield_per_mm.argtypes = [vp, C.c_double, C.c_double]
+    L.oracle_disp_yield_per_mm.restype = C.c_double
     L.oracle_poisson.argtypes = [C.c_double, C.c_uint64, u32, u32]
     L.oracle_poisson.restype = i64
     L.oracle_yield.argtypes = [vp, vp, vp, vp, vp]
@@ -141,6 +145,12 @@ def yield_per_mm(n_minus_1, beta, lam_min=200.0, lam_max=600.0):
     return lib().oracle_yield_per_mm(n_minus_1, beta, lam_min, lam_max)
 
 
+def disp_yield_per_mm(prm, p, m):
+    """Frank-Tamm photons per mm of the dispersive radiator of prm for a
+    particle of momentum p and mass m."""
+    return lib().oracle_disp_yield_per_mm(C.byref(prm), p, m)
+
+
 def poisson(mu, seed=0, event=0, track=0):
     return int(lib().oracle_poisson(mu, seed, event, track))
 
@@ -185,7 +195,10 @@ def params(workload=None, seed=None, n_minus_1=None, lambda_min=None,
                   prefilter_tables=(C.c_int32 * 4)(*(list(prefilter) + [0] * (4 - len(prefilter)))),
                   source=source,
                   yield_per_mm=float(getattr(w, "yield_per_mm", 0.0)) if w is not None else 0.0,
-                  spectrum=None if spec is None else spec.ctypes.data)
+                  spectrum=None if spec is None else spec.ctypes.data,
+                  dispersion=int(getattr(w, "dispersion", None) is not None) if w is not None else 0,
+                  disp_a=float(w.dispersion[0]) if w is not None and getattr(w, "dispersion", None) else 0.0,
+                  disp_lambda0=float(w.dispersion[1]) if w is not None and getattr(w, "dispersion", None) else 0.0)
     prm._keep = spec
     return prm
 

@@ -124,6 +124,13 @@ typedef struct {
     int32_t source;
     float yield_per_mm;
     const void *spectrum;
+    /* Dispersive radiator (Cherenkov source): when dispersion = 1 the
+     * refractive index follows the single-resonance form
+     * n(lambda) - 1 = disp_a / (1/disp_lambda0^2 - 1/lambda^2) (lambda and
+     * lambda0 in nm, a in nm^-2) and n_minus_1 is not used. */
+    int32_t dispersion;
+    float disp_a;
+    float disp_lambda0;
 } o_params;
 
 /* Per-photon results, arrays indexed by global photon index. Any pointer
@@ -251,6 +258,66 @@ double oracle_yield_per_mm(double n_minus_1, double beta, double lam_min_nm,
     return 2.0 * PI_D * ALPHA_FS * s2 * inv;
 }
 
+/* ---- dispersive radiator ------------------------------------------------
+ * 1 - beta written without cancellation: m^2 / (E (E + p)). */
+static double one_minus_beta(double p, double m)
+{
+    if (m == 0.0) return 0.0;
+    double E = sqrt(p * p + m * m);
+    return m * m / (E * (E + p));
+}
+
+/* n(lambda) - 1 of the single-resonance form, FP64, lambda in nm. */
+static double disp_n1(const o_params *prm, double lam)
+{
+    double il0 = 1.0 / (double)prm->disp_lambda0, il = 1.0 / lam;
+    return (double)prm->disp_a / ((il0 - il) * (il0 + il));
+}
+
+/* Largest inverse wavelength x_t (nm^-1) below which n(x) beta <= 1, i.e.
+ * no Cherenkov light: n increases with x = 1/lambda, and n beta = 1 at
+ * x_t^2 = 1/lambda0^2 - a beta / (1 - beta). 0 when every x emits. */
+static double disp_x_threshold(const o_params *prm, double beta, double omb)
+{
+    if (omb <= 0.0) return 0.0;
+    double il0 = 1.0 / (double)prm->disp_lambda0;
+    double u = il0 * il0 - (double)prm->disp_a * beta / omb;
+    return u > 0.0 ? sqrt(u) : 0.0;
+}
+
+/* Frank-Tamm photons per mm of a dispersive radiator:
+ * 2 pi alpha * integral over x = 1/lambda of sin^2 theta(x) =
+ * 1 - 1/(n(x) beta)^2, over the part of [1/lambda_max, 1/lambda_min] where
+ * n beta > 1. With c = 1/lambda0^2 and q = c + a, 1/n^2 =
+ * (1 - a/(q - x^2))^2, so the integrand is (1 - 1/beta^2)
+ * + (2a/beta^2)/(q - x^2) - (a^2/beta^2)/(q - x^2)^2, whose antiderivatives
+ * are x, atanh(x/sqrt q)/sqrt q and x/(2q(q - x^2)) + atanh(x/sqrt q)/(2 q^1.5). */
+static double disp_yield_per_mm(const o_params *prm, double beta, double omb)
+{
+    double xa = 1.0 / (double)prm->lambda_max, xb = 1.0 / (double)prm->lambda_min;
+    double xt = disp_x_threshold(prm, beta, omb);
+    if (xt > xa) xa = xt;
+    if (!(xb > xa)) return 0.0;
+    double il0 = 1.0 / (double)prm->disp_lambda0;
+    double a = (double)prm->disp_a, q = il0 * il0 + a, sq = sqrt(q);
+    double b2 = beta * beta;
+    /* 1 - 1/beta^2 = -(1 - beta)(1 + beta)/beta^2, without cancellation */
+    double c0 = -omb * (2.0 - omb) / b2;
+#define F1(x) (atanh((x) / sq) / sq)
+#define F2(x) ((x) / (2.0 * q * (q - (x) * (x))) + atanh((x) / sq) / (2.0 * q * sq))
+    double I = c0 * (xb - xa) + (2.0 * a / b2) * (F1(xb) - F1(xa)) -
+               (a * a / b2) * (F2(xb) - F2(xa));
+#undef F1
+#undef F2
+    return 2.0 * PI_D * ALPHA_FS * I * 1.0e6;       /* x in nm^-1 -> per mm */
+}
+
+double oracle_disp_yield_per_mm(const o_params *prm, double p, double m)
+{
+    double omb = one_minus_beta(p, m);
+    return disp_yield_per_mm(prm, 1.0 - omb, omb);
+}
+
 typedef struct {
     uint64_t seed;
     uint32_t event, track, block;
@@ -315,7 +382,10 @@ int64_t oracle_yield(const o_tracks_in *t, const o_params *prm,
     uint64_t total = 0;
     for (int64_t i = 0; i < t->n; ++i) {
         double beta = track_beta(t->p[i], t->mass[i]);
-        double mu = prm->source == SRC_ISOTROPIC
+        double omb = one_minus_beta(t->p[i], t->mass[i]);
+        double mu = prm->dispersion && prm->source == SRC_CHERENKOV
+                        ? (double)t->length[i] * disp_yield_per_mm(prm, 1.0 - omb, omb)
+                    : prm->source == SRC_ISOTROPIC
                         ? (double)t->length[i] * (double)prm->yield_per_mm
                         : (double)t->length[i] *
                               oracle_yield_per_mm(prm->n_minus_1, beta,
@@ -402,7 +472,86 @@ typedef struct {
     double u_qe;
     double u_refl[8];
     double u_smear[2];
+    int graze;           /* 2: an emission accept/reject within prob_eps */
 } o_photon;
+
+/* sin^2 of the Cherenkov angle of the dispersive radiator at lambda, the
+ * quantity the wavelength accept/reject compares, in FP32 one IEEE operation
+ * at a time from the FP32 inputs: n - 1 = a/((1/l0 - 1/l)(1/l0 + 1/l)),
+ * n beta - 1 = (n - 1) - (1 - beta) - (n - 1)(1 - beta), and
+ * sin^2 = (n beta - 1)(n beta + 1)/(n beta)^2. */
+static float disp_s2_f32(const o_params *prm, float omb, float lam)
+{
+    volatile float il = 1.0f / lam;
+    volatile float il0 = 1.0f / prm->disp_lambda0;
+    volatile float d1 = il0 - il;
+    volatile float d2 = il0 + il;
+    volatile float den = d1 * d2;
+    volatile float n1 = prm->disp_a / den;
+    volatile float t1 = n1 * omb;
+    volatile float t2 = n1 - omb;
+    volatile float nb1 = t2 - t1;
+    if (!(nb1 > 0.0f)) return 0.0f;
+    volatile float tw = 2.0f + nb1;
+    volatile float num = nb1 * tw;
+    volatile float op = 1.0f + nb1;
+    volatile float dd = op * op;
+    return num / dd;
+}
+
+/* Wavelength of a photon of a dispersive radiator: dN/dlambda is
+ * proportional to sin^2 theta(lambda) / lambda^2 (Frank-Tamm), so a
+ * candidate from the 1/lambda^2 law on the band where light is emitted,
+ * [lambda_min, min(lambda_max, 1/x_t)], is accepted with probability
+ * sin^2 theta(lambda) / sin^2 theta(lambda_min) (n, and so sin^2 theta,
+ * decrease with lambda). Trial 0 takes block 0 word 2 (candidate) and block
+ * 3 word 3 (test); trial t >= 1 takes block 8 + (t-1)/2, words
+ * 2((t-1) mod 2) and 2((t-1) mod 2) + 1; after 64 trials the last candidate
+ * stands. FP32 decisions as in disp_s2_f32. */
+static float disp_lambda(const o_params *prm, uint64_t seed, uint32_t event,
+                         uint32_t tid, uint32_t j, const uint32_t w0[4],
+                         const uint32_t w3[4], double omb, double xt,
+                         int *graze)
+{
+    float ombf = (float)omb;
+    volatile float inv1 = 1.0f / prm->lambda_min;
+    volatile float inv2 = 1.0f / prm->lambda_max;
+    float xlo = inv2;
+    if ((float)xt > xlo) xlo = (float)xt;
+    /* the threshold's FP32 rounding decides the band: flag a near tie */
+    if (xt > 0.0) {
+        float r = (float)xt;
+        float nb = xt < (double)r ? nextafterf(r, 0.0f) : nextafterf(r, 2.0f * r);
+        double mid = 0.5 * ((double)r + (double)nb);
+        if (fabs(xt - mid) < 1e-6 * fabs((double)nb - (double)r)) *graze |= 2;
+    }
+    volatile float span = inv1 - xlo;
+    float s2max = disp_s2_f32(prm, ombf, prm->lambda_min);
+    float lam = 0.0f;
+    uint32_t w[4];
+    for (int t = 0; t < 64; ++t) {
+        uint32_t wl, wa;
+        if (t == 0) {
+            wl = w0[2];
+            wa = w3[3];
+        } else {
+            draw_block(seed, event, tid, j, 8u + (uint32_t)(t - 1) / 2u, w);
+            wl = w[2 * ((t - 1) & 1)];
+            wa = w[2 * ((t - 1) & 1) + 1];
+        }
+        volatile float u = (float)u24(wl);
+        volatile float prod = u * span;
+        volatile float inv = inv1 - prod;
+        lam = 1.0f / inv;
+        if (!(s2max > 0.0f)) break;
+        volatile float s2 = disp_s2_f32(prm, ombf, lam);
+        volatile float pa = s2 / s2max;
+        double ua = u24(wa);
+        if (fabs(ua - (double)pa) < prm->prob_eps) *graze |= 2;
+        if (ua < (double)pa) break;
+    }
+    return lam;
+}
 
 /* Photon j of track i. */
 static void emit_photon(const o_tracks_in *t, const o_params *prm, int64_t i,
@@ -411,6 +560,7 @@ static void emit_photon(const o_tracks_in *t, const o_params *prm, int64_t i,
     uint32_t event = t->event[i];
     uint32_t tid = t->id ? t->id[i] : (uint32_t)i;
     uint32_t w0[4], w1[4], w2[4], w3[4];
+    ph->graze = 0;
     draw_block(prm->seed, event, tid, j, 0, w0);
     draw_block(prm->seed, event, tid, j, 1, w1);
     draw_block(prm->seed, event, tid, j, 2, w2);
@@ -442,6 +592,14 @@ static void emit_photon(const o_tracks_in *t, const o_params *prm, int64_t i,
     }
     double beta = track_beta(t->p[i], t->mass[i]);
     double nb = (1.0 + prm->n_minus_1) * beta;
+    if (prm->dispersion) {
+        /* Cherenkov angle at the photon's own wavelength */
+        double omb = one_minus_beta(t->p[i], t->mass[i]);
+        beta = 1.0 - omb;
+        ph->lambda = disp_lambda(prm, prm->seed, event, tid, j, w0, w3, omb,
+                                 disp_x_threshold(prm, beta, omb), &ph->graze);
+        nb = (1.0 + disp_n1(prm, (double)ph->lambda)) * beta;
+    }
     double ct = 1.0 / nb;
     double st = sqrt(fmax(0.0, 1.0 - ct * ct));
     v3 e1, e2;
@@ -1141,6 +1299,7 @@ int oracle_trace(void *scene, const o_tracks_in *t, const o_params *prm,
             trace_photon(sc, prm, &ph, &r, path, prm->n_prefilter > 0);
             if (run == 2) r.graze |= 2;
         }
+        r.graze |= ph.graze;
         if (out->fate) out->fate[g] = (uint8_t)r.fate;
         if (out->plane) out->plane[g] = r.plane;
         if (out->ix) out->ix[g] = r.ix;

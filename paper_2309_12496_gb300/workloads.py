@@ -657,6 +657,7 @@ class Workload:
     source: int = SOURCE_CHERENKOV
     yield_per_mm: float = 0.0         # isotropic source: mean photons per mm
     spectrum_table: int = -1          # isotropic source: CDF table index
+    dispersion: tuple | None = None   # (a nm^-2, lambda0 nm): n - 1 = a/(1/l0^2 - 1/l^2)
 
 
 def point_source(n_photons=100_000) -> Workload:
@@ -862,3 +863,22 @@ def water(n_tracks=10, seed=0) -> Workload:
     return Workload("water", water_tank_scene(), water_muons(n_tracks, seed=seed),
                     n_minus_1=0.33, lambda_min=300.0, lambda_max=600.0, seed=seed,
                     description=f"{n_tracks} muons, 2000 mm of water, 4 m tank of detector walls")
+
+
+# ------------------------------------------------- dispersive radiator
+# Single-resonance form n(lambda) - 1 = a / (1/lambda0^2 - 1/lambda^2)
+# (lambda in nm) with parameters chosen for a C4F10-like gas: n - 1 =
+# 1.59e-3 at 200 nm, 1.42e-3 at 400 nm, 1.40e-3 at 600 nm (synthetic).
+C4F10_DISPERSION = (float(np.float32(2.5324e-7)), float(np.float32(73.7)))
+
+
+def rich1_dispersive(n_tracks=1000, seed=0, meshed=True) -> Workload:
+    """The RICH1-like workload with a dispersive radiator: each photon's
+    Cherenkov angle follows n(lambda) of its own wavelength, the yield is
+    the Frank-Tamm integral of sin^2 theta(lambda), and the wavelength law
+    is sin^2 theta(lambda) / lambda^2."""
+    wl = rich1(n_tracks, seed=seed, meshed=meshed)
+    wl.name = "rich1_dispersive"
+    wl.dispersion = C4F10_DISPERSION
+    wl.description += ", dispersive n(lambda)"
+    return wl

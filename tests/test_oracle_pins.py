@@ -656,3 +656,98 @@ def test_scintillation_box_bookkeeping(oracle_lib):
     assert len(np.unique(out["n_refl"][det])) >= 4
     assert out["pixel_counts"].sum() == det.sum()
     assert (out["graze"] != 0).mean() < 0.01
+
+
+# ------------------------------------------------------ dispersive radiator
+def _n1_disp(lam_nm, a, l0):
+    """n - 1 of the single-resonance form (its definition, lambda in nm)."""
+    return a / (1.0 / l0**2 - 1.0 / lam_nm**2)
+
+
+@pytest.mark.parametrize("p", [1000.0, 50.0, 4.0, 2.75, 2.6, 2.5, 2.4])
+def test_dispersive_yield_matches_quadrature(oracle_lib, p):
+    """Frank-Tamm photons per mm with n(lambda): the oracle's closed-form
+    integral against numerical quadrature of
+    2 pi alpha int max(0, 1 - 1/(n(lambda) beta)^2) dlambda / lambda^2 over
+    200-600 nm, for pions from far above threshold to below it (between
+    2.47 and 2.64 GeV/c only the shorter wavelengths emit)."""
+    from scipy import integrate
+    a, l0 = w.C4F10_DISPERSION
+    wl = w.rich1_dispersive(1)
+    prm = oracle_lib.params(wl)
+    p, m = float(np.float32(p)), float(np.float32(w.PION_MASS))   # the FP32 inputs
+    E = math.sqrt(p * p + m * m)
+    beta = p / E
+    f = lambda lam: max(0.0, 1.0 - 1.0 / ((1 + _n1_disp(lam, a, l0)) * beta) ** 2) / lam**2
+    g = lambda lam: (1 + _n1_disp(lam, a, l0)) * beta - 1
+    hi = 600.0
+    if g(200.0) > 0 > g(600.0):       # emission stops inside the band: split there
+        from scipy import optimize
+        hi = optimize.brentq(g, 200.0, 600.0, xtol=1e-13)
+    ref = 0.0 if g(200.0) <= 0 else 2 * math.pi / 137.035999 * integrate.quad(
+        f, 200.0, hi, limit=200, epsabs=1e-15, epsrel=1e-13)[0] * 1e6
+    got = oracle_lib.disp_yield_per_mm(prm, p, m)
+    if ref == 0.0:
+        assert got == 0.0
+    else:
+        assert got == pytest.approx(ref, rel=1e-8, abs=1e-12)
+    if p < 2.45:
+        assert got == 0.0
+
+
+def test_dispersive_yield_constant_index_limit(oracle_lib):
+    """With lambda0 far below the band, n - 1 = a lambda0^2 (1 + O(lambda0^2 /
+    lambda^2)) is constant to 1e-5 and the yield equals the constant-index
+    Frank-Tamm value (itself pinned to the PDG constant) to 1e-4."""
+    wl = w.rich1_dispersive(1)
+    wl.dispersion = (float(np.float32(1.4e-3)), 1.0)
+    prm = oracle_lib.params(wl)
+    got = oracle_lib.disp_yield_per_mm(prm, 1e6, 0.0)
+    ref = oracle_lib.yield_per_mm(1.4e-3, 1.0, 200.0, 600.0)
+    assert got == pytest.approx(ref, rel=1e-4)
+
+
+def test_dispersive_emission_wavelength_law_and_angle(oracle_lib):
+    """Photons of a beta = 1 point source with n(lambda): the wavelengths
+    follow the density sin^2 theta(lambda) / lambda^2 (KS against its
+    numerically integrated CDF), and every hit of the point-source scene
+    lies at (R/2) tan theta(lambda) of its own wavelength (the source sits
+    at the centre of curvature), tan theta = sqrt(n(lambda)^2 - 1)."""
+    from scipy import integrate, stats
+    a, l0 = w.C4F10_DISPERSION
+    wl = w.point_source(100000)
+    wl.dispersion = w.C4F10_DISPERSION
+    out = oracle_lib.Scene(wl.scene).trace(wl.tracks, oracle_lib.params(wl))
+    dens = lambda lam: (1.0 - 1.0 / (1 + _n1_disp(lam, a, l0)) ** 2) / lam**2
+    norm = integrate.quad(dens, 200.0, 600.0)[0]
+    grid = np.linspace(200.0, 600.0, 401)
+    cdf_grid = np.array([integrate.quad(dens, 200.0, x)[0] / norm for x in grid])
+    lam = out["lambda"].astype(np.float64)
+    u = np.interp(lam, grid, cdf_grid)
+    assert stats.kstest(u, "uniform").pvalue > 1e-3
+    # the constant-index spectrum 1/lambda^2 is rejected by the same test
+    u_flat = (1 / 200.0 - 1 / lam) / (1 / 200.0 - 1 / 600.0)
+    assert stats.kstest(u_flat, "uniform").pvalue < 1e-6
+    det, r = _ring_radii(out, wl.scene.rects[0])
+    n = 1 + _n1_disp(out["lambda"][det].astype(np.float64), np.float64(a), np.float64(l0))
+    np.testing.assert_allclose(r, 1355.0 * np.sqrt(n * n - 1), rtol=0, atol=1e-9)
+    assert r.max() - r.min() > 3.0        # dispersion spreads the ring
+
+
+def test_dispersive_threshold_band(oracle_lib):
+    """A 2.55 GeV/c pion in C4F10-like gas is above threshold only at short
+    wavelengths: every photon's wavelength lies below the threshold
+    wavelength where n(lambda) beta = 1."""
+    a, l0 = w.C4F10_DISPERSION
+    wl = w.rich1_dispersive(1, meshed=False)
+    p, m = 2.55, w.PION_MASS
+    wl.tracks = w._make_tracks(1, (0.0, 0.0, 0.0), np.array([[0.0, 0.0, 1.0]]), p=[p],
+                               mass=[m], length=[1000.0], event=[0], tid=[0], n_fixed=[3000])
+    out = oracle_lib.Scene(wl.scene).trace(wl.tracks, oracle_lib.params(wl))
+    pf, mf = float(np.float32(p)), float(np.float32(m))
+    beta = pf / math.sqrt(pf * pf + mf * mf)
+    from scipy import optimize
+    lam_t = optimize.brentq(lambda lam: (1 + _n1_disp(lam, a, l0)) * beta - 1, 200.0, 600.0)
+    assert lam_t < 400.0
+    assert out["lambda"].max() <= lam_t * (1 + 1e-6)
+    assert out["lambda"].min() >= 200.0
