@@ -38,7 +38,9 @@
  *       per photon, block 1: reflectivity tests at mirror reflections 0..3
  *       per photon, block 2: reflectivity tests at mirror reflections 4..7
  *       per photon, block 3: w0, w1 -> Gaussian smear of the hit (loss only),
- *                            w2 -> cos(theta) of an isotropic photon
+ *                            w2 -> cos(theta) of an isotropic photon,
+ *                            w3 -> first wavelength test (dispersive radiator)
+ *       per photon, blocks 8..39: further wavelength trials (dispersive)
  *       per track (photon = 0xFFFFFFFF), blocks 0,1,...: Poisson sampler
  *     A 32-bit word w maps to the uniform (w >> 8) * 2^-24 in [0, 1).
  */
@@ -206,7 +208,21 @@ enum { RICH_SOURCE_CHERENKOV = 0, RICH_SOURCE_ISOTROPIC = 1 };
  *   (or the track's n_fixed), wavelength from the scene's RICH_TABLE_CDF
  *   table `spectrum_table` (>= 0; needs the geometry loaded), or from the
  *   1/lambda^2 law on [lambda_min, lambda_max] when spectrum_table < 0.
- *   n_minus_1 and the track momenta are not used. */
+ *   n_minus_1 and the track momenta are not used.
+ * dispersion (Cherenkov source only): 0 = constant n_minus_1; 1 = the
+ *   radiator's index follows n(lambda) - 1 = disp_a / (1/disp_lambda0^2 -
+ *   1/lambda^2) (lambda, disp_lambda0 in nm, disp_a in nm^-2; needs
+ *   lambda_min > disp_lambda0) and n_minus_1 is not used. Each photon then
+ *   has the Cherenkov angle of its own wavelength, cos(theta) =
+ *   1/(n(lambda) beta); the track's mean count is the Frank-Tamm integral
+ *   2 pi alpha L int sin^2 theta(lambda) dlambda / lambda^2 over the part of
+ *   the band where n(lambda) beta > 1 (closed form, FP64); and the
+ *   wavelength is drawn by accept/reject: a candidate from the 1/lambda^2 law
+ *   on that part of the band is kept with probability
+ *   sin^2 theta(lambda) / sin^2 theta(lambda_min), both in FP32. Trial 0
+ *   uses draw block 0 word 2 (candidate) and block 3 word 3 (test); trial
+ *   t >= 1 uses block 8 + (t-1)/2, words 2((t-1) mod 2) and 2((t-1) mod 2)+1;
+ *   after 64 trials the last candidate stands. */
 typedef struct rich_emit_params {
     uint64_t seed;
     float n_minus_1;
@@ -216,7 +232,9 @@ typedef struct rich_emit_params {
     int32_t source;
     float yield_per_mm;
     int32_t spectrum_table;
-    int32_t reserved2;
+    int32_t dispersion;
+    float disp_a;
+    float disp_lambda0;
 } rich_emit_params;
 
 /* Materialised photons, structure of arrays of DEVICE pointers (caller

@@ -47,6 +47,8 @@ struct rich_ctx {
     float inv1 = 0.f, span = 0.f;
     int32_t source = RICH_SOURCE_CHERENKOV;   // light source of the last emission
     int32_t spectrum = -1;                    // its CDF table, or -1
+    int32_t dispersion = 0;                   // its radiator: 1 dispersive
+    float disp_a = 0.f, disp_lambda0 = 0.f;
     std::vector<int32_t> table_kind;          // kinds of the scene's tables (host)
     // small device state: counters + photon total
     Counters *d_ctr = nullptr;
@@ -262,7 +264,7 @@ void free_emission(rich_ctx *ctx) {
 EmitView emit_view(const rich_ctx *ctx) {
     EmitView em{ctx->d_rec, ctx->d_cs, ctx->d_offsets, ctx->d_total, ctx->n_tracks,
                 ctx->key0, ctx->key1, ctx->inv1, ctx->span, ctx->d_perm, ctx->d_perm_ok,
-                ctx->source, ctx->spectrum};
+                ctx->source, ctx->spectrum, ctx->dispersion, ctx->disp_a, ctx->disp_lambda0};
     return em;
 }
 
@@ -270,7 +272,8 @@ EmitView emit_view(const rich_ctx *ctx) {
 // scratch (asynchronous).
 rich_status emit_core(rich_ctx *ctx, const rich_tracks *t, uint64_t seed, float n_minus_1,
                       float lambda_min, float lambda_max, int32_t source = RICH_SOURCE_CHERENKOV,
-                      float yield_per_mm = 0.f, int32_t spectrum = -1) {
+                      float yield_per_mm = 0.f, int32_t spectrum = -1, int32_t dispersion = 0,
+                      float disp_a = 0.f, float disp_lambda0 = 0.f) {
     const int64_t n = t->n;
     if (n + 1 > ctx->track_cap) {
         RICH_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -304,13 +307,18 @@ rich_status emit_core(rich_ctx *ctx, const rich_tracks *t, uint64_t seed, float 
         RICH_CUDA(launch_yield(tv, (double)n_minus_1, lambda_min, lambda_max, ctx->key0,
                                ctx->key1, ctx->d_rec, ctx->d_cs, ctx->d_counts, ctx->d_bsum,
                                ctx->stream,
-                               source == RICH_SOURCE_ISOTROPIC ? (double)yield_per_mm : -1.0));
+                               YieldModel{source == RICH_SOURCE_ISOTROPIC ? (double)yield_per_mm
+                                                                          : -1.0,
+                                          dispersion, disp_a, disp_lambda0}));
         RICH_CUDA(launch_offsets(ctx->d_counts, ctx->d_bsum, n, ctx->d_offsets, ctx->d_total,
                                  ctx->stream));
     }
     ctx->n_tracks = n;
     ctx->source = source;
     ctx->spectrum = source == RICH_SOURCE_ISOTROPIC ? spectrum : -1;
+    ctx->dispersion = dispersion;
+    ctx->disp_a = disp_a;
+    ctx->disp_lambda0 = disp_lambda0;
     ctx->has_emission = true;
     return RICH_OK;
 }
@@ -671,12 +679,23 @@ RICH_API rich_status rich_emit(rich_ctx *ctx, const rich_tracks *t,
             return fail(ctx, RICH_ERR_ARG,
                         "rich_emit: spectrum_table is not a CDF table of the loaded scene");
     }
+    if (prm->dispersion != 0 && prm->dispersion != 1)
+        return fail(ctx, RICH_ERR_ARG, "rich_emit: dispersion must be 0 or 1");
+    if (prm->dispersion) {
+        if (prm->source != RICH_SOURCE_CHERENKOV)
+            return fail(ctx, RICH_ERR_ARG, "rich_emit: dispersion applies to the Cherenkov source");
+        if (!(prm->disp_a > 0.f) || !std::isfinite(prm->disp_a) || !(prm->disp_lambda0 > 0.f) ||
+            !(prm->lambda_min > prm->disp_lambda0))
+            return fail(ctx, RICH_ERR_ARG,
+                        "rich_emit: dispersion needs disp_a > 0 and 0 < disp_lambda0 < lambda_min");
+    }
     DeviceGuard guard(ctx->device);
     const int64_t n = t->n;
     {
         const rich_status st = emit_core(ctx, t, prm->seed, prm->n_minus_1, prm->lambda_min,
                                          prm->lambda_max, prm->source, prm->yield_per_mm,
-                                         prm->spectrum_table < 0 ? -1 : prm->spectrum_table);
+                                         prm->spectrum_table < 0 ? -1 : prm->spectrum_table,
+                                         prm->dispersion, prm->disp_a, prm->disp_lambda0);
         if (st != RICH_OK) return st;
     }
     if (n_photons || out) {
@@ -868,8 +887,10 @@ RICH_API rich_status rich_trace_grad(rich_ctx *ctx, const rich_tracks *t,
     if (o->n_prefilter != 0)
         return fail(ctx, RICH_ERR_ARG,
                     "rich_trace_grad: the gradient takes in-flight efficiencies (n_prefilter = 0)");
-    if (prm->source != RICH_SOURCE_CHERENKOV)
-        return fail(ctx, RICH_ERR_ARG, "rich_trace_grad: the gradient is defined for the Cherenkov source");
+    if (prm->source != RICH_SOURCE_CHERENKOV || prm->dispersion)
+        return fail(ctx, RICH_ERR_ARG,
+                    "rich_trace_grad: the gradient is defined for the Cherenkov source with a "
+                    "constant index");
     for (int k = 0; k < 8; ++k)
         if (!std::isfinite(th->tilt[k]) || std::fabs(th->tilt[k]) > 0.5f)
             return fail(ctx, RICH_ERR_ARG, "rich_trace_grad: tilts must be finite, |tilt| <= 0.5 rad");

@@ -82,11 +82,22 @@ struct alignas(16) DevNode { // 64 B: boxes of both children + child refs
 struct alignas(16) TrackRec {  // 64 B, written by the yield kernel
     float x, y, z, len;
     float tx, ty, tz, tan_theta;  // unit direction (FP64-normalised) and tan
+                                  // theta (constant index) or 1 - beta (FP32,
+                                  // dispersive radiator)
     float rx, ry, rz;             // raw input direction
     uint32_t event;
     uint32_t id;
     uint32_t count;
-    uint32_t pad0, pad1;
+    float disp_span;              // dispersive: FP32 1/lambda_min - 1/lambda_hi
+                                  // of the emitting band
+    float disp_s2max;             // dispersive: FP32 sin^2 theta(lambda_min)
+};
+
+// Emission model of the yield kernel.
+struct YieldModel {
+    double iso_yield;      // >= 0: isotropic source, photons per mm
+    int32_t dispersion;    // 1: dispersive radiator (a, lambda0)
+    float disp_a, disp_lambda0;
 };
 
 struct SceneView {
@@ -126,6 +137,8 @@ struct EmitView {            // result of rich_emit used by the trace
     const uint32_t *perm_ok;  // device flag: perm covers this emission
     int32_t source;           // RICH_SOURCE_*
     int32_t spectrum;         // isotropic: CDF table index of the scene, or -1
+    int32_t dispersion;       // 1: dispersive radiator
+    float disp_a, disp_lambda0;
 };
 
 struct ExtView {             // caller photons
@@ -195,13 +208,14 @@ struct LaunchShape {
 };
 
 // ---------------------------------------------------------------- launchers
-// iso_yield_per_mm >= 0: isotropic source with that mean per mm (the
-// Cherenkov angle is not computed); < 0: Cherenkov source.
+// model.iso_yield >= 0: isotropic source with that mean per mm (the
+// Cherenkov angle is not computed); < 0: Cherenkov source, constant index
+// n_minus_1 or the dispersive radiator of model.
 cudaError_t launch_yield(const TracksView &t, double n_minus_1,
                          double lam_min, double lam_max, uint32_t key0,
                          uint32_t key1, TrackRec *rec, double2 *cs,
                          uint32_t *counts, unsigned long long *block_sums,
-                         cudaStream_t s, double iso_yield_per_mm = -1.0);
+                         cudaStream_t s, const YieldModel &model);
 cudaError_t launch_offsets(const uint32_t *counts,
                            const unsigned long long *block_sums,
                            int64_t n_tracks, uint64_t *offsets,

@@ -140,11 +140,57 @@ __device__ int64_t poisson_draw(double mu, TrackStream &s) {
     return (int64_t)floor(mu + 0.5);
 }
 
+// ------------------------------------------------- dispersive radiator
+// sin^2 theta of the single-resonance radiator at lambda in FP32, one IEEE
+// operation at a time (it decides the wavelength accept/reject):
+// n - 1 = a / ((1/l0 - 1/l)(1/l0 + 1/l)), n beta - 1 = (n - 1) - (1 - beta)
+// - (n - 1)(1 - beta), sin^2 = (n beta - 1)(n beta + 1) / (n beta)^2.
+__device__ __forceinline__ float disp_s2_f32(float a, float il0, float omb, float lam) {
+    const float il = __fdiv_rn(1.0f, lam);
+    const float den = __fmul_rn(__fsub_rn(il0, il), __fadd_rn(il0, il));
+    const float n1 = __fdiv_rn(a, den);
+    const float nb1 = __fsub_rn(__fsub_rn(n1, omb), __fmul_rn(n1, omb));
+    if (!(nb1 > 0.0f)) return 0.0f;
+    const float num = __fmul_rn(nb1, __fadd_rn(2.0f, nb1));
+    const float op = __fadd_rn(1.0f, nb1);
+    return __fdiv_rn(num, __fmul_rn(op, op));
+}
+
+__device__ __forceinline__ double atanh64(double z) {
+    return 0.5 * log64(__ddiv_rn(1.0 + z, 1.0 - z));
+}
+
+// Frank-Tamm photons per mm of the dispersive radiator (FP64): with
+// x = 1/lambda, c = 1/l0^2 and q = c + a, 1/n^2 = (1 - a/(q - x^2))^2, so
+// sin^2 theta integrates in closed form over the emitting part
+// [max(1/lambda_max, x_t), 1/lambda_min] of the band, x_t^2 = c - a beta /
+// (1 - beta) being where n beta = 1. Returns x_t (0: no threshold) too.
+__device__ double disp_yield_per_mm(const YieldModel &m, double beta, double omb,
+                                   double lam_min, double lam_max, double &xt) {
+    const double il0 = 1.0 / (double)m.disp_lambda0, a = (double)m.disp_a;
+    xt = 0.0;
+    if (omb > 0.0) {
+        const double u = il0 * il0 - a * beta / omb;
+        if (u > 0.0) xt = sqrt(u);
+    }
+    double xa = 1.0 / lam_max;
+    const double xb = 1.0 / lam_min;
+    if (xt > xa) xa = xt;
+    if (!(xb > xa)) return 0.0;
+    const double q = il0 * il0 + a, sq = sqrt(q), b2 = beta * beta;
+    const double c0 = -omb * (2.0 - omb) / b2;              // 1 - 1/beta^2
+    const double F1b = atanh64(xb / sq) / sq, F1a = atanh64(xa / sq) / sq;
+    const double F2b = xb / (2.0 * q * (q - xb * xb)) + atanh64(xb / sq) / (2.0 * q * sq);
+    const double F2a = xa / (2.0 * q * (q - xa * xa)) + atanh64(xa / sq) / (2.0 * q * sq);
+    const double I = c0 * (xb - xa) + (2.0 * a / b2) * (F1b - F1a) - (a * a / b2) * (F2b - F2a);
+    return 2.0 * kPi * kAlpha * I * 1.0e6;
+}
+
 template <bool RECS>
 __global__ void __launch_bounds__(kYieldBlock)
 k_yield(TracksView t, double n_minus_1, double inv_band_mm, uint32_t key0,
         uint32_t key1, TrackRec *rec, double2 *cs, uint32_t *counts,
-        unsigned long long *block_sums, double iso_yield) {
+        unsigned long long *block_sums, YieldModel model, double lam_min, double lam_max) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t count = 0;
     if (i < t.n) {
@@ -155,9 +201,24 @@ k_yield(TracksView t, double n_minus_1, double inv_band_mm, uint32_t key0,
         double beta = 1.0 - one_minus_beta;
         double nb_minus_1 = n_minus_1 * beta - one_minus_beta;
         double cos_t = 1.0, sin_t = 0.0, tan_t = 0.0, mu = 0.0;
-        if (iso_yield >= 0.0) {
+        float disp_span = 0.0f, disp_s2max = 0.0f;
+        if (model.iso_yield >= 0.0) {
             // isotropic source: mean photons = yield per mm x length
-            mu = len * iso_yield;
+            mu = len * model.iso_yield;
+        } else if (model.dispersion) {
+            // dispersive radiator: Frank-Tamm integral of sin^2 theta(lambda),
+            // and the FP32 band and normaliser of the wavelength accept/reject
+            double xt = 0.0;
+            mu = len * disp_yield_per_mm(model, beta, one_minus_beta, lam_min, lam_max, xt);
+            const float inv1 = __fdiv_rn(1.0f, (float)lam_min);
+            const float inv2 = __fdiv_rn(1.0f, (float)lam_max);
+            const float xlo = (float)xt > inv2 ? (float)xt : inv2;
+            disp_span = __fsub_rn(inv1, xlo);
+            tan_t = (double)(float)one_minus_beta;          // stored as 1 - beta
+            disp_s2max = disp_s2_f32(model.disp_a, __fdiv_rn(1.0f, model.disp_lambda0),
+                                     (float)one_minus_beta, (float)lam_min);
+            cos_t = beta;                                    // (beta, 1 - beta) in FP64
+            sin_t = one_minus_beta;
         } else if (nb_minus_1 > 0.0) {
             double nb = 1.0 + nb_minus_1;
             double tan2 = nb_minus_1 * (nb + 1.0);      // (n beta)^2 - 1
@@ -193,7 +254,8 @@ k_yield(TracksView t, double n_minus_1, double inv_band_mm, uint32_t key0,
         r.event = event;
         r.id = id;
         r.count = count;
-        r.pad0 = r.pad1 = 0;
+        r.disp_span = disp_span;
+        r.disp_s2max = disp_s2max;
         rec[i] = r;
         cs[i] = make_double2(cos_t, sin_t);
         }
@@ -345,24 +407,68 @@ __device__ __forceinline__ float spectrum_lambda(const DevTable &T, float u) {
     return __fadd_rn(T.p0, __fmul_rn(__fadd_rn((float)k, fr), T.p1));
 }
 
-// Wavelength of a photon from its draw: the source's binned spectrum, or the
-// Frank-Tamm 1/lambda^2 law on the emission band.
-__device__ __forceinline__ float photon_lambda(uint32_t w, const EmitView &em,
-                                               const DevTable *spec) {
-    return spec ? spectrum_lambda(*spec, u24f(w)) : emit_lambda(u24f(w), em.inv1, em.span);
+// Wavelength of a dispersive-radiator photon: candidates from the 1/lambda^2
+// law on the track's emitting band kept with probability
+// sin^2 theta(lambda) / sin^2 theta(lambda_min); trial 0 takes block 0 word
+// 2 and block 3 word 3, trial t >= 1 block 8 + (t-1)/2; the last of 64
+// candidates stands.
+__device__ float disp_lambda(const TrackRec &tr, uint32_t j, const EmitView &em, uint32_t wl0,
+                             uint32_t wa0) {
+    const float il0 = __fdiv_rn(1.0f, em.disp_lambda0);
+    const float omb = tr.tan_theta;
+    float lam = 0.0f;
+    for (int t = 0; t < 64; ++t) {
+        uint32_t wl = wl0, wa = wa0;
+        if (t > 0) {
+            const u4 w = philox10(8u + (uint32_t)(t - 1) / 2u, j, tr.id, tr.event, em.key0,
+                                  em.key1);
+            const bool hi = ((t - 1) & 1) != 0;
+            wl = hi ? w.z : w.x;
+            wa = hi ? w.w : w.y;
+        }
+        lam = __fdiv_rn(1.0f, __fsub_rn(em.inv1, __fmul_rn(u24f(wl), tr.disp_span)));
+        if (!(tr.disp_s2max > 0.0f)) break;
+        const float pa = __fdiv_rn(disp_s2_f32(em.disp_a, il0, omb, lam), tr.disp_s2max);
+        if (u24f(wa) < pa) break;
+    }
+    return lam;
+}
+
+// Wavelength of a fused-emission photon from its draws: the source's binned
+// spectrum, the dispersive radiator's law, or the Frank-Tamm 1/lambda^2 law
+// on the emission band.
+__device__ __forceinline__ float photon_wavelength(const TrackRec &tr, uint32_t j,
+                                                   const EmitView &em, const u4 &w0,
+                                                   const DevTable *spec) {
+    if (spec) return spectrum_lambda(*spec, u24f(w0.z));
+    if (em.dispersion) {
+        const u4 w3 = philox10(3u, j, tr.id, tr.event, em.key0, em.key1);
+        return disp_lambda(tr, j, em, w0.z, w3.w);
+    }
+    return emit_lambda(u24f(w0.z), em.inv1, em.span);
+}
+
+// FP32 tan(theta) of the dispersive radiator at lambda: sqrt((n beta)^2 - 1)
+// with n beta - 1 formed without cancellation.
+__device__ __forceinline__ float disp_tan_f32(const EmitView &em, float omb, float lam) {
+    const float il0 = __fdiv_rn(1.0f, em.disp_lambda0);
+    const float il = __fdiv_rn(1.0f, lam);
+    const float n1 = em.disp_a / ((il0 - il) * (il0 + il));
+    const float nb1 = (n1 - omb) - n1 * omb;
+    return sqrtf(fmaxf(0.0f, nb1 * (2.0f + nb1)));
 }
 
 // Fused emission of photon j of track tr (Sec. 3 angle, Sec. 4.2 photons as
 // independent rays): origin uniform on the segment, azimuth uniform,
-// wavelength from the Frank-Tamm spectrum. The direction is built as
+// wavelength `lam` from photon_wavelength. The direction is built as
 // t + tan(theta) (cos phi e1 + sin phi e2), normalised, so the small
-// Cherenkov angle is carried by tan(theta) and not by a cosine near 1.
+// Cherenkov angle is carried by tan(theta) and not by a cosine near 1;
+// a dispersive radiator takes tan(theta) of the photon's own wavelength.
 // Isotropic source (the scintillation light named in Sec. 6): the
-// direction is uniform on the sphere, cos(theta) = 1 - 2u from draw block 3,
-// and the wavelength comes from the source's spectrum table `spec`.
+// direction is uniform on the sphere, cos(theta) = 1 - 2u from draw block 3.
 __device__ __forceinline__ void emit_photon(const TrackRec &tr, uint32_t j,
-                                            const EmitView &em, const u4 &w0,
-                                            const DevTable *spec, Photon &ph) {
+                                            const EmitView &em, const u4 &w0, float lam,
+                                            Photon &ph) {
     u4 w1 = philox10(1u, j, tr.id, tr.event, em.key0, em.key1);
     f3 t = mk3(tr.tx, tr.ty, tr.tz);
     float s = u24f(w0.x) * tr.len;
@@ -378,9 +484,10 @@ __device__ __forceinline__ void emit_photon(const TrackRec &tr, uint32_t j,
         f3 e1, e2;
         basis_f(t, e1, e2);
         f3 r = fma3(e1, cp, e2 * sp);
-        ph.d = normalize3(fma3(r, tr.tan_theta, t));
+        const float tan_t = em.dispersion ? disp_tan_f32(em, tr.tan_theta, lam) : tr.tan_theta;
+        ph.d = normalize3(fma3(r, tan_t, t));
     }
-    ph.lam = photon_lambda(w0.z, em, spec);
+    ph.lam = lam;
     ph.w_qe = w0.w;
     ph.wr0 = w1.x;
     ph.wr1 = w1.y;
@@ -403,7 +510,8 @@ __global__ void k_materialize(SceneView sc, EmitView em, uint64_t n, rich_photon
         TrackRec tr = em.tracks[lo];
         Photon ph;
         const uint32_t j = (uint32_t)(g - em.offsets[lo]);
-        emit_photon(tr, j, em, philox10(0u, j, tr.id, tr.event, em.key0, em.key1), spec, ph);
+        const u4 w0 = philox10(0u, j, tr.id, tr.event, em.key0, em.key1);
+        emit_photon(tr, j, em, w0, photon_wavelength(tr, j, em, w0, spec), ph);
         out.x[g] = ph.o.x;
         out.y[g] = ph.o.y;
         out.z[g] = ph.o.z;
@@ -812,8 +920,8 @@ __device__ __forceinline__ void basis_ff(const ff3 &t, ff3 &e1, ff3 &e2) {
 // azimuth 2 pi u from an FP64 sincospi, cos and sin of the Cherenkov angle
 // from the FP64 yield pass. Isotropic source: cos(theta) = 1 - 2u (exact)
 // and sin(theta) = 2 sqrt(u (1 - u)) from the exact product u (1 - u).
-__device__ void emit_ff(const TrackRec &tr, double2 cs, uint32_t j, const EmitView &em,
-                        ff3 &o, ff3 &d) {
+__device__ void emit_ff(const TrackRec &tr, double2 cs, uint32_t j, float lam,
+                        const EmitView &em, ff3 &o, ff3 &d) {
     const u4 w0 = philox10(0u, j, tr.id, tr.event, em.key0, em.key1);
     const ff3 t = ff3_normalized(ff3v(tr.rx, tr.ry, tr.rz));
     const ff s = two_prod(u24f(w0.x), tr.len);      // exact: 24 x 24 bits
@@ -833,7 +941,17 @@ __device__ void emit_ff(const TrackRec &tr, double2 cs, uint32_t j, const EmitVi
     const ff r_x = ff_add(ff_mul(e1.x, ff_from_double(cp)), ff_mul(e2.x, ff_from_double(sp)));
     const ff r_y = ff_add(ff_mul(e1.y, ff_from_double(cp)), ff_mul(e2.y, ff_from_double(sp)));
     const ff r_z = ff_add(ff_mul(e1.z, ff_from_double(cp)), ff_mul(e2.z, ff_from_double(sp)));
-    const ff ct = ff_from_double(cs.x), st = ff_from_double(cs.y);
+    double cos_t = cs.x, sin_t = cs.y;
+    if (em.dispersion) {
+        // dispersive radiator: the angle of the photon's own wavelength, FP64,
+        // from (beta, 1 - beta) = cs and n(lambda) - 1
+        const double il0 = 1.0 / (double)em.disp_lambda0, il = 1.0 / (double)lam;
+        const double n1 = (double)em.disp_a / ((il0 - il) * (il0 + il));
+        const double nb1 = (n1 - cs.y) - n1 * cs.y;
+        cos_t = 1.0 / (1.0 + nb1);
+        sin_t = nb1 > 0.0 ? sqrt(nb1 * (2.0 + nb1)) * cos_t : 0.0;
+    }
+    const ff ct = ff_from_double(cos_t), st = ff_from_double(sin_t);
     d = ff3_normalized({ff_add(ff_mul(t.x, ct), ff_mul(r_x, st)),
                         ff_add(ff_mul(t.y, ct), ff_mul(r_y, st)),
                         ff_add(ff_mul(t.z, ct), ff_mul(r_z, st))});
@@ -1098,13 +1216,13 @@ k_trace(TraceArgs A) {
                             j = em.perm[g];
                         ph.g = toff + j;
                         const u4 w0 = philox10(0u, j, tr.id, tr.event, em.key0, em.key1);
+                        const float lam = photon_wavelength(tr, j, em, w0, spec);
                         // efficiencies before propagation (Sec. 4.3): only
                         // the wavelength is needed to decide
-                        if (P.n_prefilter &&
-                            !(u24f(w0.w) < prefilter_prob(S, P, photon_lambda(w0.z, em, spec))))
+                        if (P.n_prefilter && !(u24f(w0.w) < prefilter_prob(S, P, lam)))
                             rejected = true;
                         else
-                            emit_photon(tr, j, em, w0, spec, ph);
+                            emit_photon(tr, j, em, w0, lam, ph);
                     }
                     if (rejected) {
                         if (P.fate) P.fate[ph.g] = (uint8_t)RICH_FATE_PREFILTERED;
@@ -1338,7 +1456,7 @@ k_refine(SceneView sc, EmitView em, ExtView ext, TraceParams P, Counters *ctr) {
                 o = ff3v(ext.x[g], ext.y[g], ext.z[g]);
                 d = ff3_normalized(ff3v(ext.dx[g], ext.dy[g], ext.dz[g]));
             } else {
-                emit_ff(em.tracks[rr.index], em.cos_sin[rr.index], h.photon, em, o, d);
+                emit_ff(em.tracks[rr.index], em.cos_sin[rr.index], h.photon, h.lambda, em, o, d);
             }
             ff uf, vf;
             replay_ff(sc, o, d, rr, uf, vf);
@@ -1685,7 +1803,7 @@ cudaError_t launch_yield(const TracksView &t, double n_minus_1,
                          double lam_min, double lam_max, uint32_t key0,
                          uint32_t key1, TrackRec *rec, double2 *cs,
                          uint32_t *counts, unsigned long long *block_sums,
-                         cudaStream_t s, double iso_yield_per_mm) {
+                         cudaStream_t s, const YieldModel &model) {
     if (t.n <= 0) return cudaSuccess;
     const double inv_band_mm = 1.0e6 / lam_min - 1.0e6 / lam_max;
     const int64_t groups = (t.n + kYieldThreads - 1) / kYieldThreads;
@@ -1694,12 +1812,12 @@ cudaError_t launch_yield(const TracksView &t, double n_minus_1,
     const unsigned blocks = (unsigned)((t.n + kYieldBlock - 1) / kYieldBlock);
     if (rec)
         k_yield<true><<<blocks, kYieldBlock, 0, s>>>(t, n_minus_1, inv_band_mm, key0, key1,
-                                                     rec, cs, counts, block_sums,
-                                                     iso_yield_per_mm);
+                                                     rec, cs, counts, block_sums, model,
+                                                     lam_min, lam_max);
     else
         k_yield<false><<<blocks, kYieldBlock, 0, s>>>(t, n_minus_1, inv_band_mm, key0, key1,
-                                                      rec, cs, counts, block_sums,
-                                                      iso_yield_per_mm);
+                                                      rec, cs, counts, block_sums, model,
+                                                      lam_min, lam_max);
     return cudaGetLastError();
 }
 

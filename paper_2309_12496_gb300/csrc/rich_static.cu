@@ -60,6 +60,12 @@ extern "C" RICH_API rich_status rich_photon_counts_static(const rich_tracks *t,
         set_global_error("rich_photon_counts_static: unknown source or negative yield");
         return RICH_ERR_ARG;
     }
+    if (prm->dispersion && (!(prm->disp_a > 0.f) || !(prm->disp_lambda0 > 0.f) ||
+                            !(prm->lambda_min > prm->disp_lambda0))) {
+        set_global_error("rich_photon_counts_static: dispersion needs disp_a > 0 and "
+                         "0 < disp_lambda0 < lambda_min");
+        return RICH_ERR_ARG;
+    }
     if (!(prm->n_minus_1 >= 0.f) || !(prm->lambda_min > 0.f) ||
         !(prm->lambda_max > prm->lambda_min)) {
         set_global_error("rich_photon_counts_static: need n-1 >= 0 and 0 < lambda_min < lambda_max");
@@ -97,9 +103,12 @@ extern "C" RICH_API rich_status rich_photon_counts_static(const rich_tracks *t,
                       t->event, t->id, t->n_fixed};
         const uint32_t key0 = (uint32_t)prm->seed, key1 = (uint32_t)(prm->seed >> 32);
         // launch_yield clears the group sums this call uses before adding
+        const YieldModel model{
+            prm->source == RICH_SOURCE_ISOTROPIC ? (double)prm->yield_per_mm : -1.0,
+            prm->source == RICH_SOURCE_CHERENKOV && prm->dispersion ? 1 : 0, prm->disp_a,
+            prm->disp_lambda0};
         e = launch_yield(tv, (double)prm->n_minus_1, prm->lambda_min, prm->lambda_max, key0, key1,
-                         nullptr, nullptr, counts, sums, s,
-                         prm->source == RICH_SOURCE_ISOTROPIC ? (double)prm->yield_per_mm : -1.0);
+                         nullptr, nullptr, counts, sums, s, model);
         if (e == cudaSuccess) e = launch_offsets(counts, sums, t->n, offsets, nullptr, s);
     }
     if (e != cudaSuccess) {

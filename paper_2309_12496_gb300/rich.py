@@ -73,7 +73,21 @@ class EmitParams(C.Structure):
                 ("lambda_min", C.c_float), ("lambda_max", C.c_float),
                 ("reserved", C.c_float), ("source", C.c_int32),
                 ("yield_per_mm", C.c_float), ("spectrum_table", C.c_int32),
-                ("reserved2", C.c_int32)]
+                ("dispersion", C.c_int32), ("disp_a", C.c_float),
+                ("disp_lambda0", C.c_float)]
+
+
+def _emit_params(seed, n_minus_1, lambda_min, lambda_max, source=SOURCE_CHERENKOV,
+                 yield_per_mm=0.0, spectrum_table=-1, dispersion=None):
+    """rich_emit_params; dispersion: None (constant index) or (a nm^-2,
+    lambda0 nm) of n(lambda) - 1 = a / (1/lambda0^2 - 1/lambda^2)."""
+    return EmitParams(seed=int(seed), n_minus_1=float(n_minus_1),
+                      lambda_min=float(lambda_min), lambda_max=float(lambda_max),
+                      source=int(source), yield_per_mm=float(yield_per_mm),
+                      spectrum_table=int(spectrum_table),
+                      dispersion=0 if dispersion is None else 1,
+                      disp_a=0.0 if dispersion is None else float(dispersion[0]),
+                      disp_lambda0=0.0 if dispersion is None else float(dispersion[1]))
 
 
 class PhotonsDesc(C.Structure):
@@ -342,14 +356,13 @@ class Context:
 
     def emit(self, tracks: DeviceTracks, n_minus_1, lambda_min=200.0, lambda_max=600.0,
              seed=0, photons: PhotonBuffers | None = None, sync=True,
-             source=SOURCE_CHERENKOV, yield_per_mm=0.0, spectrum_table=-1):
+             source=SOURCE_CHERENKOV, yield_per_mm=0.0, spectrum_table=-1, dispersion=None):
         """source: SOURCE_CHERENKOV, or SOURCE_ISOTROPIC with yield_per_mm
         photons per mm and the scene's CDF table spectrum_table (-1: the
-        1/lambda^2 law on the band)."""
-        prm = EmitParams(seed=int(seed), n_minus_1=float(n_minus_1),
-                         lambda_min=float(lambda_min), lambda_max=float(lambda_max),
-                         source=int(source), yield_per_mm=float(yield_per_mm),
-                         spectrum_table=int(spectrum_table))
+        1/lambda^2 law on the band). dispersion: None or (a, lambda0) of
+        the dispersive radiator (Cherenkov source)."""
+        prm = _emit_params(seed, n_minus_1, lambda_min, lambda_max, source, yield_per_mm,
+                           spectrum_table, dispersion)
         n = C.c_uint64(0)
         pd = photons.desc() if photons is not None else None
         st = load().rich_emit(self.handle, C.byref(tracks.desc()), C.byref(prm),
@@ -475,7 +488,8 @@ def rich_hits(ctx: Context, **kw):
 
 def rich_photon_counts_static(tracks: DeviceTracks, n_minus_1, counts, offsets,
                               lambda_min=200.0, lambda_max=600.0, seed=0, stream=None,
-                              n=None, source=SOURCE_CHERENKOV, yield_per_mm=0.0):
+                              n=None, source=SOURCE_CHERENKOV, yield_per_mm=0.0,
+                              dispersion=None):
     """Per-track photon counts (int32 view of u32) and offsets (int64 view of
     u64, n + 1 entries) into caller device tensors, with no device
     allocation by the library. `n` overrides the track count passed."""
@@ -483,9 +497,8 @@ def rich_photon_counts_static(tracks: DeviceTracks, n_minus_1, counts, offsets,
     d = tracks.desc()
     if n is not None:
         d.n = int(n)
-    prm = EmitParams(seed=int(seed), n_minus_1=float(n_minus_1),
-                     lambda_min=float(lambda_min), lambda_max=float(lambda_max),
-                     source=int(source), yield_per_mm=float(yield_per_mm), spectrum_table=-1)
+    prm = _emit_params(seed, n_minus_1, lambda_min, lambda_max, source, yield_per_mm, -1,
+                       dispersion)
     s = current_stream_handle() if stream is None else stream
     st = L.rich_photon_counts_static(C.byref(d), C.byref(prm), C.c_void_p(counts.data_ptr()),
                                      C.c_void_p(offsets.data_ptr()), C.c_void_p(s))

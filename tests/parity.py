@@ -33,7 +33,8 @@ def run_gpu(wl: W.Workload, precision=rich.PREC_REFINE64, ctx=None, want_fate=Tr
         ctx.init_geometry(wl.scene)
     dt = dtracks if dtracks is not None else rich.DeviceTracks(wl.tracks)
     n = ctx.emit(dt, wl.n_minus_1, wl.lambda_min, wl.lambda_max, wl.seed, source=wl.source,
-                 yield_per_mm=wl.yield_per_mm, spectrum_table=wl.spectrum_table)
+                 yield_per_mm=wl.yield_per_mm, spectrum_table=wl.spectrum_table,
+                 dispersion=wl.dispersion)
     ne = n_events(wl.tracks) if hist else 0
     out = rich.TraceOutputs(max(n, 1), wl.scene.pixels_per_event, len(wl.scene.planes),
                             ne, n if want_fate else 0)
