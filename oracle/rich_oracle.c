@@ -156,7 +156,7 @@ enum { FATE_NONE = 0, FATE_ESCAPED = 1, FATE_MIRROR_ABSORBED = 2,
        FATE_MAX_BOUNCES = 6, FATE_MAX_STEPS = 7, FATE_PREFILTERED = 8 };
 enum { TAB_CONST = 0, TAB_GAUSS = 1, TAB_HIST = 2, TAB_CDF = 3 };
 enum { SRC_CHERENKOV = 0, SRC_ISOTROPIC = 1 };
-enum { MAT_MIRROR = 0, MAT_ABSORBER = 1, MAT_DETECTOR = 2 };
+enum { MAT_MIRROR = 0, MAT_ABSORBER = 1, MAT_DETECTOR = 2, MAT_DIELECTRIC = 3 };
 enum { MAT_SMOOTH = 1 };
 enum { PRIM_SPHERE = 0, PRIM_RECT = 1, PRIM_TRI = 2 };
 
@@ -1160,6 +1160,7 @@ static void trace_photon(const o_scene *sc, const o_params *prm,
 {
     v3 o = ph->o, d = unit(ph->d);
     int skip = -1, n_refl = 0, graze = 0;
+    int n_turn = 0;     /* direction changes: reflections and refractions */
     memset(res, 0, sizeof *res);
     res->plane = -1;
     res->fate = FATE_MAX_STEPS;
@@ -1189,7 +1190,7 @@ static void trace_photon(const o_scene *sc, const o_params *prm,
         }
         if (m->kind == MAT_MIRROR) {
             if (!front) { res->fate = FATE_ABSORBED; o = p; break; }
-            if (n_refl >= prm->max_bounces) {
+            if (n_turn >= prm->max_bounces) {
                 res->fate = FATE_MAX_BOUNCES;
                 o = p;
                 break;
@@ -1206,6 +1207,34 @@ static void trace_photon(const o_scene *sc, const o_params *prm,
             }
             d = unit(reflect(d, n_sh));
             n_refl++;
+            n_turn++;
+            o = p;
+            skip = h.prim;
+            continue;
+        }
+        if (m->kind == MAT_DIELECTRIC) {
+            /* refracting boundary (a window face): the table gives the index
+             * n_w(lambda) of the medium behind the surface relative to the
+             * one in front. Snell's law with the normal N facing the ray,
+             * eta = n_in / n_out: d' = eta d + (eta c1 - sqrt(k)) N,
+             * c1 = -d.N, k = 1 - eta^2 (1 - c1^2); total internal
+             * reflection when k < 0 */
+            if (n_turn >= prm->max_bounces) {
+                res->fate = FATE_MAX_BOUNCES;
+                o = p;
+                break;
+            }
+            double nw = (double)table_eval(&sc->tables[m->table], ph->lambda);
+            double eta = front ? 1.0 / nw : nw;
+            v3 N = front ? n_geo : scl(n_geo, -1.0);
+            double c1 = -dot(d, N);
+            double k = 1.0 - eta * eta * (1.0 - c1 * c1);
+            if (fabs(k) < 1e-6) graze |= 1;   /* near the critical angle */
+            if (k < 0.0)
+                d = unit(reflect(d, N));
+            else
+                d = unit(add(scl(d, eta), scl(N, eta * c1 - sqrt(k))));
+            n_turn++;
             o = p;
             skip = h.prim;
             continue;

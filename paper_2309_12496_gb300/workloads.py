@@ -65,7 +65,7 @@ assert RECT_DTYPE.itemsize == 80
 
 TABLE_CONST, TABLE_GAUSS, TABLE_HIST, TABLE_CDF = 0, 1, 2, 3
 SOURCE_CHERENKOV, SOURCE_ISOTROPIC = 0, 1
-MAT_MIRROR, MAT_ABSORBER, MAT_DETECTOR = 0, 1, 2
+MAT_MIRROR, MAT_ABSORBER, MAT_DETECTOR, MAT_DIELECTRIC = 0, 1, 2, 3
 MAT_SMOOTH = 1
 
 PION_MASS = 0.13957   # GeV/c^2
@@ -232,6 +232,13 @@ R_BINS_B = [0.935, 0.934, 0.932, 0.930, 0.927, 0.924, 0.921, 0.917, 0.914,
             0.910, 0.906, 0.903, 0.899, 0.896, 0.893, 0.890]
 
 
+# Refractive index of a fused-silica-like window, 25 nm bins over 200-600 nm
+# (synthetic smooth shape: 1.551 at 200 nm falling to 1.458 at 600 nm).
+QUARTZ_LAMBDA0, QUARTZ_WIDTH = 200.0, 25.0
+QUARTZ_N = [1.5510, 1.5320, 1.5170, 1.5050, 1.4950, 1.4870, 1.4810, 1.4760, 1.4720,
+            1.4690, 1.4660, 1.4640, 1.4620, 1.4610, 1.4595, 1.4580]
+
+
 # ----------------------------------------------------------- point source
 def point_source_scene(radius=2710.0, half_aperture=0.3, n_pix=256,
                        pitch=PIXEL_PITCH) -> Scene:
@@ -372,9 +379,24 @@ def _add_detector(b, h, material, n_pix, pitch):
            nx=n_pix, ny=n_pix, pitch=pitch)
 
 
+def _add_window(b, h, material, n_pix, pitch, gap, thickness):
+    """A flat window slab in front of a detector plane: the entry face at
+    `gap` from the plane (normal towards the incoming light) and the exit
+    face at gap - thickness (normal towards the plane), so the glass lies
+    behind both faces."""
+    half = n_pix * pitch / 2.0
+    n = np.cross(h.det_u, h.det_v)
+    n = n / np.linalg.norm(n)
+    o = h.det_center - half * h.det_u - half * h.det_v
+    b.rect(origin=o + gap * n, u_axis=h.det_u, v_axis=h.det_v, width=2 * half,
+           height=2 * half, material=material)
+    b.rect(origin=o + (gap - thickness) * n, u_axis=h.det_v, v_axis=h.det_u,
+           width=2 * half, height=2 * half, material=material)
+
+
 def rich1_scene(meshed=True, tiles_per_edge=45, flat_cells=(45, 32),
                 gamma=0.30, d1=950.0, flat_size=(1000.0, 800.0),
-                flat_shift=150.0, image_angle=0.12) -> Scene:
+                flat_shift=150.0, image_angle=0.12, windows=False) -> Scene:
     """RICH1-like folded geometry (synthetic, project-defined layout).
 
     Spherical mirror R = 2710 mm with its pole on the beam axis at
@@ -429,6 +451,13 @@ def rich1_scene(meshed=True, tiles_per_edge=45, flat_cells=(45, 32),
                    height=fh, material=m_flat)
     for i, h in enumerate(halves):
         _add_detector(b, h, m_det[i], 256, PIXEL_PITCH)
+    if windows:
+        # quartz windows, 6 mm thick, 20 mm in front of the two focal planes
+        # (the detector windows the paper's simplified geometry removed, Sec. 4.1)
+        t_quartz = b.table_hist(QUARTZ_LAMBDA0, QUARTZ_WIDTH, QUARTZ_N)
+        m_quartz = b.material(MAT_DIELECTRIC, t_quartz)
+        for h in halves:
+            _add_window(b, h, m_quartz, 256, PIXEL_PITCH, gap=20.0, thickness=6.0)
     half = 256 * PIXEL_PITCH / 2.0
     b.rect(origin=(half, -half, 2400.0), u_axis=(-1.0, 0.0, 0.0),
            v_axis=(0.0, 1.0, 0.0), width=256 * PIXEL_PITCH,
@@ -881,4 +910,15 @@ def rich1_dispersive(n_tracks=1000, seed=0, meshed=True) -> Workload:
     wl.name = "rich1_dispersive"
     wl.dispersion = C4F10_DISPERSION
     wl.description += ", dispersive n(lambda)"
+    return wl
+
+
+def rich1_windows(n_tracks=1000, seed=0, meshed=True) -> Workload:
+    """The RICH1-like workload with 6 mm quartz windows 20 mm in front of the
+    two focal planes: photons refract into and out of each window (Snell's
+    law with the wavelength-dependent index of the window)."""
+    wl = rich1(n_tracks, seed=seed, meshed=meshed)
+    wl.scene = rich1_scene(meshed=meshed, windows=True)
+    wl.name = "rich1_windows"
+    wl.description += ", quartz windows"
     return wl

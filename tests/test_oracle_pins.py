@@ -751,3 +751,90 @@ def test_dispersive_threshold_band(oracle_lib):
     assert lam_t < 400.0
     assert out["lambda"].max() <= lam_t * (1 + 1e-6)
     assert out["lambda"].min() >= 200.0
+
+
+# ------------------------------------------------- refraction (window slab)
+def _slab(b, z_lo, z_hi, half, material):
+    """Slab z_lo <= z <= z_hi: faces whose normals point away from the glass
+    (the material's index applies behind each face)."""
+    b.rect(origin=(-half, -half, z_hi), u_axis=(1, 0, 0), v_axis=(0, 1, 0), width=2 * half,
+           height=2 * half, material=material)                      # normal +z
+    b.rect(origin=(-half, half, z_lo), u_axis=(1, 0, 0), v_axis=(0, -1, 0), width=2 * half,
+           height=2 * half, material=material)                      # normal -z
+
+
+def test_window_slab_ring_closed_form(oracle_lib):
+    """A beta = 1 Cherenkov cone (water, n = 1.33, theta = 41 degrees) from a
+    point along +z crosses a 30 mm glass slab (900 < z < 930) before a
+    plane at z = 1000: Snell's law at both faces gives the ring radius
+    970 tan(theta) + 30 tan(theta_r), sin(theta_r) = sin(theta) / n_w(lambda)
+    with the window's binned index at each photon's wavelength (paper
+    Sec. 4.1 removed the windows; this puts one back)."""
+    b = w._Builder("slab_ring")
+    t_qe = b.table_const(1.0)
+    t_n = b.table_hist(w.QUARTZ_LAMBDA0, w.QUARTZ_WIDTH, w.QUARTZ_N)
+    m_det = b.material(w.MAT_DETECTOR, t_qe, plane=0)
+    m_glass = b.material(w.MAT_DIELECTRIC, t_n)
+    _slab(b, 900.0, 930.0, 2000.0, m_glass)
+    b.rect(origin=(-1280.0, 1280.0, 1000.0), u_axis=(1, 0, 0), v_axis=(0, -1, 0), width=2560.0,
+           height=2560.0, material=m_det, nx=256, ny=256, pitch=10.0)
+    scene = b.build()
+    tr = w._make_tracks(1, (0.0, 0.0, 0.0), np.array([[0.0, 0.0, 1.0]]), p=[1e6], mass=[0.0],
+                        length=[0.0], event=[0], tid=[0], n_fixed=[5000])
+    wl = w.Workload("slab_ring", scene, tr, n_minus_1=0.33)
+    out = oracle_lib.Scene(scene).trace(tr, oracle_lib.params(wl))
+    det = out["fate"] == 5
+    assert det.all()
+    n = 1 + float(np.float32(0.33))
+    sin_t = math.sqrt(1 - 1 / n**2)
+    lam = out["lambda"].astype(np.float32)
+    k = np.clip(np.floor((lam - np.float32(200)) / np.float32(25)), 0, 15).astype(int)
+    n_w = np.asarray(w.f32(w.QUARTZ_N), np.float64)[k]
+    sin_r = sin_t / n_w
+    r_exp = 970.0 * sin_t / math.sqrt(1 - sin_t**2) + 30.0 * sin_r / np.sqrt(1 - sin_r**2)
+    r = np.hypot(out["u"] - 1280.0, out["v"] - 1280.0)
+    np.testing.assert_allclose(r, r_exp, rtol=0, atol=1e-9)
+    assert r.max() - r.min() > 0.5            # the index varies with the wavelength
+
+
+def test_window_total_internal_reflection_fraction(oracle_lib):
+    """An isotropic source in the middle of a 6 mm slab of index 1.5 with
+    photodetector planes (QE = 1) 7 mm above and below: only photons with
+    |cos(theta)| > cos(theta_c) = sqrt(1 - 1/n^2) leave through a face, so
+    the detected fraction is 1 - cos(theta_c) = 0.2546; each escaping photon
+    lands at 3 tan(theta_in) + 7 tan(theta_out) from the source's foot,
+    sin(theta_out) = n sin(theta_in); trapped photons bounce by total
+    internal reflection until the direction-change limit."""
+    from scipy import stats
+    b = w._Builder("slab_tir")
+    t_qe = b.table_const(1.0)
+    t_n = b.table_const(1.5)
+    m_det = [b.material(w.MAT_DETECTOR, t_qe, plane=i) for i in range(2)]
+    m_glass = b.material(w.MAT_DIELECTRIC, t_n)
+    _slab(b, -3.0, 3.0, 2000.0, m_glass)
+    b.rect(origin=(-2048.0, 2048.0, 10.0), u_axis=(1, 0, 0), v_axis=(0, -1, 0), width=4096.0,
+           height=4096.0, material=m_det[0], nx=256, ny=256, pitch=16.0)
+    b.rect(origin=(-2048.0, -2048.0, -10.0), u_axis=(1, 0, 0), v_axis=(0, 1, 0), width=4096.0,
+           height=4096.0, material=m_det[1], nx=256, ny=256, pitch=16.0)
+    scene = b.build()
+    N = 40000
+    tr = w._make_tracks(1, (0.0, 0.0, 0.0), np.array([[0.0, 0.0, 1.0]]), p=[1.0], mass=[0.0],
+                        length=[0.0], event=[0], tid=[0], n_fixed=[N])
+    wl = w.Workload("slab_tir", scene, tr, n_minus_1=0.0, source=w.SOURCE_ISOTROPIC)
+    prm = oracle_lib.params(wl)
+    out = oracle_lib.Scene(scene).trace(tr, prm)
+    det = out["fate"] == 5
+    frac = 1 - math.sqrt(1 - 1 / 1.5**2)
+    assert abs(det.mean() - frac) < 4 * math.sqrt(frac * (1 - frac) / N)
+    assert set(np.unique(out["fate"][~det])) <= {1, 6}
+    assert stats.chisquare(np.bincount(out["plane"][det], minlength=2)).pvalue > 1e-3
+    for g in np.nonzero(det)[0][:400]:
+        _, d, _ = oracle_lib.emit(tr, prm, 0, int(g))
+        s_in = math.hypot(d[0], d[1])
+        s_out = 1.5 * s_in
+        r_exp = 3 * s_in / abs(d[2]) + 7 * s_out / math.sqrt(1 - s_out**2)
+        up = d[2] > 0
+        cx = 2048.0
+        r = math.hypot(out["u"][g] - cx, out["v"][g] - cx)
+        assert out["plane"][g] == (0 if up else 1)
+        assert abs(r - r_exp) < 1e-9
