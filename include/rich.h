@@ -74,7 +74,8 @@ typedef enum rich_status {
 
 /* ----------------------------------------------------- geometry description */
 enum { RICH_TABLE_CONST = 0, RICH_TABLE_GAUSS = 1, RICH_TABLE_HIST = 2, RICH_TABLE_CDF = 3 };
-enum { RICH_MAT_MIRROR = 0, RICH_MAT_ABSORBER = 1, RICH_MAT_DETECTOR = 2 };
+enum { RICH_MAT_MIRROR = 0, RICH_MAT_ABSORBER = 1, RICH_MAT_DETECTOR = 2,
+       RICH_MAT_DIELECTRIC = 3 };
 enum { RICH_MAT_SMOOTH = 1 }; /* material flag: triangles use vertex normals */
 
 #define RICH_TABLE_MAX_BINS 64
@@ -107,11 +108,18 @@ typedef struct rich_table {
 } rich_table;
 
 /* Surface material. kind: RICH_MAT_*. table: index of the reflectivity
- * (mirror) or quantum-efficiency (detector) table. plane: detector-plane
- * index for detectors (selects the hit plane and histogram slice), else -1.
- * flags: RICH_MAT_SMOOTH. Mirrors reflect on their front side and absorb on
- * the back; detectors accept on the front and are transparent from the back;
- * absorbers absorb on both sides. */
+ * (mirror) or quantum-efficiency (detector) table, or of the refractive
+ * index (dielectric). plane: detector-plane index for detectors (selects the
+ * hit plane and histogram slice), else -1. flags: RICH_MAT_SMOOTH. Mirrors
+ * reflect on their front side and absorb on the back; detectors accept on
+ * the front and are transparent from the back; absorbers absorb on both
+ * sides. A dielectric surface (a window face; rectangles and triangles only)
+ * separates the medium in front (index 1) from a medium of index
+ * table(lambda) behind it: the photon refracts by Snell's law with
+ * eta = n_in / n_out and the geometric normal, or is totally internally
+ * reflected when 1 - eta^2 (1 - cos^2 theta_i) < 0; no random draw (an
+ * ideal anti-reflection-coated face). A slab is two faces whose normals
+ * point away from the glass. */
 typedef struct rich_material {
     int32_t kind, table, plane, flags;
 } rich_material;
@@ -264,7 +272,8 @@ typedef struct rich_trace_opts {
                                caller-supplied photons (photons from
                                rich_emit use the rich_emit seed)             */
     int32_t precision;      /* RICH_PREC_*                                    */
-    int32_t max_bounces;    /* mirror reflections, 1..RICH_MAX_BOUNCES        */
+    int32_t max_bounces;    /* direction changes (mirror reflections and
+                               refractions), 1..RICH_MAX_BOUNCES             */
     int32_t max_steps;      /* surface interactions, 1..RICH_MAX_STEPS        */
     float t_min;            /* minimum hit distance after an interaction (mm) */
     /* launch knobs (0 -> tuned default) */

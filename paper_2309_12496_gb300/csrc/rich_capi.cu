@@ -50,6 +50,7 @@ struct rich_ctx {
     int32_t dispersion = 0;                   // its radiator: 1 dispersive
     float disp_a = 0.f, disp_lambda0 = 0.f;
     std::vector<int32_t> table_kind;          // kinds of the scene's tables (host)
+    bool has_dielectric = false;              // the scene refracts (window faces)
     // small device state: counters + photon total
     Counters *d_ctr = nullptr;
     unsigned long long *d_total = nullptr;
@@ -471,7 +472,7 @@ RICH_API rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc 
     bool any_smooth = false;
     for (int i = 0; i < g->n_materials; ++i) {
         const rich_material &m = g->materials[i];
-        if (m.kind < 0 || m.kind > 2) return bad("material kind");
+        if (m.kind < 0 || m.kind > 3) return bad("material kind");
         if (m.kind != RICH_MAT_ABSORBER && (m.table < 0 || m.table >= g->n_tables))
             return bad("material table index out of range");
         if (m.kind != RICH_MAT_ABSORBER && g->tables[m.table].kind == RICH_TABLE_CDF)
@@ -482,6 +483,14 @@ RICH_API rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc 
     }
     if (any_smooth && g->n_triangles && !g->tri_normals)
         return bad("smooth material without vertex normals");
+    bool any_dielectric = false;
+    for (int i = 0; i < g->n_materials; ++i)
+        any_dielectric |= g->materials[i].kind == RICH_MAT_DIELECTRIC;
+    for (int i = 0; i < g->n_spheres; ++i) {
+        const int32_t mi = g->spheres[i].material;
+        if (mi >= 0 && mi < g->n_materials && g->materials[mi].kind == RICH_MAT_DIELECTRIC)
+            return bad("refracting (dielectric) material on a sphere tile");
+    }
     // ---- sphere groups (tiles sharing a sphere)
     std::vector<DevSphereGroup> groups;
     std::vector<DevTile> tiles;
@@ -648,6 +657,7 @@ RICH_API rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc 
         RICH_CUDA(cudaMalloc(&ctx->d_grad_tiles,
                              sizeof(DevSphereGroup) * RICH_MAX_GROUPS + sizeof(DevTile) * RICH_MAX_TILES));
     }
+    ctx->has_dielectric = any_dielectric;
     ctx->table_kind.assign(g->n_tables, 0);
     for (int i = 0; i < g->n_tables; ++i) ctx->table_kind[i] = g->tables[i].kind;
     ctx->has_geometry = true;
@@ -887,6 +897,9 @@ RICH_API rich_status rich_trace_grad(rich_ctx *ctx, const rich_tracks *t,
     if (o->n_prefilter != 0)
         return fail(ctx, RICH_ERR_ARG,
                     "rich_trace_grad: the gradient takes in-flight efficiencies (n_prefilter = 0)");
+    if (ctx->has_dielectric)
+        return fail(ctx, RICH_ERR_ARG,
+                    "rich_trace_grad: the gradient is defined for scenes without refracting faces");
     if (prm->source != RICH_SOURCE_CHERENKOV || prm->dispersion)
         return fail(ctx, RICH_ERR_ARG,
                     "rich_trace_grad: the gradient is defined for the Cherenkov source with a "

@@ -396,6 +396,7 @@ struct Photon {
     uint32_t w_qe;
     uint32_t wr0, wr1, wr2, wr3;
     int skip, n_refl, steps;
+    int n_turn;            // direction changes: reflections and refractions
 };
 
 // Wavelength from a binned emission spectrum (CDF table): the bin k with
@@ -837,11 +838,13 @@ __device__ void nearest_bvh(const SceneView &sc, const DevNode *snodes, int n_sn
 // extended past its edges, the final plane. All geometry is FP32 input, so
 // it enters the replay exactly. Runs in its own pass (k_refine), one thread
 // per stored hit, so the warps are converged.
-__device__ void replay_ff(const SceneView &sc, ff3 o, ff3 d, const RefineRec &rr, ff &u,
-                          ff &v) {
+__device__ void replay_ff(const SceneView &sc, ff3 o, ff3 d, const RefineRec &rr, float lam,
+                          ff &u, ff &v) {
     for (int k = 0; k < rr.n_path; ++k) {
         const int prim = rr.path[k];
-        ff3 n;
+        ff3 n;               // reflective (shading) normal
+        ff3 ng;              // geometric unit normal
+        int mat;
         if (prim < sc.n_tiles) {
             int ti = 0;
             for (int q = 0; q < sc.n_tiles; ++q)
@@ -859,9 +862,13 @@ __device__ void replay_ff(const SceneView &sc, ff3 o, ff3 d, const RefineRec &rr
             o = ff3_axpy(t, d, o);
             const ff3 pc = ff3_sub(o, C);
             n = ff3_scale(pc, ff_neg(ff_rsqrt(ff3_dot(pc, pc))));
+            ng = n;
+            mat = sc.tiles[ti].material;
         } else if (prim < sc.tri_prim_base) {
             const DevRect &R = sc.rects[prim - sc.n_tiles];
             n = ff3v(R.nx, R.ny, R.nz);
+            ng = n;
+            mat = R.material;
             const ff t = ff_div(ff3_dot(ff3_sub(ff3v(R.ox, R.oy, R.oz), o), n), ff3_dot(d, n));
             o = ff3_axpy(t, d, o);
         } else {
@@ -870,9 +877,11 @@ __device__ void replay_ff(const SceneView &sc, ff3 o, ff3 d, const RefineRec &rr
             const ff3 v0 = ff3v(T.v0x, T.v0y, T.v0z);
             const ff3 e1 = ff3_diff(T.v1x, T.v1y, T.v1z, T.v0x, T.v0y, T.v0z);
             const ff3 e2 = ff3_diff(T.v2x, T.v2y, T.v2z, T.v0x, T.v0y, T.v0z);
-            const ff3 ng = ff3_cross(e1, e2);
-            const ff t = ff_div(ff3_dot(ff3_sub(v0, o), ng), ff3_dot(d, ng));
+            const ff3 ngt = ff3_cross(e1, e2);
+            const ff t = ff_div(ff3_dot(ff3_sub(v0, o), ngt), ff3_dot(d, ngt));
             o = ff3_axpy(t, d, o);
+            ng = ff3_normalized(ngt);
+            mat = T.material;
             const DevMaterial &M = sc.materials[T.material];
             if ((M.flags & RICH_MAT_SMOOTH) && sc.tri_normals) {
                 // barycentrics of the hit in the triangle's plane
@@ -889,8 +898,24 @@ __device__ void replay_ff(const SceneView &sc, ff3 o, ff3 d, const RefineRec &rr
                                       ff3_scale(ff3v(N[6], N[7], N[8]), b2));
                 n = ff3_normalized(m);
             } else {
-                n = ff3_normalized(ng);
+                n = ng;
             }
+        }
+        if (sc.materials[mat].kind == RICH_MAT_DIELECTRIC) {
+            // refraction at a window face (as in the trace), double-word
+            const float nw = table_eval(sc.tables[sc.materials[mat].table], lam);
+            const bool front = ff3_dot(d, ng).hi < 0.0f;
+            const ff3 N = front ? ng : ff3_scale(ng, -1.0f);
+            const ff eta = front ? ff_div(ffv(1.0f), ffv(nw)) : ffv(nw);
+            const ff c1 = ff_neg(ff3_dot(d, N));
+            const ff kk = ff_sub(ffv(1.0f),
+                                 ff_mul(ff_mul(eta, eta), ff_sub(ffv(1.0f), ff_mul(c1, c1))));
+            if (kk.hi < 0.0f)
+                d = ff3_reflect(d, N);
+            else
+                d = ff3_normalized(ff3_add(ff3_scale(d, eta),
+                                           ff3_scale(N, ff_sub(ff_mul(eta, c1), ff_sqrt(kk)))));
+            continue;
         }
         // |d| = 1 is kept by the reflection about a unit normal
         d = ff3_reflect(d, n);
@@ -1188,6 +1213,7 @@ k_trace(TraceArgs A) {
                     ph.g = g;
                     ph.skip = -1;
                     ph.n_refl = 0;
+                    ph.n_turn = 0;
                     ph.steps = 0;
                     if (EXT) {
                         ph.track = (uint32_t)g;
@@ -1268,7 +1294,7 @@ k_trace(TraceArgs A) {
                 const f3 p = fma3(ph.d, b.t, ph.o);
                 int mat_id;
                 bool front;
-                f3 n_sh;
+                f3 n_sh, n_geo;
                 if (b.kind == 0) {
                     const DevTile &T = S.tiles[b.idx];
                     const DevSphereGroup &G = S.groups[T.group];
@@ -1279,11 +1305,13 @@ k_trace(TraceArgs A) {
                     const double pz = fma(tt, (double)ph.d.z, (double)ph.o.z - G.cz);
                     const double inv = -1.0 / sqrt(px * px + py * py + pz * pz);
                     n_sh = mk3((float)(px * inv), (float)(py * inv), (float)(pz * inv));
+                    n_geo = n_sh;
                     front = dot3(ph.d, n_sh) < 0.0f;
                     mat_id = T.material;
                 } else if (b.kind == 1) {
                     const DevRect &R = S.rects[b.idx];
                     n_sh = mk3(R.nx, R.ny, R.nz);
+                    n_geo = n_sh;
                     front = dot3(ph.d, n_sh) < 0.0f;
                     mat_id = R.material;
                 } else {
@@ -1292,6 +1320,7 @@ k_trace(TraceArgs A) {
                     const f3 e2 = mk3(T.v2x - T.v0x, T.v2y - T.v0y, T.v2z - T.v0z);
                     const f3 ng = cross3(e1, e2);
                     front = dot3(ph.d, ng) < 0.0f;
+                    n_geo = normalize3(ng);
                     mat_id = T.material;
                     const DevMaterial &M0 = S.materials[mat_id];
                     if ((M0.flags & RICH_MAT_SMOOTH) && sc.tri_normals) {
@@ -1301,7 +1330,7 @@ k_trace(TraceArgs A) {
                         const f3 n2 = mk3(__ldg(N3 + 6), __ldg(N3 + 7), __ldg(N3 + 8));
                         n_sh = normalize3(fma3(n0, b.b0, fma3(n1, b.b1, n2 * b.b2)));
                     } else {
-                        n_sh = normalize3(ng);
+                        n_sh = n_geo;
                     }
                 }
                 const DevMaterial &M = S.materials[mat_id];
@@ -1310,7 +1339,7 @@ k_trace(TraceArgs A) {
                 } else if (M.kind == RICH_MAT_MIRROR) {
                     if (!front) {
                         fate = RICH_FATE_ABSORBED;
-                    } else if (ph.n_refl >= P.max_bounces) {
+                    } else if (ph.n_turn >= P.max_bounces) {
                         fate = RICH_FATE_MAX_BOUNCES;
                     } else {
                         // with the efficiencies applied before propagation
@@ -1322,11 +1351,31 @@ k_trace(TraceArgs A) {
                             fate = RICH_FATE_MIRROR_ABSORBED;
                         } else {
                             ph.d = normalize3(reflect_f(ph.d, n_sh));
-                            if (REFINE) path[ph.n_refl] = b.kind == 2 ? sc.tri_prim_base + b.idx : b.prim;
+                            if (REFINE) path[ph.n_turn] = b.kind == 2 ? sc.tri_prim_base + b.idx : b.prim;
                             ph.n_refl += 1;
+                            ph.n_turn += 1;
                             ph.o = p;
                             ph.skip = b.prim;
                         }
+                    }
+                } else if (M.kind == RICH_MAT_DIELECTRIC) {
+                    // window face: Snell's law, eta = n_in / n_out with the
+                    // table's index behind the face; total internal
+                    // reflection when k < 0
+                    if (ph.n_turn >= P.max_bounces) {
+                        fate = RICH_FATE_MAX_BOUNCES;
+                    } else {
+                        const float nw = table_eval(S.tables[M.table], ph.lam);
+                        const float eta = front ? __fdiv_rn(1.0f, nw) : nw;
+                        const f3 N = front ? n_geo : n_geo * -1.0f;
+                        const float c1 = -dot3(ph.d, N);
+                        const float k = 1.0f - eta * eta * (1.0f - c1 * c1);
+                        ph.d = k < 0.0f ? normalize3(reflect_f(ph.d, N))
+                                        : normalize3(fma3(N, eta * c1 - sqrtf(k), ph.d * eta));
+                        if (REFINE) path[ph.n_turn] = b.kind == 2 ? sc.tri_prim_base + b.idx : b.prim;
+                        ph.n_turn += 1;
+                        ph.o = p;
+                        ph.skip = b.prim;
                     }
                 } else {  // detector
                     if (!front) {
@@ -1395,7 +1444,7 @@ k_trace(TraceArgs A) {
                         RefineRec rr;
                         rr.index = ph.track;
                         rr.det_rect = (uint8_t)det_rect;
-                        rr.n_path = (uint8_t)ph.n_refl;
+                        rr.n_path = (uint8_t)ph.n_turn;
                         rr.pad = 0;
 #pragma unroll
                         for (int k = 0; k < RICH_MAX_BOUNCES; ++k) rr.path[k] = path[k];
@@ -1459,7 +1508,7 @@ k_refine(SceneView sc, EmitView em, ExtView ext, TraceParams P, Counters *ctr) {
                 emit_ff(em.tracks[rr.index], em.cos_sin[rr.index], h.photon, h.lambda, em, o, d);
             }
             ff uf, vf;
-            replay_ff(sc, o, d, rr, uf, vf);
+            replay_ff(sc, o, d, rr, h.lambda, uf, vf);
             int ix, iy;
             pixel_of_ff(sc.rects[rr.det_rect], uf, vf, ix, iy);
             u = ff_to_double(uf);

@@ -922,3 +922,61 @@ def rich1_windows(n_tracks=1000, seed=0, meshed=True) -> Workload:
     wl.name = "rich1_windows"
     wl.description += ", quartz windows"
     return wl
+
+
+def _slab(b, z_lo, z_hi, half, material):
+    """Slab z_lo <= z <= z_hi: two faces whose normals point away from the
+    glass (the material's index applies behind each face)."""
+    b.rect(origin=(-half, -half, z_hi), u_axis=(1, 0, 0), v_axis=(0, 1, 0), width=2 * half,
+           height=2 * half, material=material)                      # normal +z
+    b.rect(origin=(-half, half, z_lo), u_axis=(1, 0, 0), v_axis=(0, -1, 0), width=2 * half,
+           height=2 * half, material=material)                      # normal -z
+
+
+def slab_ring_scene() -> Scene:
+    """A 30 mm quartz slab (900 < z < 930) before a plane at z = 1000 (256^2
+    pixels of 10 mm, QE = 1): a point source at the origin along +z rings
+    the plane at 970 tan(theta) + 30 tan(theta_r)."""
+    b = _Builder("slab_ring")
+    t_qe = b.table_const(1.0)
+    t_n = b.table_hist(QUARTZ_LAMBDA0, QUARTZ_WIDTH, QUARTZ_N)
+    m_det = b.material(MAT_DETECTOR, t_qe, plane=0)
+    m_glass = b.material(MAT_DIELECTRIC, t_n)
+    _slab(b, 900.0, 930.0, 2000.0, m_glass)
+    b.rect(origin=(-1280.0, 1280.0, 1000.0), u_axis=(1, 0, 0), v_axis=(0, -1, 0), width=2560.0,
+           height=2560.0, material=m_det, nx=256, ny=256, pitch=10.0)
+    return b.build()
+
+
+def slab_tir_scene(n_glass=1.5) -> Scene:
+    """A 6 mm slab of index n_glass (-3 < z < 3, 4 m wide) between two
+    photodetector planes at z = +-10 (256^2 pixels of 16 mm, QE = 1): an
+    isotropic source inside escapes only below the critical angle."""
+    b = _Builder("slab_tir")
+    t_qe = b.table_const(1.0)
+    t_n = b.table_const(n_glass)
+    m_det = [b.material(MAT_DETECTOR, t_qe, plane=i) for i in range(2)]
+    m_glass = b.material(MAT_DIELECTRIC, t_n)
+    _slab(b, -3.0, 3.0, 2000.0, m_glass)
+    b.rect(origin=(-2048.0, 2048.0, 10.0), u_axis=(1, 0, 0), v_axis=(0, -1, 0), width=4096.0,
+           height=4096.0, material=m_det[0], nx=256, ny=256, pitch=16.0)
+    b.rect(origin=(-2048.0, -2048.0, -10.0), u_axis=(1, 0, 0), v_axis=(0, 1, 0), width=4096.0,
+           height=4096.0, material=m_det[1], nx=256, ny=256, pitch=16.0)
+    return b.build()
+
+
+def point_track(n_photons, p=1e6, mass=0.0) -> Tracks:
+    """One zero-length track at the origin along +z with a fixed count."""
+    return _make_tracks(1, (0.0, 0.0, 0.0), np.array([[0.0, 0.0, 1.0]]), p=[p], mass=[mass],
+                        length=[0.0], event=[0], tid=[0], n_fixed=[n_photons])
+
+
+def slab_ring(n_photons=5000) -> Workload:
+    return Workload("slab_ring", slab_ring_scene(), point_track(n_photons), n_minus_1=0.33,
+                    description="water-angle Cherenkov cone through a 30 mm quartz slab")
+
+
+def slab_tir(n_photons=40000) -> Workload:
+    return Workload("slab_tir", slab_tir_scene(), point_track(n_photons, p=1.0), n_minus_1=0.0,
+                    source=SOURCE_ISOTROPIC,
+                    description="isotropic source inside a 6 mm slab of index 1.5")

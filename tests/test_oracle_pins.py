@@ -754,15 +754,6 @@ def test_dispersive_threshold_band(oracle_lib):
 
 
 # ------------------------------------------------- refraction (window slab)
-def _slab(b, z_lo, z_hi, half, material):
-    """Slab z_lo <= z <= z_hi: faces whose normals point away from the glass
-    (the material's index applies behind each face)."""
-    b.rect(origin=(-half, -half, z_hi), u_axis=(1, 0, 0), v_axis=(0, 1, 0), width=2 * half,
-           height=2 * half, material=material)                      # normal +z
-    b.rect(origin=(-half, half, z_lo), u_axis=(1, 0, 0), v_axis=(0, -1, 0), width=2 * half,
-           height=2 * half, material=material)                      # normal -z
-
-
 def test_window_slab_ring_closed_form(oracle_lib):
     """A beta = 1 Cherenkov cone (water, n = 1.33, theta = 41 degrees) from a
     point along +z crosses a 30 mm glass slab (900 < z < 930) before a
@@ -770,18 +761,8 @@ def test_window_slab_ring_closed_form(oracle_lib):
     970 tan(theta) + 30 tan(theta_r), sin(theta_r) = sin(theta) / n_w(lambda)
     with the window's binned index at each photon's wavelength (paper
     Sec. 4.1 removed the windows; this puts one back)."""
-    b = w._Builder("slab_ring")
-    t_qe = b.table_const(1.0)
-    t_n = b.table_hist(w.QUARTZ_LAMBDA0, w.QUARTZ_WIDTH, w.QUARTZ_N)
-    m_det = b.material(w.MAT_DETECTOR, t_qe, plane=0)
-    m_glass = b.material(w.MAT_DIELECTRIC, t_n)
-    _slab(b, 900.0, 930.0, 2000.0, m_glass)
-    b.rect(origin=(-1280.0, 1280.0, 1000.0), u_axis=(1, 0, 0), v_axis=(0, -1, 0), width=2560.0,
-           height=2560.0, material=m_det, nx=256, ny=256, pitch=10.0)
-    scene = b.build()
-    tr = w._make_tracks(1, (0.0, 0.0, 0.0), np.array([[0.0, 0.0, 1.0]]), p=[1e6], mass=[0.0],
-                        length=[0.0], event=[0], tid=[0], n_fixed=[5000])
-    wl = w.Workload("slab_ring", scene, tr, n_minus_1=0.33)
+    wl = w.slab_ring(5000)
+    scene, tr = wl.scene, wl.tracks
     out = oracle_lib.Scene(scene).trace(tr, oracle_lib.params(wl))
     det = out["fate"] == 5
     assert det.all()
@@ -806,21 +787,9 @@ def test_window_total_internal_reflection_fraction(oracle_lib):
     sin(theta_out) = n sin(theta_in); trapped photons bounce by total
     internal reflection until the direction-change limit."""
     from scipy import stats
-    b = w._Builder("slab_tir")
-    t_qe = b.table_const(1.0)
-    t_n = b.table_const(1.5)
-    m_det = [b.material(w.MAT_DETECTOR, t_qe, plane=i) for i in range(2)]
-    m_glass = b.material(w.MAT_DIELECTRIC, t_n)
-    _slab(b, -3.0, 3.0, 2000.0, m_glass)
-    b.rect(origin=(-2048.0, 2048.0, 10.0), u_axis=(1, 0, 0), v_axis=(0, -1, 0), width=4096.0,
-           height=4096.0, material=m_det[0], nx=256, ny=256, pitch=16.0)
-    b.rect(origin=(-2048.0, -2048.0, -10.0), u_axis=(1, 0, 0), v_axis=(0, 1, 0), width=4096.0,
-           height=4096.0, material=m_det[1], nx=256, ny=256, pitch=16.0)
-    scene = b.build()
     N = 40000
-    tr = w._make_tracks(1, (0.0, 0.0, 0.0), np.array([[0.0, 0.0, 1.0]]), p=[1.0], mass=[0.0],
-                        length=[0.0], event=[0], tid=[0], n_fixed=[N])
-    wl = w.Workload("slab_tir", scene, tr, n_minus_1=0.0, source=w.SOURCE_ISOTROPIC)
+    wl = w.slab_tir(N)
+    scene, tr = wl.scene, wl.tracks
     prm = oracle_lib.params(wl)
     out = oracle_lib.Scene(scene).trace(tr, prm)
     det = out["fate"] == 5
