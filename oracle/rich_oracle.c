@@ -30,11 +30,26 @@
  *   6. hit list, per-pixel counts and per-event sums (Sec. 6: the detector
  *      writes the position of each ray into a list).
  *
+ * Variants of these steps:
+ *   - efficiencies applied before propagation (Sec. 4.3): one accept/reject
+ *     per photon on the product of listed tables at its wavelength, with its
+ *     QE uniform; accepted photons then reflect and are recorded without
+ *     further tests;
+ *   - other light sources (Sec. 6: liquids, scintillation): isotropic
+ *     emission along a segment with a yield per mm and a binned spectrum;
+ *     water is the Cherenkov source with n = 1.33;
+ *   - a dispersive radiator n(lambda): per-photon Cherenkov angle, the
+ *     Frank-Tamm integral of sin^2 theta(lambda) as the mean count, and the
+ *     wavelength law sin^2 theta(lambda)/lambda^2 by accept/reject;
+ *   - refraction at window faces (Snell's law, total internal reflection),
+ *     the windows the paper's simplified geometry removed (Sec. 4.1).
+ *
  * Precision rules. Geometry runs in FP64 on the FP32 input values promoted
- * exactly. Two quantities that decide integers are evaluated in FP32, the
+ * exactly. Quantities that decide integers are evaluated in FP32, the
  * precision the propagator itself takes those decisions in: the wavelength
- * (it selects a histogram bin) and the response probabilities R(lambda) and
- * QE(lambda) compared with a uniform. Every photon whose outcome hinges on
+ * (it selects a histogram bin), the response probabilities R(lambda) and
+ * QE(lambda) (and their product before propagation) compared with a
+ * uniform, and the dispersive radiator's wavelength acceptance. Every photon whose outcome hinges on
  * a decision closer than a margin to its threshold (a point within eps of a
  * surface, aperture, triangle, grid or pixel edge; two surfaces within eps
  * in distance; a uniform within prob_eps of its probability) is flagged as
