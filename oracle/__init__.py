@@ -62,7 +62,7 @@ class SceneIn(C.Structure):
                 ("tables", C.c_void_p), ("materials", C.c_void_p),
                 ("spheres", C.c_void_p), ("rects", C.c_void_p),
                 ("tri_v", C.c_void_p), ("tri_n", C.c_void_p),
-                ("tri_m", C.c_void_p)]
+                ("tri_m", C.c_void_p), ("tri_s", C.c_void_p)]
 
 
 class TracksIn(C.Structure):
@@ -237,14 +237,16 @@ class Scene:
                       np.ascontiguousarray(scene.tri_vertices, np.float32),
                       None if scene.tri_normals is None else
                       np.ascontiguousarray(scene.tri_normals, np.float32),
-                      np.ascontiguousarray(scene.tri_material, np.int32)]
+                      np.ascontiguousarray(scene.tri_material, np.int32),
+                      None if scene.tri_surface is None else
+                      np.ascontiguousarray(scene.tri_surface, np.int32)]
         k = self._keep
         rec = SceneIn(n_tables=len(k[0]), n_materials=len(k[1]),
                       n_spheres=len(k[2]), n_rects=len(k[3]),
                       n_triangles=scene.n_triangles, tables=_ptr(k[0]),
                       materials=_ptr(k[1]), spheres=_ptr(k[2]),
                       rects=_ptr(k[3]), tri_v=_ptr(k[4]), tri_n=_ptr(k[5]),
-                      tri_m=_ptr(k[6]))
+                      tri_m=_ptr(k[6]), tri_s=_ptr(k[7]))
         self.handle = lib().oracle_scene_create(C.byref(rec), leaf_size)
         self.n_planes = len(scene.planes)
         self.pixels_per_event = int(lib().oracle_scene_pixels_per_event(self.handle))

@@ -107,6 +107,7 @@ typedef struct {
     const float *tri_v;      /* n x 3 x 3 */
     const float *tri_n;      /* n x 3 x 3 or NULL */
     const int32_t *tri_m;    /* n */
+    const int32_t *tri_s;    /* n surface ids (>= 0 shared, -1 own) or NULL */
 } o_scene_in;
 
 typedef struct {
@@ -653,6 +654,8 @@ typedef struct {
     v3 n0, n1, n2;
     v3 ng;        /* unit geometric normal, (v1-v0)x(v2-v0) */
     int material;
+    int surface;  /* surface id (>= 0) shared by the triangles of one mirror
+                     segment, flat or window face, or -1 */
 } o_tri;
 typedef struct {
     double lo[3], hi[3];
@@ -824,6 +827,7 @@ void *oracle_scene_create(const o_scene_in *in, int leaf_size)
             t->n0 = t->n1 = t->n2 = t->ng;
         }
         t->material = in->tri_m[i];
+        t->surface = in->tri_s ? in->tri_s[i] : -1;
     }
     s->order = (int *)malloc(sizeof(int) * ((size_t)s->n_tris + 1));
     for (int64_t i = 0; i < s->n_tris; ++i) s->order[i] = (int)i;
@@ -998,6 +1002,10 @@ static int box_hit(const o_node *nd, v3 o, v3 d, double t_max, double pad)
 /* Nearest surface along o + t d, t > t_min, skipping primitive `skip`.
  * Returns 1 and fills *hit if found; *graze set when the decision is
  * within eps of changing. */
+/* Nearest surface along the ray. `skip` is the primitive the photon just
+ * left: it is not intersected again, and neither is any triangle of the
+ * same surface (a photon leaving a mirror segment, a flat mirror or a window
+ * face does not meet that surface again at its next step). */
 static int nearest(const o_scene *sc, v3 o, v3 d, int skip, double t_min,
                    double eps, int use_bvh, o_cand *hit, int *graze)
 {
@@ -1005,6 +1013,11 @@ static int nearest(const o_scene *sc, v3 o, v3 d, int skip, double t_min,
     memset(&s, 0, sizeof s);
     double near_t = INFINITY;
     int prim = 0;
+    const int tb = sc->n_spheres + sc->n_rects;
+    const int skip_surface = (skip >= tb && skip - tb < sc->n_tris)
+                                 ? sc->tris[skip - tb].surface : -1;
+#define SKIP_TRI(ti) ((tb + (ti)) == skip || \
+                      (skip_surface >= 0 && sc->tris[(ti)].surface == skip_surface))
     for (int i = 0; i < sc->n_spheres; ++i, ++prim)
         if (prim != skip)
             isect_sphere(&sc->spheres[i], prim, o, d, t_min, eps, &s, &near_t);
@@ -1024,7 +1037,7 @@ static int nearest(const o_scene *sc, v3 o, v3 d, int skip, double t_min,
                 if (nd->left < 0) {
                     for (int k = nd->first; k < nd->first + nd->count; ++k) {
                         int ti = sc->order[k];
-                        if (tri_base + ti == skip) continue;
+                        if (SKIP_TRI(ti)) continue;
                         isect_tri(&sc->tris[ti], tri_base + ti, ti, o, d,
                                   t_min, eps, &s, &near_t);
                     }
@@ -1035,12 +1048,13 @@ static int nearest(const o_scene *sc, v3 o, v3 d, int skip, double t_min,
             }
         } else {
             for (int64_t ti = 0; ti < sc->n_tris; ++ti) {
-                if (tri_base + ti == skip) continue;
+                if (SKIP_TRI(ti)) continue;
                 isect_tri(&sc->tris[ti], (int)(tri_base + ti), (int)ti, o, d,
                           t_min, eps, &s, &near_t);
             }
         }
     }
+#undef SKIP_TRI
     *graze = s.graze;
     if (s.found && s.best.edge < eps) *graze = 1;
     if (near_t < INFINITY && (!s.found || near_t < s.best.t + eps)) *graze = 1;

@@ -23,6 +23,7 @@
 #include "rich_device.cuh"
 #include "rich_ff.cuh"
 #include "rich_log_tables.h"
+#include "rich_trig_tables.h"
 
 namespace rich {
 
@@ -940,9 +941,36 @@ __device__ __forceinline__ void basis_ff(const ff3 &t, ff3 &e1, ff3 &e2) {
     e2 = {b, ff_add(ff_mul(ff_mul(t.y, t.y), a), s), ff_neg(t.y)};
 }
 
+// sin and cos of 2 pi u for the 24-bit uniform u = k 2^-24 of a draw word,
+// double-word (~48 bits) without FP64: with k = 2^16 j + r, 2 pi u = A_j + d,
+// A_j = 2 pi j / 256 from a table of (sin, cos) as hi + lo, and
+// d = r (2 pi / 2^24) < 2 pi / 256; sin d and cos d by their Taylor series
+// (the leading terms in double-word, the rest, below 1e-10, in FP32); then
+// the angle-addition formulas.
+__device__ __forceinline__ void ff_sincos_2pi(uint32_t w, ff &s, ff &c) {
+    const uint32_t k = w >> 8;
+    const int j = (int)(k >> 16);
+    const float r = (float)(k & 0xFFFFu);
+    const ff d = ff_mul(ff{kTwoPi24Hi, kTwoPi24Lo}, r);
+    const ff d2 = ff_mul(d, d);
+    const float t2 = d2.hi;
+    // sin d = d - d^3/6 + d^5/120 - d^7/5040
+    const ff d3_6 = ff_mul(ff_mul(d, d2), ff{kSixthHi, kSixthLo});
+    const float s_tail = d.hi * t2 * t2 * (1.0f / 120.0f - t2 * (1.0f / 5040.0f));
+    const ff sd = ff_add(ff_sub(d, d3_6), s_tail);
+    // cos d = 1 - d^2/2 + d^4/24 - d^6/720
+    const ff d4_24 = ff_mul(ff_mul(d2, t2), 1.0f / 24.0f);
+    const float c_tail = -t2 * t2 * t2 * (1.0f / 720.0f);
+    const ff cd = ff_add(ff_add(ff_sub(ffv(1.0f), ff{0.5f * d2.hi, 0.5f * d2.lo}), d4_24), c_tail);
+    const float4 T = __ldg(reinterpret_cast<const float4 *>(g_sincos_tab[j]));
+    const ff sa{T.x, T.y}, ca{T.z, T.w};
+    s = ff_add(ff_mul(sa, cd), ff_mul(ca, sd));
+    c = ff_sub(ff_mul(ca, cd), ff_mul(sa, sd));
+}
+
 // Emission of photon j of a track with the same draws as emit_photon:
 // the track direction normalised, the origin at s = u L along it, the
-// azimuth 2 pi u from an FP64 sincospi, cos and sin of the Cherenkov angle
+// azimuth 2 pi u from ff_sincos_2pi, cos and sin of the Cherenkov angle
 // from the FP64 yield pass. Isotropic source: cos(theta) = 1 - 2u (exact)
 // and sin(theta) = 2 sqrt(u (1 - u)) from the exact product u (1 - u).
 __device__ void emit_ff(const TrackRec &tr, double2 cs, uint32_t j, float lam,
@@ -951,21 +979,20 @@ __device__ void emit_ff(const TrackRec &tr, double2 cs, uint32_t j, float lam,
     const ff3 t = ff3_normalized(ff3v(tr.rx, tr.ry, tr.rz));
     const ff s = two_prod(u24f(w0.x), tr.len);      // exact: 24 x 24 bits
     o = ff3_axpy(s, t, ff3v(tr.x, tr.y, tr.z));
-    double sp, cp;
-    sincospi(2.0 * u24d(w0.y), &sp, &cp);
+    ff sp, cp;
+    ff_sincos_2pi(w0.y, sp, cp);
     if (em.source == RICH_SOURCE_ISOTROPIC) {
         const u4 w3 = philox10(3u, j, tr.id, tr.event, em.key0, em.key1);
         const float u = u24f(w3.z);
         const ff st = ff_mul(ff_sqrt(two_prod(u, 1.0f - u)), 2.0f);
-        d = {ff_mul(st, ff_from_double(cp)), ff_mul(st, ff_from_double(sp)),
-             ffv(1.0f - 2.0f * u)};
+        d = {ff_mul(st, cp), ff_mul(st, sp), ffv(1.0f - 2.0f * u)};
         return;
     }
     ff3 e1, e2;
     basis_ff(t, e1, e2);
-    const ff r_x = ff_add(ff_mul(e1.x, ff_from_double(cp)), ff_mul(e2.x, ff_from_double(sp)));
-    const ff r_y = ff_add(ff_mul(e1.y, ff_from_double(cp)), ff_mul(e2.y, ff_from_double(sp)));
-    const ff r_z = ff_add(ff_mul(e1.z, ff_from_double(cp)), ff_mul(e2.z, ff_from_double(sp)));
+    const ff r_x = ff_add(ff_mul(e1.x, cp), ff_mul(e2.x, sp));
+    const ff r_y = ff_add(ff_mul(e1.y, cp), ff_mul(e2.y, sp));
+    const ff r_z = ff_add(ff_mul(e1.z, cp), ff_mul(e2.z, sp));
     double cos_t = cs.x, sin_t = cs.y;
     if (em.dispersion) {
         // dispersive radiator: the angle of the photon's own wavelength, FP64,
@@ -991,19 +1018,6 @@ __device__ __forceinline__ void pixel_of_ff(const DevRect &R, ff u, ff v, int &i
     iy = iy < 0 ? 0 : (iy >= R.gy ? R.gy - 1 : iy);
 }
 
-// Sum `val` over the lanes of `peers` (lanes sharing one key) and add it
-// once, from the lowest peer, to *addr.
-__device__ __forceinline__ void peer_add(unsigned peers, double val, double *addr) {
-    double sum = 0.0;
-    unsigned m = peers;
-    while (m) {
-        const int src = __ffs(m) - 1;
-        sum += __shfl_sync(peers, val, src);
-        m &= m - 1;
-    }
-    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(addr, sum);
-}
-
 __device__ __forceinline__ void bin_hit(const SceneView &sc, const TraceParams &P,
                                         uint32_t event, int plane, int ix, int iy) {
     if (P.pixel_counts && event < P.n_hist_events) {
@@ -1022,21 +1036,39 @@ __device__ __forceinline__ void pixel_of(const DevRect &R, double u, double v, i
     iy = iy < 0 ? 0 : (iy >= R.gy ? R.gy - 1 : iy);
 }
 
-// Event sums (hits, sum u, sum v, sum lambda) with one FP64 atomic per
-// (event, plane) group of lanes of the calling converged warp.
+// Event sums (hits, sum u, sum v, sum lambda) of the lanes of a converged
+// warp: for each distinct (event, plane) key among the taking lanes, an FP64
+// butterfly sum over the warp (lanes of other keys add zero), then one FP64
+// atomic per component from the key's first lane; the hit count is the
+// lane count.
 __device__ __forceinline__ void add_event_sums(const SceneView &sc, const TraceParams &P,
                                                bool on, uint32_t event, int plane,
                                                double u, double v, float lam) {
     const bool take = on && P.event_sums && event < P.n_hist_events;
-    const unsigned act = __ballot_sync(0xFFFFFFFFu, take);
-    if (!take) return;
+    unsigned act = __ballot_sync(0xFFFFFFFFu, take);
     const long long key = (long long)event * sc.n_planes + plane;
-    const unsigned peers = __match_any_sync(act, key);
-    double *es = P.event_sums + key * 4;
-    peer_add(peers, 1.0, es + 0);
-    peer_add(peers, u, es + 1);
-    peer_add(peers, v, es + 2);
-    peer_add(peers, (double)lam, es + 3);
+    const int lane = threadIdx.x & 31;
+    while (act) {
+        const int leader = __ffs(act) - 1;
+        const long long k = __shfl_sync(0xFFFFFFFFu, key, leader);
+        const bool mine = take && key == k;
+        const unsigned grp = __ballot_sync(0xFFFFFFFFu, mine);
+        double su = mine ? u : 0.0, sv = mine ? v : 0.0, sl = mine ? (double)lam : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            su += __shfl_xor_sync(0xFFFFFFFFu, su, o);
+            sv += __shfl_xor_sync(0xFFFFFFFFu, sv, o);
+            sl += __shfl_xor_sync(0xFFFFFFFFu, sl, o);
+        }
+        if (lane == leader) {
+            double *es = P.event_sums + k * 4;
+            atomicAdd(es + 0, (double)__popc(grp));
+            atomicAdd(es + 1, su);
+            atomicAdd(es + 2, sv);
+            atomicAdd(es + 3, sl);
+        }
+        act &= ~grp;
+    }
 }
 
 // Efficiencies applied before propagation (Sec. 4.3): the FP32 product,

@@ -89,6 +89,7 @@ class Scene:
     tri_vertices: np.ndarray          # (n, 3, 3) float32
     tri_normals: np.ndarray | None    # (n, 3, 3) float32
     tri_material: np.ndarray          # (n,) int32
+    tri_surface: np.ndarray | None = None   # (n,) int32 surface ids, or None
 
     @property
     def n_triangles(self) -> int:
@@ -114,7 +115,7 @@ class _Builder:
     def __init__(self, name):
         self.name = name
         self.tables, self.materials, self.spheres, self.rects = [], [], [], []
-        self.tris, self.tri_normals, self.tri_mat = [], [], []
+        self.tris, self.tri_normals, self.tri_mat, self.tri_surf = [], [], [], []
         self.any_smooth = False
 
     def table_const(self, value):
@@ -191,6 +192,8 @@ class _Builder:
             normals = np.repeat(g[:, None, :], 3, axis=1)
         self.tri_normals.append(np.asarray(normals, np.float64))
         self.tri_mat.append(np.full(len(verts), material, np.int32))
+        # one surface per call (a mirror segment, a flat mirror, a plate)
+        self.tri_surf.append(np.full(len(verts), len(self.tri_surf), np.int32))
         self.any_smooth |= smooth
 
     def build(self) -> Scene:
@@ -200,15 +203,17 @@ class _Builder:
             tv = f32(np.concatenate(self.tris))
             tn = f32(np.concatenate(self.tri_normals))
             tm = np.concatenate(self.tri_mat).astype(np.int32)
+            ts = np.concatenate(self.tri_surf).astype(np.int32)
         else:
             tv = np.zeros((0, 3, 3), np.float32)
             tn = None
             tm = np.zeros(0, np.int32)
+            ts = np.zeros(0, np.int32)
         return Scene(self.name, arr(self.tables, TABLE_DTYPE),
                      arr(self.materials, MATERIAL_DTYPE),
                      arr(self.spheres, SPHERE_DTYPE),
                      arr(self.rects, RECT_DTYPE), tv,
-                     tn if self.any_smooth else None, tm)
+                     tn if self.any_smooth else None, tm, ts)
 
 
 def _unit(v):

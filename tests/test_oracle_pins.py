@@ -807,3 +807,33 @@ def test_window_total_internal_reflection_fraction(oracle_lib):
         r = math.hypot(out["u"][g] - cx, out["v"][g] - cx)
         assert out["plane"][g] == (0 if up else 1)
         assert abs(r - r_exp) < 1e-9
+
+
+def test_surface_skip_rule(oracle_lib):
+    """A photon leaving a surface (one mirror segment, flat or window face:
+    the triangles of one `triangles` call) is not intersected with that
+    surface again at its next step. A ray starting 1e-4 mm below a flat
+    meshed mirror and leaving it at a grazing angle re-enters a neighbouring
+    facet when only the facet just hit is skipped, and does not when the
+    whole surface is skipped; BVH and brute force agree under the rule."""
+    b = w._Builder("flat")
+    t = b.table_const(0.9)
+    m = b.material(w.MAT_MIRROR, t)
+    b.triangles(w._mesh_rectangle(np.array([-100.0, -100.0, 0.0]), np.array([1.0, 0, 0]),
+                                  np.array([0, 1.0, 0]), 200.0, 200.0, 20, 20),
+                None, m, smooth=False)
+    with_s = b.build()
+    without = w.Scene(**{**with_s.__dict__, "tri_surface": None})
+    n = with_s.n_triangles
+    rng = np.random.default_rng(1)
+    k = rng.integers(0, n, 400)
+    cen = with_s.tri_vertices[k].astype(np.float64).mean(axis=1)
+    o = cen - np.array([0, 0, 1e-4])
+    ang = rng.uniform(0, 2 * np.pi, 400)
+    d = np.stack([np.cos(ang), np.sin(ang), np.full(400, 1e-5)], axis=1)
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    t0, p0 = oracle_lib.Scene(without).raycast(o, d, skip=k, t_min=1e-3)
+    assert (p0 >= 0).sum() > 300          # neighbouring facets are re-hit
+    for bvh in (True, False):
+        t1, p1 = oracle_lib.Scene(with_s).raycast(o, d, skip=k, t_min=1e-3, use_bvh=bvh)
+        assert np.all(p1 == -1)
