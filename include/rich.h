@@ -165,6 +165,13 @@ typedef struct rich_rect {
  * tri_vertices: n_triangles x 3 vertices x 3 floats. tri_normals: same shape,
  * per-vertex unit normals used by RICH_MAT_SMOOTH materials (may be NULL when
  * no material is smooth). tri_material: n_triangles material indices.
+ * tri_surface: n_triangles surface ids (may be NULL: every triangle is a
+ * surface of its own). Triangles sharing an id >= 0 form one surface (a
+ * mirror segment, a flat mirror, a window face); -1 marks a triangle that is
+ * a surface of its own. A photon leaving a surface (after reflecting or
+ * refracting on it, or crossing it from behind) does not intersect that
+ * surface again at its next step; every analytic sphere tile and rectangle
+ * is a surface of its own.
  * Primitive ids: spheres are 0..n_spheres-1, rectangles follow, triangles
  * follow the rectangles (ids used in ties: the lowest id wins). */
 typedef struct rich_geometry_desc {
@@ -180,6 +187,7 @@ typedef struct rich_geometry_desc {
     const float *tri_vertices;
     const float *tri_normals;
     const int32_t *tri_material;
+    const int32_t *tri_surface;
 } rich_geometry_desc;
 
 /* ------------------------------------------------------------------ inputs */

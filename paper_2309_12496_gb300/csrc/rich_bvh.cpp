@@ -5,12 +5,19 @@
 // triangles per leaf), flattened into 64-byte two-wide nodes that carry
 // both children's boxes, in breadth-first order so the top levels of the
 // tree are contiguous. Triangles are re-ordered into leaf order.
+//
+// Triangles that share a surface id (one mirror segment, flat mirror or
+// window face) get a subtree of their own: each surface is built
+// separately, the triangles without a surface together, and a top level
+// joins the subtrees by the same heuristic over their boxes. A photon
+// leaving a surface then skips that surface's subtree at its root.
 #include "rich_bvh.h"
 
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <limits>
 #include <numeric>
 
@@ -56,11 +63,12 @@ struct Node {
 };
 
 struct Builder {
-    const float *v;
-    std::vector<Box> tri_box;
-    std::vector<float> cen;     // 3 per triangle
+    const std::vector<Box> &tri_box;
+    const std::vector<float> &cen;   // 3 per triangle
     std::vector<int> order;
     std::vector<Node> nodes;
+
+    Builder(const std::vector<Box> &tb, const std::vector<float> &c) : tri_box(tb), cen(c) {}
 
     int build(int first, int count) {
         Node nd;
@@ -156,9 +164,59 @@ void put_box(DevNode &d, int slot, const Box &b) {
     }
 }
 
+// Top level over subtree roots `items` (indices into `all`), each weighted
+// by its triangle count: at every level the split (along the axis and at
+// the position over the sorted centroids) that minimises
+// area(left) * n(left) + area(right) * n(right).
+int build_top(std::vector<Node> &all, std::vector<int> &items, const std::vector<int> &weight,
+              int first, int count) {
+    if (count == 1) return items[first];
+    float best = std::numeric_limits<float>::infinity();
+    int best_axis = 0, best_k = count / 2;
+    for (int axis = 0; axis < 3; ++axis) {
+        std::sort(items.begin() + first, items.begin() + first + count, [&](int a, int b) {
+            return all[a].box.lo[axis] + all[a].box.hi[axis] <
+                   all[b].box.lo[axis] + all[b].box.hi[axis];
+        });
+        std::vector<float> left_cost(count);
+        Box acc;
+        int n = 0;
+        for (int k = 0; k < count - 1; ++k) {
+            acc.grow(all[items[first + k]].box);
+            n += weight[items[first + k]];
+            left_cost[k] = acc.area() * n;
+        }
+        Box racc;
+        int nr = 0;
+        for (int k = count - 1; k >= 1; --k) {
+            racc.grow(all[items[first + k]].box);
+            nr += weight[items[first + k]];
+            const float c = left_cost[k - 1] + racc.area() * nr;
+            if (c < best) {
+                best = c;
+                best_axis = axis;
+                best_k = k;
+            }
+        }
+    }
+    std::sort(items.begin() + first, items.begin() + first + count, [&](int a, int b) {
+        return all[a].box.lo[best_axis] + all[a].box.hi[best_axis] <
+               all[b].box.lo[best_axis] + all[b].box.hi[best_axis];
+    });
+    Node nd;
+    for (int k = first; k < first + count; ++k) nd.box.grow(all[items[k]].box);
+    const int id = (int)all.size();
+    all.push_back(nd);
+    const int l = build_top(all, items, weight, first, best_k);
+    const int r = build_top(all, items, weight, first + best_k, count - best_k);
+    all[id].left = l;
+    all[id].right = r;
+    return id;
+}
+
 }  // namespace
 
-bool build_bvh(const float *vertices, int64_t n_tris, BvhResult &out,
+bool build_bvh(const float *vertices, const int32_t *surface, int64_t n_tris, BvhResult &out,
                std::string &err) {
     out = BvhResult();
     if (n_tris <= 0) return true;
@@ -166,10 +224,8 @@ bool build_bvh(const float *vertices, int64_t n_tris, BvhResult &out,
         err = "too many triangles for the BVH leaf encoding";
         return false;
     }
-    Builder b;
-    b.v = vertices;
-    b.tri_box.resize((size_t)n_tris);
-    b.cen.resize(3 * (size_t)n_tris);
+    std::vector<Box> tri_box((size_t)n_tris);
+    std::vector<float> cen(3 * (size_t)n_tris);
     for (int64_t i = 0; i < n_tris; ++i) {
         const float *t = vertices + 9 * i;
         Box bx;
@@ -181,51 +237,99 @@ bool build_bvh(const float *vertices, int64_t n_tris, BvhResult &out,
                 err = "non-finite triangle vertex";
                 return false;
             }
-            b.cen[3 * i + k] = (t[k] + t[3 + k] + t[6 + k]) * (1.0f / 3.0f);
+            cen[3 * i + k] = (t[k] + t[3 + k] + t[6 + k]) * (1.0f / 3.0f);
         }
-        b.tri_box[i] = bx;
+        tri_box[i] = bx;
     }
-    b.order.resize((size_t)n_tris);
-    std::iota(b.order.begin(), b.order.end(), 0);
-    b.nodes.reserve(2 * (size_t)n_tris);
-    const int root = b.build(0, (int)n_tris);
+    // ---- groups: one per surface id, one for the triangles without one
+    std::map<int32_t, std::vector<int>> groups;
+    for (int64_t i = 0; i < n_tris; ++i) {
+        const int32_t sid = surface ? surface[i] : -1;
+        if (sid < -1) {
+            err = "triangle surface id below -1";
+            return false;
+        }
+        groups[sid].push_back((int)i);
+    }
+    // ---- build each group, then join the subtrees
+    std::vector<Node> all;
+    std::vector<int> order_all;
+    std::vector<int> items, weight;
+    std::vector<std::pair<int32_t, int>> group_root;   // (surface id, root in all)
+    all.reserve(2 * (size_t)n_tris + 2 * groups.size());
+    for (auto &[sid, tris] : groups) {
+        Builder b(tri_box, cen);
+        b.order = tris;
+        b.nodes.reserve(2 * tris.size());
+        const int root = b.build(0, (int)tris.size());
+        const int off = (int)all.size(), base = (int)order_all.size();
+        for (Node n : b.nodes) {
+            if (n.count > 0) {
+                n.first += base;
+            } else {
+                n.left += off;
+                n.right += off;
+            }
+            all.push_back(n);
+        }
+        order_all.insert(order_all.end(), b.order.begin(), b.order.end());
+        items.push_back(root + off);
+        group_root.push_back({sid, root + off});
+    }
+    weight.assign(all.size() + groups.size() + 1, 0);
+    for (size_t g = 0; g < items.size(); ++g) {
+        const int32_t sid = group_root[g].first;
+        weight[items[g]] = (int)groups[sid].size();
+    }
+    std::vector<int> top_items = items;
+    const int root = build_top(all, top_items, weight, 0, (int)top_items.size());
 
-    out.leaf_order = b.order;
+    out.leaf_order = order_all;
     auto leaf_code = [&](const Node &n) { return ~((n.first << 3) | (n.count - 1)); };
-    // breadth-first flattening of the inner nodes
-    if (b.nodes[root].count > 0) {
+    std::vector<int> dev_index(all.size(), -1);
+    if (all[root].count > 0) {
+        // the whole tree is one leaf
         DevNode d;
         std::memset(&d, 0, sizeof d);
-        put_box(d, 0, b.nodes[root].box);
-        put_box(d, 1, b.nodes[root].box);
-        d.child0 = d.child1 = leaf_code(b.nodes[root]);
+        put_box(d, 0, all[root].box);
+        put_box(d, 1, all[root].box);
+        d.child0 = d.child1 = leaf_code(all[root]);
         out.nodes.push_back(d);
         out.depth = 1;
-        return true;
+    } else {
+        // breadth-first flattening of the inner nodes
+        std::deque<std::pair<int, int>> q;   // (node, depth)
+        q.push_back({root, 1});
+        std::vector<int> bfs;
+        while (!q.empty()) {
+            auto [n, depth] = q.front();
+            q.pop_front();
+            dev_index[n] = (int)bfs.size();
+            bfs.push_back(n);
+            out.depth = std::max(out.depth, depth);
+            for (int c : {all[n].left, all[n].right})
+                if (all[c].count == 0) q.push_back({c, depth + 1});
+        }
+        out.nodes.resize(bfs.size());
+        for (size_t i = 0; i < bfs.size(); ++i) {
+            const Node &n = all[bfs[i]];
+            DevNode &d = out.nodes[i];
+            std::memset(&d, 0, sizeof d);
+            const Node &l = all[n.left], &r = all[n.right];
+            put_box(d, 0, l.box);
+            put_box(d, 1, r.box);
+            d.child0 = l.count > 0 ? leaf_code(l) : dev_index[n.left];
+            d.child1 = r.count > 0 ? leaf_code(r) : dev_index[n.right];
+        }
     }
-    std::vector<int> dev_index(b.nodes.size(), -1);
-    std::deque<std::pair<int, int>> q;   // (build node, depth)
-    q.push_back({root, 1});
-    std::vector<int> bfs;
-    while (!q.empty()) {
-        auto [n, depth] = q.front();
-        q.pop_front();
-        dev_index[n] = (int)bfs.size();
-        bfs.push_back(n);
-        out.depth = std::max(out.depth, depth);
-        for (int c : {b.nodes[n].left, b.nodes[n].right})
-            if (b.nodes[c].count == 0) q.push_back({c, depth + 1});
-    }
-    out.nodes.resize(bfs.size());
-    for (size_t i = 0; i < bfs.size(); ++i) {
-        const Node &n = b.nodes[bfs[i]];
-        DevNode &d = out.nodes[i];
-        std::memset(&d, 0, sizeof d);
-        const Node &l = b.nodes[n.left], &r = b.nodes[n.right];
-        put_box(d, 0, l.box);
-        put_box(d, 1, r.box);
-        d.child0 = l.count > 0 ? leaf_code(l) : dev_index[n.left];
-        d.child1 = r.count > 0 ? leaf_code(r) : dev_index[n.right];
+    // ---- the subtree reference of every triangle's surface
+    out.surface_ref.assign((size_t)n_tris, kNoSurface);
+    std::vector<int> pos_of((size_t)n_tris);
+    for (size_t k = 0; k < order_all.size(); ++k) pos_of[order_all[k]] = (int)k;
+    for (auto &[sid, gr] : group_root) {
+        if (sid < 0) continue;
+        const int ref = all[gr].count > 0 ? leaf_code(all[gr]) : dev_index[gr];
+        for (int t : groups[sid]) out.surface_ref[pos_of[t]] = ref;
     }
     return true;
 }

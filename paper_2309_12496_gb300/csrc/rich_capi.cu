@@ -547,7 +547,7 @@ RICH_API rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc 
     for (int64_t i = 0; i < nt; ++i)
         if (g->tri_material[i] < 0 || g->tri_material[i] >= g->n_materials)
             return bad("triangle material index");
-    if (!build_bvh(g->tri_vertices, nt, bvh, berr)) return bad(berr);
+    if (!build_bvh(g->tri_vertices, g->tri_surface, nt, bvh, berr)) return bad(berr);
     if (bvh.depth >= RICH_BVH_STACK) return bad("BVH deeper than the traversal stack");
     // structural check: children point strictly forward (traversal ends),
     // leaf ranges stay inside the triangle array
@@ -574,7 +574,7 @@ RICH_API rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc 
         T.v2x = v[6]; T.v2y = v[7]; T.v2z = v[8];
         T.prim = prim_base + src;
         T.material = g->tri_material[src];
-        T.pad = 0;
+        T.pad = bvh.surface_ref[(size_t)k];   // subtree of the triangle's surface
         if (any_smooth) std::memcpy(&normals[9 * (size_t)k], g->tri_normals + 9 * (int64_t)src, 36);
     }
     std::vector<DevTable> tables(g->n_tables);

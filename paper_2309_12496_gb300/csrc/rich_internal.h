@@ -65,11 +65,14 @@ struct DevRectD {            // FP64 copy for the refinement replay, 96 B
     double ox, oy, oz, ux, uy, uz, vx, vy, vz, nx, ny, nz;
 };
 
-struct alignas(16) DevTri {  // 48 B: v0 | v1 | v2 | prim, material
+struct alignas(16) DevTri {  // 48 B: v0 | v1 | v2 | prim, material, surface
     float v0x, v0y, v0z, v1x;
     float v1y, v1z, v2x, v2y;
     float v2z;
-    int32_t prim, material, pad;
+    int32_t prim, material;
+    int32_t pad;              // BVH reference (node index or leaf code) of the
+                              // subtree holding exactly this triangle's
+                              // surface, or 0x7FFFFFFF when it has none
 };
 
 struct alignas(16) DevNode { // 64 B: boxes of both children + child refs

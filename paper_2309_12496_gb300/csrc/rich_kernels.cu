@@ -398,6 +398,7 @@ struct Photon {
     uint32_t wr0, wr1, wr2, wr3;
     int skip, n_refl, steps;
     int n_turn;            // direction changes: reflections and refractions
+    int skip_ref;          // BVH subtree of the surface just left, or kNoSurf
 };
 
 // Wavelength from a binned emission spectrum (CDF table): the bin k with
@@ -704,7 +705,7 @@ __device__ __forceinline__ DevTri load_tri(const DevTri *p) {
     t.v2z = c.x;
     t.prim = __float_as_int(c.y);
     t.material = __float_as_int(c.z);
-    t.pad = 0;
+    t.pad = __float_as_int(c.w);
     return t;
 }
 
@@ -768,15 +769,20 @@ __device__ __forceinline__ void load_node(const SceneView &sc, const DevNode *sn
     }
 }
 
+constexpr int kNoSurf = 0x7FFFFFFF;   // no surface subtree to skip
+
 // Nearest triangle along the ray: two-wide BVH in the "while-while" order
 // of Aila and Laine (HPG 2009): descend inner nodes (near child first, the
 // far one stacked with its entry distance) until a leaf is found, postpone
 // it, and intersect postponed leaves together once every active lane holds
 // one, which keeps the lanes of a warp on the same kind of work. The top
-// levels of the tree are read from shared memory.
+// levels of the tree are read from shared memory. The subtree `skip_ref` (the
+// surface the photon just left) is never entered.
 __device__ void nearest_bvh(const SceneView &sc, const DevNode *snodes, int n_snodes,
-                            f3 o, f3 d, int skip, float t_min, Best &b, Counters *ctr) {
+                            f3 o, f3 d, int skip, int skip_ref, float t_min, Best &b,
+                            Counters *ctr) {
     constexpr int kEmpty = INT_MIN;
+    if (skip_ref == 0) return;            // the whole tree is that surface
     const Ray r = make_ray(o, d);
     int stack_ref[RICH_BVH_STACK];
     float stack_t[RICH_BVH_STACK];
@@ -795,8 +801,10 @@ __device__ void nearest_bvh(const SceneView &sc, const DevNode *snodes, int n_sn
             int4 ch;
             load_node(sc, snodes, n_snodes, ref, na, nb, nc, ch);
             float tn0, tn1;
-            const bool h0 = slab(r, na.x, na.y, na.z, na.w, nb.x, nb.y, b.t, tn0);
-            const bool h1 = slab(r, nb.z, nb.w, nc.x, nc.y, nc.z, nc.w, b.t, tn1);
+            const bool h0 = slab(r, na.x, na.y, na.z, na.w, nb.x, nb.y, b.t, tn0) &&
+                            ch.x != skip_ref;
+            const bool h1 = slab(r, nb.z, nb.w, nc.x, nc.y, nc.z, nc.w, b.t, tn1) &&
+                            ch.y != skip_ref;
             if (h0 && h1) {
                 const bool first0 = tn0 <= tn1;
                 if (sp < RICH_BVH_STACK) {
@@ -1244,6 +1252,7 @@ k_trace(TraceArgs A) {
                     const uint64_t g = pool_next + (uint64_t)rank;
                     ph.g = g;
                     ph.skip = -1;
+                    ph.skip_ref = kNoSurf;
                     ph.n_refl = 0;
                     ph.n_turn = 0;
                     ph.steps = 0;
@@ -1319,7 +1328,9 @@ k_trace(TraceArgs A) {
             b.b0 = b.b1 = b.b2 = 0.0f;
             if (S.n_groups) nearest_tiles(S, ph.o, ph.d, ph.skip, P.t_min, b);
             nearest_rects(S, ph.o, ph.d, ph.skip, P.t_min, b);
-            if (has_tri) nearest_bvh(sc, snodes, n_snodes, ph.o, ph.d, ph.skip, P.t_min, b, A.ctr);
+            if (has_tri)
+                nearest_bvh(sc, snodes, n_snodes, ph.o, ph.d, ph.skip, ph.skip_ref, P.t_min, b,
+                            A.ctr);
             if (b.prim < 0) {
                 fate = RICH_FATE_ESCAPED;
             } else {
@@ -1327,6 +1338,7 @@ k_trace(TraceArgs A) {
                 int mat_id;
                 bool front;
                 f3 n_sh, n_geo;
+                int hit_ref = kNoSurf;    // surface subtree of a hit triangle
                 if (b.kind == 0) {
                     const DevTile &T = S.tiles[b.idx];
                     const DevSphereGroup &G = S.groups[T.group];
@@ -1354,6 +1366,7 @@ k_trace(TraceArgs A) {
                     front = dot3(ph.d, ng) < 0.0f;
                     n_geo = normalize3(ng);
                     mat_id = T.material;
+                    hit_ref = T.pad;
                     const DevMaterial &M0 = S.materials[mat_id];
                     if ((M0.flags & RICH_MAT_SMOOTH) && sc.tri_normals) {
                         const float *N3 = sc.tri_normals + 9 * (int64_t)b.idx;
@@ -1388,6 +1401,7 @@ k_trace(TraceArgs A) {
                             ph.n_turn += 1;
                             ph.o = p;
                             ph.skip = b.prim;
+                            ph.skip_ref = hit_ref;
                         }
                     }
                 } else if (M.kind == RICH_MAT_DIELECTRIC) {
@@ -1408,11 +1422,13 @@ k_trace(TraceArgs A) {
                         ph.n_turn += 1;
                         ph.o = p;
                         ph.skip = b.prim;
+                            ph.skip_ref = hit_ref;
                     }
                 } else {  // detector
                     if (!front) {
                         ph.o = p;
                         ph.skip = b.prim;
+                            ph.skip_ref = hit_ref;
                     } else {
                         const bool pass =
                             P.n_prefilter || u24f(ph.w_qe) < table_eval(S.tables[M.table], ph.lam);

@@ -56,7 +56,7 @@ class GeometryDesc(C.Structure):
                 ("tables", C.c_void_p), ("materials", C.c_void_p),
                 ("spheres", C.c_void_p), ("rects", C.c_void_p),
                 ("tri_vertices", C.c_void_p), ("tri_normals", C.c_void_p),
-                ("tri_material", C.c_void_p)]
+                ("tri_material", C.c_void_p), ("tri_surface", C.c_void_p)]
 
 
 class TracksDesc(C.Structure):
@@ -343,14 +343,16 @@ class Context:
                 np.ascontiguousarray(scene.tri_vertices, np.float32),
                 None if scene.tri_normals is None else
                 np.ascontiguousarray(scene.tri_normals, np.float32),
-                np.ascontiguousarray(scene.tri_material, np.int32)]
+                np.ascontiguousarray(scene.tri_material, np.int32),
+                None if scene.tri_surface is None else
+                np.ascontiguousarray(scene.tri_surface, np.int32)]
         p = lambda a: None if a is None or a.size == 0 else a.ctypes.data
         d = GeometryDesc(n_tables=len(keep[0]), n_materials=len(keep[1]),
                          n_spheres=len(keep[2]), n_rects=len(keep[3]),
                          n_triangles=scene.n_triangles, tables=p(keep[0]),
                          materials=p(keep[1]), spheres=p(keep[2]), rects=p(keep[3]),
                          tri_vertices=p(keep[4]), tri_normals=p(keep[5]),
-                         tri_material=p(keep[6]))
+                         tri_material=p(keep[6]), tri_surface=p(keep[7]))
         _check(self.handle, load().rich_init_geometry(self.handle, C.byref(d)))
         self.scene = scene
 

@@ -49,7 +49,7 @@ def test_struct_layouts_match_header():
     """The ctypes mirrors and numpy record layouts have the header's sizes."""
     from paper_2309_12496_gb300 import rich
     from paper_2309_12496_gb300 import workloads as W
-    assert C.sizeof(rich.GeometryDesc) == 4 * 4 + 8 + 7 * 8
+    assert C.sizeof(rich.GeometryDesc) == 4 * 4 + 8 + 8 * 8
     assert C.sizeof(rich.TracksDesc) == 8 + 12 * 8
     assert C.sizeof(rich.PhotonsDesc) == 16 + 10 * 8
     assert C.sizeof(rich.TraceOpts) == 8 + 15 * 4 + 4      # + tail padding
