@@ -1528,17 +1528,20 @@ k_trace(TraceArgs A) {
     }
 }
 
-// FP64 refinement pass: one thread per stored hit (converged warps).
+// Refinement pass: one thread per stored hit (converged warps). Hits are
+// taken in chunks of 32, chunk c by the warp with global index c over a
+// warp numbering that runs across the blocks first, so the chunks spread
+// evenly over the SMs whatever the hit count.
 template <bool EXT>
 __global__ void __launch_bounds__(256)
 k_refine(SceneView sc, EmitView em, ExtView ext, TraceParams P, Counters *ctr) {
     const uint64_t n_hits = ctr->hits < P.hit_capacity ? ctr->hits : P.hit_capacity;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t start = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    // uniform trip count so every lane takes part in the warp collectives
-    const uint64_t trips = (n_hits + stride - 1) / stride;
-    for (uint64_t it = 0; it < trips; ++it) {
-        const uint64_t i = start + it * stride;
+    const uint64_t n_chunks = (n_hits + 31) / 32;
+    const uint64_t n_warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    const int lane = threadIdx.x & 31;
+    for (uint64_t c = blockIdx.x + (uint64_t)gridDim.x * (threadIdx.x >> 5); c < n_chunks;
+         c += n_warps) {
+        const uint64_t i = c * 32 + (uint64_t)lane;
         const bool on = i < n_hits;
         double u = 0.0, v = 0.0;
         int plane = 0;
@@ -1579,8 +1582,9 @@ cudaError_t launch_refine(const SceneView &sc, const EmitView *em, const ExtView
                           const TraceParams &p, Counters *counters, int n_sm,
                           cudaStream_t s) {
     if (p.hit_capacity == 0) return cudaSuccess;
+    // every block resident at once (two 256-thread blocks per SM)
     uint64_t blocks = (p.hit_capacity + 255) / 256;
-    const uint64_t cap = (uint64_t)n_sm * 8;
+    const uint64_t cap = (uint64_t)n_sm * 2;
     if (blocks > cap) blocks = cap;
     if (ext)
         k_refine<true><<<(unsigned)blocks, 256, 0, s>>>(sc, em ? *em : EmitView{}, *ext, p,
