@@ -754,19 +754,13 @@ __device__ __forceinline__ void leaf_tris(const SceneView &sc, const Ray &r,
 __device__ __forceinline__ void load_node(const SceneView &sc, const DevNode *snodes,
                                           int n_snodes, int ref, float4 &a, float4 &b,
                                           float4 &c, int4 &ch) {
-    if (ref < n_snodes) {
-        const float4 *q = reinterpret_cast<const float4 *>(snodes + ref);
-        a = q[0];
-        b = q[1];
-        c = q[2];
-        ch = *reinterpret_cast<const int4 *>(q + 3);
-    } else {
-        const float4 *q = reinterpret_cast<const float4 *>(sc.nodes + ref);
-        a = __ldg(q);
-        b = __ldg(q + 1);
-        c = __ldg(q + 2);
-        ch = __ldg(reinterpret_cast<const int4 *>(q + 3));
-    }
+    // one generic load path for both (no divergent branch between shared and
+    // global memory)
+    const float4 *q = reinterpret_cast<const float4 *>(ref < n_snodes ? snodes + ref : sc.nodes + ref);
+    a = q[0];
+    b = q[1];
+    c = q[2];
+    ch = *reinterpret_cast<const int4 *>(q + 3);
 }
 
 constexpr int kNoSurf = 0x7FFFFFFF;   // no surface subtree to skip
