@@ -1038,14 +1038,49 @@ __device__ __forceinline__ void pixel_of(const DevRect &R, double u, double v, i
     iy = iy < 0 ? 0 : (iy >= R.gy ? R.gy - 1 : iy);
 }
 
+constexpr int kSmemKeys = 64;   // event-sum keys a block table holds
+
+// FP32 pixel of an FP32 plane position (the FP32 trace's own binning):
+// floor(u / pitch), clamped to the grid.
+__device__ __forceinline__ void pixel_of_f32(const DevRect &R, float u, float v, int &ix,
+                                             int &iy) {
+    ix = (int)floorf(__fdiv_rn(u, R.pitch));
+    iy = (int)floorf(__fdiv_rn(v, R.pitch));
+    ix = ix < 0 ? 0 : (ix >= R.gx ? R.gx - 1 : ix);
+    iy = iy < 0 ? 0 : (iy >= R.gy ? R.gy - 1 : iy);
+}
+
+// The block's shared event-sum table: used when the call's keys fit.
+__device__ __forceinline__ bool es_table_on(const SceneView &sc, const TraceParams &P) {
+    const int64_t n_keys = P.event_sums ? (int64_t)P.n_hist_events * sc.n_planes : 0;
+    return n_keys > 0 && n_keys <= kSmemKeys;
+}
+__device__ __forceinline__ void es_table_flush(const SceneView &sc, const TraceParams &P,
+                                               const double *s_es) {
+    const int n = (int)P.n_hist_events * sc.n_planes * 4;
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        if (s_es[i] != 0.0) atomicAdd(P.event_sums + i, s_es[i]);
+}
+
+__device__ __forceinline__ ff shfl_xor_ff(ff a, int o) {
+    return {__shfl_xor_sync(0xFFFFFFFFu, a.hi, o), __shfl_xor_sync(0xFFFFFFFFu, a.lo, o)};
+}
+
 // Event sums (hits, sum u, sum v, sum lambda) of the lanes of a converged
-// warp: for each distinct (event, plane) key among the taking lanes, an FP64
-// butterfly sum over the warp (lanes of other keys add zero), then one FP64
-// atomic per component from the key's first lane; the hit count is the
-// lane count.
+// warp: for each distinct (event, plane) key among the taking lanes, a
+// butterfly sum over the warp in double-word arithmetic (lanes of other keys
+// add zero; ~1e-14 relative), then one FP64 atomic per component from the
+// key's first lane, so the accumulation over warps is FP64; the hit count
+// is the lane count. With few keys (one event, a few planes) the warps of a
+// block accumulate in shared memory first, which keeps thousands of warps
+// from serialising on the same few global addresses.
+// s_es: the block's shared-memory table of the sums (all keys of the call,
+// flushed to global memory when the block ends) or null for direct global
+// atomics.
+
 __device__ __forceinline__ void add_event_sums(const SceneView &sc, const TraceParams &P,
-                                               bool on, uint32_t event, int plane,
-                                               double u, double v, float lam) {
+                                               bool on, uint32_t event, int plane, ff u,
+                                               ff v, float lam, double *s_es) {
     const bool take = on && P.event_sums && event < P.n_hist_events;
     unsigned act = __ballot_sync(0xFFFFFFFFu, take);
     const long long key = (long long)event * sc.n_planes + plane;
@@ -1055,19 +1090,19 @@ __device__ __forceinline__ void add_event_sums(const SceneView &sc, const TraceP
         const long long k = __shfl_sync(0xFFFFFFFFu, key, leader);
         const bool mine = take && key == k;
         const unsigned grp = __ballot_sync(0xFFFFFFFFu, mine);
-        double su = mine ? u : 0.0, sv = mine ? v : 0.0, sl = mine ? (double)lam : 0.0;
+        ff su = mine ? u : ffv(0.0f), sv = mine ? v : ffv(0.0f), sl = ffv(mine ? lam : 0.0f);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            su += __shfl_xor_sync(0xFFFFFFFFu, su, o);
-            sv += __shfl_xor_sync(0xFFFFFFFFu, sv, o);
-            sl += __shfl_xor_sync(0xFFFFFFFFu, sl, o);
+            su = ff_add(su, shfl_xor_ff(su, o));
+            sv = ff_add(sv, shfl_xor_ff(sv, o));
+            sl = ff_add(sl, shfl_xor_ff(sl, o));
         }
         if (lane == leader) {
-            double *es = P.event_sums + k * 4;
+            double *es = (s_es ? s_es : P.event_sums) + k * 4;
             atomicAdd(es + 0, (double)__popc(grp));
-            atomicAdd(es + 1, su);
-            atomicAdd(es + 2, sv);
-            atomicAdd(es + 3, sl);
+            atomicAdd(es + 1, ff_to_double(su));
+            atomicAdd(es + 2, ff_to_double(sv));
+            atomicAdd(es + 3, ff_to_double(sl));
         }
         act &= ~grp;
     }
@@ -1182,6 +1217,9 @@ k_trace(TraceArgs A) {
     }
     __shared__ unsigned long long s_fate[RICH_N_FATES];
     __shared__ unsigned long long s_hits;
+    __shared__ double s_es_tab[kSmemKeys * 4];
+    double *const s_es = es_table_on(sc, A.p) ? s_es_tab : nullptr;
+    for (int i = threadIdx.x; i < kSmemKeys * 4; i += blockDim.x) s_es_tab[i] = 0.0;
     if (threadIdx.x < RICH_N_FATES) s_fate[threadIdx.x] = 0;
     if (threadIdx.x == 0) s_hits = 0;
     __syncthreads();
@@ -1449,7 +1487,7 @@ k_trace(TraceArgs A) {
         const bool det = fate == RICH_FATE_DETECTED;
         const unsigned dm = __ballot_sync(kFull, det);
         bool binned_here = false;
-        double hu = 0.0, hv = 0.0;
+        float hu = 0.0f, hv = 0.0f;
         int hplane = 0;
         if (dm) {
             unsigned long long base = 0;
@@ -1467,7 +1505,7 @@ k_trace(TraceArgs A) {
                 // by the refinement pass; the rest here
                 binned_here = !(REFINE && stored);
                 int ix = 0, iy = 0;
-                if (binned_here) pixel_of(R, hu, hv, ix, iy);
+                if (binned_here) pixel_of_f32(R, hu, hv, ix, iy);
                 if (stored) {
                     rich_hit h;
                     h.event = ph.event;
@@ -1496,7 +1534,7 @@ k_trace(TraceArgs A) {
                 if (binned_here) bin_hit(sc, P, ph.event, hplane, ix, iy);
             }
         }
-        add_event_sums(sc, P, binned_here, ph.event, hplane, hu, hv, ph.lam);
+        add_event_sums(sc, P, binned_here, ph.event, hplane, ffv(hu), ffv(hv), ph.lam, s_es);
         if (fate != 0) {
             if (P.fate) P.fate[ph.g] = (uint8_t)fate;
             atomicAdd(&s_fate[fate], 1ull);
@@ -1506,6 +1544,7 @@ k_trace(TraceArgs A) {
     __syncthreads();
     if (threadIdx.x < RICH_N_FATES && s_fate[threadIdx.x])
         atomicAdd(&A.ctr->fate[threadIdx.x], s_fate[threadIdx.x]);
+    if (s_es) es_table_flush(sc, P, s_es);
     if (n_snodes_req > 0 && n_snodes == 0) {
         // the copy had not completed: give it a second bounded wait so the
         // block does not retire with a transfer into its shared memory
@@ -1531,13 +1570,17 @@ __global__ void __launch_bounds__(256)
 k_refine(SceneView sc, EmitView em, ExtView ext, TraceParams P, Counters *ctr) {
     const uint64_t n_hits = ctr->hits < P.hit_capacity ? ctr->hits : P.hit_capacity;
     const uint64_t n_chunks = (n_hits + 31) / 32;
+    __shared__ double s_es_tab[kSmemKeys * 4];
+    double *const s_es = es_table_on(sc, P) ? s_es_tab : nullptr;
+    for (int i = threadIdx.x; i < kSmemKeys * 4; i += blockDim.x) s_es_tab[i] = 0.0;
+    __syncthreads();
     const uint64_t n_warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     const int lane = threadIdx.x & 31;
     for (uint64_t c = blockIdx.x + (uint64_t)gridDim.x * (threadIdx.x >> 5); c < n_chunks;
          c += n_warps) {
         const uint64_t i = c * 32 + (uint64_t)lane;
         const bool on = i < n_hits;
-        double u = 0.0, v = 0.0;
+        ff uf = ffv(0.0f), vf = ffv(0.0f);
         int plane = 0;
         uint32_t event = 0;
         float lam = 0.0f;
@@ -1552,14 +1595,11 @@ k_refine(SceneView sc, EmitView em, ExtView ext, TraceParams P, Counters *ctr) {
             } else {
                 emit_ff(em.tracks[rr.index], em.cos_sin[rr.index], h.photon, h.lambda, em, o, d);
             }
-            ff uf, vf;
             replay_ff(sc, o, d, rr, h.lambda, uf, vf);
             int ix, iy;
             pixel_of_ff(sc.rects[rr.det_rect], uf, vf, ix, iy);
-            u = ff_to_double(uf);
-            v = ff_to_double(vf);
-            h.u = u;
-            h.v = v;
+            h.u = ff_to_double(uf);
+            h.v = ff_to_double(vf);
             h.ix = (uint16_t)ix;
             h.iy = (uint16_t)iy;
             P.hits[i] = h;
@@ -1568,8 +1608,10 @@ k_refine(SceneView sc, EmitView em, ExtView ext, TraceParams P, Counters *ctr) {
             lam = h.lambda;
             bin_hit(sc, P, event, plane, ix, iy);
         }
-        add_event_sums(sc, P, on, event, plane, u, v, lam);
+        add_event_sums(sc, P, on, event, plane, uf, vf, lam, s_es);
     }
+    __syncthreads();
+    if (s_es) es_table_flush(sc, P, s_es);
 }
 
 cudaError_t launch_refine(const SceneView &sc, const EmitView *em, const ExtView *ext,
