@@ -39,8 +39,13 @@ def _headers():
 
 
 def _flags(extra=()):
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-I", INCLUDE, "-I", CSRC,
-                   "-Xcompiler", "-fPIC,-fvisibility=hidden", *extra]
+    # Plain FP32 `/` and sqrtf compile to the hardware approximations (a few
+    # ulp): they only serve geometry, whose FP32 error budget they fit. Every
+    # FP32 operation that decides an integer (a wavelength, a table bin, an
+    # accept/reject) is written with the IEEE-rounded intrinsics (__fdiv_rn,
+    # __fmul_rn, ...), which these flags do not touch.
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-prec-div=false", "-prec-sqrt=false",
+                   "-I", INCLUDE, "-I", CSRC, "-Xcompiler", "-fPIC,-fvisibility=hidden", *extra]
 
 
 def _stale(obj, src):

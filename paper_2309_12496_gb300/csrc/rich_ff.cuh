@@ -83,28 +83,46 @@ __device__ __forceinline__ ff ff_mul(ff x, ff y) {
     return fast_two_sum(c.hi, cl);
 }
 
-// DW / DW: FP32 quotient of the leading parts, then one correction from the
-// remainder x - q y evaluated with error-free products.
+// Hardware approximations (a few ulp) of 1/x and 1/sqrt(x): the
+// double-word algorithms below start from them and correct the result from
+// an error-free remainder, which removes their error to second order.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float r;
+    asm("rsqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// DW / DW: FP32 quotient of the leading parts (from an approximate
+// reciprocal), then one correction from the remainder x - q y evaluated with
+// error-free products: relative error ~2^-44.
 __device__ __forceinline__ ff ff_div(ff x, ff y) {
-    const float th = __fdiv_rn(x.hi, y.hi);
+    const float ry = rcp_approx(y.hi);
+    const float th = __fmul_rn(x.hi, ry);
     const ff r = ff_mul(y, th);
     const ff p = two_sum(x.hi, -r.hi);
     const float dl = __fadd_rn(__fsub_rn(p.lo, r.lo), x.lo);
     const float d = __fadd_rn(p.hi, dl);
-    return fast_two_sum(th, __fdiv_rn(d, y.hi));
+    return fast_two_sum(th, __fmul_rn(d, ry));
 }
 
+// sqrt of a DW: s ~ x r with r ~ 1/sqrt(x), then s + (x - s^2) r / 2.
 __device__ __forceinline__ ff ff_sqrt(ff x) {
     if (!(x.hi > 0.0f)) return {0.0f, 0.0f};
-    const float s = __fsqrt_rn(x.hi);
+    const float r = rsqrt_approx(x.hi);
+    const float s = __fmul_rn(x.hi, r);
     const ff s2 = two_prod(s, s);
     const float e = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, s2.hi), s2.lo), x.lo);
-    return fast_two_sum(s, __fdiv_rn(e, __fmul_rn(2.0f, s)));
+    return fast_two_sum(s, __fmul_rn(e, __fmul_rn(0.5f, r)));
 }
 
-// 1 / sqrt(x), x > 0
+// 1 / sqrt(x), x > 0: one Newton step in double-word from the approximation
 __device__ __forceinline__ ff ff_rsqrt(ff x) {
-    const float r = __frsqrt_rn(x.hi);
+    const float r = rsqrt_approx(x.hi);
     const ff r2 = two_prod(r, r);
     const ff m = ff_mul(x, r2);                 // x r^2 = 1 - e
     const float e = __fsub_rn(__fsub_rn(1.0f, m.hi), m.lo);
