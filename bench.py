@@ -300,7 +300,7 @@ def main():
             "clocks": clk,
         }
     if not args.no_extras:
-        e2e = run_e2e(ctx, tracks, dev, prec, args, scene)
+        e2e = run_e2e(ctx, tracks, dev, prec, args, scene, knobs)
         if line is not None:
             line["e2e"] = e2e
             line["batched"] = run_batched(dev, prec, rank)
@@ -513,36 +513,31 @@ def run_adjoint(dev, rank):
             "note": "emit + forward trace + adjoint replay + FP64 reductions; synchronous"}
 
 
-def run_e2e(ctx, tracks, dev, prec, args, scene):
+def run_e2e(ctx, tracks, dev, prec, args, scene, knobs):
     """Same metric through the public API with host buffers: host->device
-    copy of the step's tracks from pinned memory, emit + trace, device->host
-    read of the counters and the hit list, all inside the timed region."""
+    copy of the step's tracks (one packed pinned buffer), emit + trace,
+    device->host read of the counters (the one synchronisation, which also
+    returns the photon count) and of the hit list, all inside the timed
+    region."""
     import torch
     from paper_2309_12496_gb300 import rich
-    from paper_2309_12496_gb300 import workloads as W
-    host = {}
-    for f in W.Tracks.FIELDS:
-        host[f] = torch.from_numpy(np.ascontiguousarray(getattr(tracks, f), np.float32)).pin_memory()
-    for f in ("event", "id"):
-        host[f] = torch.from_numpy(np.ascontiguousarray(getattr(tracks, f), np.uint32)
-                                   .view(np.int32)).pin_memory()
-    dt = rich.DeviceTracks(tracks, device=dev)
+    dt, host = rich.DeviceTracks.packed(tracks, device=dev)
     n0 = ctx.emit(dt, 0.0014, seed=7)
     cap = int(n0 * 1.5) + 1024
     out = rich.TraceOutputs(cap, scene.pixels_per_event, len(scene.planes), 1, 0, device=dev)
     hits_host = torch.empty(cap * rich.HIT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
-    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    h2d = host.numel() * host.element_size()
     d2h = 0
     photons = 0
     t_total = 0.0
     for k in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for f, v in host.items():
-            dt.t[f].copy_(v, non_blocking=True)
-        n = ctx.emit(dt, 0.0014, seed=5000 + k)
-        ctx.trace(out, precision=prec)
-        n_hits, _ = ctx.hits()
+        dt.upload(host)
+        ctx.emit(dt, 0.0014, seed=5000 + k, sync=False)
+        ctx.trace(out, precision=prec, **knobs)
+        n_hits, st = ctx.hits()
+        n = st["n_photons"]
         hits_host[: n_hits * 40].copy_(out.hits[: n_hits * 40], non_blocking=False)
         el = time.perf_counter() - t0
         if k >= args.warmup:

@@ -220,6 +220,37 @@ class DeviceTracks:
         self.t["n_fixed"] = (None if tracks.n_fixed is None else torch.from_numpy(
             np.ascontiguousarray(tracks.n_fixed, np.uint32).view(np.int32)).to(device))
 
+    @classmethod
+    def packed(cls, tracks: W.Tracks, device="cuda"):
+        """Tracks whose device arrays are slices of one buffer, and a pinned
+        host copy of that buffer: one host-to-device copy
+        (`dt.upload(host)`) moves a whole track set."""
+        torch = _torch()
+        fields = list(W.Tracks.FIELDS) + ["event", "id"]
+        n = tracks.n
+        host = torch.empty(len(fields) * max(n, 1), dtype=torch.int32).pin_memory()
+        hv = host.numpy()
+        for k, f in enumerate(fields):
+            a = getattr(tracks, f)
+            dtp = np.float32 if f in W.Tracks.FIELDS else np.uint32
+            hv[k * n:(k + 1) * n] = np.ascontiguousarray(a, dtp).view(np.int32)
+        dev = host.to(device)
+        self = cls.__new__(cls)
+        self.n = n
+        self.t = {}
+        for k, f in enumerate(fields):
+            v = dev[k * n:(k + 1) * n]
+            self.t[f] = v.view(torch.float32) if f in W.Tracks.FIELDS else v
+        self.t["n_fixed"] = (None if tracks.n_fixed is None else torch.from_numpy(
+            np.ascontiguousarray(tracks.n_fixed, np.uint32).view(np.int32)).to(device))
+        self._buf = dev
+        return self, host
+
+    def upload(self, host):
+        """Copy a packed pinned host buffer (from `packed`) into the device
+        arrays, asynchronously on the current stream."""
+        self._buf.copy_(host, non_blocking=True)
+
     def desc(self) -> TracksDesc:
         return TracksDesc(n=self.n, **{k: (None if v is None else v.data_ptr())
                                        for k, v in self.t.items()})
