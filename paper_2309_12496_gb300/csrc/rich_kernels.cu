@@ -195,7 +195,17 @@ k_yield(TracksView t, double n_minus_1, double inv_band_mm, uint32_t key0,
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t count = 0;
     if (i < t.n) {
+        // every input of the track in one round of loads, and the direction's
+        // normalisation next to the angle (independent chains the compiler
+        // can interleave)
         const double p = t.p[i], m = t.mass[i], len = t.length[i];
+        const float tx = t.x[i], ty = t.y[i], tz = t.z[i];
+        const float fdx = t.dx[i], fdy = t.dy[i], fdz = t.dz[i];
+        const uint32_t event = t.event[i];
+        const uint32_t id = t.id ? t.id[i] : (uint32_t)i;
+        const uint32_t n_fixed = t.n_fixed ? t.n_fixed[i] : 0u;
+        const double dx = fdx, dy = fdy, dz = fdz;
+        const double inv = RECS ? rsqrt64(dx * dx + dy * dy + dz * dz) : 0.0;
         // 1 - beta = m^2 / (E (E + p)) keeps n*beta - 1 accurate near 1
         double E = sqrt(p * p + m * m);
         double one_minus_beta = (m == 0.0) ? 0.0 : (m * m) / (E * (E + p));
@@ -228,30 +238,26 @@ k_yield(TracksView t, double n_minus_1, double inv_band_mm, uint32_t key0,
             sin_t = tan_t * cos_t;
             mu = len * 2.0 * kPi * kAlpha * (sin_t * sin_t) * inv_band_mm;
         }
-        uint32_t event = t.event[i];
-        uint32_t id = t.id ? t.id[i] : (uint32_t)i;
         if (t.n_fixed) {
-            count = t.n_fixed[i];
+            count = n_fixed;
         } else {
             TrackStream s{event, id, key0, key1, 0u, 4u, {0u, 0u, 0u, 0u}};
             int64_t k = poisson_draw(mu, s);
             count = (uint32_t)(k > 0xFFFFFFF0ll ? 0xFFFFFFF0ll : k);
         }
         if (RECS) {
-        double dx = t.dx[i], dy = t.dy[i], dz = t.dz[i];
-        double inv = rsqrt64(dx * dx + dy * dy + dz * dz);
         TrackRec r;
-        r.x = t.x[i];
-        r.y = t.y[i];
-        r.z = t.z[i];
+        r.x = tx;
+        r.y = ty;
+        r.z = tz;
         r.len = (float)len;
         r.tx = (float)(dx * inv);
         r.ty = (float)(dy * inv);
         r.tz = (float)(dz * inv);
         r.tan_theta = (float)tan_t;
-        r.rx = t.dx[i];
-        r.ry = t.dy[i];
-        r.rz = t.dz[i];
+        r.rx = fdx;
+        r.ry = fdy;
+        r.rz = fdz;
         r.event = event;
         r.id = id;
         r.count = count;
