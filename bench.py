@@ -16,7 +16,7 @@ HBM when the timed region starts; L2 is flushed (256 MiB write) before
 every timed step, outside the timed events.
 
 `--impl reference` times the FP64 CPU oracle on the same workload on the
-host cores (the reference arm of this build).
+host cores (the CPU reference arm).
 """
 from __future__ import annotations
 
