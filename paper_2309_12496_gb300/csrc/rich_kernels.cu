@@ -784,14 +784,14 @@ __device__ void nearest_bvh(const SceneView &sc, const DevNode *snodes, int n_sn
     constexpr int kEmpty = INT_MIN;
     if (skip_ref == 0) return;            // the whole tree is that surface
     const Ray r = make_ray(o, d);
-    int stack_ref[RICH_BVH_STACK];
-    float stack_t[RICH_BVH_STACK];
+    int2 stack[RICH_BVH_STACK];
     int sp = 0;
     int ref = 0, leaf = kEmpty;
     auto pop = [&]() -> int {
         while (sp > 0) {
             --sp;
-            if (stack_t[sp] <= b.t) return stack_ref[sp];
+            const int2 e = stack[sp];
+            if (__int_as_float(e.y) <= b.t) return e.x;
         }
         return kEmpty;
     };
@@ -808,8 +808,7 @@ __device__ void nearest_bvh(const SceneView &sc, const DevNode *snodes, int n_sn
             if (h0 && h1) {
                 const bool first0 = tn0 <= tn1;
                 if (sp < RICH_BVH_STACK) {
-                    stack_ref[sp] = first0 ? ch.y : ch.x;
-                    stack_t[sp] = first0 ? tn1 : tn0;
+                    stack[sp] = make_int2(first0 ? ch.y : ch.x, __float_as_int(first0 ? tn1 : tn0));
                     ++sp;
                 } else {
                     set_status(ctr, RICH_ERR_GEOMETRY);
