@@ -296,8 +296,9 @@ typedef struct rich_trace_opts {
                                registers (four blocks per SM), 1 uncapped;
                                257..768 threads: 1 caps it at 80 registers
                                (0: the 1024-thread variant, 64 registers)   */
-    int32_t bvh_smem_nodes; /* top BVH nodes staged in shared memory per block
-                               by a TMA bulk copy (-1: default)              */
+    int32_t bvh_smem_nodes; /* top BVH nodes (128 bytes each) staged in shared
+                               memory per block by a TMA bulk copy
+                               (-1: default, 768 above 256 threads)         */
     /* Efficiencies applied before propagation (Sec. 4.3: the quantum
      * efficiency and the mirror reflectivities combined into one
      * accept/reject per photon at its wavelength, and rejected photons not

@@ -23,7 +23,7 @@ CACHE = os.path.join(os.path.expanduser("~"), ".cache", "rich_gb300", "tune.json
 
 def candidates(n_triangles: int):
     """The search space (the BVH staging sizes only matter with meshes)."""
-    nodes = (0, 512, 1536) if n_triangles else (0,)
+    nodes = (0, 256, 768) if n_triangles else (0,)      # 128-byte four-wide nodes
     out = []
     for threads, bps in ((1024, 0), (512, 0), (512, 1)):
         for n in nodes:

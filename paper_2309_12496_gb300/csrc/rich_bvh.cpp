@@ -1,10 +1,12 @@
 // rich_bvh.cpp -- host builder of the triangle BVH used by the trace kernel.
 //
-// Binned surface-area-heuristic build (12 bins per axis over the triangle
-// centroids, traversal cost 1, intersection cost 1 per triangle, at most 8
-// triangles per leaf), flattened into 64-byte two-wide nodes that carry
-// both children's boxes, in breadth-first order so the top levels of the
-// tree are contiguous. Triangles are re-ordered into leaf order.
+// Binned surface-area-heuristic build of a binary tree (12 bins per axis over
+// the triangle centroids, traversal cost 1, intersection cost 1 per
+// triangle, at most 8 triangles per leaf), collapsed into four-wide nodes
+// (each node takes its binary children and opens the largest inner ones
+// until it holds four) of 128 bytes carrying the children's boxes, in
+// breadth-first order so the top levels of the tree are contiguous.
+// Triangles are re-ordered into leaf order.
 //
 // Triangles that share a surface id (one mirror segment, flat mirror or
 // window face) get a subtree of their own: each surface is built
@@ -155,12 +157,18 @@ struct Builder {
 };
 
 void put_box(DevNode &d, int slot, const Box &b) {
-    if (slot == 0) {
-        d.lo0x = b.lo[0]; d.lo0y = b.lo[1]; d.lo0z = b.lo[2];
-        d.hi0x = b.hi[0]; d.hi0y = b.hi[1]; d.hi0z = b.hi[2];
-    } else {
-        d.lo1x = b.lo[0]; d.lo1y = b.lo[1]; d.lo1z = b.lo[2];
-        d.hi1x = b.hi[0]; d.hi1y = b.hi[1]; d.hi1z = b.hi[2];
+    d.lox[slot] = b.lo[0]; d.loy[slot] = b.lo[1]; d.loz[slot] = b.lo[2];
+    d.hix[slot] = b.hi[0]; d.hiy[slot] = b.hi[1]; d.hiz[slot] = b.hi[2];
+}
+
+// An empty slot: a point box at 1e30 on every axis, which every ray's slab
+// test misses (its entry distance is beyond any tmax or its exit before 0).
+void clear_node(DevNode &d) {
+    std::memset(&d, 0, sizeof d);
+    for (int k = 0; k < 4; ++k) {
+        d.lox[k] = d.loy[k] = d.loz[k] = 1e30f;
+        d.hix[k] = d.hiy[k] = d.hiz[k] = 1e30f;
+        d.child[k] = std::numeric_limits<int32_t>::min();
     }
 }
 
@@ -286,40 +294,67 @@ bool build_bvh(const float *vertices, const int32_t *surface, int64_t n_tris, Bv
 
     out.leaf_order = order_all;
     auto leaf_code = [&](const Node &n) { return ~((n.first << 3) | (n.count - 1)); };
+    // surface roots are never opened into their parent, so each surface
+    // keeps one subtree (one node or one leaf) of its own
+    std::vector<char> is_surface_root(all.size(), 0);
+    for (auto &[sid, gr] : group_root)
+        if (sid >= 0) is_surface_root[gr] = 1;
+    // the up-to-four children of the four-wide node made from binary node n
+    auto collapse = [&](int n) {
+        std::vector<int> c = {all[n].left, all[n].right};
+        while (c.size() < 4) {
+            int best = -1;
+            float best_area = -1.0f;
+            for (size_t k = 0; k < c.size(); ++k) {
+                const Node &x = all[c[k]];
+                if (x.count > 0 || is_surface_root[c[k]]) continue;
+                const float a = x.box.area();
+                if (a > best_area) {
+                    best_area = a;
+                    best = (int)k;
+                }
+            }
+            if (best < 0) break;
+            const int x = c[best];
+            c[best] = all[x].left;
+            c.push_back(all[x].right);
+        }
+        return c;
+    };
     std::vector<int> dev_index(all.size(), -1);
     if (all[root].count > 0) {
         // the whole tree is one leaf
         DevNode d;
-        std::memset(&d, 0, sizeof d);
+        clear_node(d);
         put_box(d, 0, all[root].box);
-        put_box(d, 1, all[root].box);
-        d.child0 = d.child1 = leaf_code(all[root]);
+        d.child[0] = leaf_code(all[root]);
         out.nodes.push_back(d);
         out.depth = 1;
     } else {
-        // breadth-first flattening of the inner nodes
-        std::deque<std::pair<int, int>> q;   // (node, depth)
+        // breadth-first flattening of the four-wide nodes
+        std::deque<std::pair<int, int>> q;   // (binary node, depth)
         q.push_back({root, 1});
         std::vector<int> bfs;
+        std::vector<std::vector<int>> kids;
         while (!q.empty()) {
             auto [n, depth] = q.front();
             q.pop_front();
             dev_index[n] = (int)bfs.size();
             bfs.push_back(n);
             out.depth = std::max(out.depth, depth);
-            for (int c : {all[n].left, all[n].right})
+            kids.push_back(collapse(n));
+            for (int c : kids.back())
                 if (all[c].count == 0) q.push_back({c, depth + 1});
         }
         out.nodes.resize(bfs.size());
         for (size_t i = 0; i < bfs.size(); ++i) {
-            const Node &n = all[bfs[i]];
             DevNode &d = out.nodes[i];
-            std::memset(&d, 0, sizeof d);
-            const Node &l = all[n.left], &r = all[n.right];
-            put_box(d, 0, l.box);
-            put_box(d, 1, r.box);
-            d.child0 = l.count > 0 ? leaf_code(l) : dev_index[n.left];
-            d.child1 = r.count > 0 ? leaf_code(r) : dev_index[n.right];
+            clear_node(d);
+            for (size_t k = 0; k < kids[i].size(); ++k) {
+                const int c = kids[i][k];
+                put_box(d, (int)k, all[c].box);
+                d.child[k] = all[c].count > 0 ? leaf_code(all[c]) : dev_index[c];
+            }
         }
     }
     // ---- the subtree reference of every triangle's surface

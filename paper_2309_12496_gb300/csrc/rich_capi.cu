@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -552,7 +553,8 @@ RICH_API rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc 
     // structural check: children point strictly forward (traversal ends),
     // leaf ranges stay inside the triangle array
     for (size_t i = 0; i < bvh.nodes.size(); ++i) {
-        for (int c : {bvh.nodes[i].child0, bvh.nodes[i].child1}) {
+        for (int c : bvh.nodes[i].child) {
+            if (c == INT_MIN) continue;       // empty slot
             if (c >= 0) {
                 if ((size_t)c <= i || (size_t)c >= bvh.nodes.size()) return bad("BVH child index");
             } else {
@@ -775,7 +777,7 @@ RICH_API rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
                     "rich_trace: the emission's spectrum table is not in the current scene");
     const int cls = trace_shape_class(threads, o->wide_regs != 0);
     int smem_nodes = o->bvh_smem_nodes;
-    if (smem_nodes < 0) smem_nodes = threads > 256 ? 1536 : 0;
+    if (smem_nodes < 0) smem_nodes = threads > 256 ? 768 : 0;
     if (smem_nodes > ctx->sc.n_nodes) smem_nodes = ctx->sc.n_nodes;
     if (ctx->sc.n_tris == 0) smem_nodes = 0;
     DeviceGuard guard(ctx->device);
@@ -964,7 +966,7 @@ RICH_API rich_status rich_trace_grad(rich_ctx *ctx, const rich_tracks *t,
     const int threads = fo.block_threads ? fo.block_threads : 1024;
     const int cls = trace_shape_class(threads, fo.wide_regs != 0);
     int smem_nodes = fo.bvh_smem_nodes;
-    if (smem_nodes < 0) smem_nodes = threads > 256 ? 1536 : 0;
+    if (smem_nodes < 0) smem_nodes = threads > 256 ? 768 : 0;
     if (smem_nodes > ctx->sc.n_nodes) smem_nodes = ctx->sc.n_nodes;
     if (ctx->sc.n_tris == 0) smem_nodes = 0;
     TraceParams p{};

@@ -75,11 +75,13 @@ struct alignas(16) DevTri {  // 48 B: v0 | v1 | v2 | prim, material, surface
                               // surface, or 0x7FFFFFFF when it has none
 };
 
-struct alignas(16) DevNode { // 64 B: boxes of both children + child refs
-    float lo0x, lo0y, lo0z, hi0x;
-    float hi0y, hi0z, lo1x, lo1y;
-    float lo1z, hi1x, hi1y, hi1z;
-    int32_t child0, child1, pad0, pad1;  // >= 0 node, < 0 ~(first << 3 | (count - 1))
+struct alignas(16) DevNode { // 128 B: boxes of up to four children (by axis) + refs
+    float lox[4], hix[4];
+    float loy[4], hiy[4];
+    float loz[4], hiz[4];
+    int32_t child[4];          // >= 0 node, < 0 leaf ~(first << 3 | (count - 1)),
+                               // INT_MIN an empty slot (its box is empty too)
+    int32_t pad[4];
 };
 
 struct alignas(16) TrackRec {  // 64 B, written by the yield kernel

@@ -757,31 +757,74 @@ __device__ __forceinline__ void leaf_tris(const SceneView &sc, const Ray &r,
     }
 }
 
-__device__ __forceinline__ void load_node(const SceneView &sc, const DevNode *snodes,
-                                          int n_snodes, int ref, float4 &a, float4 &b,
-                                          float4 &c, int4 &ch) {
-    // one generic load path for both (no divergent branch between shared and
-    // global memory)
-    const float4 *q = reinterpret_cast<const float4 *>(ref < n_snodes ? snodes + ref : sc.nodes + ref);
-    a = q[0];
-    b = q[1];
-    c = q[2];
-    ch = *reinterpret_cast<const int4 *>(q + 3);
+// Box tests of the four children of a four-wide node, axis by axis (the
+// node holds lo x, hi x, lo y, hi y, lo z, hi z of the four children as six
+// float4, then the children's references), read through one generic load
+// path for shared and global memory. Returns each child's entry distance,
+// +infinity for a miss, with the widening of `slab`.
+__device__ __forceinline__ void node4_test(const Ray &r, const DevNode *p, float tmax,
+                                           float4 &key, int4 &ch) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+    const float ox = r.o.x * r.inv.x, oy = r.o.y * r.inv.y, oz = r.o.z * r.inv.z;
+    float4 tn, tf;
+    {
+        const float4 lo = q[0], hi = q[1];
+        float a, c;
+        a = fmaf(lo.x, r.inv.x, -ox); c = fmaf(hi.x, r.inv.x, -ox); tn.x = fminf(a, c); tf.x = fmaxf(a, c);
+        a = fmaf(lo.y, r.inv.x, -ox); c = fmaf(hi.y, r.inv.x, -ox); tn.y = fminf(a, c); tf.y = fmaxf(a, c);
+        a = fmaf(lo.z, r.inv.x, -ox); c = fmaf(hi.z, r.inv.x, -ox); tn.z = fminf(a, c); tf.z = fmaxf(a, c);
+        a = fmaf(lo.w, r.inv.x, -ox); c = fmaf(hi.w, r.inv.x, -ox); tn.w = fminf(a, c); tf.w = fmaxf(a, c);
+    }
+    {
+        const float4 lo = q[2], hi = q[3];
+        float a, c;
+        a = fmaf(lo.x, r.inv.y, -oy); c = fmaf(hi.x, r.inv.y, -oy); tn.x = fmaxf(tn.x, fminf(a, c)); tf.x = fminf(tf.x, fmaxf(a, c));
+        a = fmaf(lo.y, r.inv.y, -oy); c = fmaf(hi.y, r.inv.y, -oy); tn.y = fmaxf(tn.y, fminf(a, c)); tf.y = fminf(tf.y, fmaxf(a, c));
+        a = fmaf(lo.z, r.inv.y, -oy); c = fmaf(hi.z, r.inv.y, -oy); tn.z = fmaxf(tn.z, fminf(a, c)); tf.z = fminf(tf.z, fmaxf(a, c));
+        a = fmaf(lo.w, r.inv.y, -oy); c = fmaf(hi.w, r.inv.y, -oy); tn.w = fmaxf(tn.w, fminf(a, c)); tf.w = fminf(tf.w, fmaxf(a, c));
+    }
+    {
+        const float4 lo = q[4], hi = q[5];
+        float a, c;
+        a = fmaf(lo.x, r.inv.z, -oz); c = fmaf(hi.x, r.inv.z, -oz); tn.x = fmaxf(tn.x, fminf(a, c)); tf.x = fminf(tf.x, fmaxf(a, c));
+        a = fmaf(lo.y, r.inv.z, -oz); c = fmaf(hi.y, r.inv.z, -oz); tn.y = fmaxf(tn.y, fminf(a, c)); tf.y = fminf(tf.y, fmaxf(a, c));
+        a = fmaf(lo.z, r.inv.z, -oz); c = fmaf(hi.z, r.inv.z, -oz); tn.z = fmaxf(tn.z, fminf(a, c)); tf.z = fminf(tf.z, fmaxf(a, c));
+        a = fmaf(lo.w, r.inv.z, -oz); c = fmaf(hi.w, r.inv.z, -oz); tn.w = fmaxf(tn.w, fminf(a, c)); tf.w = fminf(tf.w, fmaxf(a, c));
+    }
+    ch = *reinterpret_cast<const int4 *>(q + 6);
+    const float kInf = __int_as_float(0x7f800000);
+    // 1 + 2^-20 widening keeps boxes conservative under FP32 rounding
+    key.x = fmaxf(tn.x, 0.0f) <= fminf(tf.x, tmax) * 1.00000095f ? fmaxf(tn.x, 0.0f) : kInf;
+    key.y = fmaxf(tn.y, 0.0f) <= fminf(tf.y, tmax) * 1.00000095f ? fmaxf(tn.y, 0.0f) : kInf;
+    key.z = fmaxf(tn.z, 0.0f) <= fminf(tf.z, tmax) * 1.00000095f ? fmaxf(tn.z, 0.0f) : kInf;
+    key.w = fmaxf(tn.w, 0.0f) <= fminf(tf.w, tmax) * 1.00000095f ? fmaxf(tn.w, 0.0f) : kInf;
+}
+
+__device__ __forceinline__ void cas_key(float &ka, int &ca, float &kb, int &cb) {
+    const bool sw = kb < ka;
+    const float k = sw ? kb : ka;
+    const int c = sw ? cb : ca;
+    kb = sw ? ka : kb;
+    cb = sw ? ca : cb;
+    ka = k;
+    ca = c;
 }
 
 constexpr int kNoSurf = 0x7FFFFFFF;   // no surface subtree to skip
 
-// Nearest triangle along the ray: two-wide BVH in the "while-while" order
-// of Aila and Laine (HPG 2009): descend inner nodes (near child first, the
-// far one stacked with its entry distance) until a leaf is found, postpone
-// it, and intersect postponed leaves together once every active lane holds
-// one, which keeps the lanes of a warp on the same kind of work. The top
-// levels of the tree are read from shared memory. The subtree `skip_ref` (the
-// surface the photon just left) is never entered.
+// Nearest triangle along the ray: four-wide BVH in the "while-while" order
+// of Aila and Laine (HPG 2009): descend inner nodes (nearest child first, the
+// other hit children stacked farthest first with their entry distances)
+// until a leaf is found, postpone it, and intersect postponed leaves
+// together once every active lane holds one, which keeps the lanes of a warp
+// on the same kind of work. The top levels of the tree are read from shared
+// memory. The subtree `skip_ref` (the surface the photon just left) is never
+// entered.
 __device__ void nearest_bvh(const SceneView &sc, const DevNode *snodes, int n_snodes,
                             f3 o, f3 d, int skip, int skip_ref, float t_min, Best &b,
                             Counters *ctr) {
     constexpr int kEmpty = INT_MIN;
+    const float kInf = __int_as_float(0x7f800000);
     if (skip_ref == 0) return;            // the whole tree is that surface
     const Ray r = make_ray(o, d);
     int2 stack[RICH_BVH_STACK];
@@ -795,31 +838,35 @@ __device__ void nearest_bvh(const SceneView &sc, const DevNode *snodes, int n_sn
         }
         return kEmpty;
     };
+    auto push = [&](int c, float t) {
+        if (sp < RICH_BVH_STACK) {
+            stack[sp] = make_int2(c, __float_as_int(t));
+            ++sp;
+        } else {
+            set_status(ctr, RICH_ERR_GEOMETRY);
+        }
+    };
     while (ref != kEmpty || leaf != kEmpty) {
         while (ref >= 0) {
-            float4 na, nb, nc;
+            float4 key;
             int4 ch;
-            load_node(sc, snodes, n_snodes, ref, na, nb, nc, ch);
-            float tn0, tn1;
-            const bool h0 = slab(r, na.x, na.y, na.z, na.w, nb.x, nb.y, b.t, tn0) &&
-                            ch.x != skip_ref;
-            const bool h1 = slab(r, nb.z, nb.w, nc.x, nc.y, nc.z, nc.w, b.t, tn1) &&
-                            ch.y != skip_ref;
-            if (h0 && h1) {
-                const bool first0 = tn0 <= tn1;
-                if (sp < RICH_BVH_STACK) {
-                    stack[sp] = make_int2(first0 ? ch.y : ch.x, __float_as_int(first0 ? tn1 : tn0));
-                    ++sp;
-                } else {
-                    set_status(ctr, RICH_ERR_GEOMETRY);
-                }
-                ref = first0 ? ch.x : ch.y;
-            } else if (h0) {
-                ref = ch.x;
-            } else if (h1) {
-                ref = ch.y;
-            } else {
+            node4_test(r, ref < n_snodes ? snodes + ref : sc.nodes + ref, b.t, key, ch);
+            float k0 = ch.x != skip_ref ? key.x : kInf, k1 = ch.y != skip_ref ? key.y : kInf;
+            float k2 = ch.z != skip_ref ? key.z : kInf, k3 = ch.w != skip_ref ? key.w : kInf;
+            int c0 = ch.x, c1 = ch.y, c2 = ch.z, c3 = ch.w;
+            // nearest first: sorting network of the four entry distances
+            cas_key(k0, c0, k1, c1);
+            cas_key(k2, c2, k3, c3);
+            cas_key(k0, c0, k2, c2);
+            cas_key(k1, c1, k3, c3);
+            cas_key(k1, c1, k2, c2);
+            if (k0 == kInf) {
                 ref = pop();
+            } else {
+                if (k3 != kInf) push(c3, k3);
+                if (k2 != kInf) push(c2, k2);
+                if (k1 != kInf) push(c1, k1);
+                ref = c0;
             }
             if (ref < 0 && ref != kEmpty && leaf == kEmpty) {
                 leaf = ref;
