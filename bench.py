@@ -42,10 +42,10 @@ WORKLOAD = "rich1_meshed_1000_pion_tracks"
 # FP32 operations per propagated photon of the trace kernel on this workload:
 # 2 x FFMA + FADD + FMUL thread instructions of one k_trace launch from the
 # ncu counters (smsp__sass_thread_inst_executed_op_{ffma,fadd,fmul}_pred_on)
-# divided by its 350,350 photons: (2 x 256.54 M + 41.72 M + 72.88 M) / 350,350.
-FLOPS_PER_PHOTON = 1791.6
+# divided by its 350,350 photons: (2 x 244.19 M + 37.77 M + 87.12 M) / 350,350.
+FLOPS_PER_PHOTON = 1750.4
 # dram__bytes_read.sum + dram__bytes_write.sum of the same k_trace launch.
-TRACE_DRAM_BYTES = 6945792 + 165632
+TRACE_DRAM_BYTES = 9755904 + 549888
 FP32_LANES_PER_SM = 128
 SM_COUNT_NOMINAL = 152
 
