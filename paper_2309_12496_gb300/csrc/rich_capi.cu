@@ -70,8 +70,7 @@ struct rich_ctx {
     int smem_optin = 48 * 1024;
     // gradient: nominal tiles (host), their frames (device), tilted copies
     std::vector<rich_sphere> nom_spheres;
-    DevTileNom *d_tile_nom = nullptr;
-    void *d_grad_tiles = nullptr;          // groups + tiles at theta
+    void *d_grad_tiles = nullptr;          // groups + tiles + tile duals at theta
     double *d_acc = nullptr;               // 12 FP64 accumulators
     double *h_acc = nullptr;               // pinned
     // captured emit + trace (CUDA graph) and the stream it was captured on
@@ -162,15 +161,10 @@ bool group_tiles(const rich_sphere *sp, int n, int n_materials,
     groups.resize(spheres.size());
     for (size_t gi = 0; gi < spheres.size(); ++gi) {
         DevSphereGroup &G = groups[gi];
-        G.cx = std::get<0>(spheres[gi]);
-        G.cy = std::get<1>(spheres[gi]);
-        G.cz = std::get<2>(spheres[gi]);
-        G.fcx = (float)G.cx;
-        G.fcy = (float)G.cy;
-        G.fcz = (float)G.cz;
-        G.pad = 0.0f;
+        G.fcx = std::get<0>(spheres[gi]);
+        G.fcy = std::get<1>(spheres[gi]);
+        G.fcz = std::get<2>(spheres[gi]);
         const double R = std::get<3>(spheres[gi]);
-        G.r2 = R * R;
         G.radius = (float)R;
         G.inv_radius = (float)(1.0 / R);
         G.first = (int)tiles.size();
@@ -235,6 +229,52 @@ rich_sphere tile_at_theta(const rich_sphere &s, int i, const double theta[10]) {
     }
     t.radius = (float)R;
     return t;
+}
+
+// Centre of tile i at theta with its first derivatives, for the adjoint.
+// With a1 = M(e1, alpha) a0 and a = M(e2, beta) a1 (rotations about the
+// fixed nominal axes, as tile_at_theta), the derivative of a rotation about
+// a fixed unit axis u is u x (rotated vector): da/dbeta = e2 x a and
+// da/dalpha = M(e2, beta) (e1 x a1); C = P - R a gives dC = -R da and
+// dC/dR = -a. The centre is stored as a double-word, hi + lo per axis.
+DevTileDual tile_dual(const rich_sphere &s, int i, const double theta[10]) {
+    const double R0 = s.radius, R = theta[8];
+    double P[3], a[3], u1[3], u2[3], da_dal[3] = {0, 0, 0}, da_dbe[3] = {0, 0, 0};
+    for (int k = 0; k < 3; ++k) {
+        P[k] = (double)s.center[k] + R0 * s.axis[k];
+        a[k] = s.axis[k];
+        u1[k] = s.e1[k];
+        u2[k] = s.e2[k];
+    }
+    auto cross = [](const double x[3], const double y[3], double r[3]) {
+        r[0] = x[1] * y[2] - x[2] * y[1];
+        r[1] = x[2] * y[0] - x[0] * y[2];
+        r[2] = x[0] * y[1] - x[1] * y[0];
+    };
+    if (i < 4) {
+        rotate(u1, theta[2 * i], a);            // a1
+        cross(u1, a, da_dal);                   // d a1 / d alpha
+        rotate(u2, theta[2 * i + 1], da_dal);
+        rotate(u2, theta[2 * i + 1], a);        // a
+        cross(u2, a, da_dbe);
+    }
+    DevTileDual D{};
+    for (int k = 0; k < 3; ++k) {
+        const double c = P[k] - R * a[k];
+        D.c_hi[k] = (float)c;
+        D.c_lo[k] = (float)(c - (double)D.c_hi[k]);
+        D.dc_dalpha[k] = (float)(-R * da_dal[k]);
+        D.dc_dbeta[k] = (float)(-R * da_dbe[k]);
+        D.dc_dr[k] = (float)(-a[k]);
+    }
+    return D;
+}
+
+// Device scratch of the gradient: sphere groups and tiles at theta, then
+// the tiles' dual centres.
+size_t grad_tiles_bytes() {
+    return sizeof(DevSphereGroup) * RICH_MAX_GROUPS + sizeof(DevTile) * RICH_MAX_TILES +
+           sizeof(DevTileDual) * RICH_MAX_TILES;
 }
 
 // A captured graph refers to the context's buffers: drop it before any of
@@ -410,7 +450,6 @@ RICH_API rich_status rich_destroy(rich_ctx *ctx) {
         cudaStreamSynchronize(ctx->stream);
         cudaFree(ctx->d_geom);
         cudaFree(ctx->d_refine);
-        cudaFree(ctx->d_tile_nom);
         cudaFree(ctx->d_grad_tiles);
         if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
         if (ctx->graph) cudaGraphDestroy(ctx->graph);
@@ -502,7 +541,6 @@ RICH_API rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc 
     }
     // ---- rectangles and planes
     std::vector<DevRect> rects(g->n_rects);
-    std::vector<DevRectD> rects_d(g->n_rects);
     int plane_nx[RICH_MAX_PLANES] = {0}, plane_ny[RICH_MAX_PLANES] = {0};
     int n_planes = 0;
     for (int i = 0; i < g->n_rects; ++i) {
@@ -523,11 +561,6 @@ RICH_API rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc 
         R.gy = r.ny;
         R.plane = m.kind == RICH_MAT_DETECTOR ? m.plane : -1;
         R.prim = g->n_spheres + i;
-        DevRectD &D = rects_d[i];
-        D.ox = r.origin[0]; D.oy = r.origin[1]; D.oz = r.origin[2];
-        D.ux = r.u_axis[0]; D.uy = r.u_axis[1]; D.uz = r.u_axis[2];
-        D.vx = r.v_axis[0]; D.vy = r.v_axis[1]; D.vz = r.v_axis[2];
-        D.nx = r.normal[0]; D.ny = r.normal[1]; D.nz = r.normal[2];
         if (m.kind == RICH_MAT_DETECTOR) {
             if (r.nx <= 0 || r.ny <= 0 || r.nx > 65535 || r.ny > 65535 || !(r.pitch > 0.f))
                 return bad("detector rectangle needs a pixel grid (1..65535) and a pitch");
@@ -587,15 +620,13 @@ RICH_API rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc 
     // ---- one device allocation
     auto r256 = [](size_t b) { return (b + 255) & ~size_t(255); };
     size_t sizes[] = {sizeof(DevSphereGroup) * groups.size(), sizeof(DevTile) * tiles.size(),
-                      sizeof(DevRect) * rects.size(), sizeof(DevRectD) * rects_d.size(),
-                      sizeof(DevTable) * tables.size(), sizeof(DevMaterial) * mats.size(),
+                      sizeof(DevRect) * rects.size(), sizeof(DevTable) * tables.size(), sizeof(DevMaterial) * mats.size(),
                       sizeof(DevNode) * bvh.nodes.size(), sizeof(DevTri) * tris.size(),
                       sizeof(float) * normals.size()};
-    const void *srcs[] = {groups.data(), tiles.data(), rects.data(), rects_d.data(),
-                          tables.data(), mats.data(), bvh.nodes.data(), tris.data(),
+    const void *srcs[] = {groups.data(), tiles.data(), rects.data(), tables.data(), mats.data(), bvh.nodes.data(), tris.data(),
                           normals.data()};
-    size_t total = 0, offs[9];
-    for (int i = 0; i < 9; ++i) {
+    size_t total = 0, offs[8];
+    for (int i = 0; i < 8; ++i) {
         offs[i] = total;
         total += r256(sizes[i]);
     }
@@ -607,19 +638,18 @@ RICH_API rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc 
     void *buf = nullptr;
     RICH_CUDA(cudaMalloc(&buf, std::max<size_t>(total, 256)));
     ctx->d_geom = buf;
-    for (int i = 0; i < 9; ++i)
+    for (int i = 0; i < 8; ++i)
         if (sizes[i]) RICH_CUDA(cudaMemcpy((char *)buf + offs[i], srcs[i], sizes[i], cudaMemcpyHostToDevice));
     SceneView sc{};
     auto at = [&](int i) { return sizes[i] ? (const void *)((char *)buf + offs[i]) : nullptr; };
     sc.groups = (const DevSphereGroup *)at(0);
     sc.tiles = (const DevTile *)at(1);
     sc.rects = (const DevRect *)at(2);
-    sc.rects_d = (const DevRectD *)at(3);
-    sc.tables = (const DevTable *)at(4);
-    sc.materials = (const DevMaterial *)at(5);
-    sc.nodes = (const DevNode *)at(6);
-    sc.tris = (const DevTri *)at(7);
-    sc.tri_normals = (const float *)at(8);
+    sc.tables = (const DevTable *)at(3);
+    sc.materials = (const DevMaterial *)at(4);
+    sc.nodes = (const DevNode *)at(5);
+    sc.tris = (const DevTri *)at(6);
+    sc.tri_normals = (const float *)at(7);
     sc.n_groups = (int)groups.size();
     sc.n_tiles = (int)tiles.size();
     sc.n_rects = (int)rects.size();
@@ -638,27 +668,12 @@ RICH_API rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc 
     sc.pixels_per_event = off;
     ctx->sc = sc;
     ctx->bvh_depth = bvh.depth;
-    // nominal tile frames for the gradient
+    // nominal tiles for the gradient
     ctx->nom_spheres.assign(g->spheres, g->spheres + g->n_spheres);
-    cudaFree(ctx->d_tile_nom);
-    ctx->d_tile_nom = nullptr;
     cudaFree(ctx->d_grad_tiles);
     ctx->d_grad_tiles = nullptr;
-    if (g->n_spheres) {
-        std::vector<DevTileNom> nom(g->n_spheres);
-        for (int i = 0; i < g->n_spheres; ++i) {
-            const rich_sphere &q = g->spheres[i];
-            const double R0 = q.radius;
-            nom[i] = {q.center[0] + R0 * q.axis[0], q.center[1] + R0 * q.axis[1],
-                      q.center[2] + R0 * q.axis[2], q.axis[0], q.axis[1], q.axis[2],
-                      q.e1[0], q.e1[1], q.e1[2], q.e2[0], q.e2[1], q.e2[2]};
-        }
-        RICH_CUDA(cudaMalloc(&ctx->d_tile_nom, sizeof(DevTileNom) * nom.size()));
-        RICH_CUDA(cudaMemcpy(ctx->d_tile_nom, nom.data(), sizeof(DevTileNom) * nom.size(),
-                             cudaMemcpyHostToDevice));
-        RICH_CUDA(cudaMalloc(&ctx->d_grad_tiles,
-                             sizeof(DevSphereGroup) * RICH_MAX_GROUPS + sizeof(DevTile) * RICH_MAX_TILES));
-    }
+    if (g->n_spheres)
+        RICH_CUDA(cudaMalloc(&ctx->d_grad_tiles, grad_tiles_bytes()));
     ctx->has_dielectric = any_dielectric;
     ctx->table_kind.assign(g->n_tables, 0);
     for (int i = 0; i < g->n_tables; ++i) ctx->table_kind[i] = g->tables[i].kind;
@@ -702,7 +717,6 @@ RICH_API rich_status rich_emit(rich_ctx *ctx, const rich_tracks *t,
                         "rich_emit: dispersion needs disp_a > 0 and 0 < disp_lambda0 < lambda_min");
     }
     DeviceGuard guard(ctx->device);
-    const int64_t n = t->n;
     {
         const rich_status st = emit_core(ctx, t, prm->seed, prm->n_minus_1, prm->lambda_min,
                                          prm->lambda_max, prm->source, prm->yield_per_mm,
@@ -919,10 +933,15 @@ RICH_API rich_status rich_trace_grad(rich_ctx *ctx, const rich_tracks *t,
     theta[9] = th->n_minus_1;
     // tiles at theta
     SceneView sv = ctx->sc;
+    const DevTileDual *grad_duals = nullptr;
     const int ns = (int)ctx->nom_spheres.size();
     if (ns) {
         std::vector<rich_sphere> at(ns);
-        for (int i = 0; i < ns; ++i) at[i] = tile_at_theta(ctx->nom_spheres[i], i, theta);
+        std::vector<DevTileDual> duals(ns);
+        for (int i = 0; i < ns; ++i) {
+            at[i] = tile_at_theta(ctx->nom_spheres[i], i, theta);
+            duals[i] = tile_dual(ctx->nom_spheres[i], i, theta);
+        }
         std::vector<DevSphereGroup> groups;
         std::vector<DevTile> tiles;
         std::string gerr;
@@ -934,6 +953,10 @@ RICH_API rich_status rich_trace_grad(rich_ctx *ctx, const rich_tracks *t,
         char *tb = base + sizeof(DevSphereGroup) * RICH_MAX_GROUPS;
         RICH_CUDA(cudaMemcpyAsync(tb, tiles.data(), sizeof(DevTile) * tiles.size(),
                                   cudaMemcpyHostToDevice, ctx->stream));
+        char *db = tb + sizeof(DevTile) * RICH_MAX_TILES;
+        RICH_CUDA(cudaMemcpyAsync(db, duals.data(), sizeof(DevTileDual) * ns,
+                                  cudaMemcpyHostToDevice, ctx->stream));
+        grad_duals = reinterpret_cast<const DevTileDual *>(db);
         sv.groups = reinterpret_cast<const DevSphereGroup *>(base);
         sv.tiles = reinterpret_cast<const DevTile *>(tb);
         sv.n_groups = (int)groups.size();
@@ -999,7 +1022,7 @@ RICH_API rich_status rich_trace_grad(rich_ctx *ctx, const rich_tracks *t,
     const EmitView em = emit_view(ctx);
     RICH_CUDA(launch_trace(sv, &em, nullptr, p, ctx->d_ctr, shape, ctx->stream));
     GradView gv{};
-    gv.nom = ctx->d_tile_nom;
+    gv.tiles = grad_duals;
     gv.n_tiles = ns;
     gv.n_planes = ctx->sc.n_planes;
     for (int k = 0; k < 10; ++k) gv.theta[k] = theta[k];

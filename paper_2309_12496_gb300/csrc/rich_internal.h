@@ -36,11 +36,11 @@ struct DevMaterial {
     int32_t kind, table, plane, flags;
 };
 
-struct DevSphereGroup {      // 64 B
-    double cx, cy, cz, r2;   // FP64 centre and R^2 (from the FP32 inputs)
+struct DevSphereGroup {      // 32 B
+    float fcx, fcy, fcz;     // the FP32 input centre
     float radius, inv_radius;
     int32_t first, count;    // tiles [first, first + count)
-    float fcx, fcy, fcz, pad; // the FP32 input centre (exact in both forms)
+    float pad;
 };
 
 struct DevTile {             // 160 B
@@ -59,10 +59,6 @@ struct DevRect {             // 80 B
     float nx, ny, nz;
     int32_t material;
     int32_t gx, gy, plane, prim;
-};
-
-struct DevRectD {            // FP64 copy for the refinement replay, 96 B
-    double ox, oy, oz, ux, uy, uz, vx, vy, vz, nx, ny, nz;
 };
 
 struct alignas(16) DevTri {  // 48 B: v0 | v1 | v2 | prim, material, surface
@@ -109,7 +105,6 @@ struct SceneView {
     const DevSphereGroup *groups;
     const DevTile *tiles;
     const DevRect *rects;
-    const DevRectD *rects_d;
     const DevTable *tables;
     const DevMaterial *materials;
     const DevNode *nodes;
@@ -186,17 +181,20 @@ struct TraceParams {
     int32_t prefilter_tables[4];
 };
 
-// Nominal frame of a sphere tile for the gradient: pole P = C + R a, axis
-// a (centre -> pole) and tangent axes e1, e2, in FP64.
-struct DevTileNom {           // 96 B
-    double px, py, pz, ax, ay, az, e1x, e1y, e1z, e2x, e2y, e2z;
+// Sphere tile i at the gradient's parameters: centre C = P - R a(alpha_i,
+// beta_i) as a double-word (hi + lo per axis) and its derivatives with
+// respect to alpha_i, beta_i (zero for i >= 4) and R.
+struct DevTileDual {          // 64 B
+    float c_hi[3], c_lo[3];
+    float dc_dalpha[3], dc_dbeta[3], dc_dr[3];
+    float pad;
 };
 
 // Gradient of the soft ring chi^2: parameters theta (8 tile tilts, radius of
 // curvature, n - 1), ring targets [n_tracks][n_planes] = (cu, cv, r, weight)
 // and the FP64 accumulators (loss sum, hits used, 10 gradient sums).
 struct GradView {
-    const DevTileNom *nom;
+    const DevTileDual *tiles;
     int32_t n_tiles;
     int32_t n_planes;
     double theta[10];

@@ -552,32 +552,44 @@ struct SmemScene {
     int n_groups, n_tiles, n_rects;
 };
 
-// Tiles: per distinct sphere, the FP64 quadratic |w + t d|^2 = R^2 with
-// w = o - C (precision policy: FP64 only for the large-radius sphere
-// discriminant), roots by the cancellation-free pair (q, c/q); the
-// aperture of each tile is then tested in FP32 at the point relative to
-// the centre. The nearer root on any tile hides the farther one.
-__device__ __forceinline__ void nearest_tiles(const SmemScene &S, f3 o, f3 d,
-                                              int skip, float t_min, Best &b) {
-    const double dx = d.x, dy = d.y, dz = d.z;
+// a < b for normalised double-words
+__device__ __forceinline__ bool ff_lt(ff a, ff b) {
+    return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+
+// Tiles: per distinct sphere, the quadratic |w + t d|^2 = R^2 with w = o - C
+// in double-word arithmetic (rich_ff.cuh, ~48 bits; precision policy: the
+// large-radius discriminant is the one place the trace needs more than
+// FP32, and double-words give it at FP32 issue rates), roots by the
+// cancellation-free pair (q, c/q); the aperture of each tile is then tested
+// in FP32 at the point relative to the centre. The nearer root on any tile
+// hides the farther one. Out of line, as sphere_normal: inlined, their
+// double-word registers enter the bounce loop's allocation under the
+// 64-register cap and slow mesh-only traces by a few per cent.
+__device__ __noinline__ void nearest_tiles(const SmemScene &S, f3 o, f3 d,
+                                           int skip, float t_min, Best &b) {
     for (int gi = 0; gi < S.n_groups; ++gi) {
         const DevSphereGroup &G = S.groups[gi];
-        const double wx = (double)o.x - G.cx, wy = (double)o.y - G.cy,
-                     wz = (double)o.z - G.cz;
-        const double bq = fma(wx, dx, fma(wy, dy, wz * dz));
-        const double c = fma(wx, wx, fma(wy, wy, wz * wz)) - G.r2;
-        const double disc = fma(bq, bq, -c);
-        if (disc < 0.0) continue;
-        const double sq = sqrt(disc);
-        const double q = bq > 0.0 ? -(bq + sq) : (sq - bq);
-        double r1 = q, r2 = (q != 0.0) ? c / q : 0.0;
-        const double t_lo = fmin(r1, r2), t_hi = fmax(r1, r2);
+        // w = o - C exactly (FP32 inputs)
+        const ff wx = two_sum(o.x, -G.fcx), wy = two_sum(o.y, -G.fcy),
+                 wz = two_sum(o.z, -G.fcz);
+        const ff bq = ff_add(ff_add(ff_mul(wx, d.x), ff_mul(wy, d.y)), ff_mul(wz, d.z));
+        const ff c = ff_sub(ff_add(ff_add(ff_mul(wx, wx), ff_mul(wy, wy)), ff_mul(wz, wz)),
+                            two_prod(G.radius, G.radius));
+        const ff disc = ff_sub(ff_mul(bq, bq), c);
+        if (disc.hi < 0.0f) continue;
+        const ff sq = ff_sqrt(disc);
+        const ff q = bq.hi > 0.0f ? ff_neg(ff_add(bq, sq)) : ff_sub(sq, bq);
+        const ff r2 = q.hi != 0.0f ? ff_div(c, q) : ffv(0.0f);
+        const bool q_first = ff_lt(q, r2);
+        const ff t_lo = q_first ? q : r2, t_hi = q_first ? r2 : q;
 #pragma unroll
         for (int ri = 0; ri < 2; ++ri) {
-            const double tr = ri == 0 ? t_lo : t_hi;
-            if (!(tr > (double)t_min) || !(tr < (double)b.t)) continue;
-            const f3 pc = mk3((float)fma(tr, dx, wx), (float)fma(tr, dy, wy),
-                              (float)fma(tr, dz, wz));
+            const ff tr = ri == 0 ? t_lo : t_hi;
+            // tr > t_min and tr < b.t for the double-word value
+            if (!ff_lt(ffv(t_min), tr) || !ff_lt(tr, ffv(b.t))) continue;
+            const f3 pc = mk3(ff_add(wx, ff_mul(tr, d.x)).hi, ff_add(wy, ff_mul(tr, d.y)).hi,
+                              ff_add(wz, ff_mul(tr, d.z)).hi);
             bool hit = false;
             for (int k = G.first; k < G.first + G.count; ++k) {
                 const DevTile &T = S.tiles[k];
@@ -590,7 +602,7 @@ __device__ __forceinline__ void nearest_tiles(const SmemScene &S, f3 o, f3 d,
                 for (int e = 0; e < T.n_edges; ++e)
                     in = in && (T.edges[e][0] * x + T.edges[e][1] * y <= T.edges[e][2]);
                 if (!in) continue;
-                b.t = (float)tr;
+                b.t = tr.hi;
                 b.prim = T.prim;
                 b.kind = 0;
                 b.idx = k;
@@ -600,6 +612,16 @@ __device__ __forceinline__ void nearest_tiles(const SmemScene &S, f3 o, f3 d,
             if (hit) break;
         }
     }
+}
+
+// Inward unit normal (towards the centre) at o + t d on the group's sphere,
+// from the double-word point relative to the centre.
+__device__ __noinline__ f3 sphere_normal(const DevSphereGroup &G, f3 o, f3 d, float t) {
+    const ff3 p = {ff_add(two_sum(o.x, -G.fcx), two_prod(t, d.x)),
+                   ff_add(two_sum(o.y, -G.fcy), two_prod(t, d.y)),
+                   ff_add(two_sum(o.z, -G.fcz), two_prod(t, d.z))};
+    const ff inv = ff_neg(ff_rsqrt(ff3_dot(p, p)));
+    return mk3(ff_mul(p.x, inv).hi, ff_mul(p.y, inv).hi, ff_mul(p.z, inv).hi);
 }
 
 __device__ __forceinline__ void nearest_rects(const SmemScene &S, f3 o, f3 d,
@@ -1027,14 +1049,30 @@ __device__ __forceinline__ void ff_sincos_2pi(uint32_t w, ff &s, ff &c) {
 // azimuth 2 pi u from ff_sincos_2pi, cos and sin of the Cherenkov angle
 // from the FP64 yield pass. Isotropic source: cos(theta) = 1 - 2u (exact)
 // and sin(theta) = 2 sqrt(u (1 - u)) from the exact product u (1 - u).
-__device__ void emit_ff(const TrackRec &tr, double2 cs, uint32_t j, float lam,
-                        const EmitView &em, ff3 &o, ff3 &d) {
+// Origin, unit track direction and (sin, cos) of the azimuth of photon j.
+__device__ __forceinline__ void emit_start_ff(const TrackRec &tr, uint32_t j,
+                                              const EmitView &em, ff3 &o, ff3 &t, ff &sp,
+                                              ff &cp) {
     const u4 w0 = philox10(0u, j, tr.id, tr.event, em.key0, em.key1);
-    const ff3 t = ff3_normalized(ff3v(tr.rx, tr.ry, tr.rz));
+    t = ff3_normalized(ff3v(tr.rx, tr.ry, tr.rz));
     const ff s = two_prod(u24f(w0.x), tr.len);      // exact: 24 x 24 bits
     o = ff3_axpy(s, t, ff3v(tr.x, tr.y, tr.z));
-    ff sp, cp;
     ff_sincos_2pi(w0.y, sp, cp);
+}
+
+// Unit direction of the azimuth (cos, sin) in the plane normal to t.
+__device__ __forceinline__ ff3 azimuth_dir_ff(const ff3 &t, ff sp, ff cp) {
+    ff3 e1, e2;
+    basis_ff(t, e1, e2);
+    return {ff_add(ff_mul(e1.x, cp), ff_mul(e2.x, sp)), ff_add(ff_mul(e1.y, cp), ff_mul(e2.y, sp)),
+            ff_add(ff_mul(e1.z, cp), ff_mul(e2.z, sp))};
+}
+
+__device__ void emit_ff(const TrackRec &tr, double2 cs, uint32_t j, float lam,
+                        const EmitView &em, ff3 &o, ff3 &d) {
+    ff3 t;
+    ff sp, cp;
+    emit_start_ff(tr, j, em, o, t, sp, cp);
     if (em.source == RICH_SOURCE_ISOTROPIC) {
         const u4 w3 = philox10(3u, j, tr.id, tr.event, em.key0, em.key1);
         const float u = u24f(w3.z);
@@ -1042,11 +1080,7 @@ __device__ void emit_ff(const TrackRec &tr, double2 cs, uint32_t j, float lam,
         d = {ff_mul(st, cp), ff_mul(st, sp), ffv(1.0f - 2.0f * u)};
         return;
     }
-    ff3 e1, e2;
-    basis_ff(t, e1, e2);
-    const ff r_x = ff_add(ff_mul(e1.x, cp), ff_mul(e2.x, sp));
-    const ff r_y = ff_add(ff_mul(e1.y, cp), ff_mul(e2.y, sp));
-    const ff r_z = ff_add(ff_mul(e1.z, cp), ff_mul(e2.z, sp));
+    const ff3 r = azimuth_dir_ff(t, sp, cp);
     double cos_t = cs.x, sin_t = cs.y;
     if (em.dispersion) {
         // dispersive radiator: the angle of the photon's own wavelength, FP64,
@@ -1058,9 +1092,9 @@ __device__ void emit_ff(const TrackRec &tr, double2 cs, uint32_t j, float lam,
         sin_t = nb1 > 0.0 ? sqrt(nb1 * (2.0 + nb1)) * cos_t : 0.0;
     }
     const ff ct = ff_from_double(cos_t), st = ff_from_double(sin_t);
-    d = ff3_normalized({ff_add(ff_mul(t.x, ct), ff_mul(r_x, st)),
-                        ff_add(ff_mul(t.y, ct), ff_mul(r_y, st)),
-                        ff_add(ff_mul(t.z, ct), ff_mul(r_z, st))});
+    d = ff3_normalized({ff_add(ff_mul(t.x, ct), ff_mul(r.x, st)),
+                        ff_add(ff_mul(t.y, ct), ff_mul(r.y, st)),
+                        ff_add(ff_mul(t.z, ct), ff_mul(r.z, st))});
 }
 
 // Pixel of a double-word position: floor(u / pitch), clamped to the grid.
@@ -1079,15 +1113,6 @@ __device__ __forceinline__ void bin_hit(const SceneView &sc, const TraceParams &
                             (int64_t)iy * sc.plane_nx[plane] + ix;
         atomicAdd(P.pixel_counts + idx, 1u);
     }
-}
-
-__device__ __forceinline__ void pixel_of(const DevRect &R, double u, double v, int &ix,
-                                         int &iy) {
-    const double pitch = (double)R.pitch;
-    ix = (int)floor(u / pitch);
-    iy = (int)floor(v / pitch);
-    ix = ix < 0 ? 0 : (ix >= R.gx ? R.gx - 1 : ix);
-    iy = iy < 0 ? 0 : (iy >= R.gy ? R.gy - 1 : iy);
 }
 
 constexpr int kSmemKeys = 64;   // event-sum keys a block table holds
@@ -1426,13 +1451,7 @@ k_trace(TraceArgs A) {
                 if (b.kind == 0) {
                     const DevTile &T = S.tiles[b.idx];
                     const DevSphereGroup &G = S.groups[T.group];
-                    // FP64 point relative to the centre for the normal
-                    const double tt = (double)b.t;
-                    const double px = fma(tt, (double)ph.d.x, (double)ph.o.x - G.cx);
-                    const double py = fma(tt, (double)ph.d.y, (double)ph.o.y - G.cy);
-                    const double pz = fma(tt, (double)ph.d.z, (double)ph.o.z - G.cz);
-                    const double inv = -1.0 / sqrt(px * px + py * py + pz * pz);
-                    n_sh = mk3((float)(px * inv), (float)(py * inv), (float)(pz * inv));
+                    n_sh = sphere_normal(G, ph.o, ph.d, b.t);
                     n_geo = n_sh;
                     front = dot3(ph.d, n_sh) < 0.0f;
                     mat_id = T.material;
@@ -1686,17 +1705,18 @@ cudaError_t launch_refine(const SceneView &sc, const EmitView *em, const ExtView
 // Gradient of the soft ring chi^2 with respect to theta = (tilt alpha_k,
 // beta_k of sphere tiles 0..3, radius of curvature, n - 1): every stored hit
 // is replayed along its recorded reflecting surfaces (fixed topology) in
-// forward mode, with FP64 values and 10 FP32 tangents per quantity.
+// forward mode, with double-word values (the refinement replay's arithmetic,
+// see rich_ff.cuh) and 10 FP32 tangents per quantity.
 constexpr int kNG = 10;
 struct Dm {
-    double v;
+    ff v;
     float d[kNG];
 };
 struct Dm3 {
     Dm x, y, z;
 };
 
-__device__ __forceinline__ Dm dm_c(double v) {
+__device__ __forceinline__ Dm dm_c(ff v) {
     Dm r;
     r.v = v;
 #pragma unroll
@@ -1705,198 +1725,231 @@ __device__ __forceinline__ Dm dm_c(double v) {
 }
 __device__ __forceinline__ Dm dm_add(const Dm &a, const Dm &b) {
     Dm r;
-    r.v = a.v + b.v;
+    r.v = ff_add(a.v, b.v);
 #pragma unroll
     for (int k = 0; k < kNG; ++k) r.d[k] = a.d[k] + b.d[k];
     return r;
 }
 __device__ __forceinline__ Dm dm_sub(const Dm &a, const Dm &b) {
     Dm r;
-    r.v = a.v - b.v;
+    r.v = ff_sub(a.v, b.v);
 #pragma unroll
     for (int k = 0; k < kNG; ++k) r.d[k] = a.d[k] - b.d[k];
     return r;
 }
-__device__ __forceinline__ Dm dm_mul(const Dm &a, const Dm &b) {
-    Dm r;
-    r.v = a.v * b.v;
-    const float av = (float)a.v, bv = (float)b.v;
-#pragma unroll
-    for (int k = 0; k < kNG; ++k) r.d[k] = fmaf(a.d[k], bv, av * b.d[k]);
+__device__ __forceinline__ Dm dm_addf(const Dm &a, float c) {
+    Dm r = a;
+    r.v = ff_add(a.v, c);
     return r;
 }
-__device__ __forceinline__ Dm dm_scl(const Dm &a, double s) {
+__device__ __forceinline__ Dm dm_neg(const Dm &a) {
     Dm r;
-    r.v = a.v * s;
-    const float sf = (float)s;
+    r.v = ff_neg(a.v);
 #pragma unroll
-    for (int k = 0; k < kNG; ++k) r.d[k] = a.d[k] * sf;
+    for (int k = 0; k < kNG; ++k) r.d[k] = -a.d[k];
+    return r;
+}
+__device__ __forceinline__ Dm dm_mul(const Dm &a, const Dm &b) {
+    Dm r;
+    r.v = ff_mul(a.v, b.v);
+#pragma unroll
+    for (int k = 0; k < kNG; ++k) r.d[k] = fmaf(a.d[k], b.v.hi, a.v.hi * b.d[k]);
+    return r;
+}
+__device__ __forceinline__ Dm dm_scl(const Dm &a, ff s) {
+    Dm r;
+    r.v = ff_mul(a.v, s);
+#pragma unroll
+    for (int k = 0; k < kNG; ++k) r.d[k] = a.d[k] * s.hi;
+    return r;
+}
+__device__ __forceinline__ Dm dm_scl(const Dm &a, float s) {
+    Dm r;
+    r.v = ff_mul(a.v, s);
+#pragma unroll
+    for (int k = 0; k < kNG; ++k) r.d[k] = a.d[k] * s;
     return r;
 }
 __device__ __forceinline__ Dm dm_div(const Dm &a, const Dm &b) {
     Dm r;
-    const double ib = rcp64(b.v);
-    r.v = a.v * ib;
-    const float ibf = (float)ib, rv = (float)r.v;
+    r.v = ff_div(a.v, b.v);
+    const float ib = 1.0f / b.v.hi;
 #pragma unroll
-    for (int k = 0; k < kNG; ++k) r.d[k] = (a.d[k] - rv * b.d[k]) * ibf;
+    for (int k = 0; k < kNG; ++k) r.d[k] = (a.d[k] - r.v.hi * b.d[k]) * ib;
+    return r;
+}
+__device__ __forceinline__ Dm dm_divc(const Dm &a, ff c) {
+    Dm r;
+    r.v = ff_div(a.v, c);
+    const float ic = 1.0f / c.hi;
+#pragma unroll
+    for (int k = 0; k < kNG; ++k) r.d[k] = a.d[k] * ic;
     return r;
 }
 __device__ __forceinline__ Dm dm_sqrt(const Dm &a) {
     Dm r;
-    const double is = a.v > 0.0 ? rsqrt64(a.v) : 0.0;
-    r.v = a.v * is;
-    const float h = (float)(0.5 * is);
+    r.v = ff_sqrt(a.v);
+    const float h = r.v.hi > 0.0f ? 0.5f / r.v.hi : 0.0f;
 #pragma unroll
     for (int k = 0; k < kNG; ++k) r.d[k] = a.d[k] * h;
     return r;
 }
-__device__ __forceinline__ void dm_sincos(const Dm &a, Dm &sn, Dm &cs) {
-    double s, c;
-    sincos(a.v, &s, &c);
-    sn.v = s;
-    cs.v = c;
-    const float sf = (float)s, cf = (float)c;
+// 1 / sqrt(a), a > 0: d(a^-1/2) = -a^-3/2 da / 2
+__device__ __forceinline__ Dm dm_rsqrt(const Dm &a) {
+    Dm r;
+    r.v = ff_rsqrt(a.v);
+    const float h = -0.5f * r.v.hi * r.v.hi * r.v.hi;
 #pragma unroll
-    for (int k = 0; k < kNG; ++k) {
-        sn.d[k] = cf * a.d[k];
-        cs.d[k] = -sf * a.d[k];
-    }
+    for (int k = 0; k < kNG; ++k) r.d[k] = a.d[k] * h;
+    return r;
 }
-__device__ __forceinline__ Dm3 dm3_c(d3 a) { return {dm_c(a.x), dm_c(a.y), dm_c(a.z)}; }
-__device__ __forceinline__ Dm3 dm3_add(const Dm3 &a, const Dm3 &b) {
-    return {dm_add(a.x, b.x), dm_add(a.y, b.y), dm_add(a.z, b.z)};
-}
+__device__ __forceinline__ Dm3 dm3_c(const ff3 &a) { return {dm_c(a.x), dm_c(a.y), dm_c(a.z)}; }
 __device__ __forceinline__ Dm3 dm3_sub(const Dm3 &a, const Dm3 &b) {
     return {dm_sub(a.x, b.x), dm_sub(a.y, b.y), dm_sub(a.z, b.z)};
+}
+// c - a for a constant c
+__device__ __forceinline__ Dm3 dm3_csub(const ff3 &c, const Dm3 &a) {
+    return {dm_add(dm_neg(a.x), dm_c(c.x)), dm_add(dm_neg(a.y), dm_c(c.y)),
+            dm_add(dm_neg(a.z), dm_c(c.z))};
 }
 __device__ __forceinline__ Dm3 dm3_scl(const Dm3 &a, const Dm &s) {
     return {dm_mul(a.x, s), dm_mul(a.y, s), dm_mul(a.z, s)};
 }
+// a + s b
+__device__ __forceinline__ Dm3 dm3_axpy(const Dm3 &a, const Dm3 &b, const Dm &s) {
+    return {dm_add(a.x, dm_mul(b.x, s)), dm_add(a.y, dm_mul(b.y, s)),
+            dm_add(a.z, dm_mul(b.z, s))};
+}
 __device__ __forceinline__ Dm dm3_dot(const Dm3 &a, const Dm3 &b) {
     return dm_add(dm_add(dm_mul(a.x, b.x), dm_mul(a.y, b.y)), dm_mul(a.z, b.z));
 }
-__device__ __forceinline__ Dm dm3_dotc(const Dm3 &a, d3 b) {
+__device__ __forceinline__ Dm dm3_dotc(const Dm3 &a, const ff3 &b) {
     return dm_add(dm_add(dm_scl(a.x, b.x), dm_scl(a.y, b.y)), dm_scl(a.z, b.z));
 }
-// Rodrigues rotation of v about the fixed unit axis u by the angle phi.
-__device__ __forceinline__ Dm3 dm3_rot(d3 u, const Dm &phi, const Dm3 &v) {
-    Dm sn, cs;
-    dm_sincos(phi, sn, cs);
-    const Dm uv = dm3_dotc(v, u);
-    const Dm k = dm_mul(uv, dm_sub(dm_c(1.0), cs));
-    const Dm3 uxv = {dm_sub(dm_scl(v.z, u.y), dm_scl(v.y, u.z)),
-                     dm_sub(dm_scl(v.x, u.z), dm_scl(v.z, u.x)),
-                     dm_sub(dm_scl(v.y, u.x), dm_scl(v.x, u.y))};
-    Dm3 r = dm3_add(dm3_scl(v, cs), dm3_scl(uxv, sn));
-    return dm3_add(r, {dm_scl(k, u.x), dm_scl(k, u.y), dm_scl(k, u.z)});
+__device__ __forceinline__ Dm dm3_dotf(const Dm3 &a, float bx, float by, float bz) {
+    return dm_add(dm_add(dm_scl(a.x, bx), dm_scl(a.y, by)), dm_scl(a.z, bz));
 }
+// reflection about the unit normal n, renormalised: the tangent of the
+// normal does not keep |d| = 1 to first order by itself
 __device__ __forceinline__ Dm3 dm3_reflect_unit(const Dm3 &d, const Dm3 &n) {
-    const Dm k = dm_scl(dm3_dot(d, n), 2.0);
-    Dm3 r = dm3_sub(d, dm3_scl(n, k));
-    const Dm inv = dm_div(dm_c(1.0), dm_sqrt(dm3_dot(r, r)));
-    return dm3_scl(r, inv);
+    const Dm k = dm_scl(dm3_dot(d, n), -2.0f);
+    const Dm3 r = dm3_axpy(d, n, k);
+    return dm3_scl(r, dm_rsqrt(dm3_dot(r, r)));
 }
-__device__ __forceinline__ Dm dm_theta(const GradView &gv, int k) {
-    Dm r = dm_c(gv.theta[k]);
-    r.d[k] = 1.0f;
+// component c of tile centre C(theta) with its tangents in alpha_i, beta_i
+// (ka = 2 i for i < 4, else -1) and R
+__device__ __forceinline__ Dm tile_centre(const DevTileDual &T, int c, int ka) {
+    Dm r;
+    r.v = {T.c_hi[c], T.c_lo[c]};
+#pragma unroll
+    for (int k = 0; k < kNG; ++k)
+        r.d[k] = k == 8                     ? T.dc_dr[c]
+                 : k == ka                  ? T.dc_dalpha[c]
+                 : (ka >= 0 && k == ka + 1) ? T.dc_dbeta[c]
+                                            : 0.0f;
     return r;
 }
 
 __device__ void replay_dual(const SceneView &sc, const GradView &gv, const EmitView &em,
                             const RefineRec &rr, uint32_t j, Dm &u_out, Dm &v_out) {
     const TrackRec tr = em.tracks[rr.index];
-    const TracksView &tv = gv.tracks;
-    // emission: n beta = 1 + (n - 1) beta - (1 - beta), tangent in n - 1
-    const double p = tv.p[rr.index], m = tv.mass[rr.index];
-    const double E = sqrt(p * p + m * m);
-    const double omb = (m == 0.0) ? 0.0 : (m * m) / (E * (E + p));
-    const double beta = 1.0 - omb;
-    const Dm nbm1 = dm_sub(dm_scl(dm_theta(gv, 9), beta), dm_c(omb));
-    const Dm nb = dm_add(dm_c(1.0), nbm1);
-    Dm ct, st;
-    if (nbm1.v > 0.0) {
-        ct = dm_div(dm_c(1.0), nb);
-        st = dm_mul(dm_sqrt(dm_mul(nbm1, dm_add(nb, dm_c(1.0)))), ct);
-    } else {   // below threshold: the emission leaves along the track
-        ct = dm_c(1.0);
-        st = dm_c(0.0);
-    }
-    const u4 w0 = philox10(0u, j, tr.id, tr.event, em.key0, em.key1);
-    const d3 t = normalized(mkd(tr.rx, tr.ry, tr.rz));
-    const double s = u24d(w0.x) * (double)tr.len;
-    Dm3 o = dm3_c(mkd(fma(t.x, s, (double)tr.x), fma(t.y, s, (double)tr.y),
-                      fma(t.z, s, (double)tr.z)));
-    double sp, cp;
-    sincospi(2.0 * u24d(w0.y), &sp, &cp);
-    d3 e1, e2;
-    basis_d(t, e1, e2);
-    const d3 rr_dir = mkd(cp * e1.x + sp * e2.x, cp * e1.y + sp * e2.y, cp * e1.z + sp * e2.z);
-    Dm3 d = dm3_add(dm3_scl(dm3_c(t), ct), dm3_scl(dm3_c(rr_dir), st));
-    const Dm R = dm_theta(gv, 8);
+    const double2 cs = em.cos_sin[rr.index];
+    // emission as in the refinement replay; the tangent of the Cherenkov
+    // angle in n - 1: cos = 1 / (n beta) gives d cos / dn = -cos / n and
+    // d sin / dn = -cos (d cos / dn) / sin
+    ff3 o0, t;
+    ff sp, cp;
+    emit_start_ff(tr, j, em, o0, t, sp, cp);
+    const ff3 r = azimuth_dir_ff(t, sp, cp);
+    const ff ct = ff_from_double(cs.x), st = ff_from_double(cs.y);
+    const ff3 d0 = ff3_normalized({ff_add(ff_mul(t.x, ct), ff_mul(r.x, st)),
+                                   ff_add(ff_mul(t.y, ct), ff_mul(r.y, st)),
+                                   ff_add(ff_mul(t.z, ct), ff_mul(r.z, st))});
+    const float dct = -ct.hi / (1.0f + (float)gv.theta[9]);
+    const float dst = st.hi > 0.0f ? -ct.hi * dct / st.hi : 0.0f;
+    Dm3 o = dm3_c(o0), d = dm3_c(d0);
+    d.x.d[9] = t.x.hi * dct + r.x.hi * dst;
+    d.y.d[9] = t.y.hi * dct + r.y.hi * dst;
+    d.z.d[9] = t.z.hi * dct + r.z.hi * dst;
+    Dm R = dm_c(ff_from_double(gv.theta[8]));
+    R.d[8] = 1.0f;
+    const Dm inv_R = dm_div(dm_c(ffv(1.0f)), R);
     for (int k = 0; k < rr.n_path; ++k) {
         const int prim = rr.path[k];
         Dm3 n;
         if (prim < sc.n_tiles) {
-            const DevTileNom &T = gv.nom[prim];
-            const Dm al = prim < 4 ? dm_theta(gv, 2 * prim) : dm_c(0.0);
-            const Dm be = prim < 4 ? dm_theta(gv, 2 * prim + 1) : dm_c(0.0);
-            const Dm3 a = dm3_rot(mkd(T.e2x, T.e2y, T.e2z), be,
-                                  dm3_rot(mkd(T.e1x, T.e1y, T.e1z), al,
-                                          dm3_c(mkd(T.ax, T.ay, T.az))));
-            const Dm3 C = dm3_sub(dm3_c(mkd(T.px, T.py, T.pz)), dm3_scl(a, R));
+            const DevTileDual &T = gv.tiles[prim];
+            const int ka = prim < 4 ? 2 * prim : -1;
+            const Dm3 C = {tile_centre(T, 0, ka), tile_centre(T, 1, ka), tile_centre(T, 2, ka)};
             const Dm3 w = dm3_sub(o, C);
             const Dm b = dm3_dot(w, d);
             const Dm c = dm_sub(dm3_dot(w, w), dm_mul(R, R));
             const Dm sq = dm_sqrt(dm_sub(dm_mul(b, b), c));
-            const Dm tt = b.v <= 0.0 ? dm_sub(sq, b) : dm_div(c, dm_sub(dm_scl(b, -1.0), sq));
-            o = dm3_add(o, dm3_scl(d, tt));
-            n = dm3_scl(dm3_sub(C, o), dm_div(dm_c(1.0), R));
+            // the concave side's exit root, in the form free of cancellation
+            const Dm tt = b.v.hi <= 0.0f ? dm_sub(sq, b) : dm_div(c, dm_sub(dm_neg(b), sq));
+            o = dm3_axpy(o, d, tt);
+            n = dm3_scl(dm3_sub(C, o), inv_R);
         } else if (prim < sc.tri_prim_base) {
-            const DevRectD &Rc = sc.rects_d[prim - sc.n_tiles];
-            const d3 nn = mkd(Rc.nx, Rc.ny, Rc.nz);
-            const Dm tt = dm_div(dm3_dotc(dm3_sub(dm3_c(mkd(Rc.ox, Rc.oy, Rc.oz)), o), nn),
+            const DevRect &Rc = sc.rects[prim - sc.n_tiles];
+            const ff3 nn = ff3v(Rc.nx, Rc.ny, Rc.nz);
+            const Dm tt = dm_div(dm3_dotc(dm3_csub(ff3v(Rc.ox, Rc.oy, Rc.oz), o), nn),
                                  dm3_dotc(d, nn));
-            o = dm3_add(o, dm3_scl(d, tt));
+            o = dm3_axpy(o, d, tt);
             n = dm3_c(nn);
         } else {
             const int k_tri = prim - sc.tri_prim_base;
             const DevTri T = load_tri(sc.tris + k_tri);
-            const d3 v0 = mkd(T.v0x, T.v0y, T.v0z), v1 = mkd(T.v1x, T.v1y, T.v1z),
-                     v2 = mkd(T.v2x, T.v2y, T.v2z);
-            const d3 ea = v1 - v0, eb = v2 - v0;
-            const d3 ngr = crossd(ea, eb);
-            const d3 ng = ngr * rsqrt64(dotd(ngr, ngr));
-            const Dm tt = dm_div(dm3_dotc(dm3_sub(dm3_c(v0), o), ng), dm3_dotc(d, ng));
-            o = dm3_add(o, dm3_scl(d, tt));
+            const ff3 v0 = ff3v(T.v0x, T.v0y, T.v0z);
+            const ff3 e1 = ff3_diff(T.v1x, T.v1y, T.v1z, T.v0x, T.v0y, T.v0z);
+            const ff3 e2 = ff3_diff(T.v2x, T.v2y, T.v2z, T.v0x, T.v0y, T.v0z);
+            const ff3 ngt = ff3_cross(e1, e2);
+            const Dm tt = dm_div(dm3_dotc(dm3_csub(v0, o), ngt), dm3_dotc(d, ngt));
+            o = dm3_axpy(o, d, tt);
             const DevMaterial &M = sc.materials[T.material];
             if ((M.flags & RICH_MAT_SMOOTH) && sc.tri_normals) {
                 const Dm3 q = dm3_sub(o, dm3_c(v0));
-                const double d00 = dotd(ea, ea), d01 = dotd(ea, eb), d11 = dotd(eb, eb);
-                const Dm d20 = dm3_dotc(q, ea), d21 = dm3_dotc(q, eb);
-                const double iden = rcp64(d00 * d11 - d01 * d01);
-                const Dm b1 = dm_scl(dm_sub(dm_scl(d20, d11), dm_scl(d21, d01)), iden);
-                const Dm b2 = dm_scl(dm_sub(dm_scl(d21, d00), dm_scl(d20, d01)), iden);
-                const Dm b0 = dm_sub(dm_sub(dm_c(1.0), b1), b2);
+                const ff d00 = ff3_dot(e1, e1), d01 = ff3_dot(e1, e2), d11 = ff3_dot(e2, e2);
+                const Dm d20 = dm3_dotc(q, e1), d21 = dm3_dotc(q, e2);
+                const ff den = ff_sub(ff_mul(d00, d11), ff_mul(d01, d01));
+                const Dm b1 = dm_divc(dm_sub(dm_scl(d20, d11), dm_scl(d21, d01)), den);
+                const Dm b2 = dm_divc(dm_sub(dm_scl(d21, d00), dm_scl(d20, d01)), den);
+                const Dm b0 = dm_addf(dm_neg(dm_add(b1, b2)), 1.0f);
                 const float *N = sc.tri_normals + 9 * (int64_t)k_tri;
-                const Dm3 nn = dm3_add(
-                    dm3_add(dm3_scl(dm3_c(mkd(N[0], N[1], N[2])), b0),
-                            dm3_scl(dm3_c(mkd(N[3], N[4], N[5])), b1)),
-                    dm3_scl(dm3_c(mkd(N[6], N[7], N[8])), b2));
-                n = dm3_scl(nn, dm_div(dm_c(1.0), dm_sqrt(dm3_dot(nn, nn))));
+                const Dm3 m = {
+                    dm_add(dm_add(dm_scl(b0, N[0]), dm_scl(b1, N[3])), dm_scl(b2, N[6])),
+                    dm_add(dm_add(dm_scl(b0, N[1]), dm_scl(b1, N[4])), dm_scl(b2, N[7])),
+                    dm_add(dm_add(dm_scl(b0, N[2]), dm_scl(b1, N[5])), dm_scl(b2, N[8]))};
+                n = dm3_scl(m, dm_rsqrt(dm3_dot(m, m)));
             } else {
-                n = dm3_c(ng);
+                n = dm3_c(ff3_normalized(ngt));
             }
         }
         d = dm3_reflect_unit(d, n);
     }
-    const DevRectD &Rc = sc.rects_d[rr.det_rect];
-    const d3 nn = mkd(Rc.nx, Rc.ny, Rc.nz);
-    const d3 O = mkd(Rc.ox, Rc.oy, Rc.oz);
-    const Dm tt = dm_div(dm3_dotc(dm3_sub(dm3_c(O), o), nn), dm3_dotc(d, nn));
-    const Dm3 q = dm3_sub(dm3_add(o, dm3_scl(d, tt)), dm3_c(O));
-    u_out = dm3_dotc(q, mkd(Rc.ux, Rc.uy, Rc.uz));
-    v_out = dm3_dotc(q, mkd(Rc.vx, Rc.vy, Rc.vz));
+    const DevRect &Rc = sc.rects[rr.det_rect];
+    const ff3 nn = ff3v(Rc.nx, Rc.ny, Rc.nz);
+    const ff3 O = ff3v(Rc.ox, Rc.oy, Rc.oz);
+    const Dm tt = dm_div(dm3_dotc(dm3_csub(O, o), nn), dm3_dotc(d, nn));
+    const Dm3 q = dm3_sub(dm3_axpy(o, d, tt), dm3_c(O));
+    u_out = dm3_dotf(q, Rc.ux, Rc.uy, Rc.uz);
+    v_out = dm3_dotf(q, Rc.vx, Rc.vy, Rc.vz);
+}
+
+// Box-Muller pair of the photon's smear draws (words x, y of draw block 3)
+// in FP32: u1 = (k + 1/2) 2^-24 from the leading 24 bits k of x, and
+// log u1 as logf(u1) below 1/2 and log1pf(-(1 - u1)) above, where u1 and
+// 1 - u1 are both exact in FP32, so -2 log u1 keeps its relative precision
+// as u1 approaches 1.
+__device__ __forceinline__ void smear_pair_f32(u4 w3, float &g1, float &g2) {
+    const uint32_t k = w3.x >> 8;
+    const float lg = k < (1u << 23)
+                         ? logf((float)(2u * k + 1u) * 0x1p-25f)
+                         : log1pf(-(float)(2u * ((1u << 24) - k) - 1u) * 0x1p-25f);
+    const float rad = sqrtf(-2.0f * lg);
+    float s, c;
+    sincospif(2.0f * u24f(w3.y), &s, &c);
+    g1 = rad * c;
+    g2 = rad * s;
 }
 
 constexpr int kAdjThreads = 128;
@@ -1913,11 +1966,10 @@ k_adjoint(SceneView sc, EmitView em, TraceParams P, GradView gv, Counters *ctr) 
         const RefineRec rr = P.refine[i];
         Dm u, v;
         replay_dual(sc, gv, em, rr, h.photon, u, v);
-        const DevRect Rc = sc.rects[rr.det_rect];
         int ix, iy;
-        pixel_of(Rc, u.v, v.v, ix, iy);
-        h.u = u.v;
-        h.v = v.v;
+        pixel_of_ff(sc.rects[rr.det_rect], u.v, v.v, ix, iy);
+        h.u = ff_to_double(u.v);
+        h.v = ff_to_double(v.v);
         h.ix = (uint16_t)ix;
         h.iy = (uint16_t)iy;
         P.hits[i] = h;
@@ -1925,18 +1977,18 @@ k_adjoint(SceneView sc, EmitView em, TraceParams P, GradView gv, Counters *ctr) 
         const float4 tg = gv.targets[(int64_t)rr.index * gv.n_planes + h.plane];
         if (tg.w > 0.0f) {
             const u4 w3 = philox10(3u, h.photon, h.track, h.event, em.key0, em.key1);
-            const double u1 = ((double)(w3.x >> 8) + 0.5) * 5.9604644775390625e-8;
-            const double rr_ = sqrt(-2.0 * log(u1));
-            double s2, c2;
-            sincospi(2.0 * u24d(w3.y), &s2, &c2);
-            const Dm du = dm_add(u, dm_c(gv.sigma * rr_ * c2 - (double)tg.x));
-            const Dm dv = dm_add(v, dm_c(gv.sigma * rr_ * s2 - (double)tg.y));
+            float g1, g2;
+            smear_pair_f32(w3, g1, g2);
+            const ff sg = ff_from_double(gv.sigma);
+            const Dm du = dm_addf(dm_addf(u, -tg.x), sg.hi * g1);
+            const Dm dv = dm_addf(dm_addf(v, -tg.y), sg.hi * g2);
             const Dm dist = dm_sqrt(dm_add(dm_mul(du, du), dm_mul(dv, dv)));
-            const Dm rho = dm_scl(dm_sub(dist, dm_c((double)tg.z)), 1.0 / gv.sigma);
-            acc[0] += rho.v * rho.v;
+            const Dm rho = dm_divc(dm_addf(dist, -tg.z), sg);
+            const double rv = ff_to_double(rho.v);
+            acc[0] += rv * rv;
             acc[1] += 1.0;
 #pragma unroll
-            for (int k = 0; k < kNG; ++k) acc[2 + k] += 2.0 * rho.v * (double)rho.d[k];
+            for (int k = 0; k < kNG; ++k) acc[2 + k] += 2.0 * rv * (double)rho.d[k];
         }
     }
     // block reduction, one FP64 atomic per accumulator per block
