@@ -31,6 +31,12 @@ struct ff {
 
 __device__ __forceinline__ ff ffv(float a) { return {a, 0.0f}; }
 
+// A double constant as a double-word, for constexpr use (evaluated by the
+// compiler: no FP64 operation at run time).
+__host__ __device__ constexpr ff ffc(double x) {
+    return {(float)x, (float)(x - (double)(float)x)};
+}
+
 __device__ __forceinline__ ff two_sum(float a, float b) {
     const float s = __fadd_rn(a, b);
     const float ap = __fsub_rn(s, b);
@@ -135,6 +141,14 @@ __device__ __forceinline__ ff ff_from_double(double a) {
 }
 
 __device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+
+// comparisons of normalised double-words
+__device__ __forceinline__ bool ff_lt(ff a, ff b) {
+    return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+__device__ __forceinline__ bool ff_le(ff a, ff b) {
+    return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo);
+}
 
 // floor of a double-word (the pixel index)
 __device__ __forceinline__ float ff_floor(ff a) {

@@ -30,11 +30,11 @@ namespace rich {
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kYieldThreads = 256;   // tracks per scan group / scan block
 constexpr int kYieldBlock = 32;      // threads per yield block: one warp, so
-                                     // the FP64 Poisson chains of a small
-                                     // batch spread over as many SMs as
-                                     // possible (2 FP64 lanes per SM)
+                                     // the per-track chains of a small batch
+                                     // spread over as many SMs as possible
 constexpr double kAlpha = 1.0 / 137.035999;
 constexpr double kPi = 3.14159265358979323846;
+constexpr ff k2PiAlpha = ffc(2.0 * kPi * kAlpha);
 
 int yield_block_threads() { return kYieldThreads; }
 
@@ -58,6 +58,7 @@ struct TrackStream {
         ++word;
         return u24d(v);
     }
+    __device__ float nextf() { return (float)next(); }   // exact: 24-bit uniforms
 };
 
 // FP64 natural logarithm of a positive normal x, table-driven after Tang
@@ -87,58 +88,143 @@ __device__ __forceinline__ double log64(double x) {
     return hi + (r + fma(r * r, q, lo));
 }
 
+// ------------------------------------ double-word per-track arithmetic
+// The per-track chain of the yield kernel (beta, angle, Frank-Tamm mean,
+// Poisson draw) is one dependent sequence per thread. An FP64 instruction
+// holds a warp for ~64 cycles on this GPU whatever its active lanes, so the
+// chain runs in double-word FP32 arithmetic (rich_ff.cuh, ~2^-44 relative
+// per operation against FP64's 2^-53): a count can differ from the FP64
+// draw only if a floor or a rejection test lands within ~1e-10 of its
+// threshold.
+
+constexpr ff kLn2 = ffc(0.69314718055994530942);
+
+// log of a double-word x with normal hi (2^-126 <= hi < 2^127), table-driven
+// as log64 (Tang): x = 2^e m with m in [1, 2) (both parts scaled exactly),
+// F the FP32 reciprocal of the centre of m's 1/128-wide interval (top 7
+// mantissa bits of hi), r = m F - 1 (|r| < 2^-7); log x = e log 2 - log F +
+// log(1 + r), with r - r^2/2 in double-word and the series' tail
+// r^3 (1/3 - r/4 + r^2/5 - r^3/6 + r^4/7) in FP32 (below 2^-45). x = 0
+// gives -infinity.
+__device__ __forceinline__ ff ff_log(ff x) {
+    if (!(x.hi > 0.0f)) return {__int_as_float((int)0xff800000), 0.0f};
+    const int bits = __float_as_int(x.hi);
+    const int e = ((bits >> 23) & 0xFF) - 127;
+    const int i = (bits >> (23 - kLogTableBits)) & ((1 << kLogTableBits) - 1);
+    const float sc = __int_as_float((127 - e) << 23);           // 2^-e
+    const ff m = {x.hi * sc, x.lo * sc};
+    const float F = __ldg(&g_log_tab_f[i][0]);
+    const ff lc = {__ldg(&g_log_tab_f[i][1]), __ldg(&g_log_tab_f[i][2])};
+    const ff r = ff_add(ff_mul(m, F), -1.0f);
+    const float z = r.hi;
+    const float tail =
+        z * z * z * (1.0f / 3.0f - z * (0.25f - z * (0.2f - z * (1.0f / 6.0f - z * (1.0f / 7.0f)))));
+    const ff r2 = ff_mul(r, r);
+    const ff l1p = ff_add(ff_sub(r, ff{0.5f * r2.hi, 0.5f * r2.lo}), tail);
+    const float ef = (float)e;
+    const ff el = ff_add(two_prod(ef, kLn2.hi), ef * kLn2.lo);
+    return ff_add(ff_add(el, lc), l1p);
+}
+
+// e^-x for 0 <= x < 80: x = k log 2 + r, |r| <= log(2)/2 + 2^-20, e^-r by
+// its Taylor series (terms 8..12 in FP32, below 6e-9 of the sum; 0..7 in
+// double-word Horner steps; truncation below 2^-52), then the exact
+// scaling by 2^-k.
+__device__ __forceinline__ ff ff_exp_neg(ff x) {
+    const float kf = rintf(x.hi * 1.44269504f);
+    const ff r = ff_sub(x, ff_add(two_prod(kf, kLn2.hi), kf * kLn2.lo));
+    const ff z = ff_neg(r);
+    const float zh = z.hi;
+    const float q = 1.0f / 40320.0f +
+                    zh * (1.0f / 362880.0f +
+                          zh * (1.0f / 3628800.0f + zh * (1.0f / 39916800.0f + zh * (1.0f / 479001600.0f))));
+    constexpr ff c7 = ffc(1.0 / 5040.0), c6 = ffc(1.0 / 720.0), c5 = ffc(1.0 / 120.0),
+                 c4 = ffc(1.0 / 24.0), c3 = ffc(1.0 / 6.0);
+    ff s = ff_add(c7, zh * q);
+    s = ff_add(ff_mul(s, z), c6);
+    s = ff_add(ff_mul(s, z), c5);
+    s = ff_add(ff_mul(s, z), c4);
+    s = ff_add(ff_mul(s, z), c3);
+    s = ff_add(ff_mul(s, z), 0.5f);
+    s = ff_add(ff_mul(s, z), 1.0f);
+    s = ff_add(ff_mul(s, z), 1.0f);
+    const float sc = __int_as_float((127 - (int)kf) << 23);      // 2^-k
+    return {s.hi * sc, s.lo * sc};
+}
+
+// floor of a double-word as an integer (any magnitude below 2^62)
+__device__ __forceinline__ int64_t ff_floor_i64(ff a) {
+    const float f = floorf(a.hi);
+    if (f != a.hi) return (int64_t)f;     // hi not an integer: |hi| < 2^23, lo cannot cross
+    return (int64_t)a.hi + (int64_t)floorf(a.lo);
+}
+
+// an integer (|k| < 2^48) as a double-word, exactly
+__device__ __forceinline__ ff ff_from_i64(int64_t k) {
+    const float hi = (float)k;
+    return fast_two_sum(hi, (float)(k - (int64_t)hi));
+}
+
 // log k! (k >= 0): the table below 2048, Stirling's series above (four
-// correction terms, truncation < 1/(1188 k^9)).
-__device__ __forceinline__ double log_factorial(double kd) {
-    if (kd < (double)kLogFactTable) return __ldg(&g_logfact[(int)kd]);
-    constexpr double kHalfLog2Pi = 0.91893853320467274178;
-    const double x = kd + 1.0, r = rcp64(x), r2 = r * r;
-    const double series = r * (1.0 / 12.0 - r2 * (1.0 / 360.0 - r2 * (1.0 / 1260.0 -
-                                                                     r2 * (1.0 / 1680.0))));
-    return (x - 0.5) * log64(x) - x + kHalfLog2Pi + series;
+// correction terms in FP32, truncation < 1/(1188 k^9)).
+__device__ __forceinline__ ff ff_log_factorial(int64_t k) {
+    if (k < kLogFactTable) return {__ldg(&g_logfact_ff[k][0]), __ldg(&g_logfact_ff[k][1])};
+    constexpr ff kHalfLog2Pi = ffc(0.91893853320467274178);
+    const ff x = ff_from_i64(k + 1);
+    const float r = 1.0f / x.hi, r2 = r * r;
+    const float series =
+        r * (1.0f / 12.0f - r2 * (1.0f / 360.0f - r2 * (1.0f / 1260.0f - r2 * (1.0f / 1680.0f))));
+    ff v = ff_mul(ff_add(x, -0.5f), ff_log(x));
+    v = ff_sub(v, x);
+    v = ff_add(v, kHalfLog2Pi);
+    return ff_add(v, series);
 }
 
 // Poisson(mu): CDF inversion (smallest k with u < F(k)) below mean 10; the
 // PTRS transformed rejection sampler (Hoermann 1993) above, at most 64
-// trials, then round(mu). The GPU's FP64 pipe is slow, so the rejection
-// test log V + log(1/alpha) - log(a/us^2 + b) <= -mu + k log mu - log k! is
-// taken as log(V us^2 / (alpha (a + b us^2))) with one table-driven log and
-// log k! from a table.
-__device__ int64_t poisson_draw(double mu, TrackStream &s) {
-    if (!(mu > 0.0)) return 0;
-    if (mu < 10.0) {
-        double u = s.next();
-        double pk = exp(-mu), F = pk;
+// trials, then round(mu); in double-word arithmetic. The rejection test
+// log V + log(1/alpha) - log(a/us^2 + b) <= -mu + k log mu - log k! is
+// taken as log(V us^2 / (alpha (a + b us^2))) with one logarithm and log k!
+// from a table. The uniforms are 24-bit, exact in FP32, as are U, us and
+// us^2 (the last as a double-word).
+__device__ int64_t poisson_draw(ff mu, TrackStream &s) {
+    if (!(mu.hi > 0.0f)) return 0;
+    if (ff_lt(mu, ffv(10.0f))) {
+        const ff u = ffv(s.nextf());
+        ff pk = ff_exp_neg(mu), F = pk;
         int64_t k = 0;
-        while (F <= u && k < 1000) {
+        while (ff_le(F, u) && k < 1000) {
             k += 1;
-            pk *= mu / (double)k;
-            F += pk;
+            pk = ff_mul(pk, ff_div(mu, ffv((float)k)));
+            F = ff_add(F, pk);
         }
         return k;
     }
-    // per-track constants; those that set the candidate k and the
-    // quick-accept bound in IEEE arithmetic
-    const double smu = sqrt(mu), lmu = log64(mu);
-    const double b = 0.931 + 2.53 * smu;
-    const double a = -0.059 + 0.02483 * b;
-    const double inv_alpha = 1.1239 + 1.1328 * rcp64(b - 3.4);
-    const double v_r = 0.9277 - 3.6224 / (b - 2.0);
+    constexpr ff kB0 = ffc(0.931), kB1 = ffc(2.53), kA0 = ffc(-0.059), kA1 = ffc(0.02483),
+                 kI0 = ffc(1.1239), kI1 = ffc(1.1328), kI2 = ffc(3.4), kV0 = ffc(0.9277),
+                 kV1 = ffc(3.6224), kK = ffc(0.43), kUs0 = ffc(0.07), kUs1 = ffc(0.013);
+    const ff smu = ff_sqrt(mu), lmu = ff_log(mu);
+    const ff b = ff_add(kB0, ff_mul(kB1, smu));
+    const ff a = ff_add(kA0, ff_mul(kA1, b));
+    const ff inv_alpha = ff_add(kI0, ff_div(kI1, ff_sub(b, kI2)));
+    const ff v_r = ff_sub(kV0, ff_div(kV1, ff_add(b, -2.0f)));
+    const ff two_a = {2.0f * a.hi, 2.0f * a.lo};
+    const ff mu_k = ff_add(mu, kK);
     for (int trial = 0; trial < 64; ++trial) {
-        double U = s.next() - 0.5;
-        double V = s.next();
-        double us = 0.5 - fabs(U);
-        if (!(us > 0.0)) continue;
-        double kd = floor((2.0 * a / us + b) * U + mu + 0.43);
-        if (!(kd >= 0.0)) continue;
-        if (us >= 0.07 && V <= v_r) return (int64_t)kd;
-        if (us < 0.013 && V > us) continue;
-        const double us2 = us * us;
-        const double lhs = log64(V * inv_alpha * us2 * rcp64(fma(b, us2, a)));
-        const double rhs = -mu + kd * lmu - log_factorial(kd);
-        if (lhs <= rhs) return (int64_t)kd;
+        const float U = s.nextf() - 0.5f;
+        const float V = s.nextf();
+        const float us = 0.5f - fabsf(U);
+        if (!(us > 0.0f)) continue;
+        const int64_t k = ff_floor_i64(ff_add(ff_mul(ff_add(ff_div(two_a, ffv(us)), b), U), mu_k));
+        if (k < 0) continue;
+        if (!ff_lt(ffv(us), kUs0) && ff_le(ffv(V), v_r)) return k;
+        if (ff_lt(ffv(us), kUs1) && V > us) continue;
+        const ff us2 = two_prod(us, us);
+        const ff lhs = ff_log(ff_div(ff_mul(ff_mul(inv_alpha, V), us2), ff_add(ff_mul(b, us2), a)));
+        const ff rhs = ff_sub(ff_sub(ff_mul(lmu, ff_from_i64(k)), mu), ff_log_factorial(k));
+        if (ff_le(lhs, rhs)) return k;
     }
-    return (int64_t)floor(mu + 0.5);
+    return ff_floor_i64(ff_add(mu, 0.5f));
 }
 
 // ------------------------------------------------- dispersive radiator
@@ -195,49 +281,52 @@ k_yield(TracksView t, double n_minus_1, double inv_band_mm, uint32_t key0,
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t count = 0;
     if (i < t.n) {
-        // every input of the track in one round of loads, and the direction's
-        // normalisation next to the angle (independent chains the compiler
-        // can interleave)
+        // every input of the track in one round of loads; the double-word
+        // forms of the parameters meanwhile
+        const ff nm1 = ff_from_double(n_minus_1), inv_band = ff_from_double(inv_band_mm);
         const double p = t.p[i], m = t.mass[i], len = t.length[i];
         const float tx = t.x[i], ty = t.y[i], tz = t.z[i];
         const float fdx = t.dx[i], fdy = t.dy[i], fdz = t.dz[i];
         const uint32_t event = t.event[i];
         const uint32_t id = t.id ? t.id[i] : (uint32_t)i;
         const uint32_t n_fixed = t.n_fixed ? t.n_fixed[i] : 0u;
-        const double dx = fdx, dy = fdy, dz = fdz;
-        const double inv = RECS ? rsqrt64(dx * dx + dy * dy + dz * dz) : 0.0;
+        const ff pf = ff_from_double(p), mf = ff_from_double(m), lf = ff_from_double(len);
         // 1 - beta = m^2 / (E (E + p)) keeps n*beta - 1 accurate near 1
-        double E = sqrt(p * p + m * m);
-        double one_minus_beta = (m == 0.0) ? 0.0 : (m * m) / (E * (E + p));
-        double beta = 1.0 - one_minus_beta;
-        double nb_minus_1 = n_minus_1 * beta - one_minus_beta;
-        double cos_t = 1.0, sin_t = 0.0, tan_t = 0.0, mu = 0.0;
-        float disp_span = 0.0f, disp_s2max = 0.0f;
+        const ff E = ff_sqrt(ff_add(ff_mul(pf, pf), ff_mul(mf, mf)));
+        const ff omb = mf.hi == 0.0f ? ffv(0.0f) : ff_div(ff_mul(mf, mf), ff_mul(E, ff_add(E, pf)));
+        const ff beta = ff_add(ff_neg(omb), 1.0f);
+        const ff nbm1 = ff_sub(ff_mul(nm1, beta), omb);
+        ff cos_t = ffv(1.0f), sin_t = ffv(0.0f), mu = ffv(0.0f);
+        float tan_f = 0.0f, disp_span = 0.0f, disp_s2max = 0.0f;
+        double2 cs_out;
         if (model.iso_yield >= 0.0) {
             // isotropic source: mean photons = yield per mm x length
-            mu = len * model.iso_yield;
+            mu = ff_mul(lf, ff_from_double(model.iso_yield));
         } else if (model.dispersion) {
-            // dispersive radiator: Frank-Tamm integral of sin^2 theta(lambda),
+            // dispersive radiator (FP64): Frank-Tamm integral of sin^2 theta(lambda),
             // and the FP32 band and normaliser of the wavelength accept/reject
+            const double E64 = sqrt(p * p + m * m);
+            const double omb64 = (m == 0.0) ? 0.0 : (m * m) / (E64 * (E64 + p));
             double xt = 0.0;
-            mu = len * disp_yield_per_mm(model, beta, one_minus_beta, lam_min, lam_max, xt);
+            mu = ff_from_double(len * disp_yield_per_mm(model, 1.0 - omb64, omb64, lam_min,
+                                                         lam_max, xt));
             const float inv1 = __fdiv_rn(1.0f, (float)lam_min);
             const float inv2 = __fdiv_rn(1.0f, (float)lam_max);
             const float xlo = (float)xt > inv2 ? (float)xt : inv2;
             disp_span = __fsub_rn(inv1, xlo);
-            tan_t = (double)(float)one_minus_beta;          // stored as 1 - beta
+            tan_f = (float)omb64;                            // stored as 1 - beta
             disp_s2max = disp_s2_f32(model.disp_a, __fdiv_rn(1.0f, model.disp_lambda0),
-                                     (float)one_minus_beta, (float)lam_min);
-            cos_t = beta;                                    // (beta, 1 - beta) in FP64
-            sin_t = one_minus_beta;
-        } else if (nb_minus_1 > 0.0) {
-            double nb = 1.0 + nb_minus_1;
-            double tan2 = nb_minus_1 * (nb + 1.0);      // (n beta)^2 - 1
-            tan_t = sqrt(tan2);
-            cos_t = 1.0 / nb;
-            sin_t = tan_t * cos_t;
-            mu = len * 2.0 * kPi * kAlpha * (sin_t * sin_t) * inv_band_mm;
+                                     (float)omb64, (float)lam_min);
+            cs_out = make_double2(1.0 - omb64, omb64);       // (beta, 1 - beta) in FP64
+        } else if (nbm1.hi > 0.0f) {
+            const ff nb = ff_add(nbm1, 1.0f);
+            const ff tan_t = ff_sqrt(ff_mul(nbm1, ff_add(nb, 1.0f)));   // (n beta)^2 - 1
+            cos_t = ff_div(ffv(1.0f), nb);
+            sin_t = ff_mul(tan_t, cos_t);
+            tan_f = tan_t.hi;
+            mu = ff_mul(ff_mul(lf, ff_mul(sin_t, sin_t)), ff_mul(k2PiAlpha, inv_band));
         }
+        if (!model.dispersion) cs_out = make_double2(ff_to_double(cos_t), ff_to_double(sin_t));
         if (t.n_fixed) {
             count = n_fixed;
         } else {
@@ -246,15 +335,17 @@ k_yield(TracksView t, double n_minus_1, double inv_band_mm, uint32_t key0,
             count = (uint32_t)(k > 0xFFFFFFF0ll ? 0xFFFFFFF0ll : k);
         }
         if (RECS) {
+        // the unit direction, rounded to FP32 from its double-word
+        const ff3 tn = ff3_normalized(ff3v(fdx, fdy, fdz));
         TrackRec r;
         r.x = tx;
         r.y = ty;
         r.z = tz;
         r.len = (float)len;
-        r.tx = (float)(dx * inv);
-        r.ty = (float)(dy * inv);
-        r.tz = (float)(dz * inv);
-        r.tan_theta = (float)tan_t;
+        r.tx = tn.x.hi;
+        r.ty = tn.y.hi;
+        r.tz = tn.z.hi;
+        r.tan_theta = tan_f;
         r.rx = fdx;
         r.ry = fdy;
         r.rz = fdz;
@@ -264,7 +355,7 @@ k_yield(TracksView t, double n_minus_1, double inv_band_mm, uint32_t key0,
         r.disp_span = disp_span;
         r.disp_s2max = disp_s2max;
         rec[i] = r;
-        cs[i] = make_double2(cos_t, sin_t);
+        cs[i] = cs_out;
         }
         counts[i] = count;
     }
@@ -551,11 +642,6 @@ struct SmemScene {
     const DevMaterial *materials;
     int n_groups, n_tiles, n_rects;
 };
-
-// a < b for normalised double-words
-__device__ __forceinline__ bool ff_lt(ff a, ff b) {
-    return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
-}
 
 // Tiles: per distinct sphere, the quadratic |w + t d|^2 = R^2 with w = o - C
 // in double-word arithmetic (rich_ff.cuh, ~48 bits; precision policy: the
