@@ -89,11 +89,11 @@ def test_emission_matches_oracle():
 
 def test_poisson_counts_over_wide_mean_range():
     """Photon counts of 500,000 tracks whose Frank-Tamm means span 0 to ~3000
-    (CDF inversion below 10, PTRS above) equal the oracle's exactly. Both
-    draw in FP64; the kernel's per-trial tail (one log, Stirling's series
-    for log k!, Newton reciprocals) differs from the oracle's textbook forms
-    by ~1e-13, so a count could differ only if a rejection test fell that
-    close to its threshold."""
+    (CDF inversion below 10, PTRS above) equal the oracle's exactly. The
+    oracle draws in FP64 with the textbook forms (three logs, lgamma); the
+    kernel in double-word arithmetic (~2^-44 per operation: one table-driven
+    log per trial, log k! from a table), so a count could differ only if a
+    floor or a rejection test fell within ~1e-10 of its threshold."""
     n = 500_000
     rng = np.random.default_rng(11)
     tr = W.pion_tracks(n, seed=11, p_min=0.3, p_max=100.0)
