@@ -514,38 +514,35 @@ def run_adjoint(dev, rank):
 
 
 def run_e2e(ctx, tracks, dev, prec, args, scene, knobs):
-    """Same metric through the public API with host buffers: host->device
-    copy of the step's tracks (one packed pinned buffer), emit + trace,
-    device->host read of the counters (the one synchronisation, which also
-    returns the photon count) and of the hit list, all inside the timed
-    region."""
+    """Same metric through the C ABI with host buffers (rich_run_host): the
+    host->device copy of the step's tracks (one pinned buffer), emit +
+    trace, the counters' read and the device->host copy of the hit list, all
+    inside the timed region (host clock around each synchronous call)."""
     import torch
     from paper_2309_12496_gb300 import rich
-    dt, host = rich.DeviceTracks.packed(tracks, device=dev)
+    host = rich.HostTracks(tracks)
+    dt = rich.DeviceTracks(tracks, device=dev)
     n0 = ctx.emit(dt, 0.0014, seed=7)
     cap = int(n0 * 1.5) + 1024
     out = rich.TraceOutputs(cap, scene.pixels_per_event, len(scene.planes), 1, 0, device=dev)
     hits_host = torch.empty(cap * rich.HIT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
-    h2d = host.numel() * host.element_size()
+    h2d = host.buf.numel() * host.buf.element_size()
     d2h = 0
     photons = 0
     t_total = 0.0
     for k in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        dt.upload(host)
-        ctx.emit(dt, 0.0014, seed=5000 + k, sync=False)
-        ctx.trace(out, precision=prec, **knobs)
-        n_hits, st = ctx.hits()
-        n = st["n_photons"]
-        hits_host[: n_hits * 40].copy_(out.hits[: n_hits * 40], non_blocking=False)
+        n_hits, st = ctx.run_host(host, out, hits_host, 0.0014, seed=5000 + k,
+                                  precision=prec, **knobs)
         el = time.perf_counter() - t0
         if k >= args.warmup:
             t_total += el
-            photons += n
-            d2h += n_hits * 40 + 8 * 12
+            photons += st["n_photons"]
+            d2h += n_hits * rich.HIT_DTYPE.itemsize + rich.COUNTERS_BYTES
     return {"value": photons / t_total, "unit": UNIT,
-            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h // args.steps}
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h // args.steps,
+            "api": "rich_run_host"}
 
 
 if __name__ == "__main__":

@@ -435,6 +435,25 @@ RICH_API rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
  * error recorded during the trace. */
 RICH_API rich_status rich_hits(rich_ctx *ctx, uint64_t *n_hits, rich_stats *stats);
 
+/* One step from host memory: the track arrays (HOST pointers; pinned memory
+ * makes the copies asynchronous, and arrays that lie back to back in one
+ * allocation are copied as one block) are copied into device scratch owned
+ * by the context, emitted (rich_emit) and traced with fused photons
+ * (rich_trace) into out (device buffers, as for rich_trace), the counters
+ * are read (rich_hits) and the first min(n_hits, host_hit_capacity) hit
+ * records are copied into host_hits (host memory, pinned for speed). The
+ * copy of the hit records is issued before the synchronisation for as many
+ * records as the previous call of this context found (plus a quarter), so a
+ * step usually synchronises once. Synchronous. n_hits / stats (may be NULL)
+ * as for rich_hits. Returns the status of the first step that failed;
+ * RICH_ERR_OVERFLOW also when host_hit_capacity is smaller than n_hits (the
+ * first host_hit_capacity records are copied). */
+RICH_API rich_status rich_run_host(rich_ctx *ctx, const rich_tracks *host_tracks,
+                                   const rich_emit_params *params,
+                                   const rich_trace_opts *opts, const rich_outputs *out,
+                                   rich_hit *host_hits, uint64_t host_hit_capacity,
+                                   uint64_t *n_hits, rich_stats *stats);
+
 /* Batched launch as a CUDA graph: captures rich_emit(tracks, params) +
  * rich_trace(fused photons, opts, out) -- the yield and scan kernels, the
  * counter reset, the persistent trace launch and the refinement pass -- into

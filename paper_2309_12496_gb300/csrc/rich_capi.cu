@@ -78,6 +78,11 @@ struct rich_ctx {
     cudaGraphExec_t graph_exec = nullptr;
     cudaStream_t capture_stream = nullptr;
     uint64_t graph_capacity = 0;
+    // rich_run_host: device copy of the caller's host tracks, and the hit
+    // count of its last step (sizes the next step's early hit copy)
+    void *d_host_tracks = nullptr;
+    size_t host_tracks_bytes = 0;
+    uint64_t run_host_hits = 0;
 };
 
 static thread_local std::string g_create_error;
@@ -451,6 +456,7 @@ RICH_API rich_status rich_destroy(rich_ctx *ctx) {
         cudaFree(ctx->d_geom);
         cudaFree(ctx->d_refine);
         cudaFree(ctx->d_grad_tiles);
+        cudaFree(ctx->d_host_tracks);
         if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
         if (ctx->graph) cudaGraphDestroy(ctx->graph);
         if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
@@ -1055,6 +1061,95 @@ RICH_API rich_status rich_trace_grad(rich_ctx *ctx, const rich_tracks *t,
                     "rich_trace_grad: " + std::to_string(ctx->h_ctr->hits) +
                         " hits for capacity " + std::to_string(hit_cap) +
                         " (hits beyond it are not in the gradient)");
+    return RICH_OK;
+}
+
+RICH_API rich_status rich_run_host(rich_ctx *ctx, const rich_tracks *ht,
+                                   const rich_emit_params *prm, const rich_trace_opts *o,
+                                   const rich_outputs *out, rich_hit *host_hits,
+                                   uint64_t host_hit_capacity, uint64_t *n_hits,
+                                   rich_stats *stats) {
+    if (!ctx) return RICH_ERR_ARG;
+    if (!ht || !prm || !o || !out)
+        return fail(ctx, RICH_ERR_ARG, "rich_run_host: NULL argument");
+    if (ht->n < 0) return fail(ctx, RICH_ERR_ARG, "rich_run_host: negative track count");
+    if (host_hit_capacity && !host_hits)
+        return fail(ctx, RICH_ERR_ARG, "rich_run_host: host_hits is NULL");
+    const size_t n = (size_t)ht->n;
+    // the arrays in argument order; NULL optional ones are skipped
+    const void *src[12] = {ht->x, ht->y, ht->z, ht->dx, ht->dy, ht->dz, ht->p, ht->mass,
+                           ht->length, ht->event, ht->id, ht->n_fixed};
+    for (int k = 0; k < 10; ++k)
+        if (n && !src[k])
+            return fail(ctx, RICH_ERR_ARG, "rich_run_host: a required track array is NULL");
+    DeviceGuard guard(ctx->device);
+    const size_t field = 4 * n;
+    const size_t need = std::max<size_t>(12 * field, 256);
+    if (need > ctx->host_tracks_bytes) {
+        RICH_CUDA(cudaStreamSynchronize(ctx->stream));
+        drop_graph(ctx);
+        cudaFree(ctx->d_host_tracks);
+        ctx->d_host_tracks = nullptr;
+        ctx->host_tracks_bytes = 0;
+        RICH_CUDA(cudaMalloc(&ctx->d_host_tracks, need));
+        ctx->host_tracks_bytes = need;
+    }
+    char *dbase = static_cast<char *>(ctx->d_host_tracks);
+    // runs of arrays that lie back to back on the host: one copy per run
+    if (n) {
+        int k = 0;
+        while (k < 12) {
+            if (!src[k]) { ++k; continue; }
+            int e = k + 1;
+            while (e < 12 && src[e] &&
+                   static_cast<const char *>(src[e]) == static_cast<const char *>(src[e - 1]) + field)
+                ++e;
+            RICH_CUDA(cudaMemcpyAsync(dbase + k * field, src[k], (e - k) * field,
+                                      cudaMemcpyHostToDevice, ctx->stream));
+            k = e;
+        }
+    }
+    auto dev = [&](int k) -> const void * { return src[k] ? dbase + k * field : nullptr; };
+    rich_tracks dt;
+    dt.n = ht->n;
+    dt.x = (const float *)dev(0);
+    dt.y = (const float *)dev(1);
+    dt.z = (const float *)dev(2);
+    dt.dx = (const float *)dev(3);
+    dt.dy = (const float *)dev(4);
+    dt.dz = (const float *)dev(5);
+    dt.p = (const float *)dev(6);
+    dt.mass = (const float *)dev(7);
+    dt.length = (const float *)dev(8);
+    dt.event = (const uint32_t *)dev(9);
+    dt.id = (const uint32_t *)dev(10);
+    dt.n_fixed = (const uint32_t *)dev(11);
+    rich_status st = rich_emit(ctx, &dt, prm, nullptr, nullptr);
+    if (st != RICH_OK) return st;
+    st = rich_trace(ctx, nullptr, o, out);
+    if (st != RICH_OK) return st;
+    // early copy of the expected hit records, then the counters' round trip
+    uint64_t early = ctx->run_host_hits ? ctx->run_host_hits + ctx->run_host_hits / 4 : 0;
+    early = std::min(early, std::min(host_hit_capacity, out->hit_capacity));
+    if (early)
+        RICH_CUDA(cudaMemcpyAsync(host_hits, out->hits, early * sizeof(rich_hit),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+    uint64_t nh = 0;
+    st = rich_hits(ctx, &nh, stats);
+    if (n_hits) *n_hits = nh;
+    if (st != RICH_OK) return st;
+    ctx->run_host_hits = nh;
+    const uint64_t want = std::min(nh, host_hit_capacity);
+    if (want > early) {
+        RICH_CUDA(cudaMemcpyAsync(host_hits + early, out->hits + early,
+                                  (want - early) * sizeof(rich_hit), cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+        RICH_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    if (nh > host_hit_capacity)
+        return fail(ctx, RICH_ERR_OVERFLOW,
+                    "rich_run_host: " + std::to_string(nh) + " hits for a host buffer of " +
+                        std::to_string(host_hit_capacity));
     return RICH_OK;
 }
 

@@ -284,13 +284,13 @@ k_yield(TracksView t, double n_minus_1, double inv_band_mm, uint32_t key0,
         // every input of the track in one round of loads; the double-word
         // forms of the parameters meanwhile
         const ff nm1 = ff_from_double(n_minus_1), inv_band = ff_from_double(inv_band_mm);
-        const double p = t.p[i], m = t.mass[i], len = t.length[i];
+        const float p = t.p[i], m = t.mass[i], len = t.length[i];
         const float tx = t.x[i], ty = t.y[i], tz = t.z[i];
         const float fdx = t.dx[i], fdy = t.dy[i], fdz = t.dz[i];
         const uint32_t event = t.event[i];
         const uint32_t id = t.id ? t.id[i] : (uint32_t)i;
         const uint32_t n_fixed = t.n_fixed ? t.n_fixed[i] : 0u;
-        const ff pf = ff_from_double(p), mf = ff_from_double(m), lf = ff_from_double(len);
+        const ff pf = ffv(p), mf = ffv(m), lf = ffv(len);     // FP32 inputs, exact
         // 1 - beta = m^2 / (E (E + p)) keeps n*beta - 1 accurate near 1
         const ff E = ff_sqrt(ff_add(ff_mul(pf, pf), ff_mul(mf, mf)));
         const ff omb = mf.hi == 0.0f ? ffv(0.0f) : ff_div(ff_mul(mf, mf), ff_mul(E, ff_add(E, pf)));
@@ -305,11 +305,12 @@ k_yield(TracksView t, double n_minus_1, double inv_band_mm, uint32_t key0,
         } else if (model.dispersion) {
             // dispersive radiator (FP64): Frank-Tamm integral of sin^2 theta(lambda),
             // and the FP32 band and normaliser of the wavelength accept/reject
-            const double E64 = sqrt(p * p + m * m);
-            const double omb64 = (m == 0.0) ? 0.0 : (m * m) / (E64 * (E64 + p));
+            const double p64 = p, m64 = m;
+            const double E64 = sqrt(p64 * p64 + m64 * m64);
+            const double omb64 = (m64 == 0.0) ? 0.0 : (m64 * m64) / (E64 * (E64 + p64));
             double xt = 0.0;
-            mu = ff_from_double(len * disp_yield_per_mm(model, 1.0 - omb64, omb64, lam_min,
-                                                         lam_max, xt));
+            mu = ff_from_double((double)len * disp_yield_per_mm(model, 1.0 - omb64, omb64,
+                                                                 lam_min, lam_max, xt));
             const float inv1 = __fdiv_rn(1.0f, (float)lam_min);
             const float inv2 = __fdiv_rn(1.0f, (float)lam_max);
             const float xlo = (float)xt > inv2 ? (float)xt : inv2;
@@ -341,7 +342,7 @@ k_yield(TracksView t, double n_minus_1, double inv_band_mm, uint32_t key0,
         r.x = tx;
         r.y = ty;
         r.z = tz;
-        r.len = (float)len;
+        r.len = len;
         r.tx = tn.x.hi;
         r.ty = tn.y.hi;
         r.tz = tn.z.hi;

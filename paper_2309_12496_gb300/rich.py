@@ -32,7 +32,11 @@ N_FATES = 9
 EXPORTED = ["rich_create", "rich_destroy", "rich_set_stream", "rich_init_geometry",
             "rich_emit", "rich_trace", "rich_hits", "rich_philox", "rich_last_error",
             "rich_version", "rich_photon_counts_static", "rich_trace_grad",
-            "rich_graph_capture", "rich_graph_launch"]
+            "rich_graph_capture", "rich_graph_launch", "rich_run_host"]
+
+# bytes a counters' read (rich_hits) brings back: the device counters (96 B)
+# and the photon total (8 B)
+COUNTERS_BYTES = 104
 
 # rich_hit, 40 bytes
 HIT_DTYPE = np.dtype([("event", "<u4"), ("track", "<u4"), ("photon", "<u4"),
@@ -171,13 +175,16 @@ def load():
                                       C.POINTER(TraceOpts), C.POINTER(Outputs),
                                       C.POINTER(C.c_double), C.POINTER(C.c_double),
                                       C.POINTER(C.c_uint64)]
+        L.rich_run_host.argtypes = [vp, C.POINTER(TracksDesc), C.POINTER(EmitParams),
+                                    C.POINTER(TraceOpts), C.POINTER(Outputs), vp, C.c_uint64,
+                                    C.POINTER(C.c_uint64), C.POINTER(Stats)]
         L.rich_last_error.argtypes = [vp]
         L.rich_last_error.restype = C.c_char_p
         L.rich_version.restype = C.c_char_p
         for f in ("rich_create", "rich_destroy", "rich_set_stream", "rich_init_geometry",
                   "rich_emit", "rich_trace", "rich_hits", "rich_philox",
                   "rich_photon_counts_static", "rich_trace_grad", "rich_graph_capture",
-                  "rich_graph_launch"):
+                  "rich_graph_launch", "rich_run_host"):
             getattr(L, f).restype = C.c_int
         _lib = L
         return L
@@ -254,6 +261,29 @@ class DeviceTracks:
     def desc(self) -> TracksDesc:
         return TracksDesc(n=self.n, **{k: (None if v is None else v.data_ptr())
                                        for k, v in self.t.items()})
+
+
+class HostTracks:
+    """A Tracks set in one pinned host buffer, the arrays back to back in
+    rich_tracks order (so rich_run_host copies them with one transfer)."""
+
+    def __init__(self, tracks: W.Tracks):
+        torch = _torch()
+        fields = list(W.Tracks.FIELDS) + ["event", "id"]
+        if tracks.n_fixed is not None:
+            fields.append("n_fixed")
+        n = self.n = tracks.n
+        self.buf = torch.empty(len(fields) * max(n, 1), dtype=torch.int32).pin_memory()
+        hv = self.buf.numpy()
+        for k, f in enumerate(fields):
+            dtp = np.float32 if f in W.Tracks.FIELDS else np.uint32
+            hv[k * n:(k + 1) * n] = np.ascontiguousarray(getattr(tracks, f), dtp).view(np.int32)
+        base = self.buf.data_ptr()
+        self.ptrs = {f: base + 4 * k * n for k, f in enumerate(fields)}
+
+    def desc(self) -> TracksDesc:
+        return TracksDesc(n=self.n, **{f: self.ptrs.get(f) for f in
+                                       list(W.Tracks.FIELDS) + ["event", "id", "n_fixed"]})
 
 
 class PhotonBuffers:
@@ -422,6 +452,33 @@ class Context:
                                C.byref(o), C.byref(outputs.desc()))
         _check(self.handle, st)
 
+    def run_host(self, tracks: HostTracks, outputs: TraceOutputs, hits_host, n_minus_1,
+                 lambda_min=200.0, lambda_max=600.0, seed=0, precision=PREC_REFINE64,
+                 max_bounces=8, max_steps=16, t_min=1e-3, block_threads=0, blocks_per_sm=0,
+                 refill_min=0, chunk=0, wide_regs=0, bvh_smem_nodes=-1, prefilter=()):
+        """One synchronous step from host memory (rich_run_host): host tracks
+        in, the hit records copied into hits_host (a pinned uint8 tensor of
+        n x 40 bytes). Returns (n_hits, stats dict)."""
+        prm = _emit_params(seed, n_minus_1, lambda_min, lambda_max, SOURCE_CHERENKOV, 0.0,
+                           -1, None)
+        o = TraceOpts(seed=0, precision=precision, max_bounces=max_bounces,
+                      max_steps=max_steps, t_min=t_min, block_threads=block_threads,
+                      blocks_per_sm=blocks_per_sm, refill_min=refill_min, chunk=chunk,
+                      wide_regs=wide_regs, bvh_smem_nodes=bvh_smem_nodes,
+                      **_prefilter_fields(prefilter))
+        n = C.c_uint64(0)
+        s = Stats()
+        cap = hits_host.numel() * hits_host.element_size() // HIT_DTYPE.itemsize
+        st = load().rich_run_host(self.handle, C.byref(tracks.desc()), C.byref(prm),
+                                  C.byref(o), C.byref(outputs.desc()),
+                                  C.c_void_p(hits_host.data_ptr()), cap, C.byref(n),
+                                  C.byref(s))
+        _check(self.handle, st)
+        return int(n.value), {"n_photons": int(s.n_photons), "n_hits": int(s.n_hits),
+                              "fate": [int(x) for x in s.n_fate],
+                              "device_status": int(s.device_status),
+                              "photon_order": int(s.photon_order)}
+
     def philox(self, counters, seed):
         """Library Philox4x32-10 of an (n, 4) uint32 counter array."""
         torch = _torch()
@@ -517,6 +574,10 @@ def rich_trace(ctx: Context, outputs, **kw):
 
 def rich_hits(ctx: Context, **kw):
     return ctx.hits(**kw)
+
+
+def rich_run_host(ctx: Context, tracks: HostTracks, outputs, hits_host, n_minus_1, **kw):
+    return ctx.run_host(tracks, outputs, hits_host, n_minus_1, **kw)
 
 
 def rich_photon_counts_static(tracks: DeviceTracks, n_minus_1, counts, offsets,

@@ -1,0 +1,91 @@
+"""rich_run_host (one step from host memory) against the device-buffer path
+(rich_emit + rich_trace + rich_hits on device tracks): the same hit records,
+counters and fates, with the early hit copy off (first call) and on (later
+calls); a host buffer smaller than the hit count (marked gpu)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2309_12496_gb300 import rich  # noqa: E402
+from paper_2309_12496_gb300 import workloads as W  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2309_12496_gb300 import build
+    build.build()
+
+
+def _sorted(h):
+    return np.sort(h, order=["event", "track", "photon"])
+
+
+@pytest.fixture(scope="module")
+def setup():
+    scene = W.rich1_scene(meshed=True)
+    tracks = W.pion_tracks(300, seed=4)
+    ctx = rich.Context(0)
+    ctx.init_geometry(scene)
+    dt = rich.DeviceTracks(tracks)
+    n = ctx.emit(dt, 0.0014, seed=9)
+    cap = n // 2 + 1024
+    out = rich.TraceOutputs(cap, scene.pixels_per_event, len(scene.planes), 1, n)
+    ctx.trace(out, precision=rich.PREC_REFINE64)
+    nh, st = ctx.hits()
+    ref = _sorted(out.hits_numpy(nh))
+    ref_fate = out.fate.cpu().numpy().copy()
+    yield ctx, scene, tracks, n, cap, nh, st, ref, ref_fate
+    ctx.close()
+
+
+def test_run_host_matches_device_path(setup):
+    ctx, scene, tracks, n, cap, nh, st, ref, ref_fate = setup
+    ht = rich.HostTracks(tracks)
+    out = rich.TraceOutputs(cap, scene.pixels_per_event, len(scene.planes), 1, n)
+    hits_host = torch.empty(cap * rich.HIT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    for rep in range(3):       # first call: no early copy; then the early copy
+        hits_host.zero_()
+        nh2, st2 = ctx.run_host(ht, out, hits_host, 0.0014, seed=9)
+        assert nh2 == nh
+        assert st2["n_photons"] == st["n_photons"] == n
+        assert st2["fate"] == st["fate"]
+        got = np.frombuffer(hits_host.numpy()[: nh2 * rich.HIT_DTYPE.itemsize].tobytes(),
+                            rich.HIT_DTYPE)
+        np.testing.assert_array_equal(_sorted(got), ref)
+        np.testing.assert_array_equal(out.fate.cpu().numpy(), ref_fate)
+
+
+def test_run_host_small_host_buffer(setup):
+    ctx, scene, tracks, n, cap, nh, st, ref, ref_fate = setup
+    ht = rich.HostTracks(tracks)
+    out = rich.TraceOutputs(cap, scene.pixels_per_event, len(scene.planes), 1, n)
+    k = 10
+    hits_host = torch.zeros(k * rich.HIT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    with pytest.raises(rich.RichError) as e:
+        ctx.run_host(ht, out, hits_host, 0.0014, seed=9)
+    assert e.value.status == 4                      # RICH_ERR_OVERFLOW
+    got = np.frombuffer(hits_host.numpy().tobytes(), rich.HIT_DTYPE)
+    keys = set(zip(ref["event"], ref["track"], ref["photon"]))
+    assert all((h["event"], h["track"], h["photon"]) in keys for h in got)
+    # the context stays usable
+    big = torch.empty(cap * rich.HIT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    nh2, _ = ctx.run_host(ht, out, big, 0.0014, seed=9)
+    assert nh2 == nh
+
+
+def test_run_host_zero_tracks():
+    scene = W.rich1_scene(meshed=False)
+    ctx = rich.Context(0)
+    ctx.init_geometry(scene)
+    empty = W.pion_tracks(0, seed=1)
+    ht = rich.HostTracks(empty)
+    out = rich.TraceOutputs(16, scene.pixels_per_event, len(scene.planes), 1, 0)
+    hits_host = torch.empty(16 * rich.HIT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    nh, st = ctx.run_host(ht, out, hits_host, 0.0014, seed=1)
+    assert nh == 0 and st["n_photons"] == 0
+    ctx.close()
