@@ -45,7 +45,12 @@ WORKLOAD = "rich1_meshed_1000_pion_tracks"
 # divided by its 350,350 photons: (2 x 244.19 M + 37.77 M + 87.12 M) / 350,350.
 FLOPS_PER_PHOTON = 1750.4
 # dram__bytes_read.sum + dram__bytes_write.sum of the same k_trace launch.
-TRACE_DRAM_BYTES = 9755904 + 549888
+TRACE_DRAM_BYTES = 7004416 + 252160
+# Warp instructions per photon of the same launch (smsp__inst_executed.sum
+# 99,121,278 / 350,350): the kernel is bound by instruction issue, so the
+# issue rate against 4 schedulers x SMs x clock is reported beside the FP32
+# fraction.
+WARP_INST_PER_PHOTON = 282.92
 FP32_LANES_PER_SM = 128
 SM_COUNT_NOMINAL = 152
 
@@ -272,11 +277,18 @@ def main():
         peak_tflops = 2 * FP32_LANES_PER_SM * n_sm * sm_max * 1e6 / 1e12
         if FLOPS_PER_PHOTON:
             achieved = FLOPS_PER_PHOTON * ph_step / t_trace / 1e12
+            issue_peak = 4 * n_sm * sm_max * 1e6
+            issue = WARP_INST_PER_PHOTON * ph_step / t_trace
             roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
                     "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                     "traffic": TRACE_DRAM_BYTES,
                     "kernel": "k_trace", "flops_per_photon": FLOPS_PER_PHOTON,
-                    "peak_source": f"FP32 2 x {FP32_LANES_PER_SM} lanes x {n_sm} SMs x {sm_max:.0f} MHz"}
+                    "peak_source": f"FP32 2 x {FP32_LANES_PER_SM} lanes x {n_sm} SMs x {sm_max:.0f} MHz",
+                    "timed": "k_trace + k_refine (one rich_trace call; k_trace is ~87 % of it)",
+                    "issue": {"warp_inst_per_photon": WARP_INST_PER_PHOTON,
+                              "achieved": issue, "peak": issue_peak, "unit": "warp inst/s",
+                              "frac": issue / issue_peak,
+                              "peak_source": f"4 schedulers x {n_sm} SMs x {sm_max:.0f} MHz"}}
         else:
             roof = {"bound": "alu", "achieved": None, "peak": peak_tflops, "unit": "TFLOP/s",
                     "frac": None, "traffic": None, "kernel": "k_trace",
