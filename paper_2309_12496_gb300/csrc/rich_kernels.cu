@@ -58,7 +58,17 @@ struct TrackStream {
         ++word;
         return u24d(v);
     }
-    __device__ float nextf() { return (float)next(); }   // exact: 24-bit uniforms
+    // the same uniform in FP32 (exact: 24 bits), without FP64 conversions
+    __device__ float nextf() {
+        if (word == 4) {
+            w = philox10(block, 0xFFFFFFFFu, id, event, k0, k1);
+            ++block;
+            word = 0;
+        }
+        uint32_t v = word == 0 ? w.x : (word == 1 ? w.y : (word == 2 ? w.z : w.w));
+        ++word;
+        return u24f(v);
+    }
 };
 
 // FP64 natural logarithm of a positive normal x, table-driven after Tang
@@ -152,15 +162,19 @@ __device__ __forceinline__ ff ff_exp_neg(ff x) {
     return {s.hi * sc, s.lo * sc};
 }
 
-// floor of a double-word as an integer (any magnitude below 2^62)
+// floor of a double-word as an integer (any magnitude below 2^62). The
+// 32-bit conversions take the common case: 64-bit ones issue on the FP64
+// pipe on this GPU.
 __device__ __forceinline__ int64_t ff_floor_i64(ff a) {
     const float f = floorf(a.hi);
-    if (f != a.hi) return (int64_t)f;     // hi not an integer: |hi| < 2^23, lo cannot cross
+    if (f != a.hi) return (int64_t)__float2int_rz(f);  // |hi| < 2^23, lo cannot cross
+    if (fabsf(a.hi) < 1.0e9f) return (int64_t)__float2int_rz(a.hi) + __float2int_rz(floorf(a.lo));
     return (int64_t)a.hi + (int64_t)floorf(a.lo);
 }
 
 // an integer (|k| < 2^48) as a double-word, exactly
 __device__ __forceinline__ ff ff_from_i64(int64_t k) {
+    if (k >= -(1ll << 24) && k <= (1ll << 24)) return ffv(__int2float_rn((int)k));
     const float hi = (float)k;
     return fast_two_sum(hi, (float)(k - (int64_t)hi));
 }
@@ -195,7 +209,7 @@ __device__ int64_t poisson_draw(ff mu, TrackStream &s) {
         int64_t k = 0;
         while (ff_le(F, u) && k < 1000) {
             k += 1;
-            pk = ff_mul(pk, ff_div(mu, ffv((float)k)));
+            pk = ff_mul(pk, ff_div(mu, ffv(__int2float_rn((int)k))));
             F = ff_add(F, pk);
         }
         return k;
@@ -275,15 +289,13 @@ __device__ double disp_yield_per_mm(const YieldModel &m, double beta, double omb
 
 template <bool RECS>
 __global__ void __launch_bounds__(kYieldBlock)
-k_yield(TracksView t, double n_minus_1, double inv_band_mm, uint32_t key0,
+k_yield(TracksView t, ff nm1, ff inv_band, uint32_t key0,
         uint32_t key1, TrackRec *rec, double2 *cs, uint32_t *counts,
         unsigned long long *block_sums, YieldModel model, double lam_min, double lam_max) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t count = 0;
     if (i < t.n) {
-        // every input of the track in one round of loads; the double-word
-        // forms of the parameters meanwhile
-        const ff nm1 = ff_from_double(n_minus_1), inv_band = ff_from_double(inv_band_mm);
+        // every input of the track in one round of loads
         const float p = t.p[i], m = t.mass[i], len = t.length[i];
         const float tx = t.x[i], ty = t.y[i], tz = t.z[i];
         const float fdx = t.dx[i], fdy = t.dy[i], fdz = t.dz[i];
@@ -2134,16 +2146,18 @@ cudaError_t launch_yield(const TracksView &t, double n_minus_1,
                          cudaStream_t s, const YieldModel &model) {
     if (t.n <= 0) return cudaSuccess;
     const double inv_band_mm = 1.0e6 / lam_min - 1.0e6 / lam_max;
+    // the kernel's double-word parameters, split here
+    const ff nm1 = ffc(n_minus_1), inv_band = ffc(inv_band_mm);
     const int64_t groups = (t.n + kYieldThreads - 1) / kYieldThreads;
     cudaError_t e = cudaMemsetAsync(block_sums, 0, sizeof(unsigned long long) * groups, s);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((t.n + kYieldBlock - 1) / kYieldBlock);
     if (rec)
-        k_yield<true><<<blocks, kYieldBlock, 0, s>>>(t, n_minus_1, inv_band_mm, key0, key1,
+        k_yield<true><<<blocks, kYieldBlock, 0, s>>>(t, nm1, inv_band, key0, key1,
                                                      rec, cs, counts, block_sums, model,
                                                      lam_min, lam_max);
     else
-        k_yield<false><<<blocks, kYieldBlock, 0, s>>>(t, n_minus_1, inv_band_mm, key0, key1,
+        k_yield<false><<<blocks, kYieldBlock, 0, s>>>(t, nm1, inv_band, key0, key1,
                                                       rec, cs, counts, block_sums, model,
                                                       lam_min, lam_max);
     return cudaGetLastError();

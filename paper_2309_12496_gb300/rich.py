@@ -81,6 +81,27 @@ class EmitParams(C.Structure):
                 ("disp_lambda0", C.c_float)]
 
 
+_OPTS_CACHE = {}
+
+
+def _trace_opts(seed, precision, max_bounces, max_steps, t_min, block_threads, blocks_per_sm,
+                refill_min, chunk, wide_regs, bvh_smem_nodes, prefilter):
+    """rich_trace_opts, one struct per distinct set of values (the library
+    only reads it)."""
+    key = (int(seed), precision, max_bounces, max_steps, float(t_min), block_threads,
+           blocks_per_sm, refill_min, chunk, wide_regs, bvh_smem_nodes, tuple(prefilter))
+    o = _OPTS_CACHE.get(key)
+    if o is None:
+        if len(_OPTS_CACHE) > 256:
+            _OPTS_CACHE.clear()
+        o = _OPTS_CACHE[key] = TraceOpts(
+            seed=int(seed), precision=precision, max_bounces=max_bounces, max_steps=max_steps,
+            t_min=t_min, block_threads=block_threads, blocks_per_sm=blocks_per_sm,
+            refill_min=refill_min, chunk=chunk, wide_regs=wide_regs,
+            bvh_smem_nodes=bvh_smem_nodes, **_prefilter_fields(prefilter))
+    return o
+
+
 def _emit_params(seed, n_minus_1, lambda_min, lambda_max, source=SOURCE_CHERENKOV,
                  yield_per_mm=0.0, spectrum_table=-1, dispersion=None):
     """rich_emit_params; dispersion: None (constant index) or (a nm^-2,
@@ -259,8 +280,12 @@ class DeviceTracks:
         self._buf.copy_(host, non_blocking=True)
 
     def desc(self) -> TracksDesc:
-        return TracksDesc(n=self.n, **{k: (None if v is None else v.data_ptr())
-                                       for k, v in self.t.items()})
+        """The rich_tracks descriptor (built once: the arrays are fixed)."""
+        d = getattr(self, "_desc", None)
+        if d is None:
+            d = self._desc = TracksDesc(n=self.n, **{k: (None if v is None else v.data_ptr())
+                                                     for k, v in self.t.items()})
+        return d
 
 
 class HostTracks:
@@ -282,8 +307,12 @@ class HostTracks:
         self.ptrs = {f: base + 4 * k * n for k, f in enumerate(fields)}
 
     def desc(self) -> TracksDesc:
-        return TracksDesc(n=self.n, **{f: self.ptrs.get(f) for f in
-                                       list(W.Tracks.FIELDS) + ["event", "id", "n_fixed"]})
+        d = getattr(self, "_desc", None)
+        if d is None:
+            d = self._desc = TracksDesc(n=self.n, **{f: self.ptrs.get(f) for f in
+                                                     list(W.Tracks.FIELDS) + ["event", "id",
+                                                                              "n_fixed"]})
+        return d
 
 
 class PhotonBuffers:
@@ -348,6 +377,13 @@ class TraceOutputs:
             self.fate.zero_()
 
     def desc(self) -> Outputs:
+        """The rich_outputs descriptor (built once: the buffers are fixed)."""
+        d = getattr(self, "_desc", None)
+        if d is None:
+            d = self._desc = self._make_desc()
+        return d
+
+    def _make_desc(self) -> Outputs:
         return Outputs(hits=self.hits.data_ptr(), hit_capacity=self.hit_capacity,
                        pixel_counts=None if self.pixel_counts is None else self.pixel_counts.data_ptr(),
                        event_sums=None if self.event_sums is None else self.event_sums.data_ptr(),
@@ -442,11 +478,8 @@ class Context:
               wide_regs=0, bvh_smem_nodes=-1, prefilter=()):
         """prefilter: scene table indices whose product is applied as one
         accept/reject per photon before propagation (Sec. 4.3)."""
-        o = TraceOpts(seed=int(seed), precision=precision, max_bounces=max_bounces,
-                      max_steps=max_steps, t_min=t_min, block_threads=block_threads,
-                      blocks_per_sm=blocks_per_sm, refill_min=refill_min, chunk=chunk,
-                      wide_regs=wide_regs, bvh_smem_nodes=bvh_smem_nodes,
-                      **_prefilter_fields(prefilter))
+        o = _trace_opts(seed, precision, max_bounces, max_steps, t_min, block_threads,
+                        blocks_per_sm, refill_min, chunk, wide_regs, bvh_smem_nodes, prefilter)
         pd = photons.desc() if photons is not None else None
         st = load().rich_trace(self.handle, None if pd is None else C.byref(pd),
                                C.byref(o), C.byref(outputs.desc()))
@@ -461,11 +494,8 @@ class Context:
         n x 40 bytes). Returns (n_hits, stats dict)."""
         prm = _emit_params(seed, n_minus_1, lambda_min, lambda_max, SOURCE_CHERENKOV, 0.0,
                            -1, None)
-        o = TraceOpts(seed=0, precision=precision, max_bounces=max_bounces,
-                      max_steps=max_steps, t_min=t_min, block_threads=block_threads,
-                      blocks_per_sm=blocks_per_sm, refill_min=refill_min, chunk=chunk,
-                      wide_regs=wide_regs, bvh_smem_nodes=bvh_smem_nodes,
-                      **_prefilter_fields(prefilter))
+        o = _trace_opts(0, precision, max_bounces, max_steps, t_min, block_threads,
+                        blocks_per_sm, refill_min, chunk, wide_regs, bvh_smem_nodes, prefilter)
         n = C.c_uint64(0)
         s = Stats()
         cap = hits_host.numel() * hits_host.element_size() // HIT_DTYPE.itemsize
@@ -588,7 +618,7 @@ def rich_photon_counts_static(tracks: DeviceTracks, n_minus_1, counts, offsets,
     u64, n + 1 entries) into caller device tensors, with no device
     allocation by the library. `n` overrides the track count passed."""
     L = load()
-    d = tracks.desc()
+    d = TracksDesc.from_buffer_copy(tracks.desc())
     if n is not None:
         d.n = int(n)
     prm = _emit_params(seed, n_minus_1, lambda_min, lambda_max, source, yield_per_mm, -1,
