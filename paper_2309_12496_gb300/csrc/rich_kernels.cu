@@ -1624,13 +1624,13 @@ k_trace(TraceArgs A) {
                         ph.n_turn += 1;
                         ph.o = p;
                         ph.skip = b.prim;
-                            ph.skip_ref = hit_ref;
+                        ph.skip_ref = hit_ref;
                     }
                 } else {  // detector
                     if (!front) {
                         ph.o = p;
                         ph.skip = b.prim;
-                            ph.skip_ref = hit_ref;
+                        ph.skip_ref = hit_ref;
                     } else {
                         const bool pass =
                             P.n_prefilter || u24f(ph.w_qe) < table_eval(S.tables[M.table], ph.lam);
