@@ -102,9 +102,6 @@ __device__ __forceinline__ u4 philox10(uint32_t c0, uint32_t c1, uint32_t c2,
 __device__ __forceinline__ float u24f(uint32_t w) {
     return __uint2float_rn(w >> 8) * 5.9604644775390625e-8f;
 }
-__device__ __forceinline__ double u24d(uint32_t w) {
-    return (double)(w >> 8) * 5.9604644775390625e-8;
-}
 
 // ------------------------------------------------------------ responses
 // Wavelength response of Sec. 4.3, one IEEE FP32 operation at a time.

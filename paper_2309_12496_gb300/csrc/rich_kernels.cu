@@ -48,17 +48,7 @@ __device__ __forceinline__ void set_status(Counters *c, unsigned code) {
 struct TrackStream {
     uint32_t event, id, k0, k1, block, word;
     u4 w;
-    __device__ double next() {
-        if (word == 4) {
-            w = philox10(block, 0xFFFFFFFFu, id, event, k0, k1);
-            ++block;
-            word = 0;
-        }
-        uint32_t v = word == 0 ? w.x : (word == 1 ? w.y : (word == 2 ? w.z : w.w));
-        ++word;
-        return u24d(v);
-    }
-    // the same uniform in FP32 (exact: 24 bits), without FP64 conversions
+    // the next uniform, in FP32 (exact: 24 bits)
     __device__ float nextf() {
         if (word == 4) {
             w = philox10(block, 0xFFFFFFFFu, id, event, k0, k1);
