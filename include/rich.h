@@ -269,10 +269,13 @@ typedef struct rich_photons {
 
 /* ----------------------------------------------------------------- options */
 enum {
-    RICH_PREC_FP32 = 0,     /* FP32 trace; FP64 only for the sphere quadratic */
+    RICH_PREC_FP32 = 0,     /* FP32 trace; the sphere quadratic in double-word
+                               FP32 arithmetic (hi + lo, ~48 bits) */
     RICH_PREC_REFINE64 = 1  /* FP32 trace, then the detected photon's recorded
-                               surface sequence is replayed in FP64 to give
-                               the hit position and pixel */
+                               surface sequence is replayed in double-word
+                               arithmetic (~48 bits, hit positions within
+                               ~1e-10 mm of an FP64 replay) to give the hit
+                               position and pixel */
 };
 
 typedef struct rich_trace_opts {
@@ -402,9 +405,11 @@ RICH_API rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc 
 /* Photon yield and emission (Sec. 3: cos(theta) = 1/(n beta), azimuth
  * uniform; photons are the input of the trace as in Sec. 4.2). For each
  * track computes beta, the Cherenkov angle and the Frank-Tamm mean
- * mu = L * 2*pi*alpha * sin^2(theta) * (1/lambda_min - 1/lambda_max) in FP64,
- * draws N_t ~ Poisson(mu) (or takes n_fixed), and scans the counts into
- * photon offsets kept in the context for the next fused rich_trace.
+ * mu = L * 2*pi*alpha * sin^2(theta) * (1/lambda_min - 1/lambda_max), draws
+ * N_t ~ Poisson(mu) (or takes n_fixed), all in double-word FP32 arithmetic
+ * (~2^-44 per operation; the dispersive radiator's mean in FP64), and scans
+ * the counts into photon offsets kept in the context for the next fused
+ * rich_trace.
  * tracks: DEVICE arrays (see rich_tracks). out: if non-NULL, the photons are
  * also materialised into the caller's SoA (RICH_ERR_OVERFLOW if capacity is
  * too small; nothing is written then) and out->n is set on the host after a
@@ -492,8 +497,8 @@ typedef struct rich_grad_params {
  * ignored; seed and band are used) and traced through the scene with its
  * sphere tiles moved to theta; every detected photon is then replayed along
  * its recorded reflecting surfaces (fixed topology, the photon's path
- * recomputed per photon, not stored) in forward mode: FP64 values, 10 FP32
- * tangents. The hit (u, v) is smeared by sigma (g1, g2), a Box-Muller pair
+ * recomputed per photon, not stored) in forward mode: double-word values
+ * (~48 bits), 10 FP32 tangents. The hit (u, v) is smeared by sigma (g1, g2), a Box-Muller pair
  * from the photon's draw block 3; rho = (|(u~, v~) - (cu, cv)| - r) / sigma
  * and loss = mean rho^2 over the hits whose (track index, plane) target has
  * weight > 0.
