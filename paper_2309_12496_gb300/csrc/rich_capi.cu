@@ -127,7 +127,7 @@ bool finite3(const float *v) {
 }
 
 // Tiles sharing one sphere (identical FP32 centre and radius) form a group:
-// the FP64 quadratic is solved once per group.
+// the sphere quadratic is solved once per group.
 bool group_tiles(const rich_sphere *sp, int n, int n_materials,
                  std::vector<DevSphereGroup> &groups, std::vector<DevTile> &tiles,
                  std::string &err) {

@@ -2,12 +2,13 @@
 //
 // Device layout of a scene (built by rich_init_geometry):
 //   * sphere groups: tiles sharing one sphere (centre, radius) are grouped so
-//     the FP64 quadratic is solved once per sphere and the FP32 aperture
+//     the double-word quadratic is solved once per sphere and the FP32 aperture
 //     tests run per tile;
 //   * rectangles, response tables and materials: small arrays staged into
 //     shared memory by every trace block;
 //   * triangles: 48-byte records in BVH leaf order; per-vertex normals in a
-//     parallel array; BVH2 nodes of 64 bytes holding both children's boxes.
+//     parallel array; four-wide BVH nodes of 128 bytes holding the four
+//     children's boxes by axis.
 #pragma once
 
 #include <cstdint>
@@ -82,7 +83,7 @@ struct alignas(16) DevNode { // 128 B: boxes of up to four children (by axis) + 
 
 struct alignas(16) TrackRec {  // 64 B, written by the yield kernel
     float x, y, z, len;
-    float tx, ty, tz, tan_theta;  // unit direction (FP64-normalised) and tan
+    float tx, ty, tz, tan_theta;  // unit direction (normalised in double-word) and tan
                                   // theta (constant index) or 1 - beta (FP32,
                                   // dispersive radiator)
     float rx, ry, rz;             // raw input direction
@@ -155,7 +156,7 @@ struct Counters {            // device, cleared before each trace
     unsigned int ordered;    // 1: photons were taken in azimuth order
 };
 
-// Per stored hit, what the FP64 refinement pass needs to replay the photon:
+// Per stored hit, what the refinement pass needs to replay the photon:
 // its track (or caller-photon) index, the detector rectangle and the
 // sequence of reflecting primitives (triangles by BVH leaf position).
 struct RefineRec {             // 40 B

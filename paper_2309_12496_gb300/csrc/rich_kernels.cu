@@ -1,6 +1,6 @@
 // rich_kernels.cu -- sm_103a kernels of the Cherenkov photon propagator.
 //
-//   k_yield        one thread per track, FP64: beta, Cherenkov angle
+//   k_yield        one thread per track, double-word FP32: beta, Cherenkov angle
 //                  (cos theta = 1/(n beta), Sec. 3), Frank-Tamm mean and the
 //                  keyed Poisson photon count; block sums of the counts.
 //   k_offsets      exclusive scan of the counts into photon offsets
@@ -1133,11 +1133,6 @@ __device__ __forceinline__ void ff_sincos_2pi(uint32_t w, ff &s, ff &c) {
     c = ff_sub(ff_mul(ca, cd), ff_mul(sa, sd));
 }
 
-// Emission of photon j of a track with the same draws as emit_photon:
-// the track direction normalised, the origin at s = u L along it, the
-// azimuth 2 pi u from ff_sincos_2pi, cos and sin of the Cherenkov angle
-// from the FP64 yield pass. Isotropic source: cos(theta) = 1 - 2u (exact)
-// and sin(theta) = 2 sqrt(u (1 - u)) from the exact product u (1 - u).
 // Origin, unit track direction and (sin, cos) of the azimuth of photon j.
 __device__ __forceinline__ void emit_start_ff(const TrackRec &tr, uint32_t j,
                                               const EmitView &em, ff3 &o, ff3 &t, ff &sp,
@@ -1157,6 +1152,12 @@ __device__ __forceinline__ ff3 azimuth_dir_ff(const ff3 &t, ff sp, ff cp) {
             ff_add(ff_mul(e1.z, cp), ff_mul(e2.z, sp))};
 }
 
+// Emission of photon j of a track with the same draws as emit_photon:
+// the track direction normalised, the origin at s = u L along it, the
+// azimuth 2 pi u from ff_sincos_2pi, cos and sin of the Cherenkov angle
+// from the yield pass (stored as FP64). Isotropic source: cos(theta) =
+// 1 - 2u (exact) and sin(theta) = 2 sqrt(u (1 - u)) from the exact product
+// u (1 - u).
 __device__ void emit_ff(const TrackRec &tr, double2 cs, uint32_t j, float lam,
                         const EmitView &em, ff3 &o, ff3 &d) {
     ff3 t;
@@ -1661,7 +1662,7 @@ k_trace(TraceArgs A) {
                 hv = hit_v;
                 const uint64_t slot = base + (uint64_t)__popc(dm & lt_mask);
                 const bool stored = slot < P.hit_capacity;
-                // refined hits are binned (and their pixel found, in FP64)
+                // refined hits are binned (and their pixel found, in double-word)
                 // by the refinement pass; the rest here
                 binned_here = !(REFINE && stored);
                 int ix = 0, iy = 0;
@@ -2198,7 +2199,7 @@ static cudaError_t launch_trace_t(const TraceArgs &a, const LaunchShape &shape,
     return cudaGetLastError();
 }
 
-// Kernel variants: caller photons or fused emission; FP64 refinement side
+// Kernel variants: caller photons or fused emission; refinement side
 // records or not; block shape class: up to 256 threads capped at 64
 // registers (4 blocks per SM), up to 256 threads uncapped, up to 768
 // threads capped at 80 registers, or up to 1024 threads capped at 64 (one
