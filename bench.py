@@ -307,7 +307,8 @@ def main():
             "kernel_ms": {"emit": statistics.mean([a.elapsed_time(b) for a, b, _ in ev]),
                           "trace": t_trace * 1e3},
             "hits_per_step": n_hits_last,
-            "gpu_launches": (5 if prec == rich.PREC_REFINE64 else 4) * args.steps,
+            # k_yield, k_order (with the count scan), k_trace (+ k_refine)
+            "gpu_launches": (4 if prec == rich.PREC_REFINE64 else 3) * args.steps,
             "roofline": roof,
             "clocks": clk,
         }

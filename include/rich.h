@@ -460,8 +460,9 @@ RICH_API rich_status rich_run_host(rich_ctx *ctx, const rich_tracks *host_tracks
                                    uint64_t *n_hits, rich_stats *stats);
 
 /* Batched launch as a CUDA graph: captures rich_emit(tracks, params) +
- * rich_trace(fused photons, opts, out) -- the yield and scan kernels, the
- * counter reset, the persistent trace launch and the refinement pass -- into
+ * rich_trace(fused photons, opts, out) -- the yield kernel, the count scan
+ * and azimuth ordering, the counter reset, the persistent trace launch and
+ * the refinement pass -- into
  * one graph owned by the context, after an uncaptured warm-up pass that
  * makes every allocation (the pass is also a full trace: its results are in
  * out). The graph keeps the pointers it was captured with: the caller's

@@ -83,6 +83,8 @@ struct rich_ctx {
     void *d_host_tracks = nullptr;
     size_t host_tracks_bytes = 0;
     uint64_t run_host_hits = 0;
+    // the last emission left its count scan to the ordering pass
+    bool scan_pending = false;
 };
 
 static thread_local std::string g_create_error;
@@ -320,7 +322,7 @@ EmitView emit_view(const rich_ctx *ctx) {
 rich_status emit_core(rich_ctx *ctx, const rich_tracks *t, uint64_t seed, float n_minus_1,
                       float lambda_min, float lambda_max, int32_t source = RICH_SOURCE_CHERENKOV,
                       float yield_per_mm = 0.f, int32_t spectrum = -1, int32_t dispersion = 0,
-                      float disp_a = 0.f, float disp_lambda0 = 0.f) {
+                      float disp_a = 0.f, float disp_lambda0 = 0.f, bool defer_scan = false) {
     const int64_t n = t->n;
     if (n + 1 > ctx->track_cap) {
         RICH_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -357,8 +359,12 @@ rich_status emit_core(rich_ctx *ctx, const rich_tracks *t, uint64_t seed, float 
                                YieldModel{source == RICH_SOURCE_ISOTROPIC ? (double)yield_per_mm
                                                                           : -1.0,
                                           dispersion, disp_a, disp_lambda0}));
-        RICH_CUDA(launch_offsets(ctx->d_counts, ctx->d_bsum, n, ctx->d_offsets, ctx->d_total,
-                                 ctx->stream));
+        // deferred: the ordering pass (order_photons, which the caller
+        // runs next) does the scan
+        ctx->scan_pending = defer_scan && n <= kOrderScanMaxTracks;
+        if (!ctx->scan_pending)
+            RICH_CUDA(launch_offsets(ctx->d_counts, ctx->d_bsum, n, ctx->d_offsets,
+                                     ctx->d_total, ctx->stream));
     }
     ctx->n_tracks = n;
     ctx->source = source;
@@ -386,11 +392,14 @@ rich_status order_photons(rich_ctx *ctx) {
     }
     const EmitView em = emit_view(ctx);
     if (ctx->n_tracks == 0) {
+        ctx->scan_pending = false;
         RICH_CUDA(cudaMemsetAsync(ctx->d_perm_ok, 0, sizeof(uint32_t), ctx->stream));
         return RICH_OK;
     }
+    const OrderScan scan{ctx->d_counts, ctx->d_bsum, ctx->d_offsets, ctx->d_total};
     RICH_CUDA(launch_order(em, ctx->d_perm, ctx->perm_cap, ctx->d_perm_ok, ctx->n_sm,
-                           ctx->stream));
+                           ctx->stream, ctx->scan_pending ? &scan : nullptr));
+    ctx->scan_pending = false;
     return RICH_OK;
 }
 
@@ -727,7 +736,8 @@ RICH_API rich_status rich_emit(rich_ctx *ctx, const rich_tracks *t,
         const rich_status st = emit_core(ctx, t, prm->seed, prm->n_minus_1, prm->lambda_min,
                                          prm->lambda_max, prm->source, prm->yield_per_mm,
                                          prm->spectrum_table < 0 ? -1 : prm->spectrum_table,
-                                         prm->dispersion, prm->disp_a, prm->disp_lambda0);
+                                         prm->dispersion, prm->disp_a, prm->disp_lambda0,
+                                         /*defer_scan=*/!(n_photons || out));
         if (st != RICH_OK) return st;
     }
     if (n_photons || out) {
@@ -971,7 +981,8 @@ RICH_API rich_status rich_trace_grad(rich_ctx *ctx, const rich_tracks *t,
     }
     {
         rich_status st = emit_core(ctx, t, prm->seed, th->n_minus_1, prm->lambda_min,
-                                   prm->lambda_max);
+                                   prm->lambda_max, RICH_SOURCE_CHERENKOV, 0.f, -1, 0, 0.f, 0.f,
+                                   /*defer_scan=*/true);
         if (st == RICH_OK) st = order_photons(ctx);
         if (st != RICH_OK) return st;
     }

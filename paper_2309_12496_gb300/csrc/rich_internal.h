@@ -228,8 +228,20 @@ cudaError_t launch_offsets(const uint32_t *counts,
 // order so a warp's rays are spatially coherent); tracks with more than
 // kOrderMaxPhotons photons keep index order.
 constexpr uint32_t kOrderMaxPhotons = 16384;
+// The ordering pass can also do the scan of the photon counts (offsets and
+// total from the yield pass's 256-track group sums; up to 4096 groups),
+// which saves the separate scan launch when nothing reads the offsets in
+// between.
+constexpr int kOrderScanGroups = 4096;
+constexpr int64_t kOrderScanMaxTracks = (int64_t)kOrderScanGroups * 256;
+struct OrderScan {
+    const uint32_t *counts;
+    const unsigned long long *group_sums;
+    uint64_t *offsets;             // n + 1 entries, written
+    unsigned long long *total;     // written
+};
 cudaError_t launch_order(const EmitView &em, uint32_t *perm, uint64_t cap, uint32_t *perm_ok,
-                         int n_sm, cudaStream_t s);
+                         int n_sm, cudaStream_t s, const OrderScan *scan = nullptr);
 cudaError_t launch_materialize(const SceneView &sc, const EmitView &em,
                                uint64_t n, const rich_photons &out,
                                cudaStream_t s);

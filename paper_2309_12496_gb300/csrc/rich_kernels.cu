@@ -432,30 +432,96 @@ constexpr int kAzBins = 32;
 constexpr int kOrderWarps = 4;
 constexpr uint32_t kOrderBinCache = 2048;
 
+// SCAN: the offsets are not computed yet; each block first forms the
+// exclusive prefix of the 256-track group sums in shared memory, and each
+// track's warp adds the counts before it in its group and writes its
+// offset (block 0 writes offsets[n] and the total).
+template <bool SCAN>
 __global__ void __launch_bounds__(32 * kOrderWarps) k_order(EmitView em, uint32_t *perm,
-                                                            uint64_t cap, uint32_t *perm_ok) {
-    const uint64_t total = *em.total;
+                                                            uint64_t cap, uint32_t *perm_ok,
+                                                            OrderScan scan) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    extern __shared__ unsigned long long s_gpre[];      // SCAN: one entry per group
+    __shared__ unsigned long long s_wsum[kOrderWarps];
+    __shared__ unsigned long long s_total;
+    uint64_t total;
+    if (SCAN) {
+        // a contiguous segment of groups per thread, then a block scan of
+        // the segment sums
+        const int ng = (int)((em.n_tracks + kYieldThreads - 1) / kYieldThreads);
+        const int per = (ng + (int)blockDim.x - 1) / (int)blockDim.x;
+        const int a = min((int)threadIdx.x * per, ng), b = min(a + per, ng);
+        unsigned long long seg = 0;
+        for (int g = a; g < b; ++g) seg += scan.group_sums[g];
+        unsigned long long inc = seg;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) s_wsum[w] = inc;
+        __syncthreads();
+        unsigned long long run = inc - seg;
+        for (int k = 0; k < w; ++k) run += s_wsum[k];
+        for (int g = a; g < b; ++g) {
+            s_gpre[g] = run;
+            run += scan.group_sums[g];
+        }
+        if (threadIdx.x == blockDim.x - 1) s_total = run;
+        __syncthreads();
+        total = s_total;
+    } else {
+        total = *em.total;
+    }
     const bool fits = total <= cap;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *perm_ok = fits ? 1u : 0u;
-    if (!fits) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *perm_ok = fits ? 1u : 0u;
+        if (SCAN) {
+            *scan.total = total;
+            scan.offsets[em.n_tracks] = total;
+        }
+    }
+    if (!SCAN && !fits) return;
     __shared__ uint32_t hist_all[kOrderWarps][kAzBins];
     __shared__ uint8_t bins_all[kOrderWarps][kOrderBinCache];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t *hist = hist_all[w];
     uint8_t *bins = bins_all[w];
     const int64_t warps = (int64_t)gridDim.x * kOrderWarps;
     for (int64_t t = (int64_t)blockIdx.x * kOrderWarps + w; t < em.n_tracks; t += warps) {
-        const uint64_t off = em.offsets[t];
-        const uint64_t n64 = em.offsets[t + 1] - off;
+        uint64_t off, n64;
+        if (SCAN) {
+            const int64_t g = t / kYieldThreads;
+            unsigned long long part = 0;
+            for (int64_t i = g * kYieldThreads + lane; i < t; i += 32) part += scan.counts[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
+            off = s_gpre[g] + part;
+            n64 = scan.counts[t];
+            if (lane == 0) scan.offsets[t] = off;
+            if (!fits) continue;
+        } else {
+            off = em.offsets[t];
+            n64 = em.offsets[t + 1] - off;
+        }
         if (n64 == 0 || n64 > kOrderMaxPhotons) continue;   // uniform in the warp
         const uint32_t n = (uint32_t)n64;
         const uint32_t id = em.tracks[t].id, ev = em.tracks[t].event;
         hist[lane] = 0u;
         __syncwarp();
-        for (uint32_t j = lane; j < n; j += 32) {
-            const uint32_t bin = philox10(0u, j, id, ev, em.key0, em.key1).y >> 27;
-            if (j < kOrderBinCache) bins[j] = (uint8_t)bin;
-            atomicAdd(&hist[bin], 1u);
+        // four independent draws per lane in flight
+        for (uint32_t j0 = lane; j0 < n; j0 += 128) {
+            uint32_t bn[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                bn[u] = philox10(0u, j0 + 32u * u, id, ev, em.key0, em.key1).y >> 27;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t j = j0 + 32u * u;
+                if (j < n) {
+                    if (j < kOrderBinCache) bins[j] = (uint8_t)bn[u];
+                    atomicAdd(&hist[bn[u]], 1u);
+                }
+            }
         }
         __syncwarp();
         const uint32_t c = hist[lane];
@@ -478,12 +544,21 @@ __global__ void __launch_bounds__(32 * kOrderWarps) k_order(EmitView em, uint32_
 }
 
 cudaError_t launch_order(const EmitView &em, uint32_t *perm, uint64_t cap, uint32_t *perm_ok,
-                         int n_sm, cudaStream_t s) {
+                         int n_sm, cudaStream_t s, const OrderScan *scan) {
     int64_t blocks = (em.n_tracks + kOrderWarps - 1) / kOrderWarps;
     if (blocks < 1) blocks = 1;
     const int64_t max_blocks = (int64_t)n_sm * 16;
     if (blocks > max_blocks) blocks = max_blocks;
-    k_order<<<(unsigned)blocks, 32 * kOrderWarps, 0, s>>>(em, perm, cap, perm_ok);
+    if (scan) {
+        const int64_t groups = (em.n_tracks + kYieldThreads - 1) / kYieldThreads;
+        if (groups > kOrderScanGroups) return cudaErrorInvalidValue;
+        k_order<true><<<(unsigned)blocks, 32 * kOrderWarps,
+                        sizeof(unsigned long long) * (size_t)groups, s>>>(em, perm, cap, perm_ok,
+                                                                          *scan);
+    }
+    else
+        k_order<false><<<(unsigned)blocks, 32 * kOrderWarps, 0, s>>>(em, perm, cap, perm_ok,
+                                                                     OrderScan{});
     return cudaGetLastError();
 }
 

@@ -266,6 +266,39 @@ def test_azimuth_order_changes_nothing():
         np.testing.assert_array_equal(res[False][k], res[True][k])
 
 
+def test_deferred_scan_matches_scan_pass():
+    """An unsynchronised emission leaves the count scan to the ordering pass
+    (offsets and total from the group sums); a synchronised one runs the
+    scan pass. On 3000 tracks (12 scan groups, a ragged last one, tracks
+    below threshold with no photons), the second emission of a context is
+    ordered either way and both give the same photons, fates, hits and
+    pixel counts."""
+    tr = W.pion_tracks(3000, seed=21, p_min=0.3, p_max=60.0)
+    scene = W.rich1_scene(meshed=True)
+    ctx = rich.Context(0)
+    ctx.init_geometry(scene)
+    dt = rich.DeviceTracks(tr)
+    n = int(ctx.emit(dt, 0.0014, seed=3, sync=True))
+    res = []
+    for sync in (True, False):
+        out = rich.TraceOutputs(n, scene.pixels_per_event, len(scene.planes), 1, n)
+        if sync:
+            assert int(ctx.emit(dt, 0.0014, seed=3, sync=True)) == n
+        else:
+            ctx.emit(dt, 0.0014, seed=3, sync=False)
+        ctx.trace(out, precision=rich.PREC_REFINE64)
+        nh, st = ctx.hits()
+        res.append((st["photon_order"], st["n_photons"], st["fate"], out.fate.cpu().numpy(),
+                    np.sort(out.hits_numpy(nh), order=["event", "track", "photon"]),
+                    out.pixel_counts_numpy()))
+    ctx.close()
+    assert res[0][0] == res[1][0] == 1
+    assert res[0][1] == res[1][1] == n
+    assert res[0][2] == res[1][2]
+    for k in (3, 4, 5):
+        np.testing.assert_array_equal(res[0][k], res[1][k])
+
+
 # --------------------------------------------------------------- edge cases
 def test_zero_tracks_and_empty_emission():
     wl = W.rich1(10)
