@@ -614,7 +614,12 @@ RICH_API rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc 
     }
     const int prim_base = g->n_spheres + g->n_rects;
     std::vector<DevTri> tris((size_t)nt);
+    std::vector<DevTriRef> tri_ref((size_t)nt);
     std::vector<float> normals(any_smooth ? 9 * (size_t)nt : 0);
+    auto split = [](double x, float *hl) {
+        hl[0] = (float)x;
+        hl[1] = (float)(x - (double)hl[0]);
+    };
     for (int64_t k = 0; k < nt; ++k) {
         const int src = bvh.leaf_order[(size_t)k];
         const float *v = g->tri_vertices + 9 * (int64_t)src;
@@ -626,6 +631,24 @@ RICH_API rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc 
         T.material = g->tri_material[src];
         T.pad = bvh.surface_ref[(size_t)k];   // subtree of the triangle's surface
         if (any_smooth) std::memcpy(&normals[9 * (size_t)k], g->tri_normals + 9 * (int64_t)src, 36);
+        // refinement constants: the edges are exact in FP64 (differences of
+        // FP32 numbers), their products too; one rounding per sum
+        const double e1[3] = {(double)v[3] - v[0], (double)v[4] - v[1], (double)v[5] - v[2]};
+        const double e2[3] = {(double)v[6] - v[0], (double)v[7] - v[1], (double)v[8] - v[2]};
+        const double c[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                             e1[0] * e2[1] - e1[1] * e2[0]};
+        const double cl = std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+        DevTriRef &Q = tri_ref[(size_t)k];
+        std::memset(&Q, 0, sizeof Q);
+        for (int a = 0; a < 3; ++a) split(cl > 0.0 ? c[a] / cl : 0.0, Q.ng + 2 * a);
+        const double d00 = e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2];
+        const double d01 = e1[0] * e2[0] + e1[1] * e2[1] + e1[2] * e2[2];
+        const double d11 = e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2];
+        const double den = d00 * d11 - d01 * d01;
+        split(d00, Q.d00);
+        split(d01, Q.d01);
+        split(d11, Q.d11);
+        split(den != 0.0 ? 1.0 / den : 0.0, Q.inv_den);
     }
     std::vector<DevTable> tables(g->n_tables);
     for (int i = 0; i < g->n_tables; ++i) std::memcpy(&tables[i], &g->tables[i], sizeof(DevTable));
@@ -637,11 +660,11 @@ RICH_API rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc 
     size_t sizes[] = {sizeof(DevSphereGroup) * groups.size(), sizeof(DevTile) * tiles.size(),
                       sizeof(DevRect) * rects.size(), sizeof(DevTable) * tables.size(), sizeof(DevMaterial) * mats.size(),
                       sizeof(DevNode) * bvh.nodes.size(), sizeof(DevTri) * tris.size(),
-                      sizeof(float) * normals.size()};
+                      sizeof(float) * normals.size(), sizeof(DevTriRef) * tri_ref.size()};
     const void *srcs[] = {groups.data(), tiles.data(), rects.data(), tables.data(), mats.data(), bvh.nodes.data(), tris.data(),
-                          normals.data()};
-    size_t total = 0, offs[8];
-    for (int i = 0; i < 8; ++i) {
+                          normals.data(), tri_ref.data()};
+    size_t total = 0, offs[9];
+    for (int i = 0; i < 9; ++i) {
         offs[i] = total;
         total += r256(sizes[i]);
     }
@@ -653,7 +676,7 @@ RICH_API rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc 
     void *buf = nullptr;
     RICH_CUDA(cudaMalloc(&buf, std::max<size_t>(total, 256)));
     ctx->d_geom = buf;
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 9; ++i)
         if (sizes[i]) RICH_CUDA(cudaMemcpy((char *)buf + offs[i], srcs[i], sizes[i], cudaMemcpyHostToDevice));
     SceneView sc{};
     auto at = [&](int i) { return sizes[i] ? (const void *)((char *)buf + offs[i]) : nullptr; };
@@ -665,6 +688,7 @@ RICH_API rich_status rich_init_geometry(rich_ctx *ctx, const rich_geometry_desc 
     sc.nodes = (const DevNode *)at(5);
     sc.tris = (const DevTri *)at(6);
     sc.tri_normals = (const float *)at(7);
+    sc.tri_ref = (const DevTriRef *)at(8);
     sc.n_groups = (int)groups.size();
     sc.n_tiles = (int)tiles.size();
     sc.n_rects = (int)rects.size();

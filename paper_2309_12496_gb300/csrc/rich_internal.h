@@ -81,6 +81,16 @@ struct alignas(16) DevNode { // 128 B: boxes of up to four children (by axis) + 
     int32_t pad[4];
 };
 
+// Per triangle (leaf order), constants of the double-word refinement formed
+// once on the host in FP64 and stored as hi + lo pairs: the unit geometric
+// normal and, for the barycentrics of the smooth normal, the edge dot
+// products d00 = e1.e1, d01 = e1.e2, d11 = e2.e2 and 1 / (d00 d11 - d01^2).
+struct alignas(16) DevTriRef { // 64 B
+    float ng[6];               // x hi, x lo, y hi, y lo, z hi, z lo
+    float d00[2], d01[2], d11[2], inv_den[2];
+    float pad[2];
+};
+
 struct alignas(16) TrackRec {  // 64 B, written by the yield kernel
     float x, y, z, len;
     float tx, ty, tz, tan_theta;  // unit direction (normalised in double-word) and tan
@@ -111,6 +121,7 @@ struct SceneView {
     const DevNode *nodes;
     const DevTri *tris;
     const float *tri_normals;   // 9 floats per triangle, leaf order, or null
+    const DevTriRef *tri_ref;   // per triangle, leaf order
     int32_t n_groups, n_tiles, n_rects, n_tables, n_materials, n_nodes;
     int64_t n_tris;
     int32_t tri_prim_base;

@@ -1115,23 +1115,27 @@ __device__ void replay_ff(const SceneView &sc, ff3 o, ff3 d, const RefineRec &rr
         } else {
             const int k_tri = prim - sc.tri_prim_base;   // leaf-order index
             const DevTri T = load_tri(sc.tris + k_tri);
+            // the triangle's refinement constants (unit normal, barycentric
+            // dot products), formed on the host in FP64
+            const float4 *Q = reinterpret_cast<const float4 *>(sc.tri_ref + k_tri);
+            const float4 q0 = __ldg(Q), q1 = __ldg(Q + 1);
             const ff3 v0 = ff3v(T.v0x, T.v0y, T.v0z);
-            const ff3 e1 = ff3_diff(T.v1x, T.v1y, T.v1z, T.v0x, T.v0y, T.v0z);
-            const ff3 e2 = ff3_diff(T.v2x, T.v2y, T.v2z, T.v0x, T.v0y, T.v0z);
-            const ff3 ngt = ff3_cross(e1, e2);
-            const ff t = ff_div(ff3_dot(ff3_sub(v0, o), ngt), ff3_dot(d, ngt));
+            ng = {ff{q0.x, q0.y}, ff{q0.z, q0.w}, ff{q1.x, q1.y}};
+            const ff t = ff_div(ff3_dot(ff3_sub(v0, o), ng), ff3_dot(d, ng));
             o = ff3_axpy(t, d, o);
-            ng = ff3_normalized(ngt);
             mat = T.material;
             const DevMaterial &M = sc.materials[T.material];
             if ((M.flags & RICH_MAT_SMOOTH) && sc.tri_normals) {
                 // barycentrics of the hit in the triangle's plane
+                const float4 q2 = __ldg(Q + 2), q3 = __ldg(Q + 3);
+                const ff3 e1 = ff3_diff(T.v1x, T.v1y, T.v1z, T.v0x, T.v0y, T.v0z);
+                const ff3 e2 = ff3_diff(T.v2x, T.v2y, T.v2z, T.v0x, T.v0y, T.v0z);
                 const ff3 q = ff3_sub(o, v0);
-                const ff d00 = ff3_dot(e1, e1), d01 = ff3_dot(e1, e2), d11 = ff3_dot(e2, e2);
+                const ff d00 = {q1.z, q1.w}, d01 = {q2.x, q2.y}, d11 = {q2.z, q2.w};
+                const ff inv_den = {q3.x, q3.y};
                 const ff d20 = ff3_dot(q, e1), d21 = ff3_dot(q, e2);
-                const ff den = ff_sub(ff_mul(d00, d11), ff_mul(d01, d01));
-                const ff b1 = ff_div(ff_sub(ff_mul(d11, d20), ff_mul(d01, d21)), den);
-                const ff b2 = ff_div(ff_sub(ff_mul(d00, d21), ff_mul(d01, d20)), den);
+                const ff b1 = ff_mul(ff_sub(ff_mul(d11, d20), ff_mul(d01, d21)), inv_den);
+                const ff b2 = ff_mul(ff_sub(ff_mul(d00, d21), ff_mul(d01, d20)), inv_den);
                 const ff b0 = ff_sub(ff_sub(ffv(1.0f), b1), b2);
                 const float *N = sc.tri_normals + 9 * (int64_t)k_tri;
                 const ff3 m = ff3_add(ff3_add(ff3_scale(ff3v(N[0], N[1], N[2]), b0),
@@ -2064,20 +2068,23 @@ __device__ void replay_dual(const SceneView &sc, const GradView &gv, const EmitV
         } else {
             const int k_tri = prim - sc.tri_prim_base;
             const DevTri T = load_tri(sc.tris + k_tri);
+            const float4 *Q = reinterpret_cast<const float4 *>(sc.tri_ref + k_tri);
+            const float4 q0 = __ldg(Q), q1 = __ldg(Q + 1);
             const ff3 v0 = ff3v(T.v0x, T.v0y, T.v0z);
-            const ff3 e1 = ff3_diff(T.v1x, T.v1y, T.v1z, T.v0x, T.v0y, T.v0z);
-            const ff3 e2 = ff3_diff(T.v2x, T.v2y, T.v2z, T.v0x, T.v0y, T.v0z);
-            const ff3 ngt = ff3_cross(e1, e2);
-            const Dm tt = dm_div(dm3_dotc(dm3_csub(v0, o), ngt), dm3_dotc(d, ngt));
+            const ff3 ng = {ff{q0.x, q0.y}, ff{q0.z, q0.w}, ff{q1.x, q1.y}};
+            const Dm tt = dm_div(dm3_dotc(dm3_csub(v0, o), ng), dm3_dotc(d, ng));
             o = dm3_axpy(o, d, tt);
             const DevMaterial &M = sc.materials[T.material];
             if ((M.flags & RICH_MAT_SMOOTH) && sc.tri_normals) {
+                const float4 q2 = __ldg(Q + 2), q3 = __ldg(Q + 3);
+                const ff3 e1 = ff3_diff(T.v1x, T.v1y, T.v1z, T.v0x, T.v0y, T.v0z);
+                const ff3 e2 = ff3_diff(T.v2x, T.v2y, T.v2z, T.v0x, T.v0y, T.v0z);
                 const Dm3 q = dm3_sub(o, dm3_c(v0));
-                const ff d00 = ff3_dot(e1, e1), d01 = ff3_dot(e1, e2), d11 = ff3_dot(e2, e2);
+                const ff d00 = {q1.z, q1.w}, d01 = {q2.x, q2.y}, d11 = {q2.z, q2.w};
+                const ff inv_den = {q3.x, q3.y};
                 const Dm d20 = dm3_dotc(q, e1), d21 = dm3_dotc(q, e2);
-                const ff den = ff_sub(ff_mul(d00, d11), ff_mul(d01, d01));
-                const Dm b1 = dm_divc(dm_sub(dm_scl(d20, d11), dm_scl(d21, d01)), den);
-                const Dm b2 = dm_divc(dm_sub(dm_scl(d21, d00), dm_scl(d20, d01)), den);
+                const Dm b1 = dm_scl(dm_sub(dm_scl(d20, d11), dm_scl(d21, d01)), inv_den);
+                const Dm b2 = dm_scl(dm_sub(dm_scl(d21, d00), dm_scl(d20, d01)), inv_den);
                 const Dm b0 = dm_addf(dm_neg(dm_add(b1, b2)), 1.0f);
                 const float *N = sc.tri_normals + 9 * (int64_t)k_tri;
                 const Dm3 m = {
@@ -2086,7 +2093,7 @@ __device__ void replay_dual(const SceneView &sc, const GradView &gv, const EmitV
                     dm_add(dm_add(dm_scl(b0, N[2]), dm_scl(b1, N[5])), dm_scl(b2, N[8]))};
                 n = dm3_scl(m, dm_rsqrt(dm3_dot(m, m)));
             } else {
-                n = dm3_c(ff3_normalized(ngt));
+                n = dm3_c(ng);
             }
         }
         d = dm3_reflect_unit(d, n);
