@@ -31,7 +31,7 @@ struct rich_ctx {
     // emission scratch
     int64_t track_cap = 0;
     TrackRec *d_rec = nullptr;
-    double2 *d_cs = nullptr;
+    float4 *d_cs = nullptr;
     uint32_t *d_counts = nullptr;
     uint64_t *d_offsets = nullptr;
     unsigned long long *d_bsum = nullptr;
@@ -330,7 +330,7 @@ rich_status emit_core(rich_ctx *ctx, const rich_tracks *t, uint64_t seed, float 
         const int64_t cap = std::max<int64_t>(n + 1, 1024);
         const int64_t blocks = (cap + yield_block_threads() - 1) / yield_block_threads();
         RICH_CUDA(cudaMalloc(&ctx->d_rec, sizeof(TrackRec) * cap));
-        RICH_CUDA(cudaMalloc(&ctx->d_cs, sizeof(double2) * cap));
+        RICH_CUDA(cudaMalloc(&ctx->d_cs, sizeof(float4) * cap));
         RICH_CUDA(cudaMalloc(&ctx->d_counts, sizeof(uint32_t) * cap));
         RICH_CUDA(cudaMalloc(&ctx->d_offsets, sizeof(uint64_t) * (cap + 1)));
         RICH_CUDA(cudaMalloc(&ctx->d_bsum, sizeof(unsigned long long) * (blocks + 1)));

@@ -139,7 +139,9 @@ struct TracksView {          // device SoA of rich_tracks
 
 struct EmitView {            // result of rich_emit used by the trace
     const TrackRec *tracks;
-    const double2 *cos_sin;   // FP64 cos/sin of the Cherenkov angle
+    const float4 *cos_sin;    // (cos hi, cos lo, sin hi, sin lo) of the Cherenkov
+                              // angle; dispersive radiator: (beta, 1 - beta),
+                              // double-words
     const uint64_t *offsets;  // n_tracks + 1
     const unsigned long long *total;
     int64_t n_tracks;
@@ -228,7 +230,7 @@ struct LaunchShape {
 // n_minus_1 or the dispersive radiator of model.
 cudaError_t launch_yield(const TracksView &t, double n_minus_1,
                          double lam_min, double lam_max, uint32_t key0,
-                         uint32_t key1, TrackRec *rec, double2 *cs,
+                         uint32_t key1, TrackRec *rec, float4 *cs,
                          uint32_t *counts, unsigned long long *block_sums,
                          cudaStream_t s, const YieldModel &model);
 cudaError_t launch_offsets(const uint32_t *counts,

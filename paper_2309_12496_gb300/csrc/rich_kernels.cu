@@ -280,7 +280,7 @@ __device__ double disp_yield_per_mm(const YieldModel &m, double beta, double omb
 template <bool RECS>
 __global__ void __launch_bounds__(kYieldBlock)
 k_yield(TracksView t, ff nm1, ff inv_band, uint32_t key0,
-        uint32_t key1, TrackRec *rec, double2 *cs, uint32_t *counts,
+        uint32_t key1, TrackRec *rec, float4 *cs, uint32_t *counts,
         unsigned long long *block_sums, YieldModel model, double lam_min, double lam_max) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t count = 0;
@@ -300,7 +300,7 @@ k_yield(TracksView t, ff nm1, ff inv_band, uint32_t key0,
         const ff nbm1 = ff_sub(ff_mul(nm1, beta), omb);
         ff cos_t = ffv(1.0f), sin_t = ffv(0.0f), mu = ffv(0.0f);
         float tan_f = 0.0f, disp_span = 0.0f, disp_s2max = 0.0f;
-        double2 cs_out;
+        float4 cs_out;
         if (model.iso_yield >= 0.0) {
             // isotropic source: mean photons = yield per mm x length
             mu = ff_mul(lf, ff_from_double(model.iso_yield));
@@ -320,7 +320,8 @@ k_yield(TracksView t, ff nm1, ff inv_band, uint32_t key0,
             tan_f = (float)omb64;                            // stored as 1 - beta
             disp_s2max = disp_s2_f32(model.disp_a, __fdiv_rn(1.0f, model.disp_lambda0),
                                      (float)omb64, (float)lam_min);
-            cs_out = make_double2(1.0 - omb64, omb64);       // (beta, 1 - beta) in FP64
+            const ff b_ff = ff_from_double(1.0 - omb64), o_ff = ff_from_double(omb64);
+            cs_out = make_float4(b_ff.hi, b_ff.lo, o_ff.hi, o_ff.lo);   // (beta, 1 - beta)
         } else if (nbm1.hi > 0.0f) {
             const ff nb = ff_add(nbm1, 1.0f);
             const ff tan_t = ff_sqrt(ff_mul(nbm1, ff_add(nb, 1.0f)));   // (n beta)^2 - 1
@@ -329,7 +330,7 @@ k_yield(TracksView t, ff nm1, ff inv_band, uint32_t key0,
             tan_f = tan_t.hi;
             mu = ff_mul(ff_mul(lf, ff_mul(sin_t, sin_t)), ff_mul(k2PiAlpha, inv_band));
         }
-        if (!model.dispersion) cs_out = make_double2(ff_to_double(cos_t), ff_to_double(sin_t));
+        if (!model.dispersion) cs_out = make_float4(cos_t.hi, cos_t.lo, sin_t.hi, sin_t.lo);
         if (t.n_fixed) {
             count = n_fixed;
         } else {
@@ -1234,10 +1235,10 @@ __device__ __forceinline__ ff3 azimuth_dir_ff(const ff3 &t, ff sp, ff cp) {
 // Emission of photon j of a track with the same draws as emit_photon:
 // the track direction normalised, the origin at s = u L along it, the
 // azimuth 2 pi u from ff_sincos_2pi, cos and sin of the Cherenkov angle
-// from the yield pass (stored as FP64). Isotropic source: cos(theta) =
+// from the yield pass (double-words). Isotropic source: cos(theta) =
 // 1 - 2u (exact) and sin(theta) = 2 sqrt(u (1 - u)) from the exact product
 // u (1 - u).
-__device__ void emit_ff(const TrackRec &tr, double2 cs, uint32_t j, float lam,
+__device__ void emit_ff(const TrackRec &tr, float4 cs, uint32_t j, float lam,
                         const EmitView &em, ff3 &o, ff3 &d) {
     ff3 t;
     ff sp, cp;
@@ -1250,17 +1251,18 @@ __device__ void emit_ff(const TrackRec &tr, double2 cs, uint32_t j, float lam,
         return;
     }
     const ff3 r = azimuth_dir_ff(t, sp, cp);
-    double cos_t = cs.x, sin_t = cs.y;
+    ff ct = {cs.x, cs.y}, st = {cs.z, cs.w};
     if (em.dispersion) {
         // dispersive radiator: the angle of the photon's own wavelength, FP64,
-        // from (beta, 1 - beta) = cs and n(lambda) - 1
+        // from 1 - beta (cs.z + cs.w) and n(lambda) - 1
+        const double omb = (double)cs.z + (double)cs.w;
         const double il0 = 1.0 / (double)em.disp_lambda0, il = 1.0 / (double)lam;
         const double n1 = (double)em.disp_a / ((il0 - il) * (il0 + il));
-        const double nb1 = (n1 - cs.y) - n1 * cs.y;
-        cos_t = 1.0 / (1.0 + nb1);
-        sin_t = nb1 > 0.0 ? sqrt(nb1 * (2.0 + nb1)) * cos_t : 0.0;
+        const double nb1 = (n1 - omb) - n1 * omb;
+        const double cos_t = 1.0 / (1.0 + nb1);
+        ct = ff_from_double(cos_t);
+        st = ff_from_double(nb1 > 0.0 ? sqrt(nb1 * (2.0 + nb1)) * cos_t : 0.0);
     }
-    const ff ct = ff_from_double(cos_t), st = ff_from_double(sin_t);
     d = ff3_normalized({ff_add(ff_mul(t.x, ct), ff_mul(r.x, st)),
                         ff_add(ff_mul(t.y, ct), ff_mul(r.y, st)),
                         ff_add(ff_mul(t.z, ct), ff_mul(r.z, st))});
@@ -2022,7 +2024,7 @@ __device__ __forceinline__ Dm tile_centre(const DevTileDual &T, int c, int ka) {
 __device__ void replay_dual(const SceneView &sc, const GradView &gv, const EmitView &em,
                             const RefineRec &rr, uint32_t j, Dm &u_out, Dm &v_out) {
     const TrackRec tr = em.tracks[rr.index];
-    const double2 cs = em.cos_sin[rr.index];
+    const float4 cs = em.cos_sin[rr.index];
     // emission as in the refinement replay; the tangent of the Cherenkov
     // angle in n - 1: cos = 1 / (n beta) gives d cos / dn = -cos / n and
     // d sin / dn = -cos (d cos / dn) / sin
@@ -2030,7 +2032,7 @@ __device__ void replay_dual(const SceneView &sc, const GradView &gv, const EmitV
     ff sp, cp;
     emit_start_ff(tr, j, em, o0, t, sp, cp);
     const ff3 r = azimuth_dir_ff(t, sp, cp);
-    const ff ct = ff_from_double(cs.x), st = ff_from_double(cs.y);
+    const ff ct = {cs.x, cs.y}, st = {cs.z, cs.w};
     const ff3 d0 = ff3_normalized({ff_add(ff_mul(t.x, ct), ff_mul(r.x, st)),
                                    ff_add(ff_mul(t.y, ct), ff_mul(r.y, st)),
                                    ff_add(ff_mul(t.z, ct), ff_mul(r.z, st))});
@@ -2214,7 +2216,7 @@ cudaError_t launch_philox(const uint32_t *ctr, uint64_t n, uint64_t seed, uint32
 // ============================================================== launchers
 cudaError_t launch_yield(const TracksView &t, double n_minus_1,
                          double lam_min, double lam_max, uint32_t key0,
-                         uint32_t key1, TrackRec *rec, double2 *cs,
+                         uint32_t key1, TrackRec *rec, float4 *cs,
                          uint32_t *counts, unsigned long long *block_sums,
                          cudaStream_t s, const YieldModel &model) {
     if (t.n <= 0) return cudaSuccess;
