@@ -297,6 +297,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "ms_per_step_median": statistics.median(step_ms), "ms_per_step_min": min(step_ms),
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "tracks": N_TRACKS,

@@ -452,7 +452,8 @@ RICH_API rich_status rich_hits(rich_ctx *ctx, uint64_t *n_hits, rich_stats *stat
  * step usually synchronises once. Synchronous. n_hits / stats (may be NULL)
  * as for rich_hits. Returns the status of the first step that failed;
  * RICH_ERR_OVERFLOW also when host_hit_capacity is smaller than n_hits (the
- * first host_hit_capacity records are copied). */
+ * first host_hit_capacity records are copied). host_hits NULL (capacity 0):
+ * no records are copied, only the counters are read. */
 RICH_API rich_status rich_run_host(rich_ctx *ctx, const rich_tracks *host_tracks,
                                    const rich_emit_params *params,
                                    const rich_trace_opts *opts, const rich_outputs *out,

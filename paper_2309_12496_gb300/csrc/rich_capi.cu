@@ -1181,7 +1181,7 @@ RICH_API rich_status rich_run_host(rich_ctx *ctx, const rich_tracks *ht,
                                   ctx->stream));
         RICH_CUDA(cudaStreamSynchronize(ctx->stream));
     }
-    if (nh > host_hit_capacity)
+    if (host_hits && nh > host_hit_capacity)
         return fail(ctx, RICH_ERR_OVERFLOW,
                     "rich_run_host: " + std::to_string(nh) + " hits for a host buffer of " +
                         std::to_string(host_hit_capacity));

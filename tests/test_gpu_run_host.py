@@ -78,6 +78,21 @@ def test_run_host_small_host_buffer(setup):
     assert nh2 == nh
 
 
+def test_run_host_counters_only(setup):
+    """A NULL host buffer: counters only, no overflow status."""
+    ctx, scene, tracks, n, cap, nh, st, ref, ref_fate = setup
+    from paper_2309_12496_gb300.rich import C, Stats, load, _emit_params, _trace_opts
+    ht = rich.HostTracks(tracks)
+    out = rich.TraceOutputs(cap, scene.pixels_per_event, len(scene.planes), 1, n)
+    prm = _emit_params(9, 0.0014, 200.0, 600.0)
+    o = _trace_opts(0, rich.PREC_REFINE64, 8, 16, 1e-3, 0, 0, 0, 0, 0, -1, ())
+    nh2 = C.c_uint64(0)
+    s = Stats()
+    status = load().rich_run_host(ctx.handle, C.byref(ht.desc()), C.byref(prm), C.byref(o),
+                                  C.byref(out.desc()), None, 0, C.byref(nh2), C.byref(s))
+    assert status == 0 and nh2.value == nh and s.n_photons == n
+
+
 def test_run_host_zero_tracks():
     scene = W.rich1_scene(meshed=False)
     ctx = rich.Context(0)
