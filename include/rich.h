@@ -354,7 +354,9 @@ enum {
  * event_sums: FP64 [n_hist_events][n_planes][4] = (hits, sum u, sum v,
  *   sum lambda), accumulated. May be NULL.
  * fate: one byte per photon (RICH_FATE_*) indexed by the photon's global
- *   emission index. May be NULL. */
+ *   emission index, fate_capacity entries; photons at or beyond
+ *   fate_capacity get no entry (size it from the photon total to have all).
+ *   May be NULL. */
 typedef struct rich_outputs {
     rich_hit *hits;
     uint64_t hit_capacity;
@@ -363,6 +365,7 @@ typedef struct rich_outputs {
     uint32_t n_hist_events;
     uint32_t reserved;
     uint8_t *fate;
+    uint64_t fate_capacity;
 } rich_outputs;
 
 /* Counters of the last rich_trace, read by rich_hits. */
@@ -459,6 +462,27 @@ RICH_API rich_status rich_run_host(rich_ctx *ctx, const rich_tracks *host_tracks
                                    const rich_trace_opts *opts, const rich_outputs *out,
                                    rich_hit *host_hits, uint64_t host_hit_capacity,
                                    uint64_t *n_hits, rich_stats *stats);
+
+/* Pipelined form of rich_run_host: enqueues the same step (the track copy,
+ * emit, trace, the early copy of the hit records and the counters' copy) on
+ * the context's stream and returns at once with *ticket (host) naming it;
+ * rich_run_wait completes it. At most two steps are in flight per context
+ * (RICH_ERR_STATE for a third), so the host can enqueue step i + 1 while
+ * the GPU runs step i. Each step in flight needs its own out buffers and
+ * host_hits buffer (rich_run_wait may copy further records from its out);
+ * the host track arrays must stay unchanged until the step is waited for. */
+RICH_API rich_status rich_run_host_async(rich_ctx *ctx, const rich_tracks *host_tracks,
+                                         const rich_emit_params *params,
+                                         const rich_trace_opts *opts, const rich_outputs *out,
+                                         rich_hit *host_hits, uint64_t host_hit_capacity,
+                                         uint64_t *ticket);
+
+/* Completes the pipelined step `ticket`: waits for it, reports its counters
+ * (n_hits, stats as for rich_hits; may be NULL) and copies the hit records
+ * the early copy did not cover. Statuses as for rich_run_host;
+ * RICH_ERR_STATE for a ticket that is not in flight. */
+RICH_API rich_status rich_run_wait(rich_ctx *ctx, uint64_t ticket, uint64_t *n_hits,
+                                   rich_stats *stats);
 
 /* Batched launch as a CUDA graph: captures rich_emit(tracks, params) +
  * rich_trace(fused photons, opts, out) -- the yield kernel, the count scan

@@ -18,6 +18,25 @@
 
 using namespace rich;
 
+// The counters and the photon total share one allocation (the total right
+// after the counters), so one copy reads both.
+constexpr size_t kCtrBytes = sizeof(Counters) + sizeof(unsigned long long);
+static_assert(sizeof(Counters) % 8 == 0, "the photon total follows the counters");
+
+// One step of rich_run_host / rich_run_host_async: where its counters land
+// (pinned), the event after its copies, and what its completion copies.
+struct RunSlot {
+    Counters *h_ctr = nullptr;
+    unsigned long long *h_total = nullptr;
+    cudaEvent_t ev = nullptr;
+    bool in_flight = false;
+    uint64_t ticket = 0;
+    rich_hit *host_hits = nullptr;
+    uint64_t host_cap = 0, early = 0;
+    const rich_hit *dev_hits = nullptr;
+    uint64_t dev_cap = 0;
+};
+
 struct rich_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -83,6 +102,10 @@ struct rich_ctx {
     void *d_host_tracks = nullptr;
     size_t host_tracks_bytes = 0;
     uint64_t run_host_hits = 0;
+    RunSlot run_slots[3];                  // [0], [1]: the asynchronous ring; [2]: the
+                                           // synchronous call
+    uint64_t next_ticket = 1;
+    cudaStream_t copy_stream = nullptr;    // completion copies of finished steps
     // the last emission left its count scan to the ordering pass
     bool scan_pending = false;
 };
@@ -433,24 +456,22 @@ RICH_API rich_status rich_create(rich_ctx **out, int device, void *stream) {
     DeviceGuard g(device);
     cudaDeviceProp prop;
     if ((e = cudaGetDeviceProperties(&prop, device)) != cudaSuccess ||
-        (e = cudaMalloc(&ctx->d_ctr, sizeof(Counters))) != cudaSuccess ||
-        (e = cudaMalloc(&ctx->d_total, sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMalloc(&ctx->d_ctr, kCtrBytes)) != cudaSuccess ||
         (e = cudaMalloc(&ctx->d_perm_ok, sizeof(uint32_t))) != cudaSuccess ||
         (e = cudaMemset(ctx->d_perm_ok, 0, sizeof(uint32_t))) != cudaSuccess ||
-        (e = cudaMallocHost(&ctx->h_ctr, sizeof(Counters))) != cudaSuccess ||
-        (e = cudaMallocHost(&ctx->h_total, sizeof(unsigned long long))) != cudaSuccess ||
-        (e = cudaMemset(ctx->d_ctr, 0, sizeof(Counters))) != cudaSuccess ||
-        (e = cudaMemset(ctx->d_total, 0, sizeof(unsigned long long))) != cudaSuccess) {
+        (e = cudaMallocHost(&ctx->h_ctr, kCtrBytes)) != cudaSuccess ||
+        (e = cudaMemset(ctx->d_ctr, 0, kCtrBytes)) != cudaSuccess) {
         g_create_error = std::string("rich_create: ") + cudaGetErrorString(e);
         cudaGetLastError();
         cudaFree(ctx->d_ctr);
-        cudaFree(ctx->d_total);
         cudaFree(ctx->d_perm_ok);
         cudaFreeHost(ctx->h_ctr);
-        cudaFreeHost(ctx->h_total);
         delete ctx;
         return e == cudaErrorMemoryAllocation ? RICH_ERR_OOM : RICH_ERR_CUDA;
     }
+    // the photon total sits right after the counters (one copy reads both)
+    ctx->d_total = reinterpret_cast<unsigned long long *>(ctx->d_ctr + 1);
+    ctx->h_total = reinterpret_cast<unsigned long long *>(ctx->h_ctr + 1);
     ctx->n_sm = prop.multiProcessorCount;
     ctx->smem_optin = (int)prop.sharedMemPerBlockOptin;
     *out = ctx;
@@ -466,6 +487,11 @@ RICH_API rich_status rich_destroy(rich_ctx *ctx) {
         cudaFree(ctx->d_refine);
         cudaFree(ctx->d_grad_tiles);
         cudaFree(ctx->d_host_tracks);
+        for (RunSlot &S : ctx->run_slots) {
+            cudaFreeHost(S.h_ctr);
+            if (S.ev) cudaEventDestroy(S.ev);
+        }
+        if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
         if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
         if (ctx->graph) cudaGraphDestroy(ctx->graph);
         if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
@@ -475,9 +501,7 @@ RICH_API rich_status rich_destroy(rich_ctx *ctx) {
         cudaFree(ctx->d_perm);
         cudaFree(ctx->d_perm_ok);
         cudaFree(ctx->d_ctr);
-        cudaFree(ctx->d_total);
         cudaFreeHost(ctx->h_ctr);
-        cudaFreeHost(ctx->h_total);
         cudaGetLastError();
     }
     delete ctx;
@@ -860,6 +884,7 @@ RICH_API rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
     p.event_sums = out->event_sums;
     p.n_hist_events = (out->pixel_counts || out->event_sums) ? out->n_hist_events : 0;
     p.fate = out->fate;
+    p.fate_capacity = out->fate ? out->fate_capacity : 0;
     p.refine = ctx->d_refine;
     p.smem_nodes = smem_nodes;
     p.n_prefilter = o->n_prefilter;
@@ -910,10 +935,8 @@ RICH_API rich_status rich_hits(rich_ctx *ctx, uint64_t *n_hits, rich_stats *stat
     if (!ctx) return RICH_ERR_ARG;
     if (!ctx->traced) return fail(ctx, RICH_ERR_STATE, "rich_hits: no trace to report");
     DeviceGuard guard(ctx->device);
-    RICH_CUDA(cudaMemcpyAsync(ctx->h_ctr, ctx->d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost,
+    RICH_CUDA(cudaMemcpyAsync(ctx->h_ctr, ctx->d_ctr, kCtrBytes, cudaMemcpyDeviceToHost,
                               ctx->stream));
-    RICH_CUDA(cudaMemcpyAsync(ctx->h_total, ctx->d_total, sizeof(unsigned long long),
-                              cudaMemcpyDeviceToHost, ctx->stream));
     RICH_CUDA(cudaStreamSynchronize(ctx->stream));
     if (!ctx->last_ext) ctx->known_total = std::max<uint64_t>(ctx->known_total, *ctx->h_total);
     const Counters &c = *ctx->h_ctr;
@@ -1046,6 +1069,7 @@ RICH_API rich_status rich_trace_grad(rich_ctx *ctx, const rich_tracks *t,
     p.event_sums = nullptr;
     p.n_hist_events = out->pixel_counts ? out->n_hist_events : 0;
     p.fate = out->fate;
+    p.fate_capacity = out->fate ? out->fate_capacity : 0;
     p.refine = ctx->d_refine;
     p.smem_nodes = smem_nodes;
     if (p.max_bounces < 1 || p.max_bounces > RICH_MAX_BOUNCES || p.max_steps < 1 ||
@@ -1075,10 +1099,8 @@ RICH_API rich_status rich_trace_grad(rich_ctx *ctx, const rich_tracks *t,
     RICH_CUDA(launch_adjoint(sv, em, p, gv, ctx->d_ctr, ctx->n_sm, ctx->stream));
     RICH_CUDA(cudaMemcpyAsync(ctx->h_acc, ctx->d_acc, sizeof(double) * 12,
                               cudaMemcpyDeviceToHost, ctx->stream));
-    RICH_CUDA(cudaMemcpyAsync(ctx->h_ctr, ctx->d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost,
+    RICH_CUDA(cudaMemcpyAsync(ctx->h_ctr, ctx->d_ctr, kCtrBytes, cudaMemcpyDeviceToHost,
                               ctx->stream));
-    RICH_CUDA(cudaMemcpyAsync(ctx->h_total, ctx->d_total, sizeof(unsigned long long),
-                              cudaMemcpyDeviceToHost, ctx->stream));
     RICH_CUDA(cudaStreamSynchronize(ctx->stream));
     ctx->traced = true;
     ctx->last_ext = false;
@@ -1099,25 +1121,26 @@ RICH_API rich_status rich_trace_grad(rich_ctx *ctx, const rich_tracks *t,
     return RICH_OK;
 }
 
-RICH_API rich_status rich_run_host(rich_ctx *ctx, const rich_tracks *ht,
-                                   const rich_emit_params *prm, const rich_trace_opts *o,
-                                   const rich_outputs *out, rich_hit *host_hits,
-                                   uint64_t host_hit_capacity, uint64_t *n_hits,
-                                   rich_stats *stats) {
-    if (!ctx) return RICH_ERR_ARG;
-    if (!ht || !prm || !o || !out)
-        return fail(ctx, RICH_ERR_ARG, "rich_run_host: NULL argument");
-    if (ht->n < 0) return fail(ctx, RICH_ERR_ARG, "rich_run_host: negative track count");
-    if (host_hit_capacity && !host_hits)
-        return fail(ctx, RICH_ERR_ARG, "rich_run_host: host_hits is NULL");
+// Enqueues one step from host memory into slot S (see rich_run_host).
+static rich_status run_enqueue(rich_ctx *ctx, const char *who, const rich_tracks *ht,
+                               const rich_emit_params *prm, const rich_trace_opts *o,
+                               const rich_outputs *out, rich_hit *host_hits,
+                               uint64_t host_hit_capacity, RunSlot &S) {
+    const std::string w(who);
+    if (!ht || !prm || !o || !out) return fail(ctx, RICH_ERR_ARG, w + ": NULL argument");
+    if (ht->n < 0) return fail(ctx, RICH_ERR_ARG, w + ": negative track count");
+    if (host_hit_capacity && !host_hits) return fail(ctx, RICH_ERR_ARG, w + ": host_hits is NULL");
     const size_t n = (size_t)ht->n;
     // the arrays in argument order; NULL optional ones are skipped
     const void *src[12] = {ht->x, ht->y, ht->z, ht->dx, ht->dy, ht->dz, ht->p, ht->mass,
                            ht->length, ht->event, ht->id, ht->n_fixed};
     for (int k = 0; k < 10; ++k)
-        if (n && !src[k])
-            return fail(ctx, RICH_ERR_ARG, "rich_run_host: a required track array is NULL");
-    DeviceGuard guard(ctx->device);
+        if (n && !src[k]) return fail(ctx, RICH_ERR_ARG, w + ": a required track array is NULL");
+    if (!S.h_ctr) {
+        RICH_CUDA(cudaMallocHost(&S.h_ctr, kCtrBytes));
+        S.h_total = reinterpret_cast<unsigned long long *>(S.h_ctr + 1);
+        RICH_CUDA(cudaEventCreateWithFlags(&S.ev, cudaEventDisableTiming));
+    }
     const size_t field = 4 * n;
     const size_t need = std::max<size_t>(12 * field, 256);
     if (need > ctx->host_tracks_bytes) {
@@ -1163,29 +1186,112 @@ RICH_API rich_status rich_run_host(rich_ctx *ctx, const rich_tracks *ht,
     if (st != RICH_OK) return st;
     st = rich_trace(ctx, nullptr, o, out);
     if (st != RICH_OK) return st;
-    // early copy of the expected hit records, then the counters' round trip
+    // early copy of the expected hit records, then the counters, then the
+    // step's event
     uint64_t early = ctx->run_host_hits ? ctx->run_host_hits + ctx->run_host_hits / 4 : 0;
     early = std::min(early, std::min(host_hit_capacity, out->hit_capacity));
     if (early)
         RICH_CUDA(cudaMemcpyAsync(host_hits, out->hits, early * sizeof(rich_hit),
                                   cudaMemcpyDeviceToHost, ctx->stream));
-    uint64_t nh = 0;
-    st = rich_hits(ctx, &nh, stats);
-    if (n_hits) *n_hits = nh;
-    if (st != RICH_OK) return st;
-    ctx->run_host_hits = nh;
-    const uint64_t want = std::min(nh, host_hit_capacity);
-    if (want > early) {
-        RICH_CUDA(cudaMemcpyAsync(host_hits + early, out->hits + early,
-                                  (want - early) * sizeof(rich_hit), cudaMemcpyDeviceToHost,
-                                  ctx->stream));
-        RICH_CUDA(cudaStreamSynchronize(ctx->stream));
-    }
-    if (host_hits && nh > host_hit_capacity)
-        return fail(ctx, RICH_ERR_OVERFLOW,
-                    "rich_run_host: " + std::to_string(nh) + " hits for a host buffer of " +
-                        std::to_string(host_hit_capacity));
+    RICH_CUDA(cudaMemcpyAsync(S.h_ctr, ctx->d_ctr, kCtrBytes, cudaMemcpyDeviceToHost,
+                              ctx->stream));
+    RICH_CUDA(cudaEventRecord(S.ev, ctx->stream));
+    S.host_hits = host_hits;
+    S.host_cap = host_hit_capacity;
+    S.early = early;
+    S.dev_hits = out->hits;
+    S.dev_cap = out->hit_capacity;
+    S.in_flight = true;
     return RICH_OK;
+}
+
+// Waits for the step in slot S, reports its counters (as rich_hits) and
+// copies the hit records the early copy did not cover.
+static rich_status run_complete(rich_ctx *ctx, const char *who, RunSlot &S, uint64_t *n_hits,
+                                rich_stats *stats) {
+    const std::string w(who);
+    S.in_flight = false;
+    RICH_CUDA(cudaEventSynchronize(S.ev));
+    const Counters &c = *S.h_ctr;
+    const uint64_t total = *S.h_total;
+    ctx->known_total = std::max<uint64_t>(ctx->known_total, total);
+    if (n_hits) *n_hits = c.hits;
+    if (stats) {
+        std::memset(stats, 0, sizeof *stats);
+        stats->n_photons = total;
+        stats->n_hits = c.hits;
+        for (int k = 0; k < RICH_N_FATES; ++k) stats->n_fate[k] = c.fate[k];
+        stats->device_status = c.status;
+        stats->photon_order = c.ordered;
+    }
+    if (c.status != 0)
+        return fail(ctx, (rich_status)c.status,
+                    w + ": device reported status " + std::to_string(c.status));
+    if (c.hits > S.dev_cap)
+        return fail(ctx, RICH_ERR_OVERFLOW, w + ": " + std::to_string(c.hits) +
+                                                " hits for capacity " + std::to_string(S.dev_cap));
+    ctx->run_host_hits = c.hits;
+    const uint64_t want = std::min<uint64_t>(c.hits, S.host_cap);
+    if (want > S.early) {
+        // the step's own output buffer (a later step in flight writes another)
+        if (!ctx->copy_stream)
+            RICH_CUDA(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+        RICH_CUDA(cudaMemcpyAsync(S.host_hits + S.early, S.dev_hits + S.early,
+                                  (want - S.early) * sizeof(rich_hit), cudaMemcpyDeviceToHost,
+                                  ctx->copy_stream));
+        RICH_CUDA(cudaStreamSynchronize(ctx->copy_stream));
+    }
+    if (S.host_hits && c.hits > S.host_cap)
+        return fail(ctx, RICH_ERR_OVERFLOW, w + ": " + std::to_string(c.hits) +
+                                                " hits for a host buffer of " +
+                                                std::to_string(S.host_cap));
+    return RICH_OK;
+}
+
+RICH_API rich_status rich_run_host(rich_ctx *ctx, const rich_tracks *ht,
+                                   const rich_emit_params *prm, const rich_trace_opts *o,
+                                   const rich_outputs *out, rich_hit *host_hits,
+                                   uint64_t host_hit_capacity, uint64_t *n_hits,
+                                   rich_stats *stats) {
+    if (!ctx) return RICH_ERR_ARG;
+    DeviceGuard guard(ctx->device);
+    RunSlot &S = ctx->run_slots[2];
+    const rich_status st = run_enqueue(ctx, "rich_run_host", ht, prm, o, out, host_hits,
+                                       host_hit_capacity, S);
+    if (st != RICH_OK) return st;
+    return run_complete(ctx, "rich_run_host", S, n_hits, stats);
+}
+
+RICH_API rich_status rich_run_host_async(rich_ctx *ctx, const rich_tracks *ht,
+                                         const rich_emit_params *prm, const rich_trace_opts *o,
+                                         const rich_outputs *out, rich_hit *host_hits,
+                                         uint64_t host_hit_capacity, uint64_t *ticket) {
+    if (!ctx) return RICH_ERR_ARG;
+    if (!ticket) return fail(ctx, RICH_ERR_ARG, "rich_run_host_async: ticket is NULL");
+    const uint64_t t = ctx->next_ticket;
+    RunSlot &S = ctx->run_slots[t % 2];
+    if (S.in_flight)
+        return fail(ctx, RICH_ERR_STATE,
+                    "rich_run_host_async: two steps are in flight; wait for the older one");
+    DeviceGuard guard(ctx->device);
+    const rich_status st = run_enqueue(ctx, "rich_run_host_async", ht, prm, o, out, host_hits,
+                                       host_hit_capacity, S);
+    if (st != RICH_OK) return st;
+    S.ticket = t;
+    ctx->next_ticket = t + 1;
+    *ticket = t;
+    return RICH_OK;
+}
+
+RICH_API rich_status rich_run_wait(rich_ctx *ctx, uint64_t ticket, uint64_t *n_hits,
+                                   rich_stats *stats) {
+    if (!ctx) return RICH_ERR_ARG;
+    RunSlot &S = ctx->run_slots[ticket % 2];
+    if (ticket == 0 || !S.in_flight || S.ticket != ticket)
+        return fail(ctx, RICH_ERR_STATE, "rich_run_wait: no step in flight with ticket " +
+                                             std::to_string(ticket));
+    DeviceGuard guard(ctx->device);
+    return run_complete(ctx, "rich_run_wait", S, n_hits, stats);
 }
 
 RICH_API rich_status rich_graph_capture(rich_ctx *ctx, const rich_tracks *t,

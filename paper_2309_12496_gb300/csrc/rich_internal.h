@@ -189,6 +189,7 @@ struct TraceParams {
     double *event_sums;
     uint32_t n_hist_events;
     uint8_t *fate;
+    uint64_t fate_capacity;   // entries of fate; photons beyond get none
     RefineRec *refine;        // capacity hit_capacity (refined precision only)
     int32_t smem_nodes;       // BVH nodes [0, smem_nodes) staged in shared memory
     int32_t n_prefilter;      // > 0: efficiencies applied before propagation

@@ -1605,7 +1605,7 @@ k_trace(TraceArgs A) {
                             emit_photon(tr, j, em, w0, lam, ph);
                     }
                     if (rejected) {
-                        if (P.fate) P.fate[ph.g] = (uint8_t)RICH_FATE_PREFILTERED;
+                        if (ph.g < P.fate_capacity) P.fate[ph.g] = (uint8_t)RICH_FATE_PREFILTERED;
                     } else {
                         alive = true;
                     }
@@ -1811,7 +1811,7 @@ k_trace(TraceArgs A) {
         }
         add_event_sums(sc, P, binned_here, ph.event, hplane, ffv(hu), ffv(hv), ph.lam, s_es);
         if (fate != 0) {
-            if (P.fate) P.fate[ph.g] = (uint8_t)fate;
+            if (ph.g < P.fate_capacity) P.fate[ph.g] = (uint8_t)fate;
             atomicAdd(&s_fate[fate], 1ull);
             alive = false;
         }

@@ -32,7 +32,8 @@ N_FATES = 9
 EXPORTED = ["rich_create", "rich_destroy", "rich_set_stream", "rich_init_geometry",
             "rich_emit", "rich_trace", "rich_hits", "rich_philox", "rich_last_error",
             "rich_version", "rich_photon_counts_static", "rich_trace_grad",
-            "rich_graph_capture", "rich_graph_launch", "rich_run_host"]
+            "rich_graph_capture", "rich_graph_launch", "rich_run_host", "rich_run_host_async",
+            "rich_run_wait"]
 
 # bytes a counters' read (rich_hits) brings back: the device counters (96 B)
 # and the photon total (8 B)
@@ -145,7 +146,7 @@ class Outputs(C.Structure):
     _fields_ = [("hits", C.c_void_p), ("hit_capacity", C.c_uint64),
                 ("pixel_counts", C.c_void_p), ("event_sums", C.c_void_p),
                 ("n_hist_events", C.c_uint32), ("reserved", C.c_uint32),
-                ("fate", C.c_void_p)]
+                ("fate", C.c_void_p), ("fate_capacity", C.c_uint64)]
 
 
 class GradParams(C.Structure):
@@ -199,13 +200,17 @@ def load():
         L.rich_run_host.argtypes = [vp, C.POINTER(TracksDesc), C.POINTER(EmitParams),
                                     C.POINTER(TraceOpts), C.POINTER(Outputs), vp, C.c_uint64,
                                     C.POINTER(C.c_uint64), C.POINTER(Stats)]
+        L.rich_run_host_async.argtypes = [vp, C.POINTER(TracksDesc), C.POINTER(EmitParams),
+                                          C.POINTER(TraceOpts), C.POINTER(Outputs), vp,
+                                          C.c_uint64, C.POINTER(C.c_uint64)]
+        L.rich_run_wait.argtypes = [vp, C.c_uint64, C.POINTER(C.c_uint64), C.POINTER(Stats)]
         L.rich_last_error.argtypes = [vp]
         L.rich_last_error.restype = C.c_char_p
         L.rich_version.restype = C.c_char_p
         for f in ("rich_create", "rich_destroy", "rich_set_stream", "rich_init_geometry",
                   "rich_emit", "rich_trace", "rich_hits", "rich_philox",
                   "rich_photon_counts_static", "rich_trace_grad", "rich_graph_capture",
-                  "rich_graph_launch", "rich_run_host"):
+                  "rich_graph_launch", "rich_run_host", "rich_run_host_async", "rich_run_wait"):
             getattr(L, f).restype = C.c_int
         _lib = L
         return L
@@ -389,7 +394,8 @@ class TraceOutputs:
                        event_sums=None if self.event_sums is None else self.event_sums.data_ptr(),
                        n_hist_events=self.n_hist_events if (self.pixel_counts is not None or
                                                             self.event_sums is not None) else 0,
-                       fate=None if self.fate is None else self.fate.data_ptr())
+                       fate=None if self.fate is None else self.fate.data_ptr(),
+                       fate_capacity=0 if self.fate is None else self.fate.numel())
 
     def hits_numpy(self, n):
         n = min(int(n), self.hit_capacity)
@@ -513,6 +519,35 @@ class Context:
         return n.value, {"n_photons": s.n_photons, "n_hits": s.n_hits, "fate": list(s.n_fate),
                          "device_status": s.device_status, "photon_order": s.photon_order}
 
+    def run_host_async(self, tracks: HostTracks, outputs: TraceOutputs, hits_host, n_minus_1,
+                       lambda_min=200.0, lambda_max=600.0, seed=0, precision=PREC_REFINE64,
+                       max_bounces=8, max_steps=16, t_min=1e-3, block_threads=0,
+                       blocks_per_sm=0, refill_min=0, chunk=0, wide_regs=0,
+                       bvh_smem_nodes=-1, prefilter=()):
+        """Pipelined step (rich_run_host_async): returns a ticket for
+        run_wait. Two steps may be in flight, each with its own outputs and
+        hits_host; the HostTracks must not change until waited for."""
+        prm = _emit_params(seed, n_minus_1, lambda_min, lambda_max, SOURCE_CHERENKOV, 0.0,
+                           -1, None)
+        o = _trace_opts(0, precision, max_bounces, max_steps, t_min, block_threads,
+                        blocks_per_sm, refill_min, chunk, wide_regs, bvh_smem_nodes, prefilter)
+        t = C.c_uint64(0)
+        cap = hits_host.numel() * hits_host.element_size() // HIT_DTYPE.itemsize
+        st = load().rich_run_host_async(self.handle, C.byref(tracks.desc()), C.byref(prm),
+                                        C.byref(o), C.byref(outputs.desc()), hits_host.data_ptr(),
+                                        cap, C.byref(t))
+        _check(self.handle, st)
+        return t.value
+
+    def run_wait(self, ticket):
+        """Completes a pipelined step: (n_hits, stats dict)."""
+        n = C.c_uint64(0)
+        s = Stats()
+        st = load().rich_run_wait(self.handle, int(ticket), C.byref(n), C.byref(s))
+        _check(self.handle, st)
+        return n.value, {"n_photons": s.n_photons, "n_hits": s.n_hits, "fate": list(s.n_fate),
+                         "device_status": s.device_status, "photon_order": s.photon_order}
+
     def philox(self, counters, seed):
         """Library Philox4x32-10 of an (n, 4) uint32 counter array."""
         torch = _torch()
@@ -612,6 +647,14 @@ def rich_hits(ctx: Context, **kw):
 
 def rich_run_host(ctx: Context, tracks: HostTracks, outputs, hits_host, n_minus_1, **kw):
     return ctx.run_host(tracks, outputs, hits_host, n_minus_1, **kw)
+
+
+def rich_run_host_async(ctx: Context, tracks: HostTracks, outputs, hits_host, n_minus_1, **kw):
+    return ctx.run_host_async(tracks, outputs, hits_host, n_minus_1, **kw)
+
+
+def rich_run_wait(ctx: Context, ticket):
+    return ctx.run_wait(ticket)
 
 
 def rich_photon_counts_static(tracks: DeviceTracks, n_minus_1, counts, offsets,

@@ -93,6 +93,25 @@ def test_run_host_counters_only(setup):
     assert status == 0 and nh2.value == nh and s.n_photons == n
 
 
+def test_fate_array_smaller_than_the_photon_total(setup):
+    """Photons at or beyond fate_capacity get no fate entry (nothing is
+    written past the array); the entries below it equal a full array's."""
+    ctx, scene, tracks, n, cap, nh, st, ref, ref_fate = setup
+    dt = rich.DeviceTracks(tracks)
+    k = n // 3
+    small = rich.TraceOutputs(cap, scene.pixels_per_event, len(scene.planes), 1, 0)
+    storage = torch.zeros(k + 64, dtype=torch.uint8, device="cuda")
+    small.fate = storage[:k]              # the binding passes numel() as the capacity
+    assert ctx.emit(dt, 0.0014, seed=9) == n
+    ctx.trace(small, precision=rich.PREC_REFINE64)
+    nh2, _ = ctx.hits()
+    assert nh2 == nh
+    torch.cuda.synchronize()
+    got = storage.cpu().numpy()
+    np.testing.assert_array_equal(got[:k], ref_fate[:k])
+    assert not got[k:].any()              # nothing written past the capacity
+
+
 def test_run_host_zero_tracks():
     scene = W.rich1_scene(meshed=False)
     ctx = rich.Context(0)
@@ -104,3 +123,49 @@ def test_run_host_zero_tracks():
     nh, st = ctx.run_host(ht, out, hits_host, 0.0014, seed=1)
     assert nh == 0 and st["n_photons"] == 0
     ctx.close()
+
+
+def test_run_host_async_pipeline_matches_sync(setup):
+    """Two steps in flight (rich_run_host_async / rich_run_wait), each with
+    its own outputs: every step equals the synchronous call of the same seed
+    (counters, fates, hit records); a third step in flight is refused and a
+    waited ticket is no longer in flight."""
+    ctx, scene, tracks, n, cap, nh, st, ref, ref_fate = setup
+    ht = rich.HostTracks(tracks)
+    seeds = [11, 12, 13, 14]
+    # fate arrays with room for every seed's photons (the counts differ by seed)
+    out_s = rich.TraceOutputs(cap, scene.pixels_per_event, len(scene.planes), 1, 2 * n)
+    host_s = torch.empty(cap * rich.HIT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    want = {}
+    for s in seeds:
+        nh_s, st_s = ctx.run_host(ht, out_s, host_s, 0.0014, seed=s)
+        recs = np.frombuffer(host_s.numpy()[: nh_s * rich.HIT_DTYPE.itemsize].tobytes(),
+                             rich.HIT_DTYPE)
+        want[s] = (nh_s, st_s, _sorted(recs), out_s.fate[: st_s["n_photons"]].cpu().numpy())
+    outs = [rich.TraceOutputs(cap, scene.pixels_per_event, len(scene.planes), 1, 2 * n)
+            for _ in range(2)]
+    hosts = [torch.empty(cap * rich.HIT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+             for _ in range(2)]
+    tickets = [ctx.run_host_async(ht, outs[0], hosts[0], 0.0014, seed=seeds[0])]
+    for k, s in enumerate(seeds):
+        if k + 1 < len(seeds):
+            tickets.append(ctx.run_host_async(ht, outs[(k + 1) % 2], hosts[(k + 1) % 2], 0.0014,
+                                              seed=seeds[k + 1]))
+        nh_k, st_k = ctx.run_wait(tickets[k])
+        nh_s, st_s, recs_s, fate_s = want[s]
+        assert nh_k == nh_s and st_k == st_s
+        recs = np.frombuffer(hosts[k % 2].numpy()[: nh_k * rich.HIT_DTYPE.itemsize].tobytes(),
+                             rich.HIT_DTYPE)
+        np.testing.assert_array_equal(_sorted(recs), recs_s)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(outs[k % 2].fate[: st_k["n_photons"]].cpu().numpy(), fate_s)
+    t1 = ctx.run_host_async(ht, outs[0], hosts[0], 0.0014, seed=1)
+    t2 = ctx.run_host_async(ht, outs[1], hosts[1], 0.0014, seed=2)
+    with pytest.raises(rich.RichError) as e:
+        ctx.run_host_async(ht, outs[0], hosts[0], 0.0014, seed=3)
+    assert e.value.status == 7                      # RICH_ERR_STATE
+    ctx.run_wait(t1)
+    ctx.run_wait(t2)
+    with pytest.raises(rich.RichError) as e:
+        ctx.run_wait(t2)
+    assert e.value.status == 7
