@@ -324,9 +324,13 @@ def main():
             line["other_sources"] = run_sources(dev, prec, rank)
     if line is not None and not args.no_extras and ws == 1:
         v, cores, passes, nph, el = oracle_rate(10.0)
+        v1, _, passes1, nph1, el1 = oracle_rate(3.0, n_threads=1)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"{passes} passes of the workload ({nph} photons, "
-                                          f"{el:.1f} s)"}
+                                          f"{el:.1f} s)",
+                                "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                                                  "sample": f"{passes1} passes ({nph1} photons, "
+                                                            f"{el1:.1f} s)"}}
     if line is not None:
         print(json.dumps(line))
     ctx.close()
