@@ -28,7 +28,11 @@ static_assert(sizeof(Counters) % 8 == 0, "the photon total follows the counters"
 struct RunSlot {
     Counters *h_ctr = nullptr;
     unsigned long long *h_total = nullptr;
-    cudaEvent_t ev = nullptr;
+    cudaEvent_t ev = nullptr;              // the step's kernels and counters' copy
+    cudaEvent_t ev_h2d = nullptr;          // its tracks on the device
+    cudaEvent_t ev_copy = nullptr;         // its early hit copy (copy stream)
+    void *d_tracks = nullptr;              // its device copy of the host tracks
+    size_t d_tracks_bytes = 0;
     bool in_flight = false;
     uint64_t ticket = 0;
     rich_hit *host_hits = nullptr;
@@ -97,15 +101,14 @@ struct rich_ctx {
     cudaGraphExec_t graph_exec = nullptr;
     cudaStream_t capture_stream = nullptr;
     uint64_t graph_capacity = 0;
-    // rich_run_host: device copy of the caller's host tracks, and the hit
-    // count of its last step (sizes the next step's early hit copy)
-    void *d_host_tracks = nullptr;
-    size_t host_tracks_bytes = 0;
+    // rich_run_host*: the hit count of the last completed step (sizes the
+    // next step's early hit copy), the step slots and their copy streams
     uint64_t run_host_hits = 0;
     RunSlot run_slots[3];                  // [0], [1]: the asynchronous ring; [2]: the
                                            // synchronous call
     uint64_t next_ticket = 1;
-    cudaStream_t copy_stream = nullptr;    // completion copies of finished steps
+    cudaStream_t copy_stream = nullptr;    // device-to-host copies of the steps' hits
+    cudaStream_t up_stream = nullptr;      // host-to-device copies of the steps' tracks
     // the last emission left its count scan to the ordering pass
     bool scan_pending = false;
 };
@@ -486,12 +489,15 @@ RICH_API rich_status rich_destroy(rich_ctx *ctx) {
         cudaFree(ctx->d_geom);
         cudaFree(ctx->d_refine);
         cudaFree(ctx->d_grad_tiles);
-        cudaFree(ctx->d_host_tracks);
         for (RunSlot &S : ctx->run_slots) {
             cudaFreeHost(S.h_ctr);
+            cudaFree(S.d_tracks);
             if (S.ev) cudaEventDestroy(S.ev);
+            if (S.ev_h2d) cudaEventDestroy(S.ev_h2d);
+            if (S.ev_copy) cudaEventDestroy(S.ev_copy);
         }
         if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+        if (ctx->up_stream) cudaStreamDestroy(ctx->up_stream);
         if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
         if (ctx->graph) cudaGraphDestroy(ctx->graph);
         if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
@@ -1140,20 +1146,27 @@ static rich_status run_enqueue(rich_ctx *ctx, const char *who, const rich_tracks
         RICH_CUDA(cudaMallocHost(&S.h_ctr, kCtrBytes));
         S.h_total = reinterpret_cast<unsigned long long *>(S.h_ctr + 1);
         RICH_CUDA(cudaEventCreateWithFlags(&S.ev, cudaEventDisableTiming));
+        RICH_CUDA(cudaEventCreateWithFlags(&S.ev_h2d, cudaEventDisableTiming));
+        RICH_CUDA(cudaEventCreateWithFlags(&S.ev_copy, cudaEventDisableTiming));
     }
+    if (!ctx->copy_stream)
+        RICH_CUDA(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    if (!ctx->up_stream)
+        RICH_CUDA(cudaStreamCreateWithFlags(&ctx->up_stream, cudaStreamNonBlocking));
     const size_t field = 4 * n;
     const size_t need = std::max<size_t>(12 * field, 256);
-    if (need > ctx->host_tracks_bytes) {
-        RICH_CUDA(cudaStreamSynchronize(ctx->stream));
-        drop_graph(ctx);
-        cudaFree(ctx->d_host_tracks);
-        ctx->d_host_tracks = nullptr;
-        ctx->host_tracks_bytes = 0;
-        RICH_CUDA(cudaMalloc(&ctx->d_host_tracks, need));
-        ctx->host_tracks_bytes = need;
+    if (need > S.d_tracks_bytes) {
+        // the slot is not in flight: its earlier step has completed
+        cudaFree(S.d_tracks);
+        S.d_tracks = nullptr;
+        S.d_tracks_bytes = 0;
+        RICH_CUDA(cudaMalloc(&S.d_tracks, need));
+        S.d_tracks_bytes = need;
     }
-    char *dbase = static_cast<char *>(ctx->d_host_tracks);
-    // runs of arrays that lie back to back on the host: one copy per run
+    char *dbase = static_cast<char *>(S.d_tracks);
+    // the tracks travel on the upload stream, so they can move while an
+    // earlier step computes (runs of arrays that lie back to back on the
+    // host: one copy per run); the step's kernels wait for them
     if (n) {
         int k = 0;
         while (k < 12) {
@@ -1163,10 +1176,12 @@ static rich_status run_enqueue(rich_ctx *ctx, const char *who, const rich_tracks
                    static_cast<const char *>(src[e]) == static_cast<const char *>(src[e - 1]) + field)
                 ++e;
             RICH_CUDA(cudaMemcpyAsync(dbase + k * field, src[k], (e - k) * field,
-                                      cudaMemcpyHostToDevice, ctx->stream));
+                                      cudaMemcpyHostToDevice, ctx->up_stream));
             k = e;
         }
     }
+    RICH_CUDA(cudaEventRecord(S.ev_h2d, ctx->up_stream));
+    RICH_CUDA(cudaStreamWaitEvent(ctx->stream, S.ev_h2d, 0));
     auto dev = [&](int k) -> const void * { return src[k] ? dbase + k * field : nullptr; };
     rich_tracks dt;
     dt.n = ht->n;
@@ -1186,16 +1201,20 @@ static rich_status run_enqueue(rich_ctx *ctx, const char *who, const rich_tracks
     if (st != RICH_OK) return st;
     st = rich_trace(ctx, nullptr, o, out);
     if (st != RICH_OK) return st;
-    // early copy of the expected hit records, then the counters, then the
-    // step's event
-    uint64_t early = ctx->run_host_hits ? ctx->run_host_hits + ctx->run_host_hits / 4 : 0;
-    early = std::min(early, std::min(host_hit_capacity, out->hit_capacity));
-    if (early)
-        RICH_CUDA(cudaMemcpyAsync(host_hits, out->hits, early * sizeof(rich_hit),
-                                  cudaMemcpyDeviceToHost, ctx->stream));
+    // the counters on the compute stream (the next step resets them); the
+    // early copy of the expected hit records on the copy stream, after the
+    // step's kernels (the next step writes another output buffer)
     RICH_CUDA(cudaMemcpyAsync(S.h_ctr, ctx->d_ctr, kCtrBytes, cudaMemcpyDeviceToHost,
                               ctx->stream));
     RICH_CUDA(cudaEventRecord(S.ev, ctx->stream));
+    uint64_t early = ctx->run_host_hits ? ctx->run_host_hits + ctx->run_host_hits / 4 : 0;
+    early = std::min(early, std::min(host_hit_capacity, out->hit_capacity));
+    if (early) {
+        RICH_CUDA(cudaStreamWaitEvent(ctx->copy_stream, S.ev, 0));
+        RICH_CUDA(cudaMemcpyAsync(host_hits, out->hits, early * sizeof(rich_hit),
+                                  cudaMemcpyDeviceToHost, ctx->copy_stream));
+    }
+    RICH_CUDA(cudaEventRecord(S.ev_copy, ctx->copy_stream));
     S.host_hits = host_hits;
     S.host_cap = host_hit_capacity;
     S.early = early;
@@ -1212,6 +1231,7 @@ static rich_status run_complete(rich_ctx *ctx, const char *who, RunSlot &S, uint
     const std::string w(who);
     S.in_flight = false;
     RICH_CUDA(cudaEventSynchronize(S.ev));
+    RICH_CUDA(cudaEventSynchronize(S.ev_copy));
     const Counters &c = *S.h_ctr;
     const uint64_t total = *S.h_total;
     ctx->known_total = std::max<uint64_t>(ctx->known_total, total);
@@ -1234,8 +1254,6 @@ static rich_status run_complete(rich_ctx *ctx, const char *who, RunSlot &S, uint
     const uint64_t want = std::min<uint64_t>(c.hits, S.host_cap);
     if (want > S.early) {
         // the step's own output buffer (a later step in flight writes another)
-        if (!ctx->copy_stream)
-            RICH_CUDA(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
         RICH_CUDA(cudaMemcpyAsync(S.host_hits + S.early, S.dev_hits + S.early,
                                   (want - S.early) * sizeof(rich_hit), cudaMemcpyDeviceToHost,
                                   ctx->copy_stream));
