@@ -1,7 +1,8 @@
-"""Writes rich_log_tables.h: the tables of the yield kernel's FP64 and
-double-word logarithms and of log k! (exact to 40 digits with `decimal`,
-then rounded to FP64, or split into two FP32 numbers hi + lo). Run from
-this directory: python gen_log_tables.py"""
+"""Writes rich_log_tables.h: the tables of the kernels' FP64 logarithm
+(the dispersive radiator's yield integral), of the double-word logarithm
+and of log k! (exact to 40 digits with `decimal`, then rounded to FP64, or
+split into two FP32 numbers hi + lo). Run from this directory:
+python gen_log_tables.py"""
 import math
 import struct
 from decimal import Decimal, getcontext
@@ -77,17 +78,6 @@ for i in range(n):
 lines.append("};")
 lines.append("")
 lines.append(f"constexpr int kLogFactTable = {N_LOGFACT};")
-lines.append("// log k! for k < kLogFactTable")
-lines.append(f"__device__ const double g_logfact[{N_LOGFACT}] = {{")
-acc = Decimal(0)
-vals = []
-for k in range(N_LOGFACT):
-    if k > 1:
-        acc += Decimal(k).ln()
-    vals.append(d(float(acc)))
-for i in range(0, N_LOGFACT, 4):
-    lines.append("    " + ", ".join(vals[i:i + 4]) + ",")
-lines.append("};")
 lines.append("// log k! for k < kLogFactTable as a double-word (hi, lo)")
 lines.append(f"__device__ const float g_logfact_ff[{N_LOGFACT}][2] = {{")
 acc = Decimal(0)

@@ -41,35 +41,6 @@ __device__ __forceinline__ f3 normalize3(f3 a) {
     return a * inv;
 }
 
-struct d3 {
-    double x, y, z;
-};
-__device__ __forceinline__ d3 mkd(double x, double y, double z) { return {x, y, z}; }
-__device__ __forceinline__ d3 tod(f3 a) { return {(double)a.x, (double)a.y, (double)a.z}; }
-__device__ __forceinline__ d3 operator+(d3 a, d3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
-__device__ __forceinline__ d3 operator-(d3 a, d3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
-__device__ __forceinline__ d3 operator*(d3 a, double s) { return {a.x * s, a.y * s, a.z * s}; }
-__device__ __forceinline__ double dotd(d3 a, d3 b) {
-    return fma(a.x, b.x, fma(a.y, b.y, a.z * b.z));
-}
-__device__ __forceinline__ d3 crossd(d3 a, d3 b) {
-    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
-}
-// FP64 reciprocal and reciprocal square root by one Newton-Raphson step
-// from the FP32 hardware approximation (relative error ~2^-23 squared to
-// ~2^-46): x r = 1 and x r^2 = 1 refined as r + r (1 - x r) and
-// r + r (1 - x r^2) / 2. Arguments must lie in the FP32 normal range.
-__device__ __forceinline__ double rcp64(double x) {
-    const double r = (double)__frcp_rn((float)x);
-    return fma(r, fma(-x, r, 1.0), r);
-}
-__device__ __forceinline__ double rsqrt64(double x) {
-    const double r = (double)rsqrtf((float)x);
-    const double e = fma(-x * r, r, 1.0);
-    return fma(0.5 * r, e, r);
-}
-__device__ __forceinline__ d3 normalized(d3 a) { return a * rsqrt64(dotd(a, a)); }
-
 // --------------------------------------------------------------- Philox
 // Philox4x32-10: ten rounds of (hi(M1*c2) ^ c1 ^ k0, lo(M1*c2),
 // hi(M0*c0) ^ c3 ^ k1, lo(M0*c0)), the key advanced by the Weyl increments
@@ -133,21 +104,9 @@ __device__ __forceinline__ void basis_f(f3 t, f3 &e1, f3 &e2) {
     e1 = mk3(fmaf(s * t.x * t.x, a, 1.0f), s * b, -s * t.x);
     e2 = mk3(b, fmaf(t.y * t.y, a, s), -t.y);
 }
-__device__ __forceinline__ void basis_d(d3 t, d3 &e1, d3 &e2) {
-    double s = t.z >= 0.0 ? 1.0 : -1.0;
-    double a = -rcp64(s + t.z);
-    double b = t.x * t.y * a;
-    e1 = mkd(1.0 + s * t.x * t.x * a, s * b, -s * t.x);
-    e2 = mkd(b, s + t.y * t.y * a, -t.y);
-}
-
 __device__ __forceinline__ f3 reflect_f(f3 d, f3 n) {
     float k = -2.0f * dot3(d, n);
     return fma3(n, k, d);
-}
-__device__ __forceinline__ d3 reflect_d(d3 d, d3 n) {
-    double k = -2.0 * dotd(d, n);
-    return mkd(fma(n.x, k, d.x), fma(n.y, k, d.y), fma(n.z, k, d.z));
 }
 
 }  // namespace rich

@@ -62,13 +62,11 @@ def test_fp32_log_table_is_an_exact_split():
             assert abs(lo) <= _ulp32(hi) / 2
 
 
-def test_log_factorial_tables():
-    t64 = [v for r in _array(LOG, "g_logfact[") for v in r]
+def test_log_factorial_table():
     tff = _array(LOG, "g_logfact_ff[")
-    assert len(t64) == 2048 and len(tff) == 2048
+    assert len(tff) == 2048
     for k in list(range(0, 64)) + list(range(64, 2048, 37)) + [2047]:
         exact = mp.loggamma(k + 1)
-        assert abs(mp.mpf(t64[k]) - exact) <= mp.mpf(math.ulp(t64[k] or 1e-300)) / 2 + mp.mpf(2) ** -1074
         hi, lo = tff[k]
         assert abs(mp.mpf(hi) + mp.mpf(lo) - exact) <= mp.mpf(2) ** -47 * max(abs(exact), 1)
         if hi != 0.0:
