@@ -494,18 +494,22 @@ class Context:
     def run_host(self, tracks: HostTracks, outputs: TraceOutputs, hits_host, n_minus_1,
                  lambda_min=200.0, lambda_max=600.0, seed=0, precision=PREC_REFINE64,
                  max_bounces=8, max_steps=16, t_min=1e-3, block_threads=0, blocks_per_sm=0,
-                 refill_min=0, chunk=0, wide_regs=0, bvh_smem_nodes=-1, prefilter=()):
+                 refill_min=0, chunk=0, wide_regs=0, bvh_smem_nodes=-1, prefilter=(),
+                 source=SOURCE_CHERENKOV, yield_per_mm=0.0, spectrum_table=-1,
+                 dispersion=None):
         """One synchronous step from host memory (rich_run_host): host tracks
         in, the hit records copied into hits_host (a pinned uint8 tensor of
-        n x 40 bytes). Returns (n_hits, stats dict)."""
+        n x 40 bytes). Emission arguments as for emit. Returns (n_hits,
+        stats dict)."""
         # the call's argument objects are kept between steps (only the seed
-        # and the band change in place): a step is dominated by the GPU, and
-        # the host time before the first launch delays it
-        key = (float(n_minus_1), float(lambda_min), float(lambda_max))
+        # changes in place): a step is dominated by the GPU, and the host
+        # time before the first launch delays it
+        key = (float(n_minus_1), float(lambda_min), float(lambda_max), source,
+               float(yield_per_mm), spectrum_table, dispersion)
         rh = getattr(self, "_rh", None)
         if rh is None or rh[0] != key:
-            prm = _emit_params(seed, n_minus_1, lambda_min, lambda_max, SOURCE_CHERENKOV, 0.0,
-                               -1, None)
+            prm = _emit_params(seed, n_minus_1, lambda_min, lambda_max, source, yield_per_mm,
+                               spectrum_table, dispersion)
             rh = self._rh = (key, prm, C.c_uint64(0), Stats())
         _, prm, n, s = rh
         prm.seed = int(seed)
@@ -523,12 +527,14 @@ class Context:
                        lambda_min=200.0, lambda_max=600.0, seed=0, precision=PREC_REFINE64,
                        max_bounces=8, max_steps=16, t_min=1e-3, block_threads=0,
                        blocks_per_sm=0, refill_min=0, chunk=0, wide_regs=0,
-                       bvh_smem_nodes=-1, prefilter=()):
+                       bvh_smem_nodes=-1, prefilter=(), source=SOURCE_CHERENKOV,
+                       yield_per_mm=0.0, spectrum_table=-1, dispersion=None):
         """Pipelined step (rich_run_host_async): returns a ticket for
         run_wait. Two steps may be in flight, each with its own outputs and
-        hits_host; the HostTracks must not change until waited for."""
-        prm = _emit_params(seed, n_minus_1, lambda_min, lambda_max, SOURCE_CHERENKOV, 0.0,
-                           -1, None)
+        hits_host; the HostTracks must not change until waited for.
+        Emission arguments as for emit."""
+        prm = _emit_params(seed, n_minus_1, lambda_min, lambda_max, source, yield_per_mm,
+                           spectrum_table, dispersion)
         o = _trace_opts(0, precision, max_bounces, max_steps, t_min, block_threads,
                         blocks_per_sm, refill_min, chunk, wide_regs, bvh_smem_nodes, prefilter)
         t = C.c_uint64(0)

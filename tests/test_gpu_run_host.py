@@ -169,3 +169,27 @@ def test_run_host_async_pipeline_matches_sync(setup):
     with pytest.raises(rich.RichError) as e:
         ctx.run_wait(t2)
     assert e.value.status == 7
+
+
+def test_run_host_isotropic_source_matches_device_path():
+    """rich_run_host with the emission arguments of another light source
+    (isotropic scintillation with a binned spectrum) gives the device-buffer
+    path's photons, counters and hit records."""
+    import parity as P
+    wl = W.scintillation(60)
+    ref = P.run_gpu(wl, want_fate=False, hist=False)
+    ctx = rich.Context(0)
+    ctx.init_geometry(wl.scene)
+    ht = rich.HostTracks(wl.tracks)
+    cap = ref["n"] + 1024
+    out = rich.TraceOutputs(cap, wl.scene.pixels_per_event, len(wl.scene.planes), 0, 0)
+    hits_host = torch.empty(cap * rich.HIT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    nh, st = ctx.run_host(ht, out, hits_host, wl.n_minus_1, wl.lambda_min, wl.lambda_max,
+                          seed=wl.seed, source=wl.source, yield_per_mm=wl.yield_per_mm,
+                          spectrum_table=wl.spectrum_table)
+    ctx.close()
+    assert st["n_photons"] == ref["n"] and nh == ref["n_hits"]
+    assert st["fate"] == ref["stats"]["fate"]
+    got = np.frombuffer(hits_host.numpy()[: nh * rich.HIT_DTYPE.itemsize].tobytes(),
+                        rich.HIT_DTYPE)
+    np.testing.assert_array_equal(_sorted(got), _sorted(ref["hits"]))
