@@ -193,3 +193,46 @@ def test_run_host_isotropic_source_matches_device_path():
     got = np.frombuffer(hits_host.numpy()[: nh * rich.HIT_DTYPE.itemsize].tobytes(),
                         rich.HIT_DTYPE)
     np.testing.assert_array_equal(_sorted(got), _sorted(ref["hits"]))
+
+
+def test_run_host_follow_up_copy_when_the_early_copy_falls_short():
+    """The early hit copy is sized from the previous step's count; a step
+    with many more hits than that has its remaining records copied at
+    completion (synchronous and pipelined). The records equal the
+    device-buffer path's."""
+    scene = W.rich1_scene(meshed=True)
+    small, large = W.pion_tracks(20, seed=5), W.pion_tracks(400, seed=6)
+    ctx = rich.Context(0)
+    ctx.init_geometry(scene)
+    dt = rich.DeviceTracks(large)
+    n = ctx.emit(dt, 0.0014, seed=4)
+    cap = n // 2 + 1024
+    ref_out = rich.TraceOutputs(cap, scene.pixels_per_event, len(scene.planes), 1, 0)
+    ctx.trace(ref_out, precision=rich.PREC_REFINE64)
+    nh_ref, _ = ctx.hits()
+    ref = _sorted(ref_out.hits_numpy(nh_ref))
+    hs, hl = rich.HostTracks(small), rich.HostTracks(large)
+    outs = [rich.TraceOutputs(cap, scene.pixels_per_event, len(scene.planes), 1, 0)
+            for _ in range(2)]
+    hosts = [torch.empty(cap * rich.HIT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+             for _ in range(2)]
+
+    def records(h, k):
+        return _sorted(np.frombuffer(h.numpy()[: k * rich.HIT_DTYPE.itemsize].tobytes(),
+                                     rich.HIT_DTYPE))
+
+    # synchronous: small step, then the large one
+    nh_s, _ = ctx.run_host(hs, outs[0], hosts[0], 0.0014, seed=4)
+    assert 0 < nh_s and 4 * nh_s < nh_ref
+    nh, _ = ctx.run_host(hl, outs[1], hosts[1], 0.0014, seed=4)
+    assert nh == nh_ref
+    np.testing.assert_array_equal(records(hosts[1], nh), ref)
+    # pipelined: small step completed, then small + large in flight
+    ctx.run_host(hs, outs[0], hosts[0], 0.0014, seed=4)
+    t0 = ctx.run_host_async(hs, outs[0], hosts[0], 0.0014, seed=4)
+    t1 = ctx.run_host_async(hl, outs[1], hosts[1], 0.0014, seed=4)
+    assert ctx.run_wait(t0)[0] == nh_s
+    nh, _ = ctx.run_wait(t1)
+    assert nh == nh_ref
+    np.testing.assert_array_equal(records(hosts[1], nh), ref)
+    ctx.close()
