@@ -486,6 +486,9 @@ RICH_API rich_status rich_destroy(rich_ctx *ctx) {
     {
         DeviceGuard g(ctx->device);
         cudaStreamSynchronize(ctx->stream);
+        // steps never waited for: their copies finish before their buffers go
+        if (ctx->up_stream) cudaStreamSynchronize(ctx->up_stream);
+        if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
         cudaFree(ctx->d_geom);
         cudaFree(ctx->d_refine);
         cudaFree(ctx->d_grad_tiles);
