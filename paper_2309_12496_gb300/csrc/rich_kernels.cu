@@ -32,6 +32,7 @@ constexpr int kYieldThreads = 256;   // tracks per scan group / scan block
 constexpr int kYieldBlock = 32;      // threads per yield block: one warp, so
                                      // the per-track chains of a small batch
                                      // spread over as many SMs as possible
+constexpr int kYieldLanes = 4;       // lanes per track (parallel Poisson trials)
 constexpr double kAlpha = 1.0 / 137.035999;
 constexpr double kPi = 3.14159265358979323846;
 constexpr ff k2PiAlpha = ffc(2.0 * kPi * kAlpha);
@@ -260,6 +261,58 @@ __device__ int64_t poisson_draw(ff mu, TrackStream &s) {
     return ff_floor_i64(ff_add(mu, 0.5f));
 }
 
+// The same sampler with the PTRS trials spread over a group of kYieldLanes
+// lanes (one track): in round r, lane `sub` takes trial r kYieldLanes + sub,
+// whose uniforms are words 2t and 2t + 1 of the track's stream (block t / 2,
+// words x, y for even t and z, w for odd t), and the earliest accepting
+// trial of the first round with one wins: the sequential sampler's result,
+// with the same uniforms and tests. The group's lanes run the setup and the
+// inversion below mean 10 redundantly. grp: the group's lanes in the warp.
+__device__ int64_t poisson_draw_group(ff mu, const TrackStream &s0, int sub, unsigned grp) {
+    if (!(mu.hi > 0.0f)) return 0;
+    if (ff_lt(mu, ffv(10.0f))) {
+        TrackStream s = s0;
+        return poisson_draw(mu, s);
+    }
+    constexpr ff kB0 = ffc(0.931), kB1 = ffc(2.53), kA0 = ffc(-0.059), kA1 = ffc(0.02483),
+                 kI0 = ffc(1.1239), kI1 = ffc(1.1328), kI2 = ffc(3.4), kV0 = ffc(0.9277),
+                 kV1 = ffc(3.6224), kK = ffc(0.43), kUs0 = ffc(0.07), kUs1 = ffc(0.013);
+    const ff smu = ff_sqrt(mu), lmu = ff_log(mu);
+    const ff b = ff_add(kB0, ff_mul(kB1, smu));
+    const ff a = ff_add(kA0, ff_mul(kA1, b));
+    const ff inv_alpha = ff_add(kI0, ff_div(kI1, ff_sub(b, kI2)));
+    const ff v_r = ff_sub(kV0, ff_div(kV1, ff_add(b, -2.0f)));
+    const ff two_a = {2.0f * a.hi, 2.0f * a.lo};
+    const ff mu_k = ff_add(mu, kK);
+    for (int round = 0; round < 64 / kYieldLanes; ++round) {
+        const int trial = round * kYieldLanes + sub;
+        const u4 w = philox10((uint32_t)(trial >> 1), 0xFFFFFFFFu, s0.id, s0.event, s0.k0, s0.k1);
+        const float U = u24f((trial & 1) ? w.z : w.x) - 0.5f;
+        const float V = u24f((trial & 1) ? w.w : w.y);
+        const float us = 0.5f - fabsf(U);
+        bool accept = false;
+        int64_t k = -1;
+        if (us > 0.0f) {
+            k = ff_floor_i64(ff_add(ff_mul(ff_add(ff_div(two_a, ffv(us)), b), U), mu_k));
+            if (k >= 0) {
+                if (!ff_lt(ffv(us), kUs0) && ff_le(ffv(V), v_r)) {
+                    accept = true;
+                } else if (!(ff_lt(ffv(us), kUs1) && V > us)) {
+                    const ff us2 = two_prod(us, us);
+                    const ff lhs = ff_log(
+                        ff_div(ff_mul(ff_mul(inv_alpha, V), us2), ff_add(ff_mul(b, us2), a)));
+                    const ff rhs =
+                        ff_sub(ff_sub(ff_mul(lmu, ff_from_i64(k)), mu), ff_log_factorial(k));
+                    accept = ff_le(lhs, rhs);
+                }
+            }
+        }
+        const unsigned acc = __ballot_sync(grp, accept) & grp;
+        if (acc) return __shfl_sync(grp, (long long)k, __ffs(acc) - 1);
+    }
+    return ff_floor_i64(ff_add(mu, 0.5f));
+}
+
 // ------------------------------------------------- dispersive radiator
 // sin^2 theta of the single-resonance radiator at lambda in FP32, one IEEE
 // operation at a time (it decides the wavelength accept/reject):
@@ -312,7 +365,11 @@ k_yield(TracksView t, ff nm1, ff inv_band, uint32_t key0,
         uint32_t key1, TrackRec *rec, float4 *cs, uint32_t *counts,
         unsigned long long *block_sums, YieldModel model, double lam_min, double lam_max) {
     grid_dep_launch_dependents();        // the ordering pass may be scheduled
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // kYieldLanes consecutive lanes per track; lane 0 of each group writes
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = gt / kYieldLanes;
+    const int sub = (int)(gt % kYieldLanes);
+    const unsigned grp = ((1u << kYieldLanes) - 1u) << ((threadIdx.x & 31) & ~(kYieldLanes - 1));
     uint32_t count = 0;
     if (i < t.n) {
         // every input of the track in one round of loads
@@ -364,11 +421,11 @@ k_yield(TracksView t, ff nm1, ff inv_band, uint32_t key0,
         if (t.n_fixed) {
             count = n_fixed;
         } else {
-            TrackStream s{event, id, key0, key1, 0u, 4u, {0u, 0u, 0u, 0u}};
-            int64_t k = poisson_draw(mu, s);
+            const TrackStream s{event, id, key0, key1, 0u, 4u, {0u, 0u, 0u, 0u}};
+            const int64_t k = poisson_draw_group(mu, s, sub, grp);
             count = (uint32_t)(k > 0xFFFFFFF0ll ? 0xFFFFFFF0ll : k);
         }
-        if (RECS) {
+        if (RECS && sub == 0) {
         // the unit direction, rounded to FP32 from its double-word
         const ff3 tn = ff3_normalized(ff3v(fdx, fdy, fdz));
         TrackRec r;
@@ -391,8 +448,9 @@ k_yield(TracksView t, ff nm1, ff inv_band, uint32_t key0,
         rec[i] = r;
         cs[i] = cs_out;
         }
-        counts[i] = count;
+        if (sub == 0) counts[i] = count;
     }
+    if (sub != 0) count = 0;            // one contribution per track to the sums
     // sum of the counts of this block, added to its 256-track scan group
     // (integer atomics: exact and order independent)
     unsigned long long v = count;
@@ -404,7 +462,7 @@ k_yield(TracksView t, ff nm1, ff inv_band, uint32_t key0,
     if (threadIdx.x == 0) {
         unsigned long long s = 0;
         for (int w = 0; w < kYieldBlock / 32; ++w) s += warp_sum[w];
-        const int64_t first = (int64_t)blockIdx.x * kYieldBlock;
+        const int64_t first = (int64_t)blockIdx.x * (kYieldBlock / kYieldLanes);  // first track
         if (s) atomicAdd(&block_sums[first / kYieldThreads], s);
     }
 }
@@ -2259,7 +2317,8 @@ cudaError_t launch_yield(const TracksView &t, double n_minus_1,
     const int64_t groups = (t.n + kYieldThreads - 1) / kYieldThreads;
     cudaError_t e = cudaMemsetAsync(block_sums, 0, sizeof(unsigned long long) * groups, s);
     if (e != cudaSuccess) return e;
-    const unsigned blocks = (unsigned)((t.n + kYieldBlock - 1) / kYieldBlock);
+    const unsigned blocks =
+        (unsigned)((t.n * kYieldLanes + kYieldBlock - 1) / kYieldBlock);
     if (rec)
         k_yield<true><<<blocks, kYieldBlock, 0, s>>>(t, nm1, inv_band, key0, key1,
                                                      rec, cs, counts, block_sums, model,
