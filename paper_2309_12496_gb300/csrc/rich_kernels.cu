@@ -514,9 +514,10 @@ k_offsets(const uint32_t *counts, const unsigned long long *block_sums,
 // points of the mirror and, being nearly parallel there, are focused to
 // nearby points after it, so a warp that takes consecutive entries traces
 // coherent rays at every bounce. Processing order only: every photon keeps
-// its own draws and results. One warp per track (grid-stride), counting
-// sort in shared memory (the bins of the first kOrderBinCache photons kept
-// from the counting pass), order within a bin arbitrary.
+// its own draws and results. One block of kOrderWarps warps per track
+// (grid-stride), counting sort in shared memory (the bins of the first
+// kOrderBinCache photons kept from the counting pass), order within a bin
+// arbitrary.
 constexpr int kAzBins = 32;
 constexpr int kOrderWarps = 4;
 constexpr uint32_t kOrderBinCache = 2048;
@@ -572,70 +573,67 @@ __global__ void __launch_bounds__(32 * kOrderWarps) k_order(EmitView em, uint32_
         }
     }
     if (!SCAN && !fits) return;
-    __shared__ uint32_t hist_all[kOrderWarps][kAzBins];
-    __shared__ uint8_t bins_all[kOrderWarps][kOrderBinCache];
-    uint32_t *hist = hist_all[w];
-    uint8_t *bins = bins_all[w];
-    const int64_t warps = (int64_t)gridDim.x * kOrderWarps;
-    for (int64_t t = (int64_t)blockIdx.x * kOrderWarps + w; t < em.n_tracks; t += warps) {
+    // one block per track (grid-stride): the block's warps share the bin
+    // histogram, so each lane draws and places only a few photons
+    __shared__ uint32_t hist[kAzBins];
+    __shared__ uint8_t bins[kOrderBinCache];
+    __shared__ unsigned long long s_part[kOrderWarps];
+    const int nthreads = (int)blockDim.x;
+    for (int64_t t = blockIdx.x; t < em.n_tracks; t += gridDim.x) {   // block-uniform
         uint64_t off, n64;
         if (SCAN) {
             const int64_t g = t / kYieldThreads;
             unsigned long long part = 0;
-            for (int64_t i = g * kYieldThreads + lane; i < t; i += 32) part += scan.counts[i];
+            for (int64_t i = g * kYieldThreads + threadIdx.x; i < t; i += nthreads)
+                part += scan.counts[i];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
-            off = s_gpre[g] + part;
+            if (lane == 0) s_part[w] = part;
+            __syncthreads();
+            off = s_gpre[g];
+            for (int k = 0; k < kOrderWarps; ++k) off += s_part[k];
             n64 = scan.counts[t];
-            if (lane == 0) scan.offsets[t] = off;
-            if (!fits) continue;
+            if (threadIdx.x == 0) scan.offsets[t] = off;
         } else {
             off = em.offsets[t];
             n64 = em.offsets[t + 1] - off;
         }
-        if (n64 == 0 || n64 > kOrderMaxPhotons) continue;   // uniform in the warp
-        const uint32_t n = (uint32_t)n64;
-        const uint32_t id = em.tracks[t].id, ev = em.tracks[t].event;
-        hist[lane] = 0u;
-        __syncwarp();
-        // four independent draws per lane in flight
-        for (uint32_t j0 = lane; j0 < n; j0 += 128) {
-            uint32_t bn[4];
+        if (fits && n64 != 0 && n64 <= kOrderMaxPhotons) {   // uniform in the block
+            const uint32_t n = (uint32_t)n64;
+            const uint32_t id = em.tracks[t].id, ev = em.tracks[t].event;
+            if (threadIdx.x < kAzBins) hist[threadIdx.x] = 0u;
+            __syncthreads();
+            for (uint32_t j = threadIdx.x; j < n; j += (uint32_t)nthreads) {
+                const uint32_t bin = philox10(0u, j, id, ev, em.key0, em.key1).y >> 27;
+                if (j < kOrderBinCache) bins[j] = (uint8_t)bin;
+                atomicAdd(&hist[bin], 1u);
+            }
+            __syncthreads();
+            if (w == 0) {
+                const uint32_t c = hist[lane];
+                uint32_t inc = c;
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                bn[u] = philox10(0u, j0 + 32u * u, id, ev, em.key0, em.key1).y >> 27;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const uint32_t j = j0 + 32u * u;
-                if (j < n) {
-                    if (j < kOrderBinCache) bins[j] = (uint8_t)bn[u];
-                    atomicAdd(&hist[bn[u]], 1u);
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(kFull, inc, o);
+                    if (lane >= o) inc += y;
                 }
+                hist[lane] = inc - c;                           // bin cursors
+            }
+            __syncthreads();
+            for (uint32_t j = threadIdx.x; j < n; j += (uint32_t)nthreads) {
+                const uint32_t bin = j < kOrderBinCache
+                                         ? (uint32_t)bins[j]
+                                         : philox10(0u, j, id, ev, em.key0, em.key1).y >> 27;
+                perm[off + atomicAdd(&hist[bin], 1u)] = j;
             }
         }
-        __syncwarp();
-        const uint32_t c = hist[lane];
-        uint32_t inc = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(kFull, inc, o);
-            if (lane >= o) inc += y;
-        }
-        hist[lane] = inc - c;                                   // bin cursors
-        __syncwarp();
-        for (uint32_t j = lane; j < n; j += 32) {
-            const uint32_t bin = j < kOrderBinCache
-                                     ? (uint32_t)bins[j]
-                                     : philox10(0u, j, id, ev, em.key0, em.key1).y >> 27;
-            perm[off + atomicAdd(&hist[bin], 1u)] = j;
-        }
-        __syncwarp();
+        __syncthreads();                 // the shared histogram and bins are reused
     }
 }
 
 cudaError_t launch_order(const EmitView &em, uint32_t *perm, uint64_t cap, uint32_t *perm_ok,
                          int n_sm, cudaStream_t s, const OrderScan *scan) {
-    int64_t blocks = (em.n_tracks + kOrderWarps - 1) / kOrderWarps;
+    int64_t blocks = em.n_tracks;                       // one block per track
     if (blocks < 1) blocks = 1;
     const int64_t max_blocks = (int64_t)n_sm * 16;
     if (blocks > max_blocks) blocks = max_blocks;
