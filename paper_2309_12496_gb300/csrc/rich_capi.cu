@@ -55,6 +55,7 @@ struct rich_ctx {
     int64_t track_cap = 0;
     TrackRec *d_rec = nullptr;
     float4 *d_cs = nullptr;
+    TrackFrame *d_frame = nullptr;
     uint32_t *d_counts = nullptr;
     uint64_t *d_offsets = nullptr;
     unsigned long long *d_bsum = nullptr;
@@ -324,11 +325,13 @@ void free_emission(rich_ctx *ctx) {
     drop_graph(ctx);
     cudaFree(ctx->d_rec);
     cudaFree(ctx->d_cs);
+    cudaFree(ctx->d_frame);
     cudaFree(ctx->d_counts);
     cudaFree(ctx->d_offsets);
     cudaFree(ctx->d_bsum);
     ctx->d_rec = nullptr;
     ctx->d_cs = nullptr;
+    ctx->d_frame = nullptr;
     ctx->d_counts = nullptr;
     ctx->d_offsets = nullptr;
     ctx->d_bsum = nullptr;
@@ -339,7 +342,8 @@ void free_emission(rich_ctx *ctx) {
 EmitView emit_view(const rich_ctx *ctx) {
     EmitView em{ctx->d_rec, ctx->d_cs, ctx->d_offsets, ctx->d_total, ctx->n_tracks,
                 ctx->key0, ctx->key1, ctx->inv1, ctx->span, ctx->d_perm, ctx->d_perm_ok,
-                ctx->source, ctx->spectrum, ctx->dispersion, ctx->disp_a, ctx->disp_lambda0};
+                ctx->source, ctx->spectrum, ctx->dispersion, ctx->disp_a, ctx->disp_lambda0,
+                ctx->d_frame};
     return em;
 }
 
@@ -357,6 +361,7 @@ rich_status emit_core(rich_ctx *ctx, const rich_tracks *t, uint64_t seed, float 
         const int64_t blocks = (cap + yield_block_threads() - 1) / yield_block_threads();
         RICH_CUDA(cudaMalloc(&ctx->d_rec, sizeof(TrackRec) * cap));
         RICH_CUDA(cudaMalloc(&ctx->d_cs, sizeof(float4) * cap));
+        RICH_CUDA(cudaMalloc(&ctx->d_frame, sizeof(TrackFrame) * cap));
         RICH_CUDA(cudaMalloc(&ctx->d_counts, sizeof(uint32_t) * cap));
         RICH_CUDA(cudaMalloc(&ctx->d_offsets, sizeof(uint64_t) * (cap + 1)));
         RICH_CUDA(cudaMalloc(&ctx->d_bsum, sizeof(unsigned long long) * (blocks + 1)));
@@ -384,7 +389,8 @@ rich_status emit_core(rich_ctx *ctx, const rich_tracks *t, uint64_t seed, float 
                                ctx->stream,
                                YieldModel{source == RICH_SOURCE_ISOTROPIC ? (double)yield_per_mm
                                                                           : -1.0,
-                                          dispersion, disp_a, disp_lambda0}));
+                                          dispersion, disp_a, disp_lambda0},
+                               ctx->d_frame));
         // deferred: the ordering pass (order_photons, which the caller
         // runs next) does the scan
         ctx->scan_pending = defer_scan && n <= kOrderScanMaxTracks;

@@ -137,6 +137,14 @@ struct TracksView {          // device SoA of rich_tracks
     const uint32_t *event, *id, *n_fixed;
 };
 
+// Per track, the double-word frame of the refinement's emission: the unit
+// direction t and the orthonormal basis (e1, e2) around it, as (hi, lo)
+// pairs per component (written by the yield pass).
+struct alignas(16) TrackFrame {  // 80 B
+    float t[6], e1[6], e2[6];
+    float pad[2];
+};
+
 struct EmitView {            // result of rich_emit used by the trace
     const TrackRec *tracks;
     const float4 *cos_sin;    // (cos hi, cos lo, sin hi, sin lo) of the Cherenkov
@@ -153,6 +161,7 @@ struct EmitView {            // result of rich_emit used by the trace
     int32_t spectrum;         // isotropic: CDF table index of the scene, or -1
     int32_t dispersion;       // 1: dispersive radiator
     float disp_a, disp_lambda0;
+    const TrackFrame *frame;  // per track
 };
 
 struct ExtView {             // caller photons
@@ -233,7 +242,8 @@ cudaError_t launch_yield(const TracksView &t, double n_minus_1,
                          double lam_min, double lam_max, uint32_t key0,
                          uint32_t key1, TrackRec *rec, float4 *cs,
                          uint32_t *counts, unsigned long long *block_sums,
-                         cudaStream_t s, const YieldModel &model);
+                         cudaStream_t s, const YieldModel &model,
+                         TrackFrame *frame = nullptr);
 cudaError_t launch_offsets(const uint32_t *counts,
                            const unsigned long long *block_sums,
                            int64_t n_tracks, uint64_t *offsets,

@@ -359,11 +359,14 @@ __device__ double disp_yield_per_mm(const YieldModel &m, double beta, double omb
     return 2.0 * kPi * kAlpha * I * 1.0e6;
 }
 
+__device__ __forceinline__ void basis_ff(const ff3 &t, ff3 &e1, ff3 &e2);
+
 template <bool RECS>
 __global__ void __launch_bounds__(kYieldBlock)
 k_yield(TracksView t, ff nm1, ff inv_band, uint32_t key0,
         uint32_t key1, TrackRec *rec, float4 *cs, uint32_t *counts,
-        unsigned long long *block_sums, YieldModel model, double lam_min, double lam_max) {
+        unsigned long long *block_sums, YieldModel model, double lam_min, double lam_max,
+        TrackFrame *frame) {
     grid_dep_launch_dependents();        // the ordering pass may be scheduled
     // kYieldLanes consecutive lanes per track; lane 0 of each group writes
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -426,8 +429,15 @@ k_yield(TracksView t, ff nm1, ff inv_band, uint32_t key0,
             count = (uint32_t)(k > 0xFFFFFFF0ll ? 0xFFFFFFF0ll : k);
         }
         if (RECS && sub == 0) {
-        // the unit direction, rounded to FP32 from its double-word
+        // the unit direction, rounded to FP32 from its double-word, and the
+        // double-word frame of the refinement's emission
         const ff3 tn = ff3_normalized(ff3v(fdx, fdy, fdz));
+        ff3 e1, e2;
+        basis_ff(tn, e1, e2);
+        frame[i] = TrackFrame{{tn.x.hi, tn.x.lo, tn.y.hi, tn.y.lo, tn.z.hi, tn.z.lo},
+                              {e1.x.hi, e1.x.lo, e1.y.hi, e1.y.lo, e1.z.hi, e1.z.lo},
+                              {e2.x.hi, e2.x.lo, e2.y.hi, e2.y.lo, e2.z.hi, e2.z.lo},
+                              {0.0f, 0.0f}};
         TrackRec r;
         r.x = tx;
         r.y = ty;
@@ -1298,21 +1308,26 @@ __device__ __forceinline__ void ff_sincos_2pi(uint32_t w, ff &s, ff &c) {
     c = ff_sub(ff_mul(ca, cd), ff_mul(sa, sd));
 }
 
-// Origin, unit track direction and (sin, cos) of the azimuth of photon j.
-__device__ __forceinline__ void emit_start_ff(const TrackRec &tr, uint32_t j,
-                                              const EmitView &em, ff3 &o, ff3 &t, ff &sp,
-                                              ff &cp) {
+__device__ __forceinline__ ff3 frame_vec(const float *v) {
+    return {ff{v[0], v[1]}, ff{v[2], v[3]}, ff{v[4], v[5]}};
+}
+
+// Origin, unit track direction (from the track's frame) and (sin, cos) of
+// the azimuth of photon j.
+__device__ __forceinline__ void emit_start_ff(const TrackRec &tr, const TrackFrame &fr,
+                                              uint32_t j, const EmitView &em, ff3 &o, ff3 &t,
+                                              ff &sp, ff &cp) {
     const u4 w0 = philox10(0u, j, tr.id, tr.event, em.key0, em.key1);
-    t = ff3_normalized(ff3v(tr.rx, tr.ry, tr.rz));
+    t = frame_vec(fr.t);
     const ff s = two_prod(u24f(w0.x), tr.len);      // exact: 24 x 24 bits
     o = ff3_axpy(s, t, ff3v(tr.x, tr.y, tr.z));
     ff_sincos_2pi(w0.y, sp, cp);
 }
 
-// Unit direction of the azimuth (cos, sin) in the plane normal to t.
-__device__ __forceinline__ ff3 azimuth_dir_ff(const ff3 &t, ff sp, ff cp) {
-    ff3 e1, e2;
-    basis_ff(t, e1, e2);
+// Unit direction of the azimuth (cos, sin) in the plane normal to t, from
+// the track's basis.
+__device__ __forceinline__ ff3 azimuth_dir_ff(const TrackFrame &fr, ff sp, ff cp) {
+    const ff3 e1 = frame_vec(fr.e1), e2 = frame_vec(fr.e2);
     return {ff_add(ff_mul(e1.x, cp), ff_mul(e2.x, sp)), ff_add(ff_mul(e1.y, cp), ff_mul(e2.y, sp)),
             ff_add(ff_mul(e1.z, cp), ff_mul(e2.z, sp))};
 }
@@ -1323,11 +1338,11 @@ __device__ __forceinline__ ff3 azimuth_dir_ff(const ff3 &t, ff sp, ff cp) {
 // from the yield pass (double-words). Isotropic source: cos(theta) =
 // 1 - 2u (exact) and sin(theta) = 2 sqrt(u (1 - u)) from the exact product
 // u (1 - u).
-__device__ void emit_ff(const TrackRec &tr, float4 cs, uint32_t j, float lam,
-                        const EmitView &em, ff3 &o, ff3 &d) {
+__device__ void emit_ff(const TrackRec &tr, const TrackFrame &fr, float4 cs, uint32_t j,
+                        float lam, const EmitView &em, ff3 &o, ff3 &d) {
     ff3 t;
     ff sp, cp;
-    emit_start_ff(tr, j, em, o, t, sp, cp);
+    emit_start_ff(tr, fr, j, em, o, t, sp, cp);
     if (em.source == RICH_SOURCE_ISOTROPIC) {
         const u4 w3 = philox10(3u, j, tr.id, tr.event, em.key0, em.key1);
         const float u = u24f(w3.z);
@@ -1335,7 +1350,7 @@ __device__ void emit_ff(const TrackRec &tr, float4 cs, uint32_t j, float lam,
         d = {ff_mul(st, cp), ff_mul(st, sp), ffv(1.0f - 2.0f * u)};
         return;
     }
-    const ff3 r = azimuth_dir_ff(t, sp, cp);
+    const ff3 r = azimuth_dir_ff(fr, sp, cp);
     ff ct = {cs.x, cs.y}, st = {cs.z, cs.w};
     if (em.dispersion) {
         // dispersive radiator: the angle of the photon's own wavelength, FP64,
@@ -1925,7 +1940,8 @@ k_refine(SceneView sc, EmitView em, ExtView ext, TraceParams P, Counters *ctr) {
                 o = ff3v(ext.x[g], ext.y[g], ext.z[g]);
                 d = ff3_normalized(ff3v(ext.dx[g], ext.dy[g], ext.dz[g]));
             } else {
-                emit_ff(em.tracks[rr.index], em.cos_sin[rr.index], h.photon, h.lambda, em, o, d);
+                emit_ff(em.tracks[rr.index], em.frame[rr.index], em.cos_sin[rr.index], h.photon,
+                        h.lambda, em, o, d);
             }
             replay_ff(sc, o, d, rr, h.lambda, uf, vf);
             int ix, iy;
@@ -2117,10 +2133,11 @@ __device__ void replay_dual(const SceneView &sc, const GradView &gv, const EmitV
     // emission as in the refinement replay; the tangent of the Cherenkov
     // angle in n - 1: cos = 1 / (n beta) gives d cos / dn = -cos / n and
     // d sin / dn = -cos (d cos / dn) / sin
+    const TrackFrame fr = em.frame[rr.index];
     ff3 o0, t;
     ff sp, cp;
-    emit_start_ff(tr, j, em, o0, t, sp, cp);
-    const ff3 r = azimuth_dir_ff(t, sp, cp);
+    emit_start_ff(tr, fr, j, em, o0, t, sp, cp);
+    const ff3 r = azimuth_dir_ff(fr, sp, cp);
     const ff ct = {cs.x, cs.y}, st = {cs.z, cs.w};
     const ff3 d0 = ff3_normalized({ff_add(ff_mul(t.x, ct), ff_mul(r.x, st)),
                                    ff_add(ff_mul(t.y, ct), ff_mul(r.y, st)),
@@ -2307,7 +2324,7 @@ cudaError_t launch_yield(const TracksView &t, double n_minus_1,
                          double lam_min, double lam_max, uint32_t key0,
                          uint32_t key1, TrackRec *rec, float4 *cs,
                          uint32_t *counts, unsigned long long *block_sums,
-                         cudaStream_t s, const YieldModel &model) {
+                         cudaStream_t s, const YieldModel &model, TrackFrame *frame) {
     if (t.n <= 0) return cudaSuccess;
     const double inv_band_mm = 1.0e6 / lam_min - 1.0e6 / lam_max;
     // the kernel's double-word parameters, split here
@@ -2320,11 +2337,11 @@ cudaError_t launch_yield(const TracksView &t, double n_minus_1,
     if (rec)
         k_yield<true><<<blocks, kYieldBlock, 0, s>>>(t, nm1, inv_band, key0, key1,
                                                      rec, cs, counts, block_sums, model,
-                                                     lam_min, lam_max);
+                                                     lam_min, lam_max, frame);
     else
         k_yield<false><<<blocks, kYieldBlock, 0, s>>>(t, nm1, inv_band, key0, key1,
                                                       rec, cs, counts, block_sums, model,
-                                                      lam_min, lam_max);
+                                                      lam_min, lam_max, nullptr);
     return cudaGetLastError();
 }
 
