@@ -77,8 +77,16 @@ struct rich_ctx {
     std::vector<int32_t> table_kind;          // kinds of the scene's tables (host)
     bool has_dielectric = false;              // the scene refracts (window faces)
     // small device state: counters + photon total
-    Counters *d_ctr = nullptr;
-    unsigned long long *d_total = nullptr;
+    Counters *d_ctr = nullptr;              // the last trace's counter slot
+    unsigned long long *d_total = nullptr; // the last emission's photon total
+    // two counter slots, each [Counters | the trace's photon total]: a trace
+    // counts into one and zeroes the other for the next trace, so the next
+    // trace needs no reset before its launch
+    Counters *d_ctr_slot[2] = {nullptr, nullptr};   // slot 0 is the allocation
+    int cur_slot = 0;
+    bool slot_zeroed[2] = {true, true};
+    bool capturing = false;                // inside rich_graph_capture
+    int graph_slot = 0;
     Counters *h_ctr = nullptr;            // pinned
     unsigned long long *h_total = nullptr; // pinned
     // last trace
@@ -465,11 +473,12 @@ RICH_API rich_status rich_create(rich_ctx **out, int device, void *stream) {
     DeviceGuard g(device);
     cudaDeviceProp prop;
     if ((e = cudaGetDeviceProperties(&prop, device)) != cudaSuccess ||
-        (e = cudaMalloc(&ctx->d_ctr, kCtrBytes)) != cudaSuccess ||
+        (e = cudaMalloc(&ctx->d_ctr, 2 * kCtrBytes + sizeof(unsigned long long))) != cudaSuccess ||
         (e = cudaMalloc(&ctx->d_perm_ok, sizeof(uint32_t))) != cudaSuccess ||
         (e = cudaMemset(ctx->d_perm_ok, 0, sizeof(uint32_t))) != cudaSuccess ||
         (e = cudaMallocHost(&ctx->h_ctr, kCtrBytes)) != cudaSuccess ||
-        (e = cudaMemset(ctx->d_ctr, 0, kCtrBytes)) != cudaSuccess) {
+        (e = cudaMemset(ctx->d_ctr, 0, 2 * kCtrBytes + sizeof(unsigned long long))) !=
+            cudaSuccess) {
         g_create_error = std::string("rich_create: ") + cudaGetErrorString(e);
         cudaGetLastError();
         cudaFree(ctx->d_ctr);
@@ -478,8 +487,14 @@ RICH_API rich_status rich_create(rich_ctx **out, int device, void *stream) {
         delete ctx;
         return e == cudaErrorMemoryAllocation ? RICH_ERR_OOM : RICH_ERR_CUDA;
     }
-    // the photon total sits right after the counters (one copy reads both)
-    ctx->d_total = reinterpret_cast<unsigned long long *>(ctx->d_ctr + 1);
+    // slot k at d_ctr + k kCtrBytes holds the counters and the trace's photon
+    // total (one copy reads both); the emission's total follows the slots
+    {
+        char *base = reinterpret_cast<char *>(ctx->d_ctr);
+        ctx->d_ctr_slot[0] = reinterpret_cast<Counters *>(base);
+        ctx->d_ctr_slot[1] = reinterpret_cast<Counters *>(base + kCtrBytes);
+        ctx->d_total = reinterpret_cast<unsigned long long *>(base + 2 * kCtrBytes);
+    }
     ctx->h_total = reinterpret_cast<unsigned long long *>(ctx->h_ctr + 1);
     ctx->n_sm = prop.multiProcessorCount;
     ctx->smem_optin = (int)prop.sharedMemPerBlockOptin;
@@ -515,7 +530,7 @@ RICH_API rich_status rich_destroy(rich_ctx *ctx) {
         free_emission(ctx);
         cudaFree(ctx->d_perm);
         cudaFree(ctx->d_perm_ok);
-        cudaFree(ctx->d_ctr);
+        cudaFree(ctx->d_ctr_slot[0]);
         cudaFreeHost(ctx->h_ctr);
         cudaGetLastError();
     }
@@ -831,6 +846,28 @@ RICH_API rich_status rich_emit(rich_ctx *ctx, const rich_tracks *t,
 }
 
 // -------------------------------------------------------------------- trace
+// The counter slot of the next trace: the slot the last trace did not use,
+// zeroed by that trace's kernel (else reset here; always inside a graph
+// capture, whose replays reuse the captured pointers). next: the slot the
+// trace kernel zeroes for the trace after it (none inside a capture).
+static rich_status trace_counters(rich_ctx *ctx, Counters **slot, Counters **next) {
+    const int s = ctx->cur_slot ^ 1;
+    if (!ctx->slot_zeroed[s] || ctx->capturing)
+        RICH_CUDA(cudaMemsetAsync(ctx->d_ctr_slot[s], 0, sizeof(Counters), ctx->stream));
+    *slot = ctx->d_ctr_slot[s];
+    *next = ctx->capturing ? nullptr : ctx->d_ctr_slot[ctx->cur_slot];
+    return RICH_OK;
+}
+
+// After a trace's launches: its slot is the one rich_hits reads.
+static void trace_counters_done(rich_ctx *ctx, bool next_zeroed) {
+    const int s = ctx->cur_slot ^ 1;
+    ctx->slot_zeroed[s] = false;
+    ctx->slot_zeroed[ctx->cur_slot] = next_zeroed;
+    ctx->cur_slot = s;
+    ctx->d_ctr = ctx->d_ctr_slot[s];
+}
+
 RICH_API rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
                                 const rich_trace_opts *o, const rich_outputs *out) {
     if (!ctx) return RICH_ERR_ARG;
@@ -885,7 +922,11 @@ RICH_API rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
         RICH_CUDA(cudaMalloc(&ctx->d_refine, sizeof(RefineRec) * hit_cap));
         ctx->refine_cap = hit_cap;
     }
-    RICH_CUDA(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), ctx->stream));
+    Counters *ctr = nullptr, *ctr_next = nullptr;
+    {
+        const rich_status cst = trace_counters(ctx, &ctr, &ctr_next);
+        if (cst != RICH_OK) return cst;
+    }
     TraceParams p{};
     p.precision = o->precision;
     p.max_bounces = o->max_bounces;
@@ -929,18 +970,21 @@ RICH_API rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
         ExtView ev{in->n, in->x, in->y, in->z, in->dx, in->dy, in->dz, in->lambda,
                    in->event, in->track, in->photon};
         if (in->n) {
-            RICH_CUDA(launch_trace(ctx->sc, &em, &ev, p, ctx->d_ctr, shape, ctx->stream));
+            RICH_CUDA(launch_trace(ctx->sc, &em, &ev, p, ctr, ctr_next, shape, ctx->stream));
             if (refine)
-                RICH_CUDA(launch_refine(ctx->sc, &em, &ev, p, ctx->d_ctr, ctx->n_sm, ctx->stream));
+                RICH_CUDA(launch_refine(ctx->sc, &em, &ev, p, ctr, ctx->n_sm, ctx->stream));
+        } else {
+            ctr_next = nullptr;          // no trace kernel: nothing zeroed
         }
         ctx->last_ext = true;
         ctx->last_ext_n = in->n;
     } else {
-        RICH_CUDA(launch_trace(ctx->sc, &em, nullptr, p, ctx->d_ctr, shape, ctx->stream));
+        RICH_CUDA(launch_trace(ctx->sc, &em, nullptr, p, ctr, ctr_next, shape, ctx->stream));
         if (refine)
-            RICH_CUDA(launch_refine(ctx->sc, &em, nullptr, p, ctx->d_ctr, ctx->n_sm, ctx->stream));
+            RICH_CUDA(launch_refine(ctx->sc, &em, nullptr, p, ctr, ctx->n_sm, ctx->stream));
         ctx->last_ext = false;
     }
+    trace_counters_done(ctx, ctr_next != nullptr);
     ctx->traced = true;
     ctx->last_capacity = p.hit_capacity;
     return RICH_OK;
@@ -1097,10 +1141,15 @@ RICH_API rich_status rich_trace_grad(rich_ctx *ctx, const rich_tracks *t,
     const int bps = trace_blocks_per_sm(false, true, cls, threads, shape.smem);
     if (bps < 1) return fail(ctx, RICH_ERR_ARG, "rich_trace_grad: launch shape does not fit");
     shape.blocks = bps * ctx->n_sm;
-    RICH_CUDA(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), ctx->stream));
+    Counters *ctr = nullptr, *ctr_next = nullptr;
+    {
+        const rich_status cst = trace_counters(ctx, &ctr, &ctr_next);
+        if (cst != RICH_OK) return cst;
+    }
     RICH_CUDA(cudaMemsetAsync(ctx->d_acc, 0, sizeof(double) * 12, ctx->stream));
     const EmitView em = emit_view(ctx);
-    RICH_CUDA(launch_trace(sv, &em, nullptr, p, ctx->d_ctr, shape, ctx->stream));
+    RICH_CUDA(launch_trace(sv, &em, nullptr, p, ctr, ctr_next, shape, ctx->stream));
+    trace_counters_done(ctx, ctr_next != nullptr);
     GradView gv{};
     gv.tiles = grad_duals;
     gv.n_tiles = ns;
@@ -1349,8 +1398,11 @@ RICH_API rich_status rich_graph_capture(rich_ctx *ctx, const rich_tracks *t,
     cudaStream_t user = ctx->stream;
     ctx->stream = ctx->capture_stream;
     RICH_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    ctx->capturing = true;               // the captured trace resets its own slot
     st = rich_emit(ctx, t, prm, nullptr, nullptr);
     if (st == RICH_OK) st = rich_trace(ctx, nullptr, o, out);
+    ctx->capturing = false;
+    ctx->graph_slot = ctx->cur_slot;
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
     ctx->stream = user;
@@ -1370,6 +1422,12 @@ RICH_API rich_status rich_graph_launch(rich_ctx *ctx) {
     if (!ctx->graph_exec) return fail(ctx, RICH_ERR_STATE, "rich_graph_launch: nothing captured");
     DeviceGuard guard(ctx->device);
     RICH_CUDA(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
+    // the replay counted into the captured slot; the other one is not known
+    // to be zero
+    ctx->cur_slot = ctx->graph_slot;
+    ctx->d_ctr = ctx->d_ctr_slot[ctx->graph_slot];
+    ctx->slot_zeroed[ctx->graph_slot] = false;
+    ctx->slot_zeroed[ctx->graph_slot ^ 1] = false;
     ctx->traced = true;
     ctx->last_ext = false;
     ctx->last_capacity = ctx->graph_capacity;

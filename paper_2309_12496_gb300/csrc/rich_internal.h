@@ -269,9 +269,11 @@ cudaError_t launch_order(const EmitView &em, uint32_t *perm, uint64_t cap, uint3
 cudaError_t launch_materialize(const SceneView &sc, const EmitView &em,
                                uint64_t n, const rich_photons &out,
                                cudaStream_t s);
+// counters: the trace's slot (the kernel also stores the photon total right
+// after it); next: the slot it zeroes for the next trace, or null.
 cudaError_t launch_trace(const SceneView &sc, const EmitView *em,
                          const ExtView *ext, const TraceParams &p,
-                         Counters *counters, const LaunchShape &shape,
+                         Counters *counters, Counters *next, const LaunchShape &shape,
                          cudaStream_t s);
 cudaError_t launch_refine(const SceneView &sc, const EmitView *em,
                           const ExtView *ext, const TraceParams &p,

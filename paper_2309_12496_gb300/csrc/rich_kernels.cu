@@ -541,6 +541,7 @@ __global__ void __launch_bounds__(32 * kOrderWarps) k_order(EmitView em, uint32_
                                                             uint64_t cap, uint32_t *perm_ok,
                                                             OrderScan scan) {
     grid_dep_wait();                     // the yield (and scan) pass has ended
+    grid_dep_launch_dependents();        // the trace's prologue may start
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     extern __shared__ unsigned long long s_gpre[];      // SCAN: one entry per group
     __shared__ unsigned long long s_wsum[kOrderWarps];
@@ -1473,6 +1474,7 @@ struct TraceArgs {
     ExtView ext;
     TraceParams p;
     Counters *ctr;
+    Counters *ctr_next;      // zeroed here for the next trace, or null
 };
 
 __device__ __forceinline__ uint32_t refl_word(const Photon &ph, int k,
@@ -1571,6 +1573,17 @@ k_trace(TraceArgs A) {
     if (threadIdx.x < RICH_N_FATES) s_fate[threadIdx.x] = 0;
     if (threadIdx.x == 0) s_hits = 0;
     __syncthreads();
+    // the emission (offsets, total, order) is complete from here on
+    grid_dep_wait();
+    if (blockIdx.x == 0) {
+        // the photon total beside this trace's counters, and the next
+        // trace's counter slot zeroed
+        if (threadIdx.x == 0)
+            *reinterpret_cast<unsigned long long *>(A.ctr + 1) =
+                EXT ? (unsigned long long)A.ext.n : *A.em.total;
+        if (A.ctr_next && threadIdx.x < (int)(sizeof(Counters) / sizeof(unsigned long long)))
+            reinterpret_cast<unsigned long long *>(A.ctr_next)[threadIdx.x] = 0ull;
+    }
 
     // (No early launch_dependents here: letting the refinement pass's blocks
     // be scheduled while the trace runs slowed the trace by ~5 % on large
@@ -2386,8 +2399,9 @@ static cudaError_t launch_trace_t(const TraceArgs &a, const LaunchShape &shape,
         if (e != cudaSuccess) return e;
         raised = shape.smem;
     }
-    kern<<<shape.blocks, shape.threads, shape.smem, s>>>(a);
-    return cudaGetLastError();
+    // programmatic: the prologue (staging the top BVH levels and the scene
+    // tables) may overlap the ordering pass ahead of it
+    return launch_pdl(kern, (unsigned)shape.blocks, (unsigned)shape.threads, shape.smem, s, a);
 }
 
 // Kernel variants: caller photons or fused emission; refinement side
@@ -2437,7 +2451,7 @@ static cudaError_t launch_cls(const TraceArgs &a, const LaunchShape &shape, cuda
 
 cudaError_t launch_trace(const SceneView &sc, const EmitView *em,
                          const ExtView *ext, const TraceParams &p,
-                         Counters *counters, const LaunchShape &shape,
+                         Counters *counters, Counters *next, const LaunchShape &shape,
                          cudaStream_t s) {
     TraceArgs a;
     a.sc = sc;
@@ -2445,6 +2459,7 @@ cudaError_t launch_trace(const SceneView &sc, const EmitView *em,
     a.ext = ext ? *ext : ExtView{};
     a.p = p;
     a.ctr = counters;
+    a.ctr_next = next;
     const bool refine = p.precision == RICH_PREC_REFINE64;
     if (ext) return refine ? launch_cls<true, true>(a, shape, s) : launch_cls<true, false>(a, shape, s);
     return refine ? launch_cls<false, true>(a, shape, s) : launch_cls<false, false>(a, shape, s);
