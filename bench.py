@@ -45,12 +45,12 @@ WORKLOAD = "rich1_meshed_1000_pion_tracks"
 # divided by its 350,350 photons: (2 x 244.19 M + 37.77 M + 87.12 M) / 350,350.
 FLOPS_PER_PHOTON = 1750.4
 # dram__bytes_read.sum + dram__bytes_write.sum of the same k_trace launch.
-TRACE_DRAM_BYTES = 6996480 + 259072
+TRACE_DRAM_BYTES = 7455744 + 263424
 # Warp instructions per photon of the same launch (smsp__inst_executed.sum
-# 99,206,315 / 350,350): the kernel is bound by instruction issue, so the
+# 99,229,133 / 350,350): the kernel is bound by instruction issue, so the
 # issue rate against 4 schedulers x SMs x clock is reported beside the FP32
 # fraction.
-WARP_INST_PER_PHOTON = 283.16
+WARP_INST_PER_PHOTON = 283.23
 FP32_LANES_PER_SM = 128
 SM_COUNT_NOMINAL = 152
 
