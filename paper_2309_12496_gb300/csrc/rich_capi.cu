@@ -18,8 +18,8 @@
 
 using namespace rich;
 
-// The counters and the photon total share one allocation (the total right
-// after the counters), so one copy reads both.
+// A counter slot: a trace's counters and, right after them, the photon
+// total that trace saw, so one copy reads both.
 constexpr size_t kCtrBytes = sizeof(Counters) + sizeof(unsigned long long);
 static_assert(sizeof(Counters) % 8 == 0, "the photon total follows the counters");
 
