@@ -85,6 +85,14 @@ class EmitParams(C.Structure):
 _OPTS_CACHE = {}
 
 
+def _host_hits(hits_host):
+    """(pointer, capacity in hit records) of a host hit buffer; None reads
+    the counters only."""
+    if hits_host is None:
+        return None, 0
+    return hits_host.data_ptr(), hits_host.numel() * hits_host.element_size() // HIT_DTYPE.itemsize
+
+
 def _trace_opts(seed, precision, max_bounces, max_steps, t_min, block_threads, blocks_per_sm,
                 refill_min, chunk, wide_regs, bvh_smem_nodes, prefilter):
     """rich_trace_opts, one struct per distinct set of values (the library
@@ -499,8 +507,8 @@ class Context:
                  dispersion=None):
         """One synchronous step from host memory (rich_run_host): host tracks
         in, the hit records copied into hits_host (a pinned uint8 tensor of
-        n x 40 bytes). Emission arguments as for emit. Returns (n_hits,
-        stats dict)."""
+        n x 40 bytes; None reads the counters only). Emission arguments as
+        for emit. Returns (n_hits, stats dict)."""
         # the call's argument objects are kept between steps (only the seed
         # changes in place): a step is dominated by the GPU, and the host
         # time before the first launch delays it
@@ -515,10 +523,10 @@ class Context:
         prm.seed = int(seed)
         o = _trace_opts(0, precision, max_bounces, max_steps, t_min, block_threads,
                         blocks_per_sm, refill_min, chunk, wide_regs, bvh_smem_nodes, prefilter)
-        cap = hits_host.numel() * hits_host.element_size() // HIT_DTYPE.itemsize
+        ptr, cap = _host_hits(hits_host)
         st = load().rich_run_host(self.handle, C.byref(tracks.desc()), C.byref(prm),
-                                  C.byref(o), C.byref(outputs.desc()), hits_host.data_ptr(),
-                                  cap, C.byref(n), C.byref(s))
+                                  C.byref(o), C.byref(outputs.desc()), ptr, cap, C.byref(n),
+                                  C.byref(s))
         _check(self.handle, st)
         return n.value, {"n_photons": s.n_photons, "n_hits": s.n_hits, "fate": list(s.n_fate),
                          "device_status": s.device_status, "photon_order": s.photon_order}
@@ -531,17 +539,17 @@ class Context:
                        yield_per_mm=0.0, spectrum_table=-1, dispersion=None):
         """Pipelined step (rich_run_host_async): returns a ticket for
         run_wait. Two steps may be in flight, each with its own outputs and
-        hits_host; the HostTracks must not change until waited for.
-        Emission arguments as for emit."""
+        hits_host (None: counters only); the HostTracks must not change
+        until waited for. Emission arguments as for emit."""
         prm = _emit_params(seed, n_minus_1, lambda_min, lambda_max, source, yield_per_mm,
                            spectrum_table, dispersion)
         o = _trace_opts(0, precision, max_bounces, max_steps, t_min, block_threads,
                         blocks_per_sm, refill_min, chunk, wide_regs, bvh_smem_nodes, prefilter)
         t = C.c_uint64(0)
-        cap = hits_host.numel() * hits_host.element_size() // HIT_DTYPE.itemsize
+        ptr, cap = _host_hits(hits_host)
         st = load().rich_run_host_async(self.handle, C.byref(tracks.desc()), C.byref(prm),
-                                        C.byref(o), C.byref(outputs.desc()), hits_host.data_ptr(),
-                                        cap, C.byref(t))
+                                        C.byref(o), C.byref(outputs.desc()), ptr, cap,
+                                        C.byref(t))
         _check(self.handle, st)
         return t.value
 

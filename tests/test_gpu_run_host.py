@@ -91,6 +91,11 @@ def test_run_host_counters_only(setup):
     status = load().rich_run_host(ctx.handle, C.byref(ht.desc()), C.byref(prm), C.byref(o),
                                   C.byref(out.desc()), None, 0, C.byref(nh2), C.byref(s))
     assert status == 0 and nh2.value == nh and s.n_photons == n
+    # the binding's None, synchronous and pipelined
+    nh3, st3 = ctx.run_host(ht, out, None, 0.0014, seed=9)
+    assert nh3 == nh and st3["n_photons"] == n
+    nh4, st4 = ctx.run_wait(ctx.run_host_async(ht, out, None, 0.0014, seed=9))
+    assert nh4 == nh and st4["n_photons"] == n
 
 
 def test_fate_array_smaller_than_the_photon_total(setup):
