@@ -539,9 +539,12 @@ constexpr uint32_t kOrderBinCache = 2048;
 template <bool SCAN>
 __global__ void __launch_bounds__(32 * kOrderWarps) k_order(EmitView em, uint32_t *perm,
                                                             uint64_t cap, uint32_t *perm_ok,
-                                                            OrderScan scan) {
+                                                            OrderScan scan, bool signal_early) {
     grid_dep_wait();                     // the yield (and scan) pass has ended
-    grid_dep_launch_dependents();        // the trace's prologue may start
+    // the trace's prologue may start, when every block orders one track;
+    // over many tracks per block the trace's blocks, resident early, slowed
+    // the ordering pass (RICH2, 4.9e5 tracks: 45 -> 50 ms per chunk)
+    if (signal_early) grid_dep_launch_dependents();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     extern __shared__ unsigned long long s_gpre[];      // SCAN: one entry per group
     __shared__ unsigned long long s_wsum[kOrderWarps];
@@ -648,15 +651,16 @@ cudaError_t launch_order(const EmitView &em, uint32_t *perm, uint64_t cap, uint3
     if (blocks < 1) blocks = 1;
     const int64_t max_blocks = (int64_t)n_sm * 16;
     if (blocks > max_blocks) blocks = max_blocks;
+    const bool early = em.n_tracks <= blocks;
     if (scan) {
         const int64_t groups = (em.n_tracks + kYieldThreads - 1) / kYieldThreads;
         if (groups > kOrderScanGroups) return cudaErrorInvalidValue;
         return launch_pdl(k_order<true>, (unsigned)blocks, 32 * kOrderWarps,
                           sizeof(unsigned long long) * (size_t)groups, s, em, perm, cap, perm_ok,
-                          *scan);
+                          *scan, early);
     }
     return launch_pdl(k_order<false>, (unsigned)blocks, 32 * kOrderWarps, 0, s, em, perm, cap,
-                      perm_ok, OrderScan{});
+                      perm_ok, OrderScan{}, early);
 }
 
 // ============================================================== emission
