@@ -46,10 +46,13 @@ def build(force: bool = False) -> str:
 
 
 def lib():
+    """The compiled oracle. RICH_ORACLE_LIB names another build of the same
+    source to load instead (the mutation tests load a copy with one step
+    deliberately broken, to show that a pin catches it)."""
     global _lib
     with _lock:
         if _lib is None:
-            _lib = C.CDLL(build())
+            _lib = C.CDLL(os.environ.get("RICH_ORACLE_LIB") or build())
             _declare(_lib)
         return _lib
 
@@ -113,6 +116,10 @@ def _declare(L):
     L.oracle_scene_pixels_per_event.restype = i64
     L.oracle_raycast.argtypes = [vp, i64, vp, vp, vp, C.c_double, C.c_int,
                                  vp, vp]
+    L.oracle_probe.argtypes = [vp, i64, vp, vp, vp, C.c_double, C.c_double, vp, vp,
+                               vp, vp, vp, vp]
+    L.oracle_trace_photons.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.oracle_trace_photons.restype = C.c_int
     L.oracle_table_eval.argtypes = [vp, C.c_int, C.c_float]
     L.oracle_table_eval.restype = C.c_float
     L.oracle_trace.argtypes = [vp, vp, vp, vp, i64, i64, vp]
@@ -274,6 +281,24 @@ class Scene:
                              t_min, int(use_bvh), _ptr(t), _ptr(prim))
         return t, prim
 
+    def probe(self, origins, dirs, skip=None, t_min=1e-3, eps=1e-3):
+        """Nearest hit of each ray with the normals at the hit: returns a dict
+        of prim (-1: none), t, n_geo, n_shade (the normal the reflection
+        uses), graze (bits of the nearest-hit decision; 8: the skipped
+        surface would have been nearer) and skipped_t (nearest hit on the
+        skipped surface, inf if none)."""
+        o = np.ascontiguousarray(origins, np.float64).reshape(-1, 3)
+        d = np.ascontiguousarray(dirs, np.float64).reshape(-1, 3)
+        n = len(o)
+        sk = None if skip is None else np.ascontiguousarray(skip, np.int32)
+        out = {"prim": np.empty(n, np.int32), "t": np.empty(n), "n_geo": np.empty((n, 3)),
+               "n_shade": np.empty((n, 3)), "graze": np.empty(n, np.int32),
+               "skipped_t": np.empty(n)}
+        lib().oracle_probe(self.handle, n, _ptr(o), _ptr(d), _ptr(sk), t_min, eps,
+                           _ptr(out["prim"]), _ptr(out["t"]), _ptr(out["n_geo"]),
+                           _ptr(out["n_shade"]), _ptr(out["graze"]), _ptr(out["skipped_t"]))
+        return out
+
     def grad(self, tracks, prm, theta, targets, sigma=1.0, fd=False, h_angle=1e-6,
              h_rel=1e-6):
         """Soft ring chi^2 loss at theta (10 parameters: 8 tile tilts, the
@@ -328,17 +353,7 @@ class Scene:
         out["offsets"] = off
         return out
 
-    def trace(self, tracks, prm, offsets=None, track_range=None,
-              n_hist_events=None, want_path=False, want_final=False,
-              want_hist=True):
-        """Trace every photon of tracks[track_range] and return per-photon
-        arrays indexed by global photon index (offsets from track_yield)."""
-        if offsets is None:
-            _, _, offsets = track_yield(tracks, prm)
-        offsets = np.ascontiguousarray(offsets, np.uint64)
-        tb, te = track_range if track_range is not None else (0, tracks.n)
-        n = int(offsets[-1])
-        h = _TracksHold(tracks)
+    def _outputs(self, n, prm, n_hist_events, want_path, want_final, want_hist):
         out = {
             "fate": np.zeros(n, np.uint8), "plane": np.full(n, -1, np.int32),
             "ix": np.zeros(n, np.int32), "iy": np.zeros(n, np.int32),
@@ -351,8 +366,6 @@ class Scene:
         if want_final:
             out["dir"] = np.zeros((n, 3))
             out["pos"] = np.zeros((n, 3))
-        if n_hist_events is None:
-            n_hist_events = int(tracks.event.max()) + 1 if tracks.n else 0
         if want_hist:
             out["pixel_counts"] = np.zeros(
                 (n_hist_events, self.pixels_per_event), np.uint32)
@@ -368,11 +381,50 @@ class Scene:
                         pixel_counts=_ptr(out.get("pixel_counts")),
                         event_sums=_ptr(out.get("event_sums")),
                         n_hist_events=n_hist_events if want_hist else 0)
+        return out, rec
+
+    def trace(self, tracks, prm, offsets=None, track_range=None,
+              n_hist_events=None, want_path=False, want_final=False,
+              want_hist=True):
+        """Trace every photon of tracks[track_range] and return per-photon
+        arrays indexed by global photon index (offsets from track_yield)."""
+        if offsets is None:
+            _, _, offsets = track_yield(tracks, prm)
+        offsets = np.ascontiguousarray(offsets, np.uint64)
+        tb, te = track_range if track_range is not None else (0, tracks.n)
+        n = int(offsets[-1])
+        h = _TracksHold(tracks)
+        if n_hist_events is None:
+            n_hist_events = int(tracks.event.max()) + 1 if tracks.n else 0
+        out, rec = self._outputs(n, prm, n_hist_events, want_path, want_final, want_hist)
         rc = lib().oracle_trace(self.handle, C.byref(h.rec), C.byref(prm),
                                 _ptr(offsets), tb, te, C.byref(rec))
         if rc != 0:
             raise ValueError("oracle_trace rejected its parameters")
         out["offsets"] = offsets
+        return out
+
+    def trace_photons(self, origin, direction, lam, event, track, photon, prm,
+                      n_hist_events=None, want_path=False, want_final=False,
+                      want_hist=True):
+        """Trace photons given by the caller (Sec. 4.2): FP32 origins and
+        directions (n, 3), FP32 wavelengths and the (event, track, photon)
+        keys of their draws under prm.seed. Per-photon arrays indexed by the
+        photon's position."""
+        o = np.ascontiguousarray(origin, np.float32).reshape(-1, 3)
+        d = np.ascontiguousarray(direction, np.float32).reshape(-1, 3)
+        n = len(o)
+        lam = np.ascontiguousarray(lam, np.float32).reshape(n)
+        ev = np.ascontiguousarray(event, np.uint32).reshape(n)
+        tk = np.ascontiguousarray(track, np.uint32).reshape(n)
+        ph = np.ascontiguousarray(photon, np.uint32).reshape(n)
+        if n_hist_events is None:
+            n_hist_events = int(ev.max()) + 1 if n else 0
+        out, rec = self._outputs(n, prm, n_hist_events, want_path, want_final, want_hist)
+        rc = lib().oracle_trace_photons(self.handle, n, _ptr(o), _ptr(d), _ptr(lam), _ptr(ev),
+                                        _ptr(tk), _ptr(ph), C.byref(prm), C.byref(rec))
+        if rc != 0:
+            raise ValueError("oracle_trace_photons rejected its parameters")
         return out
 
 

@@ -158,7 +158,8 @@ typedef struct {
     double *u, *v;
     float *lambda;
     uint8_t *n_refl;
-    uint8_t *graze;      /* bit 1 geometry, 2 probability, 4 pixel edge    */
+    uint8_t *graze;      /* bit 1 geometry, 2 probability, 4 pixel edge,
+                            8 the surface just left was nearer (skip rule) */
     int32_t *path;       /* max_steps primitive ids per photon, -1 padded  */
     double *dir_out;     /* final direction (3 per photon)                 */
     double *pos_out;     /* final position (3 per photon)                  */
@@ -999,19 +1000,27 @@ static int box_hit(const o_node *nd, v3 o, v3 d, double t_max, double pad)
     return 1;
 }
 
-/* Nearest surface along o + t d, t > t_min, skipping primitive `skip`.
- * Returns 1 and fills *hit if found; *graze set when the decision is
- * within eps of changing. */
-/* Nearest surface along the ray. `skip` is the primitive the photon just
- * left: it is not intersected again, and neither is any triangle of the
- * same surface (a photon leaving a mirror segment, a flat mirror or a window
- * face does not meet that surface again at its next step). */
+/* Nearest surface along o + t d, t > t_min. `skip` is the primitive the
+ * photon just left: it is not taken as a hit again, and neither is any
+ * triangle of the same surface (a photon leaving a mirror segment, a flat
+ * mirror or a window face is not intersected with that surface at its next
+ * step). For planes that rule is exact. For a concave segment it is an
+ * approximation: a photon leaving it close to the tangent plane can meet the
+ * same segment again further along the chord. So the skipped primitive and
+ * surface are still intersected, into a search of their own, and when one of
+ * them would have been the nearest hit (or within eps of it) the decision is
+ * flagged (*graze bit 8). Returns 1 and fills *hit if a hit is found; *graze
+ * bit 1 is set when the nearest-hit decision is within eps of changing.
+ * *skipped_t (may be NULL) receives the distance of the nearest hit on the
+ * skipped surface, or INFINITY. */
 static int nearest(const o_scene *sc, v3 o, v3 d, int skip, double t_min,
-                   double eps, int use_bvh, o_cand *hit, int *graze)
+                   double eps, int use_bvh, o_cand *hit, int *graze,
+                   double *skipped_t)
 {
-    o_search s;
+    o_search s, sk;
     memset(&s, 0, sizeof s);
-    double near_t = INFINITY;
+    memset(&sk, 0, sizeof sk);
+    double near_t = INFINITY, sk_near = INFINITY;
     int prim = 0;
     const int tb = sc->n_spheres + sc->n_rects;
     const int skip_surface = (skip >= tb && skip - tb < sc->n_tris)
@@ -1019,11 +1028,11 @@ static int nearest(const o_scene *sc, v3 o, v3 d, int skip, double t_min,
 #define SKIP_TRI(ti) ((tb + (ti)) == skip || \
                       (skip_surface >= 0 && sc->tris[(ti)].surface == skip_surface))
     for (int i = 0; i < sc->n_spheres; ++i, ++prim)
-        if (prim != skip)
-            isect_sphere(&sc->spheres[i], prim, o, d, t_min, eps, &s, &near_t);
+        isect_sphere(&sc->spheres[i], prim, o, d, t_min, eps,
+                     prim == skip ? &sk : &s, prim == skip ? &sk_near : &near_t);
     for (int i = 0; i < sc->n_rects; ++i, ++prim)
-        if (prim != skip)
-            isect_rect(&sc->rects[i], prim, i, o, d, t_min, eps, &s, &near_t);
+        isect_rect(&sc->rects[i], prim, i, o, d, t_min, eps,
+                   prim == skip ? &sk : &s, prim == skip ? &sk_near : &near_t);
     int tri_base = prim;
     if (sc->n_tris > 0) {
         if (use_bvh) {
@@ -1037,9 +1046,9 @@ static int nearest(const o_scene *sc, v3 o, v3 d, int skip, double t_min,
                 if (nd->left < 0) {
                     for (int k = nd->first; k < nd->first + nd->count; ++k) {
                         int ti = sc->order[k];
-                        if (SKIP_TRI(ti)) continue;
-                        isect_tri(&sc->tris[ti], tri_base + ti, ti, o, d,
-                                  t_min, eps, &s, &near_t);
+                        int skipped = SKIP_TRI(ti);
+                        isect_tri(&sc->tris[ti], tri_base + ti, ti, o, d, t_min, eps,
+                                  skipped ? &sk : &s, skipped ? &sk_near : &near_t);
                     }
                 } else {
                     stack[sp++] = nd->left;
@@ -1048,9 +1057,9 @@ static int nearest(const o_scene *sc, v3 o, v3 d, int skip, double t_min,
             }
         } else {
             for (int64_t ti = 0; ti < sc->n_tris; ++ti) {
-                if (SKIP_TRI(ti)) continue;
-                isect_tri(&sc->tris[ti], (int)(tri_base + ti), (int)ti, o, d,
-                          t_min, eps, &s, &near_t);
+                int skipped = SKIP_TRI(ti);
+                isect_tri(&sc->tris[ti], (int)(tri_base + ti), (int)ti, o, d, t_min, eps,
+                          skipped ? &sk : &s, skipped ? &sk_near : &near_t);
             }
         }
     }
@@ -1058,6 +1067,12 @@ static int nearest(const o_scene *sc, v3 o, v3 d, int skip, double t_min,
     *graze = s.graze;
     if (s.found && s.best.edge < eps) *graze = 1;
     if (near_t < INFINITY && (!s.found || near_t < s.best.t + eps)) *graze = 1;
+    /* the skip rule decided the hit: the skipped surface (on it, or within
+     * eps of its edge) lies nearer than the hit taken */
+    double sk_t = sk.found ? sk.best.t : INFINITY;
+    if (sk_near < sk_t) sk_t = sk_near;
+    if (sk_t < INFINITY && (!s.found || sk_t < s.best.t + eps)) *graze |= 8;
+    if (skipped_t) *skipped_t = sk.found ? sk.best.t : INFINITY;
     if (s.found) *hit = s.best;
     return s.found;
 }
@@ -1074,7 +1089,7 @@ void oracle_raycast(void *scene, int64_t n, const double *o, const double *d,
         v3 oo = mk(o[3 * i], o[3 * i + 1], o[3 * i + 2]);
         v3 dd = mk(d[3 * i], d[3 * i + 1], d[3 * i + 2]);
         int f = nearest(sc, oo, dd, skip ? skip[i] : -1, t_min, 1e-9, use_bvh,
-                        &h, &g);
+                        &h, &g, NULL);
         t_out[i] = f ? h.t : INFINITY;
         prim_out[i] = f ? h.prim : -1;
     }
@@ -1147,6 +1162,34 @@ static int prim_material(const o_scene *sc, const o_cand *h)
     return sc->tris[h->index].material;
 }
 
+/* Ray probe for the pins of the surface geometry: nearest hit of each ray
+ * (prim, t; -1 and INFINITY if none), the normals at the hit (geometric, and
+ * the one the reflection uses), the graze bits of the nearest-hit decision
+ * and the distance of the nearest hit on the skipped surface. */
+void oracle_probe(void *scene, int64_t n, const double *o, const double *d,
+                  const int32_t *skip, double t_min, double eps, int32_t *prim_out,
+                  double *t_out, double *n_geo_out, double *n_shade_out,
+                  int32_t *graze_out, double *skipped_t_out)
+{
+    const o_scene *sc = (const o_scene *)scene;
+    for (int64_t i = 0; i < n; ++i) {
+        o_cand h;
+        int g = 0;
+        double st;
+        v3 oo = mk(o[3 * i], o[3 * i + 1], o[3 * i + 2]);
+        v3 dd = mk(d[3 * i], d[3 * i + 1], d[3 * i + 2]);
+        int f = nearest(sc, oo, dd, skip ? skip[i] : -1, t_min, eps, 1, &h, &g, &st);
+        v3 ng = mk(0, 0, 0), ns = mk(0, 0, 0);
+        if (f) surface_normals(sc, &h, add(oo, scl(dd, h.t)), &ng, &ns);
+        prim_out[i] = f ? h.prim : -1;
+        t_out[i] = f ? h.t : INFINITY;
+        n_geo_out[3 * i] = ng.x; n_geo_out[3 * i + 1] = ng.y; n_geo_out[3 * i + 2] = ng.z;
+        n_shade_out[3 * i] = ns.x; n_shade_out[3 * i + 1] = ns.y; n_shade_out[3 * i + 2] = ns.z;
+        graze_out[i] = g;
+        skipped_t_out[i] = st;
+    }
+}
+
 typedef struct {
     int fate, plane, ix, iy, n_refl, graze;
     double u, v;
@@ -1198,12 +1241,12 @@ static void trace_photon(const o_scene *sc, const o_params *prm,
         o_cand h;
         int g = 0;
         if (!nearest(sc, o, d, skip, prm->t_min, prm->eps, prm->use_bvh, &h,
-                     &g)) {
-            if (g) graze |= 1;
+                     &g, NULL)) {
+            graze |= (g & 8) | ((g & ~8) ? 1 : 0);
             res->fate = FATE_ESCAPED;
             break;
         }
-        if (g) graze |= 1;
+        graze |= (g & 8) | ((g & ~8) ? 1 : 0);
         if (path) path[step] = h.prim;
         v3 p = add(o, scl(d, h.t));
         v3 n_geo, n_sh;
@@ -1309,19 +1352,101 @@ static void trace_photon(const o_scene *sc, const o_params *prm,
 }
 
 /* ------------------------------------------------------------------------ */
-/* 6. Driver: all photons of tracks [track_begin, track_end).               */
+/* 6. Drivers: the photons of a range of tracks, or photons supplied by the */
+/*    caller (the photon emitter's vectors of positions and momenta,        */
+/*    Sec. 4.2).                                                            */
 /* ------------------------------------------------------------------------ */
-int oracle_trace(void *scene, const o_tracks_in *t, const o_params *prm,
-                 const uint64_t *offsets, int64_t track_begin,
-                 int64_t track_end, const o_photon_out *out)
+/* One emitted photon to its fate, with the efficiencies applied before
+ * propagation when the parameters list them (Sec. 4.3). */
+static void propagate(const o_scene *sc, const o_params *prm, const o_photon *ph,
+                      o_result *r, int32_t *path)
 {
-    const o_scene *sc = (const o_scene *)scene;
+    int run = 1;
+    if (prm->n_prefilter > 0) {
+        /* Sec. 4.3: accept/reject on the product of the efficiencies
+         * before propagation, with the photon's QE uniform */
+        float P = prefilter_prob(sc, prm, ph->lambda);
+        if (!(ph->u_qe < (double)P)) {
+            prefiltered(ph, P, prm, r);
+            if (path) for (int k = 0; k < prm->max_steps; ++k) path[k] = -1;
+            run = 0;
+        } else if (fabs(ph->u_qe - (double)P) < prm->prob_eps) {
+            run = 2;
+        }
+    }
+    if (run) {
+        trace_photon(sc, prm, ph, r, path, prm->n_prefilter > 0);
+        if (run == 2) r->graze |= 2;
+    }
+    r->graze |= ph->graze;
+}
+
+/* Store the result of photon g (event ev) in the output arrays, count its
+ * pixel and add it to its event's sums. */
+static void record_photon(const o_scene *sc, const o_photon_out *out, int64_t g,
+                          int64_t ev, float lambda, const o_result *r)
+{
+    if (out->fate) out->fate[g] = (uint8_t)r->fate;
+    if (out->plane) out->plane[g] = r->plane;
+    if (out->ix) out->ix[g] = r->ix;
+    if (out->iy) out->iy[g] = r->iy;
+    if (out->u) out->u[g] = r->u;
+    if (out->v) out->v[g] = r->v;
+    if (out->lambda) out->lambda[g] = lambda;
+    if (out->n_refl) out->n_refl[g] = (uint8_t)r->n_refl;
+    if (out->graze) out->graze[g] = (uint8_t)r->graze;
+    if (out->dir_out) {
+        out->dir_out[3 * g] = r->d.x;
+        out->dir_out[3 * g + 1] = r->d.y;
+        out->dir_out[3 * g + 2] = r->d.z;
+    }
+    if (out->pos_out) {
+        out->pos_out[3 * g] = r->o.x;
+        out->pos_out[3 * g + 1] = r->o.y;
+        out->pos_out[3 * g + 2] = r->o.z;
+    }
+    if (r->fate == FATE_DETECTED && ev < out->n_hist_events) {
+        if (out->pixel_counts) {
+            int64_t idx = ev * sc->pixels_per_event + sc->plane_offset[r->plane] +
+                          (int64_t)r->iy * sc->plane_nx[r->plane] + r->ix;
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+            out->pixel_counts[idx] += 1u;
+        }
+        if (out->event_sums) {
+            double *es = out->event_sums + (ev * sc->n_planes + r->plane) * 4;
+#ifdef _OPENMP
+#pragma omp critical(oracle_sums)
+#endif
+            {
+                es[0] += 1.0;
+                es[1] += r->u;
+                es[2] += r->v;
+                es[3] += (double)lambda;
+            }
+        }
+    }
+}
+
+static int check_params(const o_scene *sc, const o_params *prm)
+{
     if (prm->max_steps > 16 || prm->max_bounces > 8) return -1;
     if (prm->n_prefilter < 0 || prm->n_prefilter > 4) return -1;
     if (prm->source != SRC_CHERENKOV && prm->source != SRC_ISOTROPIC) return -1;
     for (int k = 0; k < prm->n_prefilter; ++k)
         if (prm->prefilter_tables[k] < 0 || prm->prefilter_tables[k] >= sc->n_tables)
             return -1;
+    return 0;
+}
+
+/* All photons of tracks [track_begin, track_end), emitted from the tracks. */
+int oracle_trace(void *scene, const o_tracks_in *t, const o_params *prm,
+                 const uint64_t *offsets, int64_t track_begin,
+                 int64_t track_end, const o_photon_out *out)
+{
+    const o_scene *sc = (const o_scene *)scene;
+    if (check_params(sc, prm)) return -1;
     int64_t first = (int64_t)offsets[track_begin];
     int64_t last = (int64_t)offsets[track_end];
 #ifdef _OPENMP
@@ -1340,66 +1465,49 @@ int oracle_trace(void *scene, const o_tracks_in *t, const o_params *prm,
         emit_photon(t, prm, lo, j, &ph);
         o_result r;
         int32_t *path = out->path ? out->path + g * prm->max_steps : NULL;
-        int run = 1;
-        if (prm->n_prefilter > 0) {
-            /* Sec. 4.3: accept/reject on the product of the efficiencies
-             * before propagation, with the photon's QE uniform */
-            float P = prefilter_prob(sc, prm, ph.lambda);
-            if (!(ph.u_qe < (double)P)) {
-                prefiltered(&ph, P, prm, &r);
-                if (path) for (int k = 0; k < prm->max_steps; ++k) path[k] = -1;
-                run = 0;
-            } else if (fabs(ph.u_qe - (double)P) < prm->prob_eps) {
-                run = 2;
-            }
-        }
-        if (run) {
-            trace_photon(sc, prm, &ph, &r, path, prm->n_prefilter > 0);
-            if (run == 2) r.graze |= 2;
-        }
-        r.graze |= ph.graze;
-        if (out->fate) out->fate[g] = (uint8_t)r.fate;
-        if (out->plane) out->plane[g] = r.plane;
-        if (out->ix) out->ix[g] = r.ix;
-        if (out->iy) out->iy[g] = r.iy;
-        if (out->u) out->u[g] = r.u;
-        if (out->v) out->v[g] = r.v;
-        if (out->lambda) out->lambda[g] = ph.lambda;
-        if (out->n_refl) out->n_refl[g] = (uint8_t)r.n_refl;
-        if (out->graze) out->graze[g] = (uint8_t)r.graze;
-        if (out->dir_out) {
-            out->dir_out[3 * g] = r.d.x;
-            out->dir_out[3 * g + 1] = r.d.y;
-            out->dir_out[3 * g + 2] = r.d.z;
-        }
-        if (out->pos_out) {
-            out->pos_out[3 * g] = r.o.x;
-            out->pos_out[3 * g + 1] = r.o.y;
-            out->pos_out[3 * g + 2] = r.o.z;
-        }
-        if (r.fate == FATE_DETECTED && (int64_t)t->event[lo] < out->n_hist_events) {
-            int64_t ev = t->event[lo];
-            if (out->pixel_counts) {
-                int64_t idx = ev * sc->pixels_per_event + sc->plane_offset[r.plane] +
-                              (int64_t)r.iy * sc->plane_nx[r.plane] + r.ix;
+        propagate(sc, prm, &ph, &r, path);
+        record_photon(sc, out, g, (int64_t)t->event[lo], ph.lambda, &r);
+    }
+    return 0;
+}
+
+/* Photons given by the caller (Sec. 4.2: the emitter takes vectors of
+ * positions and momenta): origin (mm) and direction as FP32 triples, the
+ * wavelength (nm), and the key (event, track, photon) that selects the
+ * photon's reflectivity and QE draws (blocks 0-2 of the draw map, as for an
+ * emitted photon with the same key); prm->seed keys the generator. The
+ * direction need not be exactly of unit length: it is normalised in FP64.
+ * Results are indexed by the photon's position in the arrays. */
+int oracle_trace_photons(void *scene, int64_t n, const float *origin, const float *dir,
+                         const float *lambda, const uint32_t *event, const uint32_t *track,
+                         const uint32_t *photon, const o_params *prm,
+                         const o_photon_out *out)
+{
+    const o_scene *sc = (const o_scene *)scene;
+    if (check_params(sc, prm)) return -1;
 #ifdef _OPENMP
-#pragma omp atomic
+    if (prm->n_threads > 0) omp_set_num_threads(prm->n_threads);
+#pragma omp parallel for schedule(dynamic, 256)
 #endif
-                out->pixel_counts[idx] += 1u;
-            }
-            if (out->event_sums) {
-                double *es = out->event_sums + (ev * sc->n_planes + r.plane) * 4;
-#ifdef _OPENMP
-#pragma omp critical(oracle_sums)
-#endif
-                {
-                    es[0] += 1.0;
-                    es[1] += r.u;
-                    es[2] += r.v;
-                    es[3] += (double)ph.lambda;
-                }
-            }
+    for (int64_t g = 0; g < n; ++g) {
+        uint32_t w0[4], w1[4], w2[4];
+        draw_block(prm->seed, event[g], track[g], photon[g], 0, w0);
+        draw_block(prm->seed, event[g], track[g], photon[g], 1, w1);
+        draw_block(prm->seed, event[g], track[g], photon[g], 2, w2);
+        o_photon ph;
+        memset(&ph, 0, sizeof ph);
+        ph.o = fromf(origin + 3 * g);
+        ph.d = fromf(dir + 3 * g);
+        ph.lambda = lambda[g];
+        ph.u_qe = u24(w0[3]);
+        for (int k = 0; k < 4; ++k) {
+            ph.u_refl[k] = u24(w1[k]);
+            ph.u_refl[4 + k] = u24(w2[k]);
         }
+        o_result r;
+        int32_t *path = out->path ? out->path + g * prm->max_steps : NULL;
+        propagate(sc, prm, &ph, &r, path);
+        record_photon(sc, out, g, (int64_t)event[g], ph.lambda, &r);
     }
     return 0;
 }

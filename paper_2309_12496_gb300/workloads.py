@@ -246,19 +246,29 @@ QUARTZ_N = [1.5510, 1.5320, 1.5170, 1.5050, 1.4950, 1.4870, 1.4810, 1.4760, 1.47
 
 # ----------------------------------------------------------- point source
 def point_source_scene(radius=2710.0, half_aperture=0.3, n_pix=256,
-                       pitch=PIXEL_PITCH) -> Scene:
-    """One analytic spherical mirror with centre of curvature at the origin
-    and its pole on +z; a detector plane at z = R/2 facing the mirror,
-    n_pix x n_pix pixels centred on the axis. QE = 0.3 exp(-((l-400)/120)^2),
-    R = 0.9 (both analytic)."""
-    b = _Builder("point_source")
+                       pitch=PIXEL_PITCH, meshed=False, mesh_half=300.0,
+                       mesh_cells=40) -> Scene:
+    """One spherical mirror with centre of curvature at the origin and its
+    pole on +z; a detector plane at z = R/2 facing the mirror, n_pix x n_pix
+    pixels centred on the axis. QE = 0.3 exp(-((l-400)/120)^2), R = 0.9
+    (both analytic). meshed: the mirror is instead the patch of the sphere
+    over the tangent square [-mesh_half, mesh_half]^2 as 2 x mesh_cells^2
+    smooth-normal triangles (15 mm cells by default, vertex normals pointing
+    at the centre), one surface."""
+    b = _Builder("point_source_meshed" if meshed else "point_source")
     t_qe = b.table_gauss(0.3, 400.0, 120.0)
     t_r = b.table_const(0.9)
-    m_mirror = b.material(MAT_MIRROR, t_r)
+    m_mirror = b.material(MAT_MIRROR, t_r, flags=MAT_SMOOTH if meshed else 0)
     m_det = b.material(MAT_DETECTOR, t_qe, plane=0)
-    b.sphere(center=(0.0, 0.0, 0.0), radius=radius, axis=(0.0, 0.0, 1.0),
-             e1=(1.0, 0.0, 0.0), e2=(0.0, 1.0, 0.0), material=m_mirror,
-             cos_min=math.cos(half_aperture))
+    c = np.zeros(3)
+    axis, e1, e2 = np.array([0.0, 0.0, 1.0]), np.array([1.0, 0.0, 0.0]), np.array([0.0, 1.0, 0.0])
+    if meshed:
+        tris, nrm = _mesh_rect_tile(c, radius, axis, e1, e2, -mesh_half, mesh_half,
+                                    -mesh_half, mesh_half, mesh_cells, mesh_cells)
+        b.triangles(tris, nrm, m_mirror, smooth=True)
+    else:
+        b.sphere(center=c, radius=radius, axis=axis, e1=e1, e2=e2, material=m_mirror,
+                 cos_min=math.cos(half_aperture))
     half = n_pix * pitch / 2.0
     b.rect(origin=(-half, -half, radius / 2.0), u_axis=(1.0, 0.0, 0.0),
            v_axis=(0.0, 1.0, 0.0), width=n_pix * pitch, height=n_pix * pitch,
@@ -694,11 +704,14 @@ class Workload:
     dispersion: tuple | None = None   # (a nm^-2, lambda0 nm): n - 1 = a/(1/l0^2 - 1/l^2)
 
 
-def point_source(n_photons=100_000) -> Workload:
-    return Workload("point_source", point_source_scene(),
+def point_source(n_photons=100_000, meshed=False) -> Workload:
+    return Workload("point_source_meshed" if meshed else "point_source",
+                    point_source_scene(meshed=meshed),
                     point_source_tracks(n_photons), n_minus_1=0.0014,
                     description=f"{n_photons} photons from the centre of "
-                    "curvature of an R=2710 mm sphere, n=1.0014, beta=1")
+                    "curvature of an R=2710 mm sphere"
+                    + (" (smooth-normal triangle mesh)" if meshed else "")
+                    + ", n=1.0014, beta=1")
 
 
 def rich1(n_tracks=1000, seed=0, meshed=True) -> Workload:
