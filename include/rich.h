@@ -314,6 +314,13 @@ typedef struct rich_trace_opts {
      * prefilter_tables: indices into the scene's tables. */
     int32_t n_prefilter;
     int32_t prefilter_tables[4];
+    /* Iterations of each block's bounded wait for the TMA copy of the top
+     * BVH nodes into shared memory (0: default, 2^20). When the wait runs
+     * out the trace records RICH_ERR_TIMEOUT (read by rich_hits), waits
+     * again, bounded, for the copy still in flight, and reads every node from
+     * global memory instead: results are unchanged. A negative value makes
+     * the first wait give up at once (a test of that path). */
+    int32_t wait_limit;
 } rich_trace_opts;
 
 /* ----------------------------------------------------------------- outputs */
@@ -469,8 +476,10 @@ RICH_API rich_status rich_run_host(rich_ctx *ctx, const rich_tracks *host_tracks
  * rich_run_wait completes it. At most two steps are in flight per context
  * (RICH_ERR_STATE for a third), so the host can enqueue step i + 1 while
  * the GPU runs step i. Each step in flight needs its own out buffers and
- * host_hits buffer (rich_run_wait may copy further records from its out);
- * the host track arrays must stay unchanged until the step is waited for. */
+ * host_hits buffer (rich_run_wait may copy further records from its out):
+ * RICH_ERR_ARG, with nothing enqueued, when out->hits or host_hits is the
+ * one of the other step in flight. The host track arrays must stay
+ * unchanged until the step is waited for. */
 RICH_API rich_status rich_run_host_async(rich_ctx *ctx, const rich_tracks *host_tracks,
                                          const rich_emit_params *params,
                                          const rich_trace_opts *opts, const rich_outputs *out,

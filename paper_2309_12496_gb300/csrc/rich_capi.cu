@@ -868,6 +868,12 @@ static void trace_counters_done(rich_ctx *ctx, bool next_zeroed) {
     ctx->d_ctr = ctx->d_ctr_slot[s];
 }
 
+// Iterations of the trace blocks' bounded wait for the shared-memory copy of
+// the top BVH nodes: the option's value, 2^20 by default, none when negative.
+static int32_t trace_wait_limit(int32_t opt) {
+    return opt == 0 ? (1 << 20) : (opt < 0 ? 0 : opt);
+}
+
 RICH_API rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
                                 const rich_trace_opts *o, const rich_outputs *out) {
     if (!ctx) return RICH_ERR_ARG;
@@ -943,6 +949,7 @@ RICH_API rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
     p.fate_capacity = out->fate ? out->fate_capacity : 0;
     p.refine = ctx->d_refine;
     p.smem_nodes = smem_nodes;
+    p.wait_limit = trace_wait_limit(o->wait_limit);
     p.n_prefilter = o->n_prefilter;
     for (int k = 0; k < 4; ++k) p.prefilter_tables[k] = k < o->n_prefilter ? o->prefilter_tables[k] : 0;
     LaunchShape shape;
@@ -1131,6 +1138,7 @@ RICH_API rich_status rich_trace_grad(rich_ctx *ctx, const rich_tracks *t,
     p.fate_capacity = out->fate ? out->fate_capacity : 0;
     p.refine = ctx->d_refine;
     p.smem_nodes = smem_nodes;
+    p.wait_limit = trace_wait_limit(fo.wait_limit);
     if (p.max_bounces < 1 || p.max_bounces > RICH_MAX_BOUNCES || p.max_steps < 1 ||
         p.max_steps > RICH_MAX_STEPS || threads % 32 || threads > 1024)
         return fail(ctx, RICH_ERR_ARG, "rich_trace_grad: trace options out of range");
@@ -1349,6 +1357,15 @@ RICH_API rich_status rich_run_host_async(rich_ctx *ctx, const rich_tracks *ht,
     if (S.in_flight)
         return fail(ctx, RICH_ERR_STATE,
                     "rich_run_host_async: two steps are in flight; wait for the older one");
+    // the other step in flight still writes its hit records into its own
+    // buffers (its trace, its early copy, rich_run_wait's completion copy)
+    const RunSlot &other = ctx->run_slots[(t + 1) % 2];
+    if (other.in_flight && out && out->hits && out->hits == other.dev_hits)
+        return fail(ctx, RICH_ERR_ARG,
+                    "rich_run_host_async: out->hits is the hit buffer of the step in flight");
+    if (other.in_flight && host_hits && host_hits == other.host_hits)
+        return fail(ctx, RICH_ERR_ARG,
+                    "rich_run_host_async: host_hits is the host buffer of the step in flight");
     DeviceGuard guard(ctx->device);
     const rich_status st = run_enqueue(ctx, "rich_run_host_async", ht, prm, o, out, host_hits,
                                        host_hit_capacity, S);

@@ -203,6 +203,7 @@ struct TraceParams {
     int32_t smem_nodes;       // BVH nodes [0, smem_nodes) staged in shared memory
     int32_t n_prefilter;      // > 0: efficiencies applied before propagation
     int32_t prefilter_tables[4];
+    int32_t wait_limit;       // iterations of the bounded wait for the node copy
 };
 
 // Sphere tile i at the gradient's parameters: centre C = P - R a(alpha_i,

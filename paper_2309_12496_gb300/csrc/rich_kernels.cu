@@ -1554,19 +1554,26 @@ k_trace(TraceArgs A) {
         S = {g, t, r, tb, m, sc.n_groups, sc.n_tiles, sc.n_rects};
     }
     if (n_snodes_req > 0) {
-        uint32_t done = 0;
-        for (int it = 0; it < (1 << 20) && !done; ++it) {
+        auto try_wait = [&]() {
+            uint32_t ok;
             asm volatile(
                 "{\n\t.reg .pred p;\n\t"
                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
                 "selp.u32 %0, 1, 0, p;\n\t}"
-                : "=r"(done)
+                : "=r"(ok)
                 : "r"(bar)
                 : "memory");
-        }
+            return ok;
+        };
+        uint32_t done = 0;
+        for (int it = 0; it < A.p.wait_limit && !done; ++it) done = try_wait();
         if (!done) {
+            // the wait ran out: record it, read every node from global
+            // memory, and wait again (bounded) for the copy still in flight
+            // so that it does not land while the block runs on or exits
             set_status(A.ctr, RICH_ERR_TIMEOUT);
             n_snodes = 0;
+            for (int it = 0; it < (1 << 20) && !done; ++it) done = try_wait();
         }
     }
     __shared__ unsigned long long s_fate[RICH_N_FATES];

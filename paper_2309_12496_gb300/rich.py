@@ -94,11 +94,12 @@ def _host_hits(hits_host):
 
 
 def _trace_opts(seed, precision, max_bounces, max_steps, t_min, block_threads, blocks_per_sm,
-                refill_min, chunk, wide_regs, bvh_smem_nodes, prefilter):
+                refill_min, chunk, wide_regs, bvh_smem_nodes, prefilter, wait_limit=0):
     """rich_trace_opts, one struct per distinct set of values (the library
     only reads it)."""
     key = (int(seed), precision, max_bounces, max_steps, float(t_min), block_threads,
-           blocks_per_sm, refill_min, chunk, wide_regs, bvh_smem_nodes, tuple(prefilter))
+           blocks_per_sm, refill_min, chunk, wide_regs, bvh_smem_nodes, tuple(prefilter),
+           int(wait_limit))
     o = _OPTS_CACHE.get(key)
     if o is None:
         if len(_OPTS_CACHE) > 256:
@@ -107,7 +108,8 @@ def _trace_opts(seed, precision, max_bounces, max_steps, t_min, block_threads, b
             seed=int(seed), precision=precision, max_bounces=max_bounces, max_steps=max_steps,
             t_min=t_min, block_threads=block_threads, blocks_per_sm=blocks_per_sm,
             refill_min=refill_min, chunk=chunk, wide_regs=wide_regs,
-            bvh_smem_nodes=bvh_smem_nodes, **_prefilter_fields(prefilter))
+            bvh_smem_nodes=bvh_smem_nodes, wait_limit=int(wait_limit),
+            **_prefilter_fields(prefilter))
     return o
 
 
@@ -137,7 +139,7 @@ class TraceOpts(C.Structure):
                 ("blocks_per_sm", C.c_int32), ("refill_min", C.c_int32),
                 ("chunk", C.c_int32), ("wide_regs", C.c_int32),
                 ("bvh_smem_nodes", C.c_int32), ("n_prefilter", C.c_int32),
-                ("prefilter_tables", C.c_int32 * 4)]
+                ("prefilter_tables", C.c_int32 * 4), ("wait_limit", C.c_int32)]
 
 
 def _prefilter_fields(prefilter):
@@ -489,11 +491,14 @@ class Context:
     def trace(self, outputs: TraceOutputs, photons: PhotonBuffers | None = None,
               precision=PREC_REFINE64, max_bounces=8, max_steps=16, t_min=1e-3,
               seed=0, block_threads=0, blocks_per_sm=0, refill_min=0, chunk=0,
-              wide_regs=0, bvh_smem_nodes=-1, prefilter=()):
+              wide_regs=0, bvh_smem_nodes=-1, prefilter=(), wait_limit=0):
         """prefilter: scene table indices whose product is applied as one
-        accept/reject per photon before propagation (Sec. 4.3)."""
+        accept/reject per photon before propagation (Sec. 4.3). wait_limit:
+        iterations of the bounded wait for the shared-memory node copy (0:
+        default; negative: the wait gives up at once, a test of that path)."""
         o = _trace_opts(seed, precision, max_bounces, max_steps, t_min, block_threads,
-                        blocks_per_sm, refill_min, chunk, wide_regs, bvh_smem_nodes, prefilter)
+                        blocks_per_sm, refill_min, chunk, wide_regs, bvh_smem_nodes, prefilter,
+                        wait_limit)
         pd = photons.desc() if photons is not None else None
         st = load().rich_trace(self.handle, None if pd is None else C.byref(pd),
                                C.byref(o), C.byref(outputs.desc()))
@@ -621,12 +626,15 @@ class Context:
         _check(self.handle, st)
         return float(loss.value), np.array(g[:], np.float64), int(used.value)
 
-    def hits(self, allow_overflow=False):
-        """Returns (n_hits, stats dict); synchronises the context stream."""
+    def hits(self, allow_overflow=False, allow=()):
+        """Returns (n_hits, stats dict); synchronises the context stream.
+        Raises RichError on a non-OK status, except overflow with
+        allow_overflow and the statuses listed in `allow` (stats["status"]
+        then holds it)."""
         n = C.c_uint64(0)
         s = Stats()
         st = load().rich_hits(self.handle, C.byref(n), C.byref(s))
-        if not (allow_overflow and st == 4):
+        if not ((allow_overflow and st == 4) or st in allow):
             _check(self.handle, st)
         stats = {"n_photons": int(s.n_photons), "n_hits": int(s.n_hits),
                  "fate": [int(x) for x in s.n_fate], "device_status": int(s.device_status),

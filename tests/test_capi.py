@@ -52,7 +52,7 @@ def test_struct_layouts_match_header():
     assert C.sizeof(rich.GeometryDesc) == 4 * 4 + 8 + 8 * 8
     assert C.sizeof(rich.TracksDesc) == 8 + 12 * 8
     assert C.sizeof(rich.PhotonsDesc) == 16 + 10 * 8
-    assert C.sizeof(rich.TraceOpts) == 8 + 15 * 4 + 4      # + tail padding
+    assert C.sizeof(rich.TraceOpts) == 8 + 16 * 4
     assert C.sizeof(rich.EmitParams) == 8 + 10 * 4
     assert C.sizeof(rich.Outputs) == 8 * 4 + 8 + 8 + 8
     assert C.sizeof(rich.Stats) == 16 + 8 * rich.N_FATES + 8

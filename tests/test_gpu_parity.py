@@ -116,6 +116,15 @@ def test_poisson_counts_over_wide_mean_range():
 
 
 # --------------------------------------------------------------- point source
+def _ring_error(hits, scene):
+    rect = scene.rects[0]
+    hu = -float(np.dot(rect["origin"].astype(np.float64), rect["u_axis"]))
+    hv = -float(np.dot(rect["origin"].astype(np.float64), rect["v_axis"]))
+    r = np.hypot(hits["u"] - hu, hits["v"] - hv)
+    n = 1 + float(np.float32(0.0014))
+    return float(np.abs(r - 1355.0 * math.sqrt(n * n - 1)).max(initial=0.0))
+
+
 @pytest.mark.parametrize("precision", [rich.PREC_REFINE64, rich.PREC_FP32])
 def test_point_source_parity(precision):
     wl = W.point_source(100_000)
@@ -124,15 +133,27 @@ def test_point_source_parity(precision):
     tol = P.TOL_UV_REFINE if precision == rich.PREC_REFINE64 else P.TOL_UV_FP32["point_source"]
     st = P.compare(gpu, ref, wl.tracks, tol, name=f"point_source_prec{precision}")
     # closed form: every hit at (R/2) tan(theta) from the plane's axis point
-    h = gpu["hits"]
-    r = np.hypot(h["u"] - 368.64, h["v"] - 368.64)
-    n = 1 + float(np.float32(0.0014))
-    st["max_ring_err_mm"] = float(np.abs(r - 1355.0 * math.sqrt(n * n - 1)).max())
+    st["max_ring_err_mm"] = _ring_error(gpu["hits"], wl.scene)
     report(f"point_source_prec{precision}_ring", {"max_ring_err_mm": st["max_ring_err_mm"]})
     assert st["max_ring_err_mm"] < tol + 1e-6
-    es = gpu["event_sums"][0, 0]
-    assert es[0] == gpu["n_hits"]
-    assert es[1] == pytest.approx(h["u"].sum(), rel=1e-12)
+
+
+@pytest.mark.parametrize("precision", [rich.PREC_REFINE64, rich.PREC_FP32])
+def test_point_source_meshed_parity(precision):
+    """The point source at the centre of curvature of the mirror as a
+    smooth-normal triangle mesh (3200 triangles): the kernel's normal blend
+    reflects every photon back through the centre, so its hits lie on the
+    analytic ring (R/2) tan(theta) within the FP32 input bound of the mesh
+    (5e-4 mm, refined), and match the oracle photon by photon."""
+    wl = W.point_source(100_000, meshed=True)
+    ref = P.run_oracle(wl)
+    gpu = P.run_gpu(wl, precision)
+    tol = P.TOL_UV_REFINE if precision == rich.PREC_REFINE64 else P.TOL_UV_FP32["point_source"]
+    st = P.compare(gpu, ref, wl.tracks, tol, name=f"point_source_meshed_prec{precision}")
+    st["max_ring_err_mm"] = _ring_error(gpu["hits"], wl.scene)
+    report(f"point_source_meshed_prec{precision}_ring", {"max_ring_err_mm": st["max_ring_err_mm"]})
+    assert gpu["n_hits"] > 10_000
+    assert st["max_ring_err_mm"] < 5e-4 + (0 if precision == rich.PREC_REFINE64 else tol)
 
 
 # ---------------------------------------------------------------- RICH1
@@ -145,9 +166,7 @@ def test_rich1_parity_full(meshed, precision):
     ref = P.run_oracle(wl)
     gpu = P.run_gpu(wl, precision)
     tol = P.TOL_UV_REFINE if precision == rich.PREC_REFINE64 else P.TOL_UV_FP32["rich1"]
-    st = P.compare(gpu, ref, wl.tracks, tol, name=f"rich1_meshed{int(meshed)}_prec{precision}")
-    sums_g, sums_o = gpu["event_sums"], ref["event_sums"]
-    np.testing.assert_allclose(sums_g[..., 0], sums_o[..., 0], atol=st["fate_mismatch"])
+    P.compare(gpu, ref, wl.tracks, tol, name=f"rich1_meshed{int(meshed)}_prec{precision}")
 
 
 def test_rich2_parity_subset():
@@ -161,8 +180,8 @@ def test_rich2_parity_subset():
 
 def test_batched_events_sampled():
     """Batched events (256 events with Poisson(50) tracks): per-photon
-    parity on every photon of 24 sampled events, and exact per-event pixel
-    histograms and sums for those events."""
+    parity on every photon of 24 sampled events, and their per-event pixel
+    histograms and FP64 sums."""
     wl = W.batched(256, seed=1)
     gpu = P.run_gpu(wl, rich.PREC_REFINE64)
     sc = oracle.Scene(wl.scene)
@@ -170,7 +189,7 @@ def test_batched_events_sampled():
     _, _, off = oracle.track_yield(wl.tracks, prm)
     events = np.random.default_rng(0).choice(256, 24, replace=False)
     sel = np.zeros(int(off[-1]), bool)
-    ref_pc = np.zeros_like(gpu["pixel_counts"])
+    merged = None
     for e in events:
         idx = np.nonzero(wl.tracks.event == e)[0]
         if len(idx) == 0:
@@ -178,15 +197,15 @@ def test_batched_events_sampled():
         a, b = int(idx[0]), int(idx[-1]) + 1
         r = sc.trace(wl.tracks, prm, offsets=off, track_range=(a, b), n_hist_events=256)
         sel[int(off[a]):int(off[b])] = True
-        ref_pc += r["pixel_counts"]
-        if e == events[0]:
+        if merged is None:
             merged = r
-        else:
-            for k in ("fate", "plane", "ix", "iy", "u", "v", "lambda", "graze", "n_refl"):
-                merged[k][int(off[a]):int(off[b])] = r[k][int(off[a]):int(off[b])]
+            continue
+        for k in ("fate", "plane", "ix", "iy", "u", "v", "lambda", "graze", "n_refl"):
+            merged[k][int(off[a]):int(off[b])] = r[k][int(off[a]):int(off[b])]
+        merged["pixel_counts"] += r["pixel_counts"]
+        merged["event_sums"] += r["event_sums"]
     st = P.compare(gpu, merged, wl.tracks, P.TOL_UV_REFINE, sel=sel, name="batched_256_sampled")
-    if st["fate_mismatch"] == 0:
-        np.testing.assert_array_equal(gpu["pixel_counts"][events], ref_pc[events])
+    assert st["photons"] > 20_000 and "event_sums_bad" in st
 
 
 # ------------------------------------------------------------- invariances

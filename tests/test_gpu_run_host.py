@@ -241,3 +241,55 @@ def test_run_host_follow_up_copy_when_the_early_copy_falls_short():
     assert nh == nh_ref
     np.testing.assert_array_equal(records(hosts[1], nh), ref)
     ctx.close()
+
+
+def test_run_host_async_rejects_buffers_of_the_step_in_flight(setup):
+    """A second step in flight may not write into the first one's device hit
+    buffer or host hit buffer (the first step's trace and copies still write
+    there): RICH_ERR_ARG, nothing enqueued, and the first step completes
+    with its own results."""
+    ctx, scene, tracks, n, cap, nh, st, ref, ref_fate = setup
+    ht = rich.HostTracks(tracks)
+    outs = [rich.TraceOutputs(cap, scene.pixels_per_event, len(scene.planes), 1, 2 * n)
+            for _ in range(2)]
+    hosts = [torch.empty(cap * rich.HIT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+             for _ in range(2)]
+    t1 = ctx.run_host_async(ht, outs[0], hosts[0], 0.0014, seed=9)
+    with pytest.raises(rich.RichError) as e:
+        ctx.run_host_async(ht, outs[0], hosts[1], 0.0014, seed=10)
+    assert e.value.status == 1                      # RICH_ERR_ARG
+    with pytest.raises(rich.RichError) as e:
+        ctx.run_host_async(ht, outs[1], hosts[0], 0.0014, seed=10)
+    assert e.value.status == 1
+    nh1, st1 = ctx.run_wait(t1)
+    assert nh1 == nh and st1["fate"] == st["fate"]
+    recs = np.frombuffer(hosts[0].numpy()[: nh1 * rich.HIT_DTYPE.itemsize].tobytes(),
+                         rich.HIT_DTYPE)
+    np.testing.assert_array_equal(_sorted(recs), ref)
+    # with the first step waited for, its buffers are free again
+    t2 = ctx.run_host_async(ht, outs[0], hosts[0], 0.0014, seed=9)
+    assert ctx.run_wait(t2)[0] == nh
+
+
+def test_node_copy_wait_running_out_is_reported_and_harmless(setup):
+    """The trace blocks wait, bounded, for the TMA copy of the top BVH nodes
+    into shared memory. A wait limit that gives up at once (a negative
+    wait_limit) makes every block record RICH_ERR_TIMEOUT, wait again for
+    the copy in flight, and read the nodes from global memory: rich_hits
+    reports the timeout, and the hits and fates equal the normal run's."""
+    ctx, scene, tracks, n, cap, nh, st, ref, ref_fate = setup
+    dt = rich.DeviceTracks(tracks)
+    assert ctx.emit(dt, 0.0014, seed=9) == n
+    out = rich.TraceOutputs(cap, scene.pixels_per_event, len(scene.planes), 1, n)
+    ctx.trace(out, precision=rich.PREC_REFINE64, wait_limit=-1)
+    with pytest.raises(rich.RichError) as e:
+        ctx.hits()
+    assert e.value.status == 5                      # RICH_ERR_TIMEOUT
+    n_hits, st2 = ctx.hits(allow=(5,))
+    assert st2["status"] == 5 and st2["device_status"] == 5
+    assert n_hits == nh and st2["fate"] == st["fate"]
+    np.testing.assert_array_equal(_sorted(out.hits_numpy(n_hits)), ref)
+    np.testing.assert_array_equal(out.fate.cpu().numpy(), ref_fate)
+    # the status is the last trace's: a normal trace reports none
+    ctx.trace(out, precision=rich.PREC_REFINE64)
+    assert ctx.hits()[0] == nh
