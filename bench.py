@@ -39,20 +39,98 @@ UNIT = "photons/s"
 N_TRACKS = 1000
 WORKLOAD = "rich1_meshed_1000_pion_tracks"
 
-# FP32 operations per propagated photon of the trace kernel on this workload:
-# 2 x FFMA + FADD + FMUL thread instructions of one k_trace launch from the
-# ncu counters (smsp__sass_thread_inst_executed_op_{ffma,fadd,fmul}_pred_on)
-# divided by its 350,350 photons: (2 x 244.19 M + 37.77 M + 87.12 M) / 350,350.
-FLOPS_PER_PHOTON = 1750.4
-# dram__bytes_read.sum + dram__bytes_write.sum of the same k_trace launch.
-TRACE_DRAM_BYTES = 7455744 + 263424
-# Warp instructions per photon of the same launch (smsp__inst_executed.sum
-# 99,229,133 / 350,350): the kernel is bound by instruction issue, so the
-# issue rate against 4 schedulers x SMs x clock is reported beside the FP32
-# fraction.
-WARP_INST_PER_PHOTON = 283.23
-FP32_LANES_PER_SM = 128
-SM_COUNT_NOMINAL = 152
+PROFILE = os.path.join(ROOT, "profiles", "k_trace_rich1_counters.json")
+
+# Algorithmic work of the trace kernel per event, from the formulas the
+# kernel evaluates (not from its compiled instructions): FP32 arithmetic
+# (a fused multiply-add counts 2, an add or multiply 1), FP32 min/max
+# comparisons, and special-function operations (reciprocal, reciprocal
+# square root, sine/cosine). Events are tallied by the counting build of
+# the kernel (rich_trace_work).
+WORK_COST = {
+    # four-wide node: 4 children x 3 axes x 2 slab-plane FMAs; the 4
+    # widened exit distances (1 multiply each); min/max: per child 2 on the
+    # first axis, 4 on each other axis, 2 for the [0, t_best] clamp
+    "node": {"fp32": 4 * 3 * 2 * 2 + 4, "minmax": 4 * (2 + 4 + 4 + 2), "mufu": 0},
+    # watertight triangle test (Woop et al. 2013): 9 subtractions (vertices
+    # relative to the origin), 6 shear FMAs, 3 edge functions (2 products
+    # and a difference each), det (2 adds), scaled distance (3 products,
+    # 2 FMAs), one reciprocal and the distance product
+    "tri": {"fp32": 9 + 6 * 2 + 3 * 3 + 2 + (3 + 2 * 2) + 1, "minmax": 0, "mufu": 1},
+    # per bounce step: ray set-up (3 reciprocals of the direction, the
+    # shear constants: 2 products and a reciprocal), the hit point (3 FMAs)
+    "step": {"fp32": 2 + 3 * 2, "minmax": 0, "mufu": 4},
+    # per rectangle per step: plane distance (two 3-term dots as 1 product +
+    # 2 FMAs each, a 3-vector difference, a division as reciprocal and
+    # product), the in-plane point (3 FMAs) and its two coordinates (dots)
+    "rect": {"fp32": 5 + 5 + 3 + 1 + 3 * 2 + 2 * 5, "minmax": 0, "mufu": 1},
+    # per distinct sphere per step: the double-word quadratic (~40
+    # double-word operations of ~4 FP32 operations) and aperture tests
+    "sphere": {"fp32": 160 + 20, "minmax": 0, "mufu": 2},
+    # triangle shading at a hit: two edges (6), cross product (3 products +
+    # 3 FMAs), front test (dot), normalisation (dot, rsqrt, 3 products)
+    "shade_tri": {"fp32": 6 + 9 + 5 + 8, "minmax": 0, "mufu": 1},
+    # smooth normal: barycentric blend (3 products + 6 FMAs), normalisation
+    "normal": {"fp32": 3 + 12 + 8, "minmax": 0, "mufu": 1},
+    # reflection or refraction: d - 2 (d.n) n (dot, product, 3 FMAs),
+    # renormalisation, reflectivity lookup (subtract, multiply)
+    "turn": {"fp32": 5 + 1 + 6 + 8 + 2, "minmax": 0, "mufu": 1},
+    # per photon: origin (3 FMAs + 1 product), azimuth sine/cosine, frame
+    # (orthonormal basis, ~15), direction (3 products + 6 FMAs, tan theta
+    # FMAs, normalisation), wavelength (1 product, 1 subtract, reciprocal)
+    "photon": {"fp32": 7 + 15 + 9 + 6 + 8 + 2, "minmax": 0, "mufu": 4},
+    # per detected photon: plane coordinates (3 subtractions, 2 dots), QE
+    # lookup, pixel (2 products)
+    "detected": {"fp32": 3 + 10 + 2 + 2, "minmax": 0, "mufu": 0},
+}
+# bytes each tallied event reads or writes outside shared memory
+BYTES = {"node": 128, "tri": 48, "normal": 36, "track": 64, "perm": 4, "hit": 40,
+         "refine_rec": 40}
+
+
+def kernel_source_hash():
+    """Hash of the CUDA sources the trace kernel is compiled from: profile
+    counters taken from another build are not reported as this one's."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2309_12496_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "rich.h"), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def work_per_photon(w):
+    """FP32 operations, min/max operations, special-function operations and
+    bytes (L2 side and shared-memory side) per propagated photon, from the
+    tallies of the counting build and WORK_COST / BYTES."""
+    n = max(1, w["photons"])
+    nodes = w["nodes_smem"] + w["nodes_global"]
+    ev = {"node": nodes, "tri": w["tri_tests"], "step": w["steps"],
+          "rect": w["steps"] * w["rects"], "sphere": w["steps"] * w["sphere_groups"],
+          "shade_tri": w["steps"], "normal": w["smooth_normals"], "turn": w["turns"],
+          "photon": w["photons"], "detected": w["detected"]}
+    per = {k: sum(ev[e] * WORK_COST[e][k] for e in ev) / n for k in ("fp32", "minmax", "mufu")}
+    l2 = (w["nodes_global"] * BYTES["node"] + w["tri_tests"] * BYTES["tri"]
+          + w["smooth_normals"] * BYTES["normal"] + w["tracks"] * BYTES["track"]
+          + w["photons"] * BYTES["perm"]
+          + w["detected"] * (BYTES["hit"] + BYTES["refine_rec"])) / n
+    per["l2_bytes"] = l2
+    per["smem_bytes"] = w["nodes_smem"] * BYTES["node"] / n
+    per["events_per_photon"] = {e: ev[e] / n for e in ev}
+    return per
+
+
+def load_profile():
+    """Counters of one ncu capture of k_trace on this workload (committed
+    under profiles/), with the hash of the sources they were taken from."""
+    try:
+        with open(PROFILE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
 
 
 def parse():
@@ -64,6 +142,8 @@ def parse():
     ap.add_argument("--precision", default="refine64", choices=["refine64", "fp32"])
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched / e2e / cpu-baseline legs")
+    ap.add_argument("--knobs", default=None,
+                    help="trace launch knobs as JSON (skips the autotuner)")
     return ap.parse_args()
 
 
@@ -212,8 +292,13 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
+    # measured denominators of the roofline (microbenchmarks, ~0.5 s)
+    peaks = rich.measure_peaks(local) if rank == 0 else None
     from paper_2309_12496_gb300 import autotune
-    knobs, _, _ = autotune.tune(ctx, out, n0, prec)
+    if args.knobs:
+        knobs = json.loads(args.knobs)
+    else:
+        knobs, _, _ = autotune.tune(ctx, out, n0, prec)
 
     def step(seed):
         ctx.emit(dt, 0.0014, seed=seed, sync=False)
@@ -268,31 +353,8 @@ def main():
 
     line = None
     if rank == 0:
-        # dominant kernel: k_trace, timed by events on its own stream
-        t_trace = statistics.mean(trace_ms) / 1e3
+        roof, kms = roofline(ctx, dt, out, seeds, photons, flush, knobs, prec, peaks, clk)
         ph_step = my_photons / len(seeds)
-        props = torch.cuda.get_device_properties(local)
-        n_sm = props.multi_processor_count
-        sm_max = clk.get("sm_max_mhz") or 2070.0
-        peak_tflops = 2 * FP32_LANES_PER_SM * n_sm * sm_max * 1e6 / 1e12
-        if FLOPS_PER_PHOTON:
-            achieved = FLOPS_PER_PHOTON * ph_step / t_trace / 1e12
-            issue_peak = 4 * n_sm * sm_max * 1e6
-            issue = WARP_INST_PER_PHOTON * ph_step / t_trace
-            roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
-                    "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                    "traffic": TRACE_DRAM_BYTES,
-                    "kernel": "k_trace", "flops_per_photon": FLOPS_PER_PHOTON,
-                    "peak_source": f"FP32 2 x {FP32_LANES_PER_SM} lanes x {n_sm} SMs x {sm_max:.0f} MHz",
-                    "timed": "k_trace + k_refine (one rich_trace call; k_trace is ~87 % of it)",
-                    "issue": {"warp_inst_per_photon": WARP_INST_PER_PHOTON,
-                              "achieved": issue, "peak": issue_peak, "unit": "warp inst/s",
-                              "frac": issue / issue_peak,
-                              "peak_source": f"4 schedulers x {n_sm} SMs x {sm_max:.0f} MHz"}}
-        else:
-            roof = {"bound": "alu", "achieved": None, "peak": peak_tflops, "unit": "TFLOP/s",
-                    "frac": None, "traffic": None, "kernel": "k_trace",
-                    "kernel_ms": t_trace * 1e3}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup,
@@ -306,7 +368,7 @@ def main():
                        "launch": knobs,
                        "l2": "flushed before every timed step (256 MiB write)"},
             "kernel_ms": {"emit": statistics.mean([a.elapsed_time(b) for a, b, _ in ev]),
-                          "trace": t_trace * 1e3},
+                          "trace_and_refine": statistics.mean(trace_ms), **kms},
             "hits_per_step": n_hits_last,
             # k_yield, k_order (with the count scan), k_trace (+ k_refine)
             "gpu_launches": (4 if prec == rich.PREC_REFINE64 else 3) * args.steps,
@@ -317,6 +379,7 @@ def main():
         e2e = run_e2e(ctx, tracks, dev, prec, args, scene, knobs)
         if line is not None:
             line["e2e"] = e2e
+            line["point_source"] = run_point_source(dev, prec, rank, args)
             line["batched"] = run_batched(dev, prec, rank)
             line["adjoint"] = run_adjoint(dev, rank)
             line["rich2_chunked"] = run_chunked(dev, rank)
@@ -338,6 +401,92 @@ def main():
         pg.destroy_process_group()
 
 
+def roofline(ctx, dt, out, seeds, photons, flush, knobs, prec, peaks, clk):
+    """Roofline of the dominant kernel, k_trace, on the benchmark workload.
+
+    Its own duration comes from the library's kernel timing (events around
+    k_trace on the context's stream) over the same seeds as the timed steps,
+    L2 flushed before each. Its work per photon comes from the counting
+    build (rich_trace_work) on the first seed: FP32 operations and bytes
+    outside shared memory (WORK_COST, BYTES). The two bounds are those of
+    the scope: FP32 work over the measured FP32 FMA rate, and bytes over the
+    measured L2 read bandwidth; `bound` is the slower, and `frac` the
+    kernel's achieved rate over that bound's peak. Beside them: the min/max
+    (ALU) and special-function rates against their measured peaks, and,
+    from the committed ncu capture when it was taken from these sources,
+    warp instructions and DRAM / L2 bytes per photon."""
+    import torch
+    from paper_2309_12496_gb300 import rich
+    stream = torch.cuda.current_stream()
+    ctx.set_timing(True)
+    per = {"yield": [], "order": [], "trace": [], "refine": []}
+    for s in seeds:
+        flush.zero_()
+        out.clear()
+        ctx.emit(dt, 0.0014, seed=s, sync=False)
+        ctx.trace(out, precision=prec, **knobs)
+        for k, v in ctx.kernel_times().items():
+            per[k].append(v)
+    ctx.set_timing(False)
+    kms = {k: statistics.mean(v) for k, v in per.items()}
+    t_trace = kms["trace"] / 1e3
+    ph_step = float(sum(photons)) / len(photons)
+    # algorithmic work per photon (counting build, same launch shape when it
+    # has one)
+    wk = dict(knobs)
+    if wk.get("block_threads", 1024) <= 256:
+        wk.update(block_threads=768, wide_regs=1)
+    ctx.emit(dt, 0.0014, seed=seeds[0], sync=True)
+    out.clear()
+    tally = ctx.trace_work(out, **{k: v for k, v in wk.items()})
+    torch.cuda.synchronize()
+    w = work_per_photon(tally)
+    rate = ph_step / t_trace                              # photons/s in k_trace
+    fp32 = {"per_photon": w["fp32"], "achieved": w["fp32"] * rate / 1e12,
+            "peak": peaks["fp32_fma_flops"] / 1e12, "unit": "TFLOP/s"}
+    l2 = {"per_photon": w["l2_bytes"], "achieved": w["l2_bytes"] * rate / 1e9,
+          "peak": peaks["l2_read_bytes"] / 1e9, "unit": "GB/s"}
+    alu = {"per_photon": w["minmax"], "achieved": w["minmax"] * rate / 1e12,
+           "peak": peaks["fp32_minmax_ops"] / 1e12, "unit": "Tops/s"}
+    xu = {"per_photon": w["mufu"], "achieved": w["mufu"] * rate / 1e12,
+          "peak": peaks["mufu_ops"] / 1e12, "unit": "Tops/s"}
+    for b in (fp32, l2, alu, xu):
+        b["frac"] = b["achieved"] / b["peak"]
+        b["photons_per_s_bound"] = rate / b["frac"]
+    bound = "l2" if l2["frac"] >= fp32["frac"] else "fp32"
+    main = l2 if bound == "l2" else fp32
+    prof = load_profile()
+    src = kernel_source_hash()
+    fresh = prof is not None and prof.get("sources") == src
+    traffic = prof["dram_bytes_per_launch"] if fresh else None
+    issue = None
+    if fresh:
+        n_sm = peaks["n_sm"]
+        f = (clk.get("sm_mhz") or peaks["sm_clock_mhz_max"]) * 1e6
+        wi = prof["warp_inst_per_photon"]
+        issue = {"warp_inst_per_photon": wi, "achieved": wi * rate,
+                 "peak": 4 * n_sm * f, "unit": "warp inst/s",
+                 "frac": wi * rate / (4 * n_sm * f),
+                 "peak_source": f"4 schedulers x {n_sm} SMs x median SM clock"}
+    roof = {"bound": bound, "achieved": main["achieved"], "peak": main["peak"],
+            "unit": main["unit"], "frac": main["frac"], "traffic": traffic,
+            "kernel": "k_trace", "kernel_ms": kms["trace"],
+            "timed": "k_trace alone: library kernel timing (CUDA events on the context "
+                     "stream) over the timed seeds, L2 flushed before each",
+            "peak_source": "measured by rich_measure_peaks in this run (of measured)",
+            "bounds": {"fp32": fp32, "l2": l2, "alu_minmax": alu, "mufu": xu},
+            "smem_bytes_per_photon": w["smem_bytes"],
+            "events_per_photon": w["events_per_photon"],
+            "work_tally": tally, "peaks": peaks, "issue": issue,
+            "profile": {"file": os.path.relpath(PROFILE, ROOT), "sources": src,
+                        "fresh": fresh,
+                        "dram_bytes_per_photon": (prof["dram_bytes_per_launch"]
+                                                  / prof["photons"]) if fresh else None,
+                        "l2_bytes_per_photon": (prof["lts_bytes_per_launch"]
+                                                / prof["photons"]) if fresh else None}}
+    return roof, kms
+
+
 def _time_steps(fn, n_steps, warmup, flush):
     import torch
     st = torch.cuda.current_stream()
@@ -354,6 +503,33 @@ def _time_steps(fn, n_steps, warmup, flush):
         b.synchronize()
         ms.append(a.elapsed_time(b))
     return statistics.median(ms)
+
+
+def run_point_source(dev, prec, rank, args):
+    """The plain form on the point-source configuration: 10^5 photons from
+    the centre of curvature of the R = 2710 mm analytic mirror (n = 1.0014,
+    beta = 1), emit + trace per step through the C ABI, the same timing
+    protocol as the headline (L2 flushed before each step, CUDA events)."""
+    import torch
+    from paper_2309_12496_gb300 import rich
+    from paper_2309_12496_gb300 import workloads as W
+    wl = W.point_source(100_000)
+    ctx = rich.Context(int(dev.split(":")[1]))
+    ctx.init_geometry(wl.scene)
+    dt = rich.DeviceTracks(wl.tracks, device=dev)
+    n = ctx.emit(dt, wl.n_minus_1, seed=rank)
+    out = rich.TraceOutputs(n, wl.scene.pixels_per_event, 1, 1, 0, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def step():
+        out.clear()
+        ctx.emit(dt, wl.n_minus_1, seed=rank, sync=False)
+        ctx.trace(out, precision=prec)
+    ms = _time_steps(step, max(20, args.steps), max(3, args.warmup), flush)
+    n_hits, _ = ctx.hits()
+    ctx.close()
+    return {"value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "photons_per_step": n,
+            "hits_per_step": n_hits, "workload": wl.description}
 
 
 def run_batched(dev, prec, rank, n_events=4096):
@@ -374,7 +550,7 @@ def run_batched(dev, prec, rank, n_events=4096):
     # one emit + one persistent trace launch (+ refinement) captured as a
     # CUDA graph, replayed per step
     ctx.graph_capture(dt, out, wl.n_minus_1, seed=wl.seed, precision=prec)
-    ms = _time_steps(ctx.graph_launch, 3, 2, flush)
+    ms = _time_steps(ctx.graph_launch, 10, 3, flush)
     n_hits, _ = ctx.hits()
     ctx.close()
     return {"value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "photons_per_step": n,
@@ -519,16 +695,19 @@ def run_adjoint(dev, rank):
     th[:8] = [2e-3, -1e-3, 0.5e-3, 1.5e-3, -2e-3, 1e-3, 0.0, -0.7e-3]
     out = rich.TraceOutputs(n, 0, 0, 0, 0, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
-    t_fwd = _time_steps(lambda: ctx.trace(out, precision=rich.PREC_REFINE64), 5, 2, flush)
+    t_fwd = _time_steps(lambda: ctx.trace(out, precision=rich.PREC_REFINE64), 10, 3, flush)
     res = {}
 
     def step():
         res["r"] = ctx.trace_grad(dt, th, tg_dev, out, sigma=1.0, seed=wl.seed)
-    ms = _time_steps(step, 5, 2, flush)
+    ms = _time_steps(step, 10, 3, flush)
     ctx.close()
     return {"value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "photons_per_step": n,
             "forward_only_ms": t_fwd, "hits_used": res["r"][2], "loss": res["r"][0],
-            "note": "emit + forward trace + adjoint replay + FP64 reductions; synchronous"}
+            "note": "emit + forward trace + adjoint replay + FP64 reductions; synchronous. "
+                    "Analytic RICH1 geometry (the gradient's tilts act on analytic tiles); "
+                    "forward_only_ms is the forward trace on the same scene and photons, "
+                    "the fair comparison with the forward + adjoint step"}
 
 
 def run_e2e(ctx, tracks, dev, prec, args, scene, knobs):

@@ -450,6 +450,59 @@ RICH_API rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
  * error recorded during the trace. */
 RICH_API rich_status rich_hits(rich_ctx *ctx, uint64_t *n_hits, rich_stats *stats);
 
+/* ------------------------------------------------------- measurement aids */
+/* Kernel timing (the profiling aid of the stage timers the paper used,
+ * Sec. 5.1). When on, rich_emit and rich_trace record CUDA events on the
+ * context's stream around each of their kernels, and rich_kernel_times
+ * reports the durations of the last such calls. Recording an event between
+ * two kernels ends the overlap of their programmatic launch, so the kernels'
+ * sum can exceed the untimed step by a few microseconds. Calls inside a
+ * graph capture are not timed. Off by default. */
+typedef struct rich_kernel_ms {
+    float yield;    /* per-track yield and Poisson count (and the count scan
+                       pass when the emission synchronises)               */
+    float order;    /* the ordering pass (with the count scan otherwise)  */
+    float trace;    /* the persistent trace kernel                          */
+    float refine;   /* the refinement pass; -1 without refinement          */
+} rich_kernel_ms;
+
+RICH_API rich_status rich_set_timing(rich_ctx *ctx, int on);
+
+/* Durations (ms, host out) of the kernels of the last timed rich_emit and
+ * rich_trace; -1 for a kernel that was not timed. Waits for those events. */
+RICH_API rich_status rich_kernel_times(rich_ctx *ctx, rich_kernel_ms *out);
+
+/* Algorithmic work of one trace, counted by the counting build of the trace
+ * kernel (the same traversal with per-thread tallies). From these tallies
+ * and the sizes of the records the traversal reads (128-byte four-wide BVH
+ * nodes, 48-byte triangles, 36-byte vertex normals) follow the FP32
+ * operations and the bytes per photon that bound the kernel. */
+typedef struct rich_work {
+    uint64_t photons;         /* photons that entered the trace            */
+    uint64_t steps;           /* nearest-surface queries (bounce steps)    */
+    uint64_t nodes_smem;      /* four-wide node tests on nodes staged in
+                                 shared memory                             */
+    uint64_t nodes_global;    /* node tests on nodes read from global memory */
+    uint64_t tri_tests;       /* ray-triangle tests                         */
+    uint64_t smooth_normals;  /* vertex-normal blends at smooth-triangle hits */
+    uint64_t turns;           /* reflections and refractions               */
+    uint64_t detected;        /* hits                                       */
+    uint64_t tracks;          /* tracks of the emission                     */
+    int32_t sphere_groups;    /* distinct spheres tested at every step      */
+    int32_t rects;            /* rectangles tested at every step            */
+} rich_work;
+
+/* rich_trace of the last emission (fused photons; precision
+ * RICH_PREC_REFINE64; more than 256 block_threads -- the 80- and 64-register
+ * shapes, which have a counting build) through the counting build, then
+ * the counters (as rich_hits) and the tallies into *work (host).
+ * Synchronous; slower than rich_trace (for measurement only). Results
+ * (hits, fates, histograms) are those of rich_trace. RICH_ERR_ARG for
+ * another form; statuses of rich_hits otherwise (RICH_ERR_OVERFLOW still
+ * fills *work). */
+RICH_API rich_status rich_trace_work(rich_ctx *ctx, const rich_trace_opts *opts,
+                                     const rich_outputs *out, rich_work *work);
+
 /* One step from host memory: the track arrays (HOST pointers; pinned memory
  * makes the copies asynchronous, and arrays that lie back to back in one
  * allocation are copied as one block) are copied into device scratch owned

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librich.so")
 
-SOURCES = ["rich_kernels.cu", "rich_capi.cu", "rich_static.cu", "rich_bvh.cpp"]
+SOURCES = ["rich_kernels.cu", "rich_capi.cu", "rich_static.cu", "rich_peaks.cu", "rich_bvh.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -35,7 +35,7 @@ def nvcc_path() -> str:
 
 def _headers():
     hs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
-    return hs + [os.path.join(INCLUDE, "rich.h")]
+    return hs + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
 
 
 def _flags(extra=()):

@@ -86,6 +86,14 @@ struct rich_ctx {
     int cur_slot = 0;
     bool slot_zeroed[2] = {true, true};
     bool capturing = false;                // inside rich_graph_capture
+    // kernel timing (rich_set_timing): events around the kernels of the
+    // last rich_emit (0 yield, 1 ordering, 2 end) and rich_trace (3 trace,
+    // 4 refinement, 5 end); recorded[k]: event k belongs to the last call
+    bool timing = false;
+    cudaEvent_t tev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool tev_emit = false, tev_trace = false, tev_refine = false;
+    // counting build of the trace (rich_trace_work): 6 device tallies
+    unsigned long long *d_work = nullptr;
     int graph_slot = 0;
     Counters *h_ctr = nullptr;            // pinned
     unsigned long long *h_total = nullptr; // pinned
@@ -527,6 +535,9 @@ RICH_API rich_status rich_destroy(rich_ctx *ctx) {
         if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
         cudaFree(ctx->d_acc);
         cudaFreeHost(ctx->h_acc);
+        cudaFree(ctx->d_work);
+        for (cudaEvent_t &e : ctx->tev)
+            if (e) cudaEventDestroy(e);
         free_emission(ctx);
         cudaFree(ctx->d_perm);
         cudaFree(ctx->d_perm_ok);
@@ -810,6 +821,8 @@ RICH_API rich_status rich_emit(rich_ctx *ctx, const rich_tracks *t,
                         "rich_emit: dispersion needs disp_a > 0 and 0 < disp_lambda0 < lambda_min");
     }
     DeviceGuard guard(ctx->device);
+    const bool timed = ctx->timing && !ctx->capturing;
+    if (timed) RICH_CUDA(cudaEventRecord(ctx->tev[0], ctx->stream));
     {
         const rich_status st = emit_core(ctx, t, prm->seed, prm->n_minus_1, prm->lambda_min,
                                          prm->lambda_max, prm->source, prm->yield_per_mm,
@@ -825,9 +838,14 @@ RICH_API rich_status rich_emit(rich_ctx *ctx, const rich_tracks *t,
         ctx->known_total = std::max<uint64_t>(ctx->known_total, *ctx->h_total);
         if (n_photons) *n_photons = *ctx->h_total;
     }
+    if (timed) RICH_CUDA(cudaEventRecord(ctx->tev[1], ctx->stream));
     {
         const rich_status st = order_photons(ctx);
         if (st != RICH_OK) return st;
+    }
+    if (timed) {
+        RICH_CUDA(cudaEventRecord(ctx->tev[2], ctx->stream));
+        ctx->tev_emit = true;
     }
     if (out) {
         const uint64_t total = *ctx->h_total;
@@ -874,8 +892,10 @@ static int32_t trace_wait_limit(int32_t opt) {
     return opt == 0 ? (1 << 20) : (opt < 0 ? 0 : opt);
 }
 
-RICH_API rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
-                                const rich_trace_opts *o, const rich_outputs *out) {
+// rich_trace, and its counting build for rich_trace_work (work: the device
+// tallies, fused emission with refinement only).
+static rich_status trace_impl(rich_ctx *ctx, const rich_photons *in, const rich_trace_opts *o,
+                              const rich_outputs *out, unsigned long long *work) {
     if (!ctx) return RICH_ERR_ARG;
     if (!o || !out) return fail(ctx, RICH_ERR_ARG, "rich_trace: opts or outputs is NULL");
     if (!ctx->has_geometry) return fail(ctx, RICH_ERR_STATE, "rich_trace: no geometry");
@@ -970,30 +990,117 @@ RICH_API rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
         if (!bps || bps > it->second) bps = it->second;
     }
     shape.blocks = std::max(1, bps) * ctx->n_sm;
+    if (work) {
+        if (in || !refine || !trace_count_shape_ok(cls))
+            return fail(ctx, RICH_ERR_ARG,
+                        "rich_trace_work: counts the fused-emission trace with refinement in "
+                        "the 768- or 1024-thread shape");
+        p.work = work;
+    }
     EmitView em = emit_view(ctx);
+    const bool timed = ctx->timing && !ctx->capturing;
+    ctx->tev_trace = ctx->tev_refine = false;
     if (in) {
         em.key0 = (uint32_t)o->seed;
         em.key1 = (uint32_t)(o->seed >> 32);
         ExtView ev{in->n, in->x, in->y, in->z, in->dx, in->dy, in->dz, in->lambda,
                    in->event, in->track, in->photon};
         if (in->n) {
+            if (timed) RICH_CUDA(cudaEventRecord(ctx->tev[3], ctx->stream));
             RICH_CUDA(launch_trace(ctx->sc, &em, &ev, p, ctr, ctr_next, shape, ctx->stream));
+            if (timed) RICH_CUDA(cudaEventRecord(ctx->tev[4], ctx->stream));
             if (refine)
                 RICH_CUDA(launch_refine(ctx->sc, &em, &ev, p, ctr, ctx->n_sm, ctx->stream));
+            if (timed) RICH_CUDA(cudaEventRecord(ctx->tev[5], ctx->stream));
+            ctx->tev_trace = timed;
+            ctx->tev_refine = timed && refine;
         } else {
             ctr_next = nullptr;          // no trace kernel: nothing zeroed
         }
         ctx->last_ext = true;
         ctx->last_ext_n = in->n;
     } else {
-        RICH_CUDA(launch_trace(ctx->sc, &em, nullptr, p, ctr, ctr_next, shape, ctx->stream));
+        if (timed) RICH_CUDA(cudaEventRecord(ctx->tev[3], ctx->stream));
+        if (work)
+            RICH_CUDA(launch_trace_count(ctx->sc, em, p, ctr, ctr_next, shape, ctx->stream));
+        else
+            RICH_CUDA(launch_trace(ctx->sc, &em, nullptr, p, ctr, ctr_next, shape, ctx->stream));
+        if (timed) RICH_CUDA(cudaEventRecord(ctx->tev[4], ctx->stream));
         if (refine)
             RICH_CUDA(launch_refine(ctx->sc, &em, nullptr, p, ctr, ctx->n_sm, ctx->stream));
+        if (timed) RICH_CUDA(cudaEventRecord(ctx->tev[5], ctx->stream));
+        ctx->tev_trace = timed;
+        ctx->tev_refine = timed && refine;
         ctx->last_ext = false;
     }
     trace_counters_done(ctx, ctr_next != nullptr);
     ctx->traced = true;
     ctx->last_capacity = p.hit_capacity;
+    return RICH_OK;
+}
+
+RICH_API rich_status rich_trace(rich_ctx *ctx, const rich_photons *in,
+                                const rich_trace_opts *o, const rich_outputs *out) {
+    return trace_impl(ctx, in, o, out, nullptr);
+}
+
+RICH_API rich_status rich_trace_work(rich_ctx *ctx, const rich_trace_opts *o,
+                                     const rich_outputs *out, rich_work *work) {
+    if (!ctx) return RICH_ERR_ARG;
+    if (!work) return fail(ctx, RICH_ERR_ARG, "rich_trace_work: work is NULL");
+    if (ctx->capturing) return fail(ctx, RICH_ERR_STATE, "rich_trace_work: inside a capture");
+    DeviceGuard guard(ctx->device);
+    if (!ctx->d_work) RICH_CUDA(cudaMalloc(&ctx->d_work, sizeof(unsigned long long) * 6));
+    RICH_CUDA(cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned long long) * 6, ctx->stream));
+    const rich_status st = trace_impl(ctx, nullptr, o, out, ctx->d_work);
+    if (st != RICH_OK) return st;
+    unsigned long long w[6];
+    RICH_CUDA(cudaMemcpyAsync(w, ctx->d_work, sizeof w, cudaMemcpyDeviceToHost, ctx->stream));
+    uint64_t n_hits = 0;
+    rich_stats stats;
+    const rich_status hs = rich_hits(ctx, &n_hits, &stats);
+    if (hs != RICH_OK && hs != RICH_ERR_OVERFLOW) return hs;
+    std::memset(work, 0, sizeof *work);
+    work->photons = stats.n_photons - stats.n_fate[RICH_FATE_PREFILTERED];
+    work->steps = w[0];
+    work->nodes_smem = w[1];
+    work->nodes_global = w[2];
+    work->tri_tests = w[3];
+    work->smooth_normals = w[4];
+    work->turns = w[5];
+    work->detected = n_hits;
+    work->tracks = (uint64_t)ctx->n_tracks;
+    work->sphere_groups = ctx->sc.n_groups;
+    work->rects = ctx->sc.n_rects;
+    return hs;
+}
+
+RICH_API rich_status rich_set_timing(rich_ctx *ctx, int on) {
+    if (!ctx) return RICH_ERR_ARG;
+    DeviceGuard guard(ctx->device);
+    if (on && !ctx->tev[0])
+        for (cudaEvent_t &e : ctx->tev) RICH_CUDA(cudaEventCreate(&e));
+    ctx->timing = on != 0;
+    ctx->tev_emit = ctx->tev_trace = ctx->tev_refine = false;
+    return RICH_OK;
+}
+
+RICH_API rich_status rich_kernel_times(rich_ctx *ctx, rich_kernel_ms *out) {
+    if (!ctx) return RICH_ERR_ARG;
+    if (!out) return fail(ctx, RICH_ERR_ARG, "rich_kernel_times: out is NULL");
+    DeviceGuard guard(ctx->device);
+    out->yield = out->order = out->trace = out->refine = -1.f;
+    if (ctx->tev_emit) {
+        RICH_CUDA(cudaEventSynchronize(ctx->tev[2]));
+        RICH_CUDA(cudaEventElapsedTime(&out->yield, ctx->tev[0], ctx->tev[1]));
+        RICH_CUDA(cudaEventElapsedTime(&out->order, ctx->tev[1], ctx->tev[2]));
+    }
+    if (ctx->tev_trace) {
+        RICH_CUDA(cudaEventSynchronize(ctx->tev[5]));
+        RICH_CUDA(cudaEventElapsedTime(&out->trace, ctx->tev[3], ctx->tev[4]));
+        if (ctx->tev_refine)
+            RICH_CUDA(cudaEventElapsedTime(&out->refine, ctx->tev[4], ctx->tev[5]));
+    }
     return RICH_OK;
 }
 

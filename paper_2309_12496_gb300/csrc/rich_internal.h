@@ -204,6 +204,7 @@ struct TraceParams {
     int32_t n_prefilter;      // > 0: efficiencies applied before propagation
     int32_t prefilter_tables[4];
     int32_t wait_limit;       // iterations of the bounded wait for the node copy
+    unsigned long long *work; // counting build only: 6 tallies (WorkTally order)
 };
 
 // Sphere tile i at the gradient's parameters: centre C = P - R a(alpha_i,
@@ -276,6 +277,12 @@ cudaError_t launch_trace(const SceneView &sc, const EmitView *em,
                          const ExtView *ext, const TraceParams &p,
                          Counters *counters, Counters *next, const LaunchShape &shape,
                          cudaStream_t s);
+// The counting build of the trace (fused emission, refinement records; the
+// 768- and 1024-thread shape classes only): p.work receives 6 tallies.
+bool trace_count_shape_ok(int cls);
+cudaError_t launch_trace_count(const SceneView &sc, const EmitView &em, const TraceParams &p,
+                               Counters *counters, Counters *next, const LaunchShape &shape,
+                               cudaStream_t s);
 cudaError_t launch_refine(const SceneView &sc, const EmitView *em,
                           const ExtView *ext, const TraceParams &p,
                           Counters *counters, int n_sm, cudaStream_t s);

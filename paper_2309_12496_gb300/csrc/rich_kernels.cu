@@ -1018,13 +1018,27 @@ __device__ __forceinline__ bool slab(const Ray &r, float lx, float ly, float lz,
     return tn <= tf * 1.00000095f;
 }
 
+// Per-thread tallies of the counting build of the trace (COUNT = true): the
+// algorithmic events of the traversal, summed into TraceParams::work at the
+// end of the kernel. The production build compiles none of it.
+struct WorkTally {
+    uint32_t steps;          // nearest-surface queries
+    uint32_t nodes_smem;     // four-wide node tests on nodes in shared memory
+    uint32_t nodes_global;   // ... on nodes read from global memory
+    uint32_t tris;           // ray-triangle tests
+    uint32_t normals;        // vertex-normal blends at smooth triangle hits
+    uint32_t turns;          // reflections and refractions
+};
+
+template <bool COUNT>
 __device__ __forceinline__ void leaf_tris(const SceneView &sc, const Ray &r,
                                           int code, int skip, float t_min,
-                                          Best &b) {
+                                          Best &b, WorkTally *w) {
     const int first = code >> 3, count = (code & 7) + 1;
     for (int k = first; k < first + count; ++k) {
         const DevTri T = load_tri(sc.tris + k);
         if (T.prim == skip) continue;
+        if constexpr (COUNT) w->tris += 1;
         float t, b0, b1, b2;
         if (!watertight(r, T, t_min, b.t, t, b0, b1, b2)) continue;
         if (t == b.t && T.prim > b.prim) continue;
@@ -1107,9 +1121,10 @@ constexpr int kNoSurf = 0x7FFFFFFF;   // no surface subtree to skip
 // on the same kind of work. The top levels of the tree are read from shared
 // memory. The subtree `skip_ref` (the surface the photon just left) is never
 // entered.
+template <bool COUNT>
 __device__ void nearest_bvh(const SceneView &sc, const DevNode *snodes, int n_snodes,
                             f3 o, f3 d, int skip, int skip_ref, float t_min, Best &b,
-                            Counters *ctr) {
+                            Counters *ctr, WorkTally *w) {
     constexpr int kEmpty = INT_MIN;
     const float kInf = __int_as_float(0x7f800000);
     if (skip_ref == 0) return;            // the whole tree is that surface
@@ -1138,6 +1153,9 @@ __device__ void nearest_bvh(const SceneView &sc, const DevNode *snodes, int n_sn
             float4 key;
             int4 ch;
             node4_test(r, ref < n_snodes ? snodes + ref : sc.nodes + ref, b.t, key, ch);
+            if constexpr (COUNT) {
+                if (ref < n_snodes) w->nodes_smem += 1; else w->nodes_global += 1;
+            }
             float k0 = ch.x != skip_ref ? key.x : kInf, k1 = ch.y != skip_ref ? key.y : kInf;
             float k2 = ch.z != skip_ref ? key.z : kInf, k3 = ch.w != skip_ref ? key.w : kInf;
             int c0 = ch.x, c1 = ch.y, c2 = ch.z, c3 = ch.w;
@@ -1163,7 +1181,7 @@ __device__ void nearest_bvh(const SceneView &sc, const DevNode *snodes, int n_sn
             if (!__any_sync(__activemask(), leaf == kEmpty)) break;
         }
         while (leaf != kEmpty) {
-            leaf_tris(sc, r, ~leaf, skip, t_min, b);
+            leaf_tris<COUNT>(sc, r, ~leaf, skip, t_min, b, w);
             leaf = kEmpty;
             if (ref < 0 && ref != kEmpty) {
                 leaf = ref;
@@ -1489,7 +1507,7 @@ __device__ __forceinline__ uint32_t refl_word(const Photon &ph, int k,
     return k == 0 ? w.x : (k == 1 ? w.y : (k == 2 ? w.z : w.w));
 }
 
-template <bool EXT, bool REFINE, int THREADS, int MINB>
+template <bool EXT, bool REFINE, int THREADS, int MINB, bool COUNT = false>
 __global__ void __launch_bounds__(THREADS, MINB)
 k_trace(TraceArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -1614,6 +1632,7 @@ k_trace(TraceArgs A) {
     Photon ph;
     bool alive = false;
     int path[RICH_MAX_BOUNCES];
+    WorkTally tally{};
     uint64_t pool_next = 0, pool_end = 0;   // warp-uniform
     int64_t pool_track = 0;                 // warp-uniform
     bool more = true;                       // warp-uniform
@@ -1734,11 +1753,12 @@ k_trace(TraceArgs A) {
             b.kind = -1;
             b.idx = -1;
             b.b0 = b.b1 = b.b2 = 0.0f;
+            if constexpr (COUNT) tally.steps += 1;
             if (S.n_groups) nearest_tiles(S, ph.o, ph.d, ph.skip, P.t_min, b);
             nearest_rects(S, ph.o, ph.d, ph.skip, P.t_min, b);
             if (has_tri)
-                nearest_bvh(sc, snodes, n_snodes, ph.o, ph.d, ph.skip, ph.skip_ref, P.t_min, b,
-                            A.ctr);
+                nearest_bvh<COUNT>(sc, snodes, n_snodes, ph.o, ph.d, ph.skip, ph.skip_ref,
+                                   P.t_min, b, A.ctr, COUNT ? &tally : nullptr);
             if (b.prim < 0) {
                 fate = RICH_FATE_ESCAPED;
             } else {
@@ -1776,6 +1796,7 @@ k_trace(TraceArgs A) {
                         const f3 n1 = mk3(__ldg(N3 + 3), __ldg(N3 + 4), __ldg(N3 + 5));
                         const f3 n2 = mk3(__ldg(N3 + 6), __ldg(N3 + 7), __ldg(N3 + 8));
                         n_sh = normalize3(fma3(n0, b.b0, fma3(n1, b.b1, n2 * b.b2)));
+                        if constexpr (COUNT) tally.normals += 1;
                     } else {
                         n_sh = n_geo;
                     }
@@ -1798,6 +1819,7 @@ k_trace(TraceArgs A) {
                             fate = RICH_FATE_MIRROR_ABSORBED;
                         } else {
                             ph.d = normalize3(reflect_f(ph.d, n_sh));
+                            if constexpr (COUNT) tally.turns += 1;
                             if (REFINE) path[ph.n_turn] = b.kind == 2 ? sc.tri_prim_base + b.idx : b.prim;
                             ph.n_refl += 1;
                             ph.n_turn += 1;
@@ -1820,6 +1842,7 @@ k_trace(TraceArgs A) {
                         const float k = 1.0f - eta * eta * (1.0f - c1 * c1);
                         ph.d = k < 0.0f ? normalize3(reflect_f(ph.d, N))
                                         : normalize3(fma3(N, eta * c1 - sqrtf(k), ph.d * eta));
+                        if constexpr (COUNT) tally.turns += 1;
                         if (REFINE) path[ph.n_turn] = b.kind == 2 ? sc.tri_prim_base + b.idx : b.prim;
                         ph.n_turn += 1;
                         ph.o = p;
@@ -1910,6 +1933,14 @@ k_trace(TraceArgs A) {
             atomicAdd(&s_fate[fate], 1ull);
             alive = false;
         }
+    }
+    if constexpr (COUNT) {
+        atomicAdd(P.work + 0, (unsigned long long)tally.steps);
+        atomicAdd(P.work + 1, (unsigned long long)tally.nodes_smem);
+        atomicAdd(P.work + 2, (unsigned long long)tally.nodes_global);
+        atomicAdd(P.work + 3, (unsigned long long)tally.tris);
+        atomicAdd(P.work + 4, (unsigned long long)tally.normals);
+        atomicAdd(P.work + 5, (unsigned long long)tally.turns);
     }
     __syncthreads();
     if (threadIdx.x < RICH_N_FATES && s_fate[threadIdx.x])
@@ -2397,10 +2428,10 @@ size_t trace_smem_bytes(const SceneView &sc, int smem_nodes) {
            r16(sizeof(DevMaterial) * sc.n_materials);
 }
 
-template <bool EXT, bool REFINE, int THREADS, int MINB>
+template <bool EXT, bool REFINE, int THREADS, int MINB, bool COUNT = false>
 static cudaError_t launch_trace_t(const TraceArgs &a, const LaunchShape &shape,
                                   cudaStream_t s) {
-    auto kern = k_trace<EXT, REFINE, THREADS, MINB>;
+    auto kern = k_trace<EXT, REFINE, THREADS, MINB, COUNT>;
     // raise the dynamic shared-memory limit once per variant and size (the
     // attribute persists; a captured replay then issues no such call)
     static size_t raised = 48 * 1024;
@@ -2474,6 +2505,26 @@ cudaError_t launch_trace(const SceneView &sc, const EmitView *em,
     const bool refine = p.precision == RICH_PREC_REFINE64;
     if (ext) return refine ? launch_cls<true, true>(a, shape, s) : launch_cls<true, false>(a, shape, s);
     return refine ? launch_cls<false, true>(a, shape, s) : launch_cls<false, false>(a, shape, s);
+}
+
+// The counting build of the fused-emission trace with refinement records
+// (the benchmark's form) in the 768- and 1024-thread shapes: the same
+// traversal, plus per-thread tallies of its work summed into p.work.
+bool trace_count_shape_ok(int cls) { return cls == kShape768 || cls == kShape1024; }
+
+cudaError_t launch_trace_count(const SceneView &sc, const EmitView &em, const TraceParams &p,
+                               Counters *counters, Counters *next, const LaunchShape &shape,
+                               cudaStream_t s) {
+    TraceArgs a;
+    a.sc = sc;
+    a.em = em;
+    a.ext = ExtView{};
+    a.p = p;
+    a.ctr = counters;
+    a.ctr_next = next;
+    if (shape.cls == kShape768) return launch_trace_t<false, true, 768, 1, true>(a, shape, s);
+    if (shape.cls == kShape1024) return launch_trace_t<false, true, 1024, 1, true>(a, shape, s);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace rich

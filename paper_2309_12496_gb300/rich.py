@@ -33,7 +33,9 @@ EXPORTED = ["rich_create", "rich_destroy", "rich_set_stream", "rich_init_geometr
             "rich_emit", "rich_trace", "rich_hits", "rich_philox", "rich_last_error",
             "rich_version", "rich_photon_counts_static", "rich_trace_grad",
             "rich_graph_capture", "rich_graph_launch", "rich_run_host", "rich_run_host_async",
-            "rich_run_wait"]
+            "rich_run_wait", "rich_set_timing", "rich_kernel_times", "rich_trace_work"]
+# include/rich_peaks.h (microbenchmarks of the roofline denominators)
+EXPORTED_PEAKS = ["rich_measure_peaks", "rich_peaks_last_error"]
 
 # bytes a counters' read (rich_hits) brings back: the device counters (96 B)
 # and the photon total (8 B)
@@ -169,6 +171,25 @@ class Stats(C.Structure):
                 ("photon_order", C.c_uint32)]
 
 
+class KernelMs(C.Structure):
+    _fields_ = [("yield_", C.c_float), ("order", C.c_float), ("trace", C.c_float),
+                ("refine", C.c_float)]
+
+
+class Work(C.Structure):
+    _fields_ = [(f, C.c_uint64) for f in ("photons", "steps", "nodes_smem", "nodes_global",
+                                          "tri_tests", "smooth_normals", "turns", "detected",
+                                          "tracks")] + [
+        ("sphere_groups", C.c_int32), ("rects", C.c_int32)]
+
+
+class Peaks(C.Structure):
+    _fields_ = [("fp32_fma_flops", C.c_double), ("fp32_minmax_ops", C.c_double),
+                ("mufu_ops", C.c_double), ("l2_read_bytes", C.c_double),
+                ("n_sm", C.c_int32), ("reserved", C.c_int32),
+                ("sm_clock_mhz_max", C.c_double)]
+
+
 # ------------------------------------------------------------------ library
 _lib = None
 _lock = threading.Lock()
@@ -214,13 +235,21 @@ def load():
                                           C.POINTER(TraceOpts), C.POINTER(Outputs), vp,
                                           C.c_uint64, C.POINTER(C.c_uint64)]
         L.rich_run_wait.argtypes = [vp, C.c_uint64, C.POINTER(C.c_uint64), C.POINTER(Stats)]
+        L.rich_set_timing.argtypes = [vp, C.c_int]
+        L.rich_kernel_times.argtypes = [vp, C.POINTER(KernelMs)]
+        L.rich_trace_work.argtypes = [vp, C.POINTER(TraceOpts), C.POINTER(Outputs),
+                                      C.POINTER(Work)]
+        L.rich_measure_peaks.argtypes = [C.c_int, vp, C.POINTER(Peaks)]
+        L.rich_measure_peaks.restype = C.c_int
+        L.rich_peaks_last_error.restype = C.c_char_p
         L.rich_last_error.argtypes = [vp]
         L.rich_last_error.restype = C.c_char_p
         L.rich_version.restype = C.c_char_p
         for f in ("rich_create", "rich_destroy", "rich_set_stream", "rich_init_geometry",
                   "rich_emit", "rich_trace", "rich_hits", "rich_philox",
                   "rich_photon_counts_static", "rich_trace_grad", "rich_graph_capture",
-                  "rich_graph_launch", "rich_run_host", "rich_run_host_async", "rich_run_wait"):
+                  "rich_graph_launch", "rich_run_host", "rich_run_host_async", "rich_run_wait",
+                  "rich_set_timing", "rich_kernel_times", "rich_trace_work"):
             getattr(L, f).restype = C.c_int
         _lib = L
         return L
@@ -599,6 +628,31 @@ class Context:
     def graph_launch(self):
         _check(self.handle, load().rich_graph_launch(self.handle))
 
+    def set_timing(self, on=True):
+        """Kernel timing on or off (rich_set_timing)."""
+        _check(self.handle, load().rich_set_timing(self.handle, int(bool(on))))
+
+    def kernel_times(self):
+        """Durations (ms) of the kernels of the last timed emit and trace:
+        dict of yield, order, trace, refine (-1: not timed)."""
+        k = KernelMs()
+        _check(self.handle, load().rich_kernel_times(self.handle, C.byref(k)))
+        return {"yield": k.yield_, "order": k.order, "trace": k.trace, "refine": k.refine}
+
+    def trace_work(self, outputs: TraceOutputs, max_bounces=8, max_steps=16, t_min=1e-3,
+                   block_threads=0, blocks_per_sm=0, refill_min=0, chunk=0, wide_regs=0,
+                   bvh_smem_nodes=-1):
+        """rich_trace_work: the last emission traced by the counting build
+        (refined precision); returns the work tallies as a dict."""
+        o = _trace_opts(0, PREC_REFINE64, max_bounces, max_steps, t_min, block_threads,
+                        blocks_per_sm, refill_min, chunk, wide_regs, bvh_smem_nodes, ())
+        w = Work()
+        st = load().rich_trace_work(self.handle, C.byref(o), C.byref(outputs.desc()),
+                                    C.byref(w))
+        if st not in (RICH_OK, 4):
+            _check(self.handle, st)
+        return {f: getattr(w, f) for f, _ in Work._fields_}
+
     def trace_grad(self, tracks: DeviceTracks, theta, targets, outputs: TraceOutputs,
                    sigma=1.0, seed=0, lambda_min=200.0, lambda_max=600.0, max_bounces=8,
                    max_steps=16, t_min=1e-3, **launch):
@@ -640,6 +694,17 @@ class Context:
                  "fate": [int(x) for x in s.n_fate], "device_status": int(s.device_status),
                  "photon_order": int(s.photon_order), "status": int(st)}
         return int(n.value), stats
+
+
+def measure_peaks(device=0, stream=None):
+    """rich_measure_peaks: measured FP32 FMA, FP32 min/max, MUFU and L2 read
+    rates of the device (dict)."""
+    pk = Peaks()
+    s = current_stream_handle() if stream is None else stream
+    rc = load().rich_measure_peaks(int(device), C.c_void_p(s), C.byref(pk))
+    if rc != 0:
+        raise RuntimeError(load().rich_peaks_last_error().decode(errors="replace"))
+    return {f: getattr(pk, f) for f, _ in Peaks._fields_ if f != "reserved"}
 
 
 # ------------------------------------------ C-ABI-named module functions

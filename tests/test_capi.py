@@ -9,6 +9,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "rich.h")
+PEAKS_HEADER = os.path.join(ROOT, "include", "rich_peaks.h")
 
 
 @pytest.fixture(scope="module")
@@ -35,6 +36,14 @@ def test_library_exports_every_declared_symbol(lib):
     for name in declared_entry_points():
         assert hasattr(lib, name), f"{name} declared in rich.h but not exported"
     assert sorted(rich.EXPORTED) == declared_entry_points()
+    peaks = sorted(set(re.findall(r"RICH_PEAKS_API\s+[\w\s\*]+?\b(rich_\w+)\s*\(",
+                                  open(PEAKS_HEADER).read())))
+    assert peaks == sorted(rich.EXPORTED_PEAKS)
+    for name in peaks:
+        assert hasattr(lib, name), f"{name} declared in rich_peaks.h but not exported"
+    # every header in include/ is one of the two checked here
+    assert sorted(f for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")) == [
+        "rich.h", "rich_peaks.h"]
 
 
 def test_version_and_null_handling(lib):
@@ -43,6 +52,10 @@ def test_version_and_null_handling(lib):
     assert lib.rich_destroy(None) == 0
     assert lib.rich_hits(None, None, None) == 1       # RICH_ERR_ARG
     assert lib.rich_create(None, 0, None) == 1
+    assert lib.rich_measure_peaks(0, None, None) == 1
+    assert lib.rich_set_timing(None, 1) == 1
+    assert lib.rich_kernel_times(None, None) == 1
+    assert lib.rich_trace_work(None, None, None, None) == 1
 
 
 def test_struct_layouts_match_header():
@@ -56,6 +69,9 @@ def test_struct_layouts_match_header():
     assert C.sizeof(rich.EmitParams) == 8 + 10 * 4
     assert C.sizeof(rich.Outputs) == 8 * 4 + 8 + 8 + 8
     assert C.sizeof(rich.Stats) == 16 + 8 * rich.N_FATES + 8
+    assert C.sizeof(rich.KernelMs) == 16
+    assert C.sizeof(rich.Work) == 9 * 8 + 8
+    assert C.sizeof(rich.Peaks) == 4 * 8 + 8 + 8
     assert rich.HIT_DTYPE.itemsize == 40
     assert W.TABLE_DTYPE.itemsize == 280 and W.SPHERE_DTYPE.itemsize == 160
     assert W.RECT_DTYPE.itemsize == 80 and W.MATERIAL_DTYPE.itemsize == 16
