@@ -113,12 +113,17 @@ def work_per_photon(w):
           "shade_tri": w["steps"], "normal": w["smooth_normals"], "turn": w["turns"],
           "photon": w["photons"], "detected": w["detected"]}
     per = {k: sum(ev[e] * WORK_COST[e][k] for e in ev) / n for k in ("fp32", "minmax", "mufu")}
-    l2 = (w["nodes_global"] * BYTES["node"] + w["tri_tests"] * BYTES["tri"]
-          + w["smooth_normals"] * BYTES["normal"] + w["tracks"] * BYTES["track"]
-          + w["photons"] * BYTES["perm"]
-          + w["detected"] * (BYTES["hit"] + BYTES["refine_rec"])) / n
-    per["l2_bytes"] = l2
+    # the bytes the method reads and writes per photon: every BVH node and
+    # triangle its traversal tests, the vertex normals it blends, the track
+    # record, the order index, and the hit and refinement records; the
+    # kernel serves the top nodes from shared memory (smem_bytes of them)
+    outside = (w["nodes_global"] * BYTES["node"] + w["tri_tests"] * BYTES["tri"]
+               + w["smooth_normals"] * BYTES["normal"] + w["tracks"] * BYTES["track"]
+               + w["photons"] * BYTES["perm"]
+               + w["detected"] * (BYTES["hit"] + BYTES["refine_rec"])) / n
     per["smem_bytes"] = w["nodes_smem"] * BYTES["node"] / n
+    per["bytes"] = outside + per["smem_bytes"]
+    per["bytes_outside_smem"] = outside
     per["events_per_photon"] = {e: ev[e] / n for e in ev}
     return per
 
@@ -407,14 +412,19 @@ def roofline(ctx, dt, out, seeds, photons, flush, knobs, prec, peaks, clk):
     Its own duration comes from the library's kernel timing (events around
     k_trace on the context's stream) over the same seeds as the timed steps,
     L2 flushed before each. Its work per photon comes from the counting
-    build (rich_trace_work) on the first seed: FP32 operations and bytes
-    outside shared memory (WORK_COST, BYTES). The two bounds are those of
-    the scope: FP32 work over the measured FP32 FMA rate, and bytes over the
-    measured L2 read bandwidth; `bound` is the slower, and `frac` the
-    kernel's achieved rate over that bound's peak. Beside them: the min/max
-    (ALU) and special-function rates against their measured peaks, and,
-    from the committed ncu capture when it was taken from these sources,
-    warp instructions and DRAM / L2 bytes per photon."""
+    build (rich_trace_work) on the first seed: FP32 operations and the bytes
+    of the BVH nodes, triangles, normals and records its traversal reads and
+    writes (WORK_COST, BYTES), wherever the kernel keeps them. The two
+    bounds are those of the scope: FP32 work over the measured FP32 FMA
+    rate, and bytes per photon over the measured L2 read bandwidth; `bound`
+    is the slower, and `frac` the kernel's achieved rate over that bound's
+    peak. The kernel keeps the top BVH levels in shared memory, which is
+    how it could run faster than the L2 bound. Beside them: the bound with
+    only the bytes read from outside shared memory, the min/max (ALU) and
+    special-function rates against their measured peaks, and, from the
+    committed ncu capture when it was taken from these sources, warp
+    instructions and the DRAM and L2 bytes per photon that the kernel
+    actually moved."""
     import torch
     from paper_2309_12496_gb300 import rich
     stream = torch.cuda.current_stream()
@@ -444,13 +454,16 @@ def roofline(ctx, dt, out, seeds, photons, flush, knobs, prec, peaks, clk):
     rate = ph_step / t_trace                              # photons/s in k_trace
     fp32 = {"per_photon": w["fp32"], "achieved": w["fp32"] * rate / 1e12,
             "peak": peaks["fp32_fma_flops"] / 1e12, "unit": "TFLOP/s"}
-    l2 = {"per_photon": w["l2_bytes"], "achieved": w["l2_bytes"] * rate / 1e9,
+    l2 = {"per_photon": w["bytes"], "achieved": w["bytes"] * rate / 1e9,
           "peak": peaks["l2_read_bytes"] / 1e9, "unit": "GB/s"}
+    l2_out = {"per_photon": w["bytes_outside_smem"],
+              "achieved": w["bytes_outside_smem"] * rate / 1e9,
+              "peak": peaks["l2_read_bytes"] / 1e9, "unit": "GB/s"}
     alu = {"per_photon": w["minmax"], "achieved": w["minmax"] * rate / 1e12,
            "peak": peaks["fp32_minmax_ops"] / 1e12, "unit": "Tops/s"}
     xu = {"per_photon": w["mufu"], "achieved": w["mufu"] * rate / 1e12,
           "peak": peaks["mufu_ops"] / 1e12, "unit": "Tops/s"}
-    for b in (fp32, l2, alu, xu):
+    for b in (fp32, l2, l2_out, alu, xu):
         b["frac"] = b["achieved"] / b["peak"]
         b["photons_per_s_bound"] = rate / b["frac"]
     bound = "l2" if l2["frac"] >= fp32["frac"] else "fp32"
@@ -474,7 +487,8 @@ def roofline(ctx, dt, out, seeds, photons, flush, knobs, prec, peaks, clk):
             "timed": "k_trace alone: library kernel timing (CUDA events on the context "
                      "stream) over the timed seeds, L2 flushed before each",
             "peak_source": "measured by rich_measure_peaks in this run (of measured)",
-            "bounds": {"fp32": fp32, "l2": l2, "alu_minmax": alu, "mufu": xu},
+            "bounds": {"fp32": fp32, "l2": l2, "l2_outside_smem": l2_out, "alu_minmax": alu,
+                       "mufu": xu},
             "smem_bytes_per_photon": w["smem_bytes"],
             "events_per_photon": w["events_per_photon"],
             "work_tally": tally, "peaks": peaks, "issue": issue,
@@ -483,7 +497,9 @@ def roofline(ctx, dt, out, seeds, photons, flush, knobs, prec, peaks, clk):
                         "dram_bytes_per_photon": (prof["dram_bytes_per_launch"]
                                                   / prof["photons"]) if fresh else None,
                         "l2_bytes_per_photon": (prof["lts_bytes_per_launch"]
-                                                / prof["photons"]) if fresh else None}}
+                                                / prof["photons"]) if fresh else None,
+                        "l2_frac": (prof["lts_bytes_per_launch"] / prof["photons"] * rate
+                                    / peaks["l2_read_bytes"]) if fresh else None}}
     return roof, kms
 
 
