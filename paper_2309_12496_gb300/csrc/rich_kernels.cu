@@ -2289,12 +2289,19 @@ __device__ __forceinline__ void smear_pair_f32(u4 w3, float &g1, float &g2) {
 
 constexpr int kAdjThreads = 128;
 
+// Sums of the loss and the gradient: double-word FP32 per thread and over
+// the block (a warp butterfly, then shared memory; ~2^-44 relative per
+// addition), then one FP64 atomic per accumulator per block. On GB300 an
+// FP64 instruction holds the SM's FP64 unit for ~64 cycles; summing in FP64
+// per hit kept that unit the busiest of the kernel.
 __global__ void __launch_bounds__(kAdjThreads)
 k_adjoint(SceneView sc, EmitView em, TraceParams P, GradView gv, Counters *ctr) {
     const uint64_t n_hits = ctr->hits < P.hit_capacity ? ctr->hits : P.hit_capacity;
-    double acc[2 + kNG];
+    ff acc[1 + kNG];
 #pragma unroll
-    for (int k = 0; k < 2 + kNG; ++k) acc[k] = 0.0;
+    for (int k = 0; k < 1 + kNG; ++k) acc[k] = ffv(0.0f);
+    uint32_t used = 0;
+    const ff sg = ff_from_double(gv.sigma);
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_hits;
          i += (uint64_t)gridDim.x * blockDim.x) {
         rich_hit h = P.hits[i];
@@ -2314,31 +2321,41 @@ k_adjoint(SceneView sc, EmitView em, TraceParams P, GradView gv, Counters *ctr) 
             const u4 w3 = philox10(3u, h.photon, h.track, h.event, em.key0, em.key1);
             float g1, g2;
             smear_pair_f32(w3, g1, g2);
-            const ff sg = ff_from_double(gv.sigma);
             const Dm du = dm_addf(dm_addf(u, -tg.x), sg.hi * g1);
             const Dm dv = dm_addf(dm_addf(v, -tg.y), sg.hi * g2);
             const Dm dist = dm_sqrt(dm_add(dm_mul(du, du), dm_mul(dv, dv)));
             const Dm rho = dm_divc(dm_addf(dist, -tg.z), sg);
-            const double rv = ff_to_double(rho.v);
-            acc[0] += rv * rv;
-            acc[1] += 1.0;
+            acc[0] = ff_add(acc[0], ff_mul(rho.v, rho.v));
+            used += 1;
 #pragma unroll
-            for (int k = 0; k < kNG; ++k) acc[2 + k] += 2.0 * rv * (double)rho.d[k];
+            for (int k = 0; k < kNG; ++k) acc[1 + k] = ff_add(acc[1 + k], ff_mul(rho.v, 2.0f * rho.d[k]));
         }
     }
     // block reduction, one FP64 atomic per accumulator per block
-    __shared__ double red[kAdjThreads / 32][2 + kNG];
+    __shared__ ff red[kAdjThreads / 32][1 + kNG];
+    __shared__ uint32_t red_used[kAdjThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < 2 + kNG; ++k) {
-        double x = acc[k];
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFull, x, o);
+    for (int k = 0; k < 1 + kNG; ++k) {
+        ff x = acc[k];
+        for (int o = 16; o > 0; o >>= 1) x = ff_add(x, shfl_xor_ff(x, o));
         if (lane == 0) red[wid][k] = x;
     }
+    for (int o = 16; o > 0; o >>= 1) used += __shfl_xor_sync(kFull, used, o);
+    if (lane == 0) red_used[wid] = used;
     __syncthreads();
     if (threadIdx.x < 2 + kNG) {
         double x = 0.0;
-        for (int w = 0; w < kAdjThreads / 32; ++w) x += red[w][threadIdx.x];
+        if (threadIdx.x == 1) {
+            uint32_t n = 0;
+            for (int w = 0; w < kAdjThreads / 32; ++w) n += red_used[w];
+            x = (double)n;
+        } else {
+            const int k = threadIdx.x == 0 ? 0 : threadIdx.x - 1;
+            ff y = ffv(0.0f);
+            for (int w = 0; w < kAdjThreads / 32; ++w) y = ff_add(y, red[w][k]);
+            x = ff_to_double(y);
+        }
         if (x != 0.0) atomicAdd(gv.acc + threadIdx.x, x);
     }
 }
