@@ -974,7 +974,7 @@ static rich_status trace_impl(rich_ctx *ctx, const rich_photons *in, const rich_
     for (int k = 0; k < 4; ++k) p.prefilter_tables[k] = k < o->n_prefilter ? o->prefilter_tables[k] : 0;
     LaunchShape shape;
     shape.threads = threads;
-    shape.smem = trace_smem_bytes(ctx->sc, smem_nodes);
+    shape.smem = trace_smem_bytes(ctx->sc, smem_nodes, threads, cls);
     shape.cls = cls;
     if (shape.smem > (size_t)ctx->smem_optin)
         return fail(ctx, RICH_ERR_ARG, "rich_trace: staged BVH nodes exceed shared memory");
@@ -1252,7 +1252,7 @@ RICH_API rich_status rich_trace_grad(rich_ctx *ctx, const rich_tracks *t,
     LaunchShape shape;
     shape.threads = threads;
     shape.cls = cls;
-    shape.smem = trace_smem_bytes(sv, smem_nodes);
+    shape.smem = trace_smem_bytes(sv, smem_nodes, threads, cls);
     const int bps = trace_blocks_per_sm(false, true, cls, threads, shape.smem);
     if (bps < 1) return fail(ctx, RICH_ERR_ARG, "rich_trace_grad: launch shape does not fit");
     shape.blocks = bps * ctx->n_sm;

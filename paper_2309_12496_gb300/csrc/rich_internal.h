@@ -291,7 +291,7 @@ cudaError_t launch_philox(const uint32_t *ctr, uint64_t n, uint64_t seed, uint32
 cudaError_t launch_adjoint(const SceneView &sc, const EmitView &em, const TraceParams &p,
                            const GradView &gv, Counters *counters, int n_sm,
                            cudaStream_t s);
-size_t trace_smem_bytes(const SceneView &sc, int smem_nodes);
+size_t trace_smem_bytes(const SceneView &sc, int smem_nodes, int threads, int cls);
 int trace_shape_class(int threads, bool wide);
 int trace_blocks_per_sm(bool ext, bool refine, int cls, int threads, size_t smem);
 int yield_block_threads();

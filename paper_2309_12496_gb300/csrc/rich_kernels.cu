@@ -28,6 +28,13 @@
 namespace rich {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// The photon state the BVH walk does not use (wavelength, the QE and
+// reflectivity words, the keys, indices and counters) kept in per-thread
+// shared memory instead of registers.
+#ifndef RICH_COLD_SMEM
+#define RICH_COLD_SMEM 1
+#endif
 constexpr int kYieldThreads = 256;   // tracks per scan group / scan block
 constexpr int kYieldBlock = 32;      // threads per yield block: one warp, so
                                      // the per-track chains of a small batch
@@ -1507,6 +1514,28 @@ __device__ __forceinline__ uint32_t refl_word(const Photon &ph, int k,
     return k == 0 ? w.x : (k == 1 ? w.y : (k == 2 ? w.z : w.w));
 }
 
+// Cold photon state in shared memory: word f of thread t at [f * threads + t]
+// (consecutive threads in consecutive banks).
+enum : int {
+    kCLam = 0, kCWqe, kCWr0, kCWr1, kCWr2, kCWr3, kCEvent, kCId, kCJ, kCGlo, kCGhi, kCTrack,
+    kCCount,            // n_refl | n_turn << 8 | steps << 16
+    kColdWords
+};
+struct ColdState {
+    volatile uint32_t *base;
+    int stride;
+    __device__ __forceinline__ volatile uint32_t &at(int f) const {
+        return base[f * stride + (int)threadIdx.x];
+    }
+};
+__device__ __forceinline__ uint32_t cold_refl_word(const ColdState &c, int k,
+                                                   const EmitView &em) {
+    if (k < 4) return c.at(kCWr0 + k);
+    u4 w = philox10(2u, c.at(kCJ), c.at(kCId), c.at(kCEvent), em.key0, em.key1);
+    k -= 4;
+    return k == 0 ? w.x : (k == 1 ? w.y : (k == 2 ? w.z : w.w));
+}
+
 template <bool EXT, bool REFINE, int THREADS, int MINB, bool COUNT = false>
 __global__ void __launch_bounds__(THREADS, MINB)
 k_trace(TraceArgs A) {
@@ -1547,6 +1576,7 @@ k_trace(TraceArgs A) {
     const size_t scene_off = ((size_t)n_snodes_req * sizeof(DevNode) + 127) & ~size_t(127);
     // ---- stage the small scene tables into shared memory
     SmemScene S;
+    uint32_t *cold_base = nullptr;
     {
         size_t off = scene_off;
         auto carve = [&](size_t bytes) {
@@ -1570,6 +1600,8 @@ k_trace(TraceArgs A) {
         copy(tb, sc.tables, sizeof(DevTable) * sc.n_tables);
         copy(m, sc.materials, sizeof(DevMaterial) * sc.n_materials);
         S = {g, t, r, tb, m, sc.n_groups, sc.n_tiles, sc.n_rects};
+        if (RICH_COLD_SMEM && THREADS == 768)
+            cold_base = reinterpret_cast<uint32_t *>(carve(sizeof(uint32_t) * kColdWords * blockDim.x));
     }
     if (n_snodes_req > 0) {
         auto try_wait = [&]() {
@@ -1633,6 +1665,25 @@ k_trace(TraceArgs A) {
     bool alive = false;
     int path[RICH_MAX_BOUNCES];
     WorkTally tally{};
+    // the 80-register shape keeps the cold photon state in shared memory
+    // (there it removes the bounce loop's spills); the other shapes keep it
+    // in registers
+    constexpr bool kColdOn = RICH_COLD_SMEM && THREADS == 768;
+    const ColdState cold{cold_base, (int)blockDim.x};
+#define PH_LAM (kColdOn ? __uint_as_float(cold.at(kCLam)) : ph.lam)
+#define PH_WQE (kColdOn ? (uint32_t)cold.at(kCWqe) : ph.w_qe)
+#define PH_EVENT (kColdOn ? (uint32_t)cold.at(kCEvent) : ph.event)
+#define PH_ID (kColdOn ? (uint32_t)cold.at(kCId) : ph.id)
+#define PH_J (kColdOn ? (uint32_t)cold.at(kCJ) : ph.j)
+#define PH_G (kColdOn ? (((uint64_t)cold.at(kCGhi) << 32) | cold.at(kCGlo)) : ph.g)
+#define PH_TRACK (kColdOn ? (uint32_t)cold.at(kCTrack) : ph.track)
+#define PH_NREFL (kColdOn ? (int)(cold.at(kCCount) & 0xFFu) : ph.n_refl)
+#define PH_NTURN (kColdOn ? (int)((cold.at(kCCount) >> 8) & 0xFFu) : ph.n_turn)
+#define PH_STEPS (kColdOn ? (int)(cold.at(kCCount) >> 16) : ph.steps)
+#define PH_REFL_WORD(k) (kColdOn ? cold_refl_word(cold, (k), em) : refl_word(ph, (k), em))
+#define PH_ADD_REFL() do { if (kColdOn) cold.at(kCCount) = cold.at(kCCount) + 1u; else ph.n_refl += 1; } while (0)
+#define PH_ADD_TURN() do { if (kColdOn) cold.at(kCCount) = cold.at(kCCount) + 0x100u; else ph.n_turn += 1; } while (0)
+#define PH_ADD_STEP() do { if (kColdOn) cold.at(kCCount) = cold.at(kCCount) + 0x10000u; else ph.steps += 1; } while (0)
     uint64_t pool_next = 0, pool_end = 0;   // warp-uniform
     int64_t pool_track = 0;                 // warp-uniform
     bool more = true;                       // warp-uniform
@@ -1722,6 +1773,21 @@ k_trace(TraceArgs A) {
                         if (ph.g < P.fate_capacity) P.fate[ph.g] = (uint8_t)RICH_FATE_PREFILTERED;
                     } else {
                         alive = true;
+                        if (kColdOn) {
+                        cold.at(kCLam) = __float_as_uint(ph.lam);
+                        cold.at(kCWqe) = ph.w_qe;
+                        cold.at(kCWr0) = ph.wr0;
+                        cold.at(kCWr1) = ph.wr1;
+                        cold.at(kCWr2) = ph.wr2;
+                        cold.at(kCWr3) = ph.wr3;
+                        cold.at(kCEvent) = ph.event;
+                        cold.at(kCId) = ph.id;
+                        cold.at(kCJ) = ph.j;
+                        cold.at(kCGlo) = (uint32_t)ph.g;
+                        cold.at(kCGhi) = (uint32_t)(ph.g >> 32);
+                        cold.at(kCTrack) = ph.track;
+                        cold.at(kCCount) = 0u;
+                        }
                     }
                 }
                 const unsigned taken = __ballot_sync(kFull, take);
@@ -1807,22 +1873,22 @@ k_trace(TraceArgs A) {
                 } else if (M.kind == RICH_MAT_MIRROR) {
                     if (!front) {
                         fate = RICH_FATE_ABSORBED;
-                    } else if (ph.n_turn >= P.max_bounces) {
+                    } else if (PH_NTURN >= P.max_bounces) {
                         fate = RICH_FATE_MAX_BOUNCES;
                     } else {
                         // with the efficiencies applied before propagation
                         // every front-side reflection succeeds
                         const bool pass =
                             P.n_prefilter ||
-                            u24f(refl_word(ph, ph.n_refl, em)) < table_eval(S.tables[M.table], ph.lam);
+                            u24f(PH_REFL_WORD(PH_NREFL)) < table_eval(S.tables[M.table], PH_LAM);
                         if (!pass) {
                             fate = RICH_FATE_MIRROR_ABSORBED;
                         } else {
                             ph.d = normalize3(reflect_f(ph.d, n_sh));
                             if constexpr (COUNT) tally.turns += 1;
-                            if (REFINE) path[ph.n_turn] = b.kind == 2 ? sc.tri_prim_base + b.idx : b.prim;
-                            ph.n_refl += 1;
-                            ph.n_turn += 1;
+                            if (REFINE) path[PH_NTURN] = b.kind == 2 ? sc.tri_prim_base + b.idx : b.prim;
+                            PH_ADD_REFL();
+                            PH_ADD_TURN();
                             ph.o = p;
                             ph.skip = b.prim;
                             ph.skip_ref = hit_ref;
@@ -1832,10 +1898,10 @@ k_trace(TraceArgs A) {
                     // window face: Snell's law, eta = n_in / n_out with the
                     // table's index behind the face; total internal
                     // reflection when k < 0
-                    if (ph.n_turn >= P.max_bounces) {
+                    if (PH_NTURN >= P.max_bounces) {
                         fate = RICH_FATE_MAX_BOUNCES;
                     } else {
-                        const float nw = table_eval(S.tables[M.table], ph.lam);
+                        const float nw = table_eval(S.tables[M.table], PH_LAM);
                         const float eta = front ? __fdiv_rn(1.0f, nw) : nw;
                         const f3 N = front ? n_geo : n_geo * -1.0f;
                         const float c1 = -dot3(ph.d, N);
@@ -1843,8 +1909,8 @@ k_trace(TraceArgs A) {
                         ph.d = k < 0.0f ? normalize3(reflect_f(ph.d, N))
                                         : normalize3(fma3(N, eta * c1 - sqrtf(k), ph.d * eta));
                         if constexpr (COUNT) tally.turns += 1;
-                        if (REFINE) path[ph.n_turn] = b.kind == 2 ? sc.tri_prim_base + b.idx : b.prim;
-                        ph.n_turn += 1;
+                        if (REFINE) path[PH_NTURN] = b.kind == 2 ? sc.tri_prim_base + b.idx : b.prim;
+                        PH_ADD_TURN();
                         ph.o = p;
                         ph.skip = b.prim;
                         ph.skip_ref = hit_ref;
@@ -1856,7 +1922,7 @@ k_trace(TraceArgs A) {
                         ph.skip_ref = hit_ref;
                     } else {
                         const bool pass =
-                            P.n_prefilter || u24f(ph.w_qe) < table_eval(S.tables[M.table], ph.lam);
+                            P.n_prefilter || u24f(PH_WQE) < table_eval(S.tables[M.table], PH_LAM);
                         if (!pass) {
                             fate = RICH_FATE_QE_REJECTED;
                         } else {
@@ -1870,8 +1936,8 @@ k_trace(TraceArgs A) {
                     }
                 }
                 if (fate == 0) {
-                    ph.steps += 1;
-                    if (ph.steps >= P.max_steps) fate = RICH_FATE_MAX_STEPS;
+                    PH_ADD_STEP();
+                    if (PH_STEPS >= P.max_steps) fate = RICH_FATE_MAX_STEPS;
                 }
             }
         }
@@ -1901,35 +1967,37 @@ k_trace(TraceArgs A) {
                 if (binned_here) pixel_of_f32(R, hu, hv, ix, iy);
                 if (stored) {
                     rich_hit h;
-                    h.event = ph.event;
-                    h.track = ph.id;
-                    h.photon = ph.j;
+                    h.event = PH_EVENT;
+                    h.track = PH_ID;
+                    h.photon = PH_J;
                     h.plane = (uint8_t)hplane;
-                    h.n_reflections = (uint8_t)ph.n_refl;
+                    h.n_reflections = (uint8_t)PH_NREFL;
                     h.reserved = 0;
                     h.ix = (uint16_t)ix;
                     h.iy = (uint16_t)iy;
-                    h.lambda = ph.lam;
+                    h.lambda = PH_LAM;
                     h.u = hu;
                     h.v = hv;
                     P.hits[slot] = h;
                     if (REFINE) {
                         RefineRec rr;
-                        rr.index = ph.track;
+                        rr.index = PH_TRACK;
                         rr.det_rect = (uint8_t)det_rect;
-                        rr.n_path = (uint8_t)ph.n_turn;
+                        rr.n_path = (uint8_t)PH_NTURN;
                         rr.pad = 0;
 #pragma unroll
                         for (int k = 0; k < RICH_MAX_BOUNCES; ++k) rr.path[k] = path[k];
                         P.refine[slot] = rr;
                     }
                 }
-                if (binned_here) bin_hit(sc, P, ph.event, hplane, ix, iy);
+                if (binned_here) bin_hit(sc, P, PH_EVENT, hplane, ix, iy);
             }
         }
-        add_event_sums(sc, P, binned_here, ph.event, hplane, ffv(hu), ffv(hv), ph.lam, s_es);
+        add_event_sums(sc, P, binned_here, alive ? PH_EVENT : 0u, hplane, ffv(hu), ffv(hv),
+                       alive ? PH_LAM : 0.0f, s_es);
         if (fate != 0) {
-            if (ph.g < P.fate_capacity) P.fate[ph.g] = (uint8_t)fate;
+            const uint64_t g_fate = PH_G;
+            if (g_fate < P.fate_capacity) P.fate[g_fate] = (uint8_t)fate;
             atomicAdd(&s_fate[fate], 1ull);
             alive = false;
         }
@@ -2437,12 +2505,17 @@ cudaError_t launch_materialize(const SceneView &sc, const EmitView &em,
     return cudaGetLastError();
 }
 
-size_t trace_smem_bytes(const SceneView &sc, int smem_nodes) {
+enum { kShape256x4 = 0, kShape256x1 = 1, kShape1024 = 2, kShape768 = 3 };
+
+size_t trace_smem_bytes(const SceneView &sc, int smem_nodes, int threads, int cls) {
     auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
     const size_t nodes = ((size_t)smem_nodes * sizeof(DevNode) + 127) & ~size_t(127);
+    // the 768-thread shape class keeps its cold photon state here
+    const size_t cold = (RICH_COLD_SMEM && cls == kShape768)
+                            ? r16(sizeof(uint32_t) * kColdWords * (size_t)threads) : 0;
     return nodes + r16(sizeof(DevSphereGroup) * sc.n_groups) + r16(sizeof(DevTile) * sc.n_tiles) +
            r16(sizeof(DevRect) * sc.n_rects) + r16(sizeof(DevTable) * sc.n_tables) +
-           r16(sizeof(DevMaterial) * sc.n_materials);
+           r16(sizeof(DevMaterial) * sc.n_materials) + cold;
 }
 
 template <bool EXT, bool REFINE, int THREADS, int MINB, bool COUNT = false>
@@ -2468,7 +2541,6 @@ static cudaError_t launch_trace_t(const TraceArgs &a, const LaunchShape &shape,
 // registers (4 blocks per SM), up to 256 threads uncapped, up to 768
 // threads capped at 80 registers, or up to 1024 threads capped at 64 (one
 // block per SM sharing one staged copy of the BVH top).
-enum { kShape256x4 = 0, kShape256x1 = 1, kShape1024 = 2, kShape768 = 3 };
 
 template <bool EXT, bool REFINE>
 static const void *trace_kernel_t(int cls) {
