@@ -297,7 +297,10 @@ typedef struct rich_trace_opts {
     int32_t chunk;          /* photons a warp takes from the queue at a time */
     int32_t wide_regs;      /* <= 256 threads: 0 caps the trace kernel at 64
                                registers (four blocks per SM), 1 uncapped;
-                               257..768 threads: 1 caps it at 80 registers
+                               257..896 threads: 1 caps it at 72 registers
+                               (the 896-thread build, which keeps the
+                               photon state the BVH walk does not use in
+                               shared memory)
                                (0: the 1024-thread variant, 64 registers)   */
     int32_t bvh_smem_nodes; /* top BVH nodes (128 bytes each) staged in shared
                                memory per block by a TMA bulk copy

@@ -1,8 +1,8 @@
 """Autotuner of the trace launch knobs.
 
 The persistent trace kernel's speed depends on the block shape (256 threads
-capped at 64 registers, four blocks per SM; 256 uncapped; 512 or 768
-threads capped at 80 registers; 512 or 1024 threads capped at 64), on how many top BVH nodes each block stages in shared
+capped at 64 registers, four blocks per SM; 256 uncapped; 512, 768 or 896
+threads capped at 72 registers; 512 or 1024 threads capped at 64), on how many top BVH nodes each block stages in shared
 memory, on the compaction interval (refill a warp once `refill_min` lanes
 are idle) and on the photons a warp takes from the queue at a time. Which
 combination wins depends on the scene and on the number of photons (a small
@@ -35,7 +35,7 @@ def candidates(n_triangles: int):
         for refill in (24, 32):
             out.append(dict(block_threads=256, bvh_smem_nodes=0, refill_min=refill,
                             chunk=32, wide_regs=wide))
-    for threads in (768, 512):            # 80-register variant
+    for threads in (896, 768, 512):       # 72-register variant
         for n in nodes:
             for refill in (24, 32):
                 out.append(dict(block_threads=threads, blocks_per_sm=0, bvh_smem_nodes=n,

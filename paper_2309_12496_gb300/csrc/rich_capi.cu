@@ -994,7 +994,7 @@ static rich_status trace_impl(rich_ctx *ctx, const rich_photons *in, const rich_
         if (in || !refine || !trace_count_shape_ok(cls))
             return fail(ctx, RICH_ERR_ARG,
                         "rich_trace_work: counts the fused-emission trace with refinement in "
-                        "the 768- or 1024-thread shape");
+                        "the wide (up to 896 threads) or the 1024-thread shape");
         p.work = work;
     }
     EmitView em = emit_view(ctx);

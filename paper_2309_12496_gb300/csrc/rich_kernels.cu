@@ -35,6 +35,11 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 #ifndef RICH_COLD_SMEM
 #define RICH_COLD_SMEM 1
 #endif
+// Threads of the wide shape (one block per SM, 72 registers at 896; with
+// its cold photon state in shared memory it does not spill).
+#ifndef RICH_WIDE_THREADS
+#define RICH_WIDE_THREADS 896
+#endif
 constexpr int kYieldThreads = 256;   // tracks per scan group / scan block
 constexpr int kYieldBlock = 32;      // threads per yield block: one warp, so
                                      // the per-track chains of a small batch
@@ -1600,7 +1605,7 @@ k_trace(TraceArgs A) {
         copy(tb, sc.tables, sizeof(DevTable) * sc.n_tables);
         copy(m, sc.materials, sizeof(DevMaterial) * sc.n_materials);
         S = {g, t, r, tb, m, sc.n_groups, sc.n_tiles, sc.n_rects};
-        if (RICH_COLD_SMEM && THREADS == 768)
+        if (RICH_COLD_SMEM && THREADS == RICH_WIDE_THREADS)
             cold_base = reinterpret_cast<uint32_t *>(carve(sizeof(uint32_t) * kColdWords * blockDim.x));
     }
     if (n_snodes_req > 0) {
@@ -1665,10 +1670,10 @@ k_trace(TraceArgs A) {
     bool alive = false;
     int path[RICH_MAX_BOUNCES];
     WorkTally tally{};
-    // the 80-register shape keeps the cold photon state in shared memory
-    // (there it removes the bounce loop's spills); the other shapes keep it
-    // in registers
-    constexpr bool kColdOn = RICH_COLD_SMEM && THREADS == 768;
+    // the wide shape (up to 896 threads, 72 registers) keeps the cold photon
+    // state in shared memory (there it removes the bounce loop's spills);
+    // the 64-register shapes keep it in registers
+    constexpr bool kColdOn = RICH_COLD_SMEM && THREADS == RICH_WIDE_THREADS;
     const ColdState cold{cold_base, (int)blockDim.x};
 #define PH_LAM (kColdOn ? __uint_as_float(cold.at(kCLam)) : ph.lam)
 #define PH_WQE (kColdOn ? (uint32_t)cold.at(kCWqe) : ph.w_qe)
@@ -2510,7 +2515,7 @@ enum { kShape256x4 = 0, kShape256x1 = 1, kShape1024 = 2, kShape768 = 3 };
 size_t trace_smem_bytes(const SceneView &sc, int smem_nodes, int threads, int cls) {
     auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
     const size_t nodes = ((size_t)smem_nodes * sizeof(DevNode) + 127) & ~size_t(127);
-    // the 768-thread shape class keeps its cold photon state here
+    // the wide shape class keeps its cold photon state here
     const size_t cold = (RICH_COLD_SMEM && cls == kShape768)
                             ? r16(sizeof(uint32_t) * kColdWords * (size_t)threads) : 0;
     return nodes + r16(sizeof(DevSphereGroup) * sc.n_groups) + r16(sizeof(DevTile) * sc.n_tiles) +
@@ -2545,7 +2550,7 @@ static cudaError_t launch_trace_t(const TraceArgs &a, const LaunchShape &shape,
 template <bool EXT, bool REFINE>
 static const void *trace_kernel_t(int cls) {
     if (cls == kShape1024) return (const void *)k_trace<EXT, REFINE, 1024, 1>;
-    if (cls == kShape768) return (const void *)k_trace<EXT, REFINE, 768, 1>;
+    if (cls == kShape768) return (const void *)k_trace<EXT, REFINE, RICH_WIDE_THREADS, 1>;
     if (cls == kShape256x1) return (const void *)k_trace<EXT, REFINE, 256, 1>;
     return (const void *)k_trace<EXT, REFINE, 256, 4>;
 }
@@ -2556,7 +2561,7 @@ static const void *trace_kernel(bool ext, bool refine, int cls) {
 }
 
 int trace_shape_class(int threads, bool wide) {
-    if (threads > 256) return (wide && threads <= 768) ? kShape768 : kShape1024;
+    if (threads > 256) return (wide && threads <= RICH_WIDE_THREADS) ? kShape768 : kShape1024;
     return wide ? kShape256x1 : kShape256x4;
 }
 
@@ -2575,7 +2580,7 @@ int trace_blocks_per_sm(bool ext, bool refine, int cls, int threads, size_t smem
 template <bool EXT, bool REFINE>
 static cudaError_t launch_cls(const TraceArgs &a, const LaunchShape &shape, cudaStream_t s) {
     if (shape.cls == kShape1024) return launch_trace_t<EXT, REFINE, 1024, 1>(a, shape, s);
-    if (shape.cls == kShape768) return launch_trace_t<EXT, REFINE, 768, 1>(a, shape, s);
+    if (shape.cls == kShape768) return launch_trace_t<EXT, REFINE, RICH_WIDE_THREADS, 1>(a, shape, s);
     if (shape.cls == kShape256x1) return launch_trace_t<EXT, REFINE, 256, 1>(a, shape, s);
     return launch_trace_t<EXT, REFINE, 256, 4>(a, shape, s);
 }
@@ -2611,7 +2616,7 @@ cudaError_t launch_trace_count(const SceneView &sc, const EmitView &em, const Tr
     a.p = p;
     a.ctr = counters;
     a.ctr_next = next;
-    if (shape.cls == kShape768) return launch_trace_t<false, true, 768, 1, true>(a, shape, s);
+    if (shape.cls == kShape768) return launch_trace_t<false, true, RICH_WIDE_THREADS, 1, true>(a, shape, s);
     if (shape.cls == kShape1024) return launch_trace_t<false, true, 1024, 1, true>(a, shape, s);
     return cudaErrorInvalidValue;
 }
