@@ -20,6 +20,9 @@ import statistics
 
 CACHE = os.path.join(os.path.expanduser("~"), ".cache", "rich_gb300", "tune.json")
 
+# (knobs, error message) of the candidates the last tune() could not launch
+failed = []
+
 
 def candidates(n_triangles: int):
     """The search space (the BVH staging sizes only matter with meshes)."""
@@ -81,6 +84,7 @@ def tune(ctx, outputs, n_photons, precision, reps=3, use_cache=True, space=None)
         return e["knobs"], e["ms"], []
     stream = torch.cuda.current_stream()
     table = []
+    failed.clear()
     for knobs in space or candidates(ctx.scene.n_triangles):
         try:
             ctx.trace(outputs, precision=precision, **knobs)     # warm-up
@@ -94,8 +98,9 @@ def tune(ctx, outputs, n_photons, precision, reps=3, use_cache=True, space=None)
                 b.record(stream)
                 b.synchronize()
                 ms.append(a.elapsed_time(b))
-        except RuntimeError:
-            continue          # a shape that does not fit this GPU
+        except RuntimeError as e:
+            failed.append((knobs, str(e)))    # a shape that does not fit this GPU
+            continue
         table.append((knobs, statistics.median(ms)))
     best, best_ms = min(table, key=lambda kv: kv[1])
     if use_cache:

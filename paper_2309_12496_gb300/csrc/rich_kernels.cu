@@ -18,6 +18,10 @@
 #include <climits>
 #include <cstdint>
 #include <cuda_runtime.h>
+
+#include <map>
+#include <mutex>
+#include <utility>
 #include <math_constants.h>
 
 #include "rich_device.cuh"
@@ -2523,18 +2527,31 @@ size_t trace_smem_bytes(const SceneView &sc, int smem_nodes, int threads, int cl
            r16(sizeof(DevMaterial) * sc.n_materials) + cold;
 }
 
+// Dynamic shared-memory limit of a trace kernel variant: raised to `bytes`
+// when it is below, never lowered (the occupancy queries and the launches of
+// one variant ask for different sizes; the attribute persists, so a captured
+// replay issues no such call).
+static cudaError_t ensure_dyn_smem(const void *f, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, size_t> raised;   // per device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &r = raised[{dev, f}];
+    if (bytes <= r) return cudaSuccess;
+    const cudaError_t e =
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) r = bytes;
+    return e;
+}
+
 template <bool EXT, bool REFINE, int THREADS, int MINB, bool COUNT = false>
 static cudaError_t launch_trace_t(const TraceArgs &a, const LaunchShape &shape,
                                   cudaStream_t s) {
     auto kern = k_trace<EXT, REFINE, THREADS, MINB, COUNT>;
-    // raise the dynamic shared-memory limit once per variant and size (the
-    // attribute persists; a captured replay then issues no such call)
-    static size_t raised = 48 * 1024;
-    if (shape.smem > raised) {
-        cudaError_t e = cudaFuncSetAttribute(
-            kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shape.smem);
+    if (shape.smem) {
+        const cudaError_t e = ensure_dyn_smem((const void *)kern, shape.smem);
         if (e != cudaSuccess) return e;
-        raised = shape.smem;
     }
     // programmatic: the prologue (staging the top BVH levels and the scene
     // tables) may overlap the ordering pass ahead of it
@@ -2568,8 +2585,10 @@ int trace_shape_class(int threads, bool wide) {
 int trace_blocks_per_sm(bool ext, bool refine, int cls, int threads, size_t smem) {
     int n = 0;
     const void *f = trace_kernel(ext, refine, cls);
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem > 0 && ensure_dyn_smem(f, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
