@@ -298,10 +298,11 @@ typedef struct rich_trace_opts {
     int32_t wide_regs;      /* <= 256 threads: 0 caps the trace kernel at 64
                                registers (four blocks per SM), 1 uncapped;
                                257..896 threads: 1 caps it at 72 registers
-                               (the 896-thread build, which keeps the
-                               photon state the BVH walk does not use in
-                               shared memory)
-                               (0: the 1024-thread variant, 64 registers)   */
+                               (the 896-thread build), 0 at 64 (the
+                               1024-thread build); > 896 threads: the
+                               1024-thread build. Both builds of more than
+                               256 threads keep the photon state the BVH
+                               walk does not use in shared memory          */
     int32_t bvh_smem_nodes; /* top BVH nodes (128 bytes each) staged in shared
                                memory per block by a TMA bulk copy
                                (-1: default, 768 above 256 threads)         */

@@ -35,7 +35,8 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // The photon state the BVH walk does not use (wavelength, the QE and
 // reflectivity words, the keys, indices and counters) kept in per-thread
-// shared memory instead of registers.
+// shared memory instead of registers, by the two shapes of one block per SM
+// (more than 256 threads).
 #ifndef RICH_COLD_SMEM
 #define RICH_COLD_SMEM 1
 #endif
@@ -829,13 +830,28 @@ struct Best {
     float b0, b1, b2;
 };
 
+// The small scene tables staged in the trace kernel's dynamic shared memory,
+// each addressed by a 32-bit byte offset (a generic 64-bit pointer would
+// hold two registers through the bounce loop).
+extern __shared__ __align__(128) unsigned char rich_dsmem[];
 struct SmemScene {
-    const DevSphereGroup *groups;
-    const DevTile *tiles;
-    const DevRect *rects;
-    const DevTable *tables;
-    const DevMaterial *materials;
+    uint32_t o_groups, o_tiles, o_rects, o_tables, o_materials;
     int n_groups, n_tiles, n_rects;
+    __device__ __forceinline__ const DevSphereGroup *groups() const {
+        return reinterpret_cast<const DevSphereGroup *>(rich_dsmem + o_groups);
+    }
+    __device__ __forceinline__ const DevTile *tiles() const {
+        return reinterpret_cast<const DevTile *>(rich_dsmem + o_tiles);
+    }
+    __device__ __forceinline__ const DevRect *rects() const {
+        return reinterpret_cast<const DevRect *>(rich_dsmem + o_rects);
+    }
+    __device__ __forceinline__ const DevTable *tables() const {
+        return reinterpret_cast<const DevTable *>(rich_dsmem + o_tables);
+    }
+    __device__ __forceinline__ const DevMaterial *materials() const {
+        return reinterpret_cast<const DevMaterial *>(rich_dsmem + o_materials);
+    }
 };
 
 // Tiles: per distinct sphere, the quadratic |w + t d|^2 = R^2 with w = o - C
@@ -850,7 +866,7 @@ struct SmemScene {
 __device__ __noinline__ void nearest_tiles(const SmemScene &S, f3 o, f3 d,
                                            int skip, float t_min, Best &b) {
     for (int gi = 0; gi < S.n_groups; ++gi) {
-        const DevSphereGroup &G = S.groups[gi];
+        const DevSphereGroup &G = S.groups()[gi];
         // w = o - C exactly (FP32 inputs)
         const ff wx = two_sum(o.x, -G.fcx), wy = two_sum(o.y, -G.fcy),
                  wz = two_sum(o.z, -G.fcz);
@@ -873,7 +889,7 @@ __device__ __noinline__ void nearest_tiles(const SmemScene &S, f3 o, f3 d,
                               ff_add(wz, ff_mul(tr, d.z)).hi);
             bool hit = false;
             for (int k = G.first; k < G.first + G.count; ++k) {
-                const DevTile &T = S.tiles[k];
+                const DevTile &T = S.tiles()[k];
                 if (T.prim == skip) continue;
                 const float ca = (pc.x * T.ax + pc.y * T.ay + pc.z * T.az) * T.inv_radius;
                 if (!(ca >= T.cos_min)) continue;
@@ -908,7 +924,7 @@ __device__ __noinline__ f3 sphere_normal(const DevSphereGroup &G, f3 o, f3 d, fl
 __device__ __forceinline__ void nearest_rects(const SmemScene &S, f3 o, f3 d,
                                               int skip, float t_min, Best &b) {
     for (int k = 0; k < S.n_rects; ++k) {
-        const DevRect &R = S.rects[k];
+        const DevRect &R = S.rects()[k];
         if (R.prim == skip) continue;
         const f3 n = mk3(R.nx, R.ny, R.nz);
         const float den = dot3(d, n);
@@ -935,7 +951,10 @@ __device__ __forceinline__ void nearest_rects(const SmemScene &S, f3 o, f3 d,
 struct Ray {
     f3 o, d, inv;
     float sx, sy, sz;
-    int kx, ky, kz;
+    int k;              // axes of the watertight test: kx | ky << 2 | kz << 4
+    __device__ __forceinline__ int kx() const { return k & 3; }
+    __device__ __forceinline__ int ky() const { return (k >> 2) & 3; }
+    __device__ __forceinline__ int kz() const { return k >> 4; }
 };
 
 __device__ __forceinline__ float pick(float x, float y, float z, int k) {
@@ -960,9 +979,7 @@ __device__ __forceinline__ Ray make_ray(f3 o, f3 d) {
         kx = ky;
         ky = tmp;
     }
-    r.kx = kx;
-    r.ky = ky;
-    r.kz = kz;
+    r.k = kx | ky << 2 | kz << 4;
     r.sx = pick(d.x, d.y, d.z, kx) / dz;
     r.sy = pick(d.x, d.y, d.z, ky) / dz;
     r.sz = 1.0f / dz;
@@ -975,14 +992,15 @@ __device__ __forceinline__ bool watertight(const Ray &r, const DevTri &T,
     const float Ax0 = T.v0x - r.o.x, Ay0 = T.v0y - r.o.y, Az0 = T.v0z - r.o.z;
     const float Bx0 = T.v1x - r.o.x, By0 = T.v1y - r.o.y, Bz0 = T.v1z - r.o.z;
     const float Cx0 = T.v2x - r.o.x, Cy0 = T.v2y - r.o.y, Cz0 = T.v2z - r.o.z;
-    const float Akz = pick(Ax0, Ay0, Az0, r.kz), Bkz = pick(Bx0, By0, Bz0, r.kz),
-                Ckz = pick(Cx0, Cy0, Cz0, r.kz);
-    const float Ax = fmaf(-r.sx, Akz, pick(Ax0, Ay0, Az0, r.kx));
-    const float Ay = fmaf(-r.sy, Akz, pick(Ax0, Ay0, Az0, r.ky));
-    const float Bx = fmaf(-r.sx, Bkz, pick(Bx0, By0, Bz0, r.kx));
-    const float By = fmaf(-r.sy, Bkz, pick(Bx0, By0, Bz0, r.ky));
-    const float Cx = fmaf(-r.sx, Ckz, pick(Cx0, Cy0, Cz0, r.kx));
-    const float Cy = fmaf(-r.sy, Ckz, pick(Cx0, Cy0, Cz0, r.ky));
+    const int kx = r.kx(), ky = r.ky(), kz = r.kz();
+    const float Akz = pick(Ax0, Ay0, Az0, kz), Bkz = pick(Bx0, By0, Bz0, kz),
+                Ckz = pick(Cx0, Cy0, Cz0, kz);
+    const float Ax = fmaf(-r.sx, Akz, pick(Ax0, Ay0, Az0, kx));
+    const float Ay = fmaf(-r.sy, Akz, pick(Ax0, Ay0, Az0, ky));
+    const float Bx = fmaf(-r.sx, Bkz, pick(Bx0, By0, Bz0, kx));
+    const float By = fmaf(-r.sy, Bkz, pick(Bx0, By0, Bz0, ky));
+    const float Cx = fmaf(-r.sx, Ckz, pick(Cx0, Cy0, Cz0, kx));
+    const float Cy = fmaf(-r.sy, Ckz, pick(Cx0, Cy0, Cz0, ky));
     float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
     float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
     float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
@@ -1499,9 +1517,9 @@ __device__ __forceinline__ void add_event_sums(const SceneView &sc, const TraceP
 // left to right, of the listed response tables at the photon's wavelength.
 __device__ __forceinline__ float prefilter_prob(const SmemScene &S, const TraceParams &P,
                                                 float lam) {
-    float pr = table_eval(S.tables[P.prefilter_tables[0]], lam);
+    float pr = table_eval(S.tables()[P.prefilter_tables[0]], lam);
     for (int k = 1; k < P.n_prefilter; ++k)
-        pr = __fmul_rn(pr, table_eval(S.tables[P.prefilter_tables[k]], lam));
+        pr = __fmul_rn(pr, table_eval(S.tables()[P.prefilter_tables[k]], lam));
     return pr;
 }
 
@@ -1523,18 +1541,20 @@ __device__ __forceinline__ uint32_t refl_word(const Photon &ph, int k,
     return k == 0 ? w.x : (k == 1 ? w.y : (k == 2 ? w.z : w.w));
 }
 
-// Cold photon state in shared memory: word f of thread t at [f * threads + t]
-// (consecutive threads in consecutive banks).
+// Cold photon state in shared memory: the kColdWords words of thread t at
+// [t * kColdWords + f]; the stride is odd, so the 32 lanes of a warp fall in
+// 32 different banks. Addressed by one 32-bit offset into the dynamic shared
+// memory (a generic 64-bit pointer would hold two registers).
 enum : int {
     kCLam = 0, kCWqe, kCWr0, kCWr1, kCWr2, kCWr3, kCEvent, kCId, kCJ, kCGlo, kCGhi, kCTrack,
     kCCount,            // n_refl | n_turn << 8 | steps << 16
     kColdWords
 };
+static_assert(kColdWords % 2 == 1, "an odd stride keeps the lanes in distinct banks");
 struct ColdState {
-    volatile uint32_t *base;
-    int stride;
+    uint32_t off;       // byte offset of this thread's first word
     __device__ __forceinline__ volatile uint32_t &at(int f) const {
-        return base[f * stride + (int)threadIdx.x];
+        return reinterpret_cast<volatile uint32_t *>(rich_dsmem + off)[f];
     }
 };
 __device__ __forceinline__ uint32_t cold_refl_word(const ColdState &c, int k,
@@ -1585,7 +1605,7 @@ k_trace(TraceArgs A) {
     const size_t scene_off = ((size_t)n_snodes_req * sizeof(DevNode) + 127) & ~size_t(127);
     // ---- stage the small scene tables into shared memory
     SmemScene S;
-    uint32_t *cold_base = nullptr;
+    uint32_t cold_off = 0;
     {
         size_t off = scene_off;
         auto carve = [&](size_t bytes) {
@@ -1608,9 +1628,12 @@ k_trace(TraceArgs A) {
         copy(r, sc.rects, sizeof(DevRect) * sc.n_rects);
         copy(tb, sc.tables, sizeof(DevTable) * sc.n_tables);
         copy(m, sc.materials, sizeof(DevMaterial) * sc.n_materials);
-        S = {g, t, r, tb, m, sc.n_groups, sc.n_tiles, sc.n_rects};
-        if (RICH_COLD_SMEM && THREADS == RICH_WIDE_THREADS)
-            cold_base = reinterpret_cast<uint32_t *>(carve(sizeof(uint32_t) * kColdWords * blockDim.x));
+        auto o32 = [&](const void *q) {
+            return (uint32_t)(static_cast<const unsigned char *>(q) - smem);
+        };
+        S = {o32(g), o32(t), o32(r), o32(tb), o32(m), sc.n_groups, sc.n_tiles, sc.n_rects};
+        if (RICH_COLD_SMEM && THREADS > 256)
+            cold_off = (uint32_t)(carve(sizeof(uint32_t) * kColdWords * blockDim.x) - smem);
     }
     if (n_snodes_req > 0) {
         auto try_wait = [&]() {
@@ -1663,22 +1686,19 @@ k_trace(TraceArgs A) {
     const EmitView &em = A.em;
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const uint64_t N = EXT ? A.ext.n : (uint64_t)(*em.total);
-    const uint64_t chunk = (uint64_t)P.chunk;
     const bool has_tri = sc.n_tris > 0;
     const bool ordered = !EXT && em.perm && *em.perm_ok;
-    const DevTable *spec = (!EXT && em.spectrum >= 0) ? S.tables + em.spectrum : nullptr;
     if (blockIdx.x == 0 && threadIdx.x == 0) A.ctr->ordered = ordered ? 1u : 0u;
 
     Photon ph;
     bool alive = false;
     int path[RICH_MAX_BOUNCES];
     WorkTally tally{};
-    // the wide shape (up to 896 threads, 72 registers) keeps the cold photon
-    // state in shared memory (there it removes the bounce loop's spills);
-    // the 64-register shapes keep it in registers
-    constexpr bool kColdOn = RICH_COLD_SMEM && THREADS == RICH_WIDE_THREADS;
-    const ColdState cold{cold_base, (int)blockDim.x};
+    // the shapes of one block per SM (896 threads at 72 registers, 1024 at
+    // 64) keep the cold photon state in shared memory (there it removes the
+    // bounce loop's spills); the 256-thread shapes keep it in registers
+    constexpr bool kColdOn = RICH_COLD_SMEM && THREADS > 256;
+    const ColdState cold{cold_off + (uint32_t)threadIdx.x * (uint32_t)(sizeof(uint32_t) * kColdWords)};
 #define PH_LAM (kColdOn ? __uint_as_float(cold.at(kCLam)) : ph.lam)
 #define PH_WQE (kColdOn ? (uint32_t)cold.at(kCWqe) : ph.w_qe)
 #define PH_EVENT (kColdOn ? (uint32_t)cold.at(kCEvent) : ph.event)
@@ -1693,14 +1713,23 @@ k_trace(TraceArgs A) {
 #define PH_ADD_REFL() do { if (kColdOn) cold.at(kCCount) = cold.at(kCCount) + 1u; else ph.n_refl += 1; } while (0)
 #define PH_ADD_TURN() do { if (kColdOn) cold.at(kCCount) = cold.at(kCCount) + 0x100u; else ph.n_turn += 1; } while (0)
 #define PH_ADD_STEP() do { if (kColdOn) cold.at(kCCount) = cold.at(kCCount) + 0x10000u; else ph.steps += 1; } while (0)
-    uint64_t pool_next = 0, pool_end = 0;   // warp-uniform
-    int64_t pool_track = 0;                 // warp-uniform
+    // the warp's photon pool (next, end, track of next; warp-uniform) lives
+    // in shared memory between refills, so that it holds no registers
+    // through the bounce loop
+    __shared__ unsigned long long s_pool[32][3];
+    unsigned long long *const wpool = s_pool[threadIdx.x >> 5];
+    if (lane < 3) wpool[lane] = 0ull;
+    __syncwarp();
     bool more = true;                       // warp-uniform
 
     while (true) {
         // ---------------------------------------------------- refill
         unsigned idle = __ballot_sync(kFull, !alive);
         if (more && (__popc(idle) >= P.refill_min || idle == kFull)) {
+            uint64_t pool_next = wpool[0], pool_end = wpool[1];
+            int64_t pool_track = (int64_t)wpool[2];
+            const uint64_t N = EXT ? A.ext.n : (uint64_t)(*em.total);
+            const uint64_t chunk = (uint64_t)P.chunk;
             while (idle != 0u && more) {
                 if (pool_next >= pool_end) {
                     unsigned long long base = 0;
@@ -1770,6 +1799,7 @@ k_trace(TraceArgs A) {
                             j = em.perm[g];
                         ph.g = toff + j;
                         const u4 w0 = philox10(0u, j, tr.id, tr.event, em.key0, em.key1);
+                        const DevTable *spec = em.spectrum >= 0 ? S.tables() + em.spectrum : nullptr;
                         const float lam = photon_wavelength(tr, j, em, w0, spec);
                         // efficiencies before propagation (Sec. 4.3): only
                         // the wavelength is needed to decide
@@ -1811,6 +1841,13 @@ k_trace(TraceArgs A) {
                 idle &= ~(taken & ~rej);
                 if (taken == 0u && pool_next < pool_end) break;  // defensive
             }
+            __syncwarp();
+            if (lane == 0) {
+                wpool[0] = pool_next;
+                wpool[1] = pool_end;
+                wpool[2] = (unsigned long long)pool_track;
+            }
+            __syncwarp();
         }
         if (!__any_sync(kFull, alive)) {
             if (!more) break;
@@ -1843,14 +1880,14 @@ k_trace(TraceArgs A) {
                 f3 n_sh, n_geo;
                 int hit_ref = kNoSurf;    // surface subtree of a hit triangle
                 if (b.kind == 0) {
-                    const DevTile &T = S.tiles[b.idx];
-                    const DevSphereGroup &G = S.groups[T.group];
+                    const DevTile &T = S.tiles()[b.idx];
+                    const DevSphereGroup &G = S.groups()[T.group];
                     n_sh = sphere_normal(G, ph.o, ph.d, b.t);
                     n_geo = n_sh;
                     front = dot3(ph.d, n_sh) < 0.0f;
                     mat_id = T.material;
                 } else if (b.kind == 1) {
-                    const DevRect &R = S.rects[b.idx];
+                    const DevRect &R = S.rects()[b.idx];
                     n_sh = mk3(R.nx, R.ny, R.nz);
                     n_geo = n_sh;
                     front = dot3(ph.d, n_sh) < 0.0f;
@@ -1864,7 +1901,7 @@ k_trace(TraceArgs A) {
                     n_geo = normalize3(ng);
                     mat_id = T.material;
                     hit_ref = T.pad;
-                    const DevMaterial &M0 = S.materials[mat_id];
+                    const DevMaterial &M0 = S.materials()[mat_id];
                     if ((M0.flags & RICH_MAT_SMOOTH) && sc.tri_normals) {
                         const float *N3 = sc.tri_normals + 9 * (int64_t)b.idx;
                         const f3 n0 = mk3(__ldg(N3 + 0), __ldg(N3 + 1), __ldg(N3 + 2));
@@ -1876,7 +1913,7 @@ k_trace(TraceArgs A) {
                         n_sh = n_geo;
                     }
                 }
-                const DevMaterial &M = S.materials[mat_id];
+                const DevMaterial &M = S.materials()[mat_id];
                 if (M.kind == RICH_MAT_ABSORBER) {
                     fate = RICH_FATE_ABSORBED;
                 } else if (M.kind == RICH_MAT_MIRROR) {
@@ -1889,7 +1926,7 @@ k_trace(TraceArgs A) {
                         // every front-side reflection succeeds
                         const bool pass =
                             P.n_prefilter ||
-                            u24f(PH_REFL_WORD(PH_NREFL)) < table_eval(S.tables[M.table], PH_LAM);
+                            u24f(PH_REFL_WORD(PH_NREFL)) < table_eval(S.tables()[M.table], PH_LAM);
                         if (!pass) {
                             fate = RICH_FATE_MIRROR_ABSORBED;
                         } else {
@@ -1910,7 +1947,7 @@ k_trace(TraceArgs A) {
                     if (PH_NTURN >= P.max_bounces) {
                         fate = RICH_FATE_MAX_BOUNCES;
                     } else {
-                        const float nw = table_eval(S.tables[M.table], PH_LAM);
+                        const float nw = table_eval(S.tables()[M.table], PH_LAM);
                         const float eta = front ? __fdiv_rn(1.0f, nw) : nw;
                         const f3 N = front ? n_geo : n_geo * -1.0f;
                         const float c1 = -dot3(ph.d, N);
@@ -1931,13 +1968,13 @@ k_trace(TraceArgs A) {
                         ph.skip_ref = hit_ref;
                     } else {
                         const bool pass =
-                            P.n_prefilter || u24f(PH_WQE) < table_eval(S.tables[M.table], PH_LAM);
+                            P.n_prefilter || u24f(PH_WQE) < table_eval(S.tables()[M.table], PH_LAM);
                         if (!pass) {
                             fate = RICH_FATE_QE_REJECTED;
                         } else {
                             fate = RICH_FATE_DETECTED;
                             det_rect = b.idx;
-                            const DevRect &R = S.rects[b.idx];
+                            const DevRect &R = S.rects()[b.idx];
                             const f3 q = p - mk3(R.ox, R.oy, R.oz);
                             hit_u = dot3(q, mk3(R.ux, R.uy, R.uz));
                             hit_v = dot3(q, mk3(R.vx, R.vy, R.vz));
@@ -1963,8 +2000,8 @@ k_trace(TraceArgs A) {
             if (lane == leader) base = atomicAdd(&A.ctr->hits, (unsigned long long)__popc(dm));
             base = __shfl_sync(kFull, base, leader);
             if (det) {
-                const DevRect &R = S.rects[det_rect];
-                hplane = S.materials[R.material].plane;
+                const DevRect &R = S.rects()[det_rect];
+                hplane = S.materials()[R.material].plane;
                 hu = hit_u;
                 hv = hit_v;
                 const uint64_t slot = base + (uint64_t)__popc(dm & lt_mask);
@@ -2519,8 +2556,8 @@ enum { kShape256x4 = 0, kShape256x1 = 1, kShape1024 = 2, kShape768 = 3 };
 size_t trace_smem_bytes(const SceneView &sc, int smem_nodes, int threads, int cls) {
     auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
     const size_t nodes = ((size_t)smem_nodes * sizeof(DevNode) + 127) & ~size_t(127);
-    // the wide shape class keeps its cold photon state here
-    const size_t cold = (RICH_COLD_SMEM && cls == kShape768)
+    // the shapes of one block per SM keep their cold photon state here
+    const size_t cold = (RICH_COLD_SMEM && (cls == kShape768 || cls == kShape1024))
                             ? r16(sizeof(uint32_t) * kColdWords * (size_t)threads) : 0;
     return nodes + r16(sizeof(DevSphereGroup) * sc.n_groups) + r16(sizeof(DevTile) * sc.n_tiles) +
            r16(sizeof(DevRect) * sc.n_rects) + r16(sizeof(DevTable) * sc.n_tables) +
@@ -2560,9 +2597,10 @@ static cudaError_t launch_trace_t(const TraceArgs &a, const LaunchShape &shape,
 
 // Kernel variants: caller photons or fused emission; refinement side
 // records or not; block shape class: up to 256 threads capped at 64
-// registers (4 blocks per SM), up to 256 threads uncapped, up to 768
-// threads capped at 80 registers, or up to 1024 threads capped at 64 (one
-// block per SM sharing one staged copy of the BVH top).
+// registers (4 blocks per SM), up to 256 threads uncapped, up to 896
+// threads capped at 72 registers, or up to 1024 threads capped at 64 (the
+// last two one block per SM, sharing one staged copy of the BVH top, with
+// the cold photon state in shared memory).
 
 template <bool EXT, bool REFINE>
 static const void *trace_kernel_t(int cls) {
