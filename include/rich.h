@@ -289,7 +289,9 @@ typedef struct rich_trace_opts {
     float t_min;            /* minimum hit distance after an interaction (mm) */
     /* launch knobs (0 -> tuned default) */
     int32_t block_threads;  /* threads per block, multiple of 32, <= 1024;
-                               above 256 one block runs per SM             */
+                               above 256 the kernel is built for one block
+                               per SM (see wide_regs); launched with 512
+                               threads or fewer, two such blocks share one  */
     int32_t blocks_per_sm;  /* resident blocks per SM of the persistent grid
                                (0 or above the occupancy limit -> the limit) */
     int32_t refill_min;     /* refill a warp when at least this many lanes are

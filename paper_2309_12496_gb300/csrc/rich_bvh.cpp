@@ -156,9 +156,21 @@ struct Builder {
     }
 };
 
+// Centre and half extent of [lo, hi] in FP32, rounded outward: the
+// differences are exact in double, and the half extent is rounded up and
+// then widened by one more ulp, so [c - e, c + e] holds [lo, hi].
+void centre_extent(float lo, float hi, float &c, float &e) {
+    c = (float)(0.5 * ((double)lo + (double)hi));
+    const double need = std::max((double)c - (double)lo, (double)hi - (double)c);
+    float f = (float)need;
+    if ((double)f < need) f = std::nextafter(f, std::numeric_limits<float>::infinity());
+    e = std::nextafter(f, std::numeric_limits<float>::infinity());
+}
+
 void put_box(DevNode &d, int slot, const Box &b) {
-    d.lox[slot] = b.lo[0]; d.loy[slot] = b.lo[1]; d.loz[slot] = b.lo[2];
-    d.hix[slot] = b.hi[0]; d.hiy[slot] = b.hi[1]; d.hiz[slot] = b.hi[2];
+    centre_extent(b.lo[0], b.hi[0], d.cx[slot], d.ex[slot]);
+    centre_extent(b.lo[1], b.hi[1], d.cy[slot], d.ey[slot]);
+    centre_extent(b.lo[2], b.hi[2], d.cz[slot], d.ez[slot]);
 }
 
 // An empty slot: a point box at 1e30 on every axis, which every ray's slab
@@ -166,8 +178,8 @@ void put_box(DevNode &d, int slot, const Box &b) {
 void clear_node(DevNode &d) {
     std::memset(&d, 0, sizeof d);
     for (int k = 0; k < 4; ++k) {
-        d.lox[k] = d.loy[k] = d.loz[k] = 1e30f;
-        d.hix[k] = d.hiy[k] = d.hiz[k] = 1e30f;
+        d.cx[k] = d.cy[k] = d.cz[k] = 1e30f;
+        d.ex[k] = d.ey[k] = d.ez[k] = 0.0f;
         d.child[k] = std::numeric_limits<int32_t>::min();
     }
 }

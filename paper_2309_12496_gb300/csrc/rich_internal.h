@@ -73,9 +73,13 @@ struct alignas(16) DevTri {  // 48 B: v0 | v1 | v2 | prim, material, surface
 };
 
 struct alignas(16) DevNode { // 128 B: boxes of up to four children (by axis) + refs
-    float lox[4], hix[4];
-    float loy[4], hiy[4];
-    float loz[4], hiz[4];
+    // each box as centre and half extent per axis, rounded outward so that
+    // [c - e, c + e] holds the children's bounds; the slab test then forms
+    // entry and exit distances as (c - o) / d -+ e / |d| (FP32 multiply-adds)
+    // without a min/max per axis to order them
+    float cx[4], ex[4];
+    float cy[4], ey[4];
+    float cz[4], ez[4];
     int32_t child[4];          // >= 0 node, < 0 leaf ~(first << 3 | (count - 1)),
                                // INT_MIN an empty slot (its box is empty too)
     int32_t pad[4];

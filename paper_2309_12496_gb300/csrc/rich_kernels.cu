@@ -1093,38 +1093,41 @@ __device__ __forceinline__ void leaf_tris(const SceneView &sc, const Ray &r,
 }
 
 // Box tests of the four children of a four-wide node, axis by axis (the
-// node holds lo x, hi x, lo y, hi y, lo z, hi z of the four children as six
-// float4, then the children's references), read through one generic load
-// path for shared and global memory. Returns each child's entry distance,
-// +infinity for a miss, with the widening of `slab`.
+// node holds centre x, half extent x, centre y, ... of the four children as
+// six float4, then the children's references), read through one generic
+// load path for shared and global memory. Per axis the slab's entry and
+// exit distances are tc -+ e with tc = (c - o) / d and e = half extent /
+// |d|: FP32 multiply-adds, no min/max to order them. Returns each child's
+// entry distance, +infinity for a miss, with the widening of `slab`.
 __device__ __forceinline__ void node4_test(const Ray &r, const DevNode *p, float tmax,
                                            float4 &key, int4 &ch) {
     const float4 *q = reinterpret_cast<const float4 *>(p);
     const float ox = r.o.x * r.inv.x, oy = r.o.y * r.inv.y, oz = r.o.z * r.inv.z;
+    const float ax = fabsf(r.inv.x), ay = fabsf(r.inv.y), az = fabsf(r.inv.z);
     float4 tn, tf;
     {
-        const float4 lo = q[0], hi = q[1];
-        float a, c;
-        a = fmaf(lo.x, r.inv.x, -ox); c = fmaf(hi.x, r.inv.x, -ox); tn.x = fminf(a, c); tf.x = fmaxf(a, c);
-        a = fmaf(lo.y, r.inv.x, -ox); c = fmaf(hi.y, r.inv.x, -ox); tn.y = fminf(a, c); tf.y = fmaxf(a, c);
-        a = fmaf(lo.z, r.inv.x, -ox); c = fmaf(hi.z, r.inv.x, -ox); tn.z = fminf(a, c); tf.z = fmaxf(a, c);
-        a = fmaf(lo.w, r.inv.x, -ox); c = fmaf(hi.w, r.inv.x, -ox); tn.w = fminf(a, c); tf.w = fmaxf(a, c);
+        const float4 c = q[0], e = q[1];
+        float t, w;
+        t = fmaf(c.x, r.inv.x, -ox); w = e.x * ax; tn.x = t - w; tf.x = t + w;
+        t = fmaf(c.y, r.inv.x, -ox); w = e.y * ax; tn.y = t - w; tf.y = t + w;
+        t = fmaf(c.z, r.inv.x, -ox); w = e.z * ax; tn.z = t - w; tf.z = t + w;
+        t = fmaf(c.w, r.inv.x, -ox); w = e.w * ax; tn.w = t - w; tf.w = t + w;
     }
     {
-        const float4 lo = q[2], hi = q[3];
-        float a, c;
-        a = fmaf(lo.x, r.inv.y, -oy); c = fmaf(hi.x, r.inv.y, -oy); tn.x = fmaxf(tn.x, fminf(a, c)); tf.x = fminf(tf.x, fmaxf(a, c));
-        a = fmaf(lo.y, r.inv.y, -oy); c = fmaf(hi.y, r.inv.y, -oy); tn.y = fmaxf(tn.y, fminf(a, c)); tf.y = fminf(tf.y, fmaxf(a, c));
-        a = fmaf(lo.z, r.inv.y, -oy); c = fmaf(hi.z, r.inv.y, -oy); tn.z = fmaxf(tn.z, fminf(a, c)); tf.z = fminf(tf.z, fmaxf(a, c));
-        a = fmaf(lo.w, r.inv.y, -oy); c = fmaf(hi.w, r.inv.y, -oy); tn.w = fmaxf(tn.w, fminf(a, c)); tf.w = fminf(tf.w, fmaxf(a, c));
+        const float4 c = q[2], e = q[3];
+        float t, w;
+        t = fmaf(c.x, r.inv.y, -oy); w = e.x * ay; tn.x = fmaxf(tn.x, t - w); tf.x = fminf(tf.x, t + w);
+        t = fmaf(c.y, r.inv.y, -oy); w = e.y * ay; tn.y = fmaxf(tn.y, t - w); tf.y = fminf(tf.y, t + w);
+        t = fmaf(c.z, r.inv.y, -oy); w = e.z * ay; tn.z = fmaxf(tn.z, t - w); tf.z = fminf(tf.z, t + w);
+        t = fmaf(c.w, r.inv.y, -oy); w = e.w * ay; tn.w = fmaxf(tn.w, t - w); tf.w = fminf(tf.w, t + w);
     }
     {
-        const float4 lo = q[4], hi = q[5];
-        float a, c;
-        a = fmaf(lo.x, r.inv.z, -oz); c = fmaf(hi.x, r.inv.z, -oz); tn.x = fmaxf(tn.x, fminf(a, c)); tf.x = fminf(tf.x, fmaxf(a, c));
-        a = fmaf(lo.y, r.inv.z, -oz); c = fmaf(hi.y, r.inv.z, -oz); tn.y = fmaxf(tn.y, fminf(a, c)); tf.y = fminf(tf.y, fmaxf(a, c));
-        a = fmaf(lo.z, r.inv.z, -oz); c = fmaf(hi.z, r.inv.z, -oz); tn.z = fmaxf(tn.z, fminf(a, c)); tf.z = fminf(tf.z, fmaxf(a, c));
-        a = fmaf(lo.w, r.inv.z, -oz); c = fmaf(hi.w, r.inv.z, -oz); tn.w = fmaxf(tn.w, fminf(a, c)); tf.w = fminf(tf.w, fmaxf(a, c));
+        const float4 c = q[4], e = q[5];
+        float t, w;
+        t = fmaf(c.x, r.inv.z, -oz); w = e.x * az; tn.x = fmaxf(tn.x, t - w); tf.x = fminf(tf.x, t + w);
+        t = fmaf(c.y, r.inv.z, -oz); w = e.y * az; tn.y = fmaxf(tn.y, t - w); tf.y = fminf(tf.y, t + w);
+        t = fmaf(c.z, r.inv.z, -oz); w = e.z * az; tn.z = fmaxf(tn.z, t - w); tf.z = fminf(tf.z, t + w);
+        t = fmaf(c.w, r.inv.z, -oz); w = e.w * az; tn.w = fmaxf(tn.w, t - w); tf.w = fminf(tf.w, t + w);
     }
     ch = *reinterpret_cast<const int4 *>(q + 6);
     const float kInf = __int_as_float(0x7f800000);

@@ -243,6 +243,10 @@ def test_external_photons_match_fused():
     {"block_threads": 128, "refill_min": 1, "chunk": 32},
     {"block_threads": 256, "refill_min": 32, "chunk": 1024, "blocks_per_sm": 1},
     {"block_threads": 64, "refill_min": 8, "chunk": 7},
+    # the builds of one block per SM, cold photon state in shared memory
+    {"block_threads": 896, "wide_regs": 1, "bvh_smem_nodes": 256},
+    {"block_threads": 512, "blocks_per_sm": 2, "bvh_smem_nodes": 256},
+    {"block_threads": 320, "refill_min": 24, "chunk": 64, "bvh_smem_nodes": 0},
 ])
 def test_results_invariant_to_launch_shape(launch):
     """Keyed random numbers: block shape, compaction interval and chunk
