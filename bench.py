@@ -48,10 +48,12 @@ PROFILE = os.path.join(ROOT, "profiles", "k_trace_rich1_counters.json")
 # square root, sine/cosine). Events are tallied by the counting build of
 # the kernel (rich_trace_work).
 WORK_COST = {
-    # four-wide node: 4 children x 3 axes x 2 slab-plane FMAs; the 4
-    # widened exit distances (1 multiply each); min/max: per child 2 on the
-    # first axis, 4 on each other axis, 2 for the [0, t_best] clamp
-    "node": {"fp32": 4 * 3 * 2 * 2 + 4, "minmax": 4 * (2 + 4 + 4 + 2), "mufu": 0},
+    # four-wide node, boxes as centre and half extent: per child and axis
+    # the centre distance (1 FMA), the half extent over |d| (1 product) and
+    # the entry and exit distances (2 adds); the 4 widened exit distances
+    # (1 multiply each); min/max: per child 2 on each axis after the first
+    # and 2 for the [0, t_best] clamp
+    "node": {"fp32": 4 * 3 * (2 + 1 + 2) + 4, "minmax": 4 * (2 + 2 + 2), "mufu": 0},
     # watertight triangle test (Woop et al. 2013): 9 subtractions (vertices
     # relative to the origin), 6 shear FMAs, 3 edge functions (2 products
     # and a difference each), det (2 adds), scaled distance (3 products,

@@ -1092,15 +1092,29 @@ __device__ __forceinline__ void leaf_tris(const SceneView &sc, const Ray &r,
     }
 }
 
+// Three-input FP32 maximum and minimum (one instruction each on sm_100 and
+// later; exact, like two fmaxf / fminf).
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 // Box tests of the four children of a four-wide node, axis by axis (the
 // node holds centre x, half extent x, centre y, ... of the four children as
 // six float4, then the children's references), read through one generic
 // load path for shared and global memory. Per axis the slab's entry and
 // exit distances are tc -+ e with tc = (c - o) / d and e = half extent /
-// |d|: FP32 multiply-adds, no min/max to order them. Returns each child's
-// entry distance, +infinity for a miss, with the widening of `slab`.
+// |d|: FP32 multiply-adds, no min/max to order them; the axes and the
+// clamp to [0, tmax] are combined by three-input min/max. Returns each
+// child's entry distance, +infinity for a miss, with the widening of `slab`.
 __device__ __forceinline__ void node4_test(const Ray &r, const DevNode *p, float tmax,
-                                           float4 &key, int4 &ch) {
+                                           int skip_ref, float4 &key, int4 &ch) {
     const float4 *q = reinterpret_cast<const float4 *>(p);
     const float ox = r.o.x * r.inv.x, oy = r.o.y * r.inv.y, oz = r.o.z * r.inv.z;
     const float ax = fabsf(r.inv.x), ay = fabsf(r.inv.y), az = fabsf(r.inv.z);
@@ -1116,10 +1130,10 @@ __device__ __forceinline__ void node4_test(const Ray &r, const DevNode *p, float
     {
         const float4 c = q[2], e = q[3];
         float t, w;
-        t = fmaf(c.x, r.inv.y, -oy); w = e.x * ay; tn.x = fmaxf(tn.x, t - w); tf.x = fminf(tf.x, t + w);
-        t = fmaf(c.y, r.inv.y, -oy); w = e.y * ay; tn.y = fmaxf(tn.y, t - w); tf.y = fminf(tf.y, t + w);
-        t = fmaf(c.z, r.inv.y, -oy); w = e.z * ay; tn.z = fmaxf(tn.z, t - w); tf.z = fminf(tf.z, t + w);
-        t = fmaf(c.w, r.inv.y, -oy); w = e.w * ay; tn.w = fmaxf(tn.w, t - w); tf.w = fminf(tf.w, t + w);
+        t = fmaf(c.x, r.inv.y, -oy); w = e.x * ay; tn.x = max3f(tn.x, t - w, 0.0f); tf.x = min3f(tf.x, t + w, tmax);
+        t = fmaf(c.y, r.inv.y, -oy); w = e.y * ay; tn.y = max3f(tn.y, t - w, 0.0f); tf.y = min3f(tf.y, t + w, tmax);
+        t = fmaf(c.z, r.inv.y, -oy); w = e.z * ay; tn.z = max3f(tn.z, t - w, 0.0f); tf.z = min3f(tf.z, t + w, tmax);
+        t = fmaf(c.w, r.inv.y, -oy); w = e.w * ay; tn.w = max3f(tn.w, t - w, 0.0f); tf.w = min3f(tf.w, t + w, tmax);
     }
     {
         const float4 c = q[4], e = q[5];
@@ -1132,10 +1146,11 @@ __device__ __forceinline__ void node4_test(const Ray &r, const DevNode *p, float
     ch = *reinterpret_cast<const int4 *>(q + 6);
     const float kInf = __int_as_float(0x7f800000);
     // 1 + 2^-20 widening keeps boxes conservative under FP32 rounding
-    key.x = fmaxf(tn.x, 0.0f) <= fminf(tf.x, tmax) * 1.00000095f ? fmaxf(tn.x, 0.0f) : kInf;
-    key.y = fmaxf(tn.y, 0.0f) <= fminf(tf.y, tmax) * 1.00000095f ? fmaxf(tn.y, 0.0f) : kInf;
-    key.z = fmaxf(tn.z, 0.0f) <= fminf(tf.z, tmax) * 1.00000095f ? fmaxf(tn.z, 0.0f) : kInf;
-    key.w = fmaxf(tn.w, 0.0f) <= fminf(tf.w, tmax) * 1.00000095f ? fmaxf(tn.w, 0.0f) : kInf;
+    // (the subtree of the surface just left, skip_ref, counts as a miss)
+    key.x = tn.x <= tf.x * 1.00000095f && ch.x != skip_ref ? tn.x : kInf;
+    key.y = tn.y <= tf.y * 1.00000095f && ch.y != skip_ref ? tn.y : kInf;
+    key.z = tn.z <= tf.z * 1.00000095f && ch.z != skip_ref ? tn.z : kInf;
+    key.w = tn.w <= tf.w * 1.00000095f && ch.w != skip_ref ? tn.w : kInf;
 }
 
 __device__ __forceinline__ void cas_key(float &ka, int &ca, float &kb, int &cb) {
@@ -1189,12 +1204,11 @@ __device__ void nearest_bvh(const SceneView &sc, const DevNode *snodes, int n_sn
         while (ref >= 0) {
             float4 key;
             int4 ch;
-            node4_test(r, ref < n_snodes ? snodes + ref : sc.nodes + ref, b.t, key, ch);
+            node4_test(r, ref < n_snodes ? snodes + ref : sc.nodes + ref, b.t, skip_ref, key, ch);
             if constexpr (COUNT) {
                 if (ref < n_snodes) w->nodes_smem += 1; else w->nodes_global += 1;
             }
-            float k0 = ch.x != skip_ref ? key.x : kInf, k1 = ch.y != skip_ref ? key.y : kInf;
-            float k2 = ch.z != skip_ref ? key.z : kInf, k3 = ch.w != skip_ref ? key.w : kInf;
+            float k0 = key.x, k1 = key.y, k2 = key.z, k3 = key.w;
             int c0 = ch.x, c1 = ch.y, c2 = ch.z, c3 = ch.w;
             // nearest first: sorting network of the four entry distances
             cas_key(k0, c0, k1, c1);
