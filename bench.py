@@ -124,10 +124,21 @@ def work_per_photon(w):
                + w["photons"] * BYTES["perm"]
                + w["detected"] * (BYTES["hit"] + BYTES["refine_rec"])) / n
     per["smem_bytes"] = w["nodes_smem"] * BYTES["node"] / n
+    per["bytes_streamed"] = (w["tracks"] * BYTES["track"] + w["photons"] * (BYTES["perm"] + 1)
+                             + w["detected"] * (BYTES["hit"] + BYTES["refine_rec"])) / n
     per["bytes"] = outside + per["smem_bytes"]
     per["bytes_outside_smem"] = outside
     per["events_per_photon"] = {e: ev[e] / n for e in ev}
     return per
+
+
+def measured_hbm_gbs():
+    """The measured HBM copy bandwidth (MEASURED_PEAKS.json), or None."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError, TypeError):
+        return None
 
 
 def load_profile():
@@ -465,7 +476,17 @@ def roofline(ctx, dt, out, seeds, photons, flush, knobs, prec, peaks, clk):
            "peak": peaks["fp32_minmax_ops"] / 1e12, "unit": "Tops/s"}
     xu = {"per_photon": w["mufu"], "achieved": w["mufu"] * rate / 1e12,
           "peak": peaks["mufu_ops"] / 1e12, "unit": "Tops/s"}
-    for b in (fp32, l2, l2_out, alu, xu):
+    # HBM: the data k_trace streams once per step (track records, order
+    # index, fate bytes, hit and refinement records), against the measured
+    # copy bandwidth; the geometry stays L2-resident in a serving loop
+    hbm_bw = measured_hbm_gbs()
+    hbm = {"per_photon": w["bytes_streamed"], "achieved": w["bytes_streamed"] * rate / 1e9,
+           "peak": hbm_bw, "unit": "GB/s",
+           "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm_bw
+                          else "fallback 6800 GB/s (of fallback)"}
+    if not hbm_bw:
+        hbm["peak"] = 6800.0
+    for b in (fp32, l2, l2_out, alu, xu, hbm):
         b["frac"] = b["achieved"] / b["peak"]
         b["photons_per_s_bound"] = rate / b["frac"]
     bound = "l2" if l2["frac"] >= fp32["frac"] else "fp32"
@@ -490,7 +511,7 @@ def roofline(ctx, dt, out, seeds, photons, flush, knobs, prec, peaks, clk):
                      "stream) over the timed seeds, L2 flushed before each",
             "peak_source": "measured by rich_measure_peaks in this run (of measured)",
             "bounds": {"fp32": fp32, "l2": l2, "l2_outside_smem": l2_out, "alu_minmax": alu,
-                       "mufu": xu},
+                       "mufu": xu, "hbm": hbm},
             "smem_bytes_per_photon": w["smem_bytes"],
             "events_per_photon": w["events_per_photon"],
             "work_tally": tally, "peaks": peaks, "issue": issue,
