@@ -44,12 +44,16 @@ def _setup(n_tracks=300):
     return scene, ctx, dt, n
 
 
-def test_counting_build_gives_the_same_results_and_consistent_tallies():
-    """rich_trace_work traces the last emission with the counting build: the
-    same hits and fates as rich_trace, and tallies that agree with them (one
+@pytest.mark.parametrize("knobs", [
+    dict(block_threads=768, wide_regs=1, refill_min=32, chunk=32),
+    dict(block_threads=512, blocks_per_sm=2, bvh_smem_nodes=256, refill_min=32, chunk=32),
+])
+def test_counting_build_gives_the_same_results_and_consistent_tallies(knobs):
+    """rich_trace_work traces the last emission with the counting build (the
+    72-register and the 64-register builds of one block per SM): the same
+    hits and fates as rich_trace, and tallies that agree with them (one
     reflection per hit per mirror met, at least one step per photon)."""
     scene, ctx, dt, n = _setup()
-    knobs = dict(block_threads=768, wide_regs=1, refill_min=32, chunk=32)
     out = rich.TraceOutputs(n, scene.pixels_per_event, len(scene.planes), 1, n)
     ctx.trace(out, precision=rich.PREC_REFINE64, **knobs)
     nh, st = ctx.hits()
@@ -71,6 +75,29 @@ def test_counting_build_gives_the_same_results_and_consistent_tallies():
     # an unsupported form is refused
     with pytest.raises(rich.RichError):
         ctx.trace_work(out, block_threads=256)
+    ctx.close()
+
+
+def test_work_tallies_do_not_depend_on_the_launch():
+    """Each photon's traversal is fixed by its ray and the tree, so the
+    counting build's tallies are the same for any block shape; only the
+    split of node tests between staged and global nodes follows the number
+    of staged nodes."""
+    scene, ctx, dt, n = _setup()
+    out = rich.TraceOutputs(n, scene.pixels_per_event, len(scene.planes), 1, n)
+    res = []
+    for knobs in (dict(block_threads=896, wide_regs=1, bvh_smem_nodes=768),
+                  dict(block_threads=512, blocks_per_sm=2, bvh_smem_nodes=0, chunk=64),
+                  dict(block_threads=1024, bvh_smem_nodes=256, refill_min=24)):
+        ctx.emit(dt, 0.0014, seed=4, sync=True)
+        out.clear()
+        res.append(ctx.trace_work(out, **knobs))
+    for w in res[1:]:
+        for k in ("photons", "steps", "tri_tests", "smooth_normals", "turns", "detected"):
+            assert w[k] == res[0][k], k
+        assert w["nodes_smem"] + w["nodes_global"] == res[0]["nodes_smem"] + res[0]["nodes_global"]
+    assert res[1]["nodes_smem"] == 0
+    assert res[0]["nodes_smem"] > res[2]["nodes_smem"] > 0
     ctx.close()
 
 
