@@ -79,10 +79,14 @@ def test_counting_build_gives_the_same_results_and_consistent_tallies(knobs):
 
 
 def test_work_tallies_do_not_depend_on_the_launch():
-    """Each photon's traversal is fixed by its ray and the tree, so the
-    counting build's tallies are the same for any block shape; only the
-    split of node tests between staged and global nodes follows the number
-    of staged nodes."""
+    """A photon's steps, reflections, normal blends and detection are fixed
+    by its keyed draws, so those tallies are the same for any block shape.
+    Its node and triangle tests are nearly so: a lane tests its postponed
+    leaf once every lane of its warp holds one, so the distance it culls
+    with at a given node depends a little on its warp mates (which photons
+    share a warp follows the launch); the totals agree to 0.1 %. The split
+    of node tests between staged and global nodes follows the number of
+    staged nodes."""
     scene, ctx, dt, n = _setup()
     out = rich.TraceOutputs(n, scene.pixels_per_event, len(scene.planes), 1, n)
     res = []
@@ -93,9 +97,11 @@ def test_work_tallies_do_not_depend_on_the_launch():
         out.clear()
         res.append(ctx.trace_work(out, **knobs))
     for w in res[1:]:
-        for k in ("photons", "steps", "tri_tests", "smooth_normals", "turns", "detected"):
+        for k in ("photons", "steps", "smooth_normals", "turns", "detected"):
             assert w[k] == res[0][k], k
-        assert w["nodes_smem"] + w["nodes_global"] == res[0]["nodes_smem"] + res[0]["nodes_global"]
+        assert w["tri_tests"] == pytest.approx(res[0]["tri_tests"], rel=1e-3)
+        assert w["nodes_smem"] + w["nodes_global"] == pytest.approx(
+            res[0]["nodes_smem"] + res[0]["nodes_global"], rel=1e-3)
     assert res[1]["nodes_smem"] == 0
     assert res[0]["nodes_smem"] > res[2]["nodes_smem"] > 0
     ctx.close()
