@@ -398,6 +398,9 @@ def main():
         if line is not None:
             line["e2e"] = e2e
             line["point_source"] = run_point_source(dev, prec, rank, args)
+            from paper_2309_12496_gb300 import workloads as W
+            line["point_source"]["paper_scale"] = run_point_source(
+                dev, prec, rank, args, wl=W.point_source_muon(600_000))
             line["batched"] = run_batched(dev, prec, rank)
             line["adjoint"] = run_adjoint(dev, rank)
             line["rich2_chunked"] = run_chunked(dev, rank)
@@ -544,15 +547,17 @@ def _time_steps(fn, n_steps, warmup, flush):
     return statistics.median(ms)
 
 
-def run_point_source(dev, prec, rank, args):
+def run_point_source(dev, prec, rank, args, wl=None):
     """The plain form on the point-source configuration: 10^5 photons from
     the centre of curvature of the R = 2710 mm analytic mirror (n = 1.0014,
     beta = 1), emit + trace per step through the C ABI, the same timing
-    protocol as the headline (L2 flushed before each step, CUDA events)."""
+    protocol as the headline (L2 flushed before each step, CUDA events).
+    `wl` replaces the workload (the paper-scale point: 6e5 photons from one
+    100 GeV muon)."""
     import torch
     from paper_2309_12496_gb300 import rich
     from paper_2309_12496_gb300 import workloads as W
-    wl = W.point_source(100_000)
+    wl = wl or W.point_source(100_000)
     ctx = rich.Context(int(dev.split(":")[1]))
     ctx.init_geometry(wl.scene)
     dt = rich.DeviceTracks(wl.tracks, device=dev)

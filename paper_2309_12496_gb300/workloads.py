@@ -649,6 +649,16 @@ def point_source_tracks(n_photons=100_000) -> Tracks:
                         n_fixed=[n_photons])
 
 
+def muon_point_tracks(n_photons=600_000, p_gev=100.0) -> Tracks:
+    """One muon of p_gev GeV/c (m = 105.66 MeV) of zero length at the origin
+    pointing along +z, emitting a fixed n_photons on its Cherenkov cone: the
+    paper-scale point source (one 100 GeV muon, ~6e5 photons)."""
+    return _make_tracks(1, (0.0, 0.0, 0.0), np.array([[0.0, 0.0, 1.0]]),
+                        p=np.array([p_gev]), mass=np.array([MUON_MASS]),
+                        length=np.array([0.0]), event=[0], tid=[0],
+                        n_fixed=[n_photons])
+
+
 def _cone_dirs(rng, n, max_angle):
     """Directions uniform in solid angle within max_angle of +z."""
     cos_t = 1.0 - rng.random(n) * (1.0 - math.cos(max_angle))
@@ -712,6 +722,13 @@ def point_source(n_photons=100_000, meshed=False) -> Workload:
                     "curvature of an R=2710 mm sphere"
                     + (" (smooth-normal triangle mesh)" if meshed else "")
                     + ", n=1.0014, beta=1")
+
+
+def point_source_muon(n_photons=600_000) -> Workload:
+    return Workload("point_source_muon", point_source_scene(),
+                    muon_point_tracks(n_photons), n_minus_1=0.0014,
+                    description=f"{n_photons} photons from one 100 GeV/c muon at the "
+                    "centre of curvature of an R=2710 mm sphere, n=1.0014")
 
 
 def rich1(n_tracks=1000, seed=0, meshed=True) -> Workload:
