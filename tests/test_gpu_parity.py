@@ -116,13 +116,13 @@ def test_poisson_counts_over_wide_mean_range():
 
 
 # --------------------------------------------------------------- point source
-def _ring_error(hits, scene):
+def _ring_error(hits, scene, beta=1.0):
     rect = scene.rects[0]
     hu = -float(np.dot(rect["origin"].astype(np.float64), rect["u_axis"]))
     hv = -float(np.dot(rect["origin"].astype(np.float64), rect["v_axis"]))
     r = np.hypot(hits["u"] - hu, hits["v"] - hv)
-    n = 1 + float(np.float32(0.0014))
-    return float(np.abs(r - 1355.0 * math.sqrt(n * n - 1)).max(initial=0.0))
+    nb = (1 + float(np.float32(0.0014))) * beta
+    return float(np.abs(r - 1355.0 * math.sqrt(nb * nb - 1)).max(initial=0.0))
 
 
 @pytest.mark.parametrize("precision", [rich.PREC_REFINE64, rich.PREC_FP32])
@@ -136,6 +136,23 @@ def test_point_source_parity(precision):
     st["max_ring_err_mm"] = _ring_error(gpu["hits"], wl.scene)
     report(f"point_source_prec{precision}_ring", {"max_ring_err_mm": st["max_ring_err_mm"]})
     assert st["max_ring_err_mm"] < tol + 1e-6
+
+
+def test_muon_point_source_parity():
+    """The paper-scale point source (one 100 GeV/c muon at the centre of
+    curvature; 10^5 of its photons here): beta < 1 from the track's FP32
+    momentum and mass, every hit on the ring (R/2) tan(theta) with
+    cos(theta) = 1/(n beta), and photon-by-photon parity with the oracle."""
+    wl = W.point_source_muon(100_000)
+    ref = P.run_oracle(wl)
+    gpu = P.run_gpu(wl, rich.PREC_REFINE64)
+    st = P.compare(gpu, ref, wl.tracks, P.TOL_UV_REFINE, name="point_source_muon")
+    p, m = float(wl.tracks.p[0]), float(wl.tracks.mass[0])
+    beta = p / math.sqrt(p * p + m * m)
+    st["max_ring_err_mm"] = _ring_error(gpu["hits"], wl.scene, beta)
+    report("point_source_muon_ring", {"max_ring_err_mm": st["max_ring_err_mm"]})
+    assert gpu["n_hits"] > 10_000
+    assert st["max_ring_err_mm"] < P.TOL_UV_REFINE + 1e-6
 
 
 @pytest.mark.parametrize("precision", [rich.PREC_REFINE64, rich.PREC_FP32])

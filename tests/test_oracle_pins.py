@@ -272,6 +272,26 @@ def test_point_source_ring_radius(oracle_lib):
     assert set(np.unique(out["fate"])) <= {2, 4, 5}
 
 
+def test_muon_point_source_ring_radius(oracle_lib):
+    """One 100 GeV/c muon (m = 105.66 MeV) at the centre of curvature:
+    beta = p / sqrt(p^2 + m^2) = 0.99999944 from the FP32 momentum and mass,
+    cos(theta) = 1/(n beta) (Sec. 3), and every hit at (R/2) tan(theta)
+    = 71.71062 mm, 0.0143 mm inside the beta = 1 ring: a dropped mass or a
+    beta squared in the wrong place moves the ring by far more than the
+    bound."""
+    wl = w.point_source_muon(20000)
+    sc = oracle_lib.Scene(wl.scene)
+    out = sc.trace(wl.tracks, oracle_lib.params(wl))
+    det, rad = _ring_radii(out, wl.scene.rects[0])
+    p, m = float(wl.tracks.p[0]), float(wl.tracks.mass[0])
+    nb = (1 + ETA_C4F10) * p / math.sqrt(p * p + m * m)
+    expect = 1355.0 * math.sqrt(nb * nb - 1)
+    assert expect == pytest.approx(71.71062, abs=2e-5)
+    assert 1355.0 * math.sqrt((1 + ETA_C4F10) ** 2 - 1) - expect > 0.01
+    assert det.sum() > 1000
+    assert np.abs(rad - expect).max() < 1e-9
+
+
 def test_point_source_expected_counts(oracle_lib):
     """Detected fraction = R * <QE> with <QE> the spectrum-weighted mean of
     0.3 exp(-((l - 400)/120)^2) under dN/dl ~ 1/l^2 on [200, 600] nm
