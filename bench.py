@@ -461,7 +461,7 @@ def roofline(ctx, dt, out, seeds, photons, flush, knobs, prec, peaks, clk):
     # has one)
     wk = dict(knobs)
     if wk.get("block_threads", 1024) <= 256:
-        wk.update(block_threads=768, wide_regs=1)
+        wk.update(block_threads=512, blocks_per_sm=2, wide_regs=0)
     ctx.emit(dt, 0.0014, seed=seeds[0], sync=True)
     out.clear()
     tally = ctx.trace_work(out, **{k: v for k, v in wk.items()})

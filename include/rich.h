@@ -307,7 +307,7 @@ typedef struct rich_trace_opts {
                                walk does not use in shared memory          */
     int32_t bvh_smem_nodes; /* top BVH nodes (128 bytes each) staged in shared
                                memory per block by a TMA bulk copy
-                               (-1: default, 768 above 256 threads)         */
+                               (-1: default, 256 above 256 threads)         */
     /* Efficiencies applied before propagation (Sec. 4.3: the quantum
      * efficiency and the mirror reflectivities combined into one
      * accept/reject per photon at its wavelength, and rejected photons not

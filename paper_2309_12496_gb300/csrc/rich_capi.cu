@@ -933,7 +933,7 @@ static rich_status trace_impl(rich_ctx *ctx, const rich_photons *in, const rich_
                     "rich_trace: the emission's spectrum table is not in the current scene");
     const int cls = trace_shape_class(threads, o->wide_regs != 0);
     int smem_nodes = o->bvh_smem_nodes;
-    if (smem_nodes < 0) smem_nodes = threads > 256 ? 768 : 0;
+    if (smem_nodes < 0) smem_nodes = threads > 256 ? 256 : 0;
     if (smem_nodes > ctx->sc.n_nodes) smem_nodes = ctx->sc.n_nodes;
     if (ctx->sc.n_tris == 0) smem_nodes = 0;
     DeviceGuard guard(ctx->device);
@@ -1226,7 +1226,7 @@ RICH_API rich_status rich_trace_grad(rich_ctx *ctx, const rich_tracks *t,
     const int threads = fo.block_threads ? fo.block_threads : 1024;
     const int cls = trace_shape_class(threads, fo.wide_regs != 0);
     int smem_nodes = fo.bvh_smem_nodes;
-    if (smem_nodes < 0) smem_nodes = threads > 256 ? 768 : 0;
+    if (smem_nodes < 0) smem_nodes = threads > 256 ? 256 : 0;
     if (smem_nodes > ctx->sc.n_nodes) smem_nodes = ctx->sc.n_nodes;
     if (ctx->sc.n_tris == 0) smem_nodes = 0;
     TraceParams p{};

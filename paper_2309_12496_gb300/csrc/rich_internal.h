@@ -282,7 +282,7 @@ cudaError_t launch_trace(const SceneView &sc, const EmitView *em,
                          Counters *counters, Counters *next, const LaunchShape &shape,
                          cudaStream_t s);
 // The counting build of the trace (fused emission, refinement records; the
-// 768- and 1024-thread shape classes only): p.work receives 6 tallies.
+// shape classes of more than 256 threads only): p.work receives 6 tallies.
 bool trace_count_shape_ok(int cls);
 cudaError_t launch_trace_count(const SceneView &sc, const EmitView &em, const TraceParams &p,
                                Counters *counters, Counters *next, const LaunchShape &shape,

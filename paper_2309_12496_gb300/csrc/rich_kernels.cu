@@ -40,8 +40,8 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 #ifndef RICH_COLD_SMEM
 #define RICH_COLD_SMEM 1
 #endif
-// Threads of the wide shape (one block per SM, 72 registers at 896; with
-// its cold photon state in shared memory it does not spill).
+// Threads of the wide 72-register shape class (one block per SM at 896
+// threads; with its cold photon state in shared memory it does not spill).
 #ifndef RICH_WIDE_THREADS
 #define RICH_WIDE_THREADS 896
 #endif
@@ -2568,13 +2568,13 @@ cudaError_t launch_materialize(const SceneView &sc, const EmitView &em,
     return cudaGetLastError();
 }
 
-enum { kShape256x4 = 0, kShape256x1 = 1, kShape1024 = 2, kShape768 = 3 };
+enum { kShape256x4 = 0, kShape256x1 = 1, kShape1024 = 2, kShapeWide = 3 };
 
 size_t trace_smem_bytes(const SceneView &sc, int smem_nodes, int threads, int cls) {
     auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
     const size_t nodes = ((size_t)smem_nodes * sizeof(DevNode) + 127) & ~size_t(127);
     // the shapes of one block per SM keep their cold photon state here
-    const size_t cold = (RICH_COLD_SMEM && (cls == kShape768 || cls == kShape1024))
+    const size_t cold = (RICH_COLD_SMEM && (cls == kShapeWide || cls == kShape1024))
                             ? r16(sizeof(uint32_t) * kColdWords * (size_t)threads) : 0;
     return nodes + r16(sizeof(DevSphereGroup) * sc.n_groups) + r16(sizeof(DevTile) * sc.n_tiles) +
            r16(sizeof(DevRect) * sc.n_rects) + r16(sizeof(DevTable) * sc.n_tables) +
@@ -2622,7 +2622,7 @@ static cudaError_t launch_trace_t(const TraceArgs &a, const LaunchShape &shape,
 template <bool EXT, bool REFINE>
 static const void *trace_kernel_t(int cls) {
     if (cls == kShape1024) return (const void *)k_trace<EXT, REFINE, 1024, 1>;
-    if (cls == kShape768) return (const void *)k_trace<EXT, REFINE, RICH_WIDE_THREADS, 1>;
+    if (cls == kShapeWide) return (const void *)k_trace<EXT, REFINE, RICH_WIDE_THREADS, 1>;
     if (cls == kShape256x1) return (const void *)k_trace<EXT, REFINE, 256, 1>;
     return (const void *)k_trace<EXT, REFINE, 256, 4>;
 }
@@ -2633,7 +2633,7 @@ static const void *trace_kernel(bool ext, bool refine, int cls) {
 }
 
 int trace_shape_class(int threads, bool wide) {
-    if (threads > 256) return (wide && threads <= RICH_WIDE_THREADS) ? kShape768 : kShape1024;
+    if (threads > 256) return (wide && threads <= RICH_WIDE_THREADS) ? kShapeWide : kShape1024;
     return wide ? kShape256x1 : kShape256x4;
 }
 
@@ -2654,7 +2654,7 @@ int trace_blocks_per_sm(bool ext, bool refine, int cls, int threads, size_t smem
 template <bool EXT, bool REFINE>
 static cudaError_t launch_cls(const TraceArgs &a, const LaunchShape &shape, cudaStream_t s) {
     if (shape.cls == kShape1024) return launch_trace_t<EXT, REFINE, 1024, 1>(a, shape, s);
-    if (shape.cls == kShape768) return launch_trace_t<EXT, REFINE, RICH_WIDE_THREADS, 1>(a, shape, s);
+    if (shape.cls == kShapeWide) return launch_trace_t<EXT, REFINE, RICH_WIDE_THREADS, 1>(a, shape, s);
     if (shape.cls == kShape256x1) return launch_trace_t<EXT, REFINE, 256, 1>(a, shape, s);
     return launch_trace_t<EXT, REFINE, 256, 4>(a, shape, s);
 }
@@ -2676,9 +2676,10 @@ cudaError_t launch_trace(const SceneView &sc, const EmitView *em,
 }
 
 // The counting build of the fused-emission trace with refinement records
-// (the benchmark's form) in the 768- and 1024-thread shapes: the same
+// (the benchmark's form) in the two shape classes of more than 256 threads
+// (72 registers up to 896 threads, 64 registers up to 1024): the same
 // traversal, plus per-thread tallies of its work summed into p.work.
-bool trace_count_shape_ok(int cls) { return cls == kShape768 || cls == kShape1024; }
+bool trace_count_shape_ok(int cls) { return cls == kShapeWide || cls == kShape1024; }
 
 cudaError_t launch_trace_count(const SceneView &sc, const EmitView &em, const TraceParams &p,
                                Counters *counters, Counters *next, const LaunchShape &shape,
@@ -2690,7 +2691,7 @@ cudaError_t launch_trace_count(const SceneView &sc, const EmitView &em, const Tr
     a.p = p;
     a.ctr = counters;
     a.ctr_next = next;
-    if (shape.cls == kShape768) return launch_trace_t<false, true, RICH_WIDE_THREADS, 1, true>(a, shape, s);
+    if (shape.cls == kShapeWide) return launch_trace_t<false, true, RICH_WIDE_THREADS, 1, true>(a, shape, s);
     if (shape.cls == kShape1024) return launch_trace_t<false, true, 1024, 1, true>(a, shape, s);
     return cudaErrorInvalidValue;
 }
