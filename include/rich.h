@@ -287,7 +287,8 @@ typedef struct rich_trace_opts {
                                refractions), 1..RICH_MAX_BOUNCES             */
     int32_t max_steps;      /* surface interactions, 1..RICH_MAX_STEPS        */
     float t_min;            /* minimum hit distance after an interaction (mm) */
-    /* launch knobs (0 -> tuned default) */
+    /* launch knobs (0 -> default: 512 threads of the 64-register build, two
+       blocks per SM, 256 staged top nodes) */
     int32_t block_threads;  /* threads per block, multiple of 32, <= 1024;
                                above 256 the kernel is built for one block
                                per SM (see wide_regs); launched with 512

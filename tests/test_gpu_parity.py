@@ -262,7 +262,7 @@ def test_external_photons_match_fused():
     {"block_threads": 64, "refill_min": 8, "chunk": 7},
     # the builds of one block per SM, cold photon state in shared memory
     {"block_threads": 896, "wide_regs": 1, "bvh_smem_nodes": 256},
-    {"block_threads": 512, "blocks_per_sm": 2, "bvh_smem_nodes": 256},
+    {"block_threads": 1024, "bvh_smem_nodes": 768},
     {"block_threads": 320, "refill_min": 24, "chunk": 64, "bvh_smem_nodes": 0},
 ])
 def test_results_invariant_to_launch_shape(launch):
