@@ -547,7 +547,10 @@ k_offsets(const uint32_t *counts, const unsigned long long *block_sums,
 // arbitrary.
 constexpr int kAzBins = 32;
 constexpr int kOrderWarps = 4;
-constexpr uint32_t kOrderBinCache = 2048;
+// bins of the first 8192 photons kept (8 KiB): tracks of up to 8192 photons
+// draw each azimuth once (5000-photon tracks: 16.9 -> 15.4 us per 200 tracks;
+// 8 warps per block were slower on 10^4 tracks)
+constexpr uint32_t kOrderBinCache = 8192;
 
 // SCAN: the offsets are not computed yet; each block first forms the
 // exclusive prefix of the 256-track group sums in shared memory, and each
