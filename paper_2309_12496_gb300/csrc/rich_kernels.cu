@@ -2171,8 +2171,14 @@ cudaError_t launch_refine(const SceneView &sc, const EmitView *em, const ExtView
 // beta_k of sphere tiles 0..3, radius of curvature, n - 1): every stored hit
 // is replayed along its recorded reflecting surfaces (fixed topology) in
 // forward mode, with double-word values (the refinement replay's arithmetic,
-// see rich_ff.cuh) and 10 FP32 tangents per quantity.
-constexpr int kNG = 10;
+// see rich_ff.cuh) and FP32 tangents. A photon's position depends on the
+// tilts of the tiles its path meets only (one, for a photon of the RICH
+// layouts), so a replay carries 4 tangents: slots 0 and 1 the tilts of one
+// tile, 2 the radius, 3 n - 1. Forward mode is linear in the seeds: the first
+// pass seeds the first tile's tilts, the radius and n - 1, each further tile
+// of the path one more pass with its tilts alone.
+constexpr int kNG = 4;     // tangents per replay
+constexpr int kNP = 10;    // parameters
 struct Dm {
     ff v;
     float d[kNG];
@@ -2301,22 +2307,23 @@ __device__ __forceinline__ Dm3 dm3_reflect_unit(const Dm3 &d, const Dm3 &n) {
     const Dm3 r = dm3_axpy(d, n, k);
     return dm3_scl(r, dm_rsqrt(dm3_dot(r, r)));
 }
-// component c of tile centre C(theta) with its tangents in alpha_i, beta_i
-// (ka = 2 i for i < 4, else -1) and R
-__device__ __forceinline__ Dm tile_centre(const DevTileDual &T, int c, int ka) {
+// component c of tile centre C(theta) with its tangents: in the tile's own
+// tilts when it is the pass's tile (own), in R on the first pass
+__device__ __forceinline__ Dm tile_centre(const DevTileDual &T, int c, bool own, bool first) {
     Dm r;
     r.v = {T.c_hi[c], T.c_lo[c]};
-#pragma unroll
-    for (int k = 0; k < kNG; ++k)
-        r.d[k] = k == 8                     ? T.dc_dr[c]
-                 : k == ka                  ? T.dc_dalpha[c]
-                 : (ka >= 0 && k == ka + 1) ? T.dc_dbeta[c]
-                                            : 0.0f;
+    r.d[0] = own ? T.dc_dalpha[c] : 0.0f;
+    r.d[1] = own ? T.dc_dbeta[c] : 0.0f;
+    r.d[2] = first ? T.dc_dr[c] : 0.0f;
+    r.d[3] = 0.0f;
     return r;
 }
 
+// pass_tile: the tile (0..3) whose tilts are seeded in slots 0 and 1, or
+// -1; first: the radius and n - 1 seeded in slots 2 and 3
 __device__ void replay_dual(const SceneView &sc, const GradView &gv, const EmitView &em,
-                            const RefineRec &rr, uint32_t j, Dm &u_out, Dm &v_out) {
+                            const RefineRec &rr, uint32_t j, int pass_tile, bool first,
+                            Dm &u_out, Dm &v_out) {
     const TrackRec tr = em.tracks[rr.index];
     const float4 cs = em.cos_sin[rr.index];
     // emission as in the refinement replay; the tangent of the Cherenkov
@@ -2331,22 +2338,23 @@ __device__ void replay_dual(const SceneView &sc, const GradView &gv, const EmitV
     const ff3 d0 = ff3_normalized({ff_add(ff_mul(t.x, ct), ff_mul(r.x, st)),
                                    ff_add(ff_mul(t.y, ct), ff_mul(r.y, st)),
                                    ff_add(ff_mul(t.z, ct), ff_mul(r.z, st))});
-    const float dct = -ct.hi / (1.0f + (float)gv.theta[9]);
+    const float dct = first ? -ct.hi / (1.0f + (float)gv.theta[9]) : 0.0f;
     const float dst = st.hi > 0.0f ? -ct.hi * dct / st.hi : 0.0f;
     Dm3 o = dm3_c(o0), d = dm3_c(d0);
-    d.x.d[9] = t.x.hi * dct + r.x.hi * dst;
-    d.y.d[9] = t.y.hi * dct + r.y.hi * dst;
-    d.z.d[9] = t.z.hi * dct + r.z.hi * dst;
+    d.x.d[3] = t.x.hi * dct + r.x.hi * dst;
+    d.y.d[3] = t.y.hi * dct + r.y.hi * dst;
+    d.z.d[3] = t.z.hi * dct + r.z.hi * dst;
     Dm R = dm_c(ff_from_double(gv.theta[8]));
-    R.d[8] = 1.0f;
+    R.d[2] = first ? 1.0f : 0.0f;
     const Dm inv_R = dm_div(dm_c(ffv(1.0f)), R);
     for (int k = 0; k < rr.n_path; ++k) {
         const int prim = rr.path[k];
         Dm3 n;
         if (prim < sc.n_tiles) {
             const DevTileDual &T = gv.tiles[prim];
-            const int ka = prim < 4 ? 2 * prim : -1;
-            const Dm3 C = {tile_centre(T, 0, ka), tile_centre(T, 1, ka), tile_centre(T, 2, ka)};
+            const bool own = prim == pass_tile;
+            const Dm3 C = {tile_centre(T, 0, own, first), tile_centre(T, 1, own, first),
+                           tile_centre(T, 2, own, first)};
             const Dm3 w = dm3_sub(o, C);
             const Dm b = dm3_dot(w, d);
             const Dm c = dm_sub(dm3_dot(w, w), dm_mul(R, R));
@@ -2422,55 +2430,81 @@ __device__ __forceinline__ void smear_pair_f32(u4 w3, float &g1, float &g2) {
 }
 
 constexpr int kAdjThreads = 128;
+// three blocks per SM: 163 registers, no spills (12 warps per SM; four
+// blocks at 128 registers spill and are no faster)
+constexpr int kAdjMinBlocks = 3;
 
 // Sums of the loss and the gradient: double-word FP32 per thread and over
 // the block (a warp butterfly, then shared memory; ~2^-44 relative per
 // addition), then one FP64 atomic per accumulator per block. On GB300 an
 // FP64 instruction holds the SM's FP64 unit for ~64 cycles; summing in FP64
 // per hit kept that unit the busiest of the kernel.
-__global__ void __launch_bounds__(kAdjThreads)
+__global__ void __launch_bounds__(kAdjThreads, kAdjMinBlocks)
 k_adjoint(SceneView sc, EmitView em, TraceParams P, GradView gv, Counters *ctr) {
     const uint64_t n_hits = ctr->hits < P.hit_capacity ? ctr->hits : P.hit_capacity;
-    ff acc[1 + kNG];
+    ff acc[1 + kNP];
 #pragma unroll
-    for (int k = 0; k < 1 + kNG; ++k) acc[k] = ffv(0.0f);
+    for (int k = 0; k < 1 + kNP; ++k) acc[k] = ffv(0.0f);
     uint32_t used = 0;
     const ff sg = ff_from_double(gv.sigma);
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_hits;
          i += (uint64_t)gridDim.x * blockDim.x) {
         rich_hit h = P.hits[i];
         const RefineRec rr = P.refine[i];
-        Dm u, v;
-        replay_dual(sc, gv, em, rr, h.photon, u, v);
-        int ix, iy;
-        pixel_of_ff(sc.rects[rr.det_rect], u.v, v.v, ix, iy);
-        h.u = ff_to_double(u.v);
-        h.v = ff_to_double(v.v);
-        h.ix = (uint16_t)ix;
-        h.iy = (uint16_t)iy;
-        P.hits[i] = h;
-        bin_hit(sc, P, h.event, h.plane, ix, iy);
         const float4 tg = gv.targets[(int64_t)rr.index * gv.n_planes + h.plane];
+        float g1 = 0.0f, g2 = 0.0f;
         if (tg.w > 0.0f) {
             const u4 w3 = philox10(3u, h.photon, h.track, h.event, em.key0, em.key1);
-            float g1, g2;
             smear_pair_f32(w3, g1, g2);
-            const Dm du = dm_addf(dm_addf(u, -tg.x), sg.hi * g1);
-            const Dm dv = dm_addf(dm_addf(v, -tg.y), sg.hi * g2);
-            const Dm dist = dm_sqrt(dm_add(dm_mul(du, du), dm_mul(dv, dv)));
-            const Dm rho = dm_divc(dm_addf(dist, -tg.z), sg);
-            acc[0] = ff_add(acc[0], ff_mul(rho.v, rho.v));
-            used += 1;
-#pragma unroll
-            for (int k = 0; k < kNG; ++k) acc[1 + k] = ff_add(acc[1 + k], ff_mul(rho.v, 2.0f * rho.d[k]));
         }
+        // the tilted tiles (0..3) the path meets: one replay per tile
+        uint32_t rest = 0;
+        for (int k = 0; k < rr.n_path; ++k)
+            if (rr.path[k] < sc.n_tiles && rr.path[k] < 4) rest |= 1u << rr.path[k];
+        bool first = true;
+        do {
+            const int pass_tile = rest ? __ffs(rest) - 1 : -1;
+            rest &= rest - 1u;
+            Dm u, v;
+            replay_dual(sc, gv, em, rr, h.photon, pass_tile, first, u, v);
+            if (first) {
+                int ix, iy;
+                pixel_of_ff(sc.rects[rr.det_rect], u.v, v.v, ix, iy);
+                h.u = ff_to_double(u.v);
+                h.v = ff_to_double(v.v);
+                h.ix = (uint16_t)ix;
+                h.iy = (uint16_t)iy;
+                P.hits[i] = h;
+                bin_hit(sc, P, h.event, h.plane, ix, iy);
+            }
+            if (tg.w > 0.0f) {
+                const Dm du = dm_addf(dm_addf(u, -tg.x), sg.hi * g1);
+                const Dm dv = dm_addf(dm_addf(v, -tg.y), sg.hi * g2);
+                const Dm dist = dm_sqrt(dm_add(dm_mul(du, du), dm_mul(dv, dv)));
+                const Dm rho = dm_divc(dm_addf(dist, -tg.z), sg);
+                if (first) {
+                    acc[0] = ff_add(acc[0], ff_mul(rho.v, rho.v));
+                    used += 1;
+                    acc[1 + 8] = ff_add(acc[1 + 8], ff_mul(rho.v, 2.0f * rho.d[2]));
+                    acc[1 + 9] = ff_add(acc[1 + 9], ff_mul(rho.v, 2.0f * rho.d[3]));
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (q == pass_tile) {
+                        acc[1 + 2 * q] = ff_add(acc[1 + 2 * q], ff_mul(rho.v, 2.0f * rho.d[0]));
+                        acc[2 + 2 * q] = ff_add(acc[2 + 2 * q], ff_mul(rho.v, 2.0f * rho.d[1]));
+                    }
+                }
+            }
+            first = false;
+        } while (rest);
     }
     // block reduction, one FP64 atomic per accumulator per block
-    __shared__ ff red[kAdjThreads / 32][1 + kNG];
+    __shared__ ff red[kAdjThreads / 32][1 + kNP];
     __shared__ uint32_t red_used[kAdjThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < 1 + kNG; ++k) {
+    for (int k = 0; k < 1 + kNP; ++k) {
         ff x = acc[k];
         for (int o = 16; o > 0; o >>= 1) x = ff_add(x, shfl_xor_ff(x, o));
         if (lane == 0) red[wid][k] = x;
@@ -2478,7 +2512,7 @@ k_adjoint(SceneView sc, EmitView em, TraceParams P, GradView gv, Counters *ctr) 
     for (int o = 16; o > 0; o >>= 1) used += __shfl_xor_sync(kFull, used, o);
     if (lane == 0) red_used[wid] = used;
     __syncthreads();
-    if (threadIdx.x < 2 + kNG) {
+    if (threadIdx.x < 2 + kNP) {
         double x = 0.0;
         if (threadIdx.x == 1) {
             uint32_t n = 0;
