@@ -276,6 +276,35 @@ def point_source_scene(radius=2710.0, half_aperture=0.3, n_pix=256,
     return b.build()
 
 
+def two_mirror_scene(radius=20000.0, n_pix=256, pitch=PIXEL_PITCH) -> Scene:
+    """A periscope of two analytic concave tiles: light from the origin along
+    +z meets tile 0 (pole (0, 0, 1000) mm, turned 45 degrees so that it sends
+    the light along +y), then tile 1 (pole (0, 1000, 1000), sending it along
+    +z again), then a plane at z = 2000 facing it. Every detected photon's
+    path meets both tilted tiles (the gradient's several-tile case); R = 0.9,
+    QE = 0.3 exp(-((l-400)/120)^2)."""
+    b = _Builder("two_mirror")
+    t_qe = b.table_gauss(0.3, 400.0, 120.0)
+    t_r = b.table_const(0.9)
+    m_mirror = b.material(MAT_MIRROR, t_r)
+    m_det = b.material(MAT_DETECTOR, t_qe, plane=0)
+    s2 = 1.0 / math.sqrt(2.0)
+    e1 = np.array([1.0, 0.0, 0.0])
+    for pole, towards_centre in (((0.0, 0.0, 1000.0), (0.0, s2, -s2)),
+                                 ((0.0, 1000.0, 1000.0), (0.0, -s2, s2))):
+        n = np.asarray(towards_centre)
+        centre = np.asarray(pole) + radius * n
+        axis = -n                                  # centre -> pole
+        b.sphere(center=centre, radius=radius, axis=axis, e1=e1, e2=np.cross(axis, e1),
+                 material=m_mirror, cos_min=math.cos(0.02))
+    half = n_pix * pitch / 2.0
+    # u x v = -z: the plane faces the light arriving along +z
+    b.rect(origin=(-half, 1000.0 - half, 2000.0), u_axis=(0.0, 1.0, 0.0),
+           v_axis=(1.0, 0.0, 0.0), width=n_pix * pitch, height=n_pix * pitch,
+           material=m_det, nx=n_pix, ny=n_pix, pitch=pitch)
+    return b.build()
+
+
 # ------------------------------------------------------- folded RICH layout
 def _reflect_point(p, plane_point, plane_normal):
     p = np.asarray(p, np.float64)
@@ -729,6 +758,12 @@ def point_source_muon(n_photons=600_000) -> Workload:
                     muon_point_tracks(n_photons), n_minus_1=0.0014,
                     description=f"{n_photons} photons from one 100 GeV/c muon at the "
                     "centre of curvature of an R=2710 mm sphere, n=1.0014")
+
+
+def two_mirror(n_photons=20_000) -> Workload:
+    return Workload("two_mirror", two_mirror_scene(), point_source_tracks(n_photons),
+                    n_minus_1=0.0014, description=f"{n_photons} photons from a point "
+                    "through a periscope of two tilted analytic tiles")
 
 
 def rich1(n_tracks=1000, seed=0, meshed=True) -> Workload:

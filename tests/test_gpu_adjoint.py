@@ -182,3 +182,32 @@ def test_autograd_function_and_descent(setup):
         losses.append(float(lo))
     _report("adjoint_descent", {"losses": losses})
     assert losses[-1] < losses[0]
+
+
+def test_adjoint_two_tilted_tiles_per_path():
+    """Every detected photon of the periscope scene reflects off two tilted
+    tiles, so each hit takes a second replay for the second tile's tilts:
+    the four tilt components of both tiles, R and n - 1 against the oracle."""
+    wl = W.two_mirror(20_000)
+    sc = oracle.Scene(wl.scene)
+    prm = oracle.params(wl)
+    nom = sc.trace(wl.tracks, prm)
+    det = nom["fate"] == 5
+    assert det.sum() > 1000 and np.all(nom["n_refl"][det] == 2)
+    tg = W.ring_targets(1, 1, np.zeros(int(det.sum()), np.int64), nom["plane"][det],
+                        nom["u"][det], nom["v"][det])
+    th = W.nominal_theta(wl.scene, wl.n_minus_1)
+    th[:4] = [2e-3, -1e-3, 1.5e-3, 0.5e-3]
+    th32 = np.float32(th).astype(np.float64)
+    ctx = rich.Context(0)
+    ctx.init_geometry(wl.scene)
+    dt = rich.DeviceTracks(wl.tracks)
+    n = int(nom["offsets"][-1])
+    out = rich.TraceOutputs(n, wl.scene.pixels_per_event, 1, 1, n)
+    loss_g, grad_g, used_g = ctx.trace_grad(dt, th32, torch.from_numpy(tg).cuda(), out,
+                                            sigma=1.0, seed=wl.seed)
+    ctx.close()
+    loss_o, grad_o, _, used_o = sc.grad(wl.tracks, prm, th32, tg, sigma=1.0)
+    assert np.all(np.abs(grad_o[:4]) > 1e2) and np.all(grad_o[4:8] == 0.0)
+    _check_gradient(loss_g, grad_g, used_g, loss_o, grad_o, used_o, "adjoint_two_tiles",
+                    "tilted")
