@@ -68,7 +68,7 @@ struct rich_ctx {
     // azimuth order of each track's photons (sized from the last photon
     // total the host has seen; an emission that does not fit keeps index
     // order, flagged on the device)
-    uint32_t *d_perm = nullptr;
+    uint2 *d_perm = nullptr;
     uint64_t perm_cap = 0;
     uint32_t *d_perm_ok = nullptr;
     uint64_t known_total = 0;
@@ -410,7 +410,7 @@ rich_status emit_core(rich_ctx *ctx, const rich_tracks *t, uint64_t seed, float 
                                YieldModel{source == RICH_SOURCE_ISOTROPIC ? (double)yield_per_mm
                                                                           : -1.0,
                                           dispersion, disp_a, disp_lambda0},
-                               ctx->d_frame));
+                               ctx->d_frame, ctx->d_perm_ok));
         // deferred: the ordering pass (order_photons, which the caller
         // runs next) does the scan
         ctx->scan_pending = defer_scan && n <= kOrderScanMaxTracks;
@@ -439,7 +439,7 @@ rich_status order_photons(rich_ctx *ctx) {
         cudaFree(ctx->d_perm);
         ctx->d_perm = nullptr;
         ctx->perm_cap = 0;
-        RICH_CUDA(cudaMalloc(&ctx->d_perm, sizeof(uint32_t) * want));
+        RICH_CUDA(cudaMalloc(&ctx->d_perm, sizeof(uint2) * want));
         ctx->perm_cap = want;
     }
     const EmitView em = emit_view(ctx);

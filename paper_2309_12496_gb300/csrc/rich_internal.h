@@ -159,7 +159,9 @@ struct EmitView {            // result of rich_emit used by the trace
     int64_t n_tracks;
     uint32_t key0, key1;
     float inv1, span;         // FP32 1/lambda_min and 1/lambda_min - 1/lambda_max
-    const uint32_t *perm;     // per track, photon indices in azimuth order, or null
+    const uint2 *perm;        // per queue entry: (photon index in its track, track
+                              // index), each track's photons in azimuth order; entries
+                              // of tracks above kOrderMaxPhotons are not written; or null
     const uint32_t *perm_ok;  // device flag: perm covers this emission
     int32_t source;           // RICH_SOURCE_*
     int32_t spectrum;         // isotropic: CDF table index of the scene, or -1
@@ -249,7 +251,7 @@ cudaError_t launch_yield(const TracksView &t, double n_minus_1,
                          uint32_t key1, TrackRec *rec, float4 *cs,
                          uint32_t *counts, unsigned long long *block_sums,
                          cudaStream_t s, const YieldModel &model,
-                         TrackFrame *frame = nullptr);
+                         TrackFrame *frame = nullptr, uint32_t *perm_ok = nullptr);
 cudaError_t launch_offsets(const uint32_t *counts,
                            const unsigned long long *block_sums,
                            int64_t n_tracks, uint64_t *offsets,
@@ -270,7 +272,7 @@ struct OrderScan {
     uint64_t *offsets;             // n + 1 entries, written
     unsigned long long *total;     // written
 };
-cudaError_t launch_order(const EmitView &em, uint32_t *perm, uint64_t cap, uint32_t *perm_ok,
+cudaError_t launch_order(const EmitView &em, uint2 *perm, uint64_t cap, uint32_t *perm_ok,
                          int n_sm, cudaStream_t s, const OrderScan *scan = nullptr);
 cudaError_t launch_materialize(const SceneView &sc, const EmitView &em,
                                uint64_t n, const rich_photons &out,

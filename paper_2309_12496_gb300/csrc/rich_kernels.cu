@@ -383,8 +383,10 @@ __global__ void __launch_bounds__(kYieldBlock)
 k_yield(TracksView t, ff nm1, ff inv_band, uint32_t key0,
         uint32_t key1, TrackRec *rec, float4 *cs, uint32_t *counts,
         unsigned long long *block_sums, YieldModel model, double lam_min, double lam_max,
-        TrackFrame *frame) {
+        TrackFrame *frame, uint32_t *perm_ok) {
     grid_dep_launch_dependents();        // the ordering pass may be scheduled
+    // the ordering pass of this emission ORs its flags into a zeroed word
+    if (perm_ok && blockIdx.x == 0 && threadIdx.x == 0) *perm_ok = 0u;
     // kYieldLanes consecutive lanes per track; lane 0 of each group writes
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t i = gt / kYieldLanes;
@@ -557,7 +559,7 @@ constexpr uint32_t kOrderBinCache = 8192;
 // track's warp adds the counts before it in its group and writes its
 // offset (block 0 writes offsets[n] and the total).
 template <bool SCAN>
-__global__ void __launch_bounds__(32 * kOrderWarps) k_order(EmitView em, uint32_t *perm,
+__global__ void __launch_bounds__(32 * kOrderWarps) k_order(EmitView em, uint2 *perm,
                                                             uint64_t cap, uint32_t *perm_ok,
                                                             OrderScan scan, bool signal_early) {
     grid_dep_wait();                     // the yield (and scan) pass has ended
@@ -599,8 +601,11 @@ __global__ void __launch_bounds__(32 * kOrderWarps) k_order(EmitView em, uint32_
         total = *em.total;
     }
     const bool fits = total <= cap;
+    // perm_ok (zeroed by the yield pass): bit 0 the entries fit the buffer,
+    // bit 1 a track above kOrderMaxPhotons kept index order (its entries are
+    // not written)
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        *perm_ok = fits ? 1u : 0u;
+        if (fits) atomicOr(perm_ok, 1u);
         if (SCAN) {
             *scan.total = total;
             scan.offsets[em.n_tracks] = total;
@@ -632,6 +637,7 @@ __global__ void __launch_bounds__(32 * kOrderWarps) k_order(EmitView em, uint32_
             off = em.offsets[t];
             n64 = em.offsets[t + 1] - off;
         }
+        if (fits && n64 > kOrderMaxPhotons && threadIdx.x == 0) atomicOr(perm_ok, 2u);
         if (fits && n64 != 0 && n64 <= kOrderMaxPhotons) {   // uniform in the block
             const uint32_t n = (uint32_t)n64;
             const uint32_t id = em.tracks[t].id, ev = em.tracks[t].event;
@@ -658,14 +664,14 @@ __global__ void __launch_bounds__(32 * kOrderWarps) k_order(EmitView em, uint32_
                 const uint32_t bin = j < kOrderBinCache
                                          ? (uint32_t)bins[j]
                                          : philox10(0u, j, id, ev, em.key0, em.key1).y >> 27;
-                perm[off + atomicAdd(&hist[bin], 1u)] = j;
+                perm[off + atomicAdd(&hist[bin], 1u)] = make_uint2(j, (uint32_t)t);
             }
         }
         __syncthreads();                 // the shared histogram and bins are reused
     }
 }
 
-cudaError_t launch_order(const EmitView &em, uint32_t *perm, uint64_t cap, uint32_t *perm_ok,
+cudaError_t launch_order(const EmitView &em, uint2 *perm, uint64_t cap, uint32_t *perm_ok,
                          int n_sm, cudaStream_t s, const OrderScan *scan) {
     int64_t blocks = em.n_tracks;                       // one block per track
     if (blocks < 1) blocks = 1;
@@ -1707,7 +1713,12 @@ k_trace(TraceArgs A) {
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     const bool has_tri = sc.n_tris > 0;
-    const bool ordered = !EXT && em.perm && *em.perm_ok;
+    // order flags of the emission: bit 0 its queue entries are ordered; the
+    // word equal to 1 (no track left in index order) makes every entry hold
+    // its photon and track
+    const uint32_t order_flags = (!EXT && em.perm) ? *em.perm_ok : 0u;
+    const bool ordered = (order_flags & 1u) != 0u;
+    const bool entries = order_flags == 1u;
     if (blockIdx.x == 0 && threadIdx.x == 0) A.ctr->ordered = ordered ? 1u : 0u;
 
     Photon ph;
@@ -1761,28 +1772,41 @@ k_trace(TraceArgs A) {
                     }
                     pool_next = base;
                     pool_end = base + chunk < N ? base + chunk : N;
-                    if (!EXT) {
-                        // 32-ary search for the track containing pool_next
-                        int64_t lo = 0, hi = em.n_tracks;
-                        while (hi - lo > 32) {
-                            const int64_t step = (hi - lo + 31) / 32;
-                            const int64_t idx = lo + lane * step;
-                            const bool ok = idx < hi && em.offsets[idx] <= pool_next;
-                            const unsigned m = __ballot_sync(kFull, ok);
-                            const int L = 31 - __clz(m);
-                            lo = lo + L * step;
-                            hi = (lo + step < hi) ? lo + step : hi;
-                        }
-                        const int64_t idx = lo + lane;
-                        const bool ok = idx < hi && em.offsets[idx] <= pool_next;
-                        const unsigned m = __ballot_sync(kFull, ok);
-                        pool_track = lo + (31 - __clz(m));
-                    }
+                    // the track of pool_next: found below when a lane needs it
+                    pool_track = -1;
                 }
                 const int rank = __popc(idle & lt_mask);
                 const uint64_t avail = pool_end - pool_next;
                 const bool take = ((idle >> lane) & 1u) && (uint64_t)rank < avail;
-                int64_t my_track = pool_track;
+                // when every track was ordered, the queue entry names the
+                // photon and its track (no search for the track)
+                bool from_entry = false;
+                uint32_t j_entry = 0;
+                int64_t entry_track = 0;
+                if (!EXT && take && entries) {
+                    const uint2 e = em.perm[pool_next + (uint64_t)rank];
+                    from_entry = true;
+                    j_entry = e.x;
+                    entry_track = (int64_t)e.y;
+                }
+                if (!EXT && pool_track < 0 && __any_sync(kFull, take && !from_entry)) {
+                    // 32-ary search for the track containing pool_next
+                    int64_t lo = 0, hi = em.n_tracks;
+                    while (hi - lo > 32) {
+                        const int64_t step = (hi - lo + 31) / 32;
+                        const int64_t idx = lo + lane * step;
+                        const bool ok = idx < hi && em.offsets[idx] <= pool_next;
+                        const unsigned m = __ballot_sync(kFull, ok);
+                        const int L = 31 - __clz(m);
+                        lo = lo + L * step;
+                        hi = (lo + step < hi) ? lo + step : hi;
+                    }
+                    const int64_t idx = lo + lane;
+                    const bool ok = idx < hi && em.offsets[idx] <= pool_next;
+                    const unsigned m = __ballot_sync(kFull, ok);
+                    pool_track = lo + (31 - __clz(m));
+                }
+                int64_t my_track = from_entry ? entry_track : pool_track;
                 bool rejected = false;
                 if (take) {
                     const uint64_t g = pool_next + (uint64_t)rank;
@@ -1809,14 +1833,16 @@ k_trace(TraceArgs A) {
                             ph.wr0 = w1.x; ph.wr1 = w1.y; ph.wr2 = w1.z; ph.wr3 = w1.w;
                         }
                     } else {
-                        while (my_track + 1 < em.n_tracks && em.offsets[my_track + 1] <= g)
-                            ++my_track;
+                        if (!from_entry)
+                            while (my_track + 1 < em.n_tracks && em.offsets[my_track + 1] <= g)
+                                ++my_track;
                         ph.track = (uint32_t)my_track;
                         const TrackRec tr = em.tracks[my_track];
                         const uint64_t toff = em.offsets[my_track];
-                        uint32_t j = (uint32_t)(g - toff);
-                        if (ordered && em.offsets[my_track + 1] - toff <= kOrderMaxPhotons)
-                            j = em.perm[g];
+                        uint32_t j = from_entry ? j_entry : (uint32_t)(g - toff);
+                        // some tracks in index order: the ordered ones' entries
+                        if (!from_entry && ordered && em.offsets[my_track + 1] - toff <= kOrderMaxPhotons)
+                            j = em.perm[g].x;
                         ph.g = toff + j;
                         const u4 w0 = philox10(0u, j, tr.id, tr.event, em.key0, em.key1);
                         const DevTable *spec = em.spectrum >= 0 ? S.tables() + em.spectrum : nullptr;
@@ -2564,7 +2590,8 @@ cudaError_t launch_yield(const TracksView &t, double n_minus_1,
                          double lam_min, double lam_max, uint32_t key0,
                          uint32_t key1, TrackRec *rec, float4 *cs,
                          uint32_t *counts, unsigned long long *block_sums,
-                         cudaStream_t s, const YieldModel &model, TrackFrame *frame) {
+                         cudaStream_t s, const YieldModel &model, TrackFrame *frame,
+                         uint32_t *perm_ok) {
     if (t.n <= 0) return cudaSuccess;
     const double inv_band_mm = 1.0e6 / lam_min - 1.0e6 / lam_max;
     // the kernel's double-word parameters, split here
@@ -2577,11 +2604,11 @@ cudaError_t launch_yield(const TracksView &t, double n_minus_1,
     if (rec)
         k_yield<true><<<blocks, kYieldBlock, 0, s>>>(t, nm1, inv_band, key0, key1,
                                                      rec, cs, counts, block_sums, model,
-                                                     lam_min, lam_max, frame);
+                                                     lam_min, lam_max, frame, perm_ok);
     else
         k_yield<false><<<blocks, kYieldBlock, 0, s>>>(t, nm1, inv_band, key0, key1,
                                                       rec, cs, counts, block_sums, model,
-                                                      lam_min, lam_max, nullptr);
+                                                      lam_min, lam_max, nullptr, perm_ok);
     return cudaGetLastError();
 }
 
