@@ -86,7 +86,7 @@ WORK_COST = {
     "detected": {"fp32": 3 + 10 + 2 + 2, "minmax": 0, "mufu": 0},
 }
 # bytes each tallied event reads or writes outside shared memory
-BYTES = {"node": 128, "tri": 48, "normal": 36, "track": 64, "perm": 4, "hit": 40,
+BYTES = {"node": 128, "tri": 48, "normal": 36, "track": 64, "perm": 8, "hit": 40,
          "refine_rec": 40}
 
 
