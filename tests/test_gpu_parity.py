@@ -306,6 +306,39 @@ def test_azimuth_order_changes_nothing():
         np.testing.assert_array_equal(res[False][k], res[True][k])
 
 
+def test_mixed_track_sizes_order_invariant():
+    """Tracks above 16,384 photons keep index order while the others are
+    ordered by azimuth; with both kinds in one emission the trace finds each
+    photon's track by search and takes the ordered tracks' photons from
+    their queue entries. Fates, hits and pixel counts equal those of the
+    same photons traced in index order (a fresh context emitting without
+    synchronising)."""
+    tracks = W.pion_tracks(6, seed=11, n_fixed=100)
+    tracks.n_fixed[:] = [20_000, 300, 17_000, 1_000, 50, 4_000]
+    scene = W.rich1_scene(meshed=True)
+    res = {}
+    for sync in (False, True):
+        ctx = rich.Context(0)
+        ctx.init_geometry(scene)
+        dt = rich.DeviceTracks(tracks)
+        if sync:
+            n = int(ctx.emit(dt, 0.0014, seed=2, sync=True))
+        else:
+            ctx.emit(dt, 0.0014, seed=2, sync=False)
+            n = 50_000
+        out = rich.TraceOutputs(n, scene.pixels_per_event, len(scene.planes), 1, n)
+        ctx.trace(out, precision=rich.PREC_REFINE64)
+        nh, st = ctx.hits()
+        res[sync] = (st["photon_order"], st["n_photons"], out.fate[: st["n_photons"]].cpu().numpy(),
+                     np.sort(out.hits_numpy(nh), order=["event", "track", "photon"]),
+                     out.pixel_counts_numpy())
+        ctx.close()
+    assert res[False][0] == 0 and res[True][0] == 1
+    assert res[False][1] == res[True][1] == 42_350
+    for k in (2, 3, 4):
+        np.testing.assert_array_equal(res[False][k], res[True][k])
+
+
 def test_deferred_scan_matches_scan_pass():
     """An unsynchronised emission leaves the count scan to the ordering pass
     (offsets and total from the group sums); a synchronised one runs the
